@@ -1,0 +1,693 @@
+// FP64 CPU oracle for the skew-Gaussian tile rasterizer.
+//
+// TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+// call this file; only the tests, the smoke check and the CPU-baseline leg of
+// the benchmark do.  It shares no code, header, table or constant with the
+// CUDA library: every formula below is written out again from the paper.
+//
+// What it computes, and where the paper defines it:
+//   * camera set-up: OpenGL->OpenCV alignment M_cv = M_gl * diag(1,-1,-1,1)
+//     (Eq. coord_transform, Alg. 3) and the intrinsics K from W, H and the
+//     field of view (the K matrix of Sec. "Decoupled Interactive Visual
+//     Analytics Engine");
+//   * per-Gaussian projection: Sigma = R S S^T R^T from quaternion and scale
+//     (Preliminaries, Eq. 1), local-affine (EWA) projection to Sigma'
+//     (Preliminaries), dilation Sigma'+sI with the compensation
+//     sqrt(det Sigma' / det(Sigma'+sI)) and the conic (a,b,c)
+//     (Appendix "Forward Pass", the alpha expansion and the (a,b,c,d)
+//     definitions), the projected skew vector (beta_x, beta_y) (Alg. 1
+//     inputs; the 3D->2D rule is the skew-normal marginal, see below), the
+//     enhanced opacity o(x) (Eq. alpha, second form) and the SH colour
+//     (Preliminaries);
+//   * the per-pixel skew kernel alpha = d * G'(x) * (1 + erf(z)) (Alg. 1,
+//     Appendix alpha expansion) and front-to-back compositing
+//     C = sum_i c_i alpha_i prod_{j<i}(1-alpha_j) (Eq. 2, Eq. color);
+//   * gradients: the plain derivative of that composite, dC/dalpha_k
+//     (Appendix "Backward Pass", dL/dalpha_k), and of alpha and of the
+//     projection with respect to every attribute, obtained by forward-mode
+//     dual numbers applied to the same definitions (the paper defers the
+//     projection backward to 3DGS: Appendix "Backward Pass").
+//
+// Readings where the paper is silent or ambiguous (kept identical on the
+// CUDA side, and pinned by tests against mathematics rather than code):
+//   * skew projection: with the stored skew eta in the Gaussian's standardised
+//     local frame, the 3D skew normal has delta_3 = R S eta / sqrt(1+|eta|^2);
+//     under the local-affine camera delta_2 = T eta / sqrt(1+|eta|^2) with
+//     T = J W R S, and beta_2 = Sd^-1 delta_2 / sqrt(1 - delta_2^T Sd^-1 delta_2)
+//     (closure of the skew-normal family under linear maps, Azzalini &
+//     Capitanio 1999).  Dilation adds independent N(0, sI).
+//   * factor 2: alpha uses (1 + erf z) = 2 Phi, as in Alg. 1.
+//   * footprint: conservative ellipse rho^2 = 2 ln(kappa o_max comp / tau)
+//     with kappa = 1 + erf(rho0 sqrt(beta^T Sd beta) / sqrt 2),
+//     rho0^2 = 2 ln(2 o_max comp / tau), enlarged by (1 + 2^-10).
+//   * depth order key: FP32 camera z computed as ((w20 x + w21 y) + w22 z) + w23
+//     with every operation rounded to FP32 and no fused multiply-add; ties
+//     broken by Gaussian index.
+//   * alpha is clamped to alpha_max, gated by alpha_min, and the Gaussian whose
+//     transmittance would fall below T_stop is not blended (stop before it).
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+extern "C" {
+
+struct OrCamera {            // values are the FP32-rounded camera, held in FP64
+  double w2c[12];            // row-major 3x4 world-to-camera (OpenCV: +Z forward, +Y down)
+  double fx, fy, cx, cy;     // intrinsics K
+  double tan_fovx, tan_fovy; // tan(FoV/2)
+  double campos[3];          // camera centre in world space
+  int32_t width, height;
+};
+
+struct OrConfig {
+  int32_t tile_w, tile_h;
+  double alpha_min, alpha_max, t_stop, dilation, fov_clamp, near_z;
+  double bg[3];
+  int32_t antialias_comp;
+  int32_t pad_;
+};
+
+struct OrScene {
+  int64_t n;
+  const double* means;       // [n,3]
+  const double* log_scales;  // [n,3]
+  const double* quats;       // [n,4] (w,x,y,z), not normalised
+  const double* opac;        // [n] or [n,2] logits
+  const double* skew;        // [n,3] eta
+  const double* split;       // [n,3] or null
+  const double* sh;          // [n,K,3]
+  int32_t two_opac;
+  int32_t sh_degree;
+};
+
+}  // extern "C"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Forward-mode dual numbers.  Used only to differentiate the definitions
+// below; D is the number of seeded input directions.
+// ---------------------------------------------------------------------------
+template <int D>
+struct Dual {
+  double v;
+  double d[D];
+  Dual() : v(0.0) { std::fill(d, d + D, 0.0); }
+  Dual(double x) : v(x) { std::fill(d, d + D, 0.0); }  // NOLINT: implicit constant
+};
+
+template <int D> Dual<D> operator+(const Dual<D>& a, const Dual<D>& b) {
+  Dual<D> r(a.v + b.v); for (int i = 0; i < D; ++i) r.d[i] = a.d[i] + b.d[i]; return r; }
+template <int D> Dual<D> operator-(const Dual<D>& a, const Dual<D>& b) {
+  Dual<D> r(a.v - b.v); for (int i = 0; i < D; ++i) r.d[i] = a.d[i] - b.d[i]; return r; }
+template <int D> Dual<D> operator-(const Dual<D>& a) {
+  Dual<D> r(-a.v); for (int i = 0; i < D; ++i) r.d[i] = -a.d[i]; return r; }
+template <int D> Dual<D> operator*(const Dual<D>& a, const Dual<D>& b) {
+  Dual<D> r(a.v * b.v); for (int i = 0; i < D; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i]; return r; }
+template <int D> Dual<D> operator/(const Dual<D>& a, const Dual<D>& b) {
+  Dual<D> r(a.v / b.v);
+  for (int i = 0; i < D; ++i) r.d[i] = (a.d[i] * b.v - a.v * b.d[i]) / (b.v * b.v);
+  return r; }
+template <int D> Dual<D> operator+(const Dual<D>& a, double b) { return a + Dual<D>(b); }
+template <int D> Dual<D> operator+(double a, const Dual<D>& b) { return Dual<D>(a) + b; }
+template <int D> Dual<D> operator-(const Dual<D>& a, double b) { return a - Dual<D>(b); }
+template <int D> Dual<D> operator-(double a, const Dual<D>& b) { return Dual<D>(a) - b; }
+template <int D> Dual<D> operator*(const Dual<D>& a, double b) { return a * Dual<D>(b); }
+template <int D> Dual<D> operator*(double a, const Dual<D>& b) { return Dual<D>(a) * b; }
+template <int D> Dual<D> operator/(const Dual<D>& a, double b) { return a / Dual<D>(b); }
+template <int D> Dual<D> operator/(double a, const Dual<D>& b) { return Dual<D>(a) / b; }
+
+// chain rule for a scalar function f with value fv and derivative fp at a.v
+template <int D> Dual<D> apply(const Dual<D>& a, double fv, double fp) {
+  Dual<D> r(fv); for (int i = 0; i < D; ++i) r.d[i] = fp * a.d[i]; return r; }
+template <int D> Dual<D> exp(const Dual<D>& a) { double e = std::exp(a.v); return apply(a, e, e); }
+template <int D> Dual<D> log(const Dual<D>& a) { return apply(a, std::log(a.v), 1.0 / a.v); }
+template <int D> Dual<D> sqrt(const Dual<D>& a) { double s = std::sqrt(a.v); return apply(a, s, 0.5 / s); }
+// d/dx erf(x) = 2/sqrt(pi) exp(-x^2)  (Appendix, derivative of erf)
+template <int D> Dual<D> erf(const Dual<D>& a) {
+  return apply(a, std::erf(a.v), 2.0 / std::sqrt(M_PI) * std::exp(-a.v * a.v)); }
+
+inline double value(double x) { return x; }
+template <int D> double value(const Dual<D>& x) { return x.v; }
+
+using std::erf;
+using std::exp;
+using std::log;
+using std::sqrt;
+
+// clamp / max with the derivative of the branch that is taken
+template <class S> S clamp_to(const S& x, double lo, double hi) {
+  if (value(x) < lo) return S(lo);
+  if (value(x) > hi) return S(hi);
+  return x;
+}
+template <class S> S relu(const S& x) { return value(x) < 0.0 ? S(0.0) : x; }
+template <class S> S sigmoid(const S& x) { return 1.0 / (1.0 + exp(-x)); }
+
+// ---------------------------------------------------------------------------
+// Real spherical harmonics up to degree 3, evaluated on a unit direction.
+// Normalisation N_lm = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!), real form
+// sqrt(2) N_lm P_l^|m|(cos th) {cos, sin}(|m| phi) with the Condon-Shortley
+// phase, ordered m = -l..l.  Written as polynomials in (x, y, z).
+// ---------------------------------------------------------------------------
+template <class S>
+void sh_basis(int deg, const S& x, const S& y, const S& z, S* Y) {
+  const double pi = M_PI;
+  Y[0] = S(std::sqrt(1.0 / (4.0 * pi)));
+  if (deg < 1) return;
+  const double c1 = std::sqrt(3.0 / (4.0 * pi));
+  Y[1] = -c1 * y;
+  Y[2] = c1 * z;
+  Y[3] = -c1 * x;
+  if (deg < 2) return;
+  const double c2a = 0.5 * std::sqrt(15.0 / pi);
+  const double c2b = 0.25 * std::sqrt(5.0 / pi);
+  const double c2c = 0.25 * std::sqrt(15.0 / pi);
+  Y[4] = c2a * x * y;
+  Y[5] = -c2a * y * z;
+  Y[6] = c2b * (2.0 * z * z - x * x - y * y);
+  Y[7] = -c2a * x * z;
+  Y[8] = c2c * (x * x - y * y);
+  if (deg < 3) return;
+  const double c3a = 0.25 * std::sqrt(35.0 / (2.0 * pi));
+  const double c3b = 0.5 * std::sqrt(105.0 / pi);
+  const double c3c = 0.25 * std::sqrt(21.0 / (2.0 * pi));
+  const double c3d = 0.25 * std::sqrt(7.0 / pi);
+  const double c3e = 0.25 * std::sqrt(105.0 / pi);
+  Y[9] = -c3a * y * (3.0 * x * x - y * y);
+  Y[10] = c3b * x * y * z;
+  Y[11] = -c3c * y * (4.0 * z * z - x * x - y * y);
+  Y[12] = c3d * z * (2.0 * z * z - 3.0 * x * x - 3.0 * y * y);
+  Y[13] = -c3c * x * (4.0 * z * z - x * x - y * y);
+  Y[14] = c3e * z * (x * x - y * y);
+  Y[15] = -c3a * x * (x * x - 3.0 * y * y);
+}
+
+// Record of one projected Gaussian.  The first NDIFF entries are the 2D
+// quantities the per-pixel kernel consumes (and that gradients flow through).
+enum {
+  R_MX, R_MY,           // projected centre mu_2 (pixels)
+  R_A, R_B, R_C,        // conic (Sigma' + sI)^-1 = [[a,b],[b,c]]
+  R_BX, R_BY,           // projected skew vector beta_2
+  R_M, R_H,             // enhanced opacity o(delta) = m + h erf(u_2^T delta / sqrt 2)
+  R_UX, R_UY,           // u_2 = beta_2 + P(d)
+  R_CR, R_CG, R_CB,     // colour
+  NDIFF,
+  R_COMP = NDIFF,       // sqrt(det Sigma' / det(Sigma'+sI))
+  R_O1, R_O2,           // base opacities
+  R_TZ,                 // FP64 camera z
+  R_DXX, R_DXY, R_DYY,  // Sigma' + sI
+  NREC
+};
+
+constexpr int NPARAM = 18;  // mu 3, log_s 3, quat 4, logits 2, eta 3, d 3
+enum { P_MU = 0, P_LS = 3, P_Q = 6, P_L = 10, P_ETA = 12, P_D = 15 };
+
+// FP32 depth key, exactly as specified: every product and sum rounded to
+// FP32, no fused multiply-add (this file is compiled with -ffp-contract=off).
+inline float depth_f32(const OrCamera& c, const double* mu) {
+  volatile float w0 = (float)c.w2c[8], w1 = (float)c.w2c[9], w2 = (float)c.w2c[10], w3 = (float)c.w2c[11];
+  volatile float x = (float)mu[0], y = (float)mu[1], z = (float)mu[2];
+  volatile float p0 = w0 * x;
+  volatile float p1 = w1 * y;
+  volatile float s0 = p0 + p1;
+  volatile float p2 = w2 * z;
+  volatile float s1 = s0 + p2;
+  volatile float s2 = s1 + w3;
+  return s2;
+}
+
+// Projection of one Gaussian (Preliminaries; Appendix "Forward Pass").
+// theta holds the NPARAM differentiable attributes; sh the (deg+1)^2 x 3
+// colour coefficients (colour is linear in them).  Writes NREC entries.
+template <class S>
+void project(const S* theta, bool two_opac, bool has_split, const double* sh, int deg,
+             const OrCamera& c, const OrConfig& cfg, S* rec) {
+  const S* mu = theta + P_MU;
+  // world -> camera
+  S t[3];
+  for (int r = 0; r < 3; ++r)
+    t[r] = c.w2c[4 * r + 0] * mu[0] + c.w2c[4 * r + 1] * mu[1] + c.w2c[4 * r + 2] * mu[2] + c.w2c[4 * r + 3];
+
+  // rotation from the normalised quaternion (w, x, y, z)
+  const S* qq = theta + P_Q;
+  S qn = sqrt(qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3]);
+  S w = qq[0] / qn, x = qq[1] / qn, y = qq[2] / qn, z = qq[3] / qn;
+  S R[3][3] = {
+      {1.0 - 2.0 * (y * y + z * z), 2.0 * (x * y - w * z), 2.0 * (x * z + w * y)},
+      {2.0 * (x * y + w * z), 1.0 - 2.0 * (x * x + z * z), 2.0 * (y * z - w * x)},
+      {2.0 * (x * z - w * y), 2.0 * (y * z + w * x), 1.0 - 2.0 * (x * x + y * y)}};
+  // M = R S, so Sigma = M M^T = R S S^T R^T (Eq. 1)
+  S M[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) M[i][j] = R[i][j] * exp(theta[P_LS + j]);
+
+  // Jacobian of the pinhole projection at t; x/z and y/z limited to the
+  // widened frustum (the local-affine approximation of the Preliminaries)
+  S txz = clamp_to(t[0] / t[2], -cfg.fov_clamp * c.tan_fovx, cfg.fov_clamp * c.tan_fovx);
+  S tyz = clamp_to(t[1] / t[2], -cfg.fov_clamp * c.tan_fovy, cfg.fov_clamp * c.tan_fovy);
+  S J[2][3] = {{c.fx / t[2], S(0.0), -c.fx * txz / t[2]},
+               {S(0.0), c.fy / t[2], -c.fy * tyz / t[2]}};
+  S T[2][3];
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 3; ++j) {
+      S acc(0.0);
+      for (int k = 0; k < 3; ++k) {
+        S jw = J[i][0] * c.w2c[0 + k] + J[i][1] * c.w2c[4 + k] + J[i][2] * c.w2c[8 + k];
+        acc = acc + jw * M[k][j];
+      }
+      T[i][j] = acc;
+    }
+  // Sigma' = T T^T
+  S sxx = T[0][0] * T[0][0] + T[0][1] * T[0][1] + T[0][2] * T[0][2];
+  S sxy = T[0][0] * T[1][0] + T[0][1] * T[1][1] + T[0][2] * T[1][2];
+  S syy = T[1][0] * T[1][0] + T[1][1] * T[1][1] + T[1][2] * T[1][2];
+  // dilation, compensation and conic (Appendix alpha expansion)
+  S dxx = sxx + cfg.dilation, dxy = sxy, dyy = syy + cfg.dilation;
+  S det_s = sxx * syy - sxy * sxy;
+  S det_d = dxx * dyy - dxy * dxy;
+  S comp = cfg.antialias_comp ? sqrt(relu(det_s) / det_d) : S(1.0);
+  S a = dyy / det_d, b = -dxy / det_d, cc = dxx / det_d;
+
+  // projected skew vector of a local-frame skew eta (skew-normal marginal)
+  auto skew2d = [&](const S* e, S* out) {
+    S nrm = 1.0 / sqrt(1.0 + e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    S d0 = (T[0][0] * e[0] + T[0][1] * e[1] + T[0][2] * e[2]) * nrm;
+    S d1 = (T[1][0] * e[0] + T[1][1] * e[1] + T[1][2] * e[2]) * nrm;
+    S w0 = a * d0 + b * d1, w1 = b * d0 + cc * d1;
+    S q = d0 * w0 + d1 * w1;
+    S r = 1.0 / sqrt(1.0 - q);
+    out[0] = w0 * r;
+    out[1] = w1 * r;
+  };
+  S beta[2], ud[2] = {S(0.0), S(0.0)};
+  skew2d(theta + P_ETA, beta);
+  if (has_split) skew2d(theta + P_D, ud);
+
+  // enhanced opacity (Eq. alpha, second form), compensation on both halves
+  S o1 = sigmoid(theta[P_L + 0]);
+  S o2 = two_opac ? sigmoid(theta[P_L + 1]) : o1;
+
+  // colour from SH at the viewing direction
+  S dv[3] = {mu[0] - c.campos[0], mu[1] - c.campos[1], mu[2] - c.campos[2]};
+  S dl = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+  S Y[16];
+  sh_basis(deg, dv[0] / dl, dv[1] / dl, dv[2] / dl, Y);
+  const int K = (deg + 1) * (deg + 1);
+  for (int ch = 0; ch < 3; ++ch) {
+    S acc(0.5);
+    for (int k = 0; k < K; ++k) acc = acc + sh[3 * k + ch] * Y[k];
+    rec[R_CR + ch] = relu(acc);
+  }
+
+  rec[R_MX] = c.fx * t[0] / t[2] + c.cx;
+  rec[R_MY] = c.fy * t[1] / t[2] + c.cy;
+  rec[R_A] = a;
+  rec[R_B] = b;
+  rec[R_C] = cc;
+  rec[R_BX] = beta[0];
+  rec[R_BY] = beta[1];
+  rec[R_M] = comp * (o1 + o2) * 0.5;
+  rec[R_H] = comp * (o1 - o2) * 0.5;
+  rec[R_UX] = beta[0] + ud[0];
+  rec[R_UY] = beta[1] + ud[1];
+  rec[R_COMP] = comp;
+  rec[R_O1] = o1;
+  rec[R_O2] = o2;
+  rec[R_TZ] = t[2];
+  rec[R_DXX] = dxx;
+  rec[R_DXY] = dxy;
+  rec[R_DYY] = dyy;
+}
+
+// Skew kernel times opacity at pixel centre (px, py) (Alg. 1 with the
+// enhanced opacity): alpha = o(delta) * exp(-1/2(a dx^2 + c dy^2) - b dx dy)
+//                             * (1 + erf((bx dx + by dy)/sqrt 2)), unclamped.
+template <class S>
+S alpha_raw(const S* r, double px, double py) {
+  S dx = px - r[R_MX], dy = py - r[R_MY];
+  S g = exp(-0.5 * (r[R_A] * dx * dx + r[R_C] * dy * dy) - r[R_B] * dx * dy);
+  S zs = (r[R_BX] * dx + r[R_BY] * dy) / std::sqrt(2.0);
+  S zu = (r[R_UX] * dx + r[R_UY] * dy) / std::sqrt(2.0);
+  S o = r[R_M] + r[R_H] * erf(zu);
+  return o * g * (1.0 + erf(zs));
+}
+
+void load_theta(const OrScene& s, int64_t i, double* th) {
+  for (int k = 0; k < 3; ++k) th[P_MU + k] = s.means[3 * i + k];
+  for (int k = 0; k < 3; ++k) th[P_LS + k] = s.log_scales[3 * i + k];
+  for (int k = 0; k < 4; ++k) th[P_Q + k] = s.quats[4 * i + k];
+  th[P_L + 0] = s.two_opac ? s.opac[2 * i] : s.opac[i];
+  th[P_L + 1] = s.two_opac ? s.opac[2 * i + 1] : 0.0;
+  for (int k = 0; k < 3; ++k) th[P_ETA + k] = s.skew[3 * i + k];
+  for (int k = 0; k < 3; ++k) th[P_D + k] = s.split ? s.split[3 * i + k] : 0.0;
+}
+
+inline int sh_count(int deg) { return (deg + 1) * (deg + 1); }
+
+// Conservative footprint and tile rectangle.  Returns false if the Gaussian
+// can reach alpha >= alpha_min nowhere.  ext = (ex, ey, rho2).
+bool footprint(const double* rec, const OrConfig& cfg, double* ext, double* cull_margin) {
+  const double tau = cfg.alpha_min;
+  const double omax = rec[R_COMP] * std::max(rec[R_O1], rec[R_O2]);
+  *cull_margin = std::fabs(2.0 * omax - tau) / tau;
+  if (2.0 * omax < tau) return false;
+  const double rho0sq = 2.0 * std::log(2.0 * omax / tau);
+  const double bx = rec[R_BX], by = rec[R_BY];
+  const double bsb = bx * bx * rec[R_DXX] + 2.0 * bx * by * rec[R_DXY] + by * by * rec[R_DYY];
+  const double kappa = 1.0 + std::erf(std::sqrt(rho0sq * bsb) / std::sqrt(2.0));
+  *cull_margin = std::min(*cull_margin, std::fabs(kappa * omax - tau) / tau);
+  if (kappa * omax < tau) return false;
+  const double rho2 = 2.0 * std::log(kappa * omax / tau) * (1.0 + 1.0 / 1024.0);
+  ext[0] = std::sqrt(rho2 * rec[R_DXX]);
+  ext[1] = std::sqrt(rho2 * rec[R_DYY]);
+  ext[2] = rho2;
+  return true;
+}
+
+// Pixels whose centre (p + 0.5) lies in [m - e, m + e], as a tile range.
+void tile_range_1d(double m, double e, int size, int tile, int* t0, int* t1) {
+  double lo = std::ceil(m - e - 0.5), hi = std::floor(m + e - 0.5);
+  lo = std::max(lo, 0.0);
+  hi = std::min(hi, (double)size - 1.0);
+  if (lo > hi) { *t0 = 0; *t1 = 0; return; }
+  *t0 = (int)lo / tile;
+  *t1 = (int)hi / tile + 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+int or_num_threads() {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+// Alg. 3: M_cv = M_gl diag(1,-1,-1,1); W2C = M_cv^-1; K from (W, H, FoV).
+// c2w_gl is row-major 4x4.  All fields are rounded to FP32 once.
+void or_camera_from_gl(const double* c2w_gl, int32_t width, int32_t height, double fovx, double fovy,
+                       OrCamera* out) {
+  double m[4][4];
+  const double flip[4] = {1.0, -1.0, -1.0, 1.0};
+  for (int r = 0; r < 4; ++r)
+    for (int k = 0; k < 4; ++k) m[r][k] = c2w_gl[4 * r + k] * flip[k];  // right-multiply by diag
+  // inverse of a rigid transform [R t; 0 1] is [R^T, -R^T t]
+  for (int r = 0; r < 3; ++r) {
+    for (int k = 0; k < 3; ++k) out->w2c[4 * r + k] = (float)m[k][r];
+    double tr = -(m[0][r] * m[0][3] + m[1][r] * m[1][3] + m[2][r] * m[2][3]);
+    out->w2c[4 * r + 3] = (float)tr;
+  }
+  const double tx = std::tan(0.5 * fovx), ty = std::tan(0.5 * fovy);
+  out->fx = (float)(width / (2.0 * tx));
+  out->fy = (float)(height / (2.0 * ty));
+  out->cx = (float)(0.5 * width);
+  out->cy = (float)(0.5 * height);
+  out->tan_fovx = (float)tx;
+  out->tan_fovy = (float)ty;
+  for (int k = 0; k < 3; ++k) out->campos[k] = (float)m[k][3];
+  out->width = width;
+  out->height = height;
+}
+
+// Project every Gaussian.  Outputs per Gaussian: rec[NREC] (FP64), the FP32
+// depth key bits, visible (0 if culled by the near plane), rect[4] tile
+// range (tx0, ty0, tx1, ty1) with tx1/ty1 exclusive, ext[3] = (ex, ey, rho2),
+// rect_ambig = 1 where an FP32 evaluation of the rectangle or of the opacity
+// cull could differ (an edge within tol_px of a pixel-centre boundary that
+// changes the tile range, or the cull test within rel 1e-5 of alpha_min).
+int or_nrec() { return NREC; }
+int or_ndiff() { return NDIFF; }
+
+void or_preprocess(const OrScene* s, const OrCamera* c, const OrConfig* cfg, double tol_px,
+                   double* rec, uint32_t* depth_bits, int32_t* visible, int32_t* rect,
+                   double* ext, int32_t* rect_ambig) {
+  const int K = sh_count(s->sh_degree);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < s->n; ++i) {
+    double th[NPARAM];
+    load_theta(*s, i, th);
+    float dz = depth_f32(*c, s->means + 3 * i);
+    uint32_t bits;
+    std::memcpy(&bits, &dz, 4);
+    depth_bits[i] = bits;
+    double* r = rec + NREC * i;
+    int32_t* rc = rect + 4 * i;
+    rc[0] = rc[1] = rc[2] = rc[3] = 0;
+    ext[3 * i] = ext[3 * i + 1] = ext[3 * i + 2] = 0.0;
+    rect_ambig[i] = 0;
+    visible[i] = dz > (float)cfg->near_z;
+    if (!visible[i]) {
+      std::fill(r, r + NREC, 0.0);
+      continue;
+    }
+    project<double>(th, s->two_opac, s->split != nullptr, s->sh + (size_t)3 * K * i, s->sh_degree, *c, *cfg, r);
+    double e[3], margin;
+    bool on = footprint(r, *cfg, e, &margin);
+    if (margin < 1e-5) rect_ambig[i] = 1;
+    if (!on) continue;
+    ext[3 * i] = e[0]; ext[3 * i + 1] = e[1]; ext[3 * i + 2] = e[2];
+    tile_range_1d(r[R_MX], e[0], c->width, cfg->tile_w, &rc[0], &rc[2]);
+    tile_range_1d(r[R_MY], e[1], c->height, cfg->tile_h, &rc[1], &rc[3]);
+    // perturb each edge by +-tol_px: a different tile range means ambiguous
+    for (int sgn = -1; sgn <= 1; sgn += 2) {
+      int a0, a1, b0, b1;
+      tile_range_1d(r[R_MX], e[0] + sgn * tol_px, c->width, cfg->tile_w, &a0, &a1);
+      tile_range_1d(r[R_MY], e[1] + sgn * tol_px, c->height, cfg->tile_h, &b0, &b1);
+      int empty0 = (rc[0] == rc[2]) || (rc[1] == rc[3]);
+      int empty1 = (a0 == a1) || (b0 == b1);
+      if (empty0 != empty1 || (!empty0 && (a0 != rc[0] || a1 != rc[2] || b0 != rc[1] || b1 != rc[3])))
+        rect_ambig[i] = 1;
+      tile_range_1d(r[R_MX] + sgn * tol_px, e[0], c->width, cfg->tile_w, &a0, &a1);
+      tile_range_1d(r[R_MY] + sgn * tol_px, e[1], c->height, cfg->tile_h, &b0, &b1);
+      empty1 = (a0 == a1) || (b0 == b1);
+      if (empty0 != empty1 || (!empty0 && (a0 != rc[0] || a1 != rc[2] || b0 != rc[1] || b1 != rc[3])))
+        rect_ambig[i] = 1;
+    }
+  }
+}
+
+// Depth order of the visible Gaussians: by (FP32 depth bits, index).
+static std::vector<int64_t> depth_order(int64_t n, const uint32_t* depth_bits, const int32_t* visible) {
+  std::vector<int64_t> order;
+  for (int64_t i = 0; i < n; ++i)
+    if (visible[i]) order.push_back(i);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int64_t a, int64_t b) { return depth_bits[a] < depth_bits[b]; });
+  return order;
+}
+
+// One pixel, brute force over every visible Gaussian in depth order (Alg. 1,
+// Eq. color).  Fills the list of blended Gaussians with their alpha, T and
+// whether alpha was clamped, and reports decision-ambiguous pairs.
+struct Blend { int64_t id; double alpha; double T; int clamped; };
+
+static void composite_pixel(const std::vector<int64_t>& order, const double* rec, const OrConfig& cfg,
+                            int px, int py, double tol_alpha, double tol_t, double* C, double* T_out,
+                            int* ambiguous, std::vector<Blend>* blended, uint64_t* signature = nullptr) {
+  double T = 1.0, acc[3] = {0.0, 0.0, 0.0};
+  int amb = 0;
+  uint64_t sig = 1469598103934665603ull;  // FNV-1a over the discrete decisions
+  const double x = px + 0.5, y = py + 0.5;
+  for (int64_t id : order) {
+    const double* r = rec + (size_t)NREC * id;
+    double a_raw = alpha_raw<double>(r, x, y);
+    double a = std::min(cfg.alpha_max, a_raw);
+    if (std::fabs(a - cfg.alpha_min) < tol_alpha) amb = 1;
+    if (a < cfg.alpha_min) continue;
+    double Tn = T * (1.0 - a);
+    if (std::fabs(Tn - cfg.t_stop) < tol_t * cfg.t_stop) amb = 1;
+    sig = (sig ^ (uint64_t)(2 * id + (a_raw > cfg.alpha_max))) * 1099511628211ull;
+    if (Tn < cfg.t_stop) { sig = (sig ^ 0xffffull) * 1099511628211ull; break; }
+    for (int ch = 0; ch < 3; ++ch) acc[ch] += r[R_CR + ch] * a * T;
+    if (blended) blended->push_back({id, a, T, a_raw > cfg.alpha_max});
+    T = Tn;
+  }
+  for (int ch = 0; ch < 3; ++ch) C[ch] = acc[ch] + T * cfg.bg[ch];
+  *T_out = T;
+  *ambiguous = amb;
+  if (signature) *signature = sig;
+}
+
+// Render a list of pixels (pix[2*j] = px, pix[2*j+1] = py).  out_rgb [n_pix,3],
+// out_T [n_pix], out_last [n_pix] (id of the last blended Gaussian or -1),
+// out_count [n_pix] (number blended), out_amb [n_pix], out_sig [n_pix] (a
+// hash of which Gaussians were blended, which were clamped and whether the
+// transmittance stop fired; may be null).
+void or_render_pixels(const OrCamera* cam, const OrConfig* cfg, int64_t n, const double* rec,
+                      const uint32_t* depth_bits, const int32_t* visible, int64_t n_pix, const int32_t* pix,
+                      double tol_alpha, double tol_t, double* out_rgb, double* out_T, int64_t* out_last,
+                      int32_t* out_count, int32_t* out_amb, uint64_t* out_sig) {
+  (void)cam;
+  std::vector<int64_t> order = depth_order(n, depth_bits, visible);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t j = 0; j < n_pix; ++j) {
+    std::vector<Blend> bl;
+    int amb;
+    composite_pixel(order, rec, *cfg, pix[2 * j], pix[2 * j + 1], tol_alpha, tol_t, out_rgb + 3 * j,
+                    out_T + j, &amb, &bl, out_sig ? out_sig + j : nullptr);
+    out_amb[j] = amb;
+    out_count[j] = (int32_t)bl.size();
+    out_last[j] = bl.empty() ? -1 : bl.back().id;
+  }
+}
+
+// Gradients of L = sum_pixels sum_ch dL_dC[pixel, ch] * C[pixel, ch] over
+// the listed pixels (dL_dC [n_pix,3]).
+//  * d2 [n, NDIFF]: dL/d(record) — the 2D quantities of Alg. 2;
+//  * the attribute gradients (same layouts as the inputs; split may be null).
+// dC/dalpha_k = c_k T_k - (sum_{i>k} c_i alpha_i T_i + T_N bg) / (1 - alpha_k),
+// the plain derivative of C = sum_i c_i alpha_i T_i + T_N bg; zero where the
+// clamp alpha_max was active.  Everything else by dual numbers.
+void or_render_backward(const OrScene* s, const OrCamera* cam, const OrConfig* cfg, const double* rec,
+                        const uint32_t* depth_bits, const int32_t* visible, int64_t n_pix, const int32_t* pix,
+                        const double* dL_dC, double* d2, double* g_means, double* g_log_scales,
+                        double* g_quats, double* g_opac, double* g_skew, double* g_split, double* g_sh) {
+  const int64_t n = s->n;
+  std::vector<int64_t> order = depth_order(n, depth_bits, visible);
+  std::fill(d2, d2 + (size_t)n * NDIFF, 0.0);
+  int nthreads = or_num_threads();
+  std::vector<std::vector<double>> acc(nthreads);
+#pragma omp parallel
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    std::vector<double>& mine = acc[tid];
+    mine.assign((size_t)n * NDIFF, 0.0);
+#pragma omp for schedule(dynamic, 8)
+    for (int64_t j = 0; j < n_pix; ++j) {
+      const double* g = dL_dC + 3 * j;
+      if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0) continue;
+      std::vector<Blend> bl;
+      double C[3], T_final;
+      int amb;
+      composite_pixel(order, rec, *cfg, pix[2 * j], pix[2 * j + 1], 0.0, 0.0, C, &T_final, &amb, &bl);
+      const int nb = (int)bl.size();
+      // suffix[k] = sum_{i>k} c_i alpha_i T_i + T_N bg  (per channel)
+      std::vector<double> suffix(3 * (nb + 1), 0.0);
+      for (int ch = 0; ch < 3; ++ch) suffix[3 * nb + ch] = T_final * cfg->bg[ch];
+      for (int k = nb - 1; k >= 0; --k) {
+        const double* r = rec + (size_t)NREC * bl[k].id;
+        for (int ch = 0; ch < 3; ++ch)
+          suffix[3 * k + ch] = suffix[3 * (k + 1) + ch] + r[R_CR + ch] * bl[k].alpha * bl[k].T;
+      }
+      const double x = pix[2 * j] + 0.5, y = pix[2 * j + 1] + 0.5;
+      for (int k = 0; k < nb; ++k) {
+        const int64_t id = bl[k].id;
+        const double* r = rec + (size_t)NREC * id;
+        double* out = mine.data() + (size_t)NDIFF * id;
+        for (int ch = 0; ch < 3; ++ch) out[R_CR + ch] += g[ch] * bl[k].alpha * bl[k].T;
+        if (bl[k].clamped) continue;
+        double dLda = 0.0;
+        for (int ch = 0; ch < 3; ++ch)
+          dLda += g[ch] * (r[R_CR + ch] * bl[k].T - suffix[3 * (k + 1) + ch] / (1.0 - bl[k].alpha));
+        Dual<11> rr[NDIFF];
+        for (int q = 0; q < NDIFF; ++q) rr[q] = Dual<11>(r[q]);
+        for (int q = 0; q < 11; ++q) rr[q].d[q] = 1.0;  // R_MX..R_UY are entries 0..10
+        Dual<11> a = alpha_raw<Dual<11>>(rr, x, y);
+        for (int q = 0; q < 11; ++q) out[q] += dLda * a.d[q];
+      }
+    }
+  }
+  for (int t = 0; t < nthreads; ++t)
+    if (!acc[t].empty())
+      for (size_t q = 0; q < (size_t)n * NDIFF; ++q) d2[q] += acc[t][q];
+
+  // chain through the projection
+  const int K = sh_count(s->sh_degree);
+  const int nop = s->two_opac ? 2 : 1;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; ++i) {
+    for (int k = 0; k < 3; ++k) { g_means[3 * i + k] = 0; g_log_scales[3 * i + k] = 0; g_skew[3 * i + k] = 0; }
+    for (int k = 0; k < 4; ++k) g_quats[4 * i + k] = 0;
+    for (int k = 0; k < nop; ++k) g_opac[nop * i + k] = 0;
+    if (g_split) for (int k = 0; k < 3; ++k) g_split[3 * i + k] = 0;
+    for (int k = 0; k < 3 * K; ++k) g_sh[(size_t)3 * K * i + k] = 0;
+    const double* gi = d2 + (size_t)NDIFF * i;
+    bool any = false;
+    for (int q = 0; q < NDIFF; ++q) any |= gi[q] != 0.0;
+    if (!any || !visible[i]) continue;
+    double th[NPARAM];
+    load_theta(*s, i, th);
+    Dual<NPARAM> thd[NPARAM];
+    for (int q = 0; q < NPARAM; ++q) { thd[q] = Dual<NPARAM>(th[q]); thd[q].d[q] = 1.0; }
+    Dual<NPARAM> r[NREC];
+    const double* shi = s->sh + (size_t)3 * K * i;
+    project<Dual<NPARAM>>(thd, s->two_opac, s->split != nullptr, shi, s->sh_degree, *cam, *cfg, r);
+    double gth[NPARAM] = {0};
+    for (int q = 0; q < NDIFF; ++q)
+      for (int p = 0; p < NPARAM; ++p) gth[p] += gi[q] * r[q].d[p];
+    for (int k = 0; k < 3; ++k) g_means[3 * i + k] = gth[P_MU + k];
+    for (int k = 0; k < 3; ++k) g_log_scales[3 * i + k] = gth[P_LS + k];
+    for (int k = 0; k < 4; ++k) g_quats[4 * i + k] = gth[P_Q + k];
+    for (int k = 0; k < nop; ++k) g_opac[nop * i + k] = gth[P_L + k];
+    for (int k = 0; k < 3; ++k) g_skew[3 * i + k] = gth[P_ETA + k];
+    if (g_split) for (int k = 0; k < 3; ++k) g_split[3 * i + k] = gth[P_D + k];
+    // colour is linear in the coefficients: dL/dsh_k = Y_k dL/drgb where unclamped
+    double dv[3] = {th[0] - cam->campos[0], th[1] - cam->campos[1], th[2] - cam->campos[2]};
+    double dl = std::sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+    double Y[16];
+    sh_basis<double>(s->sh_degree, dv[0] / dl, dv[1] / dl, dv[2] / dl, Y);
+    for (int ch = 0; ch < 3; ++ch) {
+      double pre = 0.5;
+      for (int k = 0; k < K; ++k) pre += shi[3 * k + ch] * Y[k];
+      if (pre < 0.0) continue;
+      for (int k = 0; k < K; ++k) g_sh[(size_t)3 * K * i + 3 * k + ch] = Y[k] * gi[R_CR + ch];
+    }
+  }
+}
+
+// Tile keys of one view: for each visible Gaussian with a non-empty rect, in
+// index order, one (tile | depth) key per touched tile (row-major), then a
+// stable sort.  tile_base / val_base offset the tile id and the value.
+// Returns the number of keys; writes at most cap of them.
+int64_t or_bin(int64_t n, const uint32_t* depth_bits, const int32_t* visible, const int32_t* rect, int32_t tiles_x,
+               int64_t tile_base, int64_t val_base, int64_t cap, uint64_t* keys, int64_t* vals) {
+  std::vector<std::pair<uint64_t, int64_t>> kv;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!visible[i]) continue;
+    const int32_t* r = rect + 4 * i;
+    for (int ty = r[1]; ty < r[3]; ++ty)
+      for (int tx = r[0]; tx < r[2]; ++tx) {
+        uint64_t tile = (uint64_t)(tile_base + (int64_t)ty * tiles_x + tx);
+        kv.push_back({(tile << 32) | depth_bits[i], val_base + i});
+      }
+  }
+  std::stable_sort(kv.begin(), kv.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+  int64_t m = (int64_t)kv.size();
+  for (int64_t j = 0; j < std::min(m, cap); ++j) { keys[j] = kv[j].first; vals[j] = kv[j].second; }
+  return m;
+}
+
+// Skew kernel (with o = 1, no clamp) at arbitrary offsets, for quadrature and
+// Monte-Carlo checks: out[j] = exp(-1/2 d^T A d) (1 + erf(beta^T d / sqrt 2)).
+void or_kernel_at(const double* abc, const double* beta, int64_t m, const double* dxy, double* out) {
+  double r[NREC] = {0};
+  r[R_A] = abc[0]; r[R_B] = abc[1]; r[R_C] = abc[2];
+  r[R_BX] = beta[0]; r[R_BY] = beta[1];
+  r[R_M] = 1.0;
+  for (int64_t j = 0; j < m; ++j) out[j] = alpha_raw<double>(r, dxy[2 * j] + 0.0, dxy[2 * j + 1] + 0.0);
+}
+
+// Alpha of one record at pixel centres (for footprint checks).
+void or_alpha_at(const double* rec1, int64_t m, const int32_t* pix, double* out) {
+  for (int64_t j = 0; j < m; ++j) out[j] = alpha_raw<double>(rec1, pix[2 * j] + 0.5, pix[2 * j + 1] + 0.5);
+}
+
+// SH basis (for pinning against an independent library routine).
+void or_sh_basis(int deg, int64_t m, const double* dirs, double* out) {
+  const int K = sh_count(deg);
+  for (int64_t j = 0; j < m; ++j) sh_basis<double>(deg, dirs[3 * j], dirs[3 * j + 1], dirs[3 * j + 2], out + K * j);
+}
+
+}  // extern "C"
