@@ -1,0 +1,234 @@
+/* skewraster.h — C ABI of the GB300 (sm_103a) tile rasterizer for 3D skew
+ * Gaussians (3D Skew Gaussian Splatting).
+ *
+ * The library renders N skew Gaussians into one or more views and computes
+ * gradients of a scalar loss with respect to every Gaussian attribute.  A
+ * frame is four calls, in this order, on one CUDA stream:
+ *
+ *   sr_preprocess   project each Gaussian into each view (Preliminaries,
+ *                   Eq. 1 and the EWA local-affine projection; Appendix
+ *                   "Forward Pass": dilation, compensation, conic (a,b,c)
+ *                   and o' = d; Alg. 1 inputs beta_x, beta_y; Eq. alpha for
+ *                   the enhanced opacity; SH colour), plus a conservative
+ *                   tile rectangle and the FP32 depth key;
+ *   sr_bin_sort     one (tile | depth) key per touched tile, radix-sorted
+ *                   so each tile's Gaussians are in depth order (Preliminaries:
+ *                   "tile-based ... sorted in depth"), and per-tile ranges;
+ *   sr_render_fwd   per pixel, front-to-back alpha blending of the skew
+ *                   kernel alpha = d G'(x) (1 + erf z) with early stop
+ *                   (Alg. 1, Eq. 2, Eq. color);
+ *   sr_render_bwd   reverse replay of the blend (Alg. 2, Appendix "Backward
+ *                   Pass") and the chain rule back through the projection.
+ *
+ * Conventions shared by every entry point
+ *  - Memory: the library never allocates device memory.  Every device buffer
+ *    (attributes, cameras, workspace, images, gradients) is allocated and
+ *    owned by the caller; pointers must stay valid until the stream work
+ *    that uses them has completed.  Host structs are read during the call
+ *    only.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *    default stream).  All device work is enqueued asynchronously on it;
+ *    only sr_bin_sort with a non-NULL keys_needed and sr_read_status block
+ *    the host (they read a few bytes back from the device).
+ *  - Errors: every call returns an sr_status; nothing is thrown across the
+ *    ABI.  Host-side argument checks run first and leave the device
+ *    untouched on failure.  Device-side failures (key capacity exceeded, a
+ *    bounded wait that gave up) set bits in a status word in the workspace,
+ *    read by sr_read_status (or returned by sr_bin_sort when it syncs).
+ *  - Coordinates: cameras use the OpenCV convention (+Z forward, +Y down,
+ *    +X right).  Pixel (px, py) has its centre at (px + 0.5, py + 0.5).
+ *  - Images are planar FP32, [3][H][W] per view; views are concatenated in
+ *    view order at plan.image_offset[v] floats.  Per-pixel state (t_final,
+ *    n_contrib) is [H][W] per view at plan.pixel_offset[v].
+ */
+#ifndef SKEWRASTER_H
+#define SKEWRASTER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SR_MAX_VIEWS 256
+#define SR_ABI_VERSION 1
+
+typedef enum sr_status {
+  SR_OK = 0,
+  SR_ERR_INVALID = 1,     /* bad argument: sizes, NULL pointers, degree > 3, dtype tag */
+  SR_ERR_CAPACITY = 2,    /* more tile keys than the plan's key capacity */
+  SR_ERR_CUDA = 3,        /* a CUDA runtime call failed (launch, copy) */
+  SR_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+  SR_ERR_UNSUPPORTED = 5  /* a valid request this build does not implement */
+} sr_status;
+
+/* Storage type of the SH coefficients, log-scales and skew/split vectors.
+ * Arithmetic is FP32 whatever the storage. */
+typedef enum sr_dtype { SR_F32 = 0, SR_BF16 = 1, SR_F16 = 2 } sr_dtype;
+
+/* N Gaussians, structure of arrays, device pointers, caller-owned.
+ * Row-major, element i of an [n,k] array at ptr + i*k.  Alignment: each
+ * pointer 16-byte aligned. */
+typedef struct sr_gaussians {
+  const void* means;          /* [n,3] f32 world-space centre mu (Eq. 1) */
+  const void* log_scales;     /* [n,3] dt_scale; S = diag(exp(log_scales)) (Eq. 1) */
+  const void* quats;          /* [n,4] f32 (w,x,y,z), any norm > 0; R from q/|q| (Eq. 1) */
+  const void* opacity_logits; /* [n] f32, or [n,2] f32 when two_opacities: alpha_1, alpha_2 = sigmoid (Eq. alpha) */
+  const void* skew;           /* [n,3] dt_skew: skew eta in the Gaussian's standardised local frame */
+  const void* split_dir;      /* [n,3] dt_skew or NULL: direction d of the enhanced opacity (Eq. alpha) */
+  const void* sh;             /* [n,(deg+1)^2,3] dt_sh: SH colour coefficients (Preliminaries) */
+  int64_t n;                  /* number of Gaussians, >= 0 */
+  int32_t sh_degree;          /* 0..3 */
+  int32_t two_opacities;      /* 0: one opacity per Gaussian; 1: alpha_1, alpha_2 */
+  int32_t dt_sh, dt_scale, dt_skew; /* sr_dtype tags */
+  int32_t reserved_;
+} sr_gaussians;
+
+/* One view, OpenCV convention, FP32 (see sr_camera_from_gl). */
+typedef struct sr_camera {
+  float w2c[12];              /* row-major 3x4 world-to-camera [R | t] */
+  float fx, fy, cx, cy;       /* intrinsics K (pixels) */
+  float tan_fovx, tan_fovy;   /* tan(FoV/2), bound the local-affine Jacobian */
+  float campos[3];            /* camera centre (world), for the SH view direction */
+  int32_t width, height;      /* pixels, 1..32768 */
+} sr_camera;
+
+/* Rasterizer constants.  sr_config_default fills the values used by the
+ * paper's 3DGS baseline and this library's tests. */
+typedef struct sr_config {
+  int32_t tile_w, tile_h;     /* 16x16 (only size in this build) */
+  float alpha_min;            /* gate: pairs with alpha < alpha_min are skipped (1/255) */
+  float alpha_max;            /* clamp on alpha (0.99) */
+  float t_stop;               /* stop before the Gaussian that takes T below t_stop (1e-4) */
+  float dilation;             /* s of Sigma' + sI (0.3 px^2) */
+  float fov_clamp;            /* |x/z| <= fov_clamp * tan_fovx in the Jacobian (1.3) */
+  float near_z;               /* cull camera z <= near_z (0.2) */
+  float bg[3];                /* background colour */
+  int32_t antialias_comp;     /* 1: d = o * sqrt(det Sigma' / det(Sigma' + sI)); 0: d = o */
+  int32_t render_blocks_per_sm; /* 0 = auto; launch shape of the render kernels */
+  int32_t sort_spin_limit;    /* 0 = auto; bound on each look-back wait of the sort */
+  int32_t reserved_[4];
+} sr_config;
+
+/* Gradients of the loss w.r.t. the attributes, FP32, device, caller-owned,
+ * same layouts as sr_gaussians (FP32 whatever the storage type).  Fully
+ * overwritten by sr_render_bwd (summed over all views of the plan).
+ * split_dir may be NULL iff the scene has none.  means2d_abs (optional, [n])
+ * receives sum over views of |dL/dmu_2| and depth_grad (optional, [n]) the
+ * sum over views of dL/dz of the camera-space centre. */
+typedef struct sr_grads {
+  float* means;
+  float* log_scales;
+  float* quats;
+  float* opacity_logits;
+  float* skew;
+  float* split_dir;
+  float* sh;
+  float* means2d_abs;
+  float* depth_grad;
+} sr_grads;
+
+/* Host-side plan: sizes and workspace layout for one (N, cameras) set-up.
+ * Caller-owned plain struct filled by sr_plan_init; read-only afterwards. */
+typedef struct sr_plan {
+  int32_t abi_version;
+  int32_t n_views;
+  int64_t n;
+  int32_t sh_degree;
+  int32_t tile_w, tile_h;
+  int32_t sort_passes;        /* radix passes of 8 bits over the (tile|depth) key */
+  int32_t sort_bits;          /* 32 depth bits + tile-id bits */
+  int32_t render_mode;        /* 0: one opacity; 1: two opacities; 2: two opacities + split direction */
+  int32_t two_opacities;      /* copied from the sr_gaussians the plan was made for */
+  int32_t has_split;          /* 1 if split_dir was non-NULL */
+  int64_t key_capacity;       /* keys the workspace can hold */
+  int64_t total_tiles;
+  int64_t total_pixels;
+  int64_t tile_base[SR_MAX_VIEWS + 1];    /* first global tile id of view v */
+  int64_t image_offset[SR_MAX_VIEWS + 1]; /* float offset of view v's [3][H][W] image */
+  int64_t pixel_offset[SR_MAX_VIEWS + 1]; /* element offset of view v's [H][W] state */
+  int32_t width[SR_MAX_VIEWS], height[SR_MAX_VIEWS];
+  size_t ws_bytes;            /* workspace size to allocate (256-byte aligned base) */
+  size_t off[24];             /* internal offsets into the workspace */
+} sr_plan;
+
+/* Version of this ABI (SR_ABI_VERSION). */
+int32_t sr_abi_version(void);
+
+/* Human-readable name of a status code; never NULL. */
+const char* sr_status_string(sr_status s);
+
+/* Fill *cfg with the defaults listed in sr_config.  Returns SR_ERR_INVALID on NULL. */
+sr_status sr_config_default(sr_config* cfg);
+
+/* Camera set-up of Alg. 3: c2w_gl is the row-major 4x4 camera-to-world pose in
+ * the OpenGL/Blender convention (-Z forward, +Y up).  Applies
+ * M_cv = M_gl diag(1,-1,-1,1) (Eq. coord_transform), inverts it to W2C, and
+ * builds K with fx = W / (2 tan(fovx/2)), fy = H / (2 tan(fovy/2)),
+ * (cx, cy) = (W/2, H/2) (the K matrix).  Computed in FP64, rounded once to
+ * FP32.  Host only.  SR_ERR_INVALID on NULL, non-positive size, or a FoV
+ * outside (0, pi). */
+sr_status sr_camera_from_gl(const double c2w_gl[16], int32_t width, int32_t height, double fovx, double fovy,
+                            sr_camera* out);
+
+/* Plan the Gaussians described by g (only n, sh_degree, two_opacities,
+ * the dtype tags and whether split_dir is non-NULL are read; the data
+ * pointers may be NULL here) into n_views views (host array cams_host, used
+ * for sizes only) with room for key_capacity tile keys.  Later calls must
+ * pass Gaussians with the same description.  SR_ERR_INVALID on bad sizes
+ * (n < 0, n_views outside 1..SR_MAX_VIEWS, degree > 3, a view size outside
+ * 1..32768, tile size other than 16x16, key_capacity outside 0..2^32-1, or
+ * n * n_views >= 2^31). */
+sr_status sr_plan_init(sr_plan* plan, const sr_config* cfg, const sr_gaussians* g, const sr_camera* cams_host,
+                       int32_t n_views, int64_t key_capacity);
+
+/* Workspace bytes for the plan (same as plan->ws_bytes). */
+size_t sr_workspace_size(const sr_plan* plan);
+
+/* Project every Gaussian into every view.  cams_dev: device array of
+ * plan->n_views sr_camera whose sizes match the plan.  ws: device workspace
+ * of plan->ws_bytes bytes, 256-byte aligned.  Writes the per-(view,
+ * Gaussian) records, depth keys, tile rectangles and tile counts into ws. */
+sr_status sr_preprocess(const sr_plan* plan, const sr_gaussians* g, const sr_camera* cams_dev, const sr_config* cfg,
+                        void* ws, void* stream);
+
+/* Tile binning and depth sort: exclusive scan of the tile counts, one
+ * (global tile << 32 | FP32 depth bits) key per touched tile in Gaussian
+ * index order, a stable LSD radix sort (ties keep index order), and per-tile
+ * [start, end) ranges.  If keys_needed is non-NULL the call synchronises the
+ * stream once, stores the number of keys the frame needs, returns
+ * SR_ERR_CAPACITY (nothing to render) if it exceeds plan->key_capacity and
+ * skips radix passes whose digit is the same for every key.  If NULL, the
+ * call never blocks (for CUDA-graph capture): every pass runs and an
+ * overflow is reported through the status word (sr_read_status). */
+sr_status sr_bin_sort(const sr_plan* plan, const sr_config* cfg, void* ws, int64_t* keys_needed, void* stream);
+
+/* Forward composite of all views.  images: plan->image_offset[n_views]
+ * floats; t_final: final transmittance per pixel; n_contrib: per pixel, one
+ * past the position (within its tile's sorted range) of the last blended
+ * Gaussian.  t_final and n_contrib are plan->total_pixels elements and are
+ * needed by sr_render_bwd. */
+sr_status sr_render_fwd(const sr_plan* plan, const sr_config* cfg, void* ws, float* images, float* t_final,
+                        uint32_t* n_contrib, void* stream);
+
+/* Backward of L with dL/dimage = d_images (same layout as images): reverse
+ * replay per pixel (Alg. 2; the d/dx bracket is read with delta = x - mu,
+ * giving -sqrt(2/pi) beta e^{-z^2} inside the bracket of dL/dmu), FP32
+ * gradients reduced per warp before global atomics, then the chain rule
+ * through the projection into *out (overwritten).  Needs the ws, t_final and
+ * n_contrib of the matching forward call and the same g and cams_dev. */
+sr_status sr_render_bwd(const sr_plan* plan, const sr_gaussians* g, const sr_camera* cams_dev, const sr_config* cfg,
+                        void* ws, const float* d_images, const float* t_final, const uint32_t* n_contrib,
+                        const sr_grads* out, void* stream);
+
+/* Synchronise the stream and read the device status word.  Returns SR_OK,
+ * SR_ERR_CAPACITY or SR_ERR_TIMEOUT (first set bit), clears the word, and
+ * stores the last frame's key count in *keys_needed if non-NULL. */
+sr_status sr_read_status(const sr_plan* plan, void* ws, int64_t* keys_needed, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SKEWRASTER_H */

@@ -1,0 +1,338 @@
+// C ABI of the skew-Gaussian rasterizer: argument checks, the workspace
+// plan, and the kernel launches of each stage (declared in skewraster.h).
+#include <cmath>
+#include <cstring>
+
+#include "kernels.cuh"
+
+using namespace sr;
+
+namespace {
+
+constexpr int kDefaultSpin = 1 << 20;  // look-back polls (32 ns sleeps) before giving up
+
+int device_sms() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (cache[dev] == 0) {
+    int s = 0;
+    if (cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || s <= 0) s = 152;
+    cache[dev] = s;
+  }
+  return cache[dev];
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool valid_dtype(int32_t d) { return d == SR_F32 || d == SR_BF16 || d == SR_F16; }
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+sr_status check_config(const sr_config* c) {
+  if (!c) return SR_ERR_INVALID;
+  if (c->tile_w != kTile || c->tile_h != kTile) return SR_ERR_UNSUPPORTED;
+  if (!(c->alpha_min > 0.0f && c->alpha_min < 1.0f)) return SR_ERR_INVALID;
+  if (!(c->alpha_max > c->alpha_min && c->alpha_max < 1.0f)) return SR_ERR_INVALID;
+  if (!(c->t_stop >= 0.0f && c->t_stop < 1.0f)) return SR_ERR_INVALID;
+  if (!(c->dilation >= 0.0f) || !(c->fov_clamp > 0.0f) || !(c->near_z > 0.0f)) return SR_ERR_INVALID;
+  if (c->antialias_comp && !(c->dilation > 0.0f)) return SR_ERR_INVALID;
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(c->bg[k])) return SR_ERR_INVALID;
+  return SR_OK;
+}
+
+sr_status check_gaussians(const sr_plan* p, const sr_gaussians* g, bool need_data) {
+  if (!g) return SR_ERR_INVALID;
+  if (g->n != p->n || g->sh_degree != p->sh_degree) return SR_ERR_INVALID;
+  if ((g->two_opacities != 0) != (p->two_opacities != 0)) return SR_ERR_INVALID;
+  if ((g->split_dir != nullptr) != (p->has_split != 0)) return SR_ERR_INVALID;
+  if (!valid_dtype(g->dt_sh) || !valid_dtype(g->dt_scale) || !valid_dtype(g->dt_skew)) return SR_ERR_INVALID;
+  if (need_data && g->n > 0) {
+    if (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->skew || !g->sh) return SR_ERR_INVALID;
+    if (!aligned16(g->quats)) return SR_ERR_INVALID;  // read as float4
+  }
+  return SR_OK;
+}
+
+sr_status from_cuda(cudaError_t e) { return e == cudaSuccess ? SR_OK : SR_ERR_CUDA; }
+
+}  // namespace
+
+extern "C" {
+
+int32_t sr_abi_version(void) { return SR_ABI_VERSION; }
+
+const char* sr_status_string(sr_status s) {
+  switch (s) {
+    case SR_OK: return "ok";
+    case SR_ERR_INVALID: return "invalid argument";
+    case SR_ERR_CAPACITY: return "tile-key capacity exceeded";
+    case SR_ERR_CUDA: return "CUDA runtime error";
+    case SR_ERR_TIMEOUT: return "bounded device wait gave up";
+    case SR_ERR_UNSUPPORTED: return "unsupported request";
+  }
+  return "unknown status";
+}
+
+sr_status sr_config_default(sr_config* c) {
+  if (!c) return SR_ERR_INVALID;
+  std::memset(c, 0, sizeof(*c));
+  c->tile_w = c->tile_h = kTile;
+  c->alpha_min = 1.0f / 255.0f;
+  c->alpha_max = 0.99f;
+  c->t_stop = 1e-4f;
+  c->dilation = 0.3f;
+  c->fov_clamp = 1.3f;
+  c->near_z = 0.2f;
+  c->antialias_comp = 1;
+  return SR_OK;
+}
+
+// Alg. 3: M_cv = M_gl diag(1,-1,-1,1), W2C = M_cv^-1, K from (W, H, FoV).
+sr_status sr_camera_from_gl(const double c2w_gl[16], int32_t width, int32_t height, double fovx, double fovy,
+                            sr_camera* out) {
+  if (!c2w_gl || !out || width < 1 || height < 1 || width > 32768 || height > 32768) return SR_ERR_INVALID;
+  if (!(fovx > 0.0 && fovx < M_PI) || !(fovy > 0.0 && fovy < M_PI)) return SR_ERR_INVALID;
+  for (int k = 0; k < 16; ++k)
+    if (!std::isfinite(c2w_gl[k])) return SR_ERR_INVALID;
+  double cv[3][4];
+  for (int r = 0; r < 3; ++r) {
+    cv[r][0] = c2w_gl[4 * r + 0];
+    cv[r][1] = -c2w_gl[4 * r + 1];
+    cv[r][2] = -c2w_gl[4 * r + 2];
+    cv[r][3] = c2w_gl[4 * r + 3];
+  }
+  // rigid inverse: rotation transposed, translation -R^T t
+  for (int r = 0; r < 3; ++r) {
+    for (int k = 0; k < 3; ++k) out->w2c[4 * r + k] = (float)cv[k][r];
+    const double tr = -(cv[0][r] * cv[0][3] + cv[1][r] * cv[1][3] + cv[2][r] * cv[2][3]);
+    out->w2c[4 * r + 3] = (float)tr;
+  }
+  const double tx = std::tan(0.5 * fovx), ty = std::tan(0.5 * fovy);
+  out->fx = (float)(width / (2.0 * tx));
+  out->fy = (float)(height / (2.0 * ty));
+  out->cx = (float)(0.5 * width);
+  out->cy = (float)(0.5 * height);
+  out->tan_fovx = (float)tx;
+  out->tan_fovy = (float)ty;
+  for (int k = 0; k < 3; ++k) out->campos[k] = (float)cv[k][3];
+  out->width = width;
+  out->height = height;
+  return SR_OK;
+}
+
+sr_status sr_plan_init(sr_plan* p, const sr_config* cfg, const sr_gaussians* g, const sr_camera* cams_host,
+                       int32_t n_views, int64_t key_capacity) {
+  if (!p || !g || !cams_host) return SR_ERR_INVALID;
+  sr_status s = check_config(cfg);
+  if (s != SR_OK) return s;
+  if (g->n < 0 || g->sh_degree < 0 || g->sh_degree > 3) return SR_ERR_INVALID;
+  if (n_views < 1 || n_views > SR_MAX_VIEWS) return SR_ERR_INVALID;
+  if (key_capacity < 0 || key_capacity > (int64_t)0xffffffffLL) return SR_ERR_INVALID;
+  if (!valid_dtype(g->dt_sh) || !valid_dtype(g->dt_scale) || !valid_dtype(g->dt_skew)) return SR_ERR_INVALID;
+  const int64_t m = g->n * (int64_t)n_views;
+  if (m >= (int64_t)1 << 31) return SR_ERR_INVALID;
+  std::memset(p, 0, sizeof(*p));
+  p->abi_version = SR_ABI_VERSION;
+  p->n_views = n_views;
+  p->n = g->n;
+  p->sh_degree = g->sh_degree;
+  p->tile_w = cfg->tile_w;
+  p->tile_h = cfg->tile_h;
+  p->two_opacities = g->two_opacities ? 1 : 0;
+  p->has_split = g->split_dir ? 1 : 0;
+  p->render_mode = !p->two_opacities ? MODE_PLAIN : (p->has_split ? MODE_SPLIT : MODE_TWO);
+  p->key_capacity = key_capacity;
+  int64_t tb = 0, io = 0, po = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const int32_t w = cams_host[v].width, h = cams_host[v].height;
+    if (w < 1 || h < 1 || w > 32768 || h > 32768) return SR_ERR_INVALID;
+    p->width[v] = w;
+    p->height[v] = h;
+    p->tile_base[v] = tb;
+    p->image_offset[v] = io;
+    p->pixel_offset[v] = po;
+    tb += (int64_t)((w + kTile - 1) / kTile) * ((h + kTile - 1) / kTile);
+    io += 3 * (int64_t)w * h;
+    po += (int64_t)w * h;
+  }
+  p->tile_base[n_views] = tb;
+  p->image_offset[n_views] = io;
+  p->pixel_offset[n_views] = po;
+  p->total_tiles = tb;
+  p->total_pixels = po;
+  if (tb >= (int64_t)1 << 31) return SR_ERR_INVALID;
+  int tile_bits = 0;
+  while (((int64_t)1 << tile_bits) < tb) ++tile_bits;
+  p->sort_bits = 32 + tile_bits;
+  p->sort_passes = (p->sort_bits + 7) / 8;
+
+  const int64_t scan_blocks = (m + kScanBlock - 1) / kScanBlock;
+  const int64_t parts = (key_capacity + kSortPart - 1) / kSortPart;
+  size_t sizes[WS_NUM_SLOTS];
+  sizes[WS_STATUS] = sizeof(Status);
+  sizes[WS_VIEWS] = sizeof(ViewInfo) * SR_MAX_VIEWS;
+  sizes[WS_REC] = sizeof(float4) * 4 * (size_t)m;
+  sizes[WS_DEPTH] = sizeof(uint32_t) * (size_t)m;
+  sizes[WS_RECT] = sizeof(uint2) * (size_t)m;
+  sizes[WS_NTOUCH] = sizeof(uint32_t) * (size_t)m;
+  sizes[WS_OFFSETS] = sizeof(uint32_t) * (size_t)m;
+  sizes[WS_SCAN_PART] = sizeof(unsigned long long) * (size_t)(scan_blocks + 1);
+  sizes[WS_KEYS0] = sizes[WS_KEYS1] = sizeof(unsigned long long) * (size_t)key_capacity;
+  sizes[WS_VALS0] = sizes[WS_VALS1] = sizeof(uint32_t) * (size_t)key_capacity;
+  sizes[WS_HIST] = sizeof(uint32_t) * kMaxPasses * 256;
+  sizes[WS_LOOKBACK] = sizeof(unsigned long long) * 256 * (size_t)p->sort_passes * (size_t)parts;
+  sizes[WS_RANGES] = sizeof(uint2) * (size_t)tb;
+  sizes[WS_D2] = sizeof(float) * kD2Stride * (size_t)m;
+  size_t off = 0;
+  for (int k = 0; k < WS_NUM_SLOTS; ++k) {
+    p->off[k] = off;
+    off += align256(sizes[k] > 0 ? sizes[k] : 1);
+  }
+  p->ws_bytes = off;
+  return SR_OK;
+}
+
+size_t sr_workspace_size(const sr_plan* p) { return p ? p->ws_bytes : 0; }
+
+static sr_status check_plan(const sr_plan* p, void* ws) {
+  if (!p || p->abi_version != SR_ABI_VERSION || !ws) return SR_ERR_INVALID;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return SR_ERR_INVALID;
+  return SR_OK;
+}
+
+sr_status sr_preprocess(const sr_plan* p, const sr_gaussians* g, const sr_camera* cams_dev, const sr_config* cfg,
+                        void* ws, void* stream) {
+  sr_status s = check_plan(p, ws);
+  if (s != SR_OK) return s;
+  if ((s = check_config(cfg)) != SR_OK) return s;
+  if ((s = check_gaussians(p, g, true)) != SR_OK) return s;
+  if (!cams_dev) return SR_ERR_INVALID;
+  PreArgs a;
+  a.g = *g;
+  a.cams = cams_dev;
+  a.n_views = p->n_views;
+  a.cfg = to_dev(*cfg);
+  a.mode = p->render_mode;
+  a.ws = ws_ptrs(*p, ws);
+  return from_cuda(launch_preprocess_fwd(a, static_cast<cudaStream_t>(stream), device_sms()));
+}
+
+static BinArgs bin_args(const sr_plan* p, const sr_config* cfg, void* ws) {
+  BinArgs b;
+  b.n = p->n;
+  b.n_views = p->n_views;
+  b.passes = p->sort_passes;
+  b.cap = (unsigned long long)p->key_capacity;
+  b.total_tiles = p->total_tiles;
+  b.spin_limit = cfg->sort_spin_limit > 0 ? cfg->sort_spin_limit : kDefaultSpin;
+  b.ws = ws_ptrs(*p, ws);
+  return b;
+}
+
+sr_status sr_bin_sort(const sr_plan* p, const sr_config* cfg, void* ws, int64_t* keys_needed, void* stream) {
+  sr_status s = check_plan(p, ws);
+  if (s != SR_OK) return s;
+  if ((s = check_config(cfg)) != SR_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const BinArgs b = bin_args(p, cfg, ws);
+  cudaError_t e = launch_bin_phase1(b, st, device_sms());
+  if (e != cudaSuccess) return SR_ERR_CUDA;
+  int run[kMaxPasses];
+  for (int k = 0; k < kMaxPasses; ++k) run[k] = 1;
+  long long known = -1;
+  if (keys_needed) {
+    Status h;
+    e = cudaMemcpyAsync(&h, b.ws.status, sizeof(Status), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return SR_ERR_CUDA;
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return SR_ERR_CUDA;
+    *keys_needed = (int64_t)h.keys_needed;
+    if (h.keys_needed > (unsigned long long)p->key_capacity) return SR_ERR_CAPACITY;
+    known = (long long)h.keys_needed;
+    for (int k = 0; k < p->sort_passes; ++k) run[k] = h.pass_trivial[k] ? 0 : 1;
+  }
+  return from_cuda(launch_bin_phase2(b, run, known, st));
+}
+
+static RenderArgs render_args(const sr_plan* p, const sr_config* cfg, void* ws) {
+  const Ws w = ws_ptrs(*p, ws);
+  RenderArgs r;
+  r.rec = w.rec;
+  r.vals0 = w.vals[0];
+  r.vals1 = w.vals[1];
+  r.ranges = w.ranges;
+  r.views = w.views;
+  r.status = w.status;
+  r.n_views = p->n_views;
+  r.cfg = to_dev(*cfg);
+  r.images = nullptr;
+  r.t_final = nullptr;
+  r.n_contrib = nullptr;
+  r.d_images = nullptr;
+  r.d2 = w.d2;
+  return r;
+}
+
+sr_status sr_render_fwd(const sr_plan* p, const sr_config* cfg, void* ws, float* images, float* t_final,
+                        uint32_t* n_contrib, void* stream) {
+  sr_status s = check_plan(p, ws);
+  if (s != SR_OK) return s;
+  if ((s = check_config(cfg)) != SR_OK) return s;
+  if (!images || !t_final || !n_contrib) return SR_ERR_INVALID;
+  RenderArgs r = render_args(p, cfg, ws);
+  r.images = images;
+  r.t_final = t_final;
+  r.n_contrib = n_contrib;
+  return from_cuda(launch_render_fwd(r, p->render_mode, p->total_tiles, static_cast<cudaStream_t>(stream)));
+}
+
+sr_status sr_render_bwd(const sr_plan* p, const sr_gaussians* g, const sr_camera* cams_dev, const sr_config* cfg,
+                        void* ws, const float* d_images, const float* t_final, const uint32_t* n_contrib,
+                        const sr_grads* out, void* stream) {
+  sr_status s = check_plan(p, ws);
+  if (s != SR_OK) return s;
+  if ((s = check_config(cfg)) != SR_OK) return s;
+  if ((s = check_gaussians(p, g, true)) != SR_OK) return s;
+  if (!cams_dev || !d_images || !t_final || !n_contrib || !out) return SR_ERR_INVALID;
+  if (p->n > 0 && (!out->means || !out->log_scales || !out->quats || !out->opacity_logits || !out->skew || !out->sh))
+    return SR_ERR_INVALID;
+  if (p->has_split && p->n > 0 && !out->split_dir) return SR_ERR_INVALID;
+  if (p->n > 0 && !aligned16(out->quats)) return SR_ERR_INVALID;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Ws w = ws_ptrs(*p, ws);
+  cudaError_t e = cudaMemsetAsync(w.d2, 0, sizeof(float) * kD2Stride * (size_t)(p->n * p->n_views), st);
+  if (e != cudaSuccess) return SR_ERR_CUDA;
+  RenderArgs r = render_args(p, cfg, ws);
+  r.t_final = const_cast<float*>(t_final);
+  r.n_contrib = const_cast<uint32_t*>(n_contrib);
+  r.d_images = d_images;
+  e = launch_render_bwd(r, p->render_mode, p->total_tiles, st);
+  if (e != cudaSuccess) return SR_ERR_CUDA;
+  BwdArgs b;
+  b.g = *g;
+  b.cams = cams_dev;
+  b.n_views = p->n_views;
+  b.cfg = to_dev(*cfg);
+  b.ws = w;
+  b.out = *out;
+  return from_cuda(launch_preprocess_bwd(b, st, device_sms()));
+}
+
+sr_status sr_read_status(const sr_plan* p, void* ws, int64_t* keys_needed, void* stream) {
+  sr_status s = check_plan(p, ws);
+  if (s != SR_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Ws w = ws_ptrs(*p, ws);
+  Status h;
+  if (cudaMemcpyAsync(&h, w.status, sizeof(Status), cudaMemcpyDeviceToHost, st) != cudaSuccess) return SR_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SR_ERR_CUDA;
+  if (keys_needed) *keys_needed = (int64_t)h.keys_needed;
+  if (cudaMemsetAsync(&w.status->flags, 0, sizeof(uint32_t), st) != cudaSuccess) return SR_ERR_CUDA;
+  if (h.flags & kStatusCapacity) return SR_ERR_CAPACITY;
+  if (h.flags & kStatusTimeout) return SR_ERR_TIMEOUT;
+  return SR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,434 @@
+// Tile binning and depth sort (the tile-based, depth-sorted pipeline of the
+// Preliminaries).
+//
+//   scan       exclusive scan of the per-(view, Gaussian) tile counts
+//   duplicate  one key (global tile << 32 | FP32 depth bits) per touched
+//              tile, value = record index, emitted in record-index order
+//   histogram  digit counts of every 8-bit digit of every key, one read
+//   onesweep   one stable LSD radix pass per digit: each block ranks a
+//              partition of 4096 keys with warp match-any, publishes its
+//              digit counts and resolves its global offsets by a decoupled
+//              look-back over the preceding partitions (every wait bounded),
+//              then scatters through shared memory so writes are runs
+//   ranges     [start, end) of each tile in the sorted key list
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace sr {
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// ---------------------------------------------------------------------------
+// block-wide exclusive scan helpers
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ __forceinline__ unsigned long long block_exclusive_u64(unsigned long long x, unsigned long long* s_warp,
+                                                                  unsigned long long& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_warp[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long w = lane < NT / 32 ? s_warp[lane] : 0ull;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < NT / 32) s_warp[lane] = w;
+  }
+  __syncthreads();
+  total = s_warp[NT / 32 - 1];
+  const unsigned long long before = warp > 0 ? s_warp[warp - 1] : 0ull;
+  __syncthreads();
+  return before + inc - x;
+}
+
+// ---------------------------------------------------------------------------
+// scan of the tile counts
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ cnt, int64_t m,
+                                                                   unsigned long long* __restrict__ part) {
+  __shared__ unsigned long long s_warp[kScanThreads / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k)
+    if (base + k < m) sum += cnt[base + k];
+  unsigned long long total;
+  block_exclusive_u64<kScanThreads>(sum, s_warp, total);
+  if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) scan_parts_kernel(unsigned long long* part, int nb, Status* st,
+                                                          unsigned long long cap) {
+  __shared__ unsigned long long s_warp[32];
+  unsigned long long carry = 0;
+  for (int c0 = 0; c0 < nb; c0 += 1024) {
+    const int i = c0 + threadIdx.x;
+    const unsigned long long x = i < nb ? part[i] : 0ull;
+    unsigned long long total;
+    const unsigned long long ex = block_exclusive_u64<1024>(x, s_warp, total);
+    if (i < nb) part[i] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) {
+    part[nb] = carry;
+    st->keys_needed = carry;
+    if (carry > cap) raise_status(st, kStatusCapacity);
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint32_t* __restrict__ cnt, int64_t m,
+                                                                 const unsigned long long* __restrict__ part,
+                                                                 uint32_t* __restrict__ offsets) {
+  __shared__ unsigned long long s_warp[kScanThreads / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = base + k < m ? cnt[base + k] : 0u;
+    sum += v[k];
+  }
+  unsigned long long total;
+  unsigned long long run = block_exclusive_u64<kScanThreads>(sum, s_warp, total) + part[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < m) offsets[base + k] = run > 0xffffffffull ? 0xffffffffu : (uint32_t)run;
+    run += v[k];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// key duplication
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) duplicate_kernel(int64_t n, int n_views, const ViewInfo* __restrict__ views,
+                                                        const uint32_t* __restrict__ ntouch,
+                                                        const uint32_t* __restrict__ offsets,
+                                                        const uint2* __restrict__ rect,
+                                                        const uint32_t* __restrict__ depth,
+                                                        unsigned long long* __restrict__ keys,
+                                                        uint32_t* __restrict__ vals, unsigned long long cap) {
+  const int64_t m_total = n * n_views;
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < m_total;
+       m += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t cnt = ntouch[m];
+    if (cnt == 0) continue;
+    const int v = (int)(m / n);
+    const ViewInfo vi = views[v];
+    const uint2 r = rect[m];
+    const uint32_t tx0 = r.x & 0xffffu, ty0 = r.x >> 16, tx1 = r.y & 0xffffu, ty1 = r.y >> 16;
+    const unsigned long long d = depth[m];
+    unsigned long long pos = offsets[m];
+    for (uint32_t ty = ty0; ty < ty1; ++ty)
+      for (uint32_t tx = tx0; tx < tx1; ++tx) {
+        if (pos < cap) {
+          const unsigned long long tile = (unsigned long long)(vi.tile_base + (int64_t)ty * vi.tiles_x + tx);
+          keys[pos] = (tile << 32) | d;
+          vals[pos] = (uint32_t)m;
+        }
+        ++pos;
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// digit histograms of all passes
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) histogram_kernel(const unsigned long long* __restrict__ keys,
+                                                        const Status* __restrict__ st, unsigned long long cap,
+                                                        int passes, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t s_h[kMaxPasses][256];
+  for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&s_h[0][0])[i] = 0u;
+  __syncthreads();
+  const unsigned long long kn = st->keys_needed < cap ? st->keys_needed : cap;
+  for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < kn;
+       k += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long key = keys[k];
+    for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p][(key >> (8 * p)) & 0xffu], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
+    const uint32_t c = (&s_h[0][0])[i];
+    if (c) atomicAdd(hist + i, c);
+  }
+}
+
+// per pass: exclusive digit offsets in place, and whether one digit holds every key
+__global__ void __launch_bounds__(256) hist_scan_kernel(uint32_t* __restrict__ hist, Status* st,
+                                                        unsigned long long cap) {
+  __shared__ unsigned long long s_warp[8];
+  const int p = blockIdx.x;
+  const unsigned long long kn = st->keys_needed < cap ? st->keys_needed : cap;
+  const uint32_t c = hist[p * 256 + threadIdx.x];
+  unsigned long long total;
+  const unsigned long long ex = block_exclusive_u64<256>(c, s_warp, total);
+  hist[p * 256 + threadIdx.x] = (uint32_t)ex;
+  const int full = __syncthreads_or(kn > 0 && c == kn);
+  if (threadIdx.x == 0) st->pass_trivial[p] = full ? 1u : 0u;
+}
+
+// ---------------------------------------------------------------------------
+// one onesweep radix pass
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagInc = 2ull << 62;
+constexpr unsigned long long kValMask = (1ull << 62) - 1;
+
+struct PassArgs {
+  const unsigned long long* keys_in;
+  const uint32_t* vals_in;
+  unsigned long long* keys_out;
+  uint32_t* vals_out;
+  const uint32_t* digit_base;     // exclusive digit offsets of this pass
+  unsigned long long* lookback;   // [parts][passes][256], zeroed per frame
+  int passes;
+  Status* st;
+  unsigned long long cap;
+  int pass;
+  int shift;
+  int spin_limit;
+};
+
+__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(PassArgs a) {
+  constexpr int NW = kSortThreads / 32;
+  __shared__ unsigned long long s_buf[kSortPart];  // keys, then values (as u32) in the scatter phase
+  __shared__ uint32_t s_whist[NW][256];
+  __shared__ uint32_t s_lstart[256];
+  __shared__ unsigned long long s_gbase[256];
+  __shared__ unsigned long long s_warp[NW];
+  __shared__ uint8_t s_dig[kSortPart];
+  __shared__ uint32_t s_part;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned long long kn = a.st->keys_needed < a.cap ? a.st->keys_needed : a.cap;
+  const unsigned long long nparts = (kn + kSortPart - 1) / kSortPart;
+  if (tid == 0) s_part = atomicAdd(&a.st->part_counter[a.pass], 1u);
+  for (int i = tid; i < NW * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0u;
+  __syncthreads();
+  const unsigned long long part = s_part;
+  if (part >= nparts) return;
+  const unsigned long long base = part * kSortPart;
+
+  // load, warp-blocked: warp w owns keys [w*512, (w+1)*512) of the partition
+  unsigned long long key[kSortItems];
+  uint32_t rank[kSortItems];
+  const uint32_t lt = lanemask_lt();
+#pragma unroll
+  for (int j = 0; j < kSortItems; ++j) {
+    const unsigned long long idx = base + (unsigned long long)warp * (32 * kSortItems) + j * 32 + lane;
+    const bool valid = idx < kn;
+    key[j] = valid ? a.keys_in[idx] : ~0ull;
+    const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+    if (valid) {
+      const uint32_t d = (uint32_t)(key[j] >> a.shift) & 0xffu;
+      const uint32_t peers = __match_any_sync(vmask, d);
+      const uint32_t prev = s_whist[warp][d];
+      __syncwarp(vmask);
+      if ((peers & lt) == 0) s_whist[warp][d] = prev + __popc(peers);
+      __syncwarp(vmask);
+      rank[j] = prev + __popc(peers & lt);
+    } else {
+      rank[j] = 0u;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+
+  // per digit: counts across warps -> warp offsets; publish and look back
+  const int d = tid;  // kSortThreads == 256 digits
+  uint32_t tot = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const uint32_t c = s_whist[w][d];
+    s_whist[w][d] = tot;
+    tot += c;
+  }
+  unsigned long long* lb = a.lookback + (part * a.passes + a.pass) * 256;
+  if (part == 0) {
+    st_relaxed_u64(lb + d, kFlagInc | tot);
+  } else {
+    st_relaxed_u64(lb + d, kFlagAgg | tot);
+  }
+  unsigned long long excl = 0;
+  if (part > 0) {
+    long long q = (long long)part - 1;
+    int spins = 0;
+    while (q >= 0) {
+      const unsigned long long v = ld_relaxed_u64(a.lookback + ((unsigned long long)q * a.passes + a.pass) * 256 + d);
+      if (v & kFlagInc) {
+        excl += v & kValMask;
+        break;
+      }
+      if (v & kFlagAgg) {
+        excl += v & kValMask;
+        --q;
+        continue;
+      }
+      if (++spins > a.spin_limit) {  // bounded wait: report and go on
+        raise_status(a.st, kStatusTimeout);
+        atomicCAS(&a.st->timeout_where, 0u, (uint32_t)(a.pass * 1000000 + (part % 1000000)) + 1u);
+        break;
+      }
+      __nanosleep(32);
+    }
+    st_relaxed_u64(lb + d, kFlagInc | (excl + tot));
+  }
+  s_gbase[d] = (unsigned long long)a.digit_base[d] + excl;
+
+  // local digit starts (exclusive scan of tot over digits)
+  unsigned long long total;
+  s_lstart[d] = (uint32_t)block_exclusive_u64<kSortThreads>(tot, s_warp, total);
+  __syncthreads();
+
+  // local positions, keys through shared memory
+  uint32_t lpos[kSortItems];
+#pragma unroll
+  for (int j = 0; j < kSortItems; ++j) {
+    const unsigned long long idx = base + (unsigned long long)warp * (32 * kSortItems) + j * 32 + lane;
+    if (idx < kn) {
+      const uint32_t dg = (uint32_t)(key[j] >> a.shift) & 0xffu;
+      lpos[j] = s_lstart[dg] + s_whist[warp][dg] + rank[j];
+      s_buf[lpos[j]] = key[j];
+    }
+  }
+  __syncthreads();
+  const uint32_t count = (uint32_t)((kn - base) < (unsigned long long)kSortPart ? (kn - base) : kSortPart);
+  for (uint32_t i = tid; i < count; i += kSortThreads) {
+    const unsigned long long k = s_buf[i];
+    const uint32_t dg = (uint32_t)(k >> a.shift) & 0xffu;
+    s_dig[i] = (uint8_t)dg;
+    const unsigned long long g = s_gbase[dg] + (i - s_lstart[dg]);
+    if (g < kn) a.keys_out[g] = k;  // always true unless a look-back gave up
+  }
+  __syncthreads();
+  uint32_t* s_val = reinterpret_cast<uint32_t*>(s_buf);
+#pragma unroll
+  for (int j = 0; j < kSortItems; ++j) {
+    const unsigned long long idx = base + (unsigned long long)warp * (32 * kSortItems) + j * 32 + lane;
+    if (idx < kn) s_val[lpos[j]] = a.vals_in[idx];
+  }
+  __syncthreads();
+  for (uint32_t i = tid; i < count; i += kSortThreads) {
+    const uint32_t dg = s_dig[i];
+    const unsigned long long g = s_gbase[dg] + (i - s_lstart[dg]);
+    if (g < kn) a.vals_out[g] = s_val[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tile ranges
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) ranges_kernel(const unsigned long long* __restrict__ keys, Status* st,
+                                                     unsigned long long cap, uint2* __restrict__ ranges,
+                                                     int sorted_buf) {
+  const unsigned long long kn = st->keys_needed < cap ? st->keys_needed : cap;
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->sorted_buf = (uint32_t)sorted_buf;
+  for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < kn;
+       k += (unsigned long long)gridDim.x * blockDim.x) {
+    const uint32_t t = (uint32_t)(keys[k] >> 32);
+    if (k == 0 || (uint32_t)(keys[k - 1] >> 32) != t) ranges[t].x = (uint32_t)k;
+    if (k + 1 == kn || (uint32_t)(keys[k + 1] >> 32) != t) ranges[t].y = (uint32_t)(k + 1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+static int clamp_grid(unsigned long long blocks, int sms, int per_sm) {
+  const unsigned long long cap = (unsigned long long)sms * per_sm;
+  if (blocks < 1) blocks = 1;
+  return (int)(blocks < cap ? blocks : cap);
+}
+
+// Phase 1: scan, duplicate, histogram.  Everything device-resident.
+cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms) {
+  const int64_t m = a.n * a.n_views;
+  cudaError_t e;
+  // status word, histogram and ranges start at zero every frame
+  e = cudaMemsetAsync(a.ws.status, 0, sizeof(Status), st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(a.ws.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(a.ws.ranges, 0, sizeof(uint2) * a.total_tiles, st);
+  if (e != cudaSuccess) return e;
+  const int nb = (int)((m + kScanBlock - 1) / kScanBlock);
+  unsigned long long* part = reinterpret_cast<unsigned long long*>(a.ws.scan_part);
+  if (m > 0) {
+    scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(a.ws.ntouch, m, part);
+  }
+  scan_parts_kernel<<<1, 1024, 0, st>>>(part, nb, a.ws.status, a.cap);
+  if (m > 0) {
+    scan_down_kernel<<<nb, kScanThreads, 0, st>>>(a.ws.ntouch, m, part, a.ws.offsets);
+    duplicate_kernel<<<clamp_grid((m + 255) / 256, sms, 8), 256, 0, st>>>(
+        a.n, a.n_views, a.ws.views, a.ws.ntouch, a.ws.offsets, a.ws.rect, a.ws.depth, a.ws.keys[0], a.ws.vals[0],
+        a.cap);
+  }
+  histogram_kernel<<<clamp_grid((a.cap + 255) / 256, sms, 4), 256, 0, st>>>(a.ws.keys[0], a.ws.status, a.cap,
+                                                                           a.passes, a.ws.hist);
+  hist_scan_kernel<<<a.passes, 256, 0, st>>>(a.ws.hist, a.ws.status, a.cap);
+  return cudaGetLastError();
+}
+
+// Phase 2: radix passes (run[p] != 0) and ranges.  keys_known: exact key
+// count (sizes the grids), or -1 to size them for the capacity.
+cudaError_t launch_bin_phase2(const BinArgs& a, const int* run, long long keys_known, cudaStream_t st) {
+  const unsigned long long kn = keys_known >= 0 ? (unsigned long long)keys_known : a.cap;
+  const unsigned long long parts = (kn + kSortPart - 1) / kSortPart;
+  cudaError_t e = cudaSuccess;
+  if (parts > 0) {
+    e = cudaMemsetAsync(a.ws.lookback, 0, sizeof(unsigned long long) * 256 * a.passes * parts, st);
+    if (e != cudaSuccess) return e;
+  }
+  int cur = 0;
+  for (int p = 0; p < a.passes; ++p) {
+    if (!run[p] || parts == 0) continue;
+    PassArgs pa;
+    pa.keys_in = a.ws.keys[cur];
+    pa.vals_in = a.ws.vals[cur];
+    pa.keys_out = a.ws.keys[cur ^ 1];
+    pa.vals_out = a.ws.vals[cur ^ 1];
+    pa.digit_base = a.ws.hist + p * 256;
+    pa.lookback = a.ws.lookback;
+    pa.passes = a.passes;
+    pa.st = a.ws.status;
+    pa.cap = a.cap;
+    pa.pass = p;
+    pa.shift = 8 * p;
+    pa.spin_limit = a.spin_limit;
+    onesweep_kernel<<<(unsigned)parts, kSortThreads, 0, st>>>(pa);
+    cur ^= 1;
+  }
+  if (kn > 0) {
+    ranges_kernel<<<(unsigned)std::min<unsigned long long>((kn + 255) / 256, 1ull << 20), 256, 0, st>>>(
+        a.ws.keys[cur], a.ws.status, a.cap, a.ws.ranges, cur);
+  } else {
+    // nothing to sort: record which buffer (0) holds the (empty) result
+    ranges_kernel<<<1, 32, 0, st>>>(a.ws.keys[cur], a.ws.status, a.cap, a.ws.ranges, cur);
+  }
+  e = cudaGetLastError();
+  return e;
+}
+
+}  // namespace sr

@@ -1,0 +1,273 @@
+// Shared device-side definitions of the skew-Gaussian rasterizer (sm_103a).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "skewraster.h"
+
+namespace sr {
+
+// ---------------------------------------------------------------------------
+// Workspace layout.  sr_plan_init fills plan->off[] with these slots, each
+// 256-byte aligned; kernels receive raw pointers derived from them.
+// ---------------------------------------------------------------------------
+enum WsSlot {
+  WS_STATUS = 0,   // Status
+  WS_VIEWS,        // ViewInfo[SR_MAX_VIEWS]
+  WS_REC,          // float4[M][4] render records
+  WS_DEPTH,        // uint32_t[M] FP32 depth bits
+  WS_RECT,         // uint2[M]   tile rectangle (tx0 | ty0 << 16, tx1 | ty1 << 16), tx1/ty1 exclusive
+  WS_NTOUCH,       // uint32_t[M] tiles touched
+  WS_OFFSETS,      // uint32_t[M] exclusive scan of WS_NTOUCH
+  WS_SCAN_PART,    // uint32_t[scan blocks + 1]
+  WS_KEYS0, WS_KEYS1,  // uint64_t[cap] ping-pong
+  WS_VALS0, WS_VALS1,  // uint32_t[cap] ping-pong
+  WS_HIST,         // uint32_t[kMaxPasses][256] digit counts, then exclusive offsets
+  WS_LOOKBACK,     // uint64_t[kMaxPasses][parts][256] decoupled look-back state
+  WS_RANGES,       // uint2[total_tiles] [start, end) of each tile's sorted keys
+  WS_D2,           // float[M][16] per-(view, Gaussian) 2D gradients
+  WS_NUM_SLOTS
+};
+
+constexpr int kMaxPasses = 8;          // 64-bit keys, 8-bit digits
+constexpr int kSortThreads = 256;      // threads per onesweep partition block
+constexpr int kSortItems = 16;         // keys per thread
+constexpr int kSortPart = kSortThreads * kSortItems;  // keys per partition
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 16;
+constexpr int kScanBlock = kScanThreads * kScanItems;
+constexpr int kTile = 16;              // tile edge in pixels
+constexpr int kD2Stride = 16;          // floats per 2D-gradient record
+
+// status word flags
+constexpr uint32_t kStatusCapacity = 1u;
+constexpr uint32_t kStatusTimeout = 2u;
+
+struct Status {
+  uint32_t flags;
+  uint32_t sorted_buf;                // which ping-pong buffer holds the sorted keys
+  unsigned long long keys_needed;     // total keys of the last frame
+  uint32_t part_counter[kMaxPasses];  // onesweep partition tickets per pass
+  uint32_t pass_trivial[kMaxPasses];  // 1 if one digit holds every key of that pass
+  uint32_t timeout_where;             // pass * 1e6 + partition of the first timed-out wait
+};
+
+struct ViewInfo {
+  int32_t width, height, tiles_x, tiles_y;
+  int64_t tile_base;     // first global tile id
+  int64_t image_offset;  // float offset of the [3][H][W] image
+  int64_t pixel_offset;  // element offset of the [H][W] state
+  int64_t pad;
+};
+
+// 2D-gradient record slots (float[16] per (view, Gaussian))
+enum D2Slot { G_MX, G_MY, G_A, G_B, G_C, G_BX, G_BY, G_M, G_H, G_UX, G_UY, G_R, G_G, G_BL, G_ABS, G_PAD };
+
+// Render record: four float4 per (view, Gaussian).
+//  r0 = (mx, my, A2, B2)     exponent in log2 units: P2 = A2 dx^2 + B2 dx dy + C2 dy^2
+//  r1 = (C2, bxs, bys, m)    bxs = beta_x / sqrt 2, ...; m = comp (o1 + o2) / 2
+//  r2 = (h, uxs, uys, 0)     h = comp (o1 - o2) / 2, u_2 / sqrt 2 (enhanced opacity)
+//  r3 = (r, g, b, thr)       colour; thr: P2 < thr implies alpha < alpha_min
+// with A2 = -a log2(e) / 2, B2 = -b log2(e), C2 = -c log2(e) / 2.
+
+// Render modes, fixed per plan: what the opacity term needs.
+enum RenderMode {
+  MODE_PLAIN = 0,    // one opacity: o = m
+  MODE_TWO = 1,      // two opacities, no split direction: u_2 = beta_2, erf shared
+  MODE_SPLIT = 2     // two opacities and a split direction: a second erf
+};
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+constexpr float kInvSqrt2 = 0.7071067811865476f;
+constexpr float kTwoOverSqrtPi = 1.1283791670955126f;
+
+// Abramowitz & Stegun (1964), formula 7.1.26 (after Hastings 1955):
+//   erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2),
+//   t = 1 / (1 + p x), x >= 0, |error| <= 1.5e-7.
+constexpr float kAsP = 0.3275911f;
+constexpr float kAsA1 = 0.254829592f;
+constexpr float kAsA2 = -0.284496736f;
+constexpr float kAsA3 = 1.421413741f;
+constexpr float kAsA4 = -1.453152027f;
+constexpr float kAsA5 = 1.061405429f;
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// 1 + erf(z) and exp(-z^2) together.  For z < 0, 1 + erf(z) = erfc(|z|)
+// is evaluated directly (no cancellation); for z >= 0 it is 2 - erfc(z).
+struct OnePlusErf {
+  float E;   // 1 + erf(z)
+  float ez;  // exp(-z^2)
+};
+
+__device__ __forceinline__ OnePlusErf one_plus_erf(float z) {
+  const float x = fabsf(z);
+  const float t = rcp_approx(__fmaf_rn(kAsP, x, 1.0f));
+  float p = __fmaf_rn(t, kAsA5, kAsA4);
+  p = __fmaf_rn(t, p, kAsA3);
+  p = __fmaf_rn(t, p, kAsA2);
+  p = __fmaf_rn(t, p, kAsA1);
+  const float ez = ex2_approx(__fmul_rn(__fmul_rn(-x, x), kLog2e));
+  const float y = __fmul_rn(__fmul_rn(t, p), ez);  // erfc(|z|)
+  OnePlusErf r;
+  r.E = z >= 0.0f ? __fadd_rn(2.0f, -y) : y;
+  r.ez = ez;
+  return r;
+}
+
+// Per-pair evaluation shared by the forward and the backward kernels, with
+// explicit rounding intrinsics so both take bit-identical decisions.
+struct PairEval {
+  float dx, dy;
+  float G;       // exp(-1/2 d^T A d)
+  float E;       // 1 + erf(z)
+  float ez;      // exp(-z^2)
+  float o;       // opacity term m + h erf(u^T d / sqrt 2)
+  float eu;      // erf(u^T d / sqrt 2)  (MODE_TWO, MODE_SPLIT)
+  float ezu;     // exp(-zu^2)           (MODE_SPLIT; = ez in MODE_TWO)
+  float alpha;   // o G E, before the clamp
+};
+
+template <int MODE>
+__device__ __forceinline__ bool eval_pair(const float4& r0, const float4& r1, const float4& r2, float thr, float px,
+                                          float py, PairEval& e) {
+  e.dx = __fadd_rn(px, -r0.x);
+  e.dy = __fadd_rn(py, -r0.y);
+  const float lin = __fmaf_rn(r0.z, e.dx, __fmul_rn(r0.w, e.dy));
+  const float p2 = __fmaf_rn(lin, e.dx, __fmul_rn(__fmul_rn(r1.x, e.dy), e.dy));
+  if (!(p2 >= thr)) return false;  // alpha < alpha_min guaranteed (and NaN-safe)
+  e.G = ex2_approx(p2);
+  if (r1.y == 0.0f && r1.z == 0.0f) {  // zero skew: 1 + erf(0) = 1 exactly
+    e.E = 1.0f;
+    e.ez = 1.0f;
+  } else {
+    const OnePlusErf s = one_plus_erf(__fmaf_rn(r1.y, e.dx, __fmul_rn(r1.z, e.dy)));
+    e.E = s.E;
+    e.ez = s.ez;
+  }
+  if (MODE == MODE_PLAIN) {
+    e.o = r1.w;
+    e.eu = 0.0f;
+    e.ezu = 0.0f;
+  } else if (MODE == MODE_TWO) {
+    e.eu = __fadd_rn(e.E, -1.0f);
+    e.ezu = e.ez;
+    e.o = __fmaf_rn(r2.x, e.eu, r1.w);
+  } else {
+    if (r2.y == 0.0f && r2.z == 0.0f) {
+      e.eu = 0.0f;
+      e.ezu = 1.0f;
+    } else {
+      const OnePlusErf s = one_plus_erf(__fmaf_rn(r2.y, e.dx, __fmul_rn(r2.z, e.dy)));
+      e.eu = __fadd_rn(s.E, -1.0f);
+      e.ezu = s.ez;
+    }
+    e.o = __fmaf_rn(r2.x, e.eu, r1.w);
+  }
+  e.alpha = __fmul_rn(__fmul_rn(e.o, e.G), e.E);
+  return true;
+}
+
+// Storage loads (FP32 arithmetic whatever the storage type).
+template <int DT>
+__device__ __forceinline__ float ld(const void* p, int64_t i) {
+  if (DT == SR_F32) return __ldg(static_cast<const float*>(p) + i);
+  if (DT == SR_BF16) return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]);
+  return __half2float(static_cast<const __half*>(p)[i]);
+}
+
+__device__ __forceinline__ float ld_dyn(const void* p, int dt, int64_t i) {
+  if (dt == SR_F32) return ld<SR_F32>(p, i);
+  if (dt == SR_BF16) return ld<SR_BF16>(p, i);
+  return ld<SR_F16>(p, i);
+}
+
+// Record a status flag (first writer wins on timeout_where).
+__device__ __forceinline__ void raise_status(Status* st, uint32_t flag) { atomicOr(&st->flags, flag); }
+
+// Global tile id -> view by binary search over the tile bases.
+__device__ __forceinline__ int view_of_tile(const ViewInfo* views, int n_views, int64_t tile) {
+  int lo = 0, hi = n_views - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (views[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+struct CfgDev {
+  float alpha_min, alpha_max, t_stop, dilation, fov_clamp, near_z;
+  float bg[3];
+  int antialias;
+};
+
+inline CfgDev to_dev(const sr_config& c) {
+  CfgDev d;
+  d.alpha_min = c.alpha_min;
+  d.alpha_max = c.alpha_max;
+  d.t_stop = c.t_stop;
+  d.dilation = c.dilation;
+  d.fov_clamp = c.fov_clamp;
+  d.near_z = c.near_z;
+  d.bg[0] = c.bg[0];
+  d.bg[1] = c.bg[1];
+  d.bg[2] = c.bg[2];
+  d.antialias = c.antialias_comp;
+  return d;
+}
+
+// Pointers into the workspace.
+struct Ws {
+  Status* status;
+  ViewInfo* views;
+  float4* rec;
+  uint32_t* depth;
+  uint2* rect;
+  uint32_t* ntouch;
+  uint32_t* offsets;
+  uint32_t* scan_part;
+  unsigned long long* keys[2];
+  uint32_t* vals[2];
+  uint32_t* hist;
+  unsigned long long* lookback;
+  uint2* ranges;
+  float* d2;
+};
+
+inline Ws ws_ptrs(const sr_plan& p, void* base) {
+  char* b = static_cast<char*>(base);
+  Ws w;
+  w.status = reinterpret_cast<Status*>(b + p.off[WS_STATUS]);
+  w.views = reinterpret_cast<ViewInfo*>(b + p.off[WS_VIEWS]);
+  w.rec = reinterpret_cast<float4*>(b + p.off[WS_REC]);
+  w.depth = reinterpret_cast<uint32_t*>(b + p.off[WS_DEPTH]);
+  w.rect = reinterpret_cast<uint2*>(b + p.off[WS_RECT]);
+  w.ntouch = reinterpret_cast<uint32_t*>(b + p.off[WS_NTOUCH]);
+  w.offsets = reinterpret_cast<uint32_t*>(b + p.off[WS_OFFSETS]);
+  w.scan_part = reinterpret_cast<uint32_t*>(b + p.off[WS_SCAN_PART]);
+  w.keys[0] = reinterpret_cast<unsigned long long*>(b + p.off[WS_KEYS0]);
+  w.keys[1] = reinterpret_cast<unsigned long long*>(b + p.off[WS_KEYS1]);
+  w.vals[0] = reinterpret_cast<uint32_t*>(b + p.off[WS_VALS0]);
+  w.vals[1] = reinterpret_cast<uint32_t*>(b + p.off[WS_VALS1]);
+  w.hist = reinterpret_cast<uint32_t*>(b + p.off[WS_HIST]);
+  w.lookback = reinterpret_cast<unsigned long long*>(b + p.off[WS_LOOKBACK]);
+  w.ranges = reinterpret_cast<uint2*>(b + p.off[WS_RANGES]);
+  w.d2 = reinterpret_cast<float*>(b + p.off[WS_D2]);
+  return w;
+}
+
+}  // namespace sr

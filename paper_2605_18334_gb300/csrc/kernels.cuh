@@ -1,0 +1,59 @@
+// Argument blocks and launchers of the rasterizer's kernels (one per stage).
+#pragma once
+
+#include "common.cuh"
+
+namespace sr {
+
+struct PreArgs {        // preprocess forward
+  sr_gaussians g;
+  const sr_camera* cams;
+  int n_views;
+  CfgDev cfg;
+  int mode;             // RenderMode
+  Ws ws;
+};
+
+struct BwdArgs {        // preprocess backward
+  sr_gaussians g;
+  const sr_camera* cams;
+  int n_views;
+  CfgDev cfg;
+  Ws ws;
+  sr_grads out;
+};
+
+struct BinArgs {        // binning and sort
+  int64_t n;
+  int n_views;
+  int passes;
+  unsigned long long cap;
+  int64_t total_tiles;
+  int spin_limit;
+  Ws ws;
+};
+
+struct RenderArgs {     // forward and backward composite
+  const float4* rec;
+  const uint32_t* vals0;
+  const uint32_t* vals1;
+  const uint2* ranges;
+  const ViewInfo* views;
+  const Status* status;
+  int n_views;
+  CfgDev cfg;
+  float* images;
+  float* t_final;
+  uint32_t* n_contrib;
+  const float* d_images;
+  float* d2;
+};
+
+cudaError_t launch_preprocess_fwd(const PreArgs& a, cudaStream_t st, int sms);
+cudaError_t launch_preprocess_bwd(const BwdArgs& a, cudaStream_t st, int sms);
+cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms);
+cudaError_t launch_bin_phase2(const BinArgs& a, const int* run, long long keys_known, cudaStream_t st);
+cudaError_t launch_render_fwd(const RenderArgs& a, int mode, int64_t total_tiles, cudaStream_t st);
+cudaError_t launch_render_bwd(const RenderArgs& a, int mode, int64_t total_tiles, cudaStream_t st);
+
+}  // namespace sr

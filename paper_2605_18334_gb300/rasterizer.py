@@ -1,0 +1,264 @@
+"""Torch-facing API of the skew-Gaussian rasterizer.
+
+PyTorch supplies device memory, streams and autograd plumbing only; every
+stage runs in ``libskewraster.so`` through the C ABI (``native``):
+
+    rast = Rasterizer(GaussianDesc.of(g), cameras, Config())
+    out = rast.forward(g)                    # sr_preprocess, sr_bin_sort, sr_render_fwd
+    grads = rast.backward(g, d_images)       # sr_render_bwd
+
+``render(...)`` wraps the same calls in a ``torch.autograd.Function``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import native as N
+
+_TAG = {torch.float32: N.SR_F32, torch.bfloat16: N.SR_BF16, torch.float16: N.SR_F16}
+
+
+@dataclass
+class Config:
+    """Rasterizer constants (sr_config)."""
+    tile: int = 16
+    alpha_min: float = 1.0 / 255.0
+    alpha_max: float = 0.99
+    t_stop: float = 1e-4
+    dilation: float = 0.3
+    fov_clamp: float = 1.3
+    near_z: float = 0.2
+    bg: tuple = (0.0, 0.0, 0.0)
+    antialias_comp: bool = True
+    sort_spin_limit: int = 0
+
+    def to_c(self) -> N.sr_config:
+        c = N.sr_config()
+        c.tile_w = c.tile_h = int(self.tile)
+        c.alpha_min, c.alpha_max, c.t_stop = self.alpha_min, self.alpha_max, self.t_stop
+        c.dilation, c.fov_clamp, c.near_z = self.dilation, self.fov_clamp, self.near_z
+        for k in range(3):
+            c.bg[k] = float(self.bg[k])
+        c.antialias_comp = 1 if self.antialias_comp else 0
+        c.sort_spin_limit = int(self.sort_spin_limit)
+        return c
+
+
+def camera_from_dict(cam: dict) -> N.sr_camera:
+    """sr_camera_from_gl on a camera dict (c2w_gl, width, height, fovx, fovy),
+    then explicit intrinsics overrides (fx, fy, cx, cy, tan_fovx, tan_fovy)."""
+    c = N.sr_camera_from_gl(np.asarray(cam["c2w_gl"], np.float64), cam["width"], cam["height"], cam["fovx"],
+                            cam["fovy"])
+    for k in ("fx", "fy", "cx", "cy", "tan_fovx", "tan_fovy"):
+        if k in cam:
+            setattr(c, k, float(np.float32(cam[k])))
+    return c
+
+
+@dataclass
+class Gaussians:
+    """Device tensors of one scene (layouts of sr_gaussians)."""
+    means: torch.Tensor
+    log_scales: torch.Tensor
+    quats: torch.Tensor
+    opacity_logits: torch.Tensor
+    skew: torch.Tensor
+    sh: torch.Tensor
+    sh_degree: int
+    split_dir: torch.Tensor | None = None
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    @staticmethod
+    def from_scene(scene, device="cuda", sh_dtype=torch.float32, scale_dtype=torch.float32,
+                   skew_dtype=torch.float32) -> "Gaussians":
+        t = lambda a, dt=torch.float32: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).to(
+            device=device, dtype=dt).contiguous()
+        return Gaussians(t(scene.means), t(scene.log_scales, scale_dtype), t(scene.quats), t(scene.opacity_logits),
+                         t(scene.skew, skew_dtype), t(scene.sh, sh_dtype), int(scene.sh_degree),
+                         None if scene.split_dir is None else t(scene.split_dir, skew_dtype))
+
+    def to_c(self) -> N.sr_gaussians:
+        for name in ("means", "quats", "opacity_logits"):
+            if getattr(self, name).dtype != torch.float32:
+                raise TypeError(f"{name} must be float32")
+        g = N.sr_gaussians()
+        g.means = self.means.data_ptr()
+        g.log_scales = self.log_scales.data_ptr()
+        g.quats = self.quats.data_ptr()
+        g.opacity_logits = self.opacity_logits.data_ptr()
+        g.skew = self.skew.data_ptr()
+        g.split_dir = self.split_dir.data_ptr() if self.split_dir is not None else None
+        g.sh = self.sh.data_ptr()
+        g.n = self.n
+        g.sh_degree = int(self.sh_degree)
+        g.two_opacities = 1 if self.opacity_logits.dim() == 2 else 0
+        g.dt_sh = _TAG[self.sh.dtype]
+        g.dt_scale = _TAG[self.log_scales.dtype]
+        g.dt_skew = _TAG[self.skew.dtype]
+        for t in (self.means, self.log_scales, self.quats, self.opacity_logits, self.skew, self.sh):
+            if not t.is_contiguous() or not t.is_cuda:
+                raise ValueError("Gaussian attributes must be contiguous CUDA tensors")
+        return g
+
+
+def _stream_ptr(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Rasterizer:
+    """One plan (Gaussian count, SH degree, cameras) and its device buffers."""
+
+    def __init__(self, gaussians: Gaussians, cameras: list, config: Config | None = None,
+                 key_capacity: int | None = None, device=None):
+        self.config = config or Config()
+        self.cfg_c = self.config.to_c()
+        self.cams = [c if isinstance(c, N.sr_camera) else camera_from_dict(c) for c in cameras]
+        self.device = torch.device(device) if device is not None else gaussians.means.device
+        self.n_views = len(self.cams)
+        self._g_desc = gaussians.to_c()
+        raw = b"".join(bytes(c) for c in self.cams)
+        self.cams_dev = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(self.device)
+        if key_capacity is None:
+            key_capacity = max(1 << 16, 8 * gaussians.n * self.n_views)
+        self._make_plan(int(key_capacity))
+
+    def _make_plan(self, key_capacity: int):
+        key_capacity = min(key_capacity, 0xFFFFFFFF)
+        self.plan = N.sr_plan_init(self.cfg_c, self._g_desc, self.cams, key_capacity)
+        self.ws = torch.empty(int(self.plan.ws_bytes), dtype=torch.uint8, device=self.device)
+        p = self.plan
+        self.images = torch.empty(int(p.image_offset[self.n_views]), dtype=torch.float32, device=self.device)
+        self.t_final = torch.empty(int(p.total_pixels), dtype=torch.float32, device=self.device)
+        self.n_contrib = torch.empty(int(p.total_pixels), dtype=torch.int32, device=self.device)
+
+    @property
+    def key_capacity(self) -> int:
+        return int(self.plan.key_capacity)
+
+    def view_image(self, flat: torch.Tensor, v: int) -> torch.Tensor:
+        p = self.plan
+        return flat[p.image_offset[v]:p.image_offset[v + 1]].view(3, p.height[v], p.width[v])
+
+    def view_state(self, flat: torch.Tensor, v: int) -> torch.Tensor:
+        p = self.plan
+        return flat[p.pixel_offset[v]:p.pixel_offset[v + 1]].view(p.height[v], p.width[v])
+
+    # -- stages ------------------------------------------------------------
+    def preprocess(self, g: Gaussians, stream=None):
+        N.sr_preprocess(self.plan, g.to_c(), self.cams_dev.data_ptr(), self.cfg_c, self.ws.data_ptr(),
+                        _stream_ptr(stream))
+
+    def bin_sort(self, stream=None, sync: bool = True):
+        return N.sr_bin_sort(self.plan, self.cfg_c, self.ws.data_ptr(), _stream_ptr(stream), sync=sync)
+
+    def render_fwd(self, stream=None):
+        N.sr_render_fwd(self.plan, self.cfg_c, self.ws.data_ptr(), self.images.data_ptr(), self.t_final.data_ptr(),
+                        self.n_contrib.data_ptr(), _stream_ptr(stream))
+
+    def forward(self, g: Gaussians, stream=None, grow: bool = True) -> torch.Tensor:
+        """Preprocess, bin and sort (growing the key capacity if the frame
+        needs more), composite.  Returns the flat image buffer."""
+        self.preprocess(g, stream)
+        try:
+            self.keys = self.bin_sort(stream)
+        except N.SkewRasterError as e:
+            if e.status != N.SR_ERR_CAPACITY or not grow:
+                raise
+            self._make_plan(int(e.keys_needed * 1.25) + 1024)
+            self.preprocess(g, stream)
+            self.keys = self.bin_sort(stream)
+        self.render_fwd(stream)
+        return self.images
+
+    def backward(self, g: Gaussians, d_images: torch.Tensor, stream=None, want_stats: bool = False) -> dict:
+        """Gradients of sum(d_images * images) w.r.t. every attribute (FP32)."""
+        if d_images.dtype != torch.float32 or not d_images.is_contiguous() or d_images.numel() != self.images.numel():
+            raise ValueError("d_images must be a contiguous float32 tensor shaped like the image buffer")
+        dev = self.device
+        n = g.n
+        out = dict(means=torch.empty(n, 3, device=dev), log_scales=torch.empty(n, 3, device=dev),
+                   quats=torch.empty(n, 4, device=dev),
+                   opacity_logits=torch.empty(g.opacity_logits.shape, device=dev),
+                   skew=torch.empty(n, 3, device=dev), sh=torch.empty(g.sh.shape, device=dev),
+                   split_dir=torch.empty(n, 3, device=dev) if g.split_dir is not None else None)
+        if want_stats:
+            out["means2d_abs"] = torch.empty(n, device=dev)
+            out["depth_grad"] = torch.empty(n, device=dev)
+        gr = N.sr_grads()
+        for k in ("means", "log_scales", "quats", "opacity_logits", "skew", "sh", "split_dir", "means2d_abs",
+                  "depth_grad"):
+            t = out.get(k)
+            setattr(gr, k, t.data_ptr() if t is not None else None)
+        N.sr_render_bwd(self.plan, g.to_c(), self.cams_dev.data_ptr(), self.cfg_c, self.ws.data_ptr(),
+                        d_images.data_ptr(), self.t_final.data_ptr(), self.n_contrib.data_ptr(), gr,
+                        _stream_ptr(stream))
+        return out
+
+    # -- debugging views of the workspace (read-only copies) --------------
+    def _slot(self, k: int, nbytes: int) -> torch.Tensor:
+        off = int(self.plan.off[k])
+        return self.ws[off:off + nbytes]
+
+    def sorted_keys(self):
+        """(keys uint64 as int64 tensor, vals int32) of the last bin_sort."""
+        kn = int(self.keys)
+        st = self._slot(0, 16).clone().cpu().numpy()
+        buf = int(st[4:8].view(np.uint32)[0])
+        keys = self._slot(8 + buf, 8 * kn).view(torch.int64)
+        vals = self._slot(10 + buf, 4 * kn).view(torch.int32)
+        return keys, vals
+
+    def records(self) -> torch.Tensor:
+        m = self.plan.n * self.n_views
+        return self._slot(2, 64 * m).view(torch.float32).view(m, 16)
+
+    def depth_bits(self) -> torch.Tensor:
+        m = self.plan.n * self.n_views
+        return self._slot(3, 4 * m).view(torch.int32)
+
+    def tile_counts(self) -> torch.Tensor:
+        m = self.plan.n * self.n_views
+        return self._slot(5, 4 * m).view(torch.int32)
+
+    def rects(self) -> torch.Tensor:
+        m = self.plan.n * self.n_views
+        return self._slot(4, 8 * m).view(torch.int32).view(m, 2)
+
+    def d2(self) -> torch.Tensor:
+        m = self.plan.n * self.n_views
+        return self._slot(15, 64 * m).view(torch.float32).view(m, 16)
+
+
+class _RasterizeFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, rast, sh_degree, means, log_scales, quats, opacity_logits, skew, sh, split_dir):
+        g = Gaussians(means.detach(), log_scales.detach(), quats.detach(), opacity_logits.detach(), skew.detach(),
+                      sh.detach(), sh_degree, None if split_dir is None else split_dir.detach())
+        images = rast.forward(g).clone()
+        ctx.rast = rast
+        ctx.g = g
+        ctx.mark_non_differentiable()
+        return images
+
+    @staticmethod
+    def backward(ctx, d_images):
+        g = ctx.g
+        gr = ctx.rast.backward(g, d_images.contiguous().float())
+        cast = lambda t, like: None if t is None else t.to(like.dtype)
+        return (None, None, gr["means"], cast(gr["log_scales"], g.log_scales), gr["quats"], gr["opacity_logits"],
+                cast(gr["skew"], g.skew), cast(gr["sh"], g.sh),
+                None if g.split_dir is None else cast(gr["split_dir"], g.split_dir))
+
+
+def render(rast: Rasterizer, means, log_scales, quats, opacity_logits, skew, sh, sh_degree: int, split_dir=None):
+    """Differentiable render of every view of ``rast``: the flat image buffer
+    (views at rast.plan.image_offset[v], each [3,H,W])."""
+    return _RasterizeFn.apply(rast, sh_degree, means, log_scales, quats, opacity_logits, skew, sh, split_dir)

@@ -1,0 +1,359 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 oracle.
+
+Bars (design notes): depth keys, tile counts and sorted key lists bit-exact
+(Gaussians whose FP64 tile edge lies within 2e-3 px of a pixel-centre
+boundary are excluded and counted); images within 1e-4 max abs per channel
+on pixels that are not decision-ambiguous (counted); gradients within 1e-3
+relative error per tensor.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2605_18334_gb300 import scenes
+from paper_2605_18334_gb300.rasterizer import Config, Gaussians, Rasterizer
+from tests.parity_util import (GRAD_RTOL, IMG_ATOL, compare_keys, dequantised, gpu_records_to_oracle_layout,
+                               image_error, oracle_config, rel_err, tile_ranges)
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU-only container
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+def gpu_forward(scene, cams, cfg=None, key_capacity=None, **dtypes):
+    cfg = cfg or Config()
+    g = Gaussians.from_scene(scene, **dtypes)
+    r = Rasterizer(g, cams, cfg, key_capacity=key_capacity)
+    r.forward(g)
+    torch.cuda.synchronize()
+    return r, g
+
+
+def oracle_view(scene, cam, cfg, pixels=None):
+    oc = oracle.camera_from_gl(cam)
+    ocfg = oracle_config(cfg)
+    pre = oracle.preprocess(scene, oc, ocfg)
+    out = oracle.render(scene, oc, ocfg, pixels=pixels, pre=pre)
+    return oc, ocfg, pre, out
+
+
+def check_view(r, scene, cams, v, cfg, pixels=None, check_keys=True):
+    """Compare view v of the GPU frame with the oracle; returns stats."""
+    cam = cams[v]
+    oc, ocfg, pre, out = oracle_view(scene, cam, cfg, pixels)
+    n = scene.n
+    p = r.plan
+    stats = {}
+    # depth keys and tile counts
+    depth = r.depth_bits().cpu().numpy().view(np.uint32)[v * n:(v + 1) * n]
+    np.testing.assert_array_equal(depth, pre["depth_bits"])
+    cnt = r.tile_counts().cpu().numpy()[v * n:(v + 1) * n]
+    rect = pre["rect"]
+    or_cnt = np.where(pre["visible"], (rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1]), 0)
+    amb = pre["rect_ambig"]
+    np.testing.assert_array_equal(cnt[~amb], or_cnt[~amb])
+    stats["rect_ambiguous"] = int(amb.sum())
+    # records of the rendered Gaussians
+    sel = np.nonzero((cnt > 0) & ~amb)[0]
+    g = gpu_records_to_oracle_layout(r.records().cpu().numpy()[v * n:(v + 1) * n][sel])
+    o = pre["rec"][sel]
+    np.testing.assert_allclose(g["mx"], o[:, 0], atol=2e-3, rtol=1e-6)
+    np.testing.assert_allclose(g["my"], o[:, 1], atol=2e-3, rtol=1e-6)
+    for k, col in (("a", 2), ("b", 3), ("c", 4)):
+        scale = np.maximum(np.abs(o[:, 2]), np.abs(o[:, 4]))
+        assert np.all(np.abs(g[k] - o[:, col]) <= 2e-4 * scale + 1e-9), k
+    bscale = np.maximum(1.0, np.hypot(o[:, 5], o[:, 6]))
+    assert np.all(np.abs(g["bx"] - o[:, 5]) <= 1e-3 * bscale)
+    assert np.all(np.abs(g["by"] - o[:, 6]) <= 1e-3 * bscale)
+    np.testing.assert_allclose(g["m"], o[:, 7], atol=2e-6, rtol=1e-4)
+    np.testing.assert_allclose(g["h"], o[:, 8], atol=2e-6, rtol=1e-4)
+    np.testing.assert_allclose(g["rgb"], o[:, 11:14], atol=2e-5, rtol=1e-5)
+    # sorted keys
+    keys, vals = r.sorted_keys()
+    keys = keys.cpu().numpy().view(np.uint64)
+    vals = vals.cpu().numpy().astype(np.int64)
+    tb = int(p.tile_base[v]), int(p.tile_base[v + 1])
+    sel_k = ((keys >> np.uint64(32)) >= tb[0]) & ((keys >> np.uint64(32)) < tb[1])
+    if check_keys:
+        ok, ov = oracle.bin_keys(pre, oc, ocfg, tile_base=tb[0], val_base=v * n)
+        stats["key_excluded"] = compare_keys(keys[sel_k], vals[sel_k], ok, ov, np.nonzero(amb)[0] + v * n)
+        stats["keys"] = int(sel_k.sum())
+    # image, transmittance, last contributor
+    img = r.view_image(r.images, v).cpu().numpy()
+    T = r.view_state(r.t_final, v).cpu().numpy()
+    nc = r.view_state(r.n_contrib, v).cpu().numpy().astype(np.int64)
+    H, W = cam["height"], cam["width"]
+    if pixels is None:
+        pix = oracle.all_pixels(oc)
+        amb_px = out["ambiguous"].reshape(-1)
+        or_rgb = out["rgb"].reshape(-1, 3)
+        or_T = out["T"].reshape(-1)
+        or_last = out["last"].reshape(-1)
+    else:
+        pix = np.asarray(pixels)
+        amb_px, or_rgb, or_T, or_last = out["ambiguous"], out["rgb"], out["T"], out["last"]
+    gi = img[:, pix[:, 1], pix[:, 0]].T
+    d = np.abs(gi.astype(np.float64) - or_rgb)
+    d[amb_px] = 0
+    stats["img_max_abs"] = float(d.max()) if d.size else 0.0
+    stats["ambiguous_px"] = int(amb_px.sum())
+    assert stats["img_max_abs"] <= IMG_ATOL, stats
+    dT = np.abs(T[pix[:, 1], pix[:, 0]] - or_T)
+    dT[amb_px] = 0
+    assert dT.max() <= 1e-4, dT.max()
+    # last blended Gaussian (unique once the gate and stop decisions agree)
+    rng = tile_ranges(keys, int(p.total_tiles))
+    tiles_x = -(-W // 16)
+    tile = tb[0] + (pix[:, 1] // 16) * tiles_x + pix[:, 0] // 16
+    ncp = nc[pix[:, 1], pix[:, 0]]
+    if len(vals) == 0:
+        gl = np.full(len(pix), -1, np.int64)
+    else:
+        gl = np.where(ncp > 0, vals[np.clip(rng[tile, 0] + ncp - 1, 0, len(vals) - 1)] - v * n, -1)
+    ok = ~amb_px
+    np.testing.assert_array_equal(gl[ok], or_last[ok])
+    return stats, pre, out
+
+
+# ---------------------------------------------------------------------------
+# forward
+# ---------------------------------------------------------------------------
+
+def test_cube_1k_64px_full_frame():
+    """1,000 skew Gaussians, 64x64 view, SH degree 0 (small workload)."""
+    sc = scenes.cube_1k()
+    cams = [scenes.identity_camera(64, 64)]
+    r, _ = gpu_forward(sc, cams)
+    stats, _, _ = check_view(r, sc, cams, 0, Config())
+    assert stats["keys"] > 1000
+
+
+@pytest.mark.parametrize("W,H", [(37, 23), (16, 16), (1, 1), (95, 200)])
+def test_ragged_image_sizes(W, H):
+    sc = scenes.cube_1k(seed=3, n=600)
+    cams = [scenes.identity_camera(W, H)]
+    r, _ = gpu_forward(sc, cams)
+    check_view(r, sc, cams, 0, Config())
+
+
+def test_cluster_100k_720p_sampled_pixels():
+    """100k Gaussians, SH degree 3, 1280x720: keys bit-exact for the whole
+    frame, image at 4,000 sampled pixels."""
+    sc = scenes.cluster()
+    cams = [scenes.identity_camera(1280, 720)]
+    r, _ = gpu_forward(sc, cams)
+    rng = np.random.default_rng(0)
+    pix = np.stack([rng.integers(0, 1280, 4000), rng.integers(0, 720, 4000)], 1).astype(np.int32)
+    stats, _, _ = check_view(r, sc, cams, 0, Config(), pixels=pix)
+    assert stats["keys"] > 100_000
+
+
+@pytest.mark.parametrize("two,split", [(True, False), (True, True), (False, True)])
+def test_enhanced_opacity_modes(two, split):
+    sc = scenes.cluster(seed=5, n=3000, sh_degree=2, two_opacities=two, split=split)
+    cams = [scenes.identity_camera(160, 120)]
+    r, _ = gpu_forward(sc, cams)
+    check_view(r, sc, cams, 0, Config())
+
+
+def test_background_and_config_variants():
+    sc = scenes.cube_1k(seed=8, n=800)
+    cams = [scenes.identity_camera(80, 60)]
+    cfg = Config(bg=(0.2, 0.5, 0.9), antialias_comp=False, dilation=0.2, alpha_max=0.95, t_stop=1e-3)
+    r, _ = gpu_forward(sc, cams, cfg)
+    check_view(r, sc, cams, 0, cfg)
+
+
+@pytest.mark.parametrize("dt", [torch.bfloat16, torch.float16])
+def test_reduced_precision_storage_arithmetic_error(dt):
+    """SH, log-scales and skew stored in BF16/FP16: against the oracle fed the
+    dequantised attributes the FP32 bar holds (arithmetic error)."""
+    sc = scenes.cluster(seed=6, n=5000)
+    cams = [scenes.identity_camera(200, 150)]
+    r, _ = gpu_forward(sc, cams, sh_dtype=dt, scale_dtype=dt, skew_dtype=dt)
+    check_view(r, dequantised(sc, dt, dt, dt), cams, 0, Config())
+
+
+def test_multi_view_batched_frame():
+    """Several views of mixed resolution in one plan: shared key pool, one
+    composite launch over all tiles."""
+    sc = scenes.unbounded(seed=7, n=20_000)
+    cams = scenes.trajectory_cameras(5, resolutions=((64, 36), (128, 72), (96, 96)))
+    r, _ = gpu_forward(sc, cams)
+    for v in range(len(cams)):
+        check_view(r, sc, cams, v, Config())
+
+
+def test_zero_skew_binning_equals_symmetric_footprint():
+    """Gaussians with skew exactly 0 get kappa = 1, so their tile sets are
+    those of the plain 3DGS footprint rho^2 = 2 ln(o comp / tau)(1 + 2^-10)
+    (computed here independently in FP64); GPU keys match bit for bit."""
+    sc = scenes.unbounded(seed=4, n=20_000, skew_sigma=2.0, zero_skew_fraction=0.5)
+    cams = [scenes.orbit_camera(0.4, 320, 180)]
+    r, _ = gpu_forward(sc, cams)
+    stats, pre, _ = check_view(r, sc, cams, 0, Config())
+    zero = np.all(sc.skew == 0, axis=1) & pre["visible"]
+    rec = pre["rec"]
+    tau = np.float32(1 / 255)
+    omax = rec[:, 14] * np.maximum(rec[:, 15], rec[:, 16])
+    on = zero & (omax >= tau)
+    rho2 = 2 * np.log(omax[on] / tau) * (1 + 2 ** -10)
+    np.testing.assert_allclose(pre["ext"][on, 2], rho2, rtol=1e-12)
+
+
+def test_empty_and_fully_culled_scenes():
+    sc = scenes.cube_1k(seed=1, n=50)
+    cams = [scenes.identity_camera(48, 32)]
+    # all behind the camera
+    sc.means[:, 2] = -3.0
+    r, _ = gpu_forward(sc, cams, cfg=Config(bg=(0.1, 0.2, 0.3)))
+    img = r.view_image(r.images, 0).cpu().numpy()
+    assert r.keys == 0
+    np.testing.assert_allclose(img, np.broadcast_to(np.float32([0.1, 0.2, 0.3])[:, None, None], img.shape))
+    # no Gaussians at all
+    sc0 = sc.subset(np.arange(0))
+    r0, _ = gpu_forward(sc0, cams)
+    assert r0.keys == 0
+    assert float(r0.view_image(r0.images, 0).abs().max()) == 0.0
+
+
+def test_capacity_overflow_reports_and_recovers():
+    from paper_2605_18334_gb300 import native as N
+
+    sc = scenes.cube_1k()
+    cams = [scenes.identity_camera(64, 64)]
+    g = Gaussians.from_scene(sc)
+    r = Rasterizer(g, cams, Config(), key_capacity=100)
+    r.preprocess(g)
+    with pytest.raises(N.SkewRasterError) as e:
+        r.bin_sort()
+    assert e.value.status == N.SR_ERR_CAPACITY and e.value.keys_needed > 100
+    r.forward(g)  # grows the plan and retries
+    assert r.key_capacity >= e.value.keys_needed
+    check_view(r, sc, cams, 0, Config())
+
+
+def test_graph_captured_frame_matches_eager():
+    """The non-blocking bin/sort (no key-count read-back) inside a CUDA graph
+    gives the eager frame's image bit for bit."""
+    sc = scenes.cluster(seed=2, n=20_000)
+    cams = [scenes.identity_camera(256, 144)]
+    g = Gaussians.from_scene(sc)
+    r = Rasterizer(g, cams, Config(), key_capacity=1 << 20)
+    r.forward(g)
+    torch.cuda.synchronize()
+    eager = r.images.clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        r.preprocess(g, s)
+        r.bin_sort(s, sync=False)
+        r.render_fwd(s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        r.preprocess(g, s)
+        r.bin_sort(s, sync=False)
+        r.render_fwd(s)
+    r.images.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(r.images, eager)
+
+
+# ---------------------------------------------------------------------------
+# backward
+# ---------------------------------------------------------------------------
+
+GRAD_FIELDS = ["means", "log_scales", "quats", "opacity_logits", "skew", "sh"]
+
+
+def compare_grads(gr, og, fields, rtol=GRAD_RTOL):
+    errs = {}
+    for k in fields:
+        a = gr[k].detach().cpu().numpy().astype(np.float64)
+        b = og[k]
+        errs[k] = rel_err(a, b)
+    assert all(e <= rtol for e in errs.values()), errs
+    return errs
+
+
+def test_backward_fd_crop_2k():
+    """2k Gaussians projecting near a 32x32 crop of the 1280x720 view, full
+    upstream gradient N(0,1): every attribute gradient within 1e-3."""
+    sc, cam = scenes.fd_crop_scene()
+    cams = [cam]
+    r, g = gpu_forward(sc, cams)
+    dimg = torch.as_tensor(scenes.upstream_grad(3, 32, 32)).cuda().reshape(-1).contiguous()
+    gr = r.backward(g, dimg)
+    oc = oracle.camera_from_gl(cam)
+    og = oracle.render_backward(sc, oc, oracle_config(Config()), scenes.upstream_grad(3, 32, 32))
+    compare_grads(gr, og, GRAD_FIELDS)
+    # 2D gradients of the records too
+    d2 = r.d2().cpu().numpy()
+    cnt = r.tile_counts().cpu().numpy() > 0
+    o2 = og["d2"]
+    for col in (0, 1, 2, 3, 4, 5, 6, 7, 11, 12, 13):
+        assert rel_err(d2[cnt, col], o2[cnt, col]) <= GRAD_RTOL, col
+
+
+@pytest.mark.parametrize("two,split,deg", [(True, False, 1), (True, True, 3), (False, False, 0)])
+def test_backward_modes(two, split, deg):
+    sc = scenes.cluster(seed=9, n=1500, sh_degree=deg, two_opacities=two, split=split)
+    cams = [scenes.identity_camera(96, 72)]
+    r, g = gpu_forward(sc, cams, cfg=Config(bg=(0.3, 0.2, 0.1)))
+    up = scenes.upstream_grad(9, 72, 96)
+    gr = r.backward(g, torch.as_tensor(up).cuda().reshape(-1).contiguous())
+    og = oracle.render_backward(sc, oracle.camera_from_gl(cams[0]), oracle_config(Config(bg=(0.3, 0.2, 0.1))), up)
+    compare_grads(gr, og, GRAD_FIELDS + (["split_dir"] if split else []))
+
+
+def test_backward_cluster_100k_sparse_upstream():
+    """Full 100k / 720p frame; the upstream gradient is nonzero on 400
+    random pixels, so the oracle can sum the exact per-Gaussian gradients."""
+    sc = scenes.cluster()
+    cams = [scenes.identity_camera(1280, 720)]
+    r, g = gpu_forward(sc, cams)
+    up, flat = scenes.sparse_upstream_grad(1, 720, 1280, 400)
+    gr = r.backward(g, torch.as_tensor(up).cuda().reshape(-1).contiguous())
+    pix = np.stack([flat % 1280, flat // 1280], 1).astype(np.int32)
+    og = oracle.render_backward(sc, oracle.camera_from_gl(cams[0]), oracle_config(Config()),
+                                up.reshape(3, -1)[:, flat].T, pixels=pix)
+    compare_grads(gr, og, GRAD_FIELDS)
+
+
+def test_backward_batched_views_sum():
+    """Gradients of a multi-view plan are the sum over views."""
+    sc = scenes.cluster(seed=12, n=3000, sh_degree=1)
+    cams = [scenes.identity_camera(64, 48), scenes.camera(scenes.look_at_c2w_cv((0.5, -0.2, 0.5), (0, 0, 4)), 80, 40)]
+    r, g = gpu_forward(sc, cams)
+    ups = [scenes.upstream_grad(20 + v, c["height"], c["width"]) for v, c in enumerate(cams)]
+    flat = torch.as_tensor(np.concatenate([u.reshape(-1) for u in ups])).cuda().contiguous()
+    gr = r.backward(g, flat)
+    tot = None
+    for v, c in enumerate(cams):
+        og = oracle.render_backward(sc, oracle.camera_from_gl(c), oracle_config(Config()), ups[v])
+        tot = og if tot is None else {k: (tot[k] + og[k] if og[k] is not None else None) for k in og}
+    compare_grads(gr, tot, GRAD_FIELDS)
+
+
+def test_autograd_function():
+    from paper_2605_18334_gb300.rasterizer import render
+
+    sc = scenes.cube_1k(seed=2, n=500)
+    cams = [scenes.identity_camera(48, 48)]
+    g = Gaussians.from_scene(sc)
+    r = Rasterizer(g, cams, Config())
+    leaves = [t.clone().requires_grad_(True) for t in (g.means, g.log_scales, g.quats, g.opacity_logits, g.skew, g.sh)]
+    img = render(r, *leaves[:5], leaves[5], sh_degree=0)
+    up = torch.as_tensor(scenes.upstream_grad(4, 48, 48)).cuda().reshape(-1)
+    (img * up).sum().backward()
+    og = oracle.render_backward(sc, oracle.camera_from_gl(cams[0]), oracle_config(Config()),
+                                scenes.upstream_grad(4, 48, 48))
+    for t, k in zip(leaves, GRAD_FIELDS):
+        assert rel_err(t.grad.cpu().numpy(), og[k]) <= GRAD_RTOL, k
