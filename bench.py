@@ -1,0 +1,474 @@
+#!/usr/bin/env python
+"""Benchmark of the skew-Gaussian rasterizer on one GB300 (or N replicas).
+
+Workload (default ``unbounded_1m``): 1M skew Gaussians (60% in a ball of
+radius 2, 40% on a shell of radius 20-50), SH degree 3, one 1920x1080 view
+on a radius-6 orbit, upstream image gradient ~ N(0,1).  A step is one pass
+of the hot path: sr_preprocess, sr_bin_sort, sr_render_fwd, sr_render_bwd
+(which includes the projection backward).  Inputs are resident in HBM when
+the timed region starts; L2 is flushed (a 256 MiB memset) before every
+timed step, outside the step's CUDA events.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd / fwd+bwd frames/s, 1M skew Gaussians at 1080p: batched+BF16 vs plain FP32"
+UNIT = "frames/s"
+HBM_FALLBACK = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000, help="Gaussians (default: the 1M workload)")
+    ap.add_argument("--no-variants", action="store_true", help="only the headline FP32 fwd+bwd form")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for the CPU baseline")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def workload(n):
+    from paper_2605_18334_gb300 import scenes
+
+    sc = scenes.unbounded(seed=2, n=n)
+    cam = scenes.orbit_camera(0.0, 1920, 1080)
+    up = scenes.upstream_grad(2, 1080, 1920)
+    return sc, cam, up
+
+
+def config_dict(n):
+    return {"workload": "unbounded_1m" if n == 1_000_000 else f"unbounded_{n}", "gaussians": n,
+            "resolution": "1920x1080", "views": 1, "sh_degree": 3, "skew": "N(0,1.5^2) local frame",
+            "step": "preprocess+bin_sort+render_fwd+render_bwd", "l2": "flushed (256 MiB memset) before each step"}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.bus_id:
+                cmd += ["-i", self.bus_id]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (one process per GPU; no data-path collective)
+# ---------------------------------------------------------------------------
+
+def dist_setup(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+
+    from paper_2605_18334_gb300 import native as N
+    from paper_2605_18334_gb300.rasterizer import Config, Gaussians, Rasterizer
+
+    rank, world = dist_setup(args)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sc, cam, up = workload(args.n)
+    g = Gaussians.from_scene(sc, device=dev)
+    cfg = Config()
+    r = Rasterizer(g, [cam], cfg, key_capacity=int(12 * args.n))
+    d_img = torch.as_tensor(up, device=dev).reshape(-1).contiguous()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(gs, rr, dimg, backward=True):
+        rr.forward(gs)
+        if backward:
+            return rr.backward(gs, dimg)
+        return None
+
+    for _ in range(max(3, args.warmup)):
+        step(g, r, d_img)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
+    props = torch.cuda.get_device_properties(dev)
+    bus = getattr(props, "pci_bus_id", None)
+    launches0 = N.sr_kernel_launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(bus if isinstance(bus, str) else None) as clk:
+        for k in range(K):
+            flush.zero_()
+            e = ev[k]
+            e[0].record(stream)
+            r.preprocess(g)
+            e[1].record(stream)
+            r.keys = r.bin_sort()
+            e[2].record(stream)
+            r.render_fwd()
+            e[3].record(stream)
+            r.backward(g, d_img)
+            e[4].record(stream)
+        torch.cuda.synchronize()
+    launches = N.sr_kernel_launches() - launches0
+    barrier(world)
+    stage_ms = np.array([[ev[k][i].elapsed_time(ev[k][i + 1]) for i in range(4)] for k in range(K)])
+    step_ms = stage_ms.sum(1)
+    total_ms = max_over_ranks(float(step_ms.sum()), world)
+    ms_per_step = total_ms / K
+    value = world * K / (total_ms / 1e3)
+    tested, blended = N.sr_frame_counters(r.plan, r.ws.data_ptr(), stream.cuda_stream)
+    clocks = clk.summary()
+
+    out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K,
+           "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_dict(args.n),
+           "gpu_launches": int(launches)}
+    fwd_ms = stage_ms[:, :3].sum(1).mean()
+    out["stages_ms"] = {k: round(float(v), 4) for k, v in
+                        zip(["preprocess", "bin_sort", "render_fwd", "render_bwd"], stage_ms.mean(0))}
+    out["fwd_frames_per_s"] = round(1e3 / fwd_ms, 2)
+    out["keys"] = int(r.keys)
+    out["pairs_tested"] = tested
+    out["pairs_blended"] = blended
+    out["blends_per_s"] = round(blended / (stage_ms[:, 2].mean() / 1e3), 1)
+    out["clocks"] = clocks
+
+    # roofline of the dominant stage (measured live with the events above)
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK))
+    sms = props.multi_processor_count
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    stage_mean = stage_ms.mean(0)
+    dom = int(np.argmax(stage_mean))
+    alu_peak = sms * 128 * max_mhz * 1e6 / 1e12  # FP32 lane-ops/s (an FMA is one op), TOPS
+    if dom in (2, 3):
+        # blend loop: 25 FP32 ops per tested pair (forward), about 80 per blended pair backward
+        if dom == 2:
+            ops = tested * 25
+        else:
+            ops = tested * 25 + blended * 80
+        achieved = ops / (stage_mean[dom] / 1e3) / 1e12
+        out["roofline"] = {"kernel": ["preprocess", "bin_sort", "render_fwd", "render_bwd"][dom], "bound": "alu",
+                           "achieved": round(achieved, 3), "peak": round(alu_peak, 3), "unit": "TFLOP/s",
+                           "frac": round(achieved / alu_peak, 4), "traffic": None,
+                           "peak_source": f"{sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz (derived)"}
+    else:
+        b = 0.0
+        if dom == 0:
+            b = args.n * 248 + args.n * 16 + int((r.tile_counts() > 0).sum()) * 64
+        achieved = b / (stage_mean[dom] / 1e3) / 1e9
+        out["roofline"] = {"kernel": ["preprocess", "bin_sort"][dom], "bound": "hbm", "achieved": round(achieved, 1),
+                           "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None}
+    # HBM stages for reference
+    pre_bytes = args.n * 248 + args.n * 16 + int((r.tile_counts() > 0).sum()) * 64
+    out["hbm_stages"] = {"preprocess_GBps": round(pre_bytes / (stage_mean[0] / 1e3) / 1e9, 1),
+                         "bin_sort_GBps": round((int(r.keys) * (12 + 24 * r.plan.sort_passes)) /
+                                                (stage_mean[1] / 1e3) / 1e9, 1),
+                         "peak_GBps": hbm}
+
+    if not args.no_variants:
+        out["variants"] = variants(args, sc, cam, up, dev, flush)
+        out["e2e"] = e2e(args, sc, cam, up, dev, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(sc, cam, up, args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def timed(fn, K, flush, stream):
+    import torch
+
+    ts = []
+    for _ in range(K):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        ts.append((a, b))
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in ts]))
+
+
+def variants(args, sc, cam, up, dev, flush):
+    import torch
+
+    from paper_2605_18334_gb300.rasterizer import Config, Gaussians, Rasterizer
+
+    K = max(5, args.steps // 2)
+    stream = torch.cuda.current_stream()
+    res = {}
+    d_img = torch.as_tensor(up, device=dev).reshape(-1).contiguous()
+    for name, dt in (("fp32", torch.float32), ("bf16_storage", torch.bfloat16)):
+        g = Gaussians.from_scene(sc, device=dev, sh_dtype=dt, scale_dtype=dt, skew_dtype=dt)
+        r = Rasterizer(g, [cam], Config(), key_capacity=int(12 * args.n))
+        for _ in range(3):
+            r.forward(g)
+            r.backward(g, d_img)
+        fwd = timed(lambda: r.forward(g), K, flush, stream)
+        fb = timed(lambda: (r.forward(g), r.backward(g, d_img)), K, flush, stream)
+        res[name] = {"fwd_frames_per_s": round(1e3 / fwd, 2), "fwdbwd_frames_per_s": round(1e3 / fb, 2)}
+        del r, g
+        torch.cuda.empty_cache()
+    return res
+
+
+def e2e(args, sc, cam, up, dev, world):
+    """Same metric through the C ABI with host buffers: every step copies the
+    scene from pinned host memory, renders forward and backward, and reads the
+    image and all gradients back into pinned host memory."""
+    import torch
+
+    from paper_2605_18334_gb300.rasterizer import Config, Gaussians, Rasterizer
+
+    host = Gaussians.from_scene(sc, device="cpu")
+    for k in ("means", "log_scales", "quats", "opacity_logits", "skew", "sh"):
+        setattr(host, k, getattr(host, k).pin_memory())
+    g = Gaussians(*(torch.empty_like(getattr(host, k), device=dev) for k in
+                    ("means", "log_scales", "quats", "opacity_logits", "skew", "sh")), host.sh_degree)
+    up_h = torch.as_tensor(up).reshape(-1).contiguous().pin_memory()
+    d_img = torch.empty_like(up_h, device=dev)
+    r = Rasterizer(g, [cam], Config(), key_capacity=int(12 * args.n))
+    img_h = torch.empty(r.images.numel(), dtype=torch.float32).pin_memory()
+    grad_h = {k: torch.empty(getattr(host, k).shape, dtype=torch.float32).pin_memory()
+              for k in ("means", "log_scales", "quats", "opacity_logits", "skew", "sh")}
+    h2d = sum(getattr(host, k).numel() * getattr(host, k).element_size()
+              for k in ("means", "log_scales", "quats", "opacity_logits", "skew", "sh")) + up_h.numel() * 4
+    d2h = img_h.numel() * 4 + sum(t.numel() * 4 for t in grad_h.values())
+
+    def one():
+        for k in ("means", "log_scales", "quats", "opacity_logits", "skew", "sh"):
+            getattr(g, k).copy_(getattr(host, k), non_blocking=True)
+        d_img.copy_(up_h, non_blocking=True)
+        r.forward(g)
+        grads = r.backward(g, d_img)
+        img_h.copy_(r.images, non_blocking=True)
+        for k, t in grad_h.items():
+            t.copy_(grads[k], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    for _ in range(3):
+        one()
+    K = max(5, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        one()
+    dt = max_over_ranks(time.perf_counter() - t0, world)
+    return {"value": round(world * K / dt, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_frame_estimate(sc, cam, up, budget_s, seed=0):
+    """Time the FP64 oracle on a bounded pixel sample of the workload and
+    extrapolate to one full fwd+bwd frame: preprocess (all Gaussians) +
+    brute-force composite of every pixel + its backward.  Per-pixel costs
+    come from a linear fit over two sample sizes."""
+    import oracle
+
+    oracle.build()
+    oc = oracle.camera_from_gl(cam)
+    ocfg = oracle.config()
+    W, H = cam["width"], cam["height"]
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    pre = oracle.preprocess(sc, oc, ocfg)
+    t_pre = time.perf_counter() - t0
+
+    def fwd(n):
+        pix = np.stack([rng.integers(0, W, n), rng.integers(0, H, n)], 1).astype(np.int32)
+        t = time.perf_counter()
+        oracle.render(sc, oc, ocfg, pixels=pix, pre=pre)
+        return time.perf_counter() - t
+
+    def bwd(n):
+        pix = np.stack([rng.integers(0, W, n), rng.integers(0, H, n)], 1).astype(np.int32)
+        g = up.reshape(3, -1)[:, pix[:, 1] * W + pix[:, 0]].T
+        t = time.perf_counter()
+        oracle.render_backward(sc, oc, ocfg, g, pixels=pix, pre=pre)
+        return time.perf_counter() - t
+
+    def fit(fn, share):
+        # grow the sample until one call costs share * budget; linear fit of the last two
+        n_prev, t_prev = 8, fn(8)
+        n, t = 32, fn(32)
+        while 4 * (t - t_prev) + t_prev < share * budget_s and n < 65536:
+            n_prev, t_prev = n, t
+            n *= 4
+            t = fn(n)
+        slope = max((t - t_prev) / (n - n_prev), 1e-9)
+        return max(t - slope * n, 0.0), slope, n
+
+    af, bf, n2 = fit(fwd, 0.3)
+    ab, bb, m2 = fit(bwd, 0.3)
+    n1 = 8
+    frame_s = t_pre + af + bf * W * H + ab + bb * W * H
+    sample = (f"preprocess of all {sc.n} Gaussians, forward at {n1}+{n2} and backward at {n1}+{m2} random pixels "
+              f"of the 1920x1080 frame (brute force over every Gaussian), extrapolated linearly to all {W * H} pixels")
+    return frame_s, sample, oracle.num_threads(), time.perf_counter() - t0
+
+
+def cpu_baseline(sc, cam, up, budget_s):
+    frame_s, sample, cores, spent = oracle_frame_estimate(sc, cam, up, budget_s)
+    return {"value": round(1.0 / frame_s, 9), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "seconds_spent": round(spent, 1)}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc, cam, up = workload(args.n)
+    budget = max(2.0, min(args.cpu_budget, 120.0 / max(1, args.steps + args.warmup)))
+    for w in range(args.warmup):
+        oracle_frame_estimate(sc, cam, up, budget, seed=w)
+    frames = []
+    cores, sample = 1, ""
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        fs, sample, cores, _ = oracle_frame_estimate(sc, cam, up, budget, seed=100 + k)
+        frames.append(fs)
+    wall = time.perf_counter() - t0
+    ms = 1e3 * float(np.mean(frames))
+    value = 1e3 / ms
+    out = {"metric": METRIC, "value": round(value, 9), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(args.n),
+           "impl": "reference",
+           "cpu_baseline": {"value": round(value, 9), "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(value, 9), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "gpu_launches": 0, "wall_s": round(wall, 1)}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -222,6 +222,14 @@ sr_status sr_render_bwd(const sr_plan* plan, const sr_gaussians* g, const sr_cam
                         void* ws, const float* d_images, const float* t_final, const uint32_t* n_contrib,
                         const sr_grads* out, void* stream);
 
+/* Diagnostics: number of kernels this library has launched in this process
+ * (all devices and streams), and the last frame's work counters (pairs of
+ * pixel and Gaussian tested and blended by sr_render_fwd), read from the
+ * workspace with a stream synchronisation.  Either output may be NULL. */
+uint64_t sr_kernel_launches(void);
+sr_status sr_frame_counters(const sr_plan* plan, void* ws, uint64_t* pairs_tested, uint64_t* pairs_blended,
+                            void* stream);
+
 /* Synchronise the stream and read the device status word.  Returns SR_OK,
  * SR_ERR_CAPACITY or SR_ERR_TIMEOUT (first set bit), clears the word, and
  * stores the last frame's key count in *keys_needed if non-NULL. */

@@ -1,11 +1,18 @@
 // C ABI of the skew-Gaussian rasterizer: argument checks, the workspace
 // plan, and the kernel launches of each stage (declared in skewraster.h).
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
 #include "kernels.cuh"
 
 using namespace sr;
+
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+}  // namespace
+
+void sr::count_launches(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
 
 namespace {
 
@@ -318,6 +325,22 @@ sr_status sr_render_bwd(const sr_plan* p, const sr_gaussians* g, const sr_camera
   b.ws = w;
   b.out = *out;
   return from_cuda(launch_preprocess_bwd(b, st, device_sms()));
+}
+
+uint64_t sr_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+sr_status sr_frame_counters(const sr_plan* p, void* ws, uint64_t* pairs_tested, uint64_t* pairs_blended,
+                            void* stream) {
+  sr_status s = check_plan(p, ws);
+  if (s != SR_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Status h;
+  if (cudaMemcpyAsync(&h, ws_ptrs(*p, ws).status, sizeof(Status), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return SR_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SR_ERR_CUDA;
+  if (pairs_tested) *pairs_tested = h.pairs_tested;
+  if (pairs_blended) *pairs_blended = h.pairs_blended;
+  return SR_OK;
 }
 
 sr_status sr_read_status(const sr_plan* p, void* ws, int64_t* keys_needed, void* stream) {

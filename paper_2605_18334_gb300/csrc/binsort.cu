@@ -377,17 +377,21 @@ cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms) {
   unsigned long long* part = reinterpret_cast<unsigned long long*>(a.ws.scan_part);
   if (m > 0) {
     scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(a.ws.ntouch, m, part);
+    count_launches(1);
   }
   scan_parts_kernel<<<1, 1024, 0, st>>>(part, nb, a.ws.status, a.cap);
+  count_launches(1);
   if (m > 0) {
     scan_down_kernel<<<nb, kScanThreads, 0, st>>>(a.ws.ntouch, m, part, a.ws.offsets);
     duplicate_kernel<<<clamp_grid((m + 255) / 256, sms, 8), 256, 0, st>>>(
         a.n, a.n_views, a.ws.views, a.ws.ntouch, a.ws.offsets, a.ws.rect, a.ws.depth, a.ws.keys[0], a.ws.vals[0],
         a.cap);
+    count_launches(2);
   }
   histogram_kernel<<<clamp_grid((a.cap + 255) / 256, sms, 4), 256, 0, st>>>(a.ws.keys[0], a.ws.status, a.cap,
                                                                            a.passes, a.ws.hist);
   hist_scan_kernel<<<a.passes, 256, 0, st>>>(a.ws.hist, a.ws.status, a.cap);
+  count_launches(2);
   return cudaGetLastError();
 }
 
@@ -418,6 +422,7 @@ cudaError_t launch_bin_phase2(const BinArgs& a, const int* run, long long keys_k
     pa.shift = 8 * p;
     pa.spin_limit = a.spin_limit;
     onesweep_kernel<<<(unsigned)parts, kSortThreads, 0, st>>>(pa);
+    count_launches(1);
     cur ^= 1;
   }
   if (kn > 0) {
@@ -427,6 +432,7 @@ cudaError_t launch_bin_phase2(const BinArgs& a, const int* run, long long keys_k
     // nothing to sort: record which buffer (0) holds the (empty) result
     ranges_kernel<<<1, 32, 0, st>>>(a.ws.keys[cur], a.ws.status, a.cap, a.ws.ranges, cur);
   }
+  count_launches(1);
   e = cudaGetLastError();
   return e;
 }

@@ -53,7 +53,13 @@ struct Status {
   uint32_t part_counter[kMaxPasses];  // onesweep partition tickets per pass
   uint32_t pass_trivial[kMaxPasses];  // 1 if one digit holds every key of that pass
   uint32_t timeout_where;             // pass * 1e6 + partition of the first timed-out wait
+  uint32_t pad1;
+  unsigned long long pairs_tested;    // render_fwd: (pixel, Gaussian) pairs evaluated
+  unsigned long long pairs_blended;   // render_fwd: pairs composited
 };
+
+// host-side launch counter (diagnostics; defined in api.cu)
+void count_launches(int k);
 
 struct ViewInfo {
   int32_t width, height, tiles_x, tiles_y;

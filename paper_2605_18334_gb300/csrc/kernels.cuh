@@ -39,7 +39,7 @@ struct RenderArgs {     // forward and backward composite
   const uint32_t* vals1;
   const uint2* ranges;
   const ViewInfo* views;
-  const Status* status;
+  Status* status;
   int n_views;
   CfgDev cfg;
   float* images;

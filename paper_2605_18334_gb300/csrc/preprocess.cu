@@ -597,6 +597,7 @@ static cudaError_t launch_sized(void (*fn)(Args), const Args& a, int grid, size_
     if (e != cudaSuccess) return e;
   }
   fn<<<grid, 256, smem, st>>>(a);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -608,6 +609,7 @@ static int grid_for(int64_t n, int sms) {
 
 cudaError_t launch_preprocess_fwd(const PreArgs& a, cudaStream_t st, int sms) {
   view_table_kernel<<<1, 32, 0, st>>>(a.cams, a.n_views, a.ws.views);
+  count_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || a.g.n == 0) return e;
   const int grid = grid_for(a.g.n, sms);

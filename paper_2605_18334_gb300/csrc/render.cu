@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) render_fwd_kernel(RenderArgs a) {
   const float amin = a.cfg.alpha_min, amax = a.cfg.alpha_max, tstop = a.cfg.t_stop;
 
   float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-  uint32_t last = 0;
+  uint32_t last = 0, tested = 0, blended = 0;
   bool done = !inside;
   for (uint32_t start = range.x; start < range.y; start += 256) {
     if (__syncthreads_count(done) == 256) break;
@@ -51,7 +51,8 @@ __global__ void __launch_bounds__(256) render_fwd_kernel(RenderArgs a) {
     __syncthreads();
     const int cnt = (int)min(256u, range.y - start);
     if (!done) {
-      for (int j = 0; j < cnt; ++j) {
+      int j = 0;
+      for (; j < cnt; ++j) {
         const float4 r3 = s_r3[j];
         PairEval e;
         if (!eval_pair<MODE>(s_r0[j], s_r1[j], MODE == MODE_PLAIN ? s_r0[j] : s_r2[j], r3.w, fx, fy, e)) continue;
@@ -60,8 +61,10 @@ __global__ void __launch_bounds__(256) render_fwd_kernel(RenderArgs a) {
         const float Tn = __fmaf_rn(-T, alpha, T);
         if (Tn < tstop) {
           done = true;
+          ++j;
           break;
         }
+        ++blended;
         const float w = __fmul_rn(alpha, T);
         C0 = __fmaf_rn(r3.x, w, C0);
         C1 = __fmaf_rn(r3.y, w, C1);
@@ -69,7 +72,19 @@ __global__ void __launch_bounds__(256) render_fwd_kernel(RenderArgs a) {
         T = Tn;
         last = start + j + 1 - range.x;
       }
+      tested += j;
     }
+  }
+  // work counters: one atomic per warp
+  unsigned long long t64 = tested, b64 = blended;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    t64 += __shfl_xor_sync(0xffffffffu, t64, o);
+    b64 += __shfl_xor_sync(0xffffffffu, b64, o);
+  }
+  if ((threadIdx.x & 31) == 0 && t64) {
+    atomicAdd(&a.status->pairs_tested, t64);
+    atomicAdd(&a.status->pairs_blended, b64);
   }
   if (inside) {
     const int64_t plane = (int64_t)vi.width * vi.height;
@@ -224,6 +239,7 @@ cudaError_t launch_render_fwd(const RenderArgs& a, int mode, int64_t total_tiles
   if (mode == MODE_PLAIN) render_fwd_kernel<MODE_PLAIN><<<grid, 256, 0, st>>>(a);
   else if (mode == MODE_TWO) render_fwd_kernel<MODE_TWO><<<grid, 256, 0, st>>>(a);
   else render_fwd_kernel<MODE_SPLIT><<<grid, 256, 0, st>>>(a);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -233,6 +249,7 @@ cudaError_t launch_render_bwd(const RenderArgs& a, int mode, int64_t total_tiles
   if (mode == MODE_PLAIN) render_bwd_kernel<MODE_PLAIN><<<grid, 256, 0, st>>>(a);
   else if (mode == MODE_TWO) render_bwd_kernel<MODE_TWO><<<grid, 256, 0, st>>>(a);
   else render_bwd_kernel<MODE_SPLIT><<<grid, 256, 0, st>>>(a);
+  count_launches(1);
   return cudaGetLastError();
 }
 

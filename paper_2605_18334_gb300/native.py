@@ -20,7 +20,8 @@ SR_OK, SR_ERR_INVALID, SR_ERR_CAPACITY, SR_ERR_CUDA, SR_ERR_TIMEOUT, SR_ERR_UNSU
 SR_F32, SR_BF16, SR_F16 = 0, 1, 2
 
 EXPORTS = ["sr_abi_version", "sr_status_string", "sr_config_default", "sr_camera_from_gl", "sr_plan_init",
-           "sr_workspace_size", "sr_preprocess", "sr_bin_sort", "sr_render_fwd", "sr_render_bwd", "sr_read_status"]
+           "sr_workspace_size", "sr_preprocess", "sr_bin_sort", "sr_render_fwd", "sr_render_bwd", "sr_read_status",
+           "sr_kernel_launches", "sr_frame_counters"]
 
 
 class sr_gaussians(C.Structure):
@@ -105,6 +106,10 @@ def load(build_if_missing: bool = True):
         lib.sr_render_bwd.argtypes = [P(sr_plan), P(sr_gaussians), C.c_void_p, P(sr_config), C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p, P(sr_grads), C.c_void_p]
         lib.sr_read_status.argtypes = [P(sr_plan), C.c_void_p, P(C.c_int64), C.c_void_p]
+        lib.sr_kernel_launches.restype = C.c_uint64
+        lib.sr_kernel_launches.argtypes = []
+        lib.sr_frame_counters.argtypes = [P(sr_plan), C.c_void_p, P(C.c_uint64), P(C.c_uint64), C.c_void_p]
+        lib.sr_frame_counters.restype = C.c_int
         for name in ("sr_config_default", "sr_camera_from_gl", "sr_plan_init", "sr_preprocess", "sr_bin_sort",
                      "sr_render_fwd", "sr_render_bwd", "sr_read_status"):
             getattr(lib, name).restype = C.c_int
@@ -182,6 +187,17 @@ def sr_render_bwd(plan, g, cams_dev_ptr: int, cfg, ws_ptr: int, d_images_ptr: in
                                                 C.c_void_p(ws_ptr), C.c_void_p(d_images_ptr),
                                                 C.c_void_p(t_final_ptr), C.c_void_p(n_contrib_ptr),
                                                 C.byref(grads), C.c_void_p(stream)))
+
+
+def sr_kernel_launches() -> int:
+    return int(load().sr_kernel_launches())
+
+
+def sr_frame_counters(plan, ws_ptr: int, stream: int):
+    t, b = C.c_uint64(0), C.c_uint64(0)
+    check("sr_frame_counters", load().sr_frame_counters(C.byref(plan), C.c_void_p(ws_ptr), C.byref(t), C.byref(b),
+                                                        C.c_void_p(stream)))
+    return int(t.value), int(b.value)
 
 
 def sr_read_status(plan, ws_ptr: int, stream: int):
