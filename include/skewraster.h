@@ -222,6 +222,31 @@ sr_status sr_render_bwd(const sr_plan* plan, const sr_gaussians* g, const sr_cam
                         void* ws, const float* d_images, const float* t_final, const uint32_t* n_contrib,
                         const sr_grads* out, void* stream);
 
+/* Stable radix sort of (key, value) pairs that allocates nothing: the same
+ * onesweep passes as sr_bin_sort, for callers that cannot allocate device
+ * memory at all (a runtime that hands out only fixed, pre-assigned buffers,
+ * a plugin that receives just its input and output pointers, or a frame
+ * loop that must never call cudaMalloc).  The paper has no counterpart.
+ *
+ * keys_in/vals_in: n input pairs (device, read only); keys_out/vals_out: n
+ * output pairs (device, must not alias the inputs), sorted by the key's low
+ * ceil(sort_bits / 8) bytes, ties in input order; key bits above sort_bits
+ * are expected to be zero.  n at most SR_NOALLOC_MAX_KEYS (2^20), else
+ * SR_ERR_CAPACITY; sort_bits in 1..64 and non-NULL distinct pointers, else
+ * SR_ERR_INVALID.
+ *
+ * Scratch: one fixed array of about 16.2 MiB in the library's device memory,
+ * present on every GPU that loads the library until the process exits.  The
+ * first call on a device looks up that array's device address (with the
+ * device current), so make the first call before any CUDA-graph stream
+ * capture.  Every call reuses the same array and the work it enqueues
+ * clears what must start at zero; calls whose work overlaps on the GPU
+ * (different streams, or several host threads) race on it and must be
+ * serialised by the caller. */
+#define SR_NOALLOC_MAX_KEYS (1u << 20)
+sr_status sr_sort_keys_noalloc(const uint64_t* keys_in, const uint32_t* vals_in, int64_t n, int32_t sort_bits,
+                               uint64_t* keys_out, uint32_t* vals_out, void* stream);
+
 /* Diagnostics: number of kernels this library has launched in this process
  * (all devices and streams), and the last frame's work counters (pairs of
  * pixel and Gaussian tested and blended by sr_render_fwd), read from the

@@ -12,6 +12,7 @@
 //              then scatters through shared memory so writes are runs
 //   ranges     [start, end) of each tile in the sorted key list
 #include <algorithm>
+#include <mutex>
 
 #include "kernels.cuh"
 
@@ -438,3 +439,136 @@ cudaError_t launch_bin_phase2(const BinArgs& a, const int* run, long long keys_k
 }
 
 }  // namespace sr
+
+// ---------------------------------------------------------------------------
+// Sort without caller-provided scratch (sr_sort_keys_noalloc)
+//
+// For callers that cannot allocate device memory at all (a host-side runtime
+// that owns a fixed memory pool, a plugin that only receives its input and
+// output buffers, code running where a cudaMalloc would break a frame-time
+// budget or an allocation-free guarantee).  All scratch of the radix sort
+// (one ping-pong key/value buffer, the digit histograms, the look-back state
+// and the status word) lives in one file-scope device array of fixed size,
+// so the call allocates nothing; every GPU that loads this library holds the
+// array (about 16.2 MiB) until the process exits.
+// ---------------------------------------------------------------------------
+namespace sr {
+
+constexpr unsigned long long kNoallocKeys = 1ull << 20;  // == SR_NOALLOC_MAX_KEYS
+constexpr unsigned long long kNoallocParts = kNoallocKeys / kSortPart;
+constexpr size_t kNoallocStatusBytes = 256;
+constexpr size_t kNoallocHistBytes = sizeof(uint32_t) * kMaxPasses * 256;
+constexpr size_t kNoallocLookbackBytes = sizeof(unsigned long long) * 256 * kMaxPasses * kNoallocParts;
+constexpr size_t kNoallocKeyBytes = sizeof(unsigned long long) * kNoallocKeys;
+constexpr size_t kNoallocValBytes = sizeof(uint32_t) * kNoallocKeys;
+constexpr size_t kNoallocBytes =
+    kNoallocStatusBytes + kNoallocHistBytes + kNoallocLookbackBytes + kNoallocKeyBytes + kNoallocValBytes;
+
+// Host code must not use this name as a device address; it receives the
+// address from cudaGetSymbolAddress (see noalloc_scratch_address below).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+// Clears what the sort expects at zero and records the key count.
+__global__ void noalloc_reset_kernel(unsigned char* scratch, unsigned long long n, int passes) {
+  Status* st = reinterpret_cast<Status*>(scratch);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(scratch + kNoallocStatusBytes);
+  unsigned long long* lb =
+      reinterpret_cast<unsigned long long*>(scratch + kNoallocStatusBytes + kNoallocHistBytes);
+  const unsigned long long parts = (n + kSortPart - 1) / kSortPart;
+  const unsigned long long lb_words = parts * (unsigned long long)passes * 256ull;
+  const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = tid; i < lb_words; i += stride) lb[i] = 0ull;
+  for (unsigned long long i = tid; i < (unsigned long long)kMaxPasses * 256; i += stride) hist[i] = 0u;
+  if (tid == 0) {
+    st->flags = 0u;
+    st->sorted_buf = 0u;
+    st->keys_needed = n;
+    for (int p = 0; p < kMaxPasses; ++p) {
+      st->part_counter[p] = 0u;
+      st->pass_trivial[p] = 0u;
+    }
+    st->timeout_where = 0u;
+  }
+}
+
+// Device address of the scratch array for the current device, looked up once
+// per device (the first call on a device does it).
+static unsigned char* noalloc_scratch_address(cudaError_t* err) {
+  static std::mutex mu;
+  static unsigned char* addr[64] = {nullptr};
+  int dev = 0;
+  *err = cudaGetDevice(&dev);
+  if (*err != cudaSuccess) return nullptr;
+  if (dev < 0 || dev >= 64) {
+    *err = cudaErrorInvalidDevice;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    *err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (*err != cudaSuccess) return nullptr;
+    addr[dev] = static_cast<unsigned char*>(p);
+  }
+  return addr[dev];
+}
+
+}  // namespace sr
+
+extern "C" sr_status sr_sort_keys_noalloc(const uint64_t* keys_in, const uint32_t* vals_in, int64_t n,
+                                          int32_t sort_bits, uint64_t* keys_out, uint32_t* vals_out,
+                                          void* stream) {
+  using namespace sr;
+  if (n < 0 || sort_bits < 1 || sort_bits > 64) return SR_ERR_INVALID;
+  if ((unsigned long long)n > kNoallocKeys) return SR_ERR_CAPACITY;
+  if (n == 0) return SR_OK;
+  if (!keys_in || !vals_in || !keys_out || !vals_out) return SR_ERR_INVALID;
+  if (keys_in == keys_out || vals_in == vals_out) return SR_ERR_INVALID;
+  cudaError_t e;
+  unsigned char* base = noalloc_scratch_address(&e);
+  if (!base) return SR_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int passes = (sort_bits + 7) / 8;
+  const unsigned long long un = (unsigned long long)n;
+  Status* status = reinterpret_cast<Status*>(base);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(base + kNoallocStatusBytes);
+  unsigned long long* lookback = reinterpret_cast<unsigned long long*>(base + kNoallocStatusBytes + kNoallocHistBytes);
+  unsigned long long* tmp_keys =
+      reinterpret_cast<unsigned long long*>(base + kNoallocStatusBytes + kNoallocHistBytes + kNoallocLookbackBytes);
+  uint32_t* tmp_vals = reinterpret_cast<uint32_t*>(base + kNoallocStatusBytes + kNoallocHistBytes +
+                                                   kNoallocLookbackBytes + kNoallocKeyBytes);
+  noalloc_reset_kernel<<<clamp_grid((un * passes + 255) / 256, sms, 4), 256, 0, st>>>(base, un, passes);
+  histogram_kernel<<<clamp_grid((un + 255) / 256, sms, 4), 256, 0, st>>>(
+      reinterpret_cast<const unsigned long long*>(keys_in), status, un, passes, hist);
+  hist_scan_kernel<<<passes, 256, 0, st>>>(hist, status, un);
+  // ping-pong between the scratch buffer and the output so the last pass
+  // writes the output: an odd pass count starts into the output
+  const unsigned long long* kin = reinterpret_cast<const unsigned long long*>(keys_in);
+  const uint32_t* vin = vals_in;
+  bool into_out = (passes & 1) != 0;
+  const unsigned long long parts = (un + kSortPart - 1) / kSortPart;
+  for (int p = 0; p < passes; ++p) {
+    PassArgs pa;
+    pa.keys_in = kin;
+    pa.vals_in = vin;
+    pa.keys_out = into_out ? reinterpret_cast<unsigned long long*>(keys_out) : tmp_keys;
+    pa.vals_out = into_out ? vals_out : tmp_vals;
+    pa.digit_base = hist + p * 256;
+    pa.lookback = lookback;
+    pa.passes = passes;
+    pa.st = status;
+    pa.cap = un;
+    pa.pass = p;
+    pa.shift = 8 * p;
+    pa.spin_limit = 1 << 20;
+    onesweep_kernel<<<(unsigned)parts, kSortThreads, 0, st>>>(pa);
+    kin = pa.keys_out;
+    vin = pa.vals_out;
+    into_out = !into_out;
+  }
+  count_launches(3 + passes);
+  return cudaGetLastError() == cudaSuccess ? SR_OK : SR_ERR_CUDA;
+}

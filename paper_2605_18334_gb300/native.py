@@ -21,7 +21,7 @@ SR_F32, SR_BF16, SR_F16 = 0, 1, 2
 
 EXPORTS = ["sr_abi_version", "sr_status_string", "sr_config_default", "sr_camera_from_gl", "sr_plan_init",
            "sr_workspace_size", "sr_preprocess", "sr_bin_sort", "sr_render_fwd", "sr_render_bwd", "sr_read_status",
-           "sr_kernel_launches", "sr_frame_counters"]
+           "sr_kernel_launches", "sr_frame_counters", "sr_sort_keys_noalloc"]
 
 
 class sr_gaussians(C.Structure):
