@@ -137,8 +137,8 @@ typedef struct sr_plan {
   int64_t n;
   int32_t sh_degree;
   int32_t tile_w, tile_h;
-  int32_t sort_passes;        /* radix passes of 8 bits over the (tile|depth) key */
-  int32_t sort_bits;          /* 32 depth bits + tile-id bits */
+  int32_t sort_passes;        /* 8-bit radix passes over the tile ids (after a 4-pass depth sort of the records) */
+  int32_t sort_bits;          /* width of the (tile | depth) order: 32 depth bits + tile-id bits */
   int32_t render_mode;        /* 0: one opacity; 1: two opacities; 2: two opacities + split direction */
   int32_t two_opacities;      /* copied from the sr_gaussians the plan was made for */
   int32_t has_split;          /* 1 if split_dir was non-NULL */

@@ -173,22 +173,26 @@ sr_status sr_plan_init(sr_plan* p, const sr_config* cfg, const sr_gaussians* g, 
   int tile_bits = 0;
   while (((int64_t)1 << tile_bits) < tb) ++tile_bits;
   p->sort_bits = 32 + tile_bits;
-  p->sort_passes = (p->sort_bits + 7) / 8;
+  p->sort_passes = (tile_bits + 7) / 8;  // the depth bits are sorted once per record, not per key
 
   const int64_t scan_blocks = (m + kScanBlock - 1) / kScanBlock;
   const int64_t parts = (key_capacity + kSortPart - 1) / kSortPart;
+  const int64_t dparts = (m + kSortPart - 1) / kSortPart;
   size_t sizes[WS_NUM_SLOTS];
   sizes[WS_STATUS] = sizeof(Status);
   sizes[WS_VIEWS] = sizeof(ViewInfo) * SR_MAX_VIEWS;
   sizes[WS_REC] = sizeof(float4) * 4 * (size_t)m;
   sizes[WS_DEPTH] = sizeof(uint32_t) * (size_t)m;
+  sizes[WS_DKEY0] = sizes[WS_DKEY1] = sizeof(uint32_t) * (size_t)m;
+  sizes[WS_PERM0] = sizes[WS_PERM1] = sizeof(uint32_t) * (size_t)m;
   sizes[WS_RECT] = sizeof(uint2) * (size_t)m;
   sizes[WS_NTOUCH] = sizeof(uint32_t) * (size_t)m;
   sizes[WS_OFFSETS] = sizeof(uint32_t) * (size_t)m;
   sizes[WS_SCAN_PART] = sizeof(unsigned long long) * (size_t)(scan_blocks + 1);
-  sizes[WS_KEYS0] = sizes[WS_KEYS1] = sizeof(unsigned long long) * (size_t)key_capacity;
+  sizes[WS_KEYS0] = sizes[WS_KEYS1] = sizeof(uint32_t) * (size_t)key_capacity;
   sizes[WS_VALS0] = sizes[WS_VALS1] = sizeof(uint32_t) * (size_t)key_capacity;
-  sizes[WS_HIST] = sizeof(uint32_t) * kMaxPasses * 256;
+  sizes[WS_HIST] = sizeof(uint32_t) * 2 * kMaxPasses * 256;
+  sizes[WS_LOOKBACK_D] = sizeof(unsigned long long) * 256 * kDepthPasses * (size_t)dparts;
   sizes[WS_LOOKBACK] = sizeof(unsigned long long) * 256 * (size_t)p->sort_passes * (size_t)parts;
   sizes[WS_RANGES] = sizeof(uint2) * (size_t)tb;
   sizes[WS_D2] = sizeof(float) * kD2Stride * (size_t)m;
@@ -258,7 +262,7 @@ sr_status sr_bin_sort(const sr_plan* p, const sr_config* cfg, void* ws, int64_t*
     *keys_needed = (int64_t)h.keys_needed;
     if (h.keys_needed > (unsigned long long)p->key_capacity) return SR_ERR_CAPACITY;
     known = (long long)h.keys_needed;
-    for (int k = 0; k < p->sort_passes; ++k) run[k] = h.pass_trivial[k] ? 0 : 1;
+    for (int k = 0; k < p->sort_passes; ++k) run[k] = h.pass_trivial[kMaxPasses + k] ? 0 : 1;
   }
   return from_cuda(launch_bin_phase2(b, run, known, st));
 }

@@ -1,16 +1,22 @@
 // Tile binning and depth sort (the tile-based, depth-sorted pipeline of the
-// Preliminaries).
+// Preliminaries).  The result is the order of the key (global tile << 32 |
+// FP32 depth bits) with ties broken by record index, obtained in two sorts:
 //
-//   scan       exclusive scan of the per-(view, Gaussian) tile counts
-//   duplicate  one key (global tile << 32 | FP32 depth bits) per touched
-//              tile, value = record index, emitted in record-index order
-//   histogram  digit counts of every 8-bit digit of every key, one read
-//   onesweep   one stable LSD radix pass per digit: each block ranks a
-//              partition of 4096 keys with warp match-any, publishes its
-//              digit counts and resolves its global offsets by a decoupled
-//              look-back over the preceding partitions (every wait bounded),
-//              then scatters through shared memory so writes are runs
-//   ranges     [start, end) of each tile in the sorted key list
+//   depth sort   the M records by their 32-bit depth key (records that touch
+//                no tile carry ~0 and sink to the end): 4 stable 8-bit passes
+//                over M, not over the (much larger) number of tile keys
+//   scan         exclusive scan of the tile counts in depth order
+//   duplicate    one 32-bit global tile id per touched tile, value = record
+//                index, emitted in depth order (warp-cooperative, coalesced)
+//   tile sort    stable LSD passes over the tile-id bits only; stability
+//                keeps the depth order (and index order of equal depths)
+//                inside every tile
+//   ranges       [start, end) of each tile in the sorted list
+//
+// Every radix pass is one onesweep launch: a block ranks a partition of 4096
+// keys with warp match-any, publishes its digit counts, resolves its global
+// offsets by a decoupled look-back over the preceding partitions (each wait
+// bounded), and scatters through shared memory so writes go out in runs.
 #include <algorithm>
 #include <mutex>
 
@@ -33,9 +39,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
-// ---------------------------------------------------------------------------
-// block-wide exclusive scan helpers
-// ---------------------------------------------------------------------------
+// block-wide exclusive scan (NT threads), total in `total`
 template <int NT>
 __device__ __forceinline__ unsigned long long block_exclusive_u64(unsigned long long x, unsigned long long* s_warp,
                                                                   unsigned long long& total) {
@@ -64,17 +68,25 @@ __device__ __forceinline__ unsigned long long block_exclusive_u64(unsigned long 
   return before + inc - x;
 }
 
+__device__ __forceinline__ unsigned long long element_count(const unsigned long long* count_dev,
+                                                            unsigned long long count) {
+  if (!count_dev) return count;
+  const unsigned long long c = *count_dev;
+  return c < count ? c : count;
+}
+
 // ---------------------------------------------------------------------------
-// scan of the tile counts
+// scan of the tile counts (in the order given by perm)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ cnt, int64_t m,
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ cnt,
+                                                                   const uint32_t* __restrict__ perm, int64_t m,
                                                                    unsigned long long* __restrict__ part) {
   __shared__ unsigned long long s_warp[kScanThreads / 32];
   const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
   unsigned long long sum = 0;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k)
-    if (base + k < m) sum += cnt[base + k];
+    if (base + k < m) sum += cnt[perm[base + k]];
   unsigned long long total;
   block_exclusive_u64<kScanThreads>(sum, s_warp, total);
   if (threadIdx.x == 0) part[blockIdx.x] = total;
@@ -99,7 +111,8 @@ __global__ void __launch_bounds__(1024) scan_parts_kernel(unsigned long long* pa
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint32_t* __restrict__ cnt, int64_t m,
+__global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint32_t* __restrict__ cnt,
+                                                                 const uint32_t* __restrict__ perm, int64_t m,
                                                                  const unsigned long long* __restrict__ part,
                                                                  uint32_t* __restrict__ offsets) {
   __shared__ unsigned long long s_warp[kScanThreads / 32];
@@ -108,7 +121,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint32_t*
   unsigned long long sum = 0;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
-    v[k] = base + k < m ? cnt[base + k] : 0u;
+    v[k] = base + k < m ? cnt[perm[base + k]] : 0u;
     sum += v[k];
   }
   unsigned long long total;
@@ -121,48 +134,90 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint32_t*
 }
 
 // ---------------------------------------------------------------------------
-// key duplication
+// key duplication, in depth order.  A warp takes 32 consecutive depth-sorted
+// records and writes their keys as one contiguous run: each lane finds the
+// record that owns its output slot by a binary search over the lanes' starts
+// (lanes with no tiles have zero-length ranges and are never selected as the
+// last lane whose start is <= the slot).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) duplicate_kernel(int64_t n, int n_views, const ViewInfo* __restrict__ views,
+                                                        const uint32_t* __restrict__ perm,
                                                         const uint32_t* __restrict__ ntouch,
                                                         const uint32_t* __restrict__ offsets,
                                                         const uint2* __restrict__ rect,
-                                                        const uint32_t* __restrict__ depth,
-                                                        unsigned long long* __restrict__ keys,
-                                                        uint32_t* __restrict__ vals, unsigned long long cap) {
+                                                        uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                        unsigned long long cap) {
   const int64_t m_total = n * n_views;
-  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < m_total;
-       m += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t cnt = ntouch[m];
-    if (cnt == 0) continue;
-    const int v = (int)(m / n);
-    const ViewInfo vi = views[v];
-    const uint2 r = rect[m];
-    const uint32_t tx0 = r.x & 0xffffu, ty0 = r.x >> 16, tx1 = r.y & 0xffffu, ty1 = r.y >> 16;
-    const unsigned long long d = depth[m];
-    unsigned long long pos = offsets[m];
-    for (uint32_t ty = ty0; ty < ty1; ++ty)
-      for (uint32_t tx = tx0; tx < tx1; ++tx) {
-        if (pos < cap) {
-          const unsigned long long tile = (unsigned long long)(vi.tile_base + (int64_t)ty * vi.tiles_x + tx);
-          keys[pos] = (tile << 32) | d;
-          vals[pos] = (uint32_t)m;
-        }
-        ++pos;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w * 32 < m_total; w += warps) {
+    const int64_t j = w * 32 + lane;
+    uint32_t m = 0, cnt = 0, start = 0xffffffffu, tx0 = 0, ty0 = 0, tw = 1;
+    int64_t tbase = 0;
+    int tiles_x = 1;
+    if (j < m_total) {
+      m = perm[j];
+      cnt = ntouch[m];
+      start = offsets[j];
+      if (cnt) {
+        const uint2 r = rect[m];
+        tx0 = r.x & 0xffffu;
+        ty0 = r.x >> 16;
+        tw = (r.y & 0xffffu) - tx0;
+        const ViewInfo& vi = views[(int)(m / (uint64_t)n)];
+        tbase = vi.tile_base;
+        tiles_x = vi.tiles_x;
       }
+    }
+    // the run of this warp: [start of lane 0, end of the last valid lane)
+    const uint32_t base = __shfl_sync(0xffffffffu, start, 0);
+    const uint32_t end = __reduce_max_sync(0xffffffffu, cnt ? start + cnt : 0u);
+    // start relative to the run (non-decreasing over lanes; lanes past the
+    // last record get a huge value and are never selected)
+    const uint32_t rel = start - base;
+    // warp-uniform loop: every lane takes part in the shuffles, only lanes
+    // with p < end write
+    for (uint32_t p0 = base; p0 < end; p0 += 32) {
+      const uint32_t p = p0 + lane;
+      const uint32_t q_rel = p - base;
+      // owner: the last lane whose start <= q_rel.  Lanes without tiles share
+      // their start with the next lane, so the last lane of such a group is
+      // the one whose range covers q_rel.
+      int lo = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t s_rel = __shfl_sync(0xffffffffu, rel, lo + step);
+        if (s_rel <= q_rel) lo += step;
+      }
+      const uint32_t o_rel = __shfl_sync(0xffffffffu, rel, lo);
+      const uint32_t o_m = __shfl_sync(0xffffffffu, m, lo);
+      const uint32_t o_tx0 = __shfl_sync(0xffffffffu, tx0, lo);
+      const uint32_t o_ty0 = __shfl_sync(0xffffffffu, ty0, lo);
+      const uint32_t o_tw = __shfl_sync(0xffffffffu, tw, lo);
+      const long long o_tb = __shfl_sync(0xffffffffu, (long long)tbase, lo);
+      const int o_tx = __shfl_sync(0xffffffffu, tiles_x, lo);
+      const uint32_t q = q_rel - o_rel;
+      const uint32_t dy = q / o_tw, dx = q - dy * o_tw;
+      if (p < end && p < cap) {
+        keys[p] = (uint32_t)(o_tb + (long long)(o_ty0 + dy) * o_tx + (o_tx0 + dx));
+        vals[p] = o_m;
+      }
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
-// digit histograms of all passes
+// digit histograms of `passes` 8-bit digits
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) histogram_kernel(const unsigned long long* __restrict__ keys,
-                                                        const Status* __restrict__ st, unsigned long long cap,
-                                                        int passes, uint32_t* __restrict__ hist) {
+template <class KEY>
+__global__ void __launch_bounds__(256) histogram_kernel(const KEY* __restrict__ keys,
+                                                        const unsigned long long* count_dev,
+                                                        unsigned long long count, int passes,
+                                                        uint32_t* __restrict__ hist) {
   __shared__ uint32_t s_h[kMaxPasses][256];
   for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&s_h[0][0])[i] = 0u;
   __syncthreads();
-  const unsigned long long kn = st->keys_needed < cap ? st->keys_needed : cap;
+  const unsigned long long kn = element_count(count_dev, count);
   for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < kn;
        k += (unsigned long long)gridDim.x * blockDim.x) {
     const unsigned long long key = keys[k];
@@ -176,17 +231,18 @@ __global__ void __launch_bounds__(256) histogram_kernel(const unsigned long long
 }
 
 // per pass: exclusive digit offsets in place, and whether one digit holds every key
-__global__ void __launch_bounds__(256) hist_scan_kernel(uint32_t* __restrict__ hist, Status* st,
-                                                        unsigned long long cap) {
+__global__ void __launch_bounds__(256) hist_scan_kernel(uint32_t* __restrict__ hist, uint32_t* trivial,
+                                                        const unsigned long long* count_dev,
+                                                        unsigned long long count) {
   __shared__ unsigned long long s_warp[8];
   const int p = blockIdx.x;
-  const unsigned long long kn = st->keys_needed < cap ? st->keys_needed : cap;
+  const unsigned long long kn = element_count(count_dev, count);
   const uint32_t c = hist[p * 256 + threadIdx.x];
   unsigned long long total;
   const unsigned long long ex = block_exclusive_u64<256>(c, s_warp, total);
   hist[p * 256 + threadIdx.x] = (uint32_t)ex;
   const int full = __syncthreads_or(kn > 0 && c == kn);
-  if (threadIdx.x == 0) st->pass_trivial[p] = full ? 1u : 0u;
+  if (threadIdx.x == 0) trivial[p] = full ? 1u : 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -196,24 +252,28 @@ constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagInc = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
 
+template <class KEY>
 struct PassArgs {
-  const unsigned long long* keys_in;
-  const uint32_t* vals_in;
-  unsigned long long* keys_out;
+  const KEY* keys_in;
+  const uint32_t* vals_in;        // nullptr: the value is the element's input index
+  KEY* keys_out;
   uint32_t* vals_out;
   const uint32_t* digit_base;     // exclusive digit offsets of this pass
   unsigned long long* lookback;   // [parts][passes][256], zeroed per frame
+  uint32_t* part_counter;         // partition tickets of this pass (zeroed)
+  const unsigned long long* count_dev;  // element count on the device, or nullptr
+  unsigned long long count;       // element count (count_dev == nullptr) or the capacity bound
+  Status* st;                     // status flags (timeouts)
   int passes;
-  Status* st;
-  unsigned long long cap;
   int pass;
   int shift;
   int spin_limit;
 };
 
-__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(PassArgs a) {
+template <class KEY>
+__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(PassArgs<KEY> a) {
   constexpr int NW = kSortThreads / 32;
-  __shared__ unsigned long long s_buf[kSortPart];  // keys, then values (as u32) in the scatter phase
+  __shared__ KEY s_buf[kSortPart];  // keys, then values (as u32) in the scatter phase
   __shared__ uint32_t s_whist[NW][256];
   __shared__ uint32_t s_lstart[256];
   __shared__ unsigned long long s_gbase[256];
@@ -222,9 +282,9 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(PassArgs a) {
   __shared__ uint32_t s_part;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const unsigned long long kn = a.st->keys_needed < a.cap ? a.st->keys_needed : a.cap;
+  const unsigned long long kn = element_count(a.count_dev, a.count);
   const unsigned long long nparts = (kn + kSortPart - 1) / kSortPart;
-  if (tid == 0) s_part = atomicAdd(&a.st->part_counter[a.pass], 1u);
+  if (tid == 0) s_part = atomicAdd(a.part_counter, 1u);
   for (int i = tid; i < NW * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0u;
   __syncthreads();
   const unsigned long long part = s_part;
@@ -232,14 +292,14 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(PassArgs a) {
   const unsigned long long base = part * kSortPart;
 
   // load, warp-blocked: warp w owns keys [w*512, (w+1)*512) of the partition
-  unsigned long long key[kSortItems];
+  KEY key[kSortItems];
   uint32_t rank[kSortItems];
   const uint32_t lt = lanemask_lt();
 #pragma unroll
   for (int j = 0; j < kSortItems; ++j) {
     const unsigned long long idx = base + (unsigned long long)warp * (32 * kSortItems) + j * 32 + lane;
     const bool valid = idx < kn;
-    key[j] = valid ? a.keys_in[idx] : ~0ull;
+    key[j] = valid ? a.keys_in[idx] : (KEY)~(KEY)0;
     const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
     if (valid) {
       const uint32_t d = (uint32_t)(key[j] >> a.shift) & 0xffu;
@@ -266,11 +326,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(PassArgs a) {
     tot += c;
   }
   unsigned long long* lb = a.lookback + (part * a.passes + a.pass) * 256;
-  if (part == 0) {
-    st_relaxed_u64(lb + d, kFlagInc | tot);
-  } else {
-    st_relaxed_u64(lb + d, kFlagAgg | tot);
-  }
+  st_relaxed_u64(lb + d, (part == 0 ? kFlagInc : kFlagAgg) | tot);
   unsigned long long excl = 0;
   if (part > 0) {
     long long q = (long long)part - 1;
@@ -316,7 +372,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(PassArgs a) {
   __syncthreads();
   const uint32_t count = (uint32_t)((kn - base) < (unsigned long long)kSortPart ? (kn - base) : kSortPart);
   for (uint32_t i = tid; i < count; i += kSortThreads) {
-    const unsigned long long k = s_buf[i];
+    const KEY k = s_buf[i];
     const uint32_t dg = (uint32_t)(k >> a.shift) & 0xffu;
     s_dig[i] = (uint8_t)dg;
     const unsigned long long g = s_gbase[dg] + (i - s_lstart[dg]);
@@ -327,7 +383,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(PassArgs a) {
 #pragma unroll
   for (int j = 0; j < kSortItems; ++j) {
     const unsigned long long idx = base + (unsigned long long)warp * (32 * kSortItems) + j * 32 + lane;
-    if (idx < kn) s_val[lpos[j]] = a.vals_in[idx];
+    if (idx < kn) s_val[lpos[j]] = a.vals_in ? a.vals_in[idx] : (uint32_t)idx;
   }
   __syncthreads();
   for (uint32_t i = tid; i < count; i += kSortThreads) {
@@ -340,102 +396,137 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(PassArgs a) {
 // ---------------------------------------------------------------------------
 // tile ranges
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) ranges_kernel(const unsigned long long* __restrict__ keys, Status* st,
+__global__ void __launch_bounds__(256) ranges_kernel(const uint32_t* __restrict__ keys, Status* st,
                                                      unsigned long long cap, uint2* __restrict__ ranges,
                                                      int sorted_buf) {
-  const unsigned long long kn = st->keys_needed < cap ? st->keys_needed : cap;
+  const unsigned long long kn = element_count(&st->keys_needed, cap);
   if (blockIdx.x == 0 && threadIdx.x == 0) st->sorted_buf = (uint32_t)sorted_buf;
   for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < kn;
        k += (unsigned long long)gridDim.x * blockDim.x) {
-    const uint32_t t = (uint32_t)(keys[k] >> 32);
-    if (k == 0 || (uint32_t)(keys[k - 1] >> 32) != t) ranges[t].x = (uint32_t)k;
-    if (k + 1 == kn || (uint32_t)(keys[k + 1] >> 32) != t) ranges[t].y = (uint32_t)(k + 1);
+    const uint32_t t = keys[k];
+    if (k == 0 || keys[k - 1] != t) ranges[t].x = (uint32_t)k;
+    if (k + 1 == kn || keys[k + 1] != t) ranges[t].y = (uint32_t)(k + 1);
   }
 }
 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-
 static int clamp_grid(unsigned long long blocks, int sms, int per_sm) {
   const unsigned long long cap = (unsigned long long)sms * per_sm;
   if (blocks < 1) blocks = 1;
   return (int)(blocks < cap ? blocks : cap);
 }
 
-// Phase 1: scan, duplicate, histogram.  Everything device-resident.
+// Runs `passes` onesweep passes (those with run[p] != 0, or all if run is
+// null) from (keys_in, vals_in) through the ping-pong buffers kbuf/vbuf;
+// returns the index of the buffer holding the result, or -1 if no pass ran.
+template <class KEY>
+static int run_passes(const KEY* keys_in, const uint32_t* vals_in, KEY* const* kbuf, uint32_t* const* vbuf,
+                      const uint32_t* hist, unsigned long long* lookback, uint32_t* part_counter,
+                      const unsigned long long* count_dev, unsigned long long count, unsigned long long parts,
+                      int passes, const int* run, Status* status, int spin_limit, cudaStream_t st) {
+  int cur = -1;  // -1: still the input
+  for (int p = 0; p < passes; ++p) {
+    if (run && !run[p]) continue;
+    const int out = cur == 0 ? 1 : 0;
+    PassArgs<KEY> pa;
+    pa.keys_in = cur < 0 ? keys_in : kbuf[cur];
+    pa.vals_in = cur < 0 ? vals_in : vbuf[cur];
+    pa.keys_out = kbuf[out];
+    pa.vals_out = vbuf[out];
+    pa.digit_base = hist + p * 256;
+    pa.lookback = lookback;
+    pa.part_counter = part_counter + p;
+    pa.count_dev = count_dev;
+    pa.count = count;
+    pa.st = status;
+    pa.passes = passes;
+    pa.pass = p;
+    pa.shift = 8 * p;
+    pa.spin_limit = spin_limit;
+    onesweep_kernel<KEY><<<(unsigned)parts, kSortThreads, 0, st>>>(pa);
+    count_launches(1);
+    cur = out;
+  }
+  return cur;
+}
+
+// Phase 1: depth sort of the records, scan, duplicate, tile histograms.
 cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms) {
   const int64_t m = a.n * a.n_views;
   cudaError_t e;
-  // status word, histogram and ranges start at zero every frame
-  e = cudaMemsetAsync(a.ws.status, 0, sizeof(Status), st);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(a.ws.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(a.ws.ranges, 0, sizeof(uint2) * a.total_tiles, st);
-  if (e != cudaSuccess) return e;
-  const int nb = (int)((m + kScanBlock - 1) / kScanBlock);
-  unsigned long long* part = reinterpret_cast<unsigned long long*>(a.ws.scan_part);
+  // status word, histograms and ranges start at zero every frame
+  if ((e = cudaMemsetAsync(a.ws.status, 0, sizeof(Status), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.ws.hist, 0, sizeof(uint32_t) * 2 * kMaxPasses * 256, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.ws.ranges, 0, sizeof(uint2) * a.total_tiles, st)) != cudaSuccess) return e;
+  const unsigned long long um = (unsigned long long)m;
+  const unsigned long long dparts = (um + kSortPart - 1) / kSortPart;
+  const uint32_t* perm = a.ws.perm[0];
   if (m > 0) {
-    scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(a.ws.ntouch, m, part);
+    if ((e = cudaMemsetAsync(a.ws.lookback_d, 0, sizeof(unsigned long long) * 256 * kDepthPasses * dparts, st)) !=
+        cudaSuccess)
+      return e;
+    // depth sort of the records (values: record indices)
+    histogram_kernel<uint32_t><<<clamp_grid((um + 255) / 256, sms, 4), 256, 0, st>>>(a.ws.dkey[0], nullptr, um,
+                                                                                      kDepthPasses, a.ws.hist);
+    hist_scan_kernel<<<kDepthPasses, 256, 0, st>>>(a.ws.hist, a.ws.status->pass_trivial, nullptr, um);
+    count_launches(2);
+    uint32_t* const kb[2] = {a.ws.dkey[1], a.ws.dkey[0]};
+    uint32_t* const vb[2] = {a.ws.perm[1], a.ws.perm[0]};
+    const int r = run_passes<uint32_t>(a.ws.dkey[0], nullptr, kb, vb, a.ws.hist, a.ws.lookback_d,
+                                       a.ws.status->part_counter, nullptr, um, dparts, kDepthPasses, nullptr,
+                                       a.ws.status, a.spin_limit, st);
+    perm = vb[r];
+  }
+  const int nb = (int)((m + kScanBlock - 1) / kScanBlock);
+  if (m > 0) {
+    scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(a.ws.ntouch, perm, m, a.ws.scan_part);
     count_launches(1);
   }
-  scan_parts_kernel<<<1, 1024, 0, st>>>(part, nb, a.ws.status, a.cap);
+  scan_parts_kernel<<<1, 1024, 0, st>>>(a.ws.scan_part, nb, a.ws.status, a.cap);
   count_launches(1);
   if (m > 0) {
-    scan_down_kernel<<<nb, kScanThreads, 0, st>>>(a.ws.ntouch, m, part, a.ws.offsets);
+    scan_down_kernel<<<nb, kScanThreads, 0, st>>>(a.ws.ntouch, perm, m, a.ws.scan_part, a.ws.offsets);
     duplicate_kernel<<<clamp_grid((m + 255) / 256, sms, 8), 256, 0, st>>>(
-        a.n, a.n_views, a.ws.views, a.ws.ntouch, a.ws.offsets, a.ws.rect, a.ws.depth, a.ws.keys[0], a.ws.vals[0],
-        a.cap);
+        a.n, a.n_views, a.ws.views, perm, a.ws.ntouch, a.ws.offsets, a.ws.rect, a.ws.keys[0], a.ws.vals[0], a.cap);
     count_launches(2);
   }
-  histogram_kernel<<<clamp_grid((a.cap + 255) / 256, sms, 4), 256, 0, st>>>(a.ws.keys[0], a.ws.status, a.cap,
-                                                                           a.passes, a.ws.hist);
-  hist_scan_kernel<<<a.passes, 256, 0, st>>>(a.ws.hist, a.ws.status, a.cap);
-  count_launches(2);
+  if (a.passes > 0) {
+    uint32_t* th = a.ws.hist + kMaxPasses * 256;
+    histogram_kernel<uint32_t><<<clamp_grid((a.cap + 255) / 256, sms, 4), 256, 0, st>>>(
+        a.ws.keys[0], &a.ws.status->keys_needed, a.cap, a.passes, th);
+    hist_scan_kernel<<<a.passes, 256, 0, st>>>(th, a.ws.status->pass_trivial + kMaxPasses,
+                                               &a.ws.status->keys_needed, a.cap);
+    count_launches(2);
+  }
   return cudaGetLastError();
 }
 
-// Phase 2: radix passes (run[p] != 0) and ranges.  keys_known: exact key
+// Phase 2: tile passes (run[p] != 0) and ranges.  keys_known: exact key
 // count (sizes the grids), or -1 to size them for the capacity.
 cudaError_t launch_bin_phase2(const BinArgs& a, const int* run, long long keys_known, cudaStream_t st) {
   const unsigned long long kn = keys_known >= 0 ? (unsigned long long)keys_known : a.cap;
   const unsigned long long parts = (kn + kSortPart - 1) / kSortPart;
-  cudaError_t e = cudaSuccess;
-  if (parts > 0) {
-    e = cudaMemsetAsync(a.ws.lookback, 0, sizeof(unsigned long long) * 256 * a.passes * parts, st);
-    if (e != cudaSuccess) return e;
+  cudaError_t e;
+  int cur = 0;  // index into ws.keys / ws.vals of the sorted result
+  if (parts > 0 && a.passes > 0) {
+    if ((e = cudaMemsetAsync(a.ws.lookback, 0, sizeof(unsigned long long) * 256 * a.passes * parts, st)) !=
+        cudaSuccess)
+      return e;
+    uint32_t* const kb[2] = {a.ws.keys[1], a.ws.keys[0]};
+    uint32_t* const vb[2] = {a.ws.vals[1], a.ws.vals[0]};
+    const int r = run_passes<uint32_t>(a.ws.keys[0], a.ws.vals[0], kb, vb, a.ws.hist + kMaxPasses * 256,
+                                       a.ws.lookback, a.ws.status->part_counter + kMaxPasses,
+                                       &a.ws.status->keys_needed, a.cap, parts, a.passes, run, a.ws.status,
+                                       a.spin_limit, st);
+    cur = r < 0 ? 0 : (r == 0 ? 1 : 0);  // kb[0] is ws.keys[1]
   }
-  int cur = 0;
-  for (int p = 0; p < a.passes; ++p) {
-    if (!run[p] || parts == 0) continue;
-    PassArgs pa;
-    pa.keys_in = a.ws.keys[cur];
-    pa.vals_in = a.ws.vals[cur];
-    pa.keys_out = a.ws.keys[cur ^ 1];
-    pa.vals_out = a.ws.vals[cur ^ 1];
-    pa.digit_base = a.ws.hist + p * 256;
-    pa.lookback = a.ws.lookback;
-    pa.passes = a.passes;
-    pa.st = a.ws.status;
-    pa.cap = a.cap;
-    pa.pass = p;
-    pa.shift = 8 * p;
-    pa.spin_limit = a.spin_limit;
-    onesweep_kernel<<<(unsigned)parts, kSortThreads, 0, st>>>(pa);
-    count_launches(1);
-    cur ^= 1;
-  }
-  if (kn > 0) {
-    ranges_kernel<<<(unsigned)std::min<unsigned long long>((kn + 255) / 256, 1ull << 20), 256, 0, st>>>(
-        a.ws.keys[cur], a.ws.status, a.cap, a.ws.ranges, cur);
-  } else {
-    // nothing to sort: record which buffer (0) holds the (empty) result
-    ranges_kernel<<<1, 32, 0, st>>>(a.ws.keys[cur], a.ws.status, a.cap, a.ws.ranges, cur);
-  }
+  const unsigned grid = (unsigned)std::max<unsigned long long>(1, std::min<unsigned long long>((kn + 255) / 256,
+                                                                                               1ull << 20));
+  ranges_kernel<<<grid, 256, 0, st>>>(a.ws.keys[cur], a.ws.status, a.cap, a.ws.ranges, cur);
   count_launches(1);
-  e = cudaGetLastError();
-  return e;
+  return cudaGetLastError();
 }
 
 }  // namespace sr
@@ -463,6 +554,7 @@ constexpr size_t kNoallocKeyBytes = sizeof(unsigned long long) * kNoallocKeys;
 constexpr size_t kNoallocValBytes = sizeof(uint32_t) * kNoallocKeys;
 constexpr size_t kNoallocBytes =
     kNoallocStatusBytes + kNoallocHistBytes + kNoallocLookbackBytes + kNoallocKeyBytes + kNoallocValBytes;
+static_assert(sizeof(Status) <= kNoallocStatusBytes, "status word does not fit");
 
 // Host code must not use this name as a device address; it receives the
 // address from cudaGetSymbolAddress (see noalloc_scratch_address below).
@@ -484,7 +576,7 @@ __global__ void noalloc_reset_kernel(unsigned char* scratch, unsigned long long 
     st->flags = 0u;
     st->sorted_buf = 0u;
     st->keys_needed = n;
-    for (int p = 0; p < kMaxPasses; ++p) {
+    for (int p = 0; p < 2 * kMaxPasses; ++p) {
       st->part_counter[p] = 0u;
       st->pass_trivial[p] = 0u;
     }
@@ -520,11 +612,12 @@ extern "C" sr_status sr_sort_keys_noalloc(const uint64_t* keys_in, const uint32_
                                           int32_t sort_bits, uint64_t* keys_out, uint32_t* vals_out,
                                           void* stream) {
   using namespace sr;
+  typedef unsigned long long u64;
   if (n < 0 || sort_bits < 1 || sort_bits > 64) return SR_ERR_INVALID;
-  if ((unsigned long long)n > kNoallocKeys) return SR_ERR_CAPACITY;
+  if ((u64)n > kNoallocKeys) return SR_ERR_CAPACITY;
   if (n == 0) return SR_OK;
   if (!keys_in || !vals_in || !keys_out || !vals_out) return SR_ERR_INVALID;
-  if (keys_in == keys_out || vals_in == vals_out) return SR_ERR_INVALID;
+  if ((const void*)keys_in == (const void*)keys_out || vals_in == vals_out) return SR_ERR_INVALID;
   cudaError_t e;
   unsigned char* base = noalloc_scratch_address(&e);
   if (!base) return SR_ERR_CUDA;
@@ -532,43 +625,25 @@ extern "C" sr_status sr_sort_keys_noalloc(const uint64_t* keys_in, const uint32_
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int passes = (sort_bits + 7) / 8;
-  const unsigned long long un = (unsigned long long)n;
+  const u64 un = (u64)n;
   Status* status = reinterpret_cast<Status*>(base);
   uint32_t* hist = reinterpret_cast<uint32_t*>(base + kNoallocStatusBytes);
-  unsigned long long* lookback = reinterpret_cast<unsigned long long*>(base + kNoallocStatusBytes + kNoallocHistBytes);
-  unsigned long long* tmp_keys =
-      reinterpret_cast<unsigned long long*>(base + kNoallocStatusBytes + kNoallocHistBytes + kNoallocLookbackBytes);
+  u64* lookback = reinterpret_cast<u64*>(base + kNoallocStatusBytes + kNoallocHistBytes);
+  u64* tmp_keys = reinterpret_cast<u64*>(base + kNoallocStatusBytes + kNoallocHistBytes + kNoallocLookbackBytes);
   uint32_t* tmp_vals = reinterpret_cast<uint32_t*>(base + kNoallocStatusBytes + kNoallocHistBytes +
                                                    kNoallocLookbackBytes + kNoallocKeyBytes);
   noalloc_reset_kernel<<<clamp_grid((un * passes + 255) / 256, sms, 4), 256, 0, st>>>(base, un, passes);
-  histogram_kernel<<<clamp_grid((un + 255) / 256, sms, 4), 256, 0, st>>>(
-      reinterpret_cast<const unsigned long long*>(keys_in), status, un, passes, hist);
-  hist_scan_kernel<<<passes, 256, 0, st>>>(hist, status, un);
-  // ping-pong between the scratch buffer and the output so the last pass
+  histogram_kernel<u64><<<clamp_grid((un + 255) / 256, sms, 4), 256, 0, st>>>(
+      reinterpret_cast<const u64*>(keys_in), nullptr, un, passes, hist);
+  hist_scan_kernel<<<passes, 256, 0, st>>>(hist, status->pass_trivial, nullptr, un);
+  // ping-pong between the scratch buffer and the output so that the last pass
   // writes the output: an odd pass count starts into the output
-  const unsigned long long* kin = reinterpret_cast<const unsigned long long*>(keys_in);
-  const uint32_t* vin = vals_in;
-  bool into_out = (passes & 1) != 0;
-  const unsigned long long parts = (un + kSortPart - 1) / kSortPart;
-  for (int p = 0; p < passes; ++p) {
-    PassArgs pa;
-    pa.keys_in = kin;
-    pa.vals_in = vin;
-    pa.keys_out = into_out ? reinterpret_cast<unsigned long long*>(keys_out) : tmp_keys;
-    pa.vals_out = into_out ? vals_out : tmp_vals;
-    pa.digit_base = hist + p * 256;
-    pa.lookback = lookback;
-    pa.passes = passes;
-    pa.st = status;
-    pa.cap = un;
-    pa.pass = p;
-    pa.shift = 8 * p;
-    pa.spin_limit = 1 << 20;
-    onesweep_kernel<<<(unsigned)parts, kSortThreads, 0, st>>>(pa);
-    kin = pa.keys_out;
-    vin = pa.vals_out;
-    into_out = !into_out;
-  }
-  count_launches(3 + passes);
+  u64* const kb[2] = {(passes & 1) ? reinterpret_cast<u64*>(keys_out) : tmp_keys,
+                      (passes & 1) ? tmp_keys : reinterpret_cast<u64*>(keys_out)};
+  uint32_t* const vb[2] = {(passes & 1) ? vals_out : tmp_vals, (passes & 1) ? tmp_vals : vals_out};
+  const u64 parts = (un + kSortPart - 1) / kSortPart;
+  run_passes<u64>(reinterpret_cast<const u64*>(keys_in), vals_in, kb, vb, hist, lookback, status->part_counter,
+                  nullptr, un, parts, passes, nullptr, status, 1 << 20, st);
+  count_launches(3);
   return cudaGetLastError() == cudaSuccess ? SR_OK : SR_ERR_CUDA;
 }

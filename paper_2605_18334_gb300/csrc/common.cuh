@@ -19,20 +19,26 @@ enum WsSlot {
   WS_VIEWS,        // ViewInfo[SR_MAX_VIEWS]
   WS_REC,          // float4[M][4] render records
   WS_DEPTH,        // uint32_t[M] FP32 depth bits
+  WS_DKEY0,        // uint32_t[M] depth sort key: depth bits, or ~0 if the record touches no tile
+  WS_DKEY1,        //   ping-pong
+  WS_PERM0,        // uint32_t[M] record indices in depth order (after the depth sort)
+  WS_PERM1,        //   ping-pong
   WS_RECT,         // uint2[M]   tile rectangle (tx0 | ty0 << 16, tx1 | ty1 << 16), tx1/ty1 exclusive
   WS_NTOUCH,       // uint32_t[M] tiles touched
-  WS_OFFSETS,      // uint32_t[M] exclusive scan of WS_NTOUCH
-  WS_SCAN_PART,    // uint32_t[scan blocks + 1]
-  WS_KEYS0, WS_KEYS1,  // uint64_t[cap] ping-pong
-  WS_VALS0, WS_VALS1,  // uint32_t[cap] ping-pong
-  WS_HIST,         // uint32_t[kMaxPasses][256] digit counts, then exclusive offsets
-  WS_LOOKBACK,     // uint64_t[kMaxPasses][parts][256] decoupled look-back state
+  WS_OFFSETS,      // uint32_t[M] exclusive scan of the tile counts, in depth order
+  WS_SCAN_PART,    // uint64_t[scan blocks + 1]
+  WS_KEYS0, WS_KEYS1,  // uint32_t[cap] global tile ids, ping-pong
+  WS_VALS0, WS_VALS1,  // uint32_t[cap] record indices, ping-pong
+  WS_HIST,         // uint32_t[2 * kMaxPasses][256] digit counts -> exclusive offsets (depth, tile)
+  WS_LOOKBACK_D,   // uint64_t[parts(M)][kDepthPasses][256] look-back words of the depth sort
+  WS_LOOKBACK,     // uint64_t[parts(cap)][tile passes][256] look-back words of the tile sort
   WS_RANGES,       // uint2[total_tiles] [start, end) of each tile's sorted keys
   WS_D2,           // float[M][16] per-(view, Gaussian) 2D gradients
   WS_NUM_SLOTS
 };
 
-constexpr int kMaxPasses = 8;          // 64-bit keys, 8-bit digits
+constexpr int kMaxPasses = 8;          // per sort: 8-bit digits of at most 64-bit keys
+constexpr int kDepthPasses = 4;        // 32-bit depth keys
 constexpr int kSortThreads = 256;      // threads per onesweep partition block
 constexpr int kSortItems = 16;         // keys per thread
 constexpr int kSortPart = kSortThreads * kSortItems;  // keys per partition
@@ -50,8 +56,8 @@ struct Status {
   uint32_t flags;
   uint32_t sorted_buf;                // which ping-pong buffer holds the sorted keys
   unsigned long long keys_needed;     // total keys of the last frame
-  uint32_t part_counter[kMaxPasses];  // onesweep partition tickets per pass
-  uint32_t pass_trivial[kMaxPasses];  // 1 if one digit holds every key of that pass
+  uint32_t part_counter[2 * kMaxPasses];  // onesweep partition tickets per pass (depth sort, tile sort)
+  uint32_t pass_trivial[2 * kMaxPasses];  // 1 if one digit holds every key of that pass
   uint32_t timeout_where;             // pass * 1e6 + partition of the first timed-out wait
   uint32_t pad1;
   unsigned long long pairs_tested;    // render_fwd: (pixel, Gaussian) pairs evaluated
@@ -242,13 +248,16 @@ struct Ws {
   ViewInfo* views;
   float4* rec;
   uint32_t* depth;
+  uint32_t* dkey[2];
+  uint32_t* perm[2];
   uint2* rect;
   uint32_t* ntouch;
   uint32_t* offsets;
-  uint32_t* scan_part;
-  unsigned long long* keys[2];
+  unsigned long long* scan_part;
+  uint32_t* keys[2];
   uint32_t* vals[2];
   uint32_t* hist;
+  unsigned long long* lookback_d;
   unsigned long long* lookback;
   uint2* ranges;
   float* d2;
@@ -256,23 +265,29 @@ struct Ws {
 
 inline Ws ws_ptrs(const sr_plan& p, void* base) {
   char* b = static_cast<char*>(base);
+  auto at = [&](int slot) { return b + p.off[slot]; };
   Ws w;
-  w.status = reinterpret_cast<Status*>(b + p.off[WS_STATUS]);
-  w.views = reinterpret_cast<ViewInfo*>(b + p.off[WS_VIEWS]);
-  w.rec = reinterpret_cast<float4*>(b + p.off[WS_REC]);
-  w.depth = reinterpret_cast<uint32_t*>(b + p.off[WS_DEPTH]);
-  w.rect = reinterpret_cast<uint2*>(b + p.off[WS_RECT]);
-  w.ntouch = reinterpret_cast<uint32_t*>(b + p.off[WS_NTOUCH]);
-  w.offsets = reinterpret_cast<uint32_t*>(b + p.off[WS_OFFSETS]);
-  w.scan_part = reinterpret_cast<uint32_t*>(b + p.off[WS_SCAN_PART]);
-  w.keys[0] = reinterpret_cast<unsigned long long*>(b + p.off[WS_KEYS0]);
-  w.keys[1] = reinterpret_cast<unsigned long long*>(b + p.off[WS_KEYS1]);
-  w.vals[0] = reinterpret_cast<uint32_t*>(b + p.off[WS_VALS0]);
-  w.vals[1] = reinterpret_cast<uint32_t*>(b + p.off[WS_VALS1]);
-  w.hist = reinterpret_cast<uint32_t*>(b + p.off[WS_HIST]);
-  w.lookback = reinterpret_cast<unsigned long long*>(b + p.off[WS_LOOKBACK]);
-  w.ranges = reinterpret_cast<uint2*>(b + p.off[WS_RANGES]);
-  w.d2 = reinterpret_cast<float*>(b + p.off[WS_D2]);
+  w.status = reinterpret_cast<Status*>(at(WS_STATUS));
+  w.views = reinterpret_cast<ViewInfo*>(at(WS_VIEWS));
+  w.rec = reinterpret_cast<float4*>(at(WS_REC));
+  w.depth = reinterpret_cast<uint32_t*>(at(WS_DEPTH));
+  w.dkey[0] = reinterpret_cast<uint32_t*>(at(WS_DKEY0));
+  w.dkey[1] = reinterpret_cast<uint32_t*>(at(WS_DKEY1));
+  w.perm[0] = reinterpret_cast<uint32_t*>(at(WS_PERM0));
+  w.perm[1] = reinterpret_cast<uint32_t*>(at(WS_PERM1));
+  w.rect = reinterpret_cast<uint2*>(at(WS_RECT));
+  w.ntouch = reinterpret_cast<uint32_t*>(at(WS_NTOUCH));
+  w.offsets = reinterpret_cast<uint32_t*>(at(WS_OFFSETS));
+  w.scan_part = reinterpret_cast<unsigned long long*>(at(WS_SCAN_PART));
+  w.keys[0] = reinterpret_cast<uint32_t*>(at(WS_KEYS0));
+  w.keys[1] = reinterpret_cast<uint32_t*>(at(WS_KEYS1));
+  w.vals[0] = reinterpret_cast<uint32_t*>(at(WS_VALS0));
+  w.vals[1] = reinterpret_cast<uint32_t*>(at(WS_VALS1));
+  w.hist = reinterpret_cast<uint32_t*>(at(WS_HIST));
+  w.lookback_d = reinterpret_cast<unsigned long long*>(at(WS_LOOKBACK_D));
+  w.lookback = reinterpret_cast<unsigned long long*>(at(WS_LOOKBACK));
+  w.ranges = reinterpret_cast<uint2*>(at(WS_RANGES));
+  w.d2 = reinterpret_cast<float*>(at(WS_D2));
   return w;
 }
 

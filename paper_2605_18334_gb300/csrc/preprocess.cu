@@ -280,22 +280,49 @@ __global__ void view_table_kernel(const sr_camera* cams, int n_views, ViewInfo* 
   }
 }
 
+// Block shape of the per-Gaussian kernels: 4 warps; each warp takes 32
+// consecutive Gaussians at a time and stages their SH coefficients through a
+// padded shared-memory tile (row = 3K + 1 floats, so lane l reading its own
+// row is conflict-free), which turns the per-thread 3K-float strided loads
+// into coalesced ones.
+constexpr int kPreThreads = 128;
+constexpr int kPreWarps = kPreThreads / 32;
+
+__host__ __device__ constexpr size_t cams_bytes(int n_views) { return (sizeof(sr_camera) * n_views + 15) & ~size_t(15); }
+
+template <int K3, int DT_SH>
+__device__ __forceinline__ void stage_sh(const void* sh, int64_t base, int cnt, float* s, int lane) {
+  const int64_t off = base * K3;
+  for (int w = lane; w < cnt * K3; w += 32) {
+    const int g = w / K3, k = w - g * K3;
+    s[g * (K3 + 1) + k] = ld<DT_SH>(sh, off + w);
+  }
+}
+
 template <int DEG, int DT_SH>
-__global__ void __launch_bounds__(256) preprocess_fwd_kernel(PreArgs a) {
-  extern __shared__ sr_camera s_cams[];
+__global__ void __launch_bounds__(kPreThreads) preprocess_fwd_kernel(PreArgs a) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  constexpr int K3 = 3 * K, ROW = K3 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  sr_camera* s_cams = reinterpret_cast<sr_camera*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* s_sh = reinterpret_cast<float*>(smem_raw + cams_bytes(a.n_views)) + warp * 32 * ROW;
   for (int v = threadIdx.x; v < a.n_views; v += blockDim.x) s_cams[v] = a.cams[v];
   __syncthreads();
-  constexpr int K = (DEG + 1) * (DEG + 1);
   const int64_t n = a.g.n;
   const bool has_split = a.g.split_dir != nullptr;
   const bool two = a.g.two_opacities != 0;
   const float tau = a.cfg.alpha_min;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t base = ((int64_t)blockIdx.x * kPreWarps + warp) * 32; base < n;
+       base += (int64_t)gridDim.x * kPreWarps * 32) {
+    const int cnt = (int)(n - base < 32 ? n - base : 32);
+    stage_sh<K3, DT_SH>(a.g.sh, base, cnt, s_sh, lane);
+    __syncwarp();
+    const int64_t i = base + lane;
+    const float* sh = s_sh + lane * ROW;
+    if (lane < cnt) {
     Attr A;
     load_attr(a.g, i, has_split, A);
-    float sh[K * 3];
-#pragma unroll
-    for (int k = 0; k < K * 3; ++k) sh[k] = ld<DT_SH>(a.g.sh, (int64_t)K * 3 * i + k);
 
     for (int v = 0; v < a.n_views; ++v) {
       const sr_camera& c = s_cams[v];
@@ -359,7 +386,10 @@ __global__ void __launch_bounds__(256) preprocess_fwd_kernel(PreArgs a) {
       }
       a.ws.ntouch[m] = ntouch;
       a.ws.rect[m] = rect;
+      a.ws.dkey[0][m] = ntouch ? __float_as_uint(tz) : 0xffffffffu;
     }
+    }
+    __syncwarp();
   }
 }
 
@@ -396,23 +426,34 @@ __device__ __forceinline__ void skew_project_bwd(const Proj& P, const float* e, 
 }
 
 template <int DEG, int DT_SH>
-__global__ void __launch_bounds__(256) preprocess_bwd_kernel(BwdArgs a) {
-  extern __shared__ sr_camera s_cams[];
+__global__ void __launch_bounds__(kPreThreads, 4) preprocess_bwd_kernel(BwdArgs a) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  constexpr int K3 = 3 * K, ROW = K3 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  sr_camera* s_cams = reinterpret_cast<sr_camera*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* s_sh = reinterpret_cast<float*>(smem_raw + cams_bytes(a.n_views)) + warp * 64 * ROW;
+  float* s_gsh = s_sh + 32 * ROW;
   for (int v = threadIdx.x; v < a.n_views; v += blockDim.x) s_cams[v] = a.cams[v];
   __syncthreads();
-  constexpr int K = (DEG + 1) * (DEG + 1);
   const int64_t n = a.g.n;
   const bool has_split = a.g.split_dir != nullptr;
   const bool two = a.g.two_opacities != 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t base = ((int64_t)blockIdx.x * kPreWarps + warp) * 32; base < n;
+       base += (int64_t)gridDim.x * kPreWarps * 32) {
+    const int cnt = (int)(n - base < 32 ? n - base : 32);
+    stage_sh<K3, DT_SH>(a.g.sh, base, cnt, s_sh, lane);
+    float* gsh = s_gsh + lane * ROW;
+    const float* sh = s_sh + lane * ROW;
+#pragma unroll
+    for (int k = 0; k < K3; ++k) gsh[k] = 0.0f;
+    __syncwarp();
+    const int64_t i = base + lane;
+    if (lane < cnt) {
     float g_mu[3] = {0, 0, 0}, g_ls[3] = {0, 0, 0}, g_q[4] = {0, 0, 0, 0}, g_eta[3] = {0, 0, 0},
           g_dsp[3] = {0, 0, 0}, g_l1 = 0.0f, g_l2 = 0.0f, g_abs = 0.0f, g_depth = 0.0f;
-    float g_sh[K * 3];
-#pragma unroll
-    for (int k = 0; k < K * 3; ++k) g_sh[k] = 0.0f;
     bool loaded = false;
     Attr A;
-    float sh[K * 3];
     for (int v = 0; v < a.n_views; ++v) {
       const int64_t m = (int64_t)v * n + i;
       if (a.ws.ntouch[m] == 0) continue;
@@ -422,8 +463,6 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(BwdArgs a) {
                             q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, q3.z, q3.w};
       if (!loaded) {
         load_attr(a.g, i, has_split, A);
-#pragma unroll
-        for (int k = 0; k < K * 3; ++k) sh[k] = ld<DT_SH>(a.g.sh, (int64_t)K * 3 * i + k);
         loaded = true;
       }
       const sr_camera& c = s_cams[v];
@@ -445,7 +484,7 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(BwdArgs a) {
         const float gc_ = acc < 0.0f ? 0.0f : gd[G_R + ch];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-          g_sh[3 * k + ch] += Y[k] * gc_;
+          gsh[3 * k + ch] += Y[k] * gc_;
           gY[k] += sh[3 * k + ch] * gc_;
         }
       }
@@ -580,10 +619,17 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(BwdArgs a) {
       o = a.out.split_dir + 3 * i;
       o[0] = g_dsp[0]; o[1] = g_dsp[1]; o[2] = g_dsp[2];
     }
-#pragma unroll
-    for (int k = 0; k < K * 3; ++k) a.out.sh[(int64_t)K * 3 * i + k] = g_sh[k];
     if (a.out.means2d_abs) a.out.means2d_abs[i] = g_abs;
     if (a.out.depth_grad) a.out.depth_grad[i] = g_depth;
+    }
+    __syncwarp();
+    // SH gradients out of the padded tile with coalesced stores
+    const int64_t off = base * K3;
+    for (int w = lane; w < cnt * K3; w += 32) {
+      const int g = w / K3, k = w - g * K3;
+      a.out.sh[off + w] = s_gsh[g * ROW + k];
+    }
+    __syncwarp();
   }
 }
 
@@ -596,15 +642,20 @@ static cudaError_t launch_sized(void (*fn)(Args), const Args& a, int grid, size_
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  fn<<<grid, 256, smem, st>>>(a);
+  fn<<<grid, kPreThreads, smem, st>>>(a);
   count_launches(1);
   return cudaGetLastError();
 }
 
 static int grid_for(int64_t n, int sms) {
-  const int64_t blocks = (n + 255) / 256;
-  const int64_t cap = (int64_t)sms * 8;
+  const int64_t blocks = (n + kPreThreads - 1) / kPreThreads;
+  const int64_t cap = (int64_t)sms * 16;
   return (int)std::max<int64_t>(1, std::min(blocks, cap));
+}
+
+static size_t sh_stage_bytes(int deg, int tiles_per_warp) {
+  const int row = 3 * (deg + 1) * (deg + 1) + 1;
+  return sizeof(float) * (size_t)kPreWarps * 32 * row * tiles_per_warp;
 }
 
 cudaError_t launch_preprocess_fwd(const PreArgs& a, cudaStream_t st, int sms) {
@@ -613,7 +664,7 @@ cudaError_t launch_preprocess_fwd(const PreArgs& a, cudaStream_t st, int sms) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || a.g.n == 0) return e;
   const int grid = grid_for(a.g.n, sms);
-  const size_t smem = sizeof(sr_camera) * a.n_views;
+  const size_t smem = cams_bytes(a.n_views) + sh_stage_bytes(a.g.sh_degree, 1);
 #define SR_DEG_CASE(D)                                                                              \
   case D:                                                                                           \
     if (a.g.dt_sh == SR_F32) return launch_sized(preprocess_fwd_kernel<D, SR_F32>, a, grid, smem, st);   \
@@ -632,7 +683,7 @@ cudaError_t launch_preprocess_fwd(const PreArgs& a, cudaStream_t st, int sms) {
 cudaError_t launch_preprocess_bwd(const BwdArgs& a, cudaStream_t st, int sms) {
   if (a.g.n == 0) return cudaSuccess;
   const int grid = grid_for(a.g.n, sms);
-  const size_t smem = sizeof(sr_camera) * a.n_views;
+  const size_t smem = cams_bytes(a.n_views) + sh_stage_bytes(a.g.sh_degree, 2);
 #define SR_DEG_CASE(D)                                                                              \
   case D:                                                                                           \
     if (a.g.dt_sh == SR_F32) return launch_sized(preprocess_bwd_kernel<D, SR_F32>, a, grid, smem, st);   \

@@ -98,10 +98,39 @@ __global__ void __launch_bounds__(256) render_fwd_kernel(RenderArgs a) {
   }
 }
 
-__device__ __forceinline__ float warp_sum(float x) {
+// Sum 16 per-lane values over the warp with a transposing butterfly: at each
+// step a lane keeps half of its values and sends the other half to its
+// partner, so 8 + 4 + 2 + 1 + 1 shuffles replace 16 x 5.  Returns, in every
+// lane, the warp total of value index (lane >> 1) & 15.
+__device__ __forceinline__ float warp_transpose_sum16(float (&v)[16], int lane) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
+  for (int i = 0; i < 8; ++i) {
+    const bool hi = lane & 16;
+    const float send = hi ? v[i] : v[i + 8];
+    const float keep = hi ? v[i + 8] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const bool hi = lane & 8;
+    const float send = hi ? v[i] : v[i + 4];
+    const float keep = hi ? v[i + 4] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const bool hi = lane & 4;
+    const float send = hi ? v[i] : v[i + 2];
+    const float keep = hi ? v[i + 2] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  {
+    const bool hi = lane & 2;
+    const float send = hi ? v[0] : v[1];
+    const float keep = hi ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
 __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
@@ -113,6 +142,10 @@ template <int MODE>
 __global__ void __launch_bounds__(256) render_bwd_kernel(RenderArgs a) {
   __shared__ float4 s_r0[256], s_r1[256], s_r2[MODE == MODE_PLAIN ? 1 : 256], s_r3[256];
   __shared__ uint32_t s_id[256];
+  // per-batch gradient accumulators, component-major with a padded row so
+  // both the warps' adds (16 components of one Gaussian) and the flush (one
+  // Gaussian per thread) are free of bank conflicts
+  __shared__ float s_acc[16][257];
   __shared__ uint32_t s_max;
   const int64_t tile = blockIdx.x;
   const int v = view_of_tile(a.views, a.n_views, tile);
@@ -161,12 +194,14 @@ __global__ void __launch_bounds__(256) render_bwd_kernel(RenderArgs a) {
       if (MODE != MODE_PLAIN) s_r2[threadIdx.x] = r[2];
       s_r3[threadIdx.x] = r[3];
     }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) s_acc[k][threadIdx.x] = 0.0f;
     __syncthreads();
     for (int j = (int)(bend - bstart) - 1; j >= 0; --j) {
       const uint32_t pos = bstart + j;
-      float gr[14];
+      float gr[16];
 #pragma unroll
-      for (int k = 0; k < 14; ++k) gr[k] = 0.0f;
+      for (int k = 0; k < 16; ++k) gr[k] = 0.0f;
       bool contrib = false;
       if (pos < my_end) {
         const float4 r0 = s_r0[j], r1 = s_r1[j], r3 = s_r3[j];
@@ -215,18 +250,22 @@ __global__ void __launch_bounds__(256) render_bwd_kernel(RenderArgs a) {
         }
       }
       if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-        for (int k = 0; k < 14; ++k) gr[k] = warp_sum(gr[k]);
-        if (lane == 0) {
-          float* dst = a.d2 + kD2Stride * (int64_t)s_id[j];
-          const float gabs = sqrtf(gr[G_MX] * gr[G_MX] + gr[G_MY] * gr[G_MY]);
-          (void)gabs;
-          red_add_v4(dst, gr[0], gr[1], gr[2], gr[3]);
-          red_add_v4(dst + 4, gr[4], gr[5], gr[6], gr[7]);
-          red_add_v4(dst + 8, gr[8], gr[9], gr[10], gr[11]);
-          red_add_v4(dst + 12, gr[12], gr[13], 0.0f, 0.0f);
-        }
+        const float sum = warp_transpose_sum16(gr, lane);
+        if ((lane & 1) == 0 && sum != 0.0f) atomicAdd(&s_acc[lane >> 1][j], sum);
       }
+    }
+    __syncthreads();
+    // one set of vector atomics per Gaussian per batch
+    const int cnt = (int)(bend - bstart);
+    if ((int)threadIdx.x < cnt) {
+      float c[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) c[k] = s_acc[k][threadIdx.x];
+      float* dst = a.d2 + kD2Stride * (int64_t)s_id[threadIdx.x];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (c[4 * q] != 0.0f || c[4 * q + 1] != 0.0f || c[4 * q + 2] != 0.0f || c[4 * q + 3] != 0.0f)
+          red_add_v4(dst + 4 * q, c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]);
     }
     bend = bstart;
   }

@@ -202,39 +202,46 @@ class Rasterizer:
                         _stream_ptr(stream))
         return out
 
-    # -- debugging views of the workspace (read-only copies) --------------
+    # -- read-only views of the workspace (tests and diagnostics) ---------
+    # slot numbers of the workspace layout (csrc/common.cuh, enum WsSlot)
+    _S_STATUS, _S_REC, _S_DEPTH, _S_RECT, _S_NTOUCH = 0, 2, 3, 8, 9
+    _S_KEYS0, _S_VALS0, _S_D2 = 12, 14, 20
+
     def _slot(self, k: int, nbytes: int) -> torch.Tensor:
         off = int(self.plan.off[k])
         return self.ws[off:off + nbytes]
 
     def sorted_keys(self):
-        """(keys uint64 as int64 tensor, vals int32) of the last bin_sort."""
+        """The last frame's sorted list as (tile << 32 | FP32 depth bits) keys
+        (int64 tensor holding the uint64 bits) and record indices (int32)."""
         kn = int(self.keys)
-        st = self._slot(0, 16).clone().cpu().numpy()
+        st = self._slot(self._S_STATUS, 16).clone().cpu().numpy()
         buf = int(st[4:8].view(np.uint32)[0])
-        keys = self._slot(8 + buf, 8 * kn).view(torch.int64)
-        vals = self._slot(10 + buf, 4 * kn).view(torch.int32)
+        tiles = self._slot(self._S_KEYS0 + buf, 4 * kn).view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+        vals = self._slot(self._S_VALS0 + buf, 4 * kn).view(torch.int32)
+        depth = self.depth_bits().to(torch.int64) & 0xFFFFFFFF
+        keys = (tiles << 32) | depth[vals.to(torch.int64)] if kn else tiles
         return keys, vals
 
     def records(self) -> torch.Tensor:
         m = self.plan.n * self.n_views
-        return self._slot(2, 64 * m).view(torch.float32).view(m, 16)
+        return self._slot(self._S_REC, 64 * m).view(torch.float32).view(m, 16)
 
     def depth_bits(self) -> torch.Tensor:
         m = self.plan.n * self.n_views
-        return self._slot(3, 4 * m).view(torch.int32)
+        return self._slot(self._S_DEPTH, 4 * m).view(torch.int32)
 
     def tile_counts(self) -> torch.Tensor:
         m = self.plan.n * self.n_views
-        return self._slot(5, 4 * m).view(torch.int32)
+        return self._slot(self._S_NTOUCH, 4 * m).view(torch.int32)
 
     def rects(self) -> torch.Tensor:
         m = self.plan.n * self.n_views
-        return self._slot(4, 8 * m).view(torch.int32).view(m, 2)
+        return self._slot(self._S_RECT, 8 * m).view(torch.int32).view(m, 2)
 
     def d2(self) -> torch.Tensor:
         m = self.plan.n * self.n_views
-        return self._slot(15, 64 * m).view(torch.float32).view(m, 16)
+        return self._slot(self._S_D2, 64 * m).view(torch.float32).view(m, 16)
 
 
 class _RasterizeFn(torch.autograd.Function):
