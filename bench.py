@@ -194,12 +194,15 @@ def run_ours(args):
             return rr.backward(gs, dimg)
         return None
 
+    tune = r.autotune(g, d_img)
     for _ in range(max(3, args.warmup)):
         step(g, r, d_img)
     torch.cuda.synchronize()
 
     K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
+    NS = 5
+    names = ["preprocess", "bin_sort", "render_fwd", "render_bwd_composite", "render_bwd_project"]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(NS + 1)] for _ in range(K)]
     props = torch.cuda.get_device_properties(dev)
     bus = getattr(props, "pci_bus_id", None)
     launches0 = N.sr_kernel_launches()
@@ -216,69 +219,81 @@ def run_ours(args):
             e[2].record(stream)
             r.render_fwd()
             e[3].record(stream)
-            r.backward(g, d_img)
+            r.backward_composite(d_img)
             e[4].record(stream)
+            r.backward_project(g)
+            e[5].record(stream)
         torch.cuda.synchronize()
     launches = N.sr_kernel_launches() - launches0
     barrier(world)
-    stage_ms = np.array([[ev[k][i].elapsed_time(ev[k][i + 1]) for i in range(4)] for k in range(K)])
+    stage_ms = np.array([[ev[k][i].elapsed_time(ev[k][i + 1]) for i in range(NS)] for k in range(K)])
     step_ms = stage_ms.sum(1)
     total_ms = max_over_ranks(float(step_ms.sum()), world)
     ms_per_step = total_ms / K
     value = world * K / (total_ms / 1e3)
     tested, blended = N.sr_frame_counters(r.plan, r.ws.data_ptr(), stream.cuda_stream)
+    replayed = int(r.n_contrib.to(torch.int64).sum().item())
     clocks = clk.summary()
 
+    cfgd = config_dict(args.n)
+    cfgd["launch"] = {"fwd_pixels_per_thread": tune["fwd_pixels_per_thread"],
+                      "bwd_pixels_per_thread": tune["bwd_pixels_per_thread"], "autotuned": True}
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K,
            "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_dict(args.n),
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfgd,
            "gpu_launches": int(launches)}
     fwd_ms = stage_ms[:, :3].sum(1).mean()
-    out["stages_ms"] = {k: round(float(v), 4) for k, v in
-                        zip(["preprocess", "bin_sort", "render_fwd", "render_bwd"], stage_ms.mean(0))}
+    stage_mean = stage_ms.mean(0)
+    out["stages_ms"] = {k: round(float(v), 4) for k, v in zip(names, stage_mean)}
     out["fwd_frames_per_s"] = round(1e3 / fwd_ms, 2)
     out["keys"] = int(r.keys)
     out["pairs_tested"] = tested
+    out["pairs_replayed_bwd"] = replayed
     out["pairs_blended"] = blended
-    out["blends_per_s"] = round(blended / (stage_ms[:, 2].mean() / 1e3), 1)
+    out["blends_per_s"] = round(blended / (stage_mean[2] / 1e3), 1)
     out["clocks"] = clocks
+    out["autotune_ms"] = {"fwd": {str(k): round(v, 4) for k, v in tune["fwd_ms"].items()},
+                          "bwd": {str(k): round(v, 4) for k, v in tune["bwd_ms"].items()}}
 
     # roofline of the dominant stage (measured live with the events above)
     peaks = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK))
     sms = props.multi_processor_count
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    stage_mean = stage_ms.mean(0)
+    alu_peak = sms * 128 * max_mhz * 1e6 / 1e12  # FP32 lane-ops/s (an FMA is one op), T/s
+    # algorithmic work per unit: 25 FP32 ops per evaluated (pixel, Gaussian)
+    # pair; the backward adds 60 per blended pair for the gradient math
+    ops = {2: tested * 25, 3: replayed * 25 + blended * 60}
+    pre_bytes = args.n * 248 + args.n * 20 + int((r.tile_counts() > 0).sum()) * 64
+    nrec = int((r.tile_counts() > 0).sum())
+    proj_bytes = args.n * (248 + 4) + nrec * 64 + args.n * 248
+    bytes_ = {0: pre_bytes, 4: proj_bytes}
     dom = int(np.argmax(stage_mean))
-    alu_peak = sms * 128 * max_mhz * 1e6 / 1e12  # FP32 lane-ops/s (an FMA is one op), TOPS
-    if dom in (2, 3):
-        # blend loop: 25 FP32 ops per tested pair (forward), about 80 per blended pair backward
-        if dom == 2:
-            ops = tested * 25
-        else:
-            ops = tested * 25 + blended * 80
-        achieved = ops / (stage_mean[dom] / 1e3) / 1e12
-        out["roofline"] = {"kernel": ["preprocess", "bin_sort", "render_fwd", "render_bwd"][dom], "bound": "alu",
-                           "achieved": round(achieved, 3), "peak": round(alu_peak, 3), "unit": "TFLOP/s",
-                           "frac": round(achieved / alu_peak, 4), "traffic": None,
-                           "peak_source": f"{sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz (derived)"}
+    if dom in ops:
+        achieved = ops[dom] / (stage_mean[dom] / 1e3) / 1e12
+        out["roofline"] = {"kernel": names[dom], "bound": "alu", "achieved": round(achieved, 3),
+                           "peak": round(alu_peak, 3), "unit": "TFLOP/s", "frac": round(achieved / alu_peak, 4),
+                           "traffic": None,
+                           "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz"}
     else:
-        b = 0.0
-        if dom == 0:
-            b = args.n * 248 + args.n * 16 + int((r.tile_counts() > 0).sum()) * 64
+        b = bytes_.get(dom, 0)
         achieved = b / (stage_mean[dom] / 1e3) / 1e9
-        out["roofline"] = {"kernel": ["preprocess", "bin_sort"][dom], "bound": "hbm", "achieved": round(achieved, 1),
-                           "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None}
-    # HBM stages for reference
-    pre_bytes = args.n * 248 + args.n * 16 + int((r.tile_counts() > 0).sum()) * 64
-    out["hbm_stages"] = {"preprocess_GBps": round(pre_bytes / (stage_mean[0] / 1e3) / 1e9, 1),
-                         "bin_sort_GBps": round((int(r.keys) * (12 + 24 * r.plan.sort_passes)) /
-                                                (stage_mean[1] / 1e3) / 1e9, 1),
-                         "peak_GBps": hbm}
+        out["roofline"] = {"kernel": names[dom], "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+                           "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None}
+    out["other_stages"] = {
+        "render_fwd_TFLOPs": round(ops[2] / (stage_mean[2] / 1e3) / 1e12, 3),
+        "render_bwd_composite_TFLOPs": round(ops[3] / (stage_mean[3] / 1e3) / 1e12, 3),
+        "alu_peak_TFLOPs": round(alu_peak, 3),
+        "preprocess_GBps": round(pre_bytes / (stage_mean[0] / 1e3) / 1e9, 1),
+        "render_bwd_project_GBps": round(proj_bytes / (stage_mean[4] / 1e3) / 1e9, 1),
+        "bin_sort_GBps": round((args.n * 4 * 16 + int(r.keys) * (8 + 16 * r.plan.sort_passes + 8)) /
+                               (stage_mean[1] / 1e3) / 1e9, 1),
+        "hbm_peak_GBps": hbm}
 
     if not args.no_variants:
         out["variants"] = variants(args, sc, cam, up, dev, flush)
-        out["e2e"] = e2e(args, sc, cam, up, dev, world)
+        out["variants"]["trajectory_64"] = trajectory(args, sc, dev, flush)
+    out["e2e"] = e2e(args, sc, cam, up, dev, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, cam, up, args.cpu_budget)
     if rank == 0:
@@ -317,6 +332,7 @@ def variants(args, sc, cam, up, dev, flush):
     for name, dt in (("fp32", torch.float32), ("bf16_storage", torch.bfloat16)):
         g = Gaussians.from_scene(sc, device=dev, sh_dtype=dt, scale_dtype=dt, skew_dtype=dt)
         r = Rasterizer(g, [cam], Config(), key_capacity=int(12 * args.n))
+        r.autotune(g, d_img)
         for _ in range(3):
             r.forward(g)
             r.backward(g, d_img)
@@ -325,6 +341,66 @@ def variants(args, sc, cam, up, dev, flush):
         res[name] = {"fwd_frames_per_s": round(1e3 / fwd, 2), "fwdbwd_frames_per_s": round(1e3 / fb, 2)}
         del r, g
         torch.cuda.empty_cache()
+    return res
+
+
+def trajectory(args, sc, dev, flush, n_views=64):
+    """Batched camera trajectory: n_views cameras on the closed spline orbit,
+    resolutions cycling 640x360 / 1280x720 / 1920x1080, forward only.  One
+    plan over all views (shared key pool, one composite launch over every
+    tile), captured once in a CUDA graph and replayed, against the same views
+    rendered one by one with single-view plans."""
+    import torch
+
+    from paper_2605_18334_gb300 import scenes
+    from paper_2605_18334_gb300.rasterizer import Config, Gaussians, Rasterizer
+
+    cams = scenes.trajectory_cameras(n_views)
+    g = Gaussians.from_scene(sc, device=dev)
+    stream = torch.cuda.current_stream()
+    r = Rasterizer(g, cams, Config())
+    r.forward(g)  # sizes the key pool (grows the plan once)
+    r.autotune(g)
+    r.forward(g)
+    keys = int(r.keys)
+    s = torch.cuda.Stream()
+    s.wait_stream(stream)
+    with torch.cuda.stream(s):
+        r.preprocess(g, s)
+        r.bin_sort(s, sync=False)
+        r.render_fwd(s)
+    stream.wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        r.preprocess(g, s)
+        r.bin_sort(s, sync=False)
+        r.render_fwd(s)
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    K = max(3, args.steps // 4)
+    ms_graph = timed(graph.replay, K, flush, stream)
+    # the same views one by one, each with its own plan (sized beforehand)
+    singles = []
+    for c in cams:
+        rs = Rasterizer(g, [c], Config())
+        rs.forward(g)
+        singles.append(rs)
+    torch.cuda.synchronize()
+
+    def sequential():
+        for rs in singles:
+            rs.forward(g)
+
+    ms_seq = timed(sequential, K, flush, stream)
+    res = {"views": n_views, "resolutions": "640x360/1280x720/1920x1080 cycling", "keys": keys,
+           "batched_graph_fwd_views_per_s": round(n_views / (ms_graph / 1e3), 2),
+           "sequential_fwd_views_per_s": round(n_views / (ms_seq / 1e3), 2),
+           "batched_ms": round(ms_graph, 3), "sequential_ms": round(ms_seq, 3),
+           "launch": {"fwd_pixels_per_thread": r.config.fwd_pixels_per_thread}}
+    del singles, r, graph
+    torch.cuda.empty_cache()
     return res
 
 
@@ -362,6 +438,10 @@ def e2e(args, sc, cam, up, dev, world):
             t.copy_(grads[k], non_blocking=True)
         torch.cuda.current_stream().synchronize()
 
+    for k in ("means", "log_scales", "quats", "opacity_logits", "skew", "sh"):
+        getattr(g, k).copy_(getattr(host, k))
+    d_img.copy_(up_h)
+    r.autotune(g, d_img)
     for _ in range(3):
         one()
     K = max(5, args.steps // 2)

@@ -106,9 +106,11 @@ typedef struct sr_config {
   float near_z;               /* cull camera z <= near_z (0.2) */
   float bg[3];                /* background colour */
   int32_t antialias_comp;     /* 1: d = o * sqrt(det Sigma' / det(Sigma' + sI)); 0: d = o */
-  int32_t render_blocks_per_sm; /* 0 = auto; launch shape of the render kernels */
+  int32_t render_blocks_per_sm; /* reserved for the render launch shape (0) */
   int32_t sort_spin_limit;    /* 0 = auto; bound on each look-back wait of the sort */
-  int32_t reserved_[4];
+  int32_t fwd_pixels_per_thread; /* 1, 2 or 4 (0 = 2): pixels each thread of sr_render_fwd owns */
+  int32_t bwd_pixels_per_thread; /* 1, 2 or 4 (0 = 2): pixels each thread of sr_render_bwd owns */
+  int32_t reserved_[2];
 } sr_config;
 
 /* Gradients of the loss w.r.t. the attributes, FP32, device, caller-owned,
@@ -254,6 +256,30 @@ sr_status sr_sort_keys_noalloc(const uint64_t* keys_in, const uint32_t* vals_in,
 uint64_t sr_kernel_launches(void);
 sr_status sr_frame_counters(const sr_plan* plan, void* ws, uint64_t* pairs_tested, uint64_t* pairs_blended,
                             void* stream);
+
+/* The two halves of sr_render_bwd, for callers that time or overlap them:
+ * sr_render_bwd_composite runs the reverse replay (Alg. 2) and leaves the
+ * per-(view, Gaussian) gradients of the 2D quantities (mu_2, conic,
+ * projected skew, opacity terms, colour) in the workspace;
+ * sr_render_bwd_project then applies the chain rule through the projection
+ * (Appendix "Backward Pass", deferred to 3DGS in the paper) into *out.
+ * Same arguments and rules as sr_render_bwd. */
+sr_status sr_render_bwd_composite(const sr_plan* plan, const sr_config* cfg, void* ws, const float* d_images,
+                                  const float* t_final, const uint32_t* n_contrib, void* stream);
+sr_status sr_render_bwd_project(const sr_plan* plan, const sr_gaussians* g, const sr_camera* cams_dev,
+                                const sr_config* cfg, void* ws, const sr_grads* out, void* stream);
+
+/* Self-test of the sort's bounded waits (failure detection without a GPU
+ * fault): runs one radix pass over zero keys in the workspace in which no
+ * block takes partition 0, so the block of partition 1 waits for a
+ * look-back word that is never written.  The wait gives up after spin_limit
+ * polls, flags the status word and lets the pass finish.  Synchronises the
+ * stream; returns SR_ERR_TIMEOUT (the expected outcome) with the partition
+ * that gave up in *gave_up_partition, SR_OK if no wait gave up.  Clobbers
+ * the workspace's sort buffers and status word: call it between frames.
+ * Needs key_capacity >= 8192 and at least one tile pass (>1 tile). */
+sr_status sr_selftest_bounded_wait(const sr_plan* plan, void* ws, int32_t spin_limit, int64_t* gave_up_partition,
+                                   void* stream);
 
 /* Synchronise the stream and read the device status word.  Returns SR_OK,
  * SR_ERR_CAPACITY or SR_ERR_TIMEOUT (first set bit), clears the word, and

@@ -46,6 +46,8 @@ sr_status check_config(const sr_config* c) {
   if (c->antialias_comp && !(c->dilation > 0.0f)) return SR_ERR_INVALID;
   for (int k = 0; k < 3; ++k)
     if (!std::isfinite(c->bg[k])) return SR_ERR_INVALID;
+  for (int px : {c->fwd_pixels_per_thread, c->bwd_pixels_per_thread})
+    if (px != 0 && px != 1 && px != 2 && px != 4) return SR_ERR_INVALID;
   return SR_OK;
 }
 
@@ -283,6 +285,8 @@ static RenderArgs render_args(const sr_plan* p, const sr_config* cfg, void* ws) 
   r.n_contrib = nullptr;
   r.d_images = nullptr;
   r.d2 = w.d2;
+  r.px_fwd = cfg->fwd_pixels_per_thread > 0 ? cfg->fwd_pixels_per_thread : 2;
+  r.px_bwd = cfg->bwd_pixels_per_thread > 0 ? cfg->bwd_pixels_per_thread : 2;
   return r;
 }
 
@@ -299,6 +303,44 @@ sr_status sr_render_fwd(const sr_plan* p, const sr_config* cfg, void* ws, float*
   return from_cuda(launch_render_fwd(r, p->render_mode, p->total_tiles, static_cast<cudaStream_t>(stream)));
 }
 
+sr_status sr_render_bwd_composite(const sr_plan* p, const sr_config* cfg, void* ws, const float* d_images,
+                                  const float* t_final, const uint32_t* n_contrib, void* stream) {
+  sr_status s = check_plan(p, ws);
+  if (s != SR_OK) return s;
+  if ((s = check_config(cfg)) != SR_OK) return s;
+  if (!d_images || !t_final || !n_contrib) return SR_ERR_INVALID;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Ws w = ws_ptrs(*p, ws);
+  cudaError_t e = cudaMemsetAsync(w.d2, 0, sizeof(float) * kD2Stride * (size_t)(p->n * p->n_views), st);
+  if (e != cudaSuccess) return SR_ERR_CUDA;
+  RenderArgs r = render_args(p, cfg, ws);
+  r.t_final = const_cast<float*>(t_final);
+  r.n_contrib = const_cast<uint32_t*>(n_contrib);
+  r.d_images = d_images;
+  return from_cuda(launch_render_bwd(r, p->render_mode, p->total_tiles, st));
+}
+
+sr_status sr_render_bwd_project(const sr_plan* p, const sr_gaussians* g, const sr_camera* cams_dev,
+                                const sr_config* cfg, void* ws, const sr_grads* out, void* stream) {
+  sr_status s = check_plan(p, ws);
+  if (s != SR_OK) return s;
+  if ((s = check_config(cfg)) != SR_OK) return s;
+  if ((s = check_gaussians(p, g, true)) != SR_OK) return s;
+  if (!cams_dev || !out) return SR_ERR_INVALID;
+  if (p->n > 0 && (!out->means || !out->log_scales || !out->quats || !out->opacity_logits || !out->skew || !out->sh))
+    return SR_ERR_INVALID;
+  if (p->has_split && p->n > 0 && !out->split_dir) return SR_ERR_INVALID;
+  if (p->n > 0 && !aligned16(out->quats)) return SR_ERR_INVALID;
+  BwdArgs b;
+  b.g = *g;
+  b.cams = cams_dev;
+  b.n_views = p->n_views;
+  b.cfg = to_dev(*cfg);
+  b.ws = ws_ptrs(*p, ws);
+  b.out = *out;
+  return from_cuda(launch_preprocess_bwd(b, static_cast<cudaStream_t>(stream), device_sms()));
+}
+
 sr_status sr_render_bwd(const sr_plan* p, const sr_gaussians* g, const sr_camera* cams_dev, const sr_config* cfg,
                         void* ws, const float* d_images, const float* t_final, const uint32_t* n_contrib,
                         const sr_grads* out, void* stream) {
@@ -311,24 +353,26 @@ sr_status sr_render_bwd(const sr_plan* p, const sr_gaussians* g, const sr_camera
     return SR_ERR_INVALID;
   if (p->has_split && p->n > 0 && !out->split_dir) return SR_ERR_INVALID;
   if (p->n > 0 && !aligned16(out->quats)) return SR_ERR_INVALID;
+  s = sr_render_bwd_composite(p, cfg, ws, d_images, t_final, n_contrib, stream);
+  if (s != SR_OK) return s;
+  return sr_render_bwd_project(p, g, cams_dev, cfg, ws, out, stream);
+}
+
+sr_status sr_selftest_bounded_wait(const sr_plan* p, void* ws, int32_t spin_limit, int64_t* gave_up_partition,
+                                   void* stream) {
+  sr_status s = check_plan(p, ws);
+  if (s != SR_OK) return s;
+  if (spin_limit < 1 || p->key_capacity < 2 * kSortPart || p->sort_passes < 1) return SR_ERR_INVALID;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const Ws w = ws_ptrs(*p, ws);
-  cudaError_t e = cudaMemsetAsync(w.d2, 0, sizeof(float) * kD2Stride * (size_t)(p->n * p->n_views), st);
-  if (e != cudaSuccess) return SR_ERR_CUDA;
-  RenderArgs r = render_args(p, cfg, ws);
-  r.t_final = const_cast<float*>(t_final);
-  r.n_contrib = const_cast<uint32_t*>(n_contrib);
-  r.d_images = d_images;
-  e = launch_render_bwd(r, p->render_mode, p->total_tiles, st);
-  if (e != cudaSuccess) return SR_ERR_CUDA;
-  BwdArgs b;
-  b.g = *g;
-  b.cams = cams_dev;
-  b.n_views = p->n_views;
-  b.cfg = to_dev(*cfg);
-  b.ws = w;
-  b.out = *out;
-  return from_cuda(launch_preprocess_bwd(b, st, device_sms()));
+  if (launch_selftest_bounded_wait(w, (unsigned long long)p->key_capacity, spin_limit, st) != cudaSuccess)
+    return SR_ERR_CUDA;
+  Status h;
+  if (cudaMemcpyAsync(&h, w.status, sizeof(Status), cudaMemcpyDeviceToHost, st) != cudaSuccess) return SR_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SR_ERR_CUDA;
+  if (cudaMemsetAsync(&w.status->flags, 0, sizeof(uint32_t), st) != cudaSuccess) return SR_ERR_CUDA;
+  if (gave_up_partition) *gave_up_partition = h.timeout_where ? (int64_t)((h.timeout_where - 1) % 1000000) : -1;
+  return (h.flags & kStatusTimeout) ? SR_ERR_TIMEOUT : SR_OK;
 }
 
 uint64_t sr_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }

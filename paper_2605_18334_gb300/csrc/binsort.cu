@@ -529,6 +529,37 @@ cudaError_t launch_bin_phase2(const BinArgs& a, const int* run, long long keys_k
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Bounded-wait self-test: one onesweep pass over zero keys in which partition
+// ticket 0 is skipped, so partition 1 waits for a look-back word that nothing
+// writes.  The wait must give up after spin_limit polls, raise the timeout
+// flag and still publish, so the pass ends and the context stays usable.
+// ---------------------------------------------------------------------------
+__global__ void selftest_setup_kernel(Status* st, unsigned long long n, uint32_t* digit_base) {
+  if (threadIdx.x == 0) {
+    st->keys_needed = n;
+    st->part_counter[kMaxPasses] = 1u;  // nobody takes partition 0
+  }
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) digit_base[d] = d == 0 ? 0u : (uint32_t)n;
+}
+
+cudaError_t launch_selftest_bounded_wait(const Ws& ws, unsigned long long cap, int spin_limit, cudaStream_t st) {
+  const unsigned long long n = 4ull * kSortPart < cap ? 4ull * kSortPart : cap;
+  const unsigned long long parts = (n + kSortPart - 1) / kSortPart;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ws.status, 0, sizeof(Status), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(ws.keys[0], 0, sizeof(uint32_t) * n, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(ws.lookback, 0, sizeof(unsigned long long) * 256 * parts, st)) != cudaSuccess) return e;
+  uint32_t* th = ws.hist + kMaxPasses * 256;
+  selftest_setup_kernel<<<1, 256, 0, st>>>(ws.status, n, th);
+  uint32_t* const kb[2] = {ws.keys[1], ws.keys[0]};
+  uint32_t* const vb[2] = {ws.vals[1], ws.vals[0]};
+  count_launches(1);
+  run_passes<uint32_t>(ws.keys[0], nullptr, kb, vb, th, ws.lookback, ws.status->part_counter + kMaxPasses, nullptr,
+                       n, parts, 1, nullptr, ws.status, spin_limit, st);
+  return cudaGetLastError();
+}
+
 }  // namespace sr
 
 // ---------------------------------------------------------------------------

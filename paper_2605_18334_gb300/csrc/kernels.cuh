@@ -47,12 +47,15 @@ struct RenderArgs {     // forward and backward composite
   uint32_t* n_contrib;
   const float* d_images;
   float* d2;
+  int px_fwd;           // pixels per thread (1, 2, 4)
+  int px_bwd;
 };
 
 cudaError_t launch_preprocess_fwd(const PreArgs& a, cudaStream_t st, int sms);
 cudaError_t launch_preprocess_bwd(const BwdArgs& a, cudaStream_t st, int sms);
 cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms);
 cudaError_t launch_bin_phase2(const BinArgs& a, const int* run, long long keys_known, cudaStream_t st);
+cudaError_t launch_selftest_bounded_wait(const Ws& ws, unsigned long long cap, int spin_limit, cudaStream_t st);
 cudaError_t launch_render_fwd(const RenderArgs& a, int mode, int64_t total_tiles, cudaStream_t st);
 cudaError_t launch_render_bwd(const RenderArgs& a, int mode, int64_t total_tiles, cudaStream_t st);
 

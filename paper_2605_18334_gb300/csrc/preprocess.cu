@@ -469,6 +469,7 @@ __global__ void __launch_bounds__(kPreThreads, 4) preprocess_bwd_kernel(BwdArgs 
       Proj P;
       project(A, c, a.cfg, two, has_split, P);
       g_abs += sqrtf(gd[G_MX] * gd[G_MX] + gd[G_MY] * gd[G_MY]);
+      float gmu_v[3];  // this view's dL/dmu
 
       // colour -> SH coefficients and view direction
       float Y[16];
@@ -493,7 +494,7 @@ __global__ void __launch_bounds__(kPreThreads, 4) preprocess_bwd_kernel(BwdArgs 
       {
         const float dd = P.dir[0] * gdir[0] + P.dir[1] * gdir[1] + P.dir[2] * gdir[2];
         const float il = 1.0f / P.dlen;
-        for (int k = 0; k < 3; ++k) g_mu[k] += (gdir[k] - P.dir[k] * dd) * il;
+        for (int k = 0; k < 3; ++k) gmu_v[k] = (gdir[k] - P.dir[k] * dd) * il;
       }
 
       // opacities
@@ -597,8 +598,10 @@ __global__ void __launch_bounds__(kPreThreads, 4) preprocess_bwd_kernel(BwdArgs 
         gty += gtyz * itz;
         gtz -= gtyz * ty * itz2;
       }
-      g_depth += gtz;
-      for (int k = 0; k < 3; ++k) g_mu[k] += W[0 + k] * gtx + W[4 + k] * gty + W[8 + k] * gtz;
+      for (int k = 0; k < 3; ++k) gmu_v[k] += W[0 + k] * gtx + W[4 + k] * gty + W[8 + k] * gtz;
+      for (int k = 0; k < 3; ++k) g_mu[k] += gmu_v[k];
+      // dL/dz of the centre along this camera's axis: (W dL/dmu)_z (Eq. depth_grad)
+      g_depth += W[8] * gmu_v[0] + W[9] * gmu_v[1] + W[10] * gmu_v[2];
     }
     // write (zeros for Gaussians no view touched)
     float* o;

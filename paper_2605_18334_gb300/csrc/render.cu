@@ -1,9 +1,10 @@
 // Per-tile compositing of skew Gaussians: forward (Alg. 1, Eq. color) and
 // the reverse replay that differentiates it (Alg. 2).
 //
-// One 16x16 block per tile, one thread per pixel.  The tile's depth-sorted
-// records are staged into shared memory in batches of 256 (one gathered
-// 64-byte record per thread), then every pixel walks the batch:
+// One block per 16x16 tile; each thread owns PX vertically adjacent pixels
+// of one column, so a warp covers a 16 x 2*PX block.  The tile's depth-sorted
+// records are staged into shared memory in batches of 256 (gathered 64-byte
+// records), then every pixel walks the batch:
 //   alpha = min(alpha_max, o G' (1 + erf z)),  skip if alpha < alpha_min,
 //   stop before the Gaussian whose T' = T (1 - alpha) would fall below t_stop,
 //   C += c alpha T, T = T'.
@@ -11,90 +12,139 @@
 //
 // Backward per pixel from its last blended Gaussian down: T_k = T_{k+1} /
 // (1 - alpha_k), R_{k+1} = colour behind k normalised by T_{k+1} (the
-// background included), dL/dalpha_k = T_k sum_c g_c (c_k,c - R_{k+1},c);
-// per-pair 2D gradients are summed over the warp with shuffles and added to
-// the Gaussian's record with one vector atomic per 4 components.
+// background included), dL/dalpha_k = T_k sum_c g_c (c_k,c - R_{k+1},c).
+// A thread first sums its PX pixels' contributions to a Gaussian, the warp
+// then sums its lanes with a transposing butterfly, warps add into padded
+// shared-memory accumulators, and each block issues one set of vector atomics
+// per Gaussian per batch.
 #include "kernels.cuh"
 
 namespace sr {
 
+constexpr int kBatch = 256;
+
+struct TileCoord {
+  ViewInfo vi;
+  int tx, ty;
+};
+
+__device__ __forceinline__ TileCoord tile_coord(const RenderArgs& a, int64_t tile) {
+  TileCoord t;
+  const int v = view_of_tile(a.views, a.n_views, tile);
+  t.vi = a.views[v];
+  const int lt = (int)(tile - t.vi.tile_base);
+  t.tx = lt % t.vi.tiles_x;
+  t.ty = lt / t.vi.tiles_x;
+  return t;
+}
 
 template <int MODE>
-__global__ void __launch_bounds__(256) render_fwd_kernel(RenderArgs a) {
-  __shared__ float4 s_r0[256], s_r1[256], s_r2[MODE == MODE_PLAIN ? 1 : 256], s_r3[256];
-  const int64_t tile = blockIdx.x;
-  const int v = view_of_tile(a.views, a.n_views, tile);
-  const ViewInfo vi = a.views[v];
-  const int lt = (int)(tile - vi.tile_base);
-  const int tx = lt % vi.tiles_x, ty = lt / vi.tiles_x;
-  const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-  const int py = ty * kTile + (threadIdx.x >> 4);
-  const bool inside = px < vi.width && py < vi.height;
-  const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
-  const uint2 range = a.ranges[tile];
+__device__ __forceinline__ void stage_batch(const RenderArgs& a, const uint32_t* vals, uint32_t start, uint32_t end,
+                                            int nt, float4* s_r0, float4* s_r1, float4* s_r2, float4* s_r3,
+                                            uint32_t* s_id) {
+  for (int q = threadIdx.x; q < kBatch; q += nt) {
+    const uint32_t idx = start + q;
+    if (idx < end) {
+      const uint32_t id = vals[idx];
+      const float4* r = a.rec + 4 * (int64_t)id;
+      if (s_id) s_id[q] = id;
+      s_r0[q] = r[0];
+      s_r1[q] = r[1];
+      if (MODE != MODE_PLAIN) s_r2[q] = r[2];
+      s_r3[q] = r[3];
+    }
+  }
+}
+
+template <int MODE, int PX>
+__global__ void __launch_bounds__(256 / PX) render_fwd_kernel(RenderArgs a) {
+  constexpr int NT = 256 / PX;
+  __shared__ float4 s_r0[kBatch], s_r1[kBatch], s_r2[MODE == MODE_PLAIN ? 1 : kBatch], s_r3[kBatch];
+  const TileCoord tc = tile_coord(a, blockIdx.x);
+  const int px = tc.tx * kTile + (threadIdx.x & (kTile - 1));
+  const int py0 = tc.ty * kTile + (threadIdx.x >> 4) * PX;
+  const float fx = (float)px + 0.5f;
+  const uint2 range = a.ranges[blockIdx.x];
   const uint32_t* vals = a.status->sorted_buf ? a.vals1 : a.vals0;
   const float amin = a.cfg.alpha_min, amax = a.cfg.alpha_max, tstop = a.cfg.t_stop;
 
-  float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-  uint32_t last = 0, tested = 0, blended = 0;
-  bool done = !inside;
-  for (uint32_t start = range.x; start < range.y; start += 256) {
-    if (__syncthreads_count(done) == 256) break;
-    const uint32_t idx = start + threadIdx.x;
-    if (idx < range.y) {
-      const float4* r = a.rec + 4 * (int64_t)vals[idx];
-      s_r0[threadIdx.x] = r[0];
-      s_r1[threadIdx.x] = r[1];
-      if (MODE != MODE_PLAIN) s_r2[threadIdx.x] = r[2];
-      s_r3[threadIdx.x] = r[3];
-    }
-    __syncthreads();
-    const int cnt = (int)min(256u, range.y - start);
-    if (!done) {
-      int j = 0;
-      for (; j < cnt; ++j) {
-        const float4 r3 = s_r3[j];
-        PairEval e;
-        if (!eval_pair<MODE>(s_r0[j], s_r1[j], MODE == MODE_PLAIN ? s_r0[j] : s_r2[j], r3.w, fx, fy, e)) continue;
-        const float alpha = fminf(e.alpha, amax);
-        if (alpha < amin) continue;
-        const float Tn = __fmaf_rn(-T, alpha, T);
-        if (Tn < tstop) {
-          done = true;
-          ++j;
-          break;
-        }
-        ++blended;
-        const float w = __fmul_rn(alpha, T);
-        C0 = __fmaf_rn(r3.x, w, C0);
-        C1 = __fmaf_rn(r3.y, w, C1);
-        C2 = __fmaf_rn(r3.z, w, C2);
-        T = Tn;
-        last = start + j + 1 - range.x;
-      }
-      tested += j;
-    }
+  float T[PX], C0[PX], C1[PX], C2[PX];
+  uint32_t last[PX], stop[PX];
+  bool done[PX];
+  int active = 0;  // pixels of this thread still compositing
+#pragma unroll
+  for (int p = 0; p < PX; ++p) {
+    T[p] = 1.0f;
+    C0[p] = C1[p] = C2[p] = 0.0f;
+    last[p] = 0;
+    stop[p] = range.y;
+    done[p] = !(px < tc.vi.width && py0 + p < tc.vi.height);
+    active += done[p] ? 0 : 1;
   }
-  // work counters: one atomic per warp
-  unsigned long long t64 = tested, b64 = blended;
+  uint32_t blended = 0;
+  for (uint32_t start = range.x; start < range.y; start += kBatch) {
+    if (__syncthreads_count(active == 0) == NT) break;
+    stage_batch<MODE>(a, vals, start, range.y, NT, s_r0, s_r1, s_r2, s_r3, nullptr);
+    __syncthreads();
+    const int cnt = (int)min((uint32_t)kBatch, range.y - start);
+    if (active) {
+      for (int j = 0; j < cnt; ++j) {
+        const float4 r0 = s_r0[j], r1 = s_r1[j], r3 = s_r3[j];
+        const float4 r2 = MODE == MODE_PLAIN ? r0 : s_r2[j];
+#pragma unroll
+        for (int p = 0; p < PX; ++p) {
+          if (PX > 1 && done[p]) continue;
+          PairEval e;
+          if (!eval_pair<MODE>(r0, r1, r2, r3.w, fx, (float)(py0 + p) + 0.5f, e)) continue;
+          const float alpha = fminf(e.alpha, amax);
+          if (alpha < amin) continue;
+          const float Tn = __fmaf_rn(-T[p], alpha, T[p]);
+          if (Tn < tstop) {
+            done[p] = true;
+            stop[p] = start + j + 1;
+            if (--active == 0) goto batch_done;  // the only exit test, off the hot path
+            continue;
+          }
+          ++blended;
+          const float w = __fmul_rn(alpha, T[p]);
+          C0[p] = __fmaf_rn(r3.x, w, C0[p]);
+          C1[p] = __fmaf_rn(r3.y, w, C1[p]);
+          C2[p] = __fmaf_rn(r3.z, w, C2[p]);
+          T[p] = Tn;
+          last[p] = start + j + 1 - range.x;
+        }
+      }
+    }
+  batch_done:;
+  }
+  // work counters: pairs each pixel evaluated (up to its stop) and blended
+  unsigned long long tested = 0;
+#pragma unroll
+  for (int p = 0; p < PX; ++p)
+    if (px < tc.vi.width && py0 + p < tc.vi.height) tested += stop[p] - range.x;
+  unsigned long long b64 = blended;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    t64 += __shfl_xor_sync(0xffffffffu, t64, o);
+    tested += __shfl_xor_sync(0xffffffffu, tested, o);
     b64 += __shfl_xor_sync(0xffffffffu, b64, o);
   }
-  if ((threadIdx.x & 31) == 0 && t64) {
-    atomicAdd(&a.status->pairs_tested, t64);
+  if ((threadIdx.x & 31) == 0 && tested) {
+    atomicAdd(&a.status->pairs_tested, tested);
     atomicAdd(&a.status->pairs_blended, b64);
   }
-  if (inside) {
-    const int64_t plane = (int64_t)vi.width * vi.height;
-    const int64_t pix = (int64_t)py * vi.width + px;
-    float* img = a.images + vi.image_offset;
-    img[pix] = __fmaf_rn(T, a.cfg.bg[0], C0);
-    img[plane + pix] = __fmaf_rn(T, a.cfg.bg[1], C1);
-    img[2 * plane + pix] = __fmaf_rn(T, a.cfg.bg[2], C2);
-    a.t_final[vi.pixel_offset + pix] = T;
-    a.n_contrib[vi.pixel_offset + pix] = last;
+  const int64_t plane = (int64_t)tc.vi.width * tc.vi.height;
+  float* img = a.images + tc.vi.image_offset;
+#pragma unroll
+  for (int p = 0; p < PX; ++p) {
+    const int py = py0 + p;
+    if (px < tc.vi.width && py < tc.vi.height) {
+      const int64_t pix = (int64_t)py * tc.vi.width + px;
+      img[pix] = __fmaf_rn(T[p], a.cfg.bg[0], C0[p]);
+      img[plane + pix] = __fmaf_rn(T[p], a.cfg.bg[1], C1[p]);
+      img[2 * plane + pix] = __fmaf_rn(T[p], a.cfg.bg[2], C2[p]);
+      a.t_final[tc.vi.pixel_offset + pix] = T[p];
+      a.n_contrib[tc.vi.pixel_offset + pix] = last[p];
+    }
   }
 }
 
@@ -138,64 +188,64 @@ __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float 
                : "memory");
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(256) render_bwd_kernel(RenderArgs a) {
-  __shared__ float4 s_r0[256], s_r1[256], s_r2[MODE == MODE_PLAIN ? 1 : 256], s_r3[256];
-  __shared__ uint32_t s_id[256];
+template <int MODE, int PX>
+__global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
+  constexpr int NT = 256 / PX;
+  __shared__ float4 s_r0[kBatch], s_r1[kBatch], s_r2[MODE == MODE_PLAIN ? 1 : kBatch], s_r3[kBatch];
+  __shared__ uint32_t s_id[kBatch];
   // per-batch gradient accumulators, component-major with a padded row so
   // both the warps' adds (16 components of one Gaussian) and the flush (one
   // Gaussian per thread) are free of bank conflicts
-  __shared__ float s_acc[16][257];
+  __shared__ float s_acc[16][kBatch + 1];
   __shared__ uint32_t s_max;
-  const int64_t tile = blockIdx.x;
-  const int v = view_of_tile(a.views, a.n_views, tile);
-  const ViewInfo vi = a.views[v];
-  const int lt = (int)(tile - vi.tile_base);
-  const int tx = lt % vi.tiles_x, ty = lt / vi.tiles_x;
-  const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-  const int py = ty * kTile + (threadIdx.x >> 4);
-  const bool inside = px < vi.width && py < vi.height;
-  const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
-  const uint2 range = a.ranges[tile];
+  const TileCoord tc = tile_coord(a, blockIdx.x);
+  const int px = tc.tx * kTile + (threadIdx.x & (kTile - 1));
+  const int py0 = tc.ty * kTile + (threadIdx.x >> 4) * PX;
+  const float fx = (float)px + 0.5f;
+  const uint2 range = a.ranges[blockIdx.x];
   const uint32_t* vals = a.status->sorted_buf ? a.vals1 : a.vals0;
   const float amin = a.cfg.alpha_min, amax = a.cfg.alpha_max;
   const int lane = threadIdx.x & 31;
+  const int64_t plane = (int64_t)tc.vi.width * tc.vi.height;
+  const float* gimg = a.d_images + tc.vi.image_offset;
 
-  float T = 1.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
-  uint32_t my_last = 0;
-  if (inside) {
-    const int64_t plane = (int64_t)vi.width * vi.height;
-    const int64_t pix = (int64_t)py * vi.width + px;
-    const float* gi = a.d_images + vi.image_offset;
-    g0 = gi[pix];
-    g1 = gi[plane + pix];
-    g2 = gi[2 * plane + pix];
-    T = a.t_final[vi.pixel_offset + pix];
-    my_last = a.n_contrib[vi.pixel_offset + pix];
+  float T[PX], g0[PX], g1[PX], g2[PX], R0[PX], R1[PX], R2[PX];
+  uint32_t my_end[PX];
+  uint32_t my_max = 0;
+#pragma unroll
+  for (int p = 0; p < PX; ++p) {
+    const int py = py0 + p;
+    T[p] = 1.0f;
+    g0[p] = g1[p] = g2[p] = 0.0f;
+    my_end[p] = range.x;
+    R0[p] = a.cfg.bg[0];
+    R1[p] = a.cfg.bg[1];
+    R2[p] = a.cfg.bg[2];
+    if (px < tc.vi.width && py < tc.vi.height) {
+      const int64_t pix = (int64_t)py * tc.vi.width + px;
+      g0[p] = gimg[pix];
+      g1[p] = gimg[plane + pix];
+      g2[p] = gimg[2 * plane + pix];
+      T[p] = a.t_final[tc.vi.pixel_offset + pix];
+      const uint32_t nc = a.n_contrib[tc.vi.pixel_offset + pix];
+      my_end[p] = min(range.y, range.x + nc);
+      my_max = max(my_max, nc);
+    }
   }
-  float R0 = a.cfg.bg[0], R1 = a.cfg.bg[1], R2 = a.cfg.bg[2];
   if (threadIdx.x == 0) s_max = 0;
   __syncthreads();
-  if (my_last) atomicMax(&s_max, my_last);
+  if (my_max) atomicMax(&s_max, my_max);
   __syncthreads();
   const uint32_t end = min(range.y, range.x + s_max);
-  const uint32_t my_end = min(range.y, range.x + my_last);
 
   for (uint32_t bend = end; bend > range.x;) {
-    const uint32_t bstart = bend - range.x > 256u ? bend - 256u : range.x;
-    const uint32_t idx = bstart + threadIdx.x;
+    const uint32_t bstart = bend - range.x > (uint32_t)kBatch ? bend - kBatch : range.x;
     __syncthreads();  // previous batch fully consumed
-    if (idx < bend) {
-      const uint32_t id = vals[idx];
-      const float4* r = a.rec + 4 * (int64_t)id;
-      s_id[threadIdx.x] = id;
-      s_r0[threadIdx.x] = r[0];
-      s_r1[threadIdx.x] = r[1];
-      if (MODE != MODE_PLAIN) s_r2[threadIdx.x] = r[2];
-      s_r3[threadIdx.x] = r[3];
-    }
+    stage_batch<MODE>(a, vals, bstart, bend, NT, s_r0, s_r1, s_r2, s_r3, s_id);
+    for (int q = threadIdx.x; q < kBatch; q += NT) {
 #pragma unroll
-    for (int k = 0; k < 16; ++k) s_acc[k][threadIdx.x] = 0.0f;
+      for (int k = 0; k < 16; ++k) s_acc[k][q] = 0.0f;
+    }
     __syncthreads();
     for (int j = (int)(bend - bstart) - 1; j >= 0; --j) {
       const uint32_t pos = bstart + j;
@@ -203,50 +253,50 @@ __global__ void __launch_bounds__(256) render_bwd_kernel(RenderArgs a) {
 #pragma unroll
       for (int k = 0; k < 16; ++k) gr[k] = 0.0f;
       bool contrib = false;
-      if (pos < my_end) {
-        const float4 r0 = s_r0[j], r1 = s_r1[j], r3 = s_r3[j];
-        const float4 r2 = MODE == MODE_PLAIN ? r0 : s_r2[j];
+      const float4 r0 = s_r0[j], r1 = s_r1[j], r3 = s_r3[j];
+      const float4 r2 = MODE == MODE_PLAIN ? r0 : s_r2[j];
+      // natural-unit conic from the log2-prescaled record
+      const float a_ = -2.0f * kLn2 * r0.z, b_ = -kLn2 * r0.w, c_ = -2.0f * kLn2 * r1.x;
+#pragma unroll
+      for (int p = 0; p < PX; ++p) {
+        if (pos >= my_end[p]) continue;
         PairEval e;
-        if (eval_pair<MODE>(r0, r1, r2, r3.w, fx, fy, e)) {
-          const float alpha = fminf(e.alpha, amax);
-          if (alpha >= amin) {
-            contrib = true;
-            const float one_m = 1.0f - alpha;
-            T = T / one_m;  // T_k
-            const float w = alpha * T;
-            gr[G_R] = w * g0;
-            gr[G_G] = w * g1;
-            gr[G_BL] = w * g2;
-            const float dLda = T * (g0 * (r3.x - R0) + g1 * (r3.y - R1) + g2 * (r3.z - R2));
-            R0 = alpha * r3.x + one_m * R0;
-            R1 = alpha * r3.y + one_m * R1;
-            R2 = alpha * r3.z + one_m * R2;
-            if (e.alpha <= amax) {
-              // alpha = o G E;  natural-unit conic a = -2 ln2 A2, b = -ln2 B2, c = -2 ln2 C2
-              const float a_ = -2.0f * kLn2 * r0.z, b_ = -kLn2 * r0.w, c_ = -2.0f * kLn2 * r1.x;
-              const float S = e.G * e.E;           // skew kernel G' (1 + erf z)
-              const float gS = dLda * e.o * S;     // dL/dlog(G) path factor
-              const float gz = dLda * e.o * e.G * kTwoOverSqrtPi * e.ez;  // dL/dz
-              float gdx = -gS * (a_ * e.dx + b_ * e.dy) + gz * r1.y;
-              float gdy = -gS * (b_ * e.dx + c_ * e.dy) + gz * r1.z;
-              gr[G_M] = dLda * S;
-              gr[G_A] = -0.5f * gS * e.dx * e.dx;
-              gr[G_B] = -gS * e.dx * e.dy;
-              gr[G_C] = -0.5f * gS * e.dy * e.dy;
-              gr[G_BX] = gz * e.dx * kInvSqrt2;
-              gr[G_BY] = gz * e.dy * kInvSqrt2;
-              if (MODE != MODE_PLAIN) {
-                gr[G_H] = dLda * e.eu * S;
-                const float gzu = dLda * r2.x * S * kTwoOverSqrtPi * e.ezu;
-                gdx += gzu * r2.y;
-                gdy += gzu * r2.z;
-                gr[G_UX] = gzu * e.dx * kInvSqrt2;
-                gr[G_UY] = gzu * e.dy * kInvSqrt2;
-              }
-              gr[G_MX] = -gdx;
-              gr[G_MY] = -gdy;
-            }
+        if (!eval_pair<MODE>(r0, r1, r2, r3.w, fx, (float)(py0 + p) + 0.5f, e)) continue;
+        const float alpha = fminf(e.alpha, amax);
+        if (alpha < amin) continue;
+        contrib = true;
+        const float one_m = 1.0f - alpha;
+        T[p] = T[p] / one_m;  // T_k
+        const float w = alpha * T[p];
+        gr[G_R] += w * g0[p];
+        gr[G_G] += w * g1[p];
+        gr[G_BL] += w * g2[p];
+        const float dLda = T[p] * (g0[p] * (r3.x - R0[p]) + g1[p] * (r3.y - R1[p]) + g2[p] * (r3.z - R2[p]));
+        R0[p] = alpha * r3.x + one_m * R0[p];
+        R1[p] = alpha * r3.y + one_m * R1[p];
+        R2[p] = alpha * r3.z + one_m * R2[p];
+        if (e.alpha <= amax) {  // the clamp has zero derivative
+          const float S = e.G * e.E;           // skew kernel G' (1 + erf z)
+          const float gS = dLda * e.o * S;
+          const float gz = dLda * e.o * e.G * kTwoOverSqrtPi * e.ez;  // dL/dz
+          float gdx = -gS * (a_ * e.dx + b_ * e.dy) + gz * r1.y;
+          float gdy = -gS * (b_ * e.dx + c_ * e.dy) + gz * r1.z;
+          gr[G_M] += dLda * S;
+          gr[G_A] += -0.5f * gS * e.dx * e.dx;
+          gr[G_B] += -gS * e.dx * e.dy;
+          gr[G_C] += -0.5f * gS * e.dy * e.dy;
+          gr[G_BX] += gz * e.dx * kInvSqrt2;
+          gr[G_BY] += gz * e.dy * kInvSqrt2;
+          if (MODE != MODE_PLAIN) {
+            gr[G_H] += dLda * e.eu * S;
+            const float gzu = dLda * r2.x * S * kTwoOverSqrtPi * e.ezu;
+            gdx += gzu * r2.y;
+            gdy += gzu * r2.z;
+            gr[G_UX] += gzu * e.dx * kInvSqrt2;
+            gr[G_UY] += gzu * e.dy * kInvSqrt2;
           }
+          gr[G_MX] -= gdx;
+          gr[G_MY] -= gdy;
         }
       }
       if (__any_sync(0xffffffffu, contrib)) {
@@ -257,27 +307,43 @@ __global__ void __launch_bounds__(256) render_bwd_kernel(RenderArgs a) {
     __syncthreads();
     // one set of vector atomics per Gaussian per batch
     const int cnt = (int)(bend - bstart);
-    if ((int)threadIdx.x < cnt) {
+    for (int q = threadIdx.x; q < cnt; q += NT) {
       float c[16];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) c[k] = s_acc[k][threadIdx.x];
-      float* dst = a.d2 + kD2Stride * (int64_t)s_id[threadIdx.x];
+      for (int k = 0; k < 16; ++k) c[k] = s_acc[k][q];
+      float* dst = a.d2 + kD2Stride * (int64_t)s_id[q];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (c[4 * q] != 0.0f || c[4 * q + 1] != 0.0f || c[4 * q + 2] != 0.0f || c[4 * q + 3] != 0.0f)
-          red_add_v4(dst + 4 * q, c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]);
+      for (int k = 0; k < 4; ++k)
+        if (c[4 * k] != 0.0f || c[4 * k + 1] != 0.0f || c[4 * k + 2] != 0.0f || c[4 * k + 3] != 0.0f)
+          red_add_v4(dst + 4 * k, c[4 * k], c[4 * k + 1], c[4 * k + 2], c[4 * k + 3]);
     }
     bend = bstart;
   }
 }
 
 // ---------------------------------------------------------------------------
+template <int PX>
+static void launch_fwd_px(const RenderArgs& a, int mode, unsigned grid, cudaStream_t st) {
+  if (mode == MODE_PLAIN) render_fwd_kernel<MODE_PLAIN, PX><<<grid, 256 / PX, 0, st>>>(a);
+  else if (mode == MODE_TWO) render_fwd_kernel<MODE_TWO, PX><<<grid, 256 / PX, 0, st>>>(a);
+  else render_fwd_kernel<MODE_SPLIT, PX><<<grid, 256 / PX, 0, st>>>(a);
+}
+
+template <int PX>
+static void launch_bwd_px(const RenderArgs& a, int mode, unsigned grid, cudaStream_t st) {
+  if (mode == MODE_PLAIN) render_bwd_kernel<MODE_PLAIN, PX><<<grid, 256 / PX, 0, st>>>(a);
+  else if (mode == MODE_TWO) render_bwd_kernel<MODE_TWO, PX><<<grid, 256 / PX, 0, st>>>(a);
+  else render_bwd_kernel<MODE_SPLIT, PX><<<grid, 256 / PX, 0, st>>>(a);
+}
+
 cudaError_t launch_render_fwd(const RenderArgs& a, int mode, int64_t total_tiles, cudaStream_t st) {
   if (total_tiles == 0) return cudaSuccess;
   const unsigned grid = (unsigned)total_tiles;
-  if (mode == MODE_PLAIN) render_fwd_kernel<MODE_PLAIN><<<grid, 256, 0, st>>>(a);
-  else if (mode == MODE_TWO) render_fwd_kernel<MODE_TWO><<<grid, 256, 0, st>>>(a);
-  else render_fwd_kernel<MODE_SPLIT><<<grid, 256, 0, st>>>(a);
+  switch (a.px_fwd) {
+    case 1: launch_fwd_px<1>(a, mode, grid, st); break;
+    case 4: launch_fwd_px<4>(a, mode, grid, st); break;
+    default: launch_fwd_px<2>(a, mode, grid, st); break;
+  }
   count_launches(1);
   return cudaGetLastError();
 }
@@ -285,9 +351,11 @@ cudaError_t launch_render_fwd(const RenderArgs& a, int mode, int64_t total_tiles
 cudaError_t launch_render_bwd(const RenderArgs& a, int mode, int64_t total_tiles, cudaStream_t st) {
   if (total_tiles == 0) return cudaSuccess;
   const unsigned grid = (unsigned)total_tiles;
-  if (mode == MODE_PLAIN) render_bwd_kernel<MODE_PLAIN><<<grid, 256, 0, st>>>(a);
-  else if (mode == MODE_TWO) render_bwd_kernel<MODE_TWO><<<grid, 256, 0, st>>>(a);
-  else render_bwd_kernel<MODE_SPLIT><<<grid, 256, 0, st>>>(a);
+  switch (a.px_bwd) {
+    case 1: launch_bwd_px<1>(a, mode, grid, st); break;
+    case 4: launch_bwd_px<4>(a, mode, grid, st); break;
+    default: launch_bwd_px<2>(a, mode, grid, st); break;
+  }
   count_launches(1);
   return cudaGetLastError();
 }

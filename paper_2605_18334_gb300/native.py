@@ -21,7 +21,8 @@ SR_F32, SR_BF16, SR_F16 = 0, 1, 2
 
 EXPORTS = ["sr_abi_version", "sr_status_string", "sr_config_default", "sr_camera_from_gl", "sr_plan_init",
            "sr_workspace_size", "sr_preprocess", "sr_bin_sort", "sr_render_fwd", "sr_render_bwd", "sr_read_status",
-           "sr_kernel_launches", "sr_frame_counters", "sr_sort_keys_noalloc"]
+           "sr_kernel_launches", "sr_frame_counters", "sr_sort_keys_noalloc", "sr_render_bwd_composite",
+           "sr_render_bwd_project", "sr_selftest_bounded_wait"]
 
 
 class sr_gaussians(C.Structure):
@@ -41,7 +42,8 @@ class sr_config(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("alpha_min", C.c_float), ("alpha_max", C.c_float),
                 ("t_stop", C.c_float), ("dilation", C.c_float), ("fov_clamp", C.c_float), ("near_z", C.c_float),
                 ("bg", C.c_float * 3), ("antialias_comp", C.c_int32), ("render_blocks_per_sm", C.c_int32),
-                ("sort_spin_limit", C.c_int32), ("reserved_", C.c_int32 * 4)]
+                ("sort_spin_limit", C.c_int32), ("fwd_pixels_per_thread", C.c_int32),
+                ("bwd_pixels_per_thread", C.c_int32), ("reserved_", C.c_int32 * 2)]
 
 
 class sr_grads(C.Structure):
@@ -106,12 +108,19 @@ def load(build_if_missing: bool = True):
         lib.sr_render_bwd.argtypes = [P(sr_plan), P(sr_gaussians), C.c_void_p, P(sr_config), C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p, P(sr_grads), C.c_void_p]
         lib.sr_read_status.argtypes = [P(sr_plan), C.c_void_p, P(C.c_int64), C.c_void_p]
+        lib.sr_render_bwd_composite.argtypes = [P(sr_plan), P(sr_config), C.c_void_p, C.c_void_p, C.c_void_p,
+                                                C.c_void_p, C.c_void_p]
+        lib.sr_render_bwd_project.argtypes = [P(sr_plan), P(sr_gaussians), C.c_void_p, P(sr_config), C.c_void_p,
+                                              P(sr_grads), C.c_void_p]
+        lib.sr_selftest_bounded_wait.argtypes = [P(sr_plan), C.c_void_p, C.c_int32, P(C.c_int64), C.c_void_p]
+        lib.sr_selftest_bounded_wait.restype = C.c_int
         lib.sr_kernel_launches.restype = C.c_uint64
         lib.sr_kernel_launches.argtypes = []
         lib.sr_frame_counters.argtypes = [P(sr_plan), C.c_void_p, P(C.c_uint64), P(C.c_uint64), C.c_void_p]
         lib.sr_frame_counters.restype = C.c_int
         for name in ("sr_config_default", "sr_camera_from_gl", "sr_plan_init", "sr_preprocess", "sr_bin_sort",
-                     "sr_render_fwd", "sr_render_bwd", "sr_read_status"):
+                     "sr_render_fwd", "sr_render_bwd", "sr_read_status", "sr_render_bwd_composite",
+                     "sr_render_bwd_project"):
             getattr(lib, name).restype = C.c_int
         if lib.sr_abi_version() != SR_ABI_VERSION:
             raise RuntimeError("libskewraster ABI version mismatch")
@@ -187,6 +196,27 @@ def sr_render_bwd(plan, g, cams_dev_ptr: int, cfg, ws_ptr: int, d_images_ptr: in
                                                 C.c_void_p(ws_ptr), C.c_void_p(d_images_ptr),
                                                 C.c_void_p(t_final_ptr), C.c_void_p(n_contrib_ptr),
                                                 C.byref(grads), C.c_void_p(stream)))
+
+
+def sr_render_bwd_composite(plan, cfg, ws_ptr: int, d_images_ptr: int, t_final_ptr: int, n_contrib_ptr: int,
+                            stream: int) -> None:
+    check("sr_render_bwd_composite", load().sr_render_bwd_composite(
+        C.byref(plan), C.byref(cfg), C.c_void_p(ws_ptr), C.c_void_p(d_images_ptr), C.c_void_p(t_final_ptr),
+        C.c_void_p(n_contrib_ptr), C.c_void_p(stream)))
+
+
+def sr_render_bwd_project(plan, g, cams_dev_ptr: int, cfg, ws_ptr: int, grads, stream: int) -> None:
+    check("sr_render_bwd_project", load().sr_render_bwd_project(
+        C.byref(plan), C.byref(g), C.c_void_p(cams_dev_ptr), C.byref(cfg), C.c_void_p(ws_ptr), C.byref(grads),
+        C.c_void_p(stream)))
+
+
+def sr_selftest_bounded_wait(plan, ws_ptr: int, spin_limit: int, stream: int):
+    """Returns (status, partition that gave up or -1)."""
+    part = C.c_int64(-2)
+    s = load().sr_selftest_bounded_wait(C.byref(plan), C.c_void_p(ws_ptr), int(spin_limit), C.byref(part),
+                                        C.c_void_p(stream))
+    return s, int(part.value)
 
 
 def sr_kernel_launches() -> int:

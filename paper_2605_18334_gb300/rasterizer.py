@@ -35,6 +35,8 @@ class Config:
     bg: tuple = (0.0, 0.0, 0.0)
     antialias_comp: bool = True
     sort_spin_limit: int = 0
+    fwd_pixels_per_thread: int = 0   # 0: library default (2)
+    bwd_pixels_per_thread: int = 0
 
     def to_c(self) -> N.sr_config:
         c = N.sr_config()
@@ -45,6 +47,8 @@ class Config:
             c.bg[k] = float(self.bg[k])
         c.antialias_comp = 1 if self.antialias_comp else 0
         c.sort_spin_limit = int(self.sort_spin_limit)
+        c.fwd_pixels_per_thread = int(self.fwd_pixels_per_thread)
+        c.bwd_pixels_per_thread = int(self.bwd_pixels_per_thread)
         return c
 
 
@@ -178,8 +182,37 @@ class Rasterizer:
         self.render_fwd(stream)
         return self.images
 
+    def backward_composite(self, d_images: torch.Tensor, stream=None):
+        """Reverse replay of the last forward (2D gradients stay in the workspace)."""
+        if d_images.dtype != torch.float32 or not d_images.is_contiguous() or d_images.numel() != self.images.numel():
+            raise ValueError("d_images must be a contiguous float32 tensor shaped like the image buffer")
+        N.sr_render_bwd_composite(self.plan, self.cfg_c, self.ws.data_ptr(), d_images.data_ptr(),
+                                  self.t_final.data_ptr(), self.n_contrib.data_ptr(), _stream_ptr(stream))
+
+    def backward_project(self, g: Gaussians, stream=None, want_stats: bool = False) -> dict:
+        """Chain rule from the workspace's 2D gradients to every attribute (FP32)."""
+        dev = self.device
+        n = g.n
+        out = dict(means=torch.empty(n, 3, device=dev), log_scales=torch.empty(n, 3, device=dev),
+                   quats=torch.empty(n, 4, device=dev),
+                   opacity_logits=torch.empty(g.opacity_logits.shape, device=dev),
+                   skew=torch.empty(n, 3, device=dev), sh=torch.empty(g.sh.shape, device=dev),
+                   split_dir=torch.empty(n, 3, device=dev) if g.split_dir is not None else None)
+        if want_stats:
+            out["means2d_abs"] = torch.empty(n, device=dev)
+            out["depth_grad"] = torch.empty(n, device=dev)
+        gr = N.sr_grads()
+        for k in ("means", "log_scales", "quats", "opacity_logits", "skew", "sh", "split_dir", "means2d_abs",
+                  "depth_grad"):
+            t = out.get(k)
+            setattr(gr, k, t.data_ptr() if t is not None else None)
+        N.sr_render_bwd_project(self.plan, g.to_c(), self.cams_dev.data_ptr(), self.cfg_c, self.ws.data_ptr(), gr,
+                                _stream_ptr(stream))
+        return out
+
     def backward(self, g: Gaussians, d_images: torch.Tensor, stream=None, want_stats: bool = False) -> dict:
-        """Gradients of sum(d_images * images) w.r.t. every attribute (FP32)."""
+        """Gradients of sum(d_images * images) w.r.t. every attribute (FP32),
+        through sr_render_bwd."""
         if d_images.dtype != torch.float32 or not d_images.is_contiguous() or d_images.numel() != self.images.numel():
             raise ValueError("d_images must be a contiguous float32 tensor shaped like the image buffer")
         dev = self.device
@@ -200,6 +233,54 @@ class Rasterizer:
         N.sr_render_bwd(self.plan, g.to_c(), self.cams_dev.data_ptr(), self.cfg_c, self.ws.data_ptr(),
                         d_images.data_ptr(), self.t_final.data_ptr(), self.n_contrib.data_ptr(), gr,
                         _stream_ptr(stream))
+        return out
+
+    # -- launch-shape autotuning --------------------------------------------
+    def set_pixels_per_thread(self, fwd: int | None = None, bwd: int | None = None):
+        if fwd is not None:
+            self.config.fwd_pixels_per_thread = int(fwd)
+        if bwd is not None:
+            self.config.bwd_pixels_per_thread = int(bwd)
+        self.cfg_c = self.config.to_c()
+
+    def autotune(self, g: Gaussians, d_images: torch.Tensor | None = None, candidates=(1, 2, 4), reps: int = 3,
+                 stream=None) -> dict:
+        """Choose how many pixels each thread of the forward and backward
+        composites owns by timing every candidate on this frame (CUDA events
+        on the launching stream, best of ``reps``) and keep the fastest.
+        The results do not depend on the choice."""
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.forward(g, stream)
+
+        def best_of(fn):
+            ts = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                fn()
+                b.record(s)
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            return min(ts)
+
+        fwd = {}
+        for px in candidates:
+            self.set_pixels_per_thread(fwd=px)
+            self.render_fwd(stream)  # warm
+            fwd[px] = best_of(lambda: self.render_fwd(stream))
+        pf = min(fwd, key=fwd.get)
+        self.set_pixels_per_thread(fwd=pf)
+        out = {"fwd_ms": fwd, "fwd_pixels_per_thread": pf}
+        if d_images is not None:
+            self.render_fwd(stream)
+            bwd = {}
+            for px in candidates:
+                self.set_pixels_per_thread(bwd=px)
+                self.backward(g, d_images, stream)  # warm
+                bwd[px] = best_of(lambda: self.backward(g, d_images, stream))
+            pb = min(bwd, key=bwd.get)
+            self.set_pixels_per_thread(bwd=pb)
+            out.update(bwd_ms=bwd, bwd_pixels_per_thread=pb)
         return out
 
     # -- read-only views of the workspace (tests and diagnostics) ---------

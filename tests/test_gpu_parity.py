@@ -342,6 +342,70 @@ def test_backward_batched_views_sum():
     compare_grads(gr, tot, GRAD_FIELDS)
 
 
+@pytest.mark.parametrize("px", [1, 2, 4])
+def test_pixels_per_thread_launch_shapes(px):
+    """Every launch shape of the composites gives the oracle's image and
+    gradients (the autotuner only changes speed)."""
+    sc = scenes.cluster(seed=31, n=4000, sh_degree=1, two_opacities=True)
+    cams = [scenes.identity_camera(100, 70)]
+    cfg = Config(fwd_pixels_per_thread=px, bwd_pixels_per_thread=px, bg=(0.1, 0.0, 0.2))
+    r, g = gpu_forward(sc, cams, cfg)
+    check_view(r, sc, cams, 0, cfg)
+    up = scenes.upstream_grad(31, 70, 100)
+    gr = r.backward(g, torch.as_tensor(up).cuda().reshape(-1).contiguous())
+    og = oracle.render_backward(sc, oracle.camera_from_gl(cams[0]), oracle_config(cfg), up)
+    compare_grads(gr, og, GRAD_FIELDS)
+
+
+def test_autotune_picks_a_shape_and_keeps_results():
+    sc = scenes.cluster(seed=32, n=20_000)
+    cams = [scenes.identity_camera(256, 192)]
+    r, g = gpu_forward(sc, cams)
+    ref = r.images.clone()
+    up = torch.as_tensor(scenes.upstream_grad(32, 192, 256)).cuda().reshape(-1).contiguous()
+    ref_g = r.backward(g, up)["means"].clone()
+    res = r.autotune(g, up)
+    assert res["fwd_pixels_per_thread"] in (1, 2, 4) and res["bwd_pixels_per_thread"] in (1, 2, 4)
+    r.forward(g)
+    assert torch.equal(r.images, ref)
+    gm = r.backward(g, up)["means"]
+    assert rel_err(gm.cpu().numpy(), ref_g.cpu().numpy()) < 1e-5
+
+
+def test_densification_statistics_match_oracle():
+    """Per-Gaussian |dL/dmu_2| (the 2D positional statistic g^(uv)) and the
+    depth gradient dL/dz of the centre along the camera axis (Eq. depth_grad,
+    one iteration), against the oracle's 2D and world-space gradients."""
+    sc = scenes.cluster(seed=33, n=3000, sh_degree=2)
+    cams = [scenes.camera(scenes.look_at_c2w_cv((0.3, -0.2, -0.5), (0, 0, 4)), 120, 90)]
+    r, g = gpu_forward(sc, cams)
+    up = scenes.upstream_grad(33, 90, 120)
+    gr = r.backward(g, torch.as_tensor(up).cuda().reshape(-1).contiguous(), want_stats=True)
+    oc = oracle.camera_from_gl(cams[0])
+    og = oracle.render_backward(sc, oc, oracle_config(Config()), up)
+    uv = np.hypot(og["d2"][:, 0], og["d2"][:, 1])
+    assert rel_err(gr["means2d_abs"].cpu().numpy(), uv) <= GRAD_RTOL
+    W = oracle.camera_fields(oc)["w2c"].reshape(3, 4)[:, :3]
+    dz = og["means"] @ W[2]
+    assert rel_err(gr["depth_grad"].cpu().numpy(), dz) <= GRAD_RTOL
+
+
+@pytest.mark.parametrize("dt,bound", [(torch.bfloat16, 0.05), (torch.float16, 0.01)])
+def test_reduced_precision_storage_error_against_fp32_originals(dt, bound):
+    """Storage error: the GPU renders from BF16/FP16 SH, log-scales and skew,
+    the oracle from the FP32 originals.  The stated bound is a max abs error
+    per channel of 0.05 (BF16) / 0.01 (FP16) on non-ambiguous pixels."""
+    sc = scenes.cluster(seed=6, n=5000)
+    cams = [scenes.identity_camera(200, 150)]
+    r, _ = gpu_forward(sc, cams, sh_dtype=dt, scale_dtype=dt, skew_dtype=dt)
+    _, _, _, out = oracle_view(sc, cams[0], Config())
+    img = r.view_image(r.images, 0).cpu().numpy()
+    d = np.abs(np.transpose(img, (1, 2, 0)) - out["rgb"])
+    d[out["ambiguous"]] = 0
+    print(f"storage error {dt}: max {d.max():.3e} mean {d.mean():.3e}")
+    assert d.max() <= bound
+
+
 def test_autograd_function():
     from paper_2605_18334_gb300.rasterizer import render
 
