@@ -160,10 +160,11 @@ def preprocess(scene, cam: Camera, cfg: Config, tol_px: float = TOL_PX) -> dict:
     rect = np.zeros((n, 4), np.int32)
     ext = np.zeros((n, 3))
     amb = np.zeros(n, np.int32)
+    cnt = np.zeros(n, np.int32)
     L.or_preprocess(C.byref(a.s), C.byref(cam), C.byref(cfg), C.c_double(tol_px), _p(rec), _p(bits), _p(vis),
-                    _p(rect), _p(ext), _p(amb))
+                    _p(rect), _p(ext), _p(amb), _p(cnt))
     return dict(rec=rec, depth_bits=bits, visible=vis.astype(bool), rect=rect, ext=ext, rect_ambig=amb.astype(bool),
-                _vis32=vis)
+                ntouch=cnt, _vis32=vis)
 
 
 def all_pixels(cam: Camera) -> np.ndarray:
@@ -226,14 +227,14 @@ def render_backward(scene, cam: Camera, cfg: Config, dL_dC, pixels=None, pre=Non
 def bin_keys(pre: dict, cam: Camera, cfg: Config, tile_base: int = 0, val_base: int = 0):
     """Sorted (tile << 32 | depth bits) keys and Gaussian ids of one view."""
     n = pre["rec"].shape[0]
-    tiles_x = (cam.width + cfg.tile_w - 1) // cfg.tile_w
     L = lib()
-    cnt = L.or_bin(C.c_int64(n), _p(pre["depth_bits"]), _p(pre["_vis32"]), _p(pre["rect"]), C.c_int32(tiles_x),
-                   C.c_int64(tile_base), C.c_int64(val_base), C.c_int64(0), None, None)
+    args = [C.c_int64(n), _p(pre["rec"]), _p(pre["ext"]), _p(pre["depth_bits"]), _p(pre["_vis32"]), _p(pre["rect"]),
+            C.c_int32(cam.width), C.c_int32(cam.height), C.c_int32(cfg.tile_w), C.c_int64(tile_base),
+            C.c_int64(val_base)]
+    cnt = L.or_bin(*args, C.c_int64(0), None, None)
     keys = np.zeros(max(cnt, 1), np.uint64)
     vals = np.zeros(max(cnt, 1), np.int64)
-    L.or_bin(C.c_int64(n), _p(pre["depth_bits"]), _p(pre["_vis32"]), _p(pre["rect"]), C.c_int32(tiles_x),
-             C.c_int64(tile_base), C.c_int64(val_base), C.c_int64(cnt), _p(keys), _p(vals))
+    L.or_bin(*args, C.c_int64(cnt), _p(keys), _p(vals))
     return keys[:cnt], vals[:cnt]
 
 

@@ -380,6 +380,43 @@ void tile_range_1d(double m, double e, int size, int tile, int* t0, int* t1) {
   *t1 = (int)hi / tile + 1;
 }
 
+// Tile columns of tile row ty touched by the footprint ellipse
+// {d : d^T A d <= rho2} around (mx, my), A = [[a, b], [b, c]] the conic.
+// A tile is touched iff the ellipse meets the rectangle spanned by the
+// tile's pixel centres (clipped to the image).  For the row this is the
+// x-extent of the ellipse within the band of pixel-centre heights: the
+// boundary is x(y) = (-b y +- sqrt(a rho2 - D y^2)) / a with D = ac - b^2,
+// whose rightmost point is at y = -b rho / sqrt(D c) (leftmost at the
+// opposite height); the right end is concave in y and the left end convex,
+// so their extremes over the band sit at those heights clamped to the band.
+// edge_shift perturbs both x ends (ambiguity checks).  Returns false if the
+// row touches no tile; *near_edge is set when the band only grazes the
+// ellipse's top or bottom (within tol).
+bool row_span(const double* r, double rho2, int ty, int width, int height, int tile, double edge_shift, double tol,
+              int* t0, int* t1, bool* near_edge) {
+  const double a = r[R_A], b = r[R_B], c = r[R_C];
+  const double D = a * c - b * b;
+  const double ymax = std::sqrt(a * rho2 / D);
+  double y0 = ty * (double)tile + 0.5 - r[R_MY];
+  double y1 = std::min(ty * tile + tile - 1, height - 1) + 0.5 - r[R_MY];
+  if (near_edge) *near_edge = std::fabs(y0 - ymax) < tol || std::fabs(y1 + ymax) < tol;
+  y0 = std::max(y0, -ymax);
+  y1 = std::min(y1, ymax);
+  if (!(y0 <= y1)) return false;
+  const double ys = -b * std::sqrt(rho2) / std::sqrt(D * c);
+  const double yh = std::min(std::max(ys, y0), y1);
+  const double yl = std::min(std::max(-ys, y0), y1);
+  const double xmax = (-b * yh + std::sqrt(std::max(0.0, a * rho2 - D * yh * yh))) / a;
+  const double xmin = (-b * yl - std::sqrt(std::max(0.0, a * rho2 - D * yl * yl))) / a;
+  double lo = std::ceil(r[R_MX] + xmin - 0.5 - edge_shift), hi = std::floor(r[R_MX] + xmax - 0.5 + edge_shift);
+  lo = std::max(lo, 0.0);
+  hi = std::min(hi, (double)width - 1.0);
+  if (lo > hi) return false;
+  *t0 = (int)lo / tile;
+  *t1 = (int)hi / tile;
+  return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -429,7 +466,7 @@ int or_ndiff() { return NDIFF; }
 
 void or_preprocess(const OrScene* s, const OrCamera* c, const OrConfig* cfg, double tol_px,
                    double* rec, uint32_t* depth_bits, int32_t* visible, int32_t* rect,
-                   double* ext, int32_t* rect_ambig) {
+                   double* ext, int32_t* rect_ambig, int32_t* ntouch) {
   const int K = sh_count(s->sh_degree);
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < s->n; ++i) {
@@ -444,6 +481,7 @@ void or_preprocess(const OrScene* s, const OrCamera* c, const OrConfig* cfg, dou
     rc[0] = rc[1] = rc[2] = rc[3] = 0;
     ext[3 * i] = ext[3 * i + 1] = ext[3 * i + 2] = 0.0;
     rect_ambig[i] = 0;
+    ntouch[i] = 0;
     visible[i] = dz > (float)cfg->near_z;
     if (!visible[i]) {
       std::fill(r, r + NREC, 0.0);
@@ -470,6 +508,17 @@ void or_preprocess(const OrScene* s, const OrCamera* c, const OrConfig* cfg, dou
       tile_range_1d(r[R_MY] + sgn * tol_px, e[1], c->height, cfg->tile_h, &b0, &b1);
       empty1 = (a0 == a1) || (b0 == b1);
       if (empty0 != empty1 || (!empty0 && (a0 != rc[0] || a1 != rc[2] || b0 != rc[1] || b1 != rc[3])))
+        rect_ambig[i] = 1;
+    }
+    // exact ellipse / tile test per row of the box
+    for (int ty = rc[1]; ty < rc[3]; ++ty) {
+      int t0, t1, u0, u1, v0, v1;
+      bool near = false;
+      const bool on0 = row_span(r, e[2], ty, c->width, c->height, cfg->tile_w, 0.0, tol_px, &t0, &t1, &near);
+      const bool onm = row_span(r, e[2], ty, c->width, c->height, cfg->tile_w, -tol_px, tol_px, &u0, &u1, nullptr);
+      const bool onp = row_span(r, e[2], ty, c->width, c->height, cfg->tile_w, tol_px, tol_px, &v0, &v1, nullptr);
+      if (on0) ntouch[i] += t1 - t0 + 1;
+      if (near || on0 != onm || on0 != onp || (on0 && (t0 != u0 || t1 != u1 || t0 != v0 || t1 != v1)))
         rect_ambig[i] = 1;
     }
   }
@@ -647,21 +696,29 @@ void or_render_backward(const OrScene* s, const OrCamera* cam, const OrConfig* c
   }
 }
 
-// Tile keys of one view: for each visible Gaussian with a non-empty rect, in
-// index order, one (tile | depth) key per touched tile (row-major), then a
-// stable sort.  tile_base / val_base offset the tile id and the value.
+// Tile keys of one view: for each visible Gaussian, in index order, one
+// (tile | depth) key per tile its footprint ellipse touches (row_span,
+// row-major), then a stable sort.  tile_base / val_base offset the tile id
+// and the value.
 // Returns the number of keys; writes at most cap of them.
-int64_t or_bin(int64_t n, const uint32_t* depth_bits, const int32_t* visible, const int32_t* rect, int32_t tiles_x,
-               int64_t tile_base, int64_t val_base, int64_t cap, uint64_t* keys, int64_t* vals) {
+int64_t or_bin(int64_t n, const double* rec, const double* ext, const uint32_t* depth_bits, const int32_t* visible,
+               const int32_t* rect, int32_t width, int32_t height, int32_t tile_size, int64_t tile_base,
+               int64_t val_base, int64_t cap, uint64_t* keys, int64_t* vals) {
+  const int32_t tiles_x = (width + tile_size - 1) / tile_size;
   std::vector<std::pair<uint64_t, int64_t>> kv;
   for (int64_t i = 0; i < n; ++i) {
     if (!visible[i]) continue;
     const int32_t* r = rect + 4 * i;
-    for (int ty = r[1]; ty < r[3]; ++ty)
-      for (int tx = r[0]; tx < r[2]; ++tx) {
+    for (int ty = r[1]; ty < r[3]; ++ty) {
+      int t0, t1;
+      if (!row_span(rec + (size_t)NREC * i, ext[3 * i + 2], ty, width, height, tile_size, 0.0, 0.0, &t0, &t1,
+                    nullptr))
+        continue;
+      for (int tx = t0; tx <= t1; ++tx) {
         uint64_t tile = (uint64_t)(tile_base + (int64_t)ty * tiles_x + tx);
         kv.push_back({(tile << 32) | depth_bits[i], val_base + i});
       }
+    }
   }
   std::stable_sort(kv.begin(), kv.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
   int64_t m = (int64_t)kv.size();

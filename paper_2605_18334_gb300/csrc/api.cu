@@ -180,6 +180,7 @@ sr_status sr_plan_init(sr_plan* p, const sr_config* cfg, const sr_gaussians* g, 
   const int64_t scan_blocks = (m + kScanBlock - 1) / kScanBlock;
   const int64_t parts = (key_capacity + kSortPart - 1) / kSortPart;
   const int64_t dparts = (m + kSortPart - 1) / kSortPart;
+  static_assert(WS_NUM_SLOTS <= (int)(sizeof(p->off) / sizeof(p->off[0])), "plan offset table too small");
   size_t sizes[WS_NUM_SLOTS];
   sizes[WS_STATUS] = sizeof(Status);
   sizes[WS_VIEWS] = sizeof(ViewInfo) * SR_MAX_VIEWS;
@@ -198,6 +199,7 @@ sr_status sr_plan_init(sr_plan* p, const sr_config* cfg, const sr_gaussians* g, 
   sizes[WS_LOOKBACK] = sizeof(unsigned long long) * 256 * (size_t)p->sort_passes * (size_t)parts;
   sizes[WS_RANGES] = sizeof(uint2) * (size_t)tb;
   sizes[WS_D2] = sizeof(float) * kD2Stride * (size_t)m;
+  sizes[WS_FOOT] = sizeof(float4) * 2 * (size_t)m;
   size_t off = 0;
   for (int k = 0; k < WS_NUM_SLOTS; ++k) {
     p->off[k] = off;

@@ -134,74 +134,40 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint32_t*
 }
 
 // ---------------------------------------------------------------------------
-// key duplication, in depth order.  A warp takes 32 consecutive depth-sorted
-// records and writes their keys as one contiguous run: each lane finds the
-// record that owns its output slot by a binary search over the lanes' starts
-// (lanes with no tiles have zero-length ranges and are never selected as the
-// last lane whose start is <= the slot).
+// key duplication, in depth order: one thread per record writes one key per
+// touched tile (row by row, the spans of row_tile_span) at its scanned offset.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) duplicate_kernel(int64_t n, int n_views, const ViewInfo* __restrict__ views,
                                                         const uint32_t* __restrict__ perm,
                                                         const uint32_t* __restrict__ ntouch,
                                                         const uint32_t* __restrict__ offsets,
                                                         const uint2* __restrict__ rect,
+                                                        const float4* __restrict__ rec,
+                                                        const float4* __restrict__ foot,
                                                         uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                         unsigned long long cap) {
   const int64_t m_total = n * n_views;
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w * 32 < m_total; w += warps) {
-    const int64_t j = w * 32 + lane;
-    uint32_t m = 0, cnt = 0, start = 0xffffffffu, tx0 = 0, ty0 = 0, tw = 1;
-    int64_t tbase = 0;
-    int tiles_x = 1;
-    if (j < m_total) {
-      m = perm[j];
-      cnt = ntouch[m];
-      start = offsets[j];
-      if (cnt) {
-        const uint2 r = rect[m];
-        tx0 = r.x & 0xffffu;
-        ty0 = r.x >> 16;
-        tw = (r.y & 0xffffu) - tx0;
-        const ViewInfo& vi = views[(int)(m / (uint64_t)n)];
-        tbase = vi.tile_base;
-        tiles_x = vi.tiles_x;
-      }
-    }
-    // the run of this warp: [start of lane 0, end of the last valid lane)
-    const uint32_t base = __shfl_sync(0xffffffffu, start, 0);
-    const uint32_t end = __reduce_max_sync(0xffffffffu, cnt ? start + cnt : 0u);
-    // start relative to the run (non-decreasing over lanes; lanes past the
-    // last record get a huge value and are never selected)
-    const uint32_t rel = start - base;
-    // warp-uniform loop: every lane takes part in the shuffles, only lanes
-    // with p < end write
-    for (uint32_t p0 = base; p0 < end; p0 += 32) {
-      const uint32_t p = p0 + lane;
-      const uint32_t q_rel = p - base;
-      // owner: the last lane whose start <= q_rel.  Lanes without tiles share
-      // their start with the next lane, so the last lane of such a group is
-      // the one whose range covers q_rel.
-      int lo = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const uint32_t s_rel = __shfl_sync(0xffffffffu, rel, lo + step);
-        if (s_rel <= q_rel) lo += step;
-      }
-      const uint32_t o_rel = __shfl_sync(0xffffffffu, rel, lo);
-      const uint32_t o_m = __shfl_sync(0xffffffffu, m, lo);
-      const uint32_t o_tx0 = __shfl_sync(0xffffffffu, tx0, lo);
-      const uint32_t o_ty0 = __shfl_sync(0xffffffffu, ty0, lo);
-      const uint32_t o_tw = __shfl_sync(0xffffffffu, tw, lo);
-      const long long o_tb = __shfl_sync(0xffffffffu, (long long)tbase, lo);
-      const int o_tx = __shfl_sync(0xffffffffu, tiles_x, lo);
-      const uint32_t q = q_rel - o_rel;
-      const uint32_t dy = q / o_tw, dx = q - dy * o_tw;
-      if (p < end && p < cap) {
-        keys[p] = (uint32_t)(o_tb + (long long)(o_ty0 + dy) * o_tx + (o_tx0 + dx));
-        vals[p] = o_m;
-      }
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m_total;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t m = perm[j];
+    const uint32_t cnt = ntouch[m];
+    if (cnt == 0) continue;
+    const ViewInfo vi = views[(int)(m / (uint64_t)n)];
+    const uint2 r = rect[m];
+    const int ty0 = (int)(r.x >> 16), ty1 = (int)(r.y >> 16);
+    const float4 f0 = foot[2 * (int64_t)m], f1 = foot[2 * (int64_t)m + 1];
+    const float4 r0 = rec[4 * (int64_t)m];
+    unsigned long long pos = offsets[j];
+    const unsigned long long end = pos + cnt;
+    for (int ty = ty0; ty < ty1; ++ty) {
+      int lo, hi;
+      if (!row_tile_span(f0, f1, r0.x, r0.y, ty, vi.width, vi.height, lo, hi)) continue;
+      const uint32_t row = (uint32_t)(vi.tile_base + (int64_t)ty * vi.tiles_x);
+      for (int tx = lo; tx <= hi; ++tx, ++pos)
+        if (pos < end && pos < cap) {
+          keys[pos] = row + (uint32_t)tx;
+          vals[pos] = m;
+        }
     }
   }
 }
@@ -489,7 +455,8 @@ cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms) {
   if (m > 0) {
     scan_down_kernel<<<nb, kScanThreads, 0, st>>>(a.ws.ntouch, perm, m, a.ws.scan_part, a.ws.offsets);
     duplicate_kernel<<<clamp_grid((m + 255) / 256, sms, 8), 256, 0, st>>>(
-        a.n, a.n_views, a.ws.views, perm, a.ws.ntouch, a.ws.offsets, a.ws.rect, a.ws.keys[0], a.ws.vals[0], a.cap);
+        a.n, a.n_views, a.ws.views, perm, a.ws.ntouch, a.ws.offsets, a.ws.rect, a.ws.rec, a.ws.foot, a.ws.keys[0],
+        a.ws.vals[0], a.cap);
     count_launches(2);
   }
   if (a.passes > 0) {

@@ -34,6 +34,7 @@ enum WsSlot {
   WS_LOOKBACK,     // uint64_t[parts(cap)][tile passes][256] look-back words of the tile sort
   WS_RANGES,       // uint2[total_tiles] [start, end) of each tile's sorted keys
   WS_D2,           // float[M][16] per-(view, Gaussian) 2D gradients
+  WS_FOOT,         // float4[M][2] footprint ellipse constants (see Foot)
   WS_NUM_SLOTS
 };
 
@@ -194,6 +195,42 @@ __device__ __forceinline__ bool eval_pair(const float4& r0, const float4& r1, co
   return true;
 }
 
+// Footprint ellipse {d : d^T Sigma_d^-1 d <= rho^2} around mu_2, stored as
+//   f0 = (slope, wdet, ystar, ymax), f1 = (rho2, inv_syy, 0, 0)
+// with slope = Sxy/Syy, wdet = det(Sigma_d)/Syy, ystar = rho Sxy / sqrt(Sxx)
+// (height of the rightmost point), ymax = rho sqrt(Syy), inv_syy = 1/Syy.
+// At height y (relative to mu_y) the ellipse spans
+//   x = slope y -+ sqrt(wdet (rho2 - y^2 / Syy)).
+// Tile row ty is touched in the tile columns that hold a pixel centre inside
+// the x-extent of the ellipse restricted to the row's band of pixel-centre
+// heights: the right edge is largest at y = clamp(ystar, band), the left
+// edge smallest at y = clamp(-ystar, band) (concave / convex in y).  The
+// counting (preprocess) and emitting (duplicate) kernels call this with the
+// stored constants and explicitly rounded operations, so they agree bit for
+// bit.  Returns false if the row touches no tile.
+__device__ __forceinline__ bool row_tile_span(const float4& f0, const float4& f1, float mx, float my, int ty,
+                                              int width, int height, int& tlo, int& thi) {
+  float y0 = __fadd_rn((float)(ty * kTile) + 0.5f, -my);
+  float y1 = __fadd_rn((float)min(ty * kTile + kTile - 1, height - 1) + 0.5f, -my);
+  y0 = fmaxf(y0, -f0.w);
+  y1 = fminf(y1, f0.w);
+  if (!(y0 <= y1)) return false;
+  const float yh = fminf(fmaxf(f0.z, y0), y1);
+  const float yl = fminf(fmaxf(-f0.z, y0), y1);
+  const float hh = __fsqrt_rn(__fmul_rn(f0.y, fmaxf(0.0f, __fadd_rn(f1.x, -__fmul_rn(__fmul_rn(yh, yh), f1.y)))));
+  const float hl = __fsqrt_rn(__fmul_rn(f0.y, fmaxf(0.0f, __fadd_rn(f1.x, -__fmul_rn(__fmul_rn(yl, yl), f1.y)))));
+  const float xmax = __fadd_rn(__fmul_rn(f0.x, yh), hh);
+  const float xmin = __fadd_rn(__fmul_rn(f0.x, yl), -hl);
+  float lo = ceilf(__fadd_rn(__fadd_rn(mx, xmin), -0.5f));
+  float hi = floorf(__fadd_rn(__fadd_rn(mx, xmax), -0.5f));
+  lo = fmaxf(lo, 0.0f);
+  hi = fminf(hi, (float)(width - 1));
+  if (!(lo <= hi)) return false;
+  tlo = (int)lo / kTile;
+  thi = (int)hi / kTile;
+  return true;
+}
+
 // Storage loads (FP32 arithmetic whatever the storage type).
 template <int DT>
 __device__ __forceinline__ float ld(const void* p, int64_t i) {
@@ -261,6 +298,7 @@ struct Ws {
   unsigned long long* lookback;
   uint2* ranges;
   float* d2;
+  float4* foot;
 };
 
 inline Ws ws_ptrs(const sr_plan& p, void* base) {
@@ -288,6 +326,7 @@ inline Ws ws_ptrs(const sr_plan& p, void* base) {
   w.lookback = reinterpret_cast<unsigned long long*>(at(WS_LOOKBACK));
   w.ranges = reinterpret_cast<uint2*>(at(WS_RANGES));
   w.d2 = reinterpret_cast<float*>(at(WS_D2));
+  w.foot = reinterpret_cast<float4*>(at(WS_FOOT));
   return w;
 }
 

@@ -357,7 +357,16 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_fwd_kernel(PreArgs a) 
               const uint32_t tx0 = (uint32_t)xlo / kTile, tx1 = (uint32_t)xhi / kTile + 1;
               const uint32_t ty0 = (uint32_t)ylo / kTile, ty1 = (uint32_t)yhi / kTile + 1;
               rect = make_uint2(tx0 | (ty0 << 16), tx1 | (ty1 << 16));
-              ntouch = (tx1 - tx0) * (ty1 - ty0);
+              // exact ellipse / tile test, row by row (row_tile_span)
+              const float4 f0 = make_float4(P.sxy / dyy, P.detD / dyy, sqrtf(rho2) * P.sxy / sqrtf(dxx), ey);
+              const float4 f1 = make_float4(rho2, 1.0f / dyy, 0.0f, 0.0f);
+              a.ws.foot[2 * m] = f0;
+              a.ws.foot[2 * m + 1] = f1;
+              for (uint32_t ty = ty0; ty < ty1; ++ty) {
+                int lo, hi;
+                if (row_tile_span(f0, f1, P.mx, P.my, (int)ty, c.width, c.height, lo, hi))
+                  ntouch += (uint32_t)(hi - lo + 1);
+              }
             }
           }
         }

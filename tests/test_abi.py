@@ -99,7 +99,7 @@ def test_plan_layout(lib):
     tile_bits = math.ceil(math.log2(sum(tiles)))
     assert p.sort_bits == 32 + tile_bits and p.sort_passes == -(-tile_bits // 8)
     assert p.ws_bytes == lib.sr_workspace_size(C.byref(p)) and p.ws_bytes % 256 == 0
-    offs = list(p.off[:21])
+    offs = list(p.off[:22])
     assert offs == sorted(offs) and all(o % 256 == 0 for o in offs)
     assert p.render_mode == 0
     assert N.sr_plan_init(cfg, _desc(10, two=1), cams, 10).render_mode == 1

@@ -52,8 +52,7 @@ def check_view(r, scene, cams, v, cfg, pixels=None, check_keys=True):
     depth = r.depth_bits().cpu().numpy().view(np.uint32)[v * n:(v + 1) * n]
     np.testing.assert_array_equal(depth, pre["depth_bits"])
     cnt = r.tile_counts().cpu().numpy()[v * n:(v + 1) * n]
-    rect = pre["rect"]
-    or_cnt = np.where(pre["visible"], (rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1]), 0)
+    or_cnt = np.where(pre["visible"], pre["ntouch"], 0)
     amb = pre["rect_ambig"]
     np.testing.assert_array_equal(cnt[~amb], or_cnt[~amb])
     stats["rect_ambiguous"] = int(amb.sum())
