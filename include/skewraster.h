@@ -110,7 +110,9 @@ typedef struct sr_config {
   int32_t sort_spin_limit;    /* 0 = auto; bound on each look-back wait of the sort */
   int32_t fwd_pixels_per_thread; /* 1, 2 or 4 (0 = 2): pixels each thread of sr_render_fwd owns */
   int32_t bwd_pixels_per_thread; /* 1, 2 or 4 (0 = 2): pixels each thread of sr_render_bwd owns */
-  int32_t reserved_[2];
+  int32_t forward_only;       /* plans made with 1 record no per-pixel blend masks (less workspace);
+                                 sr_render_bwd on them returns SR_ERR_UNSUPPORTED */
+  int32_t reserved_[1];
 } sr_config;
 
 /* Gradients of the loss w.r.t. the attributes, FP32, device, caller-owned,
@@ -144,6 +146,8 @@ typedef struct sr_plan {
   int32_t render_mode;        /* 0: one opacity; 1: two opacities; 2: two opacities + split direction */
   int32_t two_opacities;      /* copied from the sr_gaussians the plan was made for */
   int32_t has_split;          /* 1 if split_dir was non-NULL */
+  int32_t forward_only;       /* from the config: no blend masks, no backward */
+  int32_t reserved1_;
   int64_t key_capacity;       /* keys the workspace can hold */
   int64_t total_tiles;
   int64_t total_pixels;

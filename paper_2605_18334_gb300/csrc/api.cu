@@ -152,6 +152,7 @@ sr_status sr_plan_init(sr_plan* p, const sr_config* cfg, const sr_gaussians* g, 
   p->two_opacities = g->two_opacities ? 1 : 0;
   p->has_split = g->split_dir ? 1 : 0;
   p->render_mode = !p->two_opacities ? MODE_PLAIN : (p->has_split ? MODE_SPLIT : MODE_TWO);
+  p->forward_only = cfg->forward_only ? 1 : 0;
   p->key_capacity = key_capacity;
   int64_t tb = 0, io = 0, po = 0;
   for (int v = 0; v < n_views; ++v) {
@@ -198,8 +199,9 @@ sr_status sr_plan_init(sr_plan* p, const sr_config* cfg, const sr_gaussians* g, 
   sizes[WS_LOOKBACK_D] = sizeof(unsigned long long) * 256 * kDepthPasses * (size_t)dparts;
   sizes[WS_LOOKBACK] = sizeof(unsigned long long) * 256 * (size_t)p->sort_passes * (size_t)parts;
   sizes[WS_RANGES] = sizeof(uint2) * (size_t)tb;
-  sizes[WS_D2] = sizeof(float) * kD2Stride * (size_t)m;
+  sizes[WS_D2] = p->forward_only ? 0 : sizeof(float) * kD2Stride * (size_t)m;
   sizes[WS_FOOT] = sizeof(float4) * 2 * (size_t)m;
+  sizes[WS_MASK] = p->forward_only ? 0 : sizeof(uint32_t) * 256 * (size_t)(key_capacity / 32 + tb + 1);
   size_t off = 0;
   for (int k = 0; k < WS_NUM_SLOTS; ++k) {
     p->off[k] = off;
@@ -287,6 +289,7 @@ static RenderArgs render_args(const sr_plan* p, const sr_config* cfg, void* ws) 
   r.n_contrib = nullptr;
   r.d_images = nullptr;
   r.d2 = w.d2;
+  r.mask = w.mask;
   r.px_fwd = cfg->fwd_pixels_per_thread > 0 ? cfg->fwd_pixels_per_thread : 2;
   r.px_bwd = cfg->bwd_pixels_per_thread > 0 ? cfg->bwd_pixels_per_thread : 2;
   return r;
@@ -311,6 +314,7 @@ sr_status sr_render_bwd_composite(const sr_plan* p, const sr_config* cfg, void* 
   if (s != SR_OK) return s;
   if ((s = check_config(cfg)) != SR_OK) return s;
   if (!d_images || !t_final || !n_contrib) return SR_ERR_INVALID;
+  if (p->forward_only) return SR_ERR_UNSUPPORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const Ws w = ws_ptrs(*p, ws);
   cudaError_t e = cudaMemsetAsync(w.d2, 0, sizeof(float) * kD2Stride * (size_t)(p->n * p->n_views), st);
@@ -351,6 +355,7 @@ sr_status sr_render_bwd(const sr_plan* p, const sr_gaussians* g, const sr_camera
   if ((s = check_config(cfg)) != SR_OK) return s;
   if ((s = check_gaussians(p, g, true)) != SR_OK) return s;
   if (!cams_dev || !d_images || !t_final || !n_contrib || !out) return SR_ERR_INVALID;
+  if (p->forward_only) return SR_ERR_UNSUPPORTED;
   if (p->n > 0 && (!out->means || !out->log_scales || !out->quats || !out->opacity_logits || !out->skew || !out->sh))
     return SR_ERR_INVALID;
   if (p->has_split && p->n > 0 && !out->split_dir) return SR_ERR_INVALID;

@@ -134,8 +134,12 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint32_t*
 }
 
 // ---------------------------------------------------------------------------
-// key duplication, in depth order: one thread per record writes one key per
-// touched tile (row by row, the spans of row_tile_span) at its scanned offset.
+// key duplication, in depth order.  A warp takes 32 consecutive depth-sorted
+// records and writes their keys as one contiguous run: each lane finds the
+// record owning its output slot by a binary search over the lanes' starts
+// and decodes the slot's tile from the owner's packed row spans (coalesced
+// writes).  Records whose tile box is too large for packed spans are written
+// afterwards by their own lane, row by row (row_tile_span).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) duplicate_kernel(int64_t n, int n_views, const ViewInfo* __restrict__ views,
                                                         const uint32_t* __restrict__ perm,
@@ -147,27 +151,90 @@ __global__ void __launch_bounds__(256) duplicate_kernel(int64_t n, int n_views, 
                                                         uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                         unsigned long long cap) {
   const int64_t m_total = n * n_views;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m_total;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t m = perm[j];
-    const uint32_t cnt = ntouch[m];
-    if (cnt == 0) continue;
-    const ViewInfo vi = views[(int)(m / (uint64_t)n)];
-    const uint2 r = rect[m];
-    const int ty0 = (int)(r.x >> 16), ty1 = (int)(r.y >> 16);
-    const float4 f0 = foot[2 * (int64_t)m], f1 = foot[2 * (int64_t)m + 1];
-    const float4 r0 = rec[4 * (int64_t)m];
-    unsigned long long pos = offsets[j];
-    const unsigned long long end = pos + cnt;
-    for (int ty = ty0; ty < ty1; ++ty) {
-      int lo, hi;
-      if (!row_tile_span(f0, f1, r0.x, r0.y, ty, vi.width, vi.height, lo, hi)) continue;
-      const uint32_t row = (uint32_t)(vi.tile_base + (int64_t)ty * vi.tiles_x);
-      for (int tx = lo; tx <= hi; ++tx, ++pos)
-        if (pos < end && pos < cap) {
-          keys[pos] = row + (uint32_t)tx;
-          vals[pos] = m;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w * 32 < m_total; w += warps) {
+    const int64_t j = w * 32 + lane;
+    uint32_t m = 0, cnt = 0, start = 0xffffffffu, tx0 = 0, ty0 = 0, sp0 = 0, sp1 = 0;
+    uint32_t row0 = 0, tiles_x = 0;  // global tile id of (0, ty0) and the view's tiles per row
+    bool tall = false;
+    ViewInfo vi;
+    if (j < m_total) {
+      m = perm[j];
+      cnt = ntouch[m];
+      start = offsets[j];
+      if (cnt) {
+        const uint2 r = rect[m];
+        tx0 = r.x & 0xffffu;
+        ty0 = r.x >> 16;
+        const float4 f1 = foot[2 * (int64_t)m + 1];
+        sp0 = __float_as_uint(f1.z);
+        sp1 = __float_as_uint(f1.w);
+        tall = sp0 == kSpansTall;
+        vi = views[(int)(m / (uint64_t)n)];
+        tiles_x = (uint32_t)vi.tiles_x;
+        row0 = (uint32_t)(vi.tile_base + (int64_t)ty0 * vi.tiles_x);
+      }
+    }
+    // the run of this warp: [start of lane 0, end of the last valid lane)
+    const uint32_t base = __shfl_sync(0xffffffffu, start, 0);
+    const uint32_t end = __reduce_max_sync(0xffffffffu, cnt ? start + cnt : 0u);
+    const uint32_t rel = start - base;  // non-decreasing over lanes; huge past the last record
+    // warp-uniform loop: every lane takes part in the shuffles
+    for (uint32_t p0 = base; p0 < end; p0 += 32) {
+      const uint32_t p = p0 + lane;
+      const uint32_t q_rel = p - base;
+      // owner: the last lane whose start <= q_rel (lanes without tiles share
+      // their start with the next lane, whose range then covers q_rel)
+      int lo = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t s_rel = __shfl_sync(0xffffffffu, rel, lo + step);
+        if (s_rel <= q_rel) lo += step;
+      }
+      const uint32_t o_rel = __shfl_sync(0xffffffffu, rel, lo);
+      const uint32_t o_m = __shfl_sync(0xffffffffu, m, lo);
+      const uint32_t o_sp0 = __shfl_sync(0xffffffffu, sp0, lo);
+      const uint32_t o_sp1 = __shfl_sync(0xffffffffu, sp1, lo);
+      const uint32_t o_tx0 = __shfl_sync(0xffffffffu, tx0, lo);
+      const uint32_t o_row0 = __shfl_sync(0xffffffffu, row0, lo);
+      const uint32_t o_tx = __shfl_sync(0xffffffffu, tiles_x, lo);
+      if (p >= end || o_sp0 == kSpansTall) continue;
+      // decode the row of the q-th key from the packed spans
+      uint32_t q = q_rel - o_rel, key = 0;
+      bool found = false;
+#pragma unroll
+      for (int rr = 0; rr < kSpanRows; ++rr) {
+        const uint32_t word = (rr < 2 ? o_sp0 : o_sp1) >> (16 * (rr & 1));
+        const uint32_t first = word & 0xffu, num = (word >> 8) & 0xffu;
+        if (!found && q < num) {
+          key = o_row0 + (uint32_t)rr * o_tx + o_tx0 + first + q;
+          found = true;
         }
+        if (!found) q -= num;
+      }
+      if (found && p < cap) {
+        keys[p] = key;
+        vals[p] = o_m;
+      }
+    }
+    if (tall && cnt) {
+      const uint2 r = rect[m];
+      const int ty1 = (int)(r.y >> 16);
+      const float4 f0 = foot[2 * (int64_t)m], f1 = foot[2 * (int64_t)m + 1];
+      const float4 r0 = rec[4 * (int64_t)m];
+      unsigned long long pos = start;
+      const unsigned long long stop = pos + cnt;
+      for (int ty = (int)ty0; ty < ty1; ++ty) {
+        int lo, hi;
+        if (!row_tile_span(f0, f1, r0.x, r0.y, ty, vi.width, vi.height, lo, hi)) continue;
+        const uint32_t row = (uint32_t)(vi.tile_base + (int64_t)ty * vi.tiles_x);
+        for (int tx = lo; tx <= hi; ++tx, ++pos)
+          if (pos < stop && pos < cap) {
+            keys[pos] = row + (uint32_t)tx;
+            vals[pos] = m;
+          }
+      }
     }
   }
 }
@@ -237,7 +304,7 @@ struct PassArgs {
 };
 
 template <class KEY>
-__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(PassArgs<KEY> a) {
+__global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(PassArgs<KEY> a) {
   constexpr int NW = kSortThreads / 32;
   __shared__ KEY s_buf[kSortPart];  // keys, then values (as u32) in the scatter phase
   __shared__ uint32_t s_whist[NW][256];
@@ -295,25 +362,44 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(PassArgs<KEY> a)
   st_relaxed_u64(lb + d, (part == 0 ? kFlagInc : kFlagAgg) | tot);
   unsigned long long excl = 0;
   if (part > 0) {
+    // walk back over the predecessors' words of this digit, four loads in
+    // flight at a time: aggregates are summed, an inclusive prefix ends the
+    // walk, a word not yet published is polled again (at most spin_limit times)
+    constexpr int kWin = 4;
+    const unsigned long long stride = (unsigned long long)a.passes * 256;
+    const unsigned long long* col = a.lookback + (unsigned long long)a.pass * 256 + d;
     long long q = (long long)part - 1;
     int spins = 0;
-    while (q >= 0) {
-      const unsigned long long v = ld_relaxed_u64(a.lookback + ((unsigned long long)q * a.passes + a.pass) * 256 + d);
-      if (v & kFlagInc) {
-        excl += v & kValMask;
-        break;
+    bool walking = true;
+    while (walking) {
+      unsigned long long w[kWin];
+#pragma unroll
+      for (int k = 0; k < kWin; ++k) w[k] = q - k >= 0 ? ld_relaxed_u64(col + (unsigned long long)(q - k) * stride) : 0ull;
+      bool stalled = false;
+#pragma unroll
+      for (int k = 0; k < kWin; ++k) {
+        if (!walking || stalled || q < 0) continue;
+        const unsigned long long v = w[k];
+        if (v & kFlagInc) {
+          excl += v & kValMask;
+          walking = false;
+        } else if (v & kFlagAgg) {
+          excl += v & kValMask;
+          --q;
+          walking = q >= 0;
+        } else {
+          stalled = true;  // not published yet: poll from q again
+        }
       }
-      if (v & kFlagAgg) {
-        excl += v & kValMask;
-        --q;
-        continue;
+      if (walking && stalled) {
+        if (++spins > a.spin_limit) {  // bounded wait: report and go on
+          raise_status(a.st, kStatusTimeout);
+          atomicCAS(&a.st->timeout_where, 0u, (uint32_t)(a.pass * 1000000 + (part % 1000000)) + 1u);
+          walking = false;
+        } else {
+          __nanosleep(32);
+        }
       }
-      if (++spins > a.spin_limit) {  // bounded wait: report and go on
-        raise_status(a.st, kStatusTimeout);
-        atomicCAS(&a.st->timeout_where, 0u, (uint32_t)(a.pass * 1000000 + (part % 1000000)) + 1u);
-        break;
-      }
-      __nanosleep(32);
     }
     st_relaxed_u64(lb + d, kFlagInc | (excl + tot));
   }

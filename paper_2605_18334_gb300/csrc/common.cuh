@@ -35,6 +35,7 @@ enum WsSlot {
   WS_RANGES,       // uint2[total_tiles] [start, end) of each tile's sorted keys
   WS_D2,           // float[M][16] per-(view, Gaussian) 2D gradients
   WS_FOOT,         // float4[M][2] footprint ellipse constants (see Foot)
+  WS_MASK,         // uint32_t[(cap/32 + tiles + 1) * 256] per-pixel blend masks (see render.cu)
   WS_NUM_SLOTS
 };
 
@@ -196,7 +197,7 @@ __device__ __forceinline__ bool eval_pair(const float4& r0, const float4& r1, co
 }
 
 // Footprint ellipse {d : d^T Sigma_d^-1 d <= rho^2} around mu_2, stored as
-//   f0 = (slope, wdet, ystar, ymax), f1 = (rho2, inv_syy, 0, 0)
+//   f0 = (slope, wdet, ystar, ymax), f1 = (rho2, inv_syy, spans, spans)
 // with slope = Sxy/Syy, wdet = det(Sigma_d)/Syy, ystar = rho Sxy / sqrt(Sxx)
 // (height of the rightmost point), ymax = rho sqrt(Syy), inv_syy = 1/Syy.
 // At height y (relative to mu_y) the ellipse spans
@@ -230,6 +231,14 @@ __device__ __forceinline__ bool row_tile_span(const float4& f0, const float4& f1
   thi = (int)hi / kTile;
   return true;
 }
+
+// Row spans of a record's touched tiles, packed for the key emission: for a
+// tile box of at most kSpanRows rows and 255 columns, 8 bits of first column
+// (relative to the box) and 8 bits of count per row, two rows per 32-bit
+// word (f1.z: rows 0-1, f1.w: rows 2-3).  Larger boxes store kSpansTall and
+// are enumerated with row_tile_span again.
+constexpr int kSpanRows = 4;
+constexpr uint32_t kSpansTall = 0xffffffffu;
 
 // Storage loads (FP32 arithmetic whatever the storage type).
 template <int DT>
@@ -299,6 +308,7 @@ struct Ws {
   uint2* ranges;
   float* d2;
   float4* foot;
+  uint32_t* mask;   // null when the plan is forward-only
 };
 
 inline Ws ws_ptrs(const sr_plan& p, void* base) {
@@ -327,6 +337,7 @@ inline Ws ws_ptrs(const sr_plan& p, void* base) {
   w.ranges = reinterpret_cast<uint2*>(at(WS_RANGES));
   w.d2 = reinterpret_cast<float*>(at(WS_D2));
   w.foot = reinterpret_cast<float4*>(at(WS_FOOT));
+  w.mask = p.forward_only ? nullptr : reinterpret_cast<uint32_t*>(at(WS_MASK));
   return w;
 }
 

@@ -47,6 +47,7 @@ struct RenderArgs {     // forward and backward composite
   uint32_t* n_contrib;
   const float* d_images;
   float* d2;
+  uint32_t* mask;       // per-pixel blend masks, or null (forward-only plan)
   int px_fwd;           // pixels per thread (1, 2, 4)
   int px_bwd;
 };

@@ -359,14 +359,24 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_fwd_kernel(PreArgs a) 
               rect = make_uint2(tx0 | (ty0 << 16), tx1 | (ty1 << 16));
               // exact ellipse / tile test, row by row (row_tile_span)
               const float4 f0 = make_float4(P.sxy / dyy, P.detD / dyy, sqrtf(rho2) * P.sxy / sqrtf(dxx), ey);
-              const float4 f1 = make_float4(rho2, 1.0f / dyy, 0.0f, 0.0f);
-              a.ws.foot[2 * m] = f0;
-              a.ws.foot[2 * m + 1] = f1;
+              float4 f1 = make_float4(rho2, 1.0f / dyy, 0.0f, 0.0f);
+              const bool small = ty1 - ty0 <= (uint32_t)kSpanRows && tx1 - tx0 <= 255u;
+              uint32_t pk0 = 0u, pk1 = 0u;
               for (uint32_t ty = ty0; ty < ty1; ++ty) {
                 int lo, hi;
-                if (row_tile_span(f0, f1, P.mx, P.my, (int)ty, c.width, c.height, lo, hi))
+                if (row_tile_span(f0, f1, P.mx, P.my, (int)ty, c.width, c.height, lo, hi)) {
                   ntouch += (uint32_t)(hi - lo + 1);
+                  if (small) {
+                    const uint32_t rr = ty - ty0;
+                    const uint32_t w = (((uint32_t)(lo - (int)tx0)) | ((uint32_t)(hi - lo + 1) << 8)) << (16 * (rr & 1));
+                    if (rr < 2) pk0 |= w; else pk1 |= w;
+                  }
+                }
               }
+              f1.z = __uint_as_float(small ? pk0 : kSpansTall);
+              f1.w = __uint_as_float(small ? pk1 : kSpansTall);
+              a.ws.foot[2 * m] = f0;
+              a.ws.foot[2 * m + 1] = f1;
             }
           }
         }

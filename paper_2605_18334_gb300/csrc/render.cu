@@ -56,20 +56,40 @@ __device__ __forceinline__ void stage_batch(const RenderArgs& a, const uint32_t*
   }
 }
 
-template <int MODE, int PX>
-__global__ void __launch_bounds__(256 / PX) render_fwd_kernel(RenderArgs a) {
+// Blend masks.  For the backward pass the forward records, per pixel, which
+// positions of its tile's sorted list it blended: one bit per position, a
+// 32-bit word per 32 positions (chunk c covers positions range.x + 32c ..).
+// Tile t's words start at chunk floor(range.x / 32) + t, which never overlaps
+// the next tile's, and the 256 pixels' words of one chunk are consecutive,
+// so the stores of a warp are coalesced.  A pixel writes every word up to the
+// one holding its stop; the backward reads only words below its last blend.
+__device__ __forceinline__ uint32_t* mask_tile_base(uint32_t* mask, uint2 range, int64_t tile) {
+  return mask + ((int64_t)(range.x >> 5) + tile) * 256;
+}
+
+// occupancy target of the forward composite: 5 blocks of 256 threads per SM
+// for one pixel per thread (<= 51 registers), the compiler's choice otherwise
+template <int PX>
+struct FwdMinBlocks {
+  static constexpr int value = PX == 1 ? 5 : 1;
+};
+
+template <int MODE, int PX, bool REC>
+__global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_kernel(RenderArgs a) {
   constexpr int NT = 256 / PX;
   __shared__ float4 s_r0[kBatch], s_r1[kBatch], s_r2[MODE == MODE_PLAIN ? 1 : kBatch], s_r3[kBatch];
   const TileCoord tc = tile_coord(a, blockIdx.x);
   const int px = tc.tx * kTile + (threadIdx.x & (kTile - 1));
   const int py0 = tc.ty * kTile + (threadIdx.x >> 4) * PX;
+  const int pi0 = (threadIdx.x >> 4) * PX * kTile + (threadIdx.x & (kTile - 1));  // pixel index in the tile
   const float fx = (float)px + 0.5f;
   const uint2 range = a.ranges[blockIdx.x];
   const uint32_t* vals = a.status->sorted_buf ? a.vals1 : a.vals0;
   const float amin = a.cfg.alpha_min, amax = a.cfg.alpha_max, tstop = a.cfg.t_stop;
+  uint32_t* mbase = REC ? mask_tile_base(a.mask, range, blockIdx.x) : nullptr;
 
   float T[PX], C0[PX], C1[PX], C2[PX];
-  uint32_t last[PX], stop[PX];
+  uint32_t last[PX], stop[PX], mw[PX];
   bool done[PX];
   int active = 0;  // pixels of this thread still compositing
 #pragma unroll
@@ -78,6 +98,7 @@ __global__ void __launch_bounds__(256 / PX) render_fwd_kernel(RenderArgs a) {
     C0[p] = C1[p] = C2[p] = 0.0f;
     last[p] = 0;
     stop[p] = range.y;
+    mw[p] = 0u;
     done[p] = !(px < tc.vi.width && py0 + p < tc.vi.height);
     active += done[p] ? 0 : 1;
   }
@@ -88,30 +109,44 @@ __global__ void __launch_bounds__(256 / PX) render_fwd_kernel(RenderArgs a) {
     __syncthreads();
     const int cnt = (int)min((uint32_t)kBatch, range.y - start);
     if (active) {
-      for (int j = 0; j < cnt; ++j) {
-        const float4 r0 = s_r0[j], r1 = s_r1[j], r3 = s_r3[j];
-        const float4 r2 = MODE == MODE_PLAIN ? r0 : s_r2[j];
+      for (int jc = 0; jc < cnt; jc += 32) {  // chunks of 32 positions (one mask word)
+        const int jend = min(cnt, jc + 32);
+        const uint32_t chunk = (start - range.x + jc) >> 5;
+        for (int j = jc; j < jend; ++j) {
+          const float4 r0 = s_r0[j], r1 = s_r1[j], r3 = s_r3[j];
+          const float4 r2 = MODE == MODE_PLAIN ? r0 : s_r2[j];
 #pragma unroll
-        for (int p = 0; p < PX; ++p) {
-          if (PX > 1 && done[p]) continue;
-          PairEval e;
-          if (!eval_pair<MODE>(r0, r1, r2, r3.w, fx, (float)(py0 + p) + 0.5f, e)) continue;
-          const float alpha = fminf(e.alpha, amax);
-          if (alpha < amin) continue;
-          const float Tn = __fmaf_rn(-T[p], alpha, T[p]);
-          if (Tn < tstop) {
-            done[p] = true;
-            stop[p] = start + j + 1;
-            if (--active == 0) goto batch_done;  // the only exit test, off the hot path
-            continue;
+          for (int p = 0; p < PX; ++p) {
+            if (PX > 1 && done[p]) continue;
+            PairEval e;
+            if (!eval_pair<MODE>(r0, r1, r2, r3.w, fx, (float)(py0 + p) + 0.5f, e)) continue;
+            const float alpha = fminf(e.alpha, amax);
+            if (alpha < amin) continue;
+            const float Tn = __fmaf_rn(-T[p], alpha, T[p]);
+            if (Tn < tstop) {
+              done[p] = true;
+              stop[p] = start + j + 1;
+              if (REC) mbase[chunk * 256 + pi0 + p * kTile] = mw[p];
+              if (--active == 0) goto batch_done;  // the only exit test, off the hot path
+              continue;
+            }
+            ++blended;
+            if (REC) mw[p] |= 1u << (j & 31);
+            const float w = __fmul_rn(alpha, T[p]);
+            C0[p] = __fmaf_rn(r3.x, w, C0[p]);
+            C1[p] = __fmaf_rn(r3.y, w, C1[p]);
+            C2[p] = __fmaf_rn(r3.z, w, C2[p]);
+            T[p] = Tn;
+            last[p] = start + j + 1 - range.x;
           }
-          ++blended;
-          const float w = __fmul_rn(alpha, T[p]);
-          C0[p] = __fmaf_rn(r3.x, w, C0[p]);
-          C1[p] = __fmaf_rn(r3.y, w, C1[p]);
-          C2[p] = __fmaf_rn(r3.z, w, C2[p]);
-          T[p] = Tn;
-          last[p] = start + j + 1 - range.x;
+        }
+        if (REC) {
+#pragma unroll
+          for (int p = 0; p < PX; ++p)
+            if (!done[p]) {
+              mbase[chunk * 256 + pi0 + p * kTile] = mw[p];
+              mw[p] = 0u;
+            }
         }
       }
     }
@@ -210,7 +245,9 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
   const float* gimg = a.d_images + tc.vi.image_offset;
 
   float T[PX], g0[PX], g1[PX], g2[PX], R0[PX], R1[PX], R2[PX];
-  uint32_t my_end[PX];
+  uint32_t my_end[PX], bw[PX];
+  const int pi0 = (threadIdx.x >> 4) * PX * kTile + (threadIdx.x & (kTile - 1));
+  const uint32_t* mbase = mask_tile_base(a.mask, range, blockIdx.x);
   uint32_t my_max = 0;
 #pragma unroll
   for (int p = 0; p < PX; ++p) {
@@ -249,6 +286,14 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
     __syncthreads();
     for (int j = (int)(bend - bstart) - 1; j >= 0; --j) {
       const uint32_t pos = bstart + j;
+      const uint32_t lp = pos - range.x, bit = lp & 31u;
+      if (bit == 31u || j == (int)(bend - bstart) - 1) {
+        // entering a new chunk from above: this pixel's blend-mask word
+        const uint32_t chunk_first = range.x + (lp & ~31u);
+#pragma unroll
+        for (int p = 0; p < PX; ++p)
+          bw[p] = chunk_first < my_end[p] ? mbase[(lp >> 5) * 256 + pi0 + p * kTile] : 0u;
+      }
       float gr[16];
 #pragma unroll
       for (int k = 0; k < 16; ++k) gr[k] = 0.0f;
@@ -259,14 +304,14 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
       const float a_ = -2.0f * kLn2 * r0.z, b_ = -kLn2 * r0.w, c_ = -2.0f * kLn2 * r1.x;
 #pragma unroll
       for (int p = 0; p < PX; ++p) {
-        if (pos >= my_end[p]) continue;
+        if (!((bw[p] >> bit) & 1u)) continue;  // not blended in the forward pass
         PairEval e;
         if (!eval_pair<MODE>(r0, r1, r2, r3.w, fx, (float)(py0 + p) + 0.5f, e)) continue;
         const float alpha = fminf(e.alpha, amax);
         if (alpha < amin) continue;
         contrib = true;
         const float one_m = 1.0f - alpha;
-        T[p] = T[p] / one_m;  // T_k
+        T[p] = __fdividef(T[p], one_m);  // T_k (alpha <= alpha_max < 1)
         const float w = alpha * T[p];
         gr[G_R] += w * g0[p];
         gr[G_G] += w * g1[p];
@@ -322,11 +367,20 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-template <int PX>
+template <int PX, bool REC>
 static void launch_fwd_px(const RenderArgs& a, int mode, unsigned grid, cudaStream_t st) {
-  if (mode == MODE_PLAIN) render_fwd_kernel<MODE_PLAIN, PX><<<grid, 256 / PX, 0, st>>>(a);
-  else if (mode == MODE_TWO) render_fwd_kernel<MODE_TWO, PX><<<grid, 256 / PX, 0, st>>>(a);
-  else render_fwd_kernel<MODE_SPLIT, PX><<<grid, 256 / PX, 0, st>>>(a);
+  if (mode == MODE_PLAIN) render_fwd_kernel<MODE_PLAIN, PX, REC><<<grid, 256 / PX, 0, st>>>(a);
+  else if (mode == MODE_TWO) render_fwd_kernel<MODE_TWO, PX, REC><<<grid, 256 / PX, 0, st>>>(a);
+  else render_fwd_kernel<MODE_SPLIT, PX, REC><<<grid, 256 / PX, 0, st>>>(a);
+}
+
+template <bool REC>
+static void launch_fwd_rec(const RenderArgs& a, int mode, unsigned grid, cudaStream_t st) {
+  switch (a.px_fwd) {
+    case 1: launch_fwd_px<1, REC>(a, mode, grid, st); break;
+    case 4: launch_fwd_px<4, REC>(a, mode, grid, st); break;
+    default: launch_fwd_px<2, REC>(a, mode, grid, st); break;
+  }
 }
 
 template <int PX>
@@ -339,11 +393,8 @@ static void launch_bwd_px(const RenderArgs& a, int mode, unsigned grid, cudaStre
 cudaError_t launch_render_fwd(const RenderArgs& a, int mode, int64_t total_tiles, cudaStream_t st) {
   if (total_tiles == 0) return cudaSuccess;
   const unsigned grid = (unsigned)total_tiles;
-  switch (a.px_fwd) {
-    case 1: launch_fwd_px<1>(a, mode, grid, st); break;
-    case 4: launch_fwd_px<4>(a, mode, grid, st); break;
-    default: launch_fwd_px<2>(a, mode, grid, st); break;
-  }
+  if (a.mask) launch_fwd_rec<true>(a, mode, grid, st);
+  else launch_fwd_rec<false>(a, mode, grid, st);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -43,7 +43,7 @@ class sr_config(C.Structure):
                 ("t_stop", C.c_float), ("dilation", C.c_float), ("fov_clamp", C.c_float), ("near_z", C.c_float),
                 ("bg", C.c_float * 3), ("antialias_comp", C.c_int32), ("render_blocks_per_sm", C.c_int32),
                 ("sort_spin_limit", C.c_int32), ("fwd_pixels_per_thread", C.c_int32),
-                ("bwd_pixels_per_thread", C.c_int32), ("reserved_", C.c_int32 * 2)]
+                ("bwd_pixels_per_thread", C.c_int32), ("forward_only", C.c_int32), ("reserved_", C.c_int32 * 1)]
 
 
 class sr_grads(C.Structure):
@@ -55,6 +55,7 @@ class sr_plan(C.Structure):
     _fields_ = [("abi_version", C.c_int32), ("n_views", C.c_int32), ("n", C.c_int64), ("sh_degree", C.c_int32),
                 ("tile_w", C.c_int32), ("tile_h", C.c_int32), ("sort_passes", C.c_int32), ("sort_bits", C.c_int32),
                 ("render_mode", C.c_int32), ("two_opacities", C.c_int32), ("has_split", C.c_int32),
+                ("forward_only", C.c_int32), ("reserved1_", C.c_int32),
                 ("key_capacity", C.c_int64), ("total_tiles", C.c_int64), ("total_pixels", C.c_int64),
                 ("tile_base", C.c_int64 * (SR_MAX_VIEWS + 1)), ("image_offset", C.c_int64 * (SR_MAX_VIEWS + 1)),
                 ("pixel_offset", C.c_int64 * (SR_MAX_VIEWS + 1)), ("width", C.c_int32 * SR_MAX_VIEWS),

@@ -37,6 +37,7 @@ class Config:
     sort_spin_limit: int = 0
     fwd_pixels_per_thread: int = 0   # 0: library default (2)
     bwd_pixels_per_thread: int = 0
+    forward_only: bool = False       # plan without backward state (blend masks)
 
     def to_c(self) -> N.sr_config:
         c = N.sr_config()
@@ -49,6 +50,7 @@ class Config:
         c.sort_spin_limit = int(self.sort_spin_limit)
         c.fwd_pixels_per_thread = int(self.fwd_pixels_per_thread)
         c.bwd_pixels_per_thread = int(self.bwd_pixels_per_thread)
+        c.forward_only = 1 if self.forward_only else 0
         return c
 
 
@@ -146,6 +148,15 @@ class Rasterizer:
     @property
     def key_capacity(self) -> int:
         return int(self.plan.key_capacity)
+
+    def set_cameras(self, cameras: list):
+        """Replace the cameras of the plan with views of the same sizes."""
+        cams = [c if isinstance(c, N.sr_camera) else camera_from_dict(c) for c in cameras]
+        if len(cams) != self.n_views or any((c.width, c.height) != (o.width, o.height) for c, o in zip(cams, self.cams)):
+            raise ValueError("set_cameras needs the same number of views with the same sizes")
+        self.cams = cams
+        raw = b"".join(bytes(c) for c in cams)
+        self.cams_dev.copy_(torch.frombuffer(bytearray(raw), dtype=torch.uint8))
 
     def view_image(self, flat: torch.Tensor, v: int) -> torch.Tensor:
         p = self.plan
@@ -323,6 +334,44 @@ class Rasterizer:
     def d2(self) -> torch.Tensor:
         m = self.plan.n * self.n_views
         return self._slot(self._S_D2, 64 * m).view(torch.float32).view(m, 16)
+
+
+def render_views_recompute(g: Gaussians, cameras: list, d_images: list, config: Config | None = None,
+                           rasterizers: dict | None = None):
+    """Forward and backward of several views through one single-view
+    workspace per image size, rebuilding each view's tile key list for its
+    backward instead of keeping it (the key lists, records and blend masks of
+    a view live only while that view is processed).  Returns the images
+    (list of [3,H,W] tensors) and the attribute gradients summed over views.
+    ``rasterizers`` may carry plans from an earlier call (keyed by size)."""
+    config = config or Config()
+    rasterizers = {} if rasterizers is None else rasterizers
+
+    def plan_for(cam):
+        c = cam if isinstance(cam, N.sr_camera) else camera_from_dict(cam)
+        key = (c.width, c.height)
+        if key not in rasterizers:
+            rasterizers[key] = Rasterizer(g, [c], config)
+        r = rasterizers[key]
+        r.set_cameras([c])
+        return r
+
+    images = []
+    for cam in cameras:  # forward: keep only the images
+        r = plan_for(cam)
+        images.append(r.forward(g).view(3, r.plan.height[0], r.plan.width[0]).clone())
+    total = None
+    for cam, dimg in zip(cameras, d_images):  # backward: rebuild the keys, then replay
+        r = plan_for(cam)
+        r.forward(g)
+        gr = r.backward(g, dimg.reshape(-1).contiguous())
+        if total is None:
+            total = gr
+        else:
+            for k, t in gr.items():
+                if t is not None:
+                    total[k] += t
+    return images, total
 
 
 class _RasterizeFn(torch.autograd.Function):

@@ -405,6 +405,21 @@ def test_reduced_precision_storage_error_against_fp32_originals(dt, bound):
     assert d.max() <= bound
 
 
+def test_forward_only_plan_renders_the_same_and_refuses_backward():
+    from paper_2605_18334_gb300 import native as N
+
+    sc = scenes.cluster(seed=34, n=8000)
+    cams = [scenes.identity_camera(160, 96), scenes.identity_camera(64, 64)]
+    r, g = gpu_forward(sc, cams)
+    r_fo, _ = gpu_forward(sc, cams, Config(forward_only=True))
+    assert r_fo.plan.ws_bytes < r.plan.ws_bytes
+    assert torch.equal(r.images, r_fo.images)
+    up = torch.zeros_like(r_fo.images)
+    with pytest.raises(N.SkewRasterError) as e:
+        r_fo.backward(g, up)
+    assert e.value.status == N.SR_ERR_UNSUPPORTED
+
+
 def test_autograd_function():
     from paper_2605_18334_gb300.rasterizer import render
 
@@ -420,3 +435,24 @@ def test_autograd_function():
                                 scenes.upstream_grad(4, 48, 48))
     for t, k in zip(leaves, GRAD_FIELDS):
         assert rel_err(t.grad.cpu().numpy(), og[k]) <= GRAD_RTOL, k
+
+
+def test_recompute_keys_matches_batched_plan():
+    """Several views rendered with the tile key lists rebuilt for the
+    backward (one workspace per image size) give the batched plan's images
+    and gradients."""
+    from paper_2605_18334_gb300.rasterizer import render_views_recompute
+
+    sc = scenes.cluster(seed=35, n=6000, sh_degree=1)
+    cams = scenes.trajectory_cameras(4, resolutions=((96, 64), (64, 48)))
+    cams = [dict(c, c2w_gl=scenes.camera(scenes.look_at_c2w_cv(e, (0, 0, 4)), c["width"], c["height"])["c2w_gl"])
+            for c, e in zip(cams, [(0.3, -0.1, 0.0), (-0.4, 0.2, 0.5), (0.1, 0.3, -0.3), (0.0, 0.0, 0.2)])]
+    r, g = gpu_forward(sc, cams)
+    ups = [torch.as_tensor(scenes.upstream_grad(50 + v, c["height"], c["width"])).cuda() for v, c in enumerate(cams)]
+    flat = torch.cat([u.reshape(-1) for u in ups]).contiguous()
+    ref = r.backward(g, flat)
+    imgs, tot = render_views_recompute(g, cams, ups)
+    for v in range(len(cams)):
+        assert torch.equal(imgs[v], r.view_image(r.images, v))
+    for k in GRAD_FIELDS:
+        assert rel_err(tot[k].cpu().numpy(), ref[k].cpu().numpy()) < 1e-5, k
