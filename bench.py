@@ -159,12 +159,14 @@ def barrier(world):
 
 
 def max_over_ranks(x: float, world: int) -> float:
+    """The largest of the ranks' values (timing only; no data-path collective)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -342,6 +344,26 @@ def variants(args, sc, cam, up, dev, flush):
         res[name] = {"fwd_frames_per_s": round(1e3 / fwd, 2), "fwdbwd_frames_per_s": round(1e3 / fb, 2)}
         del r, g
         torch.cuda.empty_cache()
+    # batched + BF16: 8 views of the orbit at 1080p in one plan, BF16 SH,
+    # log-scale and skew storage, forward and forward+backward
+    from paper_2605_18334_gb300 import scenes
+
+    cams8 = scenes.trajectory_cameras(8, resolutions=((1920, 1080),))
+    g = Gaussians.from_scene(sc, device=dev, sh_dtype=torch.bfloat16, scale_dtype=torch.bfloat16,
+                             skew_dtype=torch.bfloat16)
+    r = Rasterizer(g, cams8, Config(), key_capacity=int(12 * args.n * 8))
+    up8 = torch.cat([torch.as_tensor(scenes.upstream_grad(70 + v, 1080, 1920), device=dev).reshape(-1)
+                     for v in range(8)]).contiguous()
+    r.autotune(g, up8)
+    for _ in range(2):
+        r.forward(g)
+        r.backward(g, up8)
+    fwd = timed(lambda: r.forward(g), K, flush, stream)
+    fb = timed(lambda: (r.forward(g), r.backward(g, up8)), K, flush, stream)
+    res["batched8_bf16"] = {"views": 8, "fwd_frames_per_s": round(8e3 / fwd, 2),
+                            "fwdbwd_frames_per_s": round(8e3 / fb, 2), "keys": int(r.keys)}
+    del r, g
+    torch.cuda.empty_cache()
     return res
 
 

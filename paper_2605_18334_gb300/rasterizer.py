@@ -336,6 +336,24 @@ class Rasterizer:
         return self._slot(self._S_D2, 64 * m).view(torch.float32).view(m, 16)
 
 
+def shard_views(cameras: list, rank: int, world: int) -> list:
+    """Indices of the views rank ``rank`` of ``world`` renders: views are
+    independent, so they are dealt out largest first (by pixel count) to the
+    rank with the least work so far (ties to the lowest rank).  No data moves
+    between ranks; each renders its share with its own plan."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("bad rank / world")
+    size = [int(c["width"]) * int(c["height"]) if isinstance(c, dict) else int(c.width) * int(c.height)
+            for c in cameras]
+    load = [0] * world
+    owner = [0] * len(cameras)
+    for i in sorted(range(len(cameras)), key=lambda k: (-size[k], k)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        owner[i] = r
+        load[r] += size[i]
+    return [i for i in range(len(cameras)) if owner[i] == rank]
+
+
 def render_views_recompute(g: Gaussians, cameras: list, d_images: list, config: Config | None = None,
                            rasterizers: dict | None = None):
     """Forward and backward of several views through one single-view
