@@ -241,7 +241,7 @@ sr_status sr_render_bwd(const sr_plan* plan, const sr_gaussians* g, const sr_cam
  * SR_ERR_CAPACITY; sort_bits in 1..64 and non-NULL distinct pointers, else
  * SR_ERR_INVALID.
  *
- * Scratch: one fixed array of about 16.2 MiB in the library's device memory,
+ * Scratch: one fixed array of about 16 MiB in the library's device memory,
  * present on every GPU that loads the library until the process exits.  The
  * first call on a device looks up that array's device address (with the
  * device current), so make the first call before any CUDA-graph stream

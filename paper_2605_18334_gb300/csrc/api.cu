@@ -241,6 +241,7 @@ static BinArgs bin_args(const sr_plan* p, const sr_config* cfg, void* ws) {
   b.n = p->n;
   b.n_views = p->n_views;
   b.passes = p->sort_passes;
+  b.tile_bits = p->sort_bits - 32;
   b.cap = (unsigned long long)p->key_capacity;
   b.total_tiles = p->total_tiles;
   b.spin_limit = cfg->sort_spin_limit > 0 ? cfg->sort_spin_limit : kDefaultSpin;

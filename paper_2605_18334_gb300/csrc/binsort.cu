@@ -138,10 +138,97 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint32_t*
 // records and writes their keys as one contiguous run: each lane finds the
 // record owning its output slot by a binary search over the lanes' starts
 // and decodes the slot's tile from the owner's packed row spans (coalesced
-// writes).  Records whose tile box is too large for packed spans are written
-// afterwards by their own lane, row by row (row_tile_span).
+// writes).  Records whose tile box is too large for packed spans are then
+// taken one at a time by the whole warp: a lane per tile row computes the
+// row's span (row_tile_span), a warp scan places the rows, and the keys go
+// out 32 at a time by the same owner search.  The digit histograms of the
+// tile sort are counted on the way (keys are written once and not re-read).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) duplicate_kernel(int64_t n, int n_views, const ViewInfo* __restrict__ views,
+// Digit histograms of the tile sort, counted per span of consecutive tile ids
+// [a, a + len) instead of per key.  Digit 0 runs through consecutive values:
+// whole cycles of 256 go to one counter, the rest into a difference array
+// (two or four adds); a higher digit p changes only at multiples of 256^p,
+// so the span splits into a few constant-digit pieces.
+struct TileHist {
+  int diff0[257];            // difference array of digit 0 (partial cycles)
+  uint32_t cycles0;          // whole cycles of digit 0 (each adds 1 to every bin)
+  uint32_t h[kMaxPasses][256];  // digits 1.. (row 0 unused)
+};
+
+__device__ __forceinline__ void tile_hist_span(TileHist& th, int passes, uint32_t a, uint32_t len) {
+  if (len == 0) return;
+  const uint32_t full = len >> 8, rem = len & 0xffu;
+  if (full) atomicAdd(&th.cycles0, full);
+  if (rem) {
+    const uint32_t a0 = a & 0xffu, e0 = a0 + rem;
+    atomicAdd(&th.diff0[a0], 1);
+    if (e0 <= 256u) {
+      atomicAdd(&th.diff0[e0], -1);
+    } else {
+      atomicAdd(&th.diff0[256], -1);
+      atomicAdd(&th.diff0[0], 1);
+      atomicAdd(&th.diff0[e0 - 256u], -1);
+    }
+  }
+  const uint32_t b = a + len - 1;
+  for (int p = 1; p < passes; ++p) {
+    const int sh = 8 * p;
+    const uint32_t unit_mask = sh >= 32 ? 0xffffffffu : ((1u << sh) - 1u);
+    for (uint32_t t = a;;) {
+      const uint32_t seg_end = min(b, t | unit_mask);
+      atomicAdd(&th.h[p][(t >> sh) & 0xffu], seg_end - t + 1u);
+      if (seg_end == b) break;
+      t = seg_end + 1u;
+    }
+  }
+}
+
+// index of the last lane whose (non-decreasing) x is <= q
+__device__ __forceinline__ int warp_owner(uint32_t x, uint32_t q) {
+  int lo = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1) {
+    const uint32_t s = __shfl_sync(0xffffffffu, x, lo + step);
+    if (s <= q) lo += step;
+  }
+  return lo;
+}
+
+// one lane's record in the duplication pipeline
+struct DupFields {
+  uint32_t m, start, cnt, rx, ry, sp0, sp1;
+};
+
+__device__ __forceinline__ void dup_load_index(const uint32_t* __restrict__ perm,
+                                               const uint32_t* __restrict__ offsets, int64_t m_total, int64_t w,
+                                               int lane, uint32_t& m, uint32_t& start) {
+  const int64_t j = w * 32 + lane;
+  if (j < m_total) {
+    m = perm[j];
+    start = offsets[j];
+  } else {
+    m = 0;
+    start = 0xffffffffu;
+  }
+}
+
+__device__ __forceinline__ void dup_load_fields(const uint32_t* __restrict__ ntouch, const uint2* __restrict__ rect,
+                                                const float4* __restrict__ foot, int64_t m_total, int64_t w, int lane,
+                                                DupFields& f) {
+  f.cnt = 0;
+  f.rx = f.ry = f.sp0 = f.sp1 = 0;
+  if (w * 32 + lane < m_total) {
+    f.cnt = ntouch[f.m];
+    const uint2 r = rect[f.m];
+    const uint2 sp = reinterpret_cast<const uint2*>(foot + 2 * (int64_t)f.m + 1)[1];  // f1.zw: packed spans
+    f.rx = r.x;
+    f.ry = r.y;
+    f.sp0 = sp.x;
+    f.sp1 = sp.y;
+  }
+}
+
+__global__ void __launch_bounds__(256, 5) duplicate_kernel(int64_t n, int n_views, const ViewInfo* __restrict__ views,
                                                         const uint32_t* __restrict__ perm,
                                                         const uint32_t* __restrict__ ntouch,
                                                         const uint32_t* __restrict__ offsets,
@@ -149,33 +236,55 @@ __global__ void __launch_bounds__(256) duplicate_kernel(int64_t n, int n_views, 
                                                         const float4* __restrict__ rec,
                                                         const float4* __restrict__ foot,
                                                         uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                                                        unsigned long long cap) {
+                                                        unsigned long long cap, uint32_t* __restrict__ tile_hist,
+                                                        int passes) {
+  __shared__ TileHist th;
+  for (int i = threadIdx.x; i < 257; i += blockDim.x) th.diff0[i] = 0;
+  for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&th.h[0][0])[i] = 0u;
+  if (threadIdx.x == 0) th.cycles0 = 0u;
+  __syncthreads();
   const int64_t m_total = n * n_views;
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w * 32 < m_total; w += warps) {
-    const int64_t j = w * 32 + lane;
-    uint32_t m = 0, cnt = 0, start = 0xffffffffu, tx0 = 0, ty0 = 0, sp0 = 0, sp1 = 0;
+  // Three-stage software pipeline over the warp's groups of 32 records: the
+  // sorted index and key offset of group i+2, then the record fields of
+  // group i+1 (which depend on the index), are in flight while group i is
+  // written.
+  const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  DupFields cur, nxt;
+  uint32_t nn_m = 0, nn_start = 0xffffffffu;
+  dup_load_index(perm, offsets, m_total, w0, lane, cur.m, cur.start);
+  dup_load_fields(ntouch, rect, foot, m_total, w0, lane, cur);
+  dup_load_index(perm, offsets, m_total, w0 + warps, lane, nxt.m, nxt.start);
+  for (int64_t w = w0; w * 32 < m_total; w += warps) {
+    dup_load_fields(ntouch, rect, foot, m_total, w + warps, lane, nxt);
+    dup_load_index(perm, offsets, m_total, w + 2 * warps, lane, nn_m, nn_start);
+    const uint32_t m = cur.m, cnt = cur.cnt, start = cur.start, sp0 = cur.sp0, sp1 = cur.sp1;
+    const uint32_t tx0 = cur.rx & 0xffffu, ty0 = cur.rx >> 16, ty1 = cur.ry >> 16;
+    const bool tall = cnt && sp0 == kSpansTall;
     uint32_t row0 = 0, tiles_x = 0;  // global tile id of (0, ty0) and the view's tiles per row
-    bool tall = false;
-    ViewInfo vi;
-    if (j < m_total) {
-      m = perm[j];
-      cnt = ntouch[m];
-      start = offsets[j];
-      if (cnt) {
-        const uint2 r = rect[m];
-        tx0 = r.x & 0xffffu;
-        ty0 = r.x >> 16;
-        const float4 f1 = foot[2 * (int64_t)m + 1];
-        sp0 = __float_as_uint(f1.z);
-        sp1 = __float_as_uint(f1.w);
-        tall = sp0 == kSpansTall;
-        vi = views[(int)(m / (uint64_t)n)];
-        tiles_x = (uint32_t)vi.tiles_x;
-        row0 = (uint32_t)(vi.tile_base + (int64_t)ty0 * vi.tiles_x);
+    float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 f1xy = make_float2(0.f, 0.f), mu = f1xy;
+    if (cnt) {
+      const ViewInfo& vi = views[(int)(m / (uint64_t)n)];
+      tiles_x = (uint32_t)vi.tiles_x;
+      row0 = (uint32_t)(vi.tile_base + (int64_t)ty0 * vi.tiles_x);
+      if (tall) {  // loaded here, in parallel, for the warp-wide pass below
+        f0 = foot[2 * (int64_t)m];
+        f1xy = reinterpret_cast<const float2*>(foot + 2 * (int64_t)m + 1)[0];
+        mu = reinterpret_cast<const float2*>(rec + 4 * (int64_t)m)[0];
+      } else {
+        // histogram of this record's keys, one call per packed row span
+#pragma unroll
+        for (int rr = 0; rr < kSpanRows; ++rr) {
+          const uint32_t word = (rr < 2 ? sp0 : sp1) >> (16 * (rr & 1));
+          tile_hist_span(th, passes, row0 + (uint32_t)rr * tiles_x + tx0 + (word & 0xffu), (word >> 8) & 0xffu);
+        }
       }
     }
+    cur = nxt;
+    nxt.m = nn_m;
+    nxt.start = nn_start;
     // the run of this warp: [start of lane 0, end of the last valid lane)
     const uint32_t base = __shfl_sync(0xffffffffu, start, 0);
     const uint32_t end = __reduce_max_sync(0xffffffffu, cnt ? start + cnt : 0u);
@@ -186,12 +295,7 @@ __global__ void __launch_bounds__(256) duplicate_kernel(int64_t n, int n_views, 
       const uint32_t q_rel = p - base;
       // owner: the last lane whose start <= q_rel (lanes without tiles share
       // their start with the next lane, whose range then covers q_rel)
-      int lo = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const uint32_t s_rel = __shfl_sync(0xffffffffu, rel, lo + step);
-        if (s_rel <= q_rel) lo += step;
-      }
+      const int lo = warp_owner(rel, q_rel);
       const uint32_t o_rel = __shfl_sync(0xffffffffu, rel, lo);
       const uint32_t o_m = __shfl_sync(0xffffffffu, m, lo);
       const uint32_t o_sp0 = __shfl_sync(0xffffffffu, sp0, lo);
@@ -199,43 +303,98 @@ __global__ void __launch_bounds__(256) duplicate_kernel(int64_t n, int n_views, 
       const uint32_t o_tx0 = __shfl_sync(0xffffffffu, tx0, lo);
       const uint32_t o_row0 = __shfl_sync(0xffffffffu, row0, lo);
       const uint32_t o_tx = __shfl_sync(0xffffffffu, tiles_x, lo);
-      if (p >= end || o_sp0 == kSpansTall) continue;
-      // decode the row of the q-th key from the packed spans
-      uint32_t q = q_rel - o_rel, key = 0;
-      bool found = false;
+      bool on = false;
+      uint32_t key = 0;
+      if (p < end && o_sp0 != kSpansTall) {
+        // decode the row of the q-th key from the packed spans
+        uint32_t q = q_rel - o_rel;
+        bool found = false;
 #pragma unroll
-      for (int rr = 0; rr < kSpanRows; ++rr) {
-        const uint32_t word = (rr < 2 ? o_sp0 : o_sp1) >> (16 * (rr & 1));
-        const uint32_t first = word & 0xffu, num = (word >> 8) & 0xffu;
-        if (!found && q < num) {
-          key = o_row0 + (uint32_t)rr * o_tx + o_tx0 + first + q;
-          found = true;
+        for (int rr = 0; rr < kSpanRows; ++rr) {
+          const uint32_t word = (rr < 2 ? o_sp0 : o_sp1) >> (16 * (rr & 1));
+          const uint32_t first = word & 0xffu, num = (word >> 8) & 0xffu;
+          if (!found && q < num) {
+            key = o_row0 + (uint32_t)rr * o_tx + o_tx0 + first + q;
+            found = true;
+          }
+          if (!found) q -= num;
         }
-        if (!found) q -= num;
+        on = found && p < cap;
       }
-      if (found && p < cap) {
+      if (on) {
         keys[p] = key;
         vals[p] = o_m;
       }
     }
-    if (tall && cnt) {
-      const uint2 r = rect[m];
-      const int ty1 = (int)(r.y >> 16);
-      const float4 f0 = foot[2 * (int64_t)m], f1 = foot[2 * (int64_t)m + 1];
-      const float4 r0 = rec[4 * (int64_t)m];
-      unsigned long long pos = start;
-      const unsigned long long stop = pos + cnt;
-      for (int ty = (int)ty0; ty < ty1; ++ty) {
-        int lo, hi;
-        if (!row_tile_span(f0, f1, r0.x, r0.y, ty, vi.width, vi.height, lo, hi)) continue;
-        const uint32_t row = (uint32_t)(vi.tile_base + (int64_t)ty * vi.tiles_x);
-        for (int tx = lo; tx <= hi; ++tx, ++pos)
-          if (pos < stop && pos < cap) {
-            keys[pos] = row + (uint32_t)tx;
-            vals[pos] = m;
+    // tall records, one at a time across the warp
+    uint32_t pending = __ballot_sync(0xffffffffu, tall);
+    while (pending) {
+      const int src = __ffs(pending) - 1;
+      pending &= pending - 1;
+      const uint32_t tm = __shfl_sync(0xffffffffu, m, src);
+      const uint32_t tstart = __shfl_sync(0xffffffffu, start, src);
+      const uint32_t tcnt = __shfl_sync(0xffffffffu, cnt, src);
+      const int t_ty0 = (int)__shfl_sync(0xffffffffu, ty0, src), t_ty1 = (int)__shfl_sync(0xffffffffu, ty1, src);
+      const float4 g0 = make_float4(__shfl_sync(0xffffffffu, f0.x, src), __shfl_sync(0xffffffffu, f0.y, src),
+                                    __shfl_sync(0xffffffffu, f0.z, src), __shfl_sync(0xffffffffu, f0.w, src));
+      const float4 g1 = make_float4(__shfl_sync(0xffffffffu, f1xy.x, src), __shfl_sync(0xffffffffu, f1xy.y, src),
+                                    0.f, 0.f);
+      const float mx = __shfl_sync(0xffffffffu, mu.x, src), my = __shfl_sync(0xffffffffu, mu.y, src);
+      const ViewInfo& vi = views[(int)(tm / (uint64_t)n)];
+      uint32_t done = 0;  // keys of this record placed by earlier row groups
+      for (int rb = t_ty0; rb < t_ty1; rb += 32) {
+        const int ty = rb + lane;
+        int tlo = 0, thi = -1;
+        const bool ok = ty < t_ty1 && row_tile_span(g0, g1, mx, my, ty, vi.width, vi.height, tlo, thi);
+        const uint32_t num = ok ? (uint32_t)(thi - tlo + 1) : 0u;
+        uint32_t inc = num;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= o) inc += y;
+        }
+        const uint32_t excl = inc - num;
+        const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+        const uint32_t first_key = (uint32_t)(vi.tile_base + (int64_t)ty * vi.tiles_x) + (uint32_t)tlo;
+        // histogram: this lane's row span, up to the record's count
+        tile_hist_span(th, passes, first_key, done + excl >= tcnt ? 0u : min(num, tcnt - done - excl));
+        for (uint32_t c0 = 0; c0 < total; c0 += 32) {
+          const uint32_t q = c0 + lane;
+          const int ow = warp_owner(excl, q);
+          const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, ow);
+          const uint32_t o_key = __shfl_sync(0xffffffffu, first_key, ow);
+          const unsigned long long pos = (unsigned long long)tstart + done + q;
+          const bool on = q < total && done + q < tcnt && pos < cap;
+          const uint32_t key = o_key + (q - o_excl);
+          if (on) {
+            keys[pos] = key;
+            vals[pos] = tm;
           }
+        }
+        done += total;
       }
     }
+  }
+  __syncthreads();
+  // digit 0: prefix sum of the difference array (one warp), plus whole cycles
+  if (threadIdx.x < 32) {
+    int run = 0;
+    for (int c = 0; c < 8; ++c) {
+      const int v = th.diff0[c * 32 + threadIdx.x];
+      int inc = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if ((int)threadIdx.x >= o) inc += y;
+      }
+      const uint32_t cnt0 = (uint32_t)(run + inc) + th.cycles0;
+      if (cnt0) atomicAdd(tile_hist + c * 32 + threadIdx.x, cnt0);
+      run += __shfl_sync(0xffffffffu, inc, 31);
+    }
+  }
+  for (int i = 256 + threadIdx.x; i < passes * 256; i += blockDim.x) {
+    const uint32_t c = (&th.h[0][0])[i];
+    if (c) atomicAdd(tile_hist + i, c);
   }
 }
 
@@ -281,6 +440,10 @@ __global__ void __launch_bounds__(256) hist_scan_kernel(uint32_t* __restrict__ h
 // ---------------------------------------------------------------------------
 // one onesweep radix pass
 // ---------------------------------------------------------------------------
+// Look-back word of (partition, pass, digit): a flag in bits 62-63 (0: not
+// published, kFlagAgg: the partition's count of the digit, kFlagInc: the
+// inclusive prefix of the digit up to and including the partition) and the
+// value below it.
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagInc = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
@@ -292,92 +455,142 @@ struct PassArgs {
   KEY* keys_out;
   uint32_t* vals_out;
   const uint32_t* digit_base;     // exclusive digit offsets of this pass
-  unsigned long long* lookback;   // [parts][passes][256], zeroed per frame
+  unsigned long long* lookback;   // [parts][passes][256] look-back words, zeroed per frame
   uint32_t* part_counter;         // partition tickets of this pass (zeroed)
   const unsigned long long* count_dev;  // element count on the device, or nullptr
   unsigned long long count;       // element count (count_dev == nullptr) or the capacity bound
   Status* st;                     // status flags (timeouts)
+  uint2* ranges;                  // last pass of the tile sort: tile ranges to reduce into, else nullptr
+  unsigned long long n_tiles;     // number of tiles (bounds the range writes)
+  int sorted_buf;                 // last pass of the tile sort: index of the output buffer
   int passes;
   int pass;
   int shift;
+  int bits;                       // digit width of this pass (8, less on the last pass of a narrower key)
   int spin_limit;
 };
+
+// shared memory of one onesweep block: the partition's keys and values in
+// their block-local sorted order, per-warp digit counts, digit starts
+template <class KEY>
+struct SortSmem {
+  KEY key[kSortPart];
+  uint32_t val[kSortPart];
+  uint32_t whist[kSortThreads / 32][256];
+  uint32_t lstart[256];
+  unsigned long long gofs[256];
+  unsigned long long warp_tot[kSortThreads / 32];
+  uint32_t part;
+};
+
+constexpr int kLookbackWindow = 4;  // look-back words in flight per digit
 
 template <class KEY>
 __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(PassArgs<KEY> a) {
   constexpr int NW = kSortThreads / 32;
-  __shared__ KEY s_buf[kSortPart];  // keys, then values (as u32) in the scatter phase
-  __shared__ uint32_t s_whist[NW][256];
-  __shared__ uint32_t s_lstart[256];
-  __shared__ unsigned long long s_gbase[256];
-  __shared__ unsigned long long s_warp[NW];
-  __shared__ uint8_t s_dig[kSortPart];
-  __shared__ uint32_t s_part;
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  SortSmem<KEY>& sm = *reinterpret_cast<SortSmem<KEY>*>(s_raw);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t dmask = (1u << a.bits) - 1u;  // this pass's digit: bits [shift, shift + bits)
   const unsigned long long kn = element_count(a.count_dev, a.count);
   const unsigned long long nparts = (kn + kSortPart - 1) / kSortPart;
-  if (tid == 0) s_part = atomicAdd(a.part_counter, 1u);
-  for (int i = tid; i < NW * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0u;
+  if (tid == 0) sm.part = atomicAdd(a.part_counter, 1u);
+  for (int i = tid; i < NW * 256; i += kSortThreads) (&sm.whist[0][0])[i] = 0u;
   __syncthreads();
-  const unsigned long long part = s_part;
+  const unsigned long long part = sm.part;
   if (part >= nparts) return;
   const unsigned long long base = part * kSortPart;
+  // warp-blocked: warp w owns elements [w*512, (w+1)*512) of the partition;
+  // element j of this thread is wbase + 32 j, valid while 32 j < rem
+  const unsigned long long wbase = base + (unsigned long long)warp * (32 * kSortItems) + lane;
+  const int rem = wbase >= kn ? 0 : (kn - wbase < 32ull * kSortItems ? (int)(kn - wbase) : 32 * kSortItems);
 
-  // load, warp-blocked: warp w owns keys [w*512, (w+1)*512) of the partition
+  // all key and value loads first, so a thread's 32 reads are in flight together
   KEY key[kSortItems];
-  uint32_t rank[kSortItems];
+  uint32_t val[kSortItems];
+  const KEY* kp = a.keys_in + wbase;
+#pragma unroll
+  for (int j = 0; j < kSortItems; ++j) key[j] = 32 * j < rem ? kp[32 * j] : (KEY)~(KEY)0;
+  if (a.vals_in) {
+    const uint32_t* vp = a.vals_in + wbase;
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) val[j] = 32 * j < rem ? vp[32 * j] : 0u;
+  } else {
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) val[j] = (uint32_t)wbase + 32 * j;
+  }
+
+  // rank inside the warp (lanes holding the same digit are peers); ranks are
+  // below 512, two to a register
+  uint32_t rank2[kSortItems / 2];
   const uint32_t lt = lanemask_lt();
 #pragma unroll
   for (int j = 0; j < kSortItems; ++j) {
-    const unsigned long long idx = base + (unsigned long long)warp * (32 * kSortItems) + j * 32 + lane;
-    const bool valid = idx < kn;
-    key[j] = valid ? a.keys_in[idx] : (KEY)~(KEY)0;
+    const bool valid = 32 * j < rem;
     const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
     if (valid) {
-      const uint32_t d = (uint32_t)(key[j] >> a.shift) & 0xffu;
+      const uint32_t d = (uint32_t)(key[j] >> a.shift) & dmask;
       const uint32_t peers = __match_any_sync(vmask, d);
-      const uint32_t prev = s_whist[warp][d];
+      const uint32_t prev = sm.whist[warp][d];
       __syncwarp(vmask);
-      if ((peers & lt) == 0) s_whist[warp][d] = prev + __popc(peers);
+      if ((peers & lt) == 0) sm.whist[warp][d] = prev + __popc(peers);
       __syncwarp(vmask);
-      rank[j] = prev + __popc(peers & lt);
-    } else {
-      rank[j] = 0u;
+      const uint32_t r = prev + __popc(peers & lt);
+      rank2[j >> 1] = (j & 1) ? (rank2[j >> 1] | (r << 16)) : r;
+    } else if (!(j & 1)) {
+      rank2[j >> 1] = 0u;
     }
     __syncwarp();
   }
   __syncthreads();
 
-  // per digit: counts across warps -> warp offsets; publish and look back
+  // per digit (thread d): counts across warps -> warp offsets; publish the
+  // partition's count of digit d
   const int d = tid;  // kSortThreads == 256 digits
   uint32_t tot = 0;
 #pragma unroll
   for (int w = 0; w < NW; ++w) {
-    const uint32_t c = s_whist[w][d];
-    s_whist[w][d] = tot;
+    const uint32_t c = sm.whist[w][d];
+    sm.whist[w][d] = tot;
     tot += c;
   }
   unsigned long long* lb = a.lookback + (part * a.passes + a.pass) * 256;
   st_relaxed_u64(lb + d, (part == 0 ? kFlagInc : kFlagAgg) | tot);
+
+  // block-local order: digit starts, then keys and values into shared memory
+  unsigned long long total;
+  sm.lstart[d] = (uint32_t)block_exclusive_u64<kSortThreads>(tot, sm.warp_tot, total);
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kSortItems; ++j) {
+    if (32 * j < rem) {
+      const uint32_t dg = (uint32_t)(key[j] >> a.shift) & dmask;
+      const uint32_t lpos = sm.lstart[dg] + sm.whist[warp][dg] + ((rank2[j >> 1] >> (16 * (j & 1))) & 0xffffu);
+      sm.key[lpos] = key[j];
+      sm.val[lpos] = val[j];
+    }
+  }
+
+  // decoupled look-back over the predecessors' words of digit d, a window of
+  // kLookbackWindow loads in flight: aggregates are summed, an inclusive
+  // prefix ends the walk, a word not yet published is polled again (at most
+  // spin_limit times)
   unsigned long long excl = 0;
   if (part > 0) {
-    // walk back over the predecessors' words of this digit, four loads in
-    // flight at a time: aggregates are summed, an inclusive prefix ends the
-    // walk, a word not yet published is polled again (at most spin_limit times)
-    constexpr int kWin = 4;
     const unsigned long long stride = (unsigned long long)a.passes * 256;
     const unsigned long long* col = a.lookback + (unsigned long long)a.pass * 256 + d;
     long long q = (long long)part - 1;
     int spins = 0;
     bool walking = true;
     while (walking) {
-      unsigned long long w[kWin];
+      unsigned long long w[kLookbackWindow];
 #pragma unroll
-      for (int k = 0; k < kWin; ++k) w[k] = q - k >= 0 ? ld_relaxed_u64(col + (unsigned long long)(q - k) * stride) : 0ull;
+      for (int k = 0; k < kLookbackWindow; ++k)
+        w[k] = q - k >= 0 ? ld_relaxed_u64(col + (unsigned long long)(q - k) * stride) : 0ull;
       bool stalled = false;
 #pragma unroll
-      for (int k = 0; k < kWin; ++k) {
+      for (int k = 0; k < kLookbackWindow; ++k) {
         if (!walking || stalled || q < 0) continue;
         const unsigned long long v = w[k];
         if (v & kFlagInc) {
@@ -403,46 +616,30 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(PassArgs<KEY>
     }
     st_relaxed_u64(lb + d, kFlagInc | (excl + tot));
   }
-  s_gbase[d] = (unsigned long long)a.digit_base[d] + excl;
-
-  // local digit starts (exclusive scan of tot over digits)
-  unsigned long long total;
-  s_lstart[d] = (uint32_t)block_exclusive_u64<kSortThreads>(tot, s_warp, total);
+  // global position of local element i of digit dg: gofs[dg] + i
+  sm.gofs[d] = (unsigned long long)a.digit_base[d] + excl - sm.lstart[d];
   __syncthreads();
 
-  // local positions, keys through shared memory
-  uint32_t lpos[kSortItems];
-#pragma unroll
-  for (int j = 0; j < kSortItems; ++j) {
-    const unsigned long long idx = base + (unsigned long long)warp * (32 * kSortItems) + j * 32 + lane;
-    if (idx < kn) {
-      const uint32_t dg = (uint32_t)(key[j] >> a.shift) & 0xffu;
-      lpos[j] = s_lstart[dg] + s_whist[warp][dg] + rank[j];
-      s_buf[lpos[j]] = key[j];
+  // scatter in block-local order, so each digit's run goes out contiguously
+  const uint32_t count = (uint32_t)((kn - base) < (unsigned long long)kSortPart ? (kn - base) : kSortPart);
+#pragma unroll 4
+  for (uint32_t i = tid; i < count; i += kSortThreads) {
+    const KEY k = sm.key[i];
+    const uint32_t dg = (uint32_t)(k >> a.shift) & dmask;
+    const unsigned long long g = sm.gofs[dg] + i;
+    if (g < kn) {  // always true unless a look-back gave up
+      a.keys_out[g] = k;
+      a.vals_out[g] = sm.val[i];
+      // after the last pass the keys are sorted, and the equal keys of this
+      // partition are one run in block-local order: its ends bound the tile's
+      // range (partitions combine by atomicMax on (~start, end))
+      if (a.ranges && (unsigned long long)k < a.n_tiles) {
+        if (i == 0 || sm.key[i - 1] != k) atomicMax(&a.ranges[k].x, ~(uint32_t)g);
+        if (i + 1 == count || sm.key[i + 1] != k) atomicMax(&a.ranges[k].y, (uint32_t)(g + 1));
+      }
     }
   }
-  __syncthreads();
-  const uint32_t count = (uint32_t)((kn - base) < (unsigned long long)kSortPart ? (kn - base) : kSortPart);
-  for (uint32_t i = tid; i < count; i += kSortThreads) {
-    const KEY k = s_buf[i];
-    const uint32_t dg = (uint32_t)(k >> a.shift) & 0xffu;
-    s_dig[i] = (uint8_t)dg;
-    const unsigned long long g = s_gbase[dg] + (i - s_lstart[dg]);
-    if (g < kn) a.keys_out[g] = k;  // always true unless a look-back gave up
-  }
-  __syncthreads();
-  uint32_t* s_val = reinterpret_cast<uint32_t*>(s_buf);
-#pragma unroll
-  for (int j = 0; j < kSortItems; ++j) {
-    const unsigned long long idx = base + (unsigned long long)warp * (32 * kSortItems) + j * 32 + lane;
-    if (idx < kn) s_val[lpos[j]] = a.vals_in ? a.vals_in[idx] : (uint32_t)idx;
-  }
-  __syncthreads();
-  for (uint32_t i = tid; i < count; i += kSortThreads) {
-    const uint32_t dg = s_dig[i];
-    const unsigned long long g = s_gbase[dg] + (i - s_lstart[dg]);
-    if (g < kn) a.vals_out[g] = s_val[i];
-  }
+  if (a.ranges && part == 0 && tid == 0) a.st->sorted_buf = (uint32_t)a.sorted_buf;
 }
 
 // ---------------------------------------------------------------------------
@@ -456,7 +653,7 @@ __global__ void __launch_bounds__(256) ranges_kernel(const uint32_t* __restrict_
   for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < kn;
        k += (unsigned long long)gridDim.x * blockDim.x) {
     const uint32_t t = keys[k];
-    if (k == 0 || keys[k - 1] != t) ranges[t].x = (uint32_t)k;
+    if (k == 0 || keys[k - 1] != t) ranges[t].x = ~(uint32_t)k;
     if (k + 1 == kn || keys[k + 1] != t) ranges[t].y = (uint32_t)(k + 1);
   }
 }
@@ -477,8 +674,15 @@ template <class KEY>
 static int run_passes(const KEY* keys_in, const uint32_t* vals_in, KEY* const* kbuf, uint32_t* const* vbuf,
                       const uint32_t* hist, unsigned long long* lookback, uint32_t* part_counter,
                       const unsigned long long* count_dev, unsigned long long count, unsigned long long parts,
-                      int passes, const int* run, Status* status, int spin_limit, cudaStream_t st) {
+                      int passes, int key_bits, const int* run, Status* status, int spin_limit,
+                      cudaStream_t st, uint2* ranges = nullptr, unsigned long long n_tiles = 0,
+                      const int* buf_ids = nullptr) {
   int cur = -1;  // -1: still the input
+  int last = -1;
+  for (int p = 0; p < passes; ++p)
+    if (!run || run[p]) last = p;
+  // above the 48 KB default; a host-side attribute, no stream work
+  cudaFuncSetAttribute(onesweep_kernel<KEY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SortSmem<KEY>));
   for (int p = 0; p < passes; ++p) {
     if (run && !run[p]) continue;
     const int out = cur == 0 ? 1 : 0;
@@ -496,8 +700,12 @@ static int run_passes(const KEY* keys_in, const uint32_t* vals_in, KEY* const* k
     pa.passes = passes;
     pa.pass = p;
     pa.shift = 8 * p;
+    pa.bits = std::max(1, std::min(8, key_bits - 8 * p));
     pa.spin_limit = spin_limit;
-    onesweep_kernel<KEY><<<(unsigned)parts, kSortThreads, 0, st>>>(pa);
+    pa.ranges = p == last ? ranges : nullptr;
+    pa.n_tiles = n_tiles;
+    pa.sorted_buf = (p == last && buf_ids) ? buf_ids[out] : 0;
+    onesweep_kernel<KEY><<<(unsigned)parts, kSortThreads, sizeof(SortSmem<KEY>), st>>>(pa);
     count_launches(1);
     cur = out;
   }
@@ -527,7 +735,7 @@ cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms) {
     uint32_t* const kb[2] = {a.ws.dkey[1], a.ws.dkey[0]};
     uint32_t* const vb[2] = {a.ws.perm[1], a.ws.perm[0]};
     const int r = run_passes<uint32_t>(a.ws.dkey[0], nullptr, kb, vb, a.ws.hist, a.ws.lookback_d,
-                                       a.ws.status->part_counter, nullptr, um, dparts, kDepthPasses, nullptr,
+                                       a.ws.status->part_counter, nullptr, um, dparts, kDepthPasses, 32, nullptr,
                                        a.ws.status, a.spin_limit, st);
     perm = vb[r];
   }
@@ -540,18 +748,16 @@ cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms) {
   count_launches(1);
   if (m > 0) {
     scan_down_kernel<<<nb, kScanThreads, 0, st>>>(a.ws.ntouch, perm, m, a.ws.scan_part, a.ws.offsets);
-    duplicate_kernel<<<clamp_grid((m + 255) / 256, sms, 8), 256, 0, st>>>(
+    // keys and the tile sort's digit histograms
+    duplicate_kernel<<<clamp_grid((m + 255) / 256, sms, 5), 256, 0, st>>>(
         a.n, a.n_views, a.ws.views, perm, a.ws.ntouch, a.ws.offsets, a.ws.rect, a.ws.rec, a.ws.foot, a.ws.keys[0],
-        a.ws.vals[0], a.cap);
+        a.ws.vals[0], a.cap, a.ws.hist + kMaxPasses * 256, a.passes);
     count_launches(2);
   }
   if (a.passes > 0) {
-    uint32_t* th = a.ws.hist + kMaxPasses * 256;
-    histogram_kernel<uint32_t><<<clamp_grid((a.cap + 255) / 256, sms, 4), 256, 0, st>>>(
-        a.ws.keys[0], &a.ws.status->keys_needed, a.cap, a.passes, th);
-    hist_scan_kernel<<<a.passes, 256, 0, st>>>(th, a.ws.status->pass_trivial + kMaxPasses,
+    hist_scan_kernel<<<a.passes, 256, 0, st>>>(a.ws.hist + kMaxPasses * 256, a.ws.status->pass_trivial + kMaxPasses,
                                                &a.ws.status->keys_needed, a.cap);
-    count_launches(2);
+    count_launches(1);
   }
   return cudaGetLastError();
 }
@@ -562,23 +768,26 @@ cudaError_t launch_bin_phase2(const BinArgs& a, const int* run, long long keys_k
   const unsigned long long kn = keys_known >= 0 ? (unsigned long long)keys_known : a.cap;
   const unsigned long long parts = (kn + kSortPart - 1) / kSortPart;
   cudaError_t e;
-  int cur = 0;  // index into ws.keys / ws.vals of the sorted result
+  int r = -1;  // buffer of kb/vb holding the sorted result, -1: no pass ran
   if (parts > 0 && a.passes > 0) {
     if ((e = cudaMemsetAsync(a.ws.lookback, 0, sizeof(unsigned long long) * 256 * a.passes * parts, st)) !=
         cudaSuccess)
       return e;
     uint32_t* const kb[2] = {a.ws.keys[1], a.ws.keys[0]};
     uint32_t* const vb[2] = {a.ws.vals[1], a.ws.vals[0]};
-    const int r = run_passes<uint32_t>(a.ws.keys[0], a.ws.vals[0], kb, vb, a.ws.hist + kMaxPasses * 256,
-                                       a.ws.lookback, a.ws.status->part_counter + kMaxPasses,
-                                       &a.ws.status->keys_needed, a.cap, parts, a.passes, run, a.ws.status,
-                                       a.spin_limit, st);
-    cur = r < 0 ? 0 : (r == 0 ? 1 : 0);  // kb[0] is ws.keys[1]
+    const int ws_index[2] = {1, 0};  // kb[i] is ws.keys[ws_index[i]]
+    // the last pass also reduces the tile ranges and records the buffer
+    r = run_passes<uint32_t>(a.ws.keys[0], a.ws.vals[0], kb, vb, a.ws.hist + kMaxPasses * 256, a.ws.lookback,
+                             a.ws.status->part_counter + kMaxPasses, &a.ws.status->keys_needed, a.cap, parts,
+                             a.passes, a.tile_bits, run, a.ws.status, a.spin_limit, st, a.ws.ranges,
+                             (unsigned long long)a.total_tiles, ws_index);
   }
-  const unsigned grid = (unsigned)std::max<unsigned long long>(1, std::min<unsigned long long>((kn + 255) / 256,
-                                                                                               1ull << 20));
-  ranges_kernel<<<grid, 256, 0, st>>>(a.ws.keys[cur], a.ws.status, a.cap, a.ws.ranges, cur);
-  count_launches(1);
+  if (r < 0) {  // no pass ran (one tile, or every pass trivial): ranges from the unsorted-equals-sorted keys
+    const unsigned grid = (unsigned)std::max<unsigned long long>(1, std::min<unsigned long long>((kn + 255) / 256,
+                                                                                                 1ull << 20));
+    ranges_kernel<<<grid, 256, 0, st>>>(a.ws.keys[0], a.ws.status, a.cap, a.ws.ranges, 0);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 
@@ -609,7 +818,7 @@ cudaError_t launch_selftest_bounded_wait(const Ws& ws, unsigned long long cap, i
   uint32_t* const vb[2] = {ws.vals[1], ws.vals[0]};
   count_launches(1);
   run_passes<uint32_t>(ws.keys[0], nullptr, kb, vb, th, ws.lookback, ws.status->part_counter + kMaxPasses, nullptr,
-                       n, parts, 1, nullptr, ws.status, spin_limit, st);
+                       n, parts, 1, 8, nullptr, ws.status, spin_limit, st);
   return cudaGetLastError();
 }
 
@@ -625,7 +834,7 @@ cudaError_t launch_selftest_bounded_wait(const Ws& ws, unsigned long long cap, i
 // (one ping-pong key/value buffer, the digit histograms, the look-back state
 // and the status word) lives in one file-scope device array of fixed size,
 // so the call allocates nothing; every GPU that loads this library holds the
-// array (about 16.2 MiB) until the process exits.
+// array (about 16 MiB) until the process exits.
 // ---------------------------------------------------------------------------
 namespace sr {
 
@@ -727,7 +936,7 @@ extern "C" sr_status sr_sort_keys_noalloc(const uint64_t* keys_in, const uint32_
   uint32_t* const vb[2] = {(passes & 1) ? vals_out : tmp_vals, (passes & 1) ? tmp_vals : vals_out};
   const u64 parts = (un + kSortPart - 1) / kSortPart;
   run_passes<u64>(reinterpret_cast<const u64*>(keys_in), vals_in, kb, vb, hist, lookback, status->part_counter,
-                  nullptr, un, parts, passes, nullptr, status, 1 << 20, st);
+                  nullptr, un, parts, passes, 8 * passes, nullptr, status, 1 << 20, st);
   count_launches(3);
   return cudaGetLastError() == cudaSuccess ? SR_OK : SR_ERR_CUDA;
 }

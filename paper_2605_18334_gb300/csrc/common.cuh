@@ -232,6 +232,14 @@ __device__ __forceinline__ bool row_tile_span(const float4& f0, const float4& f1
   return true;
 }
 
+// Tile ranges: [start, end) of each tile's run in the sorted key list, stored
+// as (~start, end) so that both ends can be reduced with atomicMax into a
+// zero-initialised array; end == 0 marks an empty tile.
+__device__ __forceinline__ uint2 tile_range(const uint2* ranges, int64_t tile) {
+  const uint2 v = ranges[tile];
+  return v.y ? make_uint2(~v.x, v.y) : make_uint2(0u, 0u);
+}
+
 // Row spans of a record's touched tiles, packed for the key emission: for a
 // tile box of at most kSpanRows rows and 255 columns, 8 bits of first column
 // (relative to the box) and 8 bits of count per row, two rows per 32-bit

@@ -27,6 +27,7 @@ struct BinArgs {        // binning and sort
   int64_t n;
   int n_views;
   int passes;
+  int tile_bits;        // significant bits of the global tile ids (passes = ceil(tile_bits / 8))
   unsigned long long cap;
   int64_t total_tiles;
   int spin_limit;

@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
   const int py0 = tc.ty * kTile + (threadIdx.x >> 4) * PX;
   const int pi0 = (threadIdx.x >> 4) * PX * kTile + (threadIdx.x & (kTile - 1));  // pixel index in the tile
   const float fx = (float)px + 0.5f;
-  const uint2 range = a.ranges[blockIdx.x];
+  const uint2 range = tile_range(a.ranges, blockIdx.x);
   const uint32_t* vals = a.status->sorted_buf ? a.vals1 : a.vals0;
   const float amin = a.cfg.alpha_min, amax = a.cfg.alpha_max, tstop = a.cfg.t_stop;
   uint32_t* mbase = REC ? mask_tile_base(a.mask, range, blockIdx.x) : nullptr;
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
   const int px = tc.tx * kTile + (threadIdx.x & (kTile - 1));
   const int py0 = tc.ty * kTile + (threadIdx.x >> 4) * PX;
   const float fx = (float)px + 0.5f;
-  const uint2 range = a.ranges[blockIdx.x];
+  const uint2 range = tile_range(a.ranges, blockIdx.x);
   const uint32_t* vals = a.status->sorted_buf ? a.vals1 : a.vals0;
   const float amin = a.cfg.alpha_min, amax = a.cfg.alpha_max;
   const int lane = threadIdx.x & 31;
