@@ -235,12 +235,30 @@ __device__ __forceinline__ void project(const Attr& A, const sr_camera& c, const
   P.my = c.fy * P.t[1] / tz + c.cy;
 }
 
+// three consecutive elements of a storage-typed array, the three loads in
+// one branch of the (warp-uniform) type switch so they issue back to back
+__device__ __forceinline__ void ld3_dyn(const void* p, int dt, int64_t i, float* out) {
+  if (dt == SR_F32) {
+    const float* f = static_cast<const float*>(p) + i;
+    const float x = __ldg(f), y = __ldg(f + 1), z = __ldg(f + 2);
+    out[0] = x; out[1] = y; out[2] = z;
+  } else if (dt == SR_BF16) {
+    const __nv_bfloat16* h = static_cast<const __nv_bfloat16*>(p) + i;
+    const __nv_bfloat16 x = h[0], y = h[1], z = h[2];
+    out[0] = __bfloat162float(x); out[1] = __bfloat162float(y); out[2] = __bfloat162float(z);
+  } else {
+    const __half* h = static_cast<const __half*>(p) + i;
+    const __half x = h[0], y = h[1], z = h[2];
+    out[0] = __half2float(x); out[1] = __half2float(y); out[2] = __half2float(z);
+  }
+}
+
 __device__ __forceinline__ void load_attr(const sr_gaussians& g, int64_t i, bool has_split, Attr& A) {
   const float* means = static_cast<const float*>(g.means);
   A.mu[0] = __ldg(means + 3 * i);
   A.mu[1] = __ldg(means + 3 * i + 1);
   A.mu[2] = __ldg(means + 3 * i + 2);
-  for (int k = 0; k < 3; ++k) A.ls[k] = ld_dyn(g.log_scales, g.dt_scale, 3 * i + k);
+  ld3_dyn(g.log_scales, g.dt_scale, 3 * i, A.ls);
   const float4 q = __ldg(reinterpret_cast<const float4*>(g.quats) + i);
   A.qr[0] = q.x;
   A.qr[1] = q.y;
@@ -254,8 +272,12 @@ __device__ __forceinline__ void load_attr(const sr_gaussians& g, int64_t i, bool
     A.l1 = __ldg(op + i);
     A.l2 = A.l1;
   }
-  for (int k = 0; k < 3; ++k) A.eta[k] = ld_dyn(g.skew, g.dt_skew, 3 * i + k);
-  for (int k = 0; k < 3; ++k) A.dsp[k] = has_split ? ld_dyn(g.split_dir, g.dt_skew, 3 * i + k) : 0.0f;
+  ld3_dyn(g.skew, g.dt_skew, 3 * i, A.eta);
+  if (has_split) {
+    ld3_dyn(g.split_dir, g.dt_skew, 3 * i, A.dsp);
+  } else {
+    A.dsp[0] = A.dsp[1] = A.dsp[2] = 0.0f;
+  }
 }
 
 
@@ -293,6 +315,19 @@ __host__ __device__ constexpr size_t cams_bytes(int n_views) { return (sizeof(sr
 template <int K3, int DT_SH>
 __device__ __forceinline__ void stage_sh(const void* sh, int64_t base, int cnt, float* s, int lane) {
   const int64_t off = base * K3;
+  if (cnt == 32) {
+    // a full group: every load is issued before the first store, so the
+    // group's K3 coalesced loads wait on one memory latency, not K3
+    float v[K3];
+#pragma unroll
+    for (int i = 0; i < K3; ++i) v[i] = ld<DT_SH>(sh, off + lane + 32 * i);
+#pragma unroll
+    for (int i = 0; i < K3; ++i) {
+      const int w = lane + 32 * i, g = w / K3, k = w - g * K3;
+      s[g * (K3 + 1) + k] = v[i];
+    }
+    return;
+  }
   for (int w = lane; w < cnt * K3; w += 32) {
     const int g = w / K3, k = w - g * K3;
     s[g * (K3 + 1) + k] = ld<DT_SH>(sh, off + w);
