@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for the CPU baseline")
     ap.add_argument("--workload", default="unbounded_1m", choices=["unbounded_1m", "mixed_5m"])
+    ap.add_argument("--fwd-px", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="forward pixels per thread (0: autotune)")
+    ap.add_argument("--bwd-px", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="backward pixels per thread (0: autotune)")
     return ap.parse_args()
 
 
@@ -197,7 +201,12 @@ def run_ours(args):
             return rr.backward(gs, dimg)
         return None
 
-    tune = r.autotune(g, d_img)
+    if args.fwd_px and args.bwd_px:  # fixed launch shapes (e.g. for a profiler run)
+        r.set_pixels_per_thread(args.fwd_px, args.bwd_px)
+        tune = {"fwd_pixels_per_thread": args.fwd_px, "bwd_pixels_per_thread": args.bwd_px, "fwd_ms": {},
+                "bwd_ms": {}, "fixed": True}
+    else:
+        tune = r.autotune(g, d_img)
     for _ in range(max(3, args.warmup)):
         step(g, r, d_img)
     torch.cuda.synchronize()
@@ -240,7 +249,7 @@ def run_ours(args):
 
     cfgd = config_dict(args.n)
     cfgd["launch"] = {"fwd_pixels_per_thread": tune["fwd_pixels_per_thread"],
-                      "bwd_pixels_per_thread": tune["bwd_pixels_per_thread"], "autotuned": True}
+                      "bwd_pixels_per_thread": tune["bwd_pixels_per_thread"], "autotuned": not tune.get("fixed")}
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K,
            "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfgd,

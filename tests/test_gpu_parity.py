@@ -456,3 +456,31 @@ def test_recompute_keys_matches_batched_plan():
         assert torch.equal(imgs[v], r.view_image(r.images, v))
     for k in GRAD_FIELDS:
         assert rel_err(tot[k].cpu().numpy(), ref[k].cpu().numpy()) < 1e-5, k
+
+
+def test_unbounded_1m_1080p_in_the_bench_launch_configuration():
+    """The timed workload at full size (1M skew Gaussians, SH 3, 1920x1080,
+    key capacity 12 N, the autotuned launch shapes): depth keys and tile
+    counts of all 1M Gaussians and the whole sorted key list bit-exact, the
+    image at 2,048 sampled pixels (plus the four corners), and the gradients
+    of an upstream gradient that is nonzero on 256 random pixels, all against
+    the oracle."""
+    sc = scenes.unbounded(seed=2, n=1_000_000)
+    cam = scenes.orbit_camera(0.0, 1920, 1080)
+    g = Gaussians.from_scene(sc)
+    r = Rasterizer(g, [cam], Config(), key_capacity=12 * sc.n)
+    up_dense = torch.as_tensor(scenes.upstream_grad(2, 1080, 1920)).cuda().reshape(-1).contiguous()
+    r.autotune(g, up_dense)
+    r.forward(g)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(11)
+    pix = np.stack([rng.integers(0, 1920, 2048), rng.integers(0, 1080, 2048)], 1)
+    pix = np.concatenate([pix, [[0, 0], [1919, 0], [0, 1079], [1919, 1079]]]).astype(np.int32)
+    stats, _, _ = check_view(r, sc, [cam], 0, Config(), pixels=pix)
+    assert stats["keys"] > 6_000_000
+    up, flat = scenes.sparse_upstream_grad(3, 1080, 1920, 256)
+    gr = r.backward(g, torch.as_tensor(up).cuda().reshape(-1).contiguous())
+    pix_b = np.stack([flat % 1920, flat // 1920], 1).astype(np.int32)
+    og = oracle.render_backward(sc, oracle.camera_from_gl(cam), oracle_config(Config()),
+                                up.reshape(3, -1)[:, flat].T, pixels=pix_b)
+    compare_grads(gr, og, GRAD_FIELDS)
