@@ -284,16 +284,26 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
       for (int k = 0; k < 16; ++k) s_acc[k][q] = 0.0f;
     }
     __syncthreads();
-    for (int j = (int)(bend - bstart) - 1; j >= 0; --j) {
-      const uint32_t pos = bstart + j;
-      const uint32_t lp = pos - range.x, bit = lp & 31u;
-      if (bit == 31u || j == (int)(bend - bstart) - 1) {
-        // entering a new chunk from above: this pixel's blend-mask word
-        const uint32_t chunk_first = range.x + (lp & ~31u);
+    // walk the batch from the top, one 32-position mask chunk at a time; the
+    // warp visits only the positions one of its lanes blended, in descending
+    // order (the replay recovers T and the colour behind from the top down)
+    for (int jhi = (int)(bend - bstart) - 1; jhi >= 0;) {
+      const uint32_t lp_hi = bstart + (uint32_t)jhi - range.x;
+      const uint32_t chunk = lp_hi >> 5;
+      const uint32_t chunk_first = range.x + (chunk << 5);  // position of bit 0
+      const int jlo = chunk_first > bstart ? (int)(chunk_first - bstart) : 0;
 #pragma unroll
-        for (int p = 0; p < PX; ++p)
-          bw[p] = chunk_first < my_end[p] ? mbase[(lp >> 5) * 256 + pi0 + p * kTile] : 0u;
-      }
+      for (int p = 0; p < PX; ++p)
+        bw[p] = chunk_first < my_end[p] ? mbase[chunk * 256 + pi0 + p * kTile] : 0u;
+      uint32_t mine = 0u;
+#pragma unroll
+      for (int p = 0; p < PX; ++p) mine |= bw[p];
+      const uint32_t hi_bit = (uint32_t)jhi + bstart - chunk_first, lo_bit = (uint32_t)jlo + bstart - chunk_first;
+      uint32_t todo = __reduce_or_sync(0xffffffffu, mine) & ((2u << hi_bit) - 1u) & ~((1u << lo_bit) - 1u);
+      while (todo) {
+        const uint32_t bit = 31u - __clz(todo);
+        todo &= ~(1u << bit);
+        const int j = (int)(chunk_first + bit - bstart);
       float gr[16];
 #pragma unroll
       for (int k = 0; k < 16; ++k) gr[k] = 0.0f;
@@ -348,6 +358,8 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
         const float sum = warp_transpose_sum16(gr, lane);
         if ((lane & 1) == 0 && sum != 0.0f) atomicAdd(&s_acc[lane >> 1][j], sum);
       }
+      }
+      jhi = jlo - 1;
     }
     __syncthreads();
     // one set of vector atomics per Gaussian per batch
