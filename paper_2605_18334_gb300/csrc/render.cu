@@ -38,6 +38,25 @@ __device__ __forceinline__ TileCoord tile_coord(const RenderArgs& a, int64_t til
   return t;
 }
 
+// Pixels of a thread: PX vertically adjacent pixels of one column.  A warp
+// covers an 8-wide block of 4*PX rows (2 warps across the tile), more compact
+// than a 16-wide strip, so fewer of its lanes sit outside a Gaussian that
+// touches it.  pi0: index in the tile of the thread's first pixel (row-major).
+struct PixelMap {
+  int px, py0, pi0;
+};
+template <int PX>
+__device__ __forceinline__ PixelMap pixel_map(const TileCoord& tc) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lx = (warp & 1) * 8 + (lane & 7);
+  const int ly = (warp >> 1) * 4 * PX + (lane >> 3) * PX;
+  PixelMap m;
+  m.px = tc.tx * kTile + lx;
+  m.py0 = tc.ty * kTile + ly;
+  m.pi0 = ly * kTile + lx;
+  return m;
+}
+
 template <int MODE>
 __device__ __forceinline__ void stage_batch(const RenderArgs& a, const uint32_t* vals, uint32_t start, uint32_t end,
                                             int nt, float4* s_r0, float4* s_r1, float4* s_r2, float4* s_r3,
@@ -79,9 +98,8 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
   constexpr int NT = 256 / PX;
   __shared__ float4 s_r0[kBatch], s_r1[kBatch], s_r2[MODE == MODE_PLAIN ? 1 : kBatch], s_r3[kBatch];
   const TileCoord tc = tile_coord(a, blockIdx.x);
-  const int px = tc.tx * kTile + (threadIdx.x & (kTile - 1));
-  const int py0 = tc.ty * kTile + (threadIdx.x >> 4) * PX;
-  const int pi0 = (threadIdx.x >> 4) * PX * kTile + (threadIdx.x & (kTile - 1));  // pixel index in the tile
+  const PixelMap pm = pixel_map<PX>(tc);
+  const int px = pm.px, py0 = pm.py0, pi0 = pm.pi0;
   const float fx = (float)px + 0.5f;
   const uint2 range = tile_range(a.ranges, blockIdx.x);
   const uint32_t* vals = a.status->sorted_buf ? a.vals1 : a.vals0;
@@ -234,8 +252,8 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
   __shared__ float s_acc[16][kBatch + 1];
   __shared__ uint32_t s_max;
   const TileCoord tc = tile_coord(a, blockIdx.x);
-  const int px = tc.tx * kTile + (threadIdx.x & (kTile - 1));
-  const int py0 = tc.ty * kTile + (threadIdx.x >> 4) * PX;
+  const PixelMap pm = pixel_map<PX>(tc);
+  const int px = pm.px, py0 = pm.py0;
   const float fx = (float)px + 0.5f;
   const uint2 range = tile_range(a.ranges, blockIdx.x);
   const uint32_t* vals = a.status->sorted_buf ? a.vals1 : a.vals0;
@@ -246,7 +264,7 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
 
   float T[PX], g0[PX], g1[PX], g2[PX], R0[PX], R1[PX], R2[PX];
   uint32_t my_end[PX], bw[PX];
-  const int pi0 = (threadIdx.x >> 4) * PX * kTile + (threadIdx.x & (kTile - 1));
+  const int pi0 = pm.pi0;
   const uint32_t* mbase = mask_tile_base(a.mask, range, blockIdx.x);
   uint32_t my_max = 0;
 #pragma unroll
