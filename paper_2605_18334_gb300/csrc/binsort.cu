@@ -194,9 +194,15 @@ __device__ __forceinline__ int warp_owner(uint32_t x, uint32_t q) {
   return lo;
 }
 
+// prefix count of packed row rr (one byte per row)
+__device__ __forceinline__ uint32_t span_cum(uint32_t cum_lo, uint32_t cum_hi, int rr) {
+  return ((rr < 4 ? cum_lo : cum_hi) >> (8 * (rr & 3))) & 0xffu;
+}
+
 // one lane's record in the duplication pipeline
 struct DupFields {
-  uint32_t m, start, cnt, rx, ry, sp0, sp1;
+  uint32_t m, start, cnt, rx, ry;
+  uint4 sp;  // the footprint's second float4, as bits (packed row spans or kSpansTall)
 };
 
 __device__ __forceinline__ void dup_load_index(const uint32_t* __restrict__ perm,
@@ -216,19 +222,18 @@ __device__ __forceinline__ void dup_load_fields(const uint32_t* __restrict__ nto
                                                 const float4* __restrict__ foot, int64_t m_total, int64_t w, int lane,
                                                 DupFields& f) {
   f.cnt = 0;
-  f.rx = f.ry = f.sp0 = f.sp1 = 0;
+  f.rx = f.ry = 0;
+  f.sp = make_uint4(0u, 0u, 0u, 0u);
   if (w * 32 + lane < m_total) {
     f.cnt = ntouch[f.m];
     const uint2 r = rect[f.m];
-    const uint2 sp = reinterpret_cast<const uint2*>(foot + 2 * (int64_t)f.m + 1)[1];  // f1.zw: packed spans
+    f.sp = reinterpret_cast<const uint4*>(foot)[2 * (int64_t)f.m + 1];
     f.rx = r.x;
     f.ry = r.y;
-    f.sp0 = sp.x;
-    f.sp1 = sp.y;
   }
 }
 
-__global__ void __launch_bounds__(256, 5) duplicate_kernel(int64_t n, int n_views, const ViewInfo* __restrict__ views,
+__global__ void __launch_bounds__(256, 4) duplicate_kernel(int64_t n, int n_views, const ViewInfo* __restrict__ views,
                                                         const uint32_t* __restrict__ perm,
                                                         const uint32_t* __restrict__ ntouch,
                                                         const uint32_t* __restrict__ offsets,
@@ -259,9 +264,10 @@ __global__ void __launch_bounds__(256, 5) duplicate_kernel(int64_t n, int n_view
   for (int64_t w = w0; w * 32 < m_total; w += warps) {
     dup_load_fields(ntouch, rect, foot, m_total, w + warps, lane, nxt);
     dup_load_index(perm, offsets, m_total, w + 2 * warps, lane, nn_m, nn_start);
-    const uint32_t m = cur.m, cnt = cur.cnt, start = cur.start, sp0 = cur.sp0, sp1 = cur.sp1;
+    const uint32_t m = cur.m, cnt = cur.cnt, start = cur.start;
+    const uint32_t cum_lo = cur.sp.x, cum_hi = cur.sp.y, firsts = cur.sp.z;
     const uint32_t tx0 = cur.rx & 0xffffu, ty0 = cur.rx >> 16, ty1 = cur.ry >> 16;
-    const bool tall = cnt && sp0 == kSpansTall;
+    const bool tall = cnt && cur.sp.w == kSpansTall;
     uint32_t row0 = 0, tiles_x = 0;  // global tile id of (0, ty0) and the view's tiles per row
     float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 f1xy = make_float2(0.f, 0.f), mu = f1xy;
@@ -271,14 +277,17 @@ __global__ void __launch_bounds__(256, 5) duplicate_kernel(int64_t n, int n_view
       row0 = (uint32_t)(vi.tile_base + (int64_t)ty0 * vi.tiles_x);
       if (tall) {  // loaded here, in parallel, for the warp-wide pass below
         f0 = foot[2 * (int64_t)m];
-        f1xy = reinterpret_cast<const float2*>(foot + 2 * (int64_t)m + 1)[0];
+        f1xy = make_float2(__uint_as_float(cur.sp.x), __uint_as_float(cur.sp.y));
         mu = reinterpret_cast<const float2*>(rec + 4 * (int64_t)m)[0];
       } else {
         // histogram of this record's keys, one call per packed row span
 #pragma unroll
         for (int rr = 0; rr < kSpanRows; ++rr) {
-          const uint32_t word = (rr < 2 ? sp0 : sp1) >> (16 * (rr & 1));
-          tile_hist_span(th, passes, row0 + (uint32_t)rr * tiles_x + tx0 + (word & 0xffu), (word >> 8) & 0xffu);
+          const uint32_t c0 = span_cum(cum_lo, cum_hi, rr);
+          if (c0 < cnt) {
+            const uint32_t c1 = rr + 1 < kSpanRows ? min(span_cum(cum_lo, cum_hi, rr + 1), cnt) : cnt;
+            tile_hist_span(th, passes, row0 + (uint32_t)rr * tiles_x + tx0 + ((firsts >> (4 * rr)) & 15u), c1 - c0);
+          }
         }
       }
     }
@@ -298,28 +307,24 @@ __global__ void __launch_bounds__(256, 5) duplicate_kernel(int64_t n, int n_view
       const int lo = warp_owner(rel, q_rel);
       const uint32_t o_rel = __shfl_sync(0xffffffffu, rel, lo);
       const uint32_t o_m = __shfl_sync(0xffffffffu, m, lo);
-      const uint32_t o_sp0 = __shfl_sync(0xffffffffu, sp0, lo);
-      const uint32_t o_sp1 = __shfl_sync(0xffffffffu, sp1, lo);
+      const uint32_t o_cum_lo = __shfl_sync(0xffffffffu, cum_lo, lo);
+      const uint32_t o_cum_hi = __shfl_sync(0xffffffffu, cum_hi, lo);
+      const uint32_t o_firsts = __shfl_sync(0xffffffffu, firsts, lo);
+      const bool o_tall = __shfl_sync(0xffffffffu, (uint32_t)tall, lo) != 0u;
       const uint32_t o_tx0 = __shfl_sync(0xffffffffu, tx0, lo);
       const uint32_t o_row0 = __shfl_sync(0xffffffffu, row0, lo);
       const uint32_t o_tx = __shfl_sync(0xffffffffu, tiles_x, lo);
       bool on = false;
       uint32_t key = 0;
-      if (p < end && o_sp0 != kSpansTall) {
-        // decode the row of the q-th key from the packed spans
-        uint32_t q = q_rel - o_rel;
-        bool found = false;
-#pragma unroll
-        for (int rr = 0; rr < kSpanRows; ++rr) {
-          const uint32_t word = (rr < 2 ? o_sp0 : o_sp1) >> (16 * (rr & 1));
-          const uint32_t first = word & 0xffu, num = (word >> 8) & 0xffu;
-          if (!found && q < num) {
-            key = o_row0 + (uint32_t)rr * o_tx + o_tx0 + first + q;
-            found = true;
-          }
-          if (!found) q -= num;
-        }
-        on = found && p < cap;
+      if (p < end && !o_tall) {
+        // the q-th key's row: the last row whose prefix count is <= q (a
+        // byte-wise compare of q against the eight prefixes, then a popcount)
+        const uint32_t q = q_rel - o_rel;
+        const uint32_t qq = q * 0x01010101u;
+        const uint32_t row = ((__popc(__vcmpgeu4(qq, o_cum_lo)) + __popc(__vcmpgeu4(qq, o_cum_hi))) >> 3) - 1u;
+        const uint32_t first = (o_firsts >> (4 * row)) & 15u;
+        key = o_row0 + row * o_tx + o_tx0 + first + (q - span_cum(o_cum_lo, o_cum_hi, (int)row));
+        on = p < cap;
       }
       if (on) {
         keys[p] = key;
@@ -749,7 +754,7 @@ cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms) {
   if (m > 0) {
     scan_down_kernel<<<nb, kScanThreads, 0, st>>>(a.ws.ntouch, perm, m, a.ws.scan_part, a.ws.offsets);
     // keys and the tile sort's digit histograms
-    duplicate_kernel<<<clamp_grid((m + 255) / 256, sms, 5), 256, 0, st>>>(
+    duplicate_kernel<<<clamp_grid((m + 255) / 256, sms, 4), 256, 0, st>>>(
         a.n, a.n_views, a.ws.views, perm, a.ws.ntouch, a.ws.offsets, a.ws.rect, a.ws.rec, a.ws.foot, a.ws.keys[0],
         a.ws.vals[0], a.cap, a.ws.hist + kMaxPasses * 256, a.passes);
     count_launches(2);

@@ -240,13 +240,19 @@ __device__ __forceinline__ uint2 tile_range(const uint2* ranges, int64_t tile) {
   return v.y ? make_uint2(~v.x, v.y) : make_uint2(0u, 0u);
 }
 
-// Row spans of a record's touched tiles, packed for the key emission: for a
-// tile box of at most kSpanRows rows and 255 columns, 8 bits of first column
-// (relative to the box) and 8 bits of count per row, two rows per 32-bit
-// word (f1.z: rows 0-1, f1.w: rows 2-3).  Larger boxes store kSpansTall and
-// are enumerated with row_tile_span again.
-constexpr int kSpanRows = 4;
+// Row spans of a record's touched tiles, packed for the key emission when the
+// tile box has at most kSpanRows rows, every row's first touched column lies
+// within 15 of the box's first column and the record touches at most 255
+// tiles: the footprint's second float4 then holds, as bits,
+//   x, y  the exclusive prefix count of each row, one byte per row (rows
+//         0-3 in x, 4-7 in y; 255 for rows below the box),
+//   z     the first column of each row relative to the box, 4 bits per row,
+//   w     kSpansPacked.
+// Other records keep (rho2, 1/Syy, 0, kSpansTall) there and are enumerated
+// with row_tile_span again.
+constexpr int kSpanRows = 8;
 constexpr uint32_t kSpansTall = 0xffffffffu;
+constexpr uint32_t kSpansPacked = 0u;
 
 // Storage loads (FP32 arithmetic whatever the storage type).
 template <int DT>

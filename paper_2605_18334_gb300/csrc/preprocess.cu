@@ -395,23 +395,37 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_fwd_kernel(PreArgs a) 
               // exact ellipse / tile test, row by row (row_tile_span)
               const float4 f0 = make_float4(P.sxy / dyy, P.detD / dyy, sqrtf(rho2) * P.sxy / sqrtf(dxx), ey);
               float4 f1 = make_float4(rho2, 1.0f / dyy, 0.0f, 0.0f);
-              const bool small = ty1 - ty0 <= (uint32_t)kSpanRows && tx1 - tx0 <= 255u;
-              uint32_t pk0 = 0u, pk1 = 0u;
+              const uint32_t nrows = ty1 - ty0;
+              bool packed = nrows <= (uint32_t)kSpanRows;
+              uint32_t cum_lo = 0u, cum_hi = 0u, firsts = 0u;
               for (uint32_t ty = ty0; ty < ty1; ++ty) {
+                const uint32_t rr = ty - ty0;
+                if (packed) {  // this row's exclusive prefix (checked <= 255 below)
+                  const uint32_t c8 = min(ntouch, 255u) << (8 * (rr & 3));
+                  if (rr < 4) cum_lo |= c8; else cum_hi |= c8;
+                }
                 int lo, hi;
                 if (row_tile_span(f0, f1, P.mx, P.my, (int)ty, c.width, c.height, lo, hi)) {
                   ntouch += (uint32_t)(hi - lo + 1);
-                  if (small) {
-                    const uint32_t rr = ty - ty0;
-                    const uint32_t w = (((uint32_t)(lo - (int)tx0)) | ((uint32_t)(hi - lo + 1) << 8)) << (16 * (rr & 1));
-                    if (rr < 2) pk0 |= w; else pk1 |= w;
-                  }
+                  const uint32_t first = (uint32_t)(lo - (int)tx0);
+                  packed = packed && first <= 15u;
+                  if (packed) firsts |= first << (4 * rr);
                 }
               }
-              f1.z = __uint_as_float(small ? pk0 : kSpansTall);
-              f1.w = __uint_as_float(small ? pk1 : kSpansTall);
+              packed = packed && ntouch <= 255u;
+              if (packed) {  // rows below the box never own a key
+                if (nrows < 4) {
+                  cum_lo |= 0xffffffffu << (8 * nrows);
+                  cum_hi = 0xffffffffu;
+                } else if (nrows < 8) {
+                  cum_hi |= 0xffffffffu << (8 * (nrows - 4));
+                }
+              }
               a.ws.foot[2 * m] = f0;
-              a.ws.foot[2 * m + 1] = f1;
+              a.ws.foot[2 * m + 1] =
+                  packed ? make_float4(__uint_as_float(cum_lo), __uint_as_float(cum_hi), __uint_as_float(firsts),
+                                       __uint_as_float(kSpansPacked))
+                         : make_float4(f1.x, f1.y, 0.0f, __uint_as_float(kSpansTall));
             }
           }
         }
