@@ -78,15 +78,34 @@ __device__ __forceinline__ unsigned long long element_count(const unsigned long 
 // ---------------------------------------------------------------------------
 // scan of the tile counts (in the order given by perm)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ cnt,
-                                                                   const uint32_t* __restrict__ perm, int64_t m,
+// the kScanItems counts of this thread, in order (16-byte loads when the
+// thread's slice is whole; the counts array is 256-byte aligned)
+__device__ __forceinline__ void scan_load(const uint32_t* __restrict__ cnt, int64_t base, int64_t m,
+                                          uint32_t (&v)[kScanItems]) {
+  if (base + kScanItems <= m) {
+#pragma unroll
+    for (int k = 0; k < kScanItems; k += 4) {
+      const uint4 q = __ldg(reinterpret_cast<const uint4*>(cnt + base + k));
+      v[k] = q.x;
+      v[k + 1] = q.y;
+      v[k + 2] = q.z;
+      v[k + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) v[k] = base + k < m ? cnt[base + k] : 0u;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ cnt, int64_t m,
                                                                    unsigned long long* __restrict__ part) {
   __shared__ unsigned long long s_warp[kScanThreads / 32];
   const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  scan_load(cnt, base, m, v);
   unsigned long long sum = 0;
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k)
-    if (base + k < m) sum += cnt[perm[base + k]];
+  for (int k = 0; k < kScanItems; ++k) sum += v[k];
   unsigned long long total;
   block_exclusive_u64<kScanThreads>(sum, s_warp, total);
   if (threadIdx.x == 0) part[blockIdx.x] = total;
@@ -111,25 +130,32 @@ __global__ void __launch_bounds__(1024) scan_parts_kernel(unsigned long long* pa
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint32_t* __restrict__ cnt,
-                                                                 const uint32_t* __restrict__ perm, int64_t m,
+__global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint32_t* __restrict__ cnt, int64_t m,
                                                                  const unsigned long long* __restrict__ part,
                                                                  uint32_t* __restrict__ offsets) {
   __shared__ unsigned long long s_warp[kScanThreads / 32];
   const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
   uint32_t v[kScanItems];
+  scan_load(cnt, base, m, v);
   unsigned long long sum = 0;
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    v[k] = base + k < m ? cnt[perm[base + k]] : 0u;
-    sum += v[k];
-  }
+  for (int k = 0; k < kScanItems; ++k) sum += v[k];
   unsigned long long total;
   unsigned long long run = block_exclusive_u64<kScanThreads>(sum, s_warp, total) + part[blockIdx.x];
+  uint32_t o[kScanItems];
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
-    if (base + k < m) offsets[base + k] = run > 0xffffffffull ? 0xffffffffu : (uint32_t)run;
+    o[k] = run > 0xffffffffull ? 0xffffffffu : (uint32_t)run;
     run += v[k];
+  }
+  if (base + kScanItems <= m) {
+#pragma unroll
+    for (int k = 0; k < kScanItems; k += 4)
+      *reinterpret_cast<uint4*>(offsets + base + k) = make_uint4(o[k], o[k + 1], o[k + 2], o[k + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+      if (base + k < m) offsets[base + k] = o[k];
   }
 }
 
@@ -218,14 +244,15 @@ __device__ __forceinline__ void dup_load_index(const uint32_t* __restrict__ perm
   }
 }
 
-__device__ __forceinline__ void dup_load_fields(const uint32_t* __restrict__ ntouch, const uint2* __restrict__ rect,
-                                                const float4* __restrict__ foot, int64_t m_total, int64_t w, int lane,
-                                                DupFields& f) {
+__device__ __forceinline__ void dup_load_fields(const uint32_t* __restrict__ cnt_sorted,
+                                                const uint2* __restrict__ rect, const float4* __restrict__ foot,
+                                                int64_t m_total, int64_t w, int lane, DupFields& f) {
   f.cnt = 0;
   f.rx = f.ry = 0;
   f.sp = make_uint4(0u, 0u, 0u, 0u);
-  if (w * 32 + lane < m_total) {
-    f.cnt = ntouch[f.m];
+  const int64_t j = w * 32 + lane;
+  if (j < m_total) {
+    f.cnt = cnt_sorted[j];
     const uint2 r = rect[f.m];
     f.sp = reinterpret_cast<const uint4*>(foot)[2 * (int64_t)f.m + 1];
     f.rx = r.x;
@@ -235,7 +262,7 @@ __device__ __forceinline__ void dup_load_fields(const uint32_t* __restrict__ nto
 
 __global__ void __launch_bounds__(256, 4) duplicate_kernel(int64_t n, int n_views, const ViewInfo* __restrict__ views,
                                                         const uint32_t* __restrict__ perm,
-                                                        const uint32_t* __restrict__ ntouch,
+                                                        const uint32_t* __restrict__ cnt_sorted,
                                                         const uint32_t* __restrict__ offsets,
                                                         const uint2* __restrict__ rect,
                                                         const float4* __restrict__ rec,
@@ -259,10 +286,10 @@ __global__ void __launch_bounds__(256, 4) duplicate_kernel(int64_t n, int n_view
   DupFields cur, nxt;
   uint32_t nn_m = 0, nn_start = 0xffffffffu;
   dup_load_index(perm, offsets, m_total, w0, lane, cur.m, cur.start);
-  dup_load_fields(ntouch, rect, foot, m_total, w0, lane, cur);
+  dup_load_fields(cnt_sorted, rect, foot, m_total, w0, lane, cur);
   dup_load_index(perm, offsets, m_total, w0 + warps, lane, nxt.m, nxt.start);
   for (int64_t w = w0; w * 32 < m_total; w += warps) {
-    dup_load_fields(ntouch, rect, foot, m_total, w + warps, lane, nxt);
+    dup_load_fields(cnt_sorted, rect, foot, m_total, w + warps, lane, nxt);
     dup_load_index(perm, offsets, m_total, w + 2 * warps, lane, nn_m, nn_start);
     const uint32_t m = cur.m, cnt = cur.cnt, start = cur.start;
     const uint32_t cum_lo = cur.sp.x, cum_hi = cur.sp.y, firsts = cur.sp.z;
@@ -468,6 +495,8 @@ struct PassArgs {
   uint2* ranges;                  // last pass of the tile sort: tile ranges to reduce into, else nullptr
   unsigned long long n_tiles;     // number of tiles (bounds the range writes)
   int sorted_buf;                 // last pass of the tile sort: index of the output buffer
+  const uint32_t* out_gather;     // last pass of the depth sort: keys_out receives out_gather[value]
+                                  // (the sorted keys are not needed afterwards), else nullptr
   int passes;
   int pass;
   int shift;
@@ -633,8 +662,9 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(PassArgs<KEY>
     const uint32_t dg = (uint32_t)(k >> a.shift) & dmask;
     const unsigned long long g = sm.gofs[dg] + i;
     if (g < kn) {  // always true unless a look-back gave up
-      a.keys_out[g] = k;
-      a.vals_out[g] = sm.val[i];
+      const uint32_t v = sm.val[i];
+      a.keys_out[g] = a.out_gather ? (KEY)a.out_gather[v] : k;
+      a.vals_out[g] = v;
       // after the last pass the keys are sorted, and the equal keys of this
       // partition are one run in block-local order: its ends bound the tile's
       // range (partitions combine by atomicMax on (~start, end))
@@ -681,7 +711,7 @@ static int run_passes(const KEY* keys_in, const uint32_t* vals_in, KEY* const* k
                       const unsigned long long* count_dev, unsigned long long count, unsigned long long parts,
                       int passes, int key_bits, const int* run, Status* status, int spin_limit,
                       cudaStream_t st, uint2* ranges = nullptr, unsigned long long n_tiles = 0,
-                      const int* buf_ids = nullptr) {
+                      const int* buf_ids = nullptr, const uint32_t* last_gather = nullptr) {
   int cur = -1;  // -1: still the input
   int last = -1;
   for (int p = 0; p < passes; ++p)
@@ -710,6 +740,7 @@ static int run_passes(const KEY* keys_in, const uint32_t* vals_in, KEY* const* k
     pa.ranges = p == last ? ranges : nullptr;
     pa.n_tiles = n_tiles;
     pa.sorted_buf = (p == last && buf_ids) ? buf_ids[out] : 0;
+    pa.out_gather = p == last ? last_gather : nullptr;
     onesweep_kernel<KEY><<<(unsigned)parts, kSortThreads, sizeof(SortSmem<KEY>), st>>>(pa);
     count_launches(1);
     cur = out;
@@ -728,6 +759,7 @@ cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms) {
   const unsigned long long um = (unsigned long long)m;
   const unsigned long long dparts = (um + kSortPart - 1) / kSortPart;
   const uint32_t* perm = a.ws.perm[0];
+  const uint32_t* cnt_sorted = a.ws.dkey[0];
   if (m > 0) {
     if ((e = cudaMemsetAsync(a.ws.lookback_d, 0, sizeof(unsigned long long) * 256 * kDepthPasses * dparts, st)) !=
         cudaSuccess)
@@ -739,23 +771,26 @@ cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms) {
     count_launches(2);
     uint32_t* const kb[2] = {a.ws.dkey[1], a.ws.dkey[0]};
     uint32_t* const vb[2] = {a.ws.perm[1], a.ws.perm[0]};
+    // the last pass writes, in place of the sorted depth keys, the records'
+    // tile counts in depth order (what the scan and the key emission read)
     const int r = run_passes<uint32_t>(a.ws.dkey[0], nullptr, kb, vb, a.ws.hist, a.ws.lookback_d,
                                        a.ws.status->part_counter, nullptr, um, dparts, kDepthPasses, 32, nullptr,
-                                       a.ws.status, a.spin_limit, st);
+                                       a.ws.status, a.spin_limit, st, nullptr, 0, nullptr, a.ws.ntouch);
     perm = vb[r];
+    cnt_sorted = kb[r];
   }
   const int nb = (int)((m + kScanBlock - 1) / kScanBlock);
   if (m > 0) {
-    scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(a.ws.ntouch, perm, m, a.ws.scan_part);
+    scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(cnt_sorted, m, a.ws.scan_part);
     count_launches(1);
   }
   scan_parts_kernel<<<1, 1024, 0, st>>>(a.ws.scan_part, nb, a.ws.status, a.cap);
   count_launches(1);
   if (m > 0) {
-    scan_down_kernel<<<nb, kScanThreads, 0, st>>>(a.ws.ntouch, perm, m, a.ws.scan_part, a.ws.offsets);
+    scan_down_kernel<<<nb, kScanThreads, 0, st>>>(cnt_sorted, m, a.ws.scan_part, a.ws.offsets);
     // keys and the tile sort's digit histograms
     duplicate_kernel<<<clamp_grid((m + 255) / 256, sms, 4), 256, 0, st>>>(
-        a.n, a.n_views, a.ws.views, perm, a.ws.ntouch, a.ws.offsets, a.ws.rect, a.ws.rec, a.ws.foot, a.ws.keys[0],
+        a.n, a.n_views, a.ws.views, perm, cnt_sorted, a.ws.offsets, a.ws.rect, a.ws.rec, a.ws.foot, a.ws.keys[0],
         a.ws.vals[0], a.cap, a.ws.hist + kMaxPasses * 256, a.passes);
     count_launches(2);
   }
