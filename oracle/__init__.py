@@ -229,8 +229,8 @@ def bin_keys(pre: dict, cam: Camera, cfg: Config, tile_base: int = 0, val_base: 
     n = pre["rec"].shape[0]
     L = lib()
     args = [C.c_int64(n), _p(pre["rec"]), _p(pre["ext"]), _p(pre["depth_bits"]), _p(pre["_vis32"]), _p(pre["rect"]),
-            C.c_int32(cam.width), C.c_int32(cam.height), C.c_int32(cfg.tile_w), C.c_int64(tile_base),
-            C.c_int64(val_base)]
+            C.c_int32(cam.width), C.c_int32(cam.height), C.c_int32(cfg.tile_w), C.c_double(cfg.alpha_min),
+            C.c_int64(tile_base), C.c_int64(val_base)]
     cnt = L.or_bin(*args, C.c_int64(0), None, None)
     keys = np.zeros(max(cnt, 1), np.uint64)
     vals = np.zeros(max(cnt, 1), np.int64)

@@ -380,35 +380,80 @@ void tile_range_1d(double m, double e, int size, int tile, int* t0, int* t1) {
   *t1 = (int)hi / tile + 1;
 }
 
-// Tile columns of tile row ty touched by the footprint ellipse
-// {d : d^T A d <= rho2} around (mx, my), A = [[a, b], [b, c]] the conic.
-// A tile is touched iff the ellipse meets the rectangle spanned by the
-// tile's pixel centres (clipped to the image).  For the row this is the
-// x-extent of the ellipse within the band of pixel-centre heights: the
-// boundary is x(y) = (-b y +- sqrt(a rho2 - D y^2)) / a with D = ac - b^2,
-// whose rightmost point is at y = -b rho / sqrt(D c) (leftmost at the
-// opposite height); the right end is concave in y and the left end convex,
-// so their extremes over the band sit at those heights clamped to the band.
-// edge_shift perturbs both x ends (ambiguity checks).  Returns false if the
-// row touches no tile; *near_edge is set when the band only grazes the
-// ellipse's top or bottom (within tol).
-bool row_span(const double* r, double rho2, int ty, int width, int height, int tile, double edge_shift, double tol,
-              int* t0, int* t1, bool* near_edge) {
-  const double a = r[R_A], b = r[R_B], c = r[R_C];
+// x-extent, relative to mu_x, of the ellipse {d : d^T [[a, b], [b, c]] d <=
+// rho2} within the heights [y0, y1] (relative to mu_y); false if they do not
+// meet.  The boundary is x(y) = (-b y +- sqrt(a rho2 - D y^2)) / a with
+// D = ac - b^2; its rightmost point is at y = -b rho / sqrt(D c) (leftmost at
+// the opposite height), the right end is concave in y and the left end
+// convex, so their extremes over the band sit at those heights clamped to the
+// band.  *ymax receives the ellipse's half height.
+bool ellipse_band(double a, double b, double c, double rho2, double y0, double y1, double* xl, double* xr,
+                  double* ymax) {
   const double D = a * c - b * b;
-  const double ymax = std::sqrt(a * rho2 / D);
-  double y0 = ty * (double)tile + 0.5 - r[R_MY];
-  double y1 = std::min(ty * tile + tile - 1, height - 1) + 0.5 - r[R_MY];
-  if (near_edge) *near_edge = std::fabs(y0 - ymax) < tol || std::fabs(y1 + ymax) < tol;
-  y0 = std::max(y0, -ymax);
-  y1 = std::min(y1, ymax);
+  *ymax = rho2 > 0.0 ? std::sqrt(a * rho2 / D) : -1.0;
+  y0 = std::max(y0, -*ymax);
+  y1 = std::min(y1, *ymax);
   if (!(y0 <= y1)) return false;
   const double ys = -b * std::sqrt(rho2) / std::sqrt(D * c);
   const double yh = std::min(std::max(ys, y0), y1);
   const double yl = std::min(std::max(-ys, y0), y1);
-  const double xmax = (-b * yh + std::sqrt(std::max(0.0, a * rho2 - D * yh * yh))) / a;
-  const double xmin = (-b * yl - std::sqrt(std::max(0.0, a * rho2 - D * yl * yl))) / a;
-  double lo = std::ceil(r[R_MX] + xmin - 0.5 - edge_shift), hi = std::floor(r[R_MX] + xmax - 0.5 + edge_shift);
+  *xr = (-b * yh + std::sqrt(std::max(0.0, a * rho2 - D * yh * yh))) / a;
+  *xl = (-b * yl - std::sqrt(std::max(0.0, a * rho2 - D * yl * yl))) / a;
+  return true;
+}
+
+// Tile columns of tile row ty touched by the footprint of a record (the
+// Gaussian's conic A = [[a, b], [b, c]], skew beta, E1 radius rho2):
+//   S = (E1 and beta^T d >= 0) union (E2 and beta^T d < 0),
+//   E1 = {d^T A d <= rho2},
+//   E2 = {d^T (A + beta beta^T) d <= rho_-^2}, rho_-^2 = 2 ln(o_max comp / tau)(1 + 2^-10),
+// E2 bounding the side z = beta^T d / sqrt 2 < 0, where 1 + erf z = erfc|z| <= e^{-z^2}.
+// The row touches the tile columns holding a pixel centre in the x-extent of
+// the footprint within the row's band of pixel-centre heights, taken as
+// E1's extent cut by the hull of the half-plane's extent (the band clipped
+// to E1's heights) and E2's; with beta = 0, E1's extent alone.  edge_shift
+// perturbs both x ends (ambiguity checks).  Returns false if the row touches
+// no tile; *near_edge is set when the band's edge lies within tol of a height
+// where the rule changes discontinuously (the top or bottom of E1 or E2, or
+// a horizontal half-plane boundary).
+bool row_span(const double* r, double rho2, double tau, int ty, int width, int height, int tile, double edge_shift,
+              double tol, int* t0, int* t1, bool* near_edge) {
+  const double a = r[R_A], b = r[R_B], c = r[R_C];
+  const double y0 = ty * (double)tile + 0.5 - r[R_MY];
+  const double y1 = std::min(ty * tile + tile - 1, height - 1) + 0.5 - r[R_MY];
+  double xl, xr, ymax1;
+  const bool on1 = ellipse_band(a, b, c, rho2, y0, y1, &xl, &xr, &ymax1);
+  bool near = std::fabs(y0 - ymax1) < tol || std::fabs(y1 + ymax1) < tol;
+  bool on = on1;
+  const double bx = r[R_BX], by = r[R_BY];
+  if (on && (bx != 0.0 || by != 0.0)) {
+    const double c0 = std::max(y0, -ymax1), c1 = std::min(y1, ymax1);
+    bool hon = true;
+    double hl = -INFINITY, hr = INFINITY;
+    if (bx > 0.0) {
+      hl = std::min(-by * c0 / bx, -by * c1 / bx);
+    } else if (bx < 0.0) {
+      hr = std::max(-by * c0 / bx, -by * c1 / bx);
+    } else {
+      hon = by > 0.0 ? c1 >= 0.0 : c0 <= 0.0;
+      near = near || std::fabs(c0) < tol || std::fabs(c1) < tol;
+    }
+    const double omax = r[R_COMP] * std::max(r[R_O1], r[R_O2]);
+    const double rho2m = 2.0 * std::log(omax / tau) * (1.0 + 1.0 / 1024.0);
+    double l2 = 0.0, r2 = 0.0, ymax2 = -1.0;
+    const bool e2on = rho2m > 0.0 && ellipse_band(a + bx * bx, b + bx * by, c + by * by, rho2m, y0, y1, &l2, &r2,
+                                                  &ymax2);
+    if (ymax2 > 0.0) near = near || std::fabs(y0 - ymax2) < tol || std::fabs(y1 + ymax2) < tol;
+    if (!hon && !e2on) {
+      on = false;
+    } else {
+      xl = std::max(xl, hon ? (e2on ? std::min(hl, l2) : hl) : l2);
+      xr = std::min(xr, hon ? (e2on ? std::max(hr, r2) : hr) : r2);
+    }
+  }
+  if (near_edge) *near_edge = near;
+  if (!on) return false;
+  double lo = std::ceil(r[R_MX] + xl - 0.5 - edge_shift), hi = std::floor(r[R_MX] + xr - 0.5 + edge_shift);
   lo = std::max(lo, 0.0);
   hi = std::min(hi, (double)width - 1.0);
   if (lo > hi) return false;
@@ -514,9 +559,12 @@ void or_preprocess(const OrScene* s, const OrCamera* c, const OrConfig* cfg, dou
     for (int ty = rc[1]; ty < rc[3]; ++ty) {
       int t0, t1, u0, u1, v0, v1;
       bool near = false;
-      const bool on0 = row_span(r, e[2], ty, c->width, c->height, cfg->tile_w, 0.0, tol_px, &t0, &t1, &near);
-      const bool onm = row_span(r, e[2], ty, c->width, c->height, cfg->tile_w, -tol_px, tol_px, &u0, &u1, nullptr);
-      const bool onp = row_span(r, e[2], ty, c->width, c->height, cfg->tile_w, tol_px, tol_px, &v0, &v1, nullptr);
+      const double tau = cfg->alpha_min;
+      const bool on0 = row_span(r, e[2], tau, ty, c->width, c->height, cfg->tile_w, 0.0, tol_px, &t0, &t1, &near);
+      const bool onm =
+          row_span(r, e[2], tau, ty, c->width, c->height, cfg->tile_w, -tol_px, tol_px, &u0, &u1, nullptr);
+      const bool onp =
+          row_span(r, e[2], tau, ty, c->width, c->height, cfg->tile_w, tol_px, tol_px, &v0, &v1, nullptr);
       if (on0) ntouch[i] += t1 - t0 + 1;
       if (near || on0 != onm || on0 != onp || (on0 && (t0 != u0 || t1 != u1 || t0 != v0 || t1 != v1)))
         rect_ambig[i] = 1;
@@ -697,12 +745,12 @@ void or_render_backward(const OrScene* s, const OrCamera* cam, const OrConfig* c
 }
 
 // Tile keys of one view: for each visible Gaussian, in index order, one
-// (tile | depth) key per tile its footprint ellipse touches (row_span,
+// (tile | depth) key per tile its footprint touches (row_span,
 // row-major), then a stable sort.  tile_base / val_base offset the tile id
 // and the value.
 // Returns the number of keys; writes at most cap of them.
 int64_t or_bin(int64_t n, const double* rec, const double* ext, const uint32_t* depth_bits, const int32_t* visible,
-               const int32_t* rect, int32_t width, int32_t height, int32_t tile_size, int64_t tile_base,
+               const int32_t* rect, int32_t width, int32_t height, int32_t tile_size, double tau, int64_t tile_base,
                int64_t val_base, int64_t cap, uint64_t* keys, int64_t* vals) {
   const int32_t tiles_x = (width + tile_size - 1) / tile_size;
   std::vector<std::pair<uint64_t, int64_t>> kv;
@@ -711,7 +759,7 @@ int64_t or_bin(int64_t n, const double* rec, const double* ext, const uint32_t* 
     const int32_t* r = rect + 4 * i;
     for (int ty = r[1]; ty < r[3]; ++ty) {
       int t0, t1;
-      if (!row_span(rec + (size_t)NREC * i, ext[3 * i + 2], ty, width, height, tile_size, 0.0, 0.0, &t0, &t1,
+      if (!row_span(rec + (size_t)NREC * i, ext[3 * i + 2], tau, ty, width, height, tile_size, 0.0, 0.0, &t0, &t1,
                     nullptr))
         continue;
       for (int tx = t0; tx <= t1; ++tx) {

@@ -200,7 +200,7 @@ sr_status sr_plan_init(sr_plan* p, const sr_config* cfg, const sr_gaussians* g, 
   sizes[WS_LOOKBACK] = sizeof(unsigned long long) * 256 * (size_t)p->sort_passes * (size_t)parts;
   sizes[WS_RANGES] = sizeof(uint2) * (size_t)tb;
   sizes[WS_D2] = p->forward_only ? 0 : sizeof(float) * kD2Stride * (size_t)m;
-  sizes[WS_FOOT] = sizeof(float4) * 2 * (size_t)m;
+  sizes[WS_FOOT] = sizeof(float4) * 4 * (size_t)m;
   sizes[WS_MASK] = p->forward_only ? 0 : sizeof(uint32_t) * 256 * (size_t)(key_capacity / 32 + tb + 1);
   size_t off = 0;
   for (int k = 0; k < WS_NUM_SLOTS; ++k) {

@@ -254,7 +254,7 @@ __device__ __forceinline__ void dup_load_fields(const uint32_t* __restrict__ cnt
   if (j < m_total) {
     f.cnt = cnt_sorted[j];
     const uint2 r = rect[f.m];
-    f.sp = reinterpret_cast<const uint4*>(foot)[2 * (int64_t)f.m + 1];
+    f.sp = reinterpret_cast<const uint4*>(foot)[4 * (int64_t)f.m + 1];
     f.rx = r.x;
     f.ry = r.y;
   }
@@ -296,17 +296,11 @@ __global__ void __launch_bounds__(256, 4) duplicate_kernel(int64_t n, int n_view
     const uint32_t tx0 = cur.rx & 0xffffu, ty0 = cur.rx >> 16, ty1 = cur.ry >> 16;
     const bool tall = cnt && cur.sp.w == kSpansTall;
     uint32_t row0 = 0, tiles_x = 0;  // global tile id of (0, ty0) and the view's tiles per row
-    float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f);
-    float2 f1xy = make_float2(0.f, 0.f), mu = f1xy;
     if (cnt) {
       const ViewInfo& vi = views[(int)(m / (uint64_t)n)];
       tiles_x = (uint32_t)vi.tiles_x;
       row0 = (uint32_t)(vi.tile_base + (int64_t)ty0 * vi.tiles_x);
-      if (tall) {  // loaded here, in parallel, for the warp-wide pass below
-        f0 = foot[2 * (int64_t)m];
-        f1xy = make_float2(__uint_as_float(cur.sp.x), __uint_as_float(cur.sp.y));
-        mu = reinterpret_cast<const float2*>(rec + 4 * (int64_t)m)[0];
-      } else {
+      if (!tall) {
         // histogram of this record's keys, one call per packed row span
 #pragma unroll
         for (int rr = 0; rr < kSpanRows; ++rr) {
@@ -367,17 +361,17 @@ __global__ void __launch_bounds__(256, 4) duplicate_kernel(int64_t n, int n_view
       const uint32_t tstart = __shfl_sync(0xffffffffu, start, src);
       const uint32_t tcnt = __shfl_sync(0xffffffffu, cnt, src);
       const int t_ty0 = (int)__shfl_sync(0xffffffffu, ty0, src), t_ty1 = (int)__shfl_sync(0xffffffffu, ty1, src);
-      const float4 g0 = make_float4(__shfl_sync(0xffffffffu, f0.x, src), __shfl_sync(0xffffffffu, f0.y, src),
-                                    __shfl_sync(0xffffffffu, f0.z, src), __shfl_sync(0xffffffffu, f0.w, src));
-      const float4 g1 = make_float4(__shfl_sync(0xffffffffu, f1xy.x, src), __shfl_sync(0xffffffffu, f1xy.y, src),
-                                    0.f, 0.f);
-      const float mx = __shfl_sync(0xffffffffu, mu.x, src), my = __shfl_sync(0xffffffffu, mu.y, src);
+      // the record's footprint constants (one address for the whole warp)
+      const float4* ft = foot + 4 * (int64_t)tm;
+      const float4 g0 = ft[0], g1 = ft[1], g2 = ft[2], g3 = ft[3];
+      const float2 mu = reinterpret_cast<const float2*>(rec + 4 * (int64_t)tm)[0];
+      const float mx = mu.x, my = mu.y;
       const ViewInfo& vi = views[(int)(tm / (uint64_t)n)];
       uint32_t done = 0;  // keys of this record placed by earlier row groups
       for (int rb = t_ty0; rb < t_ty1; rb += 32) {
         const int ty = rb + lane;
         int tlo = 0, thi = -1;
-        const bool ok = ty < t_ty1 && row_tile_span(g0, g1, mx, my, ty, vi.width, vi.height, tlo, thi);
+        const bool ok = ty < t_ty1 && row_tile_span(g0, g1, g2, g3, mx, my, ty, vi.width, vi.height, tlo, thi);
         const uint32_t num = ok ? (uint32_t)(thi - tlo + 1) : 0u;
         uint32_t inc = num;
 #pragma unroll

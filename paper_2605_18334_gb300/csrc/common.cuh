@@ -34,7 +34,7 @@ enum WsSlot {
   WS_LOOKBACK,     // uint64_t[parts(cap)][tile passes][256] look-back words of the tile sort
   WS_RANGES,       // uint2[total_tiles] [start, end) of each tile's sorted keys
   WS_D2,           // float[M][16] per-(view, Gaussian) 2D gradients
-  WS_FOOT,         // float4[M][2] footprint ellipse constants (see Foot)
+  WS_FOOT,         // float4[M][4] footprint constants or packed row spans (row_tile_span)
   WS_MASK,         // uint32_t[(cap/32 + tiles + 1) * 256] per-pixel blend masks (see render.cu)
   WS_NUM_SLOTS
 };
@@ -196,34 +196,78 @@ __device__ __forceinline__ bool eval_pair(const float4& r0, const float4& r1, co
   return true;
 }
 
-// Footprint ellipse {d : d^T Sigma_d^-1 d <= rho^2} around mu_2, stored as
-//   f0 = (slope, wdet, ystar, ymax), f1 = (rho2, inv_syy, spans, spans)
-// with slope = Sxy/Syy, wdet = det(Sigma_d)/Syy, ystar = rho Sxy / sqrt(Sxx)
-// (height of the rightmost point), ymax = rho sqrt(Syy), inv_syy = 1/Syy.
-// At height y (relative to mu_y) the ellipse spans
+// Footprint of a record: the region
+//   S = (E1 and beta^T d >= 0)  union  (E2 and beta^T d < 0)
+// around mu_2, with E1 = {d^T Sigma_d^-1 d <= rho^2} (the conservative
+// ellipse: alpha >= tau implies d in E1) and, on the side where
+// z = beta^T d / sqrt 2 < 0, the smaller ellipse
+// E2 = {d^T (Sigma_d^-1 + beta beta^T) d <= rho_-^2}, rho_-^2 =
+// 2 ln(o_max comp / tau)(1 + 2^-10): there 1 + erf z = erfc|z| <= e^{-z^2},
+// so alpha <= o_max comp exp(-d^T (Sigma_d^-1 + beta beta^T) d / 2).
+// An ellipse with covariance Sigma is stored as e = (slope, wdet, ystar,
+// ymax) and (rho2, inv_syy): slope = Sxy/Syy, wdet = det(Sigma)/Syy,
+// ystar = rho Sxy / sqrt(Sxx) (height of its rightmost point), ymax =
+// rho sqrt(Syy), inv_syy = 1/Syy; at height y (relative to mu_y) it spans
 //   x = slope y -+ sqrt(wdet (rho2 - y^2 / Syy)).
-// Tile row ty is touched in the tile columns that hold a pixel centre inside
-// the x-extent of the ellipse restricted to the row's band of pixel-centre
-// heights: the right edge is largest at y = clamp(ystar, band), the left
-// edge smallest at y = clamp(-ystar, band) (concave / convex in y).  The
-// counting (preprocess) and emitting (duplicate) kernels call this with the
-// stored constants and explicitly rounded operations, so they agree bit for
-// bit.  Returns false if the row touches no tile.
-__device__ __forceinline__ bool row_tile_span(const float4& f0, const float4& f1, float mx, float my, int ty,
-                                              int width, int height, int& tlo, int& thi) {
-  float y0 = __fadd_rn((float)(ty * kTile) + 0.5f, -my);
-  float y1 = __fadd_rn((float)min(ty * kTile + kTile - 1, height - 1) + 0.5f, -my);
-  y0 = fmaxf(y0, -f0.w);
-  y1 = fminf(y1, f0.w);
+// Record layout: f0 = E1's e; f1 = (rho2, inv_syy) of E1 (or the packed row
+// spans, see below); f2 = E2's e; f3 = (rho_-^2, inv_syy of E2, beta_x,
+// beta_y).  With beta = 0 the footprint is E1 alone.
+//
+// x-extent (relative to mu_x) of an ellipse within the band of heights
+// [y0, y1] (relative to mu_y): the right edge is largest at y =
+// clamp(ystar, band), the left edge smallest at y = clamp(-ystar, band)
+// (concave / convex in y).  False if they do not meet.
+__device__ __forceinline__ bool ellipse_band(const float4& e, float rho2, float inv_syy, float y0, float y1,
+                                             float& xl, float& xr) {
+  y0 = fmaxf(y0, -e.w);
+  y1 = fminf(y1, e.w);
   if (!(y0 <= y1)) return false;
-  const float yh = fminf(fmaxf(f0.z, y0), y1);
-  const float yl = fminf(fmaxf(-f0.z, y0), y1);
-  const float hh = __fsqrt_rn(__fmul_rn(f0.y, fmaxf(0.0f, __fadd_rn(f1.x, -__fmul_rn(__fmul_rn(yh, yh), f1.y)))));
-  const float hl = __fsqrt_rn(__fmul_rn(f0.y, fmaxf(0.0f, __fadd_rn(f1.x, -__fmul_rn(__fmul_rn(yl, yl), f1.y)))));
-  const float xmax = __fadd_rn(__fmul_rn(f0.x, yh), hh);
-  const float xmin = __fadd_rn(__fmul_rn(f0.x, yl), -hl);
-  float lo = ceilf(__fadd_rn(__fadd_rn(mx, xmin), -0.5f));
-  float hi = floorf(__fadd_rn(__fadd_rn(mx, xmax), -0.5f));
+  const float yh = fminf(fmaxf(e.z, y0), y1);
+  const float yl = fminf(fmaxf(-e.z, y0), y1);
+  const float hh = __fsqrt_rn(__fmul_rn(e.y, fmaxf(0.0f, __fadd_rn(rho2, -__fmul_rn(__fmul_rn(yh, yh), inv_syy)))));
+  const float hl = __fsqrt_rn(__fmul_rn(e.y, fmaxf(0.0f, __fadd_rn(rho2, -__fmul_rn(__fmul_rn(yl, yl), inv_syy)))));
+  xr = __fadd_rn(__fmul_rn(e.x, yh), hh);
+  xl = __fadd_rn(__fmul_rn(e.x, yl), -hl);
+  return true;
+}
+
+// Tile row ty is touched in the tile columns that hold a pixel centre inside
+// the x-extent of the footprint within the row's band of pixel-centre
+// heights, taken as E1's extent cut by the hull of the half-plane's extent
+// and E2's (a superset of S's extent).  The counting (preprocess) and
+// emitting (duplicate) kernels call this with the stored constants and
+// explicitly rounded operations, so they agree bit for bit.  Returns false
+// if the row touches no tile.
+__device__ __forceinline__ bool row_tile_span(const float4& f0, const float4& f1, const float4& f2,
+                                              const float4& f3, float mx, float my, int ty, int width, int height,
+                                              int& tlo, int& thi) {
+  const float y0 = __fadd_rn((float)(ty * kTile) + 0.5f, -my);
+  const float y1 = __fadd_rn((float)min(ty * kTile + kTile - 1, height - 1) + 0.5f, -my);
+  float xl, xr;
+  if (!ellipse_band(f0, f1.x, f1.y, y0, y1, xl, xr)) return false;
+  const float bx = f3.z, by = f3.w;
+  if (bx != 0.0f || by != 0.0f) {
+    // the half-plane beta^T d >= 0 within the band (clipped to E1's heights)
+    const float c0 = fmaxf(y0, -f0.w), c1 = fminf(y1, f0.w);
+    bool hon = true;
+    float hl = -INFINITY, hr = INFINITY;
+    if (bx > 0.0f) {
+      hl = fminf(__fdiv_rn(-__fmul_rn(by, c0), bx), __fdiv_rn(-__fmul_rn(by, c1), bx));
+    } else if (bx < 0.0f) {
+      hr = fmaxf(__fdiv_rn(-__fmul_rn(by, c0), bx), __fdiv_rn(-__fmul_rn(by, c1), bx));
+    } else {
+      hon = by > 0.0f ? c1 >= 0.0f : c0 <= 0.0f;
+    }
+    float l2 = 0.0f, r2 = 0.0f;
+    const bool e2on = ellipse_band(f2, f3.x, f3.y, y0, y1, l2, r2);
+    if (!hon && !e2on) return false;
+    const float ul = hon ? (e2on ? fminf(hl, l2) : hl) : l2;
+    const float ur = hon ? (e2on ? fmaxf(hr, r2) : hr) : r2;
+    xl = fmaxf(xl, ul);
+    xr = fminf(xr, ur);
+  }
+  float lo = ceilf(__fadd_rn(__fadd_rn(mx, xl), -0.5f));
+  float hi = floorf(__fadd_rn(__fadd_rn(mx, xr), -0.5f));
   lo = fmaxf(lo, 0.0f);
   hi = fminf(hi, (float)(width - 1));
   if (!(lo <= hi)) return false;
@@ -249,7 +293,7 @@ __device__ __forceinline__ uint2 tile_range(const uint2* ranges, int64_t tile) {
 //   z     the first column of each row relative to the box, 4 bits per row,
 //   w     kSpansPacked.
 // Other records keep (rho2, 1/Syy, 0, kSpansTall) there and are enumerated
-// with row_tile_span again.
+// with row_tile_span again (from f0..f3).
 constexpr int kSpanRows = 8;
 constexpr uint32_t kSpansTall = 0xffffffffu;
 constexpr uint32_t kSpansPacked = 0u;

@@ -335,7 +335,7 @@ __device__ __forceinline__ void stage_sh(const void* sh, int64_t base, int cnt, 
 }
 
 template <int DEG, int DT_SH>
-__global__ void __launch_bounds__(kPreThreads) preprocess_fwd_kernel(PreArgs a) {
+__global__ void __launch_bounds__(kPreThreads, 5) preprocess_fwd_kernel(PreArgs a) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   constexpr int K3 = 3 * K, ROW = K3 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -392,9 +392,21 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_fwd_kernel(PreArgs a) 
               const uint32_t tx0 = (uint32_t)xlo / kTile, tx1 = (uint32_t)xhi / kTile + 1;
               const uint32_t ty0 = (uint32_t)ylo / kTile, ty1 = (uint32_t)yhi / kTile + 1;
               rect = make_uint2(tx0 | (ty0 << 16), tx1 | (ty1 << 16));
-              // exact ellipse / tile test, row by row (row_tile_span)
+              // exact footprint / tile test, row by row (row_tile_span): E1 ...
               const float4 f0 = make_float4(P.sxy / dyy, P.detD / dyy, sqrtf(rho2) * P.sxy / sqrtf(dxx), ey);
               float4 f1 = make_float4(rho2, 1.0f / dyy, 0.0f, 0.0f);
+              // ... and E2, the smaller ellipse on the side beta^T d < 0, with
+              // conic Sigma_d^-1 + beta beta^T (determinant (1 + bsb) / det Sigma_d)
+              const float rho2m = 2.0f * logf(omax / tau) * (1.0f + 1.0f / 1024.0f);
+              float4 f2 = make_float4(0.0f, 0.0f, 0.0f, -1.0f);  // ymax < 0: empty
+              float4 f3 = make_float4(0.0f, 0.0f, bx, by);
+              if (rho2m > 0.0f && (bx != 0.0f || by != 0.0f)) {
+                const float a2 = P.a + bx * bx, b2 = P.b + bx * by, c2 = P.c + by * by;
+                const float det2 = (1.0f + bsb) / P.detD;
+                f2 = make_float4(-b2 / a2, 1.0f / a2, -sqrtf(rho2m) * b2 / sqrtf(c2 * det2), sqrtf(rho2m * a2 / det2));
+                f3.x = rho2m;
+                f3.y = det2 / a2;
+              }
               const uint32_t nrows = ty1 - ty0;
               bool packed = nrows <= (uint32_t)kSpanRows;
               uint32_t cum_lo = 0u, cum_hi = 0u, firsts = 0u;
@@ -405,7 +417,7 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_fwd_kernel(PreArgs a) 
                   if (rr < 4) cum_lo |= c8; else cum_hi |= c8;
                 }
                 int lo, hi;
-                if (row_tile_span(f0, f1, P.mx, P.my, (int)ty, c.width, c.height, lo, hi)) {
+                if (row_tile_span(f0, f1, f2, f3, P.mx, P.my, (int)ty, c.width, c.height, lo, hi)) {
                   ntouch += (uint32_t)(hi - lo + 1);
                   const uint32_t first = (uint32_t)(lo - (int)tx0);
                   packed = packed && first <= 15u;
@@ -421,11 +433,15 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_fwd_kernel(PreArgs a) 
                   cum_hi |= 0xffffffffu << (8 * (nrows - 4));
                 }
               }
-              a.ws.foot[2 * m] = f0;
-              a.ws.foot[2 * m + 1] =
+              a.ws.foot[4 * m + 1] =
                   packed ? make_float4(__uint_as_float(cum_lo), __uint_as_float(cum_hi), __uint_as_float(firsts),
                                        __uint_as_float(kSpansPacked))
                          : make_float4(f1.x, f1.y, 0.0f, __uint_as_float(kSpansTall));
+              if (!packed) {  // the emission enumerates the rows again
+                a.ws.foot[4 * m] = f0;
+                a.ws.foot[4 * m + 2] = f2;
+                a.ws.foot[4 * m + 3] = f3;
+              }
             }
           }
         }
