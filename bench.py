@@ -281,11 +281,18 @@ def run_ours(args):
     proj_bytes = args.n * (248 + 4) + nrec * 64 + args.n * 248
     bytes_ = {0: pre_bytes, 4: proj_bytes}
     dom = int(np.argmax(stage_mean))
+    # DRAM bytes per launch (read + write) of the dominant kernel from the ncu
+    # capture summarised in profiles/kernels_full_unbounded_1m_1080p.md, for
+    # the launch shape it was taken in (None for any other shape or workload)
+    ncu_traffic = {("render_bwd_composite", 2): 96.63e6}
+    traffic = None
+    if args.n == 1_000_000:
+        traffic = ncu_traffic.get((names[dom], tune["bwd_pixels_per_thread"] if dom == 3 else tune["fwd_pixels_per_thread"]))
     if dom in ops:
         achieved = ops[dom] / (stage_mean[dom] / 1e3) / 1e12
         out["roofline"] = {"kernel": names[dom], "bound": "alu", "achieved": round(achieved, 3),
                            "peak": round(alu_peak, 3), "unit": "TFLOP/s", "frac": round(achieved / alu_peak, 4),
-                           "traffic": None,
+                           "traffic": traffic,
                            "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz"}
     else:
         b = bytes_.get(dom, 0)
