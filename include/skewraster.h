@@ -290,6 +290,58 @@ sr_status sr_selftest_bounded_wait(const sr_plan* plan, void* ws, int32_t spin_l
  * stores the last frame's key count in *keys_needed if non-NULL. */
 sr_status sr_read_status(const sr_plan* plan, void* ws, int64_t* keys_needed, void* stream);
 
+/* ---- Training step ------------------------------------------------------
+ * The paper optimises its skew Gaussians inside the 3DGS framework
+ * (Preliminaries: gradient descent "driven by photometric loss"; Appendix
+ * "Implementation": the 3DGS protocol, learning rate 1e-4 for the skew
+ * parameters).  These two calls are that loop's other steps. */
+
+/* Bytes of device scratch sr_loss_l1_dssim needs for a plan's views. */
+size_t sr_loss_scratch_size(const sr_plan* plan);
+
+/* Photometric loss of all views of a plan and its gradient:
+ *   L = (1 - lambda) mean |C - T| + lambda (1 - mean SSIM(C, T)),
+ * means over the 3 channels and all pixels of all views; SSIM per channel
+ * with an 11 x 11 Gaussian window (sigma 1.5, normalised, zero padding),
+ * C1 = 0.01^2, C2 = 0.03^2 (values in [0, 1]).
+ * images, targets, d_images: device FP32, plan->image_offset[n_views] floats,
+ * each view [3][H][W] at its image offset (the layout of sr_render_fwd);
+ * d_images receives dL/dC (it may be the d_images of sr_render_bwd).
+ * loss: device float[1]; ssim_l1: optional device float[2] receiving the
+ * mean SSIM and the mean |C - T|.  ws: the plan's workspace after
+ * sr_preprocess (its view table).  scratch: device, sr_loss_scratch_size
+ * bytes, 256-byte aligned, overwritten.  lambda in [0, 1].
+ * Errors: SR_ERR_INVALID for NULL pointers, misalignment or lambda out of
+ * range; SR_ERR_CUDA if a launch fails. */
+sr_status sr_loss_l1_dssim(const sr_plan* plan, void* ws, const float* images, const float* targets, float lambda,
+                           float* d_images, float* loss, float* ssim_l1, void* scratch, void* stream);
+
+/* One Adam step (Kingma & Ba 2015, the update of torch.optim.Adam) over up to
+ * SR_ADAM_MAX_GROUPS parameter groups in one launch:
+ *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+ *   p -= lr / (1 - b1^step) * m / (sqrt(v) / sqrt(1 - b2^step) + eps).
+ * Each group: FP32 device arrays param (updated in place), grad, m, v (the
+ * moment states, zero before step 1, updated in place) of n elements; lr,
+ * and lr_rest for the elements whose index modulo period (> 0) is at least
+ * split_at (the higher-order SH coefficients of an [N][K][3] array:
+ * period 3K, split_at 3).  step >= 1.
+ * Errors: SR_ERR_INVALID for n_groups out of range, NULL arrays with n > 0,
+ * step < 1, betas outside [0, 1) or eps <= 0; SR_ERR_CUDA if the launch fails. */
+#define SR_ADAM_MAX_GROUPS 16
+typedef struct sr_adam_group {
+  float* param;
+  const float* grad;
+  float* m;
+  float* v;
+  int64_t n;
+  float lr;
+  float lr_rest;
+  int32_t period;
+  int32_t split_at;
+} sr_adam_group;
+sr_status sr_adam_step(const sr_adam_group* groups, int32_t n_groups, int64_t step, float beta1, float beta2,
+                       float eps, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -399,6 +399,41 @@ sr_status sr_frame_counters(const sr_plan* p, void* ws, uint64_t* pairs_tested, 
   return SR_OK;
 }
 
+size_t sr_loss_scratch_size(const sr_plan* p) {
+  if (!p || p->abi_version != SR_ABI_VERSION) return 0;
+  return loss_scratch_bytes(p->total_pixels, p->total_tiles);
+}
+
+sr_status sr_loss_l1_dssim(const sr_plan* p, void* ws, const float* images, const float* targets, float lambda,
+                           float* d_images, float* loss, float* ssim_l1, void* scratch, void* stream) {
+  sr_status s = check_plan(p, ws);
+  if (s != SR_OK) return s;
+  if (!images || !targets || !d_images || !loss || !scratch) return SR_ERR_INVALID;
+  if (!(lambda >= 0.0f && lambda <= 1.0f)) return SR_ERR_INVALID;
+  if (((uintptr_t)scratch & 255) != 0) return SR_ERR_INVALID;
+  if (p->tile_w != kTile || p->tile_h != kTile) return SR_ERR_UNSUPPORTED;
+  if (p->total_pixels == 0) return SR_OK;
+  const Ws w = ws_ptrs(*p, ws);
+  const cudaError_t e = launch_loss(images, targets, lambda, d_images, loss, ssim_l1, scratch, w.views, p->n_views,
+                                    p->total_tiles, p->total_pixels, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SR_OK : SR_ERR_CUDA;
+}
+
+sr_status sr_adam_step(const sr_adam_group* groups, int32_t n_groups, int64_t step, float beta1, float beta2,
+                       float eps, void* stream) {
+  if (!groups || n_groups < 1 || n_groups > SR_ADAM_MAX_GROUPS || step < 1) return SR_ERR_INVALID;
+  if (!(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f && eps > 0.0f)) return SR_ERR_INVALID;
+  for (int i = 0; i < n_groups; ++i) {
+    const sr_adam_group& g = groups[i];
+    if (g.n < 0 || g.period < 0 || g.split_at < 0) return SR_ERR_INVALID;
+    if (g.n > 0 && (!g.param || !g.grad || !g.m || !g.v)) return SR_ERR_INVALID;
+  }
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const cudaError_t e = launch_adam(groups, n_groups, step, beta1, beta2, eps, sms, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SR_OK : SR_ERR_CUDA;
+}
+
 sr_status sr_read_status(const sr_plan* p, void* ws, int64_t* keys_needed, void* stream) {
   sr_status s = check_plan(p, ws);
   if (s != SR_OK) return s;

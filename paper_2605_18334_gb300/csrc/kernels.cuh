@@ -60,5 +60,11 @@ cudaError_t launch_bin_phase2(const BinArgs& a, const int* run, long long keys_k
 cudaError_t launch_selftest_bounded_wait(const Ws& ws, unsigned long long cap, int spin_limit, cudaStream_t st);
 cudaError_t launch_render_fwd(const RenderArgs& a, int mode, int64_t total_tiles, cudaStream_t st);
 cudaError_t launch_render_bwd(const RenderArgs& a, int mode, int64_t total_tiles, cudaStream_t st);
+size_t loss_scratch_bytes(int64_t total_pixels, int64_t total_tiles);
+cudaError_t launch_loss(const float* images, const float* targets, float lambda, float* d_images, float* loss,
+                        float* ssim_l1, void* scratch, const ViewInfo* views, int n_views, int64_t total_tiles,
+                        int64_t total_pixels, cudaStream_t st);
+cudaError_t launch_adam(const sr_adam_group* groups, int n_groups, int64_t step, float b1, float b2, float eps,
+                        int sms, cudaStream_t st);
 
 }  // namespace sr

@@ -1,0 +1,359 @@
+// The training step around the rasterizer: the photometric loss and its
+// gradient, and a fused Adam update.  The paper trains its skew Gaussians
+// inside the 3DGS framework (Preliminaries: "driven by photometric loss";
+// Appendix "Implementation": the 3DGS protocol, learning rate 1e-4 for the
+// skew parameters), so the objective is 3DGS's
+//   L = (1 - lambda) mean |C - T| + lambda (1 - mean SSIM(C, T)),
+// SSIM per channel with an 11 x 11 Gaussian window (sigma 1.5, normalised,
+// zero padding), C1 = 0.01^2, C2 = 0.03^2, means over the 3 channels and
+// all pixels of all views.
+//
+// SSIM at pixel q, from windowed moments mu_x, mu_y, s_x = E[x^2] - mu_x^2,
+// s_y, s_xy = E[xy] - mu_x mu_y:
+//   S = A1 A2 / (B1 B2),  A1 = 2 mu_x mu_y + C1, A2 = 2 s_xy + C2,
+//                         B1 = mu_x^2 + mu_y^2 + C1, B2 = s_x + s_y + C2.
+// With a = dS/dmu_x = 2 A2 (mu_y B1 - mu_x A1) / (B1^2 B2),
+//      b = dS/ds_x = -A1 A2 / (B1 B2^2), c = dS/ds_xy = 2 A1 / (B1 B2),
+// and dmu_x(q)/dx_p = w(p - q), ds_x/dx_p = 2 w (x_p - mu_x), ds_xy/dx_p =
+// w (y_p - mu_y), the gradient of sum_q g S(q) is
+//   dx_p = (w * u)(p) + 2 x_p (w * v)(p) + y_p (w * k)(p),
+//   u = g (a - 2 mu_x b - mu_y c), v = g b, k = g c
+// (w symmetric, so the adjoint correlation is the same filter).  One kernel
+// computes the moments and u, v, k per 16 x 16 tile (a 26 x 26 halo in
+// shared memory, separable passes), a second filters u, v, k the same way.
+#include <cmath>
+
+#include "kernels.cuh"
+
+namespace sr {
+
+constexpr int kWin = 11, kHalf = 5, kHalo = kTile + 2 * kHalf;  // 26
+constexpr float kC1 = 0.0001f, kC2 = 0.0009f;                  // (0.01)^2, (0.03)^2
+
+__constant__ float c_win[kWin];
+
+struct LossArgs {
+  const float* images;
+  const float* targets;
+  float* d_images;
+  float* loss;          // [1]
+  float* ssim_l1;       // [2] or nullptr: mean SSIM, mean |C - T|
+  float* maps;          // u, v, k: [3][3 * total pixels] (channel-major per view like the images)
+  float* partial;       // [2][blocks]: per-block sums of S and |C - T|
+  const ViewInfo* views;
+  int n_views;
+  int64_t total_tiles;
+  int64_t total_values;  // 3 * total pixels
+  float lambda;
+};
+
+struct TileRef {
+  ViewInfo vi;
+  int x0, y0;       // first pixel of the tile
+  int64_t plane;    // offset of this channel's [H][W] plane
+};
+
+__device__ __forceinline__ TileRef loss_tile(const LossArgs& a, int64_t b) {
+  TileRef t;
+  const int ch = (int)(b / a.total_tiles);
+  const int64_t tile = b - (int64_t)ch * a.total_tiles;
+  const int v = view_of_tile(a.views, a.n_views, tile);
+  t.vi = a.views[v];
+  const int lt = (int)(tile - t.vi.tile_base);
+  t.x0 = (lt % t.vi.tiles_x) * kTile;
+  t.y0 = (lt / t.vi.tiles_x) * kTile;
+  t.plane = t.vi.image_offset + (int64_t)ch * t.vi.width * t.vi.height;
+  return t;
+}
+
+// Separable window sum of NM maps held in s_in[NM][kHalo][kHalo + 1] (the
+// tile and its halo); returns the filtered values of this thread's pixel.
+template <int NM>
+__device__ __forceinline__ void window_sum(float (*s_in)[kHalo][kHalo + 1], float (*s_h)[kHalo][kTile + 1],
+                                           float* out) {
+  for (int i = threadIdx.x; i < kHalo * kTile; i += blockDim.x) {
+    const int r = i / kTile, c = i - r * kTile;
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int k = 0; k < kWin; ++k) acc = __fmaf_rn(c_win[k], s_in[m][r][c + k], acc);
+      s_h[m][r][c] = acc;
+    }
+  }
+  __syncthreads();
+  const int ty = threadIdx.x / kTile, tx = threadIdx.x - ty * kTile;
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kWin; ++k) acc = __fmaf_rn(c_win[k], s_h[m][ty + k][tx], acc);
+    out[m] = acc;
+  }
+}
+
+__device__ __forceinline__ void block_sum2(float a, float b, float* s_red, float* out_a, float* out_b) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    s_red[2 * warp] = a;
+    s_red[2 * warp + 1] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float sa = 0.0f, sb = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      sa += s_red[2 * w];
+      sb += s_red[2 * w + 1];
+    }
+    *out_a = sa;
+    *out_b = sb;
+  }
+}
+
+// moments, SSIM and the maps u, v, k of one channel of one tile
+__global__ void __launch_bounds__(256) ssim_fwd_kernel(LossArgs a) {
+  __shared__ float s_in[5][kHalo][kHalo + 1];  // x, y, x^2, y^2, xy
+  __shared__ float s_h[5][kHalo][kTile + 1];
+  __shared__ float s_red[16];
+  const TileRef t = loss_tile(a, blockIdx.x);
+  const int W = t.vi.width, H = t.vi.height;
+  for (int i = threadIdx.x; i < kHalo * kHalo; i += blockDim.x) {
+    const int r = i / kHalo, c = i - r * kHalo;
+    const int px = t.x0 - kHalf + c, py = t.y0 - kHalf + r;
+    float x = 0.0f, y = 0.0f;
+    if (px >= 0 && px < W && py >= 0 && py < H) {
+      const int64_t o = t.plane + (int64_t)py * W + px;
+      x = a.images[o];
+      y = a.targets[o];
+    }
+    s_in[0][r][c] = x;
+    s_in[1][r][c] = y;
+    s_in[2][r][c] = x * x;
+    s_in[3][r][c] = y * y;
+    s_in[4][r][c] = x * y;
+  }
+  __syncthreads();
+  float mo[5];
+  window_sum<5>(s_in, s_h, mo);
+  const int ty = threadIdx.x / kTile, tx = threadIdx.x - ty * kTile;
+  const int px = t.x0 + tx, py = t.y0 + ty;
+  float s_val = 0.0f, l1 = 0.0f;
+  if (px < W && py < H) {
+    const float mx = mo[0], my = mo[1];
+    const float sx = mo[2] - mx * mx, sy = mo[3] - my * my, sxy = mo[4] - mx * my;
+    const float A1 = 2.0f * mx * my + kC1, A2 = 2.0f * sxy + kC2;
+    const float B1 = mx * mx + my * my + kC1, B2 = sx + sy + kC2;
+    const float inv = 1.0f / (B1 * B2);
+    s_val = A1 * A2 * inv;
+    const float da = 2.0f * A2 * (my * B1 - mx * A1) * inv / B1;
+    const float db = -s_val / B2;
+    const float dc = 2.0f * A1 * inv;
+    const float g = -a.lambda / (float)a.total_values;  // dL/dS
+    const int64_t o = t.plane + (int64_t)py * W + px;
+    a.maps[o] = g * (da - 2.0f * mx * db - my * dc);
+    a.maps[a.total_values + o] = g * db;
+    a.maps[2 * a.total_values + o] = g * dc;
+    l1 = fabsf(s_in[0][ty + kHalf][tx + kHalf] - s_in[1][ty + kHalf][tx + kHalf]);
+  }
+  block_sum2(s_val, l1, s_red, &a.partial[blockIdx.x], &a.partial[gridDim.x + blockIdx.x]);
+}
+
+// dL/dC = (w * u) + 2 x (w * v) + y (w * k) + (1 - lambda) sign(x - y) / N
+__global__ void __launch_bounds__(256) ssim_bwd_kernel(LossArgs a) {
+  __shared__ float s_in[3][kHalo][kHalo + 1];
+  __shared__ float s_h[3][kHalo][kTile + 1];
+  const TileRef t = loss_tile(a, blockIdx.x);
+  const int W = t.vi.width, H = t.vi.height;
+  for (int i = threadIdx.x; i < kHalo * kHalo; i += blockDim.x) {
+    const int r = i / kHalo, c = i - r * kHalo;
+    const int px = t.x0 - kHalf + c, py = t.y0 - kHalf + r;
+    float u = 0.0f, v = 0.0f, k = 0.0f;
+    if (px >= 0 && px < W && py >= 0 && py < H) {
+      const int64_t o = t.plane + (int64_t)py * W + px;
+      u = a.maps[o];
+      v = a.maps[a.total_values + o];
+      k = a.maps[2 * a.total_values + o];
+    }
+    s_in[0][r][c] = u;
+    s_in[1][r][c] = v;
+    s_in[2][r][c] = k;
+  }
+  __syncthreads();
+  float f[3];
+  window_sum<3>(s_in, s_h, f);
+  const int ty = threadIdx.x / kTile, tx = threadIdx.x - ty * kTile;
+  const int px = t.x0 + tx, py = t.y0 + ty;
+  if (px < W && py < H) {
+    const int64_t o = t.plane + (int64_t)py * W + px;
+    const float x = a.images[o], y = a.targets[o];
+    const float d = x - y;
+    const float sgn = d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f);
+    a.d_images[o] = f[0] + 2.0f * x * f[1] + y * f[2] + (1.0f - a.lambda) * sgn / (float)a.total_values;
+  }
+}
+
+// L from the per-block sums (one block, fixed order: deterministic)
+__global__ void __launch_bounds__(256) loss_reduce_kernel(LossArgs a, int blocks) {
+  __shared__ float s_red[16];
+  float s = 0.0f, l = 0.0f;
+  for (int i = threadIdx.x; i < blocks; i += blockDim.x) {
+    s += a.partial[i];
+    l += a.partial[blocks + i];
+  }
+  float ts = 0.0f, tl = 0.0f;
+  block_sum2(s, l, s_red, &ts, &tl);
+  if (threadIdx.x == 0) {
+    const float n = (float)a.total_values;
+    const float ms = ts / n, ml = tl / n;
+    a.loss[0] = (1.0f - a.lambda) * ml + a.lambda * (1.0f - ms);
+    if (a.ssim_l1) {
+      a.ssim_l1[0] = ms;
+      a.ssim_l1[1] = ml;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Adam (Kingma & Ba 2015), the update of torch.optim.Adam:
+//   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+//   p -= (lr / (1 - b1^t)) m / (sqrt(v) / sqrt(1 - b2^t) + eps)
+// over several parameter groups in one launch (blockIdx.y = group); within
+// a group, elements whose index modulo `period` is at least `split_at` use
+// lr_rest (the higher-order SH coefficients of an [N][K][3] array).
+// ---------------------------------------------------------------------------
+struct AdamGroupDev {
+  float* p;
+  const float* g;
+  float* m;
+  float* v;
+  int64_t n;
+  float step_size, step_size_rest;  // lr / (1 - b1^t) for the two learning rates
+  int32_t period, split_at;
+};
+
+struct AdamArgs {
+  AdamGroupDev grp[SR_ADAM_MAX_GROUPS];
+  float b1, b2, eps, inv_sqrt_bc2;  // inv_sqrt_bc2 = 1 / sqrt(1 - b2^t)
+};
+
+__device__ __forceinline__ void adam_one(float& p, float g, float& m, float& v, float step_size, const AdamArgs& a) {
+  m = __fmaf_rn(a.b1, m, (1.0f - a.b1) * g);
+  v = __fmaf_rn(a.b2, v, (1.0f - a.b2) * g * g);
+  const float denom = __fmaf_rn(__fsqrt_rn(v), a.inv_sqrt_bc2, a.eps);
+  p -= step_size * __fdiv_rn(m, denom);
+}
+
+__global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
+  const AdamGroupDev& G = a.grp[blockIdx.y];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool vec = G.period == 0 && (((uintptr_t)G.p | (uintptr_t)G.g | (uintptr_t)G.m | (uintptr_t)G.v) & 15) == 0;
+  if (vec) {
+    const int64_t n4 = G.n / 4;
+    for (int64_t i = tid; i < n4; i += stride) {
+      float4 p = reinterpret_cast<float4*>(G.p)[i];
+      const float4 g = reinterpret_cast<const float4*>(G.g)[i];
+      float4 m = reinterpret_cast<float4*>(G.m)[i];
+      float4 v = reinterpret_cast<float4*>(G.v)[i];
+      adam_one(p.x, g.x, m.x, v.x, G.step_size, a);
+      adam_one(p.y, g.y, m.y, v.y, G.step_size, a);
+      adam_one(p.z, g.z, m.z, v.z, G.step_size, a);
+      adam_one(p.w, g.w, m.w, v.w, G.step_size, a);
+      reinterpret_cast<float4*>(G.p)[i] = p;
+      reinterpret_cast<float4*>(G.m)[i] = m;
+      reinterpret_cast<float4*>(G.v)[i] = v;
+    }
+    for (int64_t i = 4 * n4 + tid; i < G.n; i += stride) adam_one(G.p[i], G.g[i], G.m[i], G.v[i], G.step_size, a);
+  } else {
+    for (int64_t i = tid; i < G.n; i += stride) {
+      const bool rest = G.period > 0 && (int32_t)(i % G.period) >= G.split_at;
+      adam_one(G.p[i], G.g[i], G.m[i], G.v[i], rest ? G.step_size_rest : G.step_size, a);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static cudaError_t upload_window(cudaStream_t st) {
+  float w[kWin];
+  double sum = 0.0, e[kWin];
+  for (int k = 0; k < kWin; ++k) {
+    const double d = k - kHalf;
+    e[k] = std::exp(-d * d / (2.0 * 1.5 * 1.5));
+    sum += e[k];
+  }
+  for (int k = 0; k < kWin; ++k) w[k] = (float)(e[k] / sum);
+  return cudaMemcpyToSymbolAsync(c_win, w, sizeof(w), 0, cudaMemcpyHostToDevice, st);
+}
+
+size_t loss_scratch_bytes(int64_t total_pixels, int64_t total_tiles) {
+  const size_t maps = sizeof(float) * 9 * (size_t)total_pixels;
+  const size_t part = sizeof(float) * 2 * 3 * (size_t)total_tiles;
+  return (maps + 255) / 256 * 256 + (part + 255) / 256 * 256;
+}
+
+cudaError_t launch_loss(const float* images, const float* targets, float lambda, float* d_images, float* loss,
+                        float* ssim_l1, void* scratch, const ViewInfo* views, int n_views, int64_t total_tiles,
+                        int64_t total_pixels, cudaStream_t st) {
+  cudaError_t e = upload_window(st);
+  if (e != cudaSuccess) return e;
+  LossArgs a;
+  a.images = images;
+  a.targets = targets;
+  a.d_images = d_images;
+  a.loss = loss;
+  a.ssim_l1 = ssim_l1;
+  a.maps = static_cast<float*>(scratch);
+  a.partial = reinterpret_cast<float*>(static_cast<char*>(scratch) +
+                                       (sizeof(float) * 9 * (size_t)total_pixels + 255) / 256 * 256);
+  a.views = views;
+  a.n_views = n_views;
+  a.total_tiles = total_tiles;
+  a.total_values = 3 * total_pixels;
+  a.lambda = lambda;
+  const int64_t blocks = 3 * total_tiles;
+  ssim_fwd_kernel<<<(unsigned)blocks, 256, 0, st>>>(a);
+  ssim_bwd_kernel<<<(unsigned)blocks, 256, 0, st>>>(a);
+  loss_reduce_kernel<<<1, 256, 0, st>>>(a, (int)blocks);
+  count_launches(3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(const sr_adam_group* groups, int n_groups, int64_t step, float b1, float b2, float eps,
+                        int sms, cudaStream_t st) {
+  AdamArgs a;
+  const double bc1 = 1.0 - std::pow((double)b1, (double)step);
+  const double bc2 = 1.0 - std::pow((double)b2, (double)step);
+  int64_t max_n = 0;
+  for (int i = 0; i < n_groups; ++i) {
+    const sr_adam_group& g = groups[i];
+    AdamGroupDev& d = a.grp[i];
+    d.p = g.param;
+    d.g = g.grad;
+    d.m = g.m;
+    d.v = g.v;
+    d.n = g.n;
+    d.step_size = (float)(g.lr / bc1);
+    d.step_size_rest = (float)(g.lr_rest / bc1);
+    d.period = g.period;
+    d.split_at = g.split_at;
+    max_n = std::max<int64_t>(max_n, g.n);
+  }
+  a.b1 = b1;
+  a.b2 = b2;
+  a.eps = eps;
+  a.inv_sqrt_bc2 = (float)(1.0 / std::sqrt(bc2));
+  const int64_t want = (max_n / 4 + 255) / 256;
+  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
+  adam_kernel<<<dim3(gx, (unsigned)n_groups), 256, 0, st>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace sr

@@ -22,7 +22,15 @@ SR_F32, SR_BF16, SR_F16 = 0, 1, 2
 EXPORTS = ["sr_abi_version", "sr_status_string", "sr_config_default", "sr_camera_from_gl", "sr_plan_init",
            "sr_workspace_size", "sr_preprocess", "sr_bin_sort", "sr_render_fwd", "sr_render_bwd", "sr_read_status",
            "sr_kernel_launches", "sr_frame_counters", "sr_sort_keys_noalloc", "sr_render_bwd_composite",
-           "sr_render_bwd_project", "sr_selftest_bounded_wait"]
+           "sr_render_bwd_project", "sr_selftest_bounded_wait", "sr_loss_scratch_size", "sr_loss_l1_dssim",
+           "sr_adam_step"]
+
+SR_ADAM_MAX_GROUPS = 16
+
+
+class sr_adam_group(C.Structure):
+    _fields_ = [("param", C.c_void_p), ("grad", C.c_void_p), ("m", C.c_void_p), ("v", C.c_void_p), ("n", C.c_int64),
+                ("lr", C.c_float), ("lr_rest", C.c_float), ("period", C.c_int32), ("split_at", C.c_int32)]
 
 
 class sr_gaussians(C.Structure):
@@ -119,6 +127,14 @@ def load(build_if_missing: bool = True):
         lib.sr_kernel_launches.argtypes = []
         lib.sr_frame_counters.argtypes = [P(sr_plan), C.c_void_p, P(C.c_uint64), P(C.c_uint64), C.c_void_p]
         lib.sr_frame_counters.restype = C.c_int
+        lib.sr_loss_scratch_size.restype = C.c_size_t
+        lib.sr_loss_scratch_size.argtypes = [P(sr_plan)]
+        lib.sr_loss_l1_dssim.argtypes = [P(sr_plan), C.c_void_p, C.c_void_p, C.c_void_p, C.c_float, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.sr_loss_l1_dssim.restype = C.c_int
+        lib.sr_adam_step.argtypes = [P(sr_adam_group), C.c_int32, C.c_int64, C.c_float, C.c_float, C.c_float,
+                                     C.c_void_p]
+        lib.sr_adam_step.restype = C.c_int
         for name in ("sr_config_default", "sr_camera_from_gl", "sr_plan_init", "sr_preprocess", "sr_bin_sort",
                      "sr_render_fwd", "sr_render_bwd", "sr_read_status", "sr_render_bwd_composite",
                      "sr_render_bwd_project"):
@@ -229,6 +245,25 @@ def sr_frame_counters(plan, ws_ptr: int, stream: int):
     check("sr_frame_counters", load().sr_frame_counters(C.byref(plan), C.c_void_p(ws_ptr), C.byref(t), C.byref(b),
                                                         C.c_void_p(stream)))
     return int(t.value), int(b.value)
+
+
+def sr_loss_scratch_size(plan) -> int:
+    return int(load().sr_loss_scratch_size(C.byref(plan)))
+
+
+def sr_loss_l1_dssim(plan, ws_ptr: int, images_ptr: int, targets_ptr: int, lam: float, d_images_ptr: int,
+                     loss_ptr: int, ssim_l1_ptr: int, scratch_ptr: int, stream: int):
+    check("sr_loss_l1_dssim", load().sr_loss_l1_dssim(
+        C.byref(plan), C.c_void_p(ws_ptr), C.c_void_p(images_ptr), C.c_void_p(targets_ptr), C.c_float(lam),
+        C.c_void_p(d_images_ptr), C.c_void_p(loss_ptr), C.c_void_p(ssim_l1_ptr or None), C.c_void_p(scratch_ptr),
+        C.c_void_p(stream)))
+
+
+def sr_adam_step(groups: list, step: int, beta1: float, beta2: float, eps: float, stream: int):
+    """groups: sr_adam_group structures (device pointers as ints)."""
+    arr = (sr_adam_group * len(groups))(*groups)
+    check("sr_adam_step", load().sr_adam_step(arr, len(groups), C.c_int64(step), C.c_float(beta1), C.c_float(beta2),
+                                              C.c_float(eps), C.c_void_p(stream)))
 
 
 def sr_read_status(plan, ws_ptr: int, stream: int):

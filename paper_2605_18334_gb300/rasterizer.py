@@ -221,13 +221,17 @@ class Rasterizer:
                                 _stream_ptr(stream))
         return out
 
-    def backward(self, g: Gaussians, d_images: torch.Tensor, stream=None, want_stats: bool = False) -> dict:
+    def backward(self, g: Gaussians, d_images: torch.Tensor, stream=None, want_stats: bool = False,
+                 out: dict | None = None) -> dict:
         """Gradients of sum(d_images * images) w.r.t. every attribute (FP32),
-        through sr_render_bwd."""
+        through sr_render_bwd (into ``out``'s tensors when given, e.g. the
+        previous call's result)."""
         if d_images.dtype != torch.float32 or not d_images.is_contiguous() or d_images.numel() != self.images.numel():
             raise ValueError("d_images must be a contiguous float32 tensor shaped like the image buffer")
         dev = self.device
         n = g.n
+        if out is not None and out["means"].shape[0] == n and (out.get("means2d_abs") is not None) == want_stats:
+            return self._backward_into(g, d_images, stream, out)
         out = dict(means=torch.empty(n, 3, device=dev), log_scales=torch.empty(n, 3, device=dev),
                    quats=torch.empty(n, 4, device=dev),
                    opacity_logits=torch.empty(g.opacity_logits.shape, device=dev),
@@ -236,6 +240,17 @@ class Rasterizer:
         if want_stats:
             out["means2d_abs"] = torch.empty(n, device=dev)
             out["depth_grad"] = torch.empty(n, device=dev)
+        gr = N.sr_grads()
+        for k in ("means", "log_scales", "quats", "opacity_logits", "skew", "sh", "split_dir", "means2d_abs",
+                  "depth_grad"):
+            t = out.get(k)
+            setattr(gr, k, t.data_ptr() if t is not None else None)
+        N.sr_render_bwd(self.plan, g.to_c(), self.cams_dev.data_ptr(), self.cfg_c, self.ws.data_ptr(),
+                        d_images.data_ptr(), self.t_final.data_ptr(), self.n_contrib.data_ptr(), gr,
+                        _stream_ptr(stream))
+        return out
+
+    def _backward_into(self, g: Gaussians, d_images: torch.Tensor, stream, out: dict) -> dict:
         gr = N.sr_grads()
         for k in ("means", "log_scales", "quats", "opacity_logits", "skew", "sh", "split_dir", "means2d_abs",
                   "depth_grad"):

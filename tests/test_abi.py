@@ -166,3 +166,28 @@ def test_stage_calls_reject_invalid_arguments_without_device_work(lib):
     # corrupted plan
     p.abi_version = 99
     assert lib.sr_bin_sort(C.byref(p), C.byref(cfg), C.c_void_p(4096), None, None) == N.SR_ERR_INVALID
+
+
+def test_training_calls_reject_invalid_arguments_without_device_work(lib):
+    cfg = Config().to_c()
+    cams = [N.sr_camera_from_gl(np.eye(4), 64, 48, 1.0, 1.0)]
+    p = N.sr_plan_init(cfg, _desc(100, deg=0), cams, 1000)
+    assert lib.sr_loss_scratch_size(C.byref(p)) >= 9 * 4 * 64 * 48
+    ok = C.c_void_p(4096)
+    # lambda out of range, NULL buffers, misaligned scratch
+    assert lib.sr_loss_l1_dssim(C.byref(p), ok, ok, ok, C.c_float(1.5), ok, ok, None, ok, None) == N.SR_ERR_INVALID
+    assert lib.sr_loss_l1_dssim(C.byref(p), ok, None, ok, C.c_float(0.2), ok, ok, None, ok, None) == N.SR_ERR_INVALID
+    assert lib.sr_loss_l1_dssim(C.byref(p), ok, ok, ok, C.c_float(0.2), ok, ok, None, C.c_void_p(4096 + 16),
+                                None) == N.SR_ERR_INVALID
+    g = N.sr_adam_group()
+    g.param = g.grad = g.m = g.v = 4096
+    g.n, g.lr, g.lr_rest = 10, 1e-3, 1e-3
+    arr = (N.sr_adam_group * 1)(g)
+    assert lib.sr_adam_step(arr, 0, 1, C.c_float(0.9), C.c_float(0.999), C.c_float(1e-15), None) == N.SR_ERR_INVALID
+    assert lib.sr_adam_step(arr, 17, 1, C.c_float(0.9), C.c_float(0.999), C.c_float(1e-15), None) == N.SR_ERR_INVALID
+    assert lib.sr_adam_step(arr, 1, 0, C.c_float(0.9), C.c_float(0.999), C.c_float(1e-15), None) == N.SR_ERR_INVALID
+    assert lib.sr_adam_step(arr, 1, 1, C.c_float(1.0), C.c_float(0.999), C.c_float(1e-15), None) == N.SR_ERR_INVALID
+    assert lib.sr_adam_step(arr, 1, 1, C.c_float(0.9), C.c_float(0.999), C.c_float(0.0), None) == N.SR_ERR_INVALID
+    g.grad = None
+    arr = (N.sr_adam_group * 1)(g)
+    assert lib.sr_adam_step(arr, 1, 1, C.c_float(0.9), C.c_float(0.999), C.c_float(1e-15), None) == N.SR_ERR_INVALID
