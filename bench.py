@@ -312,6 +312,7 @@ def run_ours(args):
     if not args.no_variants:
         out["variants"] = variants(args, sc, cam, up, dev, flush)
         out["variants"]["trajectory_64"] = trajectory(args, sc, dev, flush)
+        out["variants"]["train_step"] = train_step(args, sc, cam, dev, flush)
     out["e2e"] = e2e(args, sc, cam, up, dev, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, cam, up, args.cpu_budget)
@@ -381,6 +382,53 @@ def variants(args, sc, cam, up, dev, flush):
     del r, g
     torch.cuda.empty_cache()
     return res
+
+
+def train_step(args, sc, cam, dev, flush):
+    """Training step at the headline frame: render, photometric loss (L1 +
+    D-SSIM) and its gradient, backward to every attribute, one Adam update of
+    all 62 FP32 values per Gaussian; per-stage CUDA events, L2 flushed before
+    each step.  The target is a fixed synthetic image (uniform noise)."""
+    import numpy as np
+    import torch
+
+    from paper_2605_18334_gb300.rasterizer import Gaussians
+    from paper_2605_18334_gb300.train import Trainer
+
+    K = max(5, args.steps // 2)
+    stream = torch.cuda.current_stream()
+    g = Gaussians.from_scene(sc, device=dev)
+    target = torch.as_tensor(np.random.default_rng(3).uniform(0, 1, 3 * 1080 * 1920).astype(np.float32),
+                             device=dev).contiguous()
+    tr = Trainer(g, [cam], target, key_capacity=int(12 * args.n))
+    tr.rast.autotune(g, target)
+    for _ in range(3):
+        tr.step()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
+    for k in range(K):
+        flush.zero_()
+        e = ev[k]
+        e[0].record(stream)
+        tr.rast.forward(g)
+        e[1].record(stream)
+        tr.loss(target)
+        e[2].record(stream)
+        tr.grads = tr.rast.backward(g, tr.loss.d_images, out=tr.grads)
+        e[3].record(stream)
+        tr.adam.step(tr.grads)
+        e[4].record(stream)
+    torch.cuda.synchronize()
+    ms = np.array([[ev[k][i].elapsed_time(ev[k][i + 1]) for i in range(4)] for k in range(K)]).mean(0)
+    n_vals = sum(getattr(g, f).numel() for f in ("means", "log_scales", "quats", "opacity_logits", "skew", "sh"))
+    adam_bytes = n_vals * 28  # read param, grad, m, v; write param, m, v (FP32)
+    out = {"steps_per_s": round(1e3 / ms.sum(), 2),
+           "stages_ms": {"forward": round(ms[0], 4), "loss": round(ms[1], 4), "backward": round(ms[2], 4),
+                         "adam": round(ms[3], 4)},
+           "adam_GBps": round(adam_bytes / (ms[3] / 1e3) / 1e9, 1), "loss": round(float(tr.loss.loss.item()), 6)}
+    del tr, g
+    torch.cuda.empty_cache()
+    return out
 
 
 def trajectory(args, sc, dev, flush, n_views=64):

@@ -122,20 +122,31 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(LossArgs a) {
   __shared__ float s_red[16];
   const TileRef t = loss_tile(a, blockIdx.x);
   const int W = t.vi.width, H = t.vi.height;
-  for (int i = threadIdx.x; i < kHalo * kHalo; i += blockDim.x) {
-    const int r = i / kHalo, c = i - r * kHalo;
+  // the tile and its halo: every load of the thread issued before the stores
+  constexpr int kPer = (kHalo * kHalo + 255) / 256;
+  float xs[kPer], ys[kPer];
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int i = threadIdx.x + 256 * j, r = i / kHalo, c = i - r * kHalo;
     const int px = t.x0 - kHalf + c, py = t.y0 - kHalf + r;
-    float x = 0.0f, y = 0.0f;
-    if (px >= 0 && px < W && py >= 0 && py < H) {
+    xs[j] = ys[j] = 0.0f;
+    if (i < kHalo * kHalo && px >= 0 && px < W && py >= 0 && py < H) {
       const int64_t o = t.plane + (int64_t)py * W + px;
-      x = a.images[o];
-      y = a.targets[o];
+      xs[j] = a.images[o];
+      ys[j] = a.targets[o];
     }
-    s_in[0][r][c] = x;
-    s_in[1][r][c] = y;
-    s_in[2][r][c] = x * x;
-    s_in[3][r][c] = y * y;
-    s_in[4][r][c] = x * y;
+  }
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int i = threadIdx.x + 256 * j, r = i / kHalo, c = i - r * kHalo;
+    if (i < kHalo * kHalo) {
+      const float x = xs[j], y = ys[j];
+      s_in[0][r][c] = x;
+      s_in[1][r][c] = y;
+      s_in[2][r][c] = x * x;
+      s_in[3][r][c] = y * y;
+      s_in[4][r][c] = x * y;
+    }
   }
   __syncthreads();
   float mo[5];
@@ -169,19 +180,28 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(LossArgs a) {
   __shared__ float s_h[3][kHalo][kTile + 1];
   const TileRef t = loss_tile(a, blockIdx.x);
   const int W = t.vi.width, H = t.vi.height;
-  for (int i = threadIdx.x; i < kHalo * kHalo; i += blockDim.x) {
-    const int r = i / kHalo, c = i - r * kHalo;
+  constexpr int kPer = (kHalo * kHalo + 255) / 256;
+  float us[kPer], vs[kPer], ks[kPer];
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int i = threadIdx.x + 256 * j, r = i / kHalo, c = i - r * kHalo;
     const int px = t.x0 - kHalf + c, py = t.y0 - kHalf + r;
-    float u = 0.0f, v = 0.0f, k = 0.0f;
-    if (px >= 0 && px < W && py >= 0 && py < H) {
+    us[j] = vs[j] = ks[j] = 0.0f;
+    if (i < kHalo * kHalo && px >= 0 && px < W && py >= 0 && py < H) {
       const int64_t o = t.plane + (int64_t)py * W + px;
-      u = a.maps[o];
-      v = a.maps[a.total_values + o];
-      k = a.maps[2 * a.total_values + o];
+      us[j] = a.maps[o];
+      vs[j] = a.maps[a.total_values + o];
+      ks[j] = a.maps[2 * a.total_values + o];
     }
-    s_in[0][r][c] = u;
-    s_in[1][r][c] = v;
-    s_in[2][r][c] = k;
+  }
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int i = threadIdx.x + 256 * j, r = i / kHalo, c = i - r * kHalo;
+    if (i < kHalo * kHalo) {
+      s_in[0][r][c] = us[j];
+      s_in[1][r][c] = vs[j];
+      s_in[2][r][c] = ks[j];
+    }
   }
   __syncthreads();
   float f[3];
@@ -252,23 +272,35 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
   const AdamGroupDev& G = a.grp[blockIdx.y];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool vec = G.period == 0 && (((uintptr_t)G.p | (uintptr_t)G.g | (uintptr_t)G.m | (uintptr_t)G.v) & 15) == 0;
+  // 16-byte vectors when the arrays are aligned and a period (if any) is a
+  // multiple of 4, so the 4 elements of a vector sit in one period
+  const bool vec = (G.period % 4) == 0 &&
+                   (((uintptr_t)G.p | (uintptr_t)G.g | (uintptr_t)G.m | (uintptr_t)G.v) & 15) == 0;
   if (vec) {
     const int64_t n4 = G.n / 4;
+    const int32_t p4 = G.period / 4;
     for (int64_t i = tid; i < n4; i += stride) {
       float4 p = reinterpret_cast<float4*>(G.p)[i];
       const float4 g = reinterpret_cast<const float4*>(G.g)[i];
       float4 m = reinterpret_cast<float4*>(G.m)[i];
       float4 v = reinterpret_cast<float4*>(G.v)[i];
-      adam_one(p.x, g.x, m.x, v.x, G.step_size, a);
-      adam_one(p.y, g.y, m.y, v.y, G.step_size, a);
-      adam_one(p.z, g.z, m.z, v.z, G.step_size, a);
-      adam_one(p.w, g.w, m.w, v.w, G.step_size, a);
+      const int32_t pos = p4 ? (int32_t)(i % p4) * 4 : 0;  // index of .x within its period
+      const float s0 = p4 && pos >= G.split_at ? G.step_size_rest : G.step_size;
+      const float s1 = p4 && pos + 1 >= G.split_at ? G.step_size_rest : G.step_size;
+      const float s2 = p4 && pos + 2 >= G.split_at ? G.step_size_rest : G.step_size;
+      const float s3 = p4 && pos + 3 >= G.split_at ? G.step_size_rest : G.step_size;
+      adam_one(p.x, g.x, m.x, v.x, s0, a);
+      adam_one(p.y, g.y, m.y, v.y, s1, a);
+      adam_one(p.z, g.z, m.z, v.z, s2, a);
+      adam_one(p.w, g.w, m.w, v.w, s3, a);
       reinterpret_cast<float4*>(G.p)[i] = p;
       reinterpret_cast<float4*>(G.m)[i] = m;
       reinterpret_cast<float4*>(G.v)[i] = v;
     }
-    for (int64_t i = 4 * n4 + tid; i < G.n; i += stride) adam_one(G.p[i], G.g[i], G.m[i], G.v[i], G.step_size, a);
+    for (int64_t i = 4 * n4 + tid; i < G.n; i += stride) {
+      const bool rest = G.period > 0 && (int32_t)(i % G.period) >= G.split_at;
+      adam_one(G.p[i], G.g[i], G.m[i], G.v[i], rest ? G.step_size_rest : G.step_size, a);
+    }
   } else {
     for (int64_t i = tid; i < G.n; i += stride) {
       const bool rest = G.period > 0 && (int32_t)(i % G.period) >= G.split_at;
