@@ -66,30 +66,42 @@ __device__ __forceinline__ TileRef loss_tile(const LossArgs& a, int64_t b) {
   return t;
 }
 
-// Separable window sum of NM maps held in s_in[NM][kHalo][kHalo + 1] (the
-// tile and its halo); returns the filtered values of this thread's pixel.
-template <int NM>
-__device__ __forceinline__ void window_sum(float (*s_in)[kHalo][kHalo + 1], float (*s_h)[kHalo][kTile + 1],
-                                           float* out) {
-  for (int i = threadIdx.x; i < kHalo * kTile; i += blockDim.x) {
-    const int r = i / kTile, c = i - r * kTile;
+// Separable window sums over a 16 x 16 tile with a 5-pixel halo, in shared
+// memory, with sliding windows in registers: the horizontal pass takes one
+// (halo row, map) per thread (26 loads, 16 outputs of 11 taps), the
+// vertical pass one (tile column, map) per thread; s_v[m][y][x] receives map
+// m filtered at tile pixel (x, y).  MAP(m, r, c) reads map m at halo (r, c).
+template <int NM, class Map>
+__device__ __forceinline__ void window_sums(const Map& MAP, float (*s_h)[kHalo][kTile + 1],
+                                            float (*s_v)[kTile][kTile + 1]) {
+  for (int it = threadIdx.x; it < NM * kHalo; it += blockDim.x) {
+    const int m = it / kHalo, r = it - m * kHalo;
+    float in[kHalo];
 #pragma unroll
-    for (int m = 0; m < NM; ++m) {
+    for (int c = 0; c < kHalo; ++c) in[c] = MAP(m, r, c);
+#pragma unroll
+    for (int c = 0; c < kTile; ++c) {
       float acc = 0.0f;
 #pragma unroll
-      for (int k = 0; k < kWin; ++k) acc = __fmaf_rn(c_win[k], s_in[m][r][c + k], acc);
+      for (int k = 0; k < kWin; ++k) acc = __fmaf_rn(c_win[k], in[c + k], acc);
       s_h[m][r][c] = acc;
     }
   }
   __syncthreads();
-  const int ty = threadIdx.x / kTile, tx = threadIdx.x - ty * kTile;
+  for (int it = threadIdx.x; it < NM * kTile; it += blockDim.x) {
+    const int m = it / kTile, c = it - m * kTile;
+    float in[kHalo];
 #pragma unroll
-  for (int m = 0; m < NM; ++m) {
-    float acc = 0.0f;
+    for (int r = 0; r < kHalo; ++r) in[r] = s_h[m][r][c];
 #pragma unroll
-    for (int k = 0; k < kWin; ++k) acc = __fmaf_rn(c_win[k], s_h[m][ty + k][tx], acc);
-    out[m] = acc;
+    for (int r = 0; r < kTile; ++r) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int k = 0; k < kWin; ++k) acc = __fmaf_rn(c_win[k], in[r + k], acc);
+      s_v[m][r][c] = acc;
+    }
   }
+  __syncthreads();
 }
 
 __device__ __forceinline__ void block_sum2(float a, float b, float* s_red, float* out_a, float* out_b) {
@@ -117,8 +129,9 @@ __device__ __forceinline__ void block_sum2(float a, float b, float* s_red, float
 
 // moments, SSIM and the maps u, v, k of one channel of one tile
 __global__ void __launch_bounds__(256) ssim_fwd_kernel(LossArgs a) {
-  __shared__ float s_in[5][kHalo][kHalo + 1];  // x, y, x^2, y^2, xy
+  __shared__ float s_in[2][kHalo][kHalo + 1];  // x, y of the tile and its halo
   __shared__ float s_h[5][kHalo][kTile + 1];
+  __shared__ float s_v[5][kTile][kTile + 1];   // windowed x, y, x^2, y^2, xy
   __shared__ float s_red[16];
   const TileRef t = loss_tile(a, blockIdx.x);
   const int W = t.vi.width, H = t.vi.height;
@@ -140,17 +153,22 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(LossArgs a) {
   for (int j = 0; j < kPer; ++j) {
     const int i = threadIdx.x + 256 * j, r = i / kHalo, c = i - r * kHalo;
     if (i < kHalo * kHalo) {
-      const float x = xs[j], y = ys[j];
-      s_in[0][r][c] = x;
-      s_in[1][r][c] = y;
-      s_in[2][r][c] = x * x;
-      s_in[3][r][c] = y * y;
-      s_in[4][r][c] = x * y;
+      s_in[0][r][c] = xs[j];
+      s_in[1][r][c] = ys[j];
     }
   }
   __syncthreads();
+  const auto moments = [&](int m, int r, int c) {
+    const float x = s_in[0][r][c], y = s_in[1][r][c];
+    return m == 0 ? x : m == 1 ? y : m == 2 ? x * x : m == 3 ? y * y : x * y;
+  };
+  window_sums<5>(moments, s_h, s_v);
   float mo[5];
-  window_sum<5>(s_in, s_h, mo);
+  {
+    const int ty = threadIdx.x / kTile, tx = threadIdx.x - ty * kTile;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) mo[m] = s_v[m][ty][tx];
+  }
   const int ty = threadIdx.x / kTile, tx = threadIdx.x - ty * kTile;
   const int px = t.x0 + tx, py = t.y0 + ty;
   float s_val = 0.0f, l1 = 0.0f;
@@ -178,6 +196,7 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(LossArgs a) {
 __global__ void __launch_bounds__(256) ssim_bwd_kernel(LossArgs a) {
   __shared__ float s_in[3][kHalo][kHalo + 1];
   __shared__ float s_h[3][kHalo][kTile + 1];
+  __shared__ float s_v[3][kTile][kTile + 1];
   const TileRef t = loss_tile(a, blockIdx.x);
   const int W = t.vi.width, H = t.vi.height;
   constexpr int kPer = (kHalo * kHalo + 255) / 256;
@@ -204,8 +223,14 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(LossArgs a) {
     }
   }
   __syncthreads();
+  const auto maps = [&](int m, int r, int c) { return s_in[m][r][c]; };
+  window_sums<3>(maps, s_h, s_v);
   float f[3];
-  window_sum<3>(s_in, s_h, f);
+  {
+    const int ty = threadIdx.x / kTile, tx = threadIdx.x - ty * kTile;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) f[m] = s_v[m][ty][tx];
+  }
   const int ty = threadIdx.x / kTile, tx = threadIdx.x - ty * kTile;
   const int px = t.x0 + tx, py = t.y0 + ty;
   if (px < W && py < H) {
