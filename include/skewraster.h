@@ -342,6 +342,16 @@ typedef struct sr_adam_group {
 sr_status sr_adam_step(const sr_adam_group* groups, int32_t n_groups, int64_t step, float beta1, float beta2,
                        float eps, void* stream);
 
+/* Densification statistics over iterations (Sec. "Depth-Aware Densification
+ * Strategy"), from one backward's sr_grads.means2d_abs (g^(uv) of this step)
+ * and sr_grads.depth_grad (dL/dz of the centre): for each of the n Gaussians
+ * with a nonzero g^(uv), uv_sum += g^(uv) and seen += 1 (the 3DGS average
+ * is uv_sum / seen); z_max = max(z_max, |dL/dz|), the paper's g^(z).  All
+ * arrays device, [n], the accumulators updated in place (zero them to start).
+ * Errors: SR_ERR_INVALID for n < 0 or NULL arrays with n > 0. */
+sr_status sr_densify_stats(const float* means2d_abs, const float* depth_grad, int64_t n, float* uv_sum,
+                           int32_t* seen, float* z_max, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

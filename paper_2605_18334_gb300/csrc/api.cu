@@ -434,6 +434,17 @@ sr_status sr_adam_step(const sr_adam_group* groups, int32_t n_groups, int64_t st
   return e == cudaSuccess ? SR_OK : SR_ERR_CUDA;
 }
 
+sr_status sr_densify_stats(const float* means2d_abs, const float* depth_grad, int64_t n, float* uv_sum,
+                           int32_t* seen, float* z_max, void* stream) {
+  if (n < 0) return SR_ERR_INVALID;
+  if (n > 0 && (!means2d_abs || !depth_grad || !uv_sum || !seen || !z_max)) return SR_ERR_INVALID;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const cudaError_t e =
+      launch_densify_stats(means2d_abs, depth_grad, n, uv_sum, seen, z_max, sms, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SR_OK : SR_ERR_CUDA;
+}
+
 sr_status sr_read_status(const sr_plan* p, void* ws, int64_t* keys_needed, void* stream) {
   sr_status s = check_plan(p, ws);
   if (s != SR_OK) return s;

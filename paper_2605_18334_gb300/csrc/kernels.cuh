@@ -66,5 +66,7 @@ cudaError_t launch_loss(const float* images, const float* targets, float lambda,
                         int64_t total_pixels, cudaStream_t st);
 cudaError_t launch_adam(const sr_adam_group* groups, int n_groups, int64_t step, float b1, float b2, float eps,
                         int sms, cudaStream_t st);
+cudaError_t launch_densify_stats(const float* g_uv, const float* g_z, int64_t n, float* uv_sum, int32_t* seen,
+                                 float* z_max, int sms, cudaStream_t st);
 
 }  // namespace sr

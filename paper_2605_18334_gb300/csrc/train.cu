@@ -335,6 +335,26 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Densification statistics over iterations (Sec. "Depth-Aware Densification
+// Strategy"): the 2D positional gradient norm g^(uv) accumulated with the
+// number of steps a Gaussian was seen in, and g^(z) = max over iterations of
+// |dL/dz| of its centre.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) densify_stats_kernel(const float* __restrict__ g_uv,
+                                                            const float* __restrict__ g_z, int64_t n,
+                                                            float* __restrict__ uv_sum, int32_t* __restrict__ seen,
+                                                            float* __restrict__ z_max) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float u = g_uv[i];
+    if (u > 0.0f) {
+      uv_sum[i] += u;
+      seen[i] += 1;
+    }
+    z_max[i] = fmaxf(z_max[i], fabsf(g_z[i]));
+  }
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 static cudaError_t upload_window(cudaStream_t st) {
@@ -409,6 +429,15 @@ cudaError_t launch_adam(const sr_adam_group* groups, int n_groups, int64_t step,
   const int64_t want = (max_n / 4 + 255) / 256;
   const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
   adam_kernel<<<dim3(gx, (unsigned)n_groups), 256, 0, st>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_densify_stats(const float* g_uv, const float* g_z, int64_t n, float* uv_sum, int32_t* seen,
+                                 float* z_max, int sms, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8));
+  densify_stats_kernel<<<grid, 256, 0, st>>>(g_uv, g_z, n, uv_sum, seen, z_max);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -23,7 +23,7 @@ EXPORTS = ["sr_abi_version", "sr_status_string", "sr_config_default", "sr_camera
            "sr_workspace_size", "sr_preprocess", "sr_bin_sort", "sr_render_fwd", "sr_render_bwd", "sr_read_status",
            "sr_kernel_launches", "sr_frame_counters", "sr_sort_keys_noalloc", "sr_render_bwd_composite",
            "sr_render_bwd_project", "sr_selftest_bounded_wait", "sr_loss_scratch_size", "sr_loss_l1_dssim",
-           "sr_adam_step"]
+           "sr_adam_step", "sr_densify_stats"]
 
 SR_ADAM_MAX_GROUPS = 16
 
@@ -135,6 +135,9 @@ def load(build_if_missing: bool = True):
         lib.sr_adam_step.argtypes = [P(sr_adam_group), C.c_int32, C.c_int64, C.c_float, C.c_float, C.c_float,
                                      C.c_void_p]
         lib.sr_adam_step.restype = C.c_int
+        lib.sr_densify_stats.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p]
+        lib.sr_densify_stats.restype = C.c_int
         for name in ("sr_config_default", "sr_camera_from_gl", "sr_plan_init", "sr_preprocess", "sr_bin_sort",
                      "sr_render_fwd", "sr_render_bwd", "sr_read_status", "sr_render_bwd_composite",
                      "sr_render_bwd_project"):
@@ -264,6 +267,13 @@ def sr_adam_step(groups: list, step: int, beta1: float, beta2: float, eps: float
     arr = (sr_adam_group * len(groups))(*groups)
     check("sr_adam_step", load().sr_adam_step(arr, len(groups), C.c_int64(step), C.c_float(beta1), C.c_float(beta2),
                                               C.c_float(eps), C.c_void_p(stream)))
+
+
+def sr_densify_stats(g_uv_ptr: int, g_z_ptr: int, n: int, uv_sum_ptr: int, seen_ptr: int, z_max_ptr: int,
+                     stream: int):
+    check("sr_densify_stats", load().sr_densify_stats(C.c_void_p(g_uv_ptr), C.c_void_p(g_z_ptr), C.c_int64(n),
+                                                      C.c_void_p(uv_sum_ptr), C.c_void_p(seen_ptr),
+                                                      C.c_void_p(z_max_ptr), C.c_void_p(stream)))
 
 
 def sr_read_status(plan, ws_ptr: int, stream: int):

@@ -91,13 +91,22 @@ class Trainer:
     """Fits a scene's attributes to target images of its cameras."""
 
     def __init__(self, g: Gaussians, cameras: list, targets: torch.Tensor, config: Config | None = None,
-                 lr: dict | None = None, lam: float = 0.2, key_capacity: int | None = None):
+                 lr: dict | None = None, lam: float = 0.2, key_capacity: int | None = None,
+                 densify_stats: bool = False):
         self.g = g
         self.rast = Rasterizer(g, cameras, config, key_capacity=key_capacity)
         self.targets = targets
         self.loss = PhotometricLoss(self.rast, lam)
         self.adam = Adam(g, lr)
         self.grads = None
+        # densification statistics over the steps (Sec. "Depth-Aware
+        # Densification Strategy"): g^(uv) summed with its step count, g^(z) max
+        self.densify_stats = densify_stats
+        if densify_stats:
+            dev = g.means.device
+            self.uv_sum = torch.zeros(g.n, device=dev)
+            self.seen = torch.zeros(g.n, dtype=torch.int32, device=dev)
+            self.z_max = torch.zeros(g.n, device=dev)
 
     def step(self, stream=None) -> torch.Tensor:
         """One training step; returns the device loss of the rendered frame."""
@@ -105,6 +114,11 @@ class Trainer:
         if self.loss.d_images.numel() != self.rast.images.numel():  # the plan grew: new image buffer sizes
             self.loss = PhotometricLoss(self.rast, self.loss.lam)
         loss = self.loss(self.targets, stream)
-        self.grads = self.rast.backward(self.g, self.loss.d_images, stream, out=self.grads)
+        self.grads = self.rast.backward(self.g, self.loss.d_images, stream, want_stats=self.densify_stats,
+                                        out=self.grads)
+        if self.densify_stats:
+            N.sr_densify_stats(self.grads["means2d_abs"].data_ptr(), self.grads["depth_grad"].data_ptr(), self.g.n,
+                               self.uv_sum.data_ptr(), self.seen.data_ptr(), self.z_max.data_ptr(),
+                               _stream_ptr(stream))
         self.adam.step(self.grads, stream)
         return loss

@@ -203,3 +203,33 @@ def test_training_steps_reduce_the_loss():
     tr = Trainer(g, cams, targets, lr=dict(means=1e-3))
     losses = [float(tr.step().item()) for _ in range(40)]
     assert losses[-1] < 0.8 * losses[0], losses
+
+
+@pytest.mark.gpu
+def test_densification_statistics_accumulate_over_steps():
+    """uv_sum / seen / z_max after several steps equal the per-step
+    statistics of the backward accumulated on the host."""
+    _gpu()
+    from paper_2605_18334_gb300 import scenes
+    from paper_2605_18334_gb300.rasterizer import Config, Gaussians, Rasterizer
+    from paper_2605_18334_gb300.train import Trainer
+
+    sc = scenes.cluster(seed=13, n=2000, sh_degree=1)
+    cams = [scenes.identity_camera(80, 60)]
+    tgt = torch.rand(3 * 80 * 60, device="cuda")
+    g = Gaussians.from_scene(sc)
+    tr = Trainer(g, cams, tgt, densify_stats=True)
+    uv = np.zeros(sc.n)
+    seen = np.zeros(sc.n, np.int64)
+    zmax = np.zeros(sc.n)
+    for _ in range(4):
+        tr.step()
+        a = tr.grads["means2d_abs"].cpu().numpy().astype(np.float64)
+        z = np.abs(tr.grads["depth_grad"].cpu().numpy().astype(np.float64))
+        uv += np.where(a > 0, a, 0)
+        seen += (a > 0)
+        zmax = np.maximum(zmax, z)
+    np.testing.assert_allclose(tr.uv_sum.cpu().numpy(), uv, rtol=1e-6, atol=1e-12)
+    np.testing.assert_array_equal(tr.seen.cpu().numpy(), seen)
+    np.testing.assert_array_equal(tr.z_max.cpu().numpy(), zmax.astype(np.float32))
+    assert seen.max() == 4 and zmax.max() > 0
