@@ -210,8 +210,11 @@ __device__ __forceinline__ bool eval_pair(const float4& r0, const float4& r1, co
 // rho sqrt(Syy), inv_syy = 1/Syy; at height y (relative to mu_y) it spans
 //   x = slope y -+ sqrt(wdet (rho2 - y^2 / Syy)).
 // Record layout: f0 = E1's e; f1 = (rho2, inv_syy) of E1 (or the packed row
-// spans, see below); f2 = E2's e; f3 = (rho_-^2, inv_syy of E2, beta_x,
-// beta_y).  With beta = 0 the footprint is E1 alone.
+// spans, see below); f2 = E2's e; f3 = (rho_-^2, inv_syy of E2, slope,
+// side) with the half-plane's boundary x = slope y (slope = -beta_y /
+// beta_x) and side = +1 / -1 for beta_x > 0 / < 0 (the half-plane is to the
+// right / left of the line), +2 / -2 for beta_x = 0 and beta_y > 0 / < 0
+// (above / below mu), 0 for beta = 0 (the footprint is E1 alone).
 //
 // x-extent (relative to mu_x) of an ellipse within the band of heights
 // [y0, y1] (relative to mu_y): the right edge is largest at y =
@@ -245,18 +248,18 @@ __device__ __forceinline__ bool row_tile_span(const float4& f0, const float4& f1
   const float y1 = __fadd_rn((float)min(ty * kTile + kTile - 1, height - 1) + 0.5f, -my);
   float xl, xr;
   if (!ellipse_band(f0, f1.x, f1.y, y0, y1, xl, xr)) return false;
-  const float bx = f3.z, by = f3.w;
-  if (bx != 0.0f || by != 0.0f) {
+  const float side = f3.w;
+  if (side != 0.0f) {
     // the half-plane beta^T d >= 0 within the band (clipped to E1's heights)
     const float c0 = fmaxf(y0, -f0.w), c1 = fminf(y1, f0.w);
     bool hon = true;
     float hl = -INFINITY, hr = INFINITY;
-    if (bx > 0.0f) {
-      hl = fminf(__fdiv_rn(-__fmul_rn(by, c0), bx), __fdiv_rn(-__fmul_rn(by, c1), bx));
-    } else if (bx < 0.0f) {
-      hr = fmaxf(__fdiv_rn(-__fmul_rn(by, c0), bx), __fdiv_rn(-__fmul_rn(by, c1), bx));
+    if (side == 1.0f) {
+      hl = fminf(__fmul_rn(f3.z, c0), __fmul_rn(f3.z, c1));
+    } else if (side == -1.0f) {
+      hr = fmaxf(__fmul_rn(f3.z, c0), __fmul_rn(f3.z, c1));
     } else {
-      hon = by > 0.0f ? c1 >= 0.0f : c0 <= 0.0f;
+      hon = side > 0.0f ? c1 >= 0.0f : c0 <= 0.0f;
     }
     float l2 = 0.0f, r2 = 0.0f;
     const bool e2on = ellipse_band(f2, f3.x, f3.y, y0, y1, l2, r2);

@@ -399,7 +399,9 @@ __global__ void __launch_bounds__(kPreThreads, 5) preprocess_fwd_kernel(PreArgs 
               // conic Sigma_d^-1 + beta beta^T (determinant (1 + bsb) / det Sigma_d)
               const float rho2m = 2.0f * logf(omax / tau) * (1.0f + 1.0f / 1024.0f);
               float4 f2 = make_float4(0.0f, 0.0f, 0.0f, -1.0f);  // ymax < 0: empty
-              float4 f3 = make_float4(0.0f, 0.0f, bx, by);
+              const float side = bx > 0.0f ? 1.0f : bx < 0.0f ? -1.0f : by > 0.0f ? 2.0f : by < 0.0f ? -2.0f : 0.0f;
+              // the slope stays finite (a huge slope and a zero height must not make a NaN)
+              float4 f3 = make_float4(0.0f, 0.0f, bx != 0.0f ? fminf(fmaxf(-by / bx, -1e30f), 1e30f) : 0.0f, side);
               if (rho2m > 0.0f && (bx != 0.0f || by != 0.0f)) {
                 const float a2 = P.a + bx * bx, b2 = P.b + bx * by, c2 = P.c + by * by;
                 const float det2 = (1.0f + bsb) / P.detD;
