@@ -202,6 +202,7 @@ sr_status sr_plan_init(sr_plan* p, const sr_config* cfg, const sr_gaussians* g, 
   sizes[WS_D2] = p->forward_only ? 0 : sizeof(float) * kD2Stride * (size_t)m;
   sizes[WS_FOOT] = sizeof(float4) * 4 * (size_t)m;
   sizes[WS_MASK] = p->forward_only ? 0 : sizeof(uint32_t) * 256 * (size_t)(key_capacity / 32 + tb + 1);
+  sizes[WS_TILE_ORDER] = sizeof(uint32_t) * ((size_t)tb + 128);
   size_t off = 0;
   for (int k = 0; k < WS_NUM_SLOTS; ++k) {
     p->off[k] = off;
@@ -291,6 +292,7 @@ static RenderArgs render_args(const sr_plan* p, const sr_config* cfg, void* ws) 
   r.d_images = nullptr;
   r.d2 = w.d2;
   r.mask = w.mask;
+  r.tile_order = w.tile_order;
   r.px_fwd = cfg->fwd_pixels_per_thread > 0 ? cfg->fwd_pixels_per_thread : 2;
   r.px_bwd = cfg->bwd_pixels_per_thread > 0 ? cfg->bwd_pixels_per_thread : 2;
   return r;

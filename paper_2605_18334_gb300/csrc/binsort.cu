@@ -796,6 +796,70 @@ cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Composite order: tiles by descending length of their key lists (log2
+// buckets; empty tiles last), so the heaviest tiles start first and the last
+// wave of the composites holds light ones.  Counters (cnt[64], cursor[64])
+// follow the order array and start at zero.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int tile_bucket(const uint2* ranges, int64_t t) {
+  const uint2 r = tile_range(ranges, t);
+  const uint32_t len = r.y - r.x;
+  return len ? __clz(len) : 32;  // 0 for the longest lists
+}
+
+// one block for up to kOrderOneBlock tiles: count, scan and scatter in
+// shared memory
+constexpr int64_t kOrderOneBlock = 65536;
+__global__ void __launch_bounds__(1024) tile_order_block_kernel(const uint2* __restrict__ ranges, int64_t tiles,
+                                                                uint32_t* __restrict__ order) {
+  __shared__ uint32_t s_cnt[33], s_cur[33];
+  if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0u;
+  __syncthreads();
+  for (int64_t t = threadIdx.x; t < tiles; t += blockDim.x) atomicAdd(&s_cnt[tile_bucket(ranges, t)], 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int b = 0; b < 33; ++b) {
+      s_cur[b] = run;
+      run += s_cnt[b];
+    }
+  }
+  __syncthreads();
+  for (int64_t t = threadIdx.x; t < tiles; t += blockDim.x)
+    order[atomicAdd(&s_cur[tile_bucket(ranges, t)], 1u)] = (uint32_t)t;
+}
+
+__global__ void __launch_bounds__(256) tile_order_count_kernel(const uint2* __restrict__ ranges, int64_t tiles,
+                                                               uint32_t* __restrict__ cnt) {
+  __shared__ uint32_t s_cnt[33];
+  if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0u;
+  __syncthreads();
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&s_cnt[tile_bucket(ranges, t)], 1u);
+  __syncthreads();
+  if (threadIdx.x < 33 && s_cnt[threadIdx.x]) atomicAdd(&cnt[threadIdx.x], s_cnt[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(256) tile_order_scatter_kernel(const uint2* __restrict__ ranges, int64_t tiles,
+                                                                 const uint32_t* __restrict__ cnt,
+                                                                 uint32_t* __restrict__ cursor,
+                                                                 uint32_t* __restrict__ order) {
+  __shared__ uint32_t s_base[33];
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int b = 0; b < 33; ++b) {
+      s_base[b] = run;
+      run += cnt[b];
+    }
+  }
+  __syncthreads();
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += (int64_t)gridDim.x * blockDim.x) {
+    const int b = tile_bucket(ranges, t);
+    order[s_base[b] + atomicAdd(&cursor[b], 1u)] = (uint32_t)t;
+  }
+}
+
 // Phase 2: tile passes (run[p] != 0) and ranges.  keys_known: exact key
 // count (sizes the grids), or -1 to size them for the capacity.
 cudaError_t launch_bin_phase2(const BinArgs& a, const int* run, long long keys_known, cudaStream_t st) {
@@ -821,6 +885,19 @@ cudaError_t launch_bin_phase2(const BinArgs& a, const int* run, long long keys_k
                                                                                                  1ull << 20));
     ranges_kernel<<<grid, 256, 0, st>>>(a.ws.keys[0], a.ws.status, a.cap, a.ws.ranges, 0);
     count_launches(1);
+  }
+  // composite order of the tiles
+  if (a.total_tiles <= kOrderOneBlock) {
+    tile_order_block_kernel<<<1, 1024, 0, st>>>(a.ws.ranges, a.total_tiles, a.ws.tile_order);
+    count_launches(1);
+  } else {
+    uint32_t* counters = a.ws.tile_order + a.total_tiles;
+    if ((e = cudaMemsetAsync(counters, 0, sizeof(uint32_t) * 128, st)) != cudaSuccess) return e;
+    const unsigned tgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((a.total_tiles + 255) / 256, 1024));
+    tile_order_count_kernel<<<tgrid, 256, 0, st>>>(a.ws.ranges, a.total_tiles, counters);
+    tile_order_scatter_kernel<<<tgrid, 256, 0, st>>>(a.ws.ranges, a.total_tiles, counters, counters + 64,
+                                                     a.ws.tile_order);
+    count_launches(2);
   }
   return cudaGetLastError();
 }

@@ -36,6 +36,7 @@ enum WsSlot {
   WS_D2,           // float[M][16] per-(view, Gaussian) 2D gradients
   WS_FOOT,         // float4[M][4] footprint constants or packed row spans (row_tile_span)
   WS_MASK,         // uint32_t[(cap/32 + tiles + 1) * 256] per-pixel blend masks (see render.cu)
+  WS_TILE_ORDER,   // uint32_t[tiles] composite order (longest key lists first) + uint32_t[2][64] counters
   WS_NUM_SLOTS
 };
 
@@ -370,6 +371,7 @@ struct Ws {
   float* d2;
   float4* foot;
   uint32_t* mask;   // null when the plan is forward-only
+  uint32_t* tile_order;
 };
 
 inline Ws ws_ptrs(const sr_plan& p, void* base) {
@@ -399,6 +401,7 @@ inline Ws ws_ptrs(const sr_plan& p, void* base) {
   w.d2 = reinterpret_cast<float*>(at(WS_D2));
   w.foot = reinterpret_cast<float4*>(at(WS_FOOT));
   w.mask = p.forward_only ? nullptr : reinterpret_cast<uint32_t*>(at(WS_MASK));
+  w.tile_order = reinterpret_cast<uint32_t*>(at(WS_TILE_ORDER));
   return w;
 }
 

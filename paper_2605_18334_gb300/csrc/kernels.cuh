@@ -39,6 +39,7 @@ struct RenderArgs {     // forward and backward composite
   const uint32_t* vals0;
   const uint32_t* vals1;
   const uint2* ranges;
+  const uint32_t* tile_order;  // blockIdx.x -> tile (longest key lists first)
   const ViewInfo* views;
   Status* status;
   int n_views;

@@ -97,14 +97,15 @@ template <int MODE, int PX, bool REC>
 __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_kernel(RenderArgs a) {
   constexpr int NT = 256 / PX;
   __shared__ float4 s_r0[kBatch], s_r1[kBatch], s_r2[MODE == MODE_PLAIN ? 1 : kBatch], s_r3[kBatch];
-  const TileCoord tc = tile_coord(a, blockIdx.x);
+  const int64_t tile = a.tile_order[blockIdx.x];
+  const TileCoord tc = tile_coord(a, tile);
   const PixelMap pm = pixel_map<PX>(tc);
   const int px = pm.px, py0 = pm.py0, pi0 = pm.pi0;
   const float fx = (float)px + 0.5f;
-  const uint2 range = tile_range(a.ranges, blockIdx.x);
+  const uint2 range = tile_range(a.ranges, tile);
   const uint32_t* vals = a.status->sorted_buf ? a.vals1 : a.vals0;
   const float amin = a.cfg.alpha_min, amax = a.cfg.alpha_max, tstop = a.cfg.t_stop;
-  uint32_t* mbase = REC ? mask_tile_base(a.mask, range, blockIdx.x) : nullptr;
+  uint32_t* mbase = REC ? mask_tile_base(a.mask, range, tile) : nullptr;
 
   float T[PX], C0[PX], C1[PX], C2[PX];
   uint32_t last[PX], stop[PX], mw[PX];
@@ -251,11 +252,12 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
   // Gaussian per thread) are free of bank conflicts
   __shared__ float s_acc[16][kBatch + 1];
   __shared__ uint32_t s_max;
-  const TileCoord tc = tile_coord(a, blockIdx.x);
+  const int64_t tile = a.tile_order[blockIdx.x];
+  const TileCoord tc = tile_coord(a, tile);
   const PixelMap pm = pixel_map<PX>(tc);
   const int px = pm.px, py0 = pm.py0;
   const float fx = (float)px + 0.5f;
-  const uint2 range = tile_range(a.ranges, blockIdx.x);
+  const uint2 range = tile_range(a.ranges, tile);
   const uint32_t* vals = a.status->sorted_buf ? a.vals1 : a.vals0;
   const float amin = a.cfg.alpha_min, amax = a.cfg.alpha_max;
   const int lane = threadIdx.x & 31;
@@ -265,7 +267,7 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
   float T[PX], g0[PX], g1[PX], g2[PX], R0[PX], R1[PX], R2[PX];
   uint32_t my_end[PX], bw[PX];
   const int pi0 = pm.pi0;
-  const uint32_t* mbase = mask_tile_base(a.mask, range, blockIdx.x);
+  const uint32_t* mbase = mask_tile_base(a.mask, range, tile);
   uint32_t my_max = 0;
 #pragma unroll
   for (int p = 0; p < PX; ++p) {

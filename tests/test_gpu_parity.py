@@ -484,3 +484,17 @@ def test_unbounded_1m_1080p_in_the_bench_launch_configuration():
     og = oracle.render_backward(sc, oracle.camera_from_gl(cam), oracle_config(Config()),
                                 up.reshape(3, -1)[:, flat].T, pixels=pix_b)
     compare_grads(gr, og, GRAD_FIELDS)
+
+
+def test_composite_order_over_many_tiles():
+    """Nine 1080p views (73,440 tiles, past the one-block ordering of the
+    composites' tile order): every view's keys bit-exact and its image at
+    sampled pixels against the oracle."""
+    sc = scenes.unbounded(seed=21, n=3000)
+    cams = scenes.trajectory_cameras(9, resolutions=((1920, 1080),))
+    r, _ = gpu_forward(sc, cams)
+    assert int(r.plan.total_tiles) > 65536
+    rng = np.random.default_rng(21)
+    for v in range(len(cams)):
+        pix = np.stack([rng.integers(0, 1920, 300), rng.integers(0, 1080, 300)], 1).astype(np.int32)
+        check_view(r, sc, cams, v, Config(), pixels=pix)
