@@ -157,14 +157,16 @@ struct PairEval {
   float alpha;   // o G E, before the clamp
 };
 
-template <int MODE>
+// GATE = false skips the early rejection, for pairs known to pass it (the
+// backward replays only pairs the forward blended).
+template <int MODE, bool GATE = true>
 __device__ __forceinline__ bool eval_pair(const float4& r0, const float4& r1, const float4& r2, float thr, float px,
                                           float py, PairEval& e) {
   e.dx = __fadd_rn(px, -r0.x);
   e.dy = __fadd_rn(py, -r0.y);
   const float lin = __fmaf_rn(r0.z, e.dx, __fmul_rn(r0.w, e.dy));
   const float p2 = __fmaf_rn(lin, e.dx, __fmul_rn(__fmul_rn(r1.x, e.dy), e.dy));
-  if (!(p2 >= thr)) return false;  // alpha < alpha_min guaranteed (and NaN-safe)
+  if (GATE && !(p2 >= thr)) return false;  // alpha < alpha_min guaranteed (and NaN-safe)
   e.G = ex2_approx(p2);
   if (r1.y == 0.0f && r1.z == 0.0f) {  // zero skew: 1 + erf(0) = 1 exactly
     e.E = 1.0f;

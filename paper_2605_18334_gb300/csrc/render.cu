@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
   const float fx = (float)px + 0.5f;
   const uint2 range = tile_range(a.ranges, tile);
   const uint32_t* vals = a.status->sorted_buf ? a.vals1 : a.vals0;
-  const float amin = a.cfg.alpha_min, amax = a.cfg.alpha_max;
+  const float amax = a.cfg.alpha_max;
   const int lane = threadIdx.x & 31;
   const int64_t plane = (int64_t)tc.vi.width * tc.vi.height;
   const float* gimg = a.d_images + tc.vi.image_offset;
@@ -336,9 +336,9 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
       for (int p = 0; p < PX; ++p) {
         if (!((bw[p] >> bit) & 1u)) continue;  // not blended in the forward pass
         PairEval e;
-        if (!eval_pair<MODE>(r0, r1, r2, r3.w, fx, (float)(py0 + p) + 0.5f, e)) continue;
+        // blended in the forward pass: the same arithmetic passes the alpha gate again
+        eval_pair<MODE, false>(r0, r1, r2, r3.w, fx, (float)(py0 + p) + 0.5f, e);
         const float alpha = fminf(e.alpha, amax);
-        if (alpha < amin) continue;
         contrib = true;
         const float one_m = 1.0f - alpha;
         T[p] = __fdividef(T[p], one_m);  // T_k (alpha <= alpha_max < 1)
