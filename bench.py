@@ -284,7 +284,7 @@ def run_ours(args):
     # DRAM bytes per launch (read + write) of the dominant kernel from the ncu
     # capture summarised in profiles/kernels_full_unbounded_1m_1080p.md, for
     # the launch shape it was taken in (None for any other shape or workload)
-    ncu_traffic = {("render_bwd_composite", 2): 96.63e6}
+    ncu_traffic = {("render_bwd_composite", 2): 96.93e6}
     traffic = None
     if args.n == 1_000_000:
         traffic = ncu_traffic.get((names[dom], tune["bwd_pixels_per_thread"] if dom == 3 else tune["fwd_pixels_per_thread"]))
