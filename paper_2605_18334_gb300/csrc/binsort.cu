@@ -4,19 +4,22 @@
 //
 //   depth sort   the M records by their 32-bit depth key (records that touch
 //                no tile carry ~0 and sink to the end): 4 stable 8-bit passes
-//                over M, not over the (much larger) number of tile keys
+//                over M, not over the (much larger) number of tile keys; the
+//                last pass writes the records' tile counts in depth order
 //   scan         exclusive scan of the tile counts in depth order
 //   duplicate    one 32-bit global tile id per touched tile, value = record
-//                index, emitted in depth order (warp-cooperative, coalesced)
+//                index, emitted in depth order (warp-cooperative, coalesced),
+//                counting the tile sort's digit histograms on the way
 //   tile sort    stable LSD passes over the tile-id bits only; stability
 //                keeps the depth order (and index order of equal depths)
-//                inside every tile
-//   ranges       [start, end) of each tile in the sorted list
+//                inside every tile; the last pass also reduces the tile ranges
+//   order        the composites' tile order, longest key lists first
 //
 // Every radix pass is one onesweep launch: a block ranks a partition of 4096
-// keys with warp match-any, publishes its digit counts, resolves its global
-// offsets by a decoupled look-back over the preceding partitions (each wait
-// bounded), and scatters through shared memory so writes go out in runs.
+// keys with warp match-any, stages them in shared memory in block-local
+// order, resolves its global offsets by a decoupled look-back over the
+// preceding partitions (each wait bounded), and scatters each digit's run
+// contiguously.
 #include <algorithm>
 #include <mutex>
 
@@ -742,7 +745,8 @@ static int run_passes(const KEY* keys_in, const uint32_t* vals_in, KEY* const* k
   return cur;
 }
 
-// Phase 1: depth sort of the records, scan, duplicate, tile histograms.
+// Phase 1: depth sort of the records, scan, key duplication (with the tile
+// sort's digit histograms).
 cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms) {
   const int64_t m = a.n * a.n_views;
   cudaError_t e;
