@@ -50,6 +50,10 @@ def parse():
                     help="forward pixels per thread (0: autotune)")
     ap.add_argument("--bwd-px", type=int, default=0, choices=[0, 1, 2, 4],
                     help="backward pixels per thread (0: autotune)")
+    ap.add_argument("--fwd-batch", type=int, default=256, choices=[128, 256, 512],
+                    help="forward records per staged batch when the launch shape is fixed")
+    ap.add_argument("--bwd-batch", type=int, default=256, choices=[128, 256],
+                    help="backward records per staged batch when the launch shape is fixed")
     return ap.parse_args()
 
 
@@ -203,6 +207,7 @@ def run_ours(args):
 
     if args.fwd_px and args.bwd_px:  # fixed launch shapes (e.g. for a profiler run)
         r.set_pixels_per_thread(args.fwd_px, args.bwd_px)
+        r.set_batch(args.fwd_batch, args.bwd_batch)
         tune = {"fwd_pixels_per_thread": args.fwd_px, "bwd_pixels_per_thread": args.bwd_px, "fwd_ms": {},
                 "bwd_ms": {}, "fixed": True}
     else:
@@ -249,7 +254,9 @@ def run_ours(args):
 
     cfgd = config_dict(args.n)
     cfgd["launch"] = {"fwd_pixels_per_thread": tune["fwd_pixels_per_thread"],
-                      "bwd_pixels_per_thread": tune["bwd_pixels_per_thread"], "autotuned": not tune.get("fixed")}
+                      "bwd_pixels_per_thread": tune["bwd_pixels_per_thread"],
+                      "fwd_batch": r.config.fwd_batch or 256, "bwd_batch": r.config.bwd_batch or 256,
+                      "autotuned": not tune.get("fixed")}
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K,
            "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfgd,
@@ -265,7 +272,9 @@ def run_ours(args):
     out["blends_per_s"] = round(blended / (stage_mean[2] / 1e3), 1)
     out["clocks"] = clocks
     out["autotune_ms"] = {"fwd": {str(k): round(v, 4) for k, v in tune["fwd_ms"].items()},
-                          "bwd": {str(k): round(v, 4) for k, v in tune["bwd_ms"].items()}}
+                          "bwd": {str(k): round(v, 4) for k, v in tune["bwd_ms"].items()},
+                          "fwd_batch": {str(k): round(v, 4) for k, v in tune.get("fwd_batch_ms", {}).items()},
+                          "bwd_batch": {str(k): round(v, 4) for k, v in tune.get("bwd_batch_ms", {}).items()}}
 
     # roofline of the dominant stage (measured live with the events above)
     peaks = measured_peaks()
@@ -284,10 +293,12 @@ def run_ours(args):
     # DRAM bytes per launch (read + write) of the dominant kernel from the ncu
     # capture summarised in profiles/kernels_full_unbounded_1m_1080p.md, for
     # the launch shape it was taken in (None for any other shape or workload)
-    ncu_traffic = {("render_bwd_composite", 2): 96.93e6}
+    ncu_traffic = {("render_bwd_composite", 2, 256): 96.93e6}
     traffic = None
     if args.n == 1_000_000:
-        traffic = ncu_traffic.get((names[dom], tune["bwd_pixels_per_thread"] if dom == 3 else tune["fwd_pixels_per_thread"]))
+        shape = ((tune["bwd_pixels_per_thread"], r.config.bwd_batch or 256) if dom == 3 else
+                 (tune["fwd_pixels_per_thread"], r.config.fwd_batch or 256))
+        traffic = ncu_traffic.get((names[dom],) + shape)
     if dom in ops:
         achieved = ops[dom] / (stage_mean[dom] / 1e3) / 1e12
         out["roofline"] = {"kernel": names[dom], "bound": "alu", "achieved": round(achieved, 3),

@@ -106,13 +106,13 @@ typedef struct sr_config {
   float near_z;               /* cull camera z <= near_z (0.2) */
   float bg[3];                /* background colour */
   int32_t antialias_comp;     /* 1: d = o * sqrt(det Sigma' / det(Sigma' + sI)); 0: d = o */
-  int32_t render_blocks_per_sm; /* reserved for the render launch shape (0) */
+  int32_t fwd_batch;          /* 128, 256 or 512 (0 = 256): records sr_render_fwd stages in shared memory per batch */
   int32_t sort_spin_limit;    /* 0 = auto; bound on each look-back wait of the sort */
   int32_t fwd_pixels_per_thread; /* 1, 2 or 4 (0 = 2): pixels each thread of sr_render_fwd owns */
   int32_t bwd_pixels_per_thread; /* 1, 2 or 4 (0 = 2): pixels each thread of sr_render_bwd owns */
   int32_t forward_only;       /* plans made with 1 record no per-pixel blend masks (less workspace);
                                  sr_render_bwd on them returns SR_ERR_UNSUPPORTED */
-  int32_t reserved_[1];
+  int32_t bwd_batch;          /* 128 or 256 (0 = 256): records sr_render_bwd stages per batch */
 } sr_config;
 
 /* Gradients of the loss w.r.t. the attributes, FP32, device, caller-owned,

@@ -48,6 +48,8 @@ sr_status check_config(const sr_config* c) {
     if (!std::isfinite(c->bg[k])) return SR_ERR_INVALID;
   for (int px : {c->fwd_pixels_per_thread, c->bwd_pixels_per_thread})
     if (px != 0 && px != 1 && px != 2 && px != 4) return SR_ERR_INVALID;
+  if (c->fwd_batch != 0 && c->fwd_batch != 128 && c->fwd_batch != 256 && c->fwd_batch != 512) return SR_ERR_INVALID;
+  if (c->bwd_batch != 0 && c->bwd_batch != 128 && c->bwd_batch != 256) return SR_ERR_INVALID;
   return SR_OK;
 }
 
@@ -293,6 +295,8 @@ static RenderArgs render_args(const sr_plan* p, const sr_config* cfg, void* ws) 
   r.d2 = w.d2;
   r.mask = w.mask;
   r.tile_order = w.tile_order;
+  r.batch_fwd = cfg->fwd_batch > 0 ? cfg->fwd_batch : 256;
+  r.batch_bwd = cfg->bwd_batch > 0 ? cfg->bwd_batch : 256;
   r.px_fwd = cfg->fwd_pixels_per_thread > 0 ? cfg->fwd_pixels_per_thread : 2;
   r.px_bwd = cfg->bwd_pixels_per_thread > 0 ? cfg->bwd_pixels_per_thread : 2;
   return r;

@@ -21,7 +21,6 @@
 
 namespace sr {
 
-constexpr int kBatch = 256;
 
 struct TileCoord {
   ViewInfo vi;
@@ -57,11 +56,11 @@ __device__ __forceinline__ PixelMap pixel_map(const TileCoord& tc) {
   return m;
 }
 
-template <int MODE>
+template <int MODE, int BATCH>
 __device__ __forceinline__ void stage_batch(const RenderArgs& a, const uint32_t* vals, uint32_t start, uint32_t end,
                                             int nt, float4* s_r0, float4* s_r1, float4* s_r2, float4* s_r3,
                                             uint32_t* s_id) {
-  for (int q = threadIdx.x; q < kBatch; q += nt) {
+  for (int q = threadIdx.x; q < BATCH; q += nt) {
     const uint32_t idx = start + q;
     if (idx < end) {
       const uint32_t id = vals[idx];
@@ -93,10 +92,10 @@ struct FwdMinBlocks {
   static constexpr int value = PX == 1 ? 5 : 1;
 };
 
-template <int MODE, int PX, bool REC>
+template <int MODE, int PX, bool REC, int BATCH>
 __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_kernel(RenderArgs a) {
   constexpr int NT = 256 / PX;
-  __shared__ float4 s_r0[kBatch], s_r1[kBatch], s_r2[MODE == MODE_PLAIN ? 1 : kBatch], s_r3[kBatch];
+  __shared__ float4 s_r0[BATCH], s_r1[BATCH], s_r2[MODE == MODE_PLAIN ? 1 : BATCH], s_r3[BATCH];
   const int64_t tile = a.tile_order[blockIdx.x];
   const TileCoord tc = tile_coord(a, tile);
   const PixelMap pm = pixel_map<PX>(tc);
@@ -122,11 +121,11 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
     active += done[p] ? 0 : 1;
   }
   uint32_t blended = 0;
-  for (uint32_t start = range.x; start < range.y; start += kBatch) {
+  for (uint32_t start = range.x; start < range.y; start += BATCH) {
     if (__syncthreads_count(active == 0) == NT) break;
-    stage_batch<MODE>(a, vals, start, range.y, NT, s_r0, s_r1, s_r2, s_r3, nullptr);
+    stage_batch<MODE, BATCH>(a, vals, start, range.y, NT, s_r0, s_r1, s_r2, s_r3, nullptr);
     __syncthreads();
-    const int cnt = (int)min((uint32_t)kBatch, range.y - start);
+    const int cnt = (int)min((uint32_t)BATCH, range.y - start);
     if (active) {
       for (int jc = 0; jc < cnt; jc += 32) {  // chunks of 32 positions (one mask word)
         const int jend = min(cnt, jc + 32);
@@ -242,15 +241,15 @@ __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float 
                : "memory");
 }
 
-template <int MODE, int PX>
+template <int MODE, int PX, int BATCH>
 __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
   constexpr int NT = 256 / PX;
-  __shared__ float4 s_r0[kBatch], s_r1[kBatch], s_r2[MODE == MODE_PLAIN ? 1 : kBatch], s_r3[kBatch];
-  __shared__ uint32_t s_id[kBatch];
+  __shared__ float4 s_r0[BATCH], s_r1[BATCH], s_r2[MODE == MODE_PLAIN ? 1 : BATCH], s_r3[BATCH];
+  __shared__ uint32_t s_id[BATCH];
   // per-batch gradient accumulators, component-major with a padded row so
   // both the warps' adds (16 components of one Gaussian) and the flush (one
   // Gaussian per thread) are free of bank conflicts
-  __shared__ float s_acc[16][kBatch + 1];
+  __shared__ float s_acc[16][BATCH + 1];
   __shared__ uint32_t s_max;
   const int64_t tile = a.tile_order[blockIdx.x];
   const TileCoord tc = tile_coord(a, tile);
@@ -296,10 +295,10 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
   const uint32_t end = min(range.y, range.x + s_max);
 
   for (uint32_t bend = end; bend > range.x;) {
-    const uint32_t bstart = bend - range.x > (uint32_t)kBatch ? bend - kBatch : range.x;
+    const uint32_t bstart = bend - range.x > (uint32_t)BATCH ? bend - BATCH : range.x;
     __syncthreads();  // previous batch fully consumed
-    stage_batch<MODE>(a, vals, bstart, bend, NT, s_r0, s_r1, s_r2, s_r3, s_id);
-    for (int q = threadIdx.x; q < kBatch; q += NT) {
+    stage_batch<MODE, BATCH>(a, vals, bstart, bend, NT, s_r0, s_r1, s_r2, s_r3, s_id);
+    for (int q = threadIdx.x; q < BATCH; q += NT) {
 #pragma unroll
       for (int k = 0; k < 16; ++k) s_acc[k][q] = 0.0f;
     }
@@ -399,27 +398,45 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-template <int PX, bool REC>
+template <int PX, bool REC, int BATCH>
 static void launch_fwd_px(const RenderArgs& a, int mode, unsigned grid, cudaStream_t st) {
-  if (mode == MODE_PLAIN) render_fwd_kernel<MODE_PLAIN, PX, REC><<<grid, 256 / PX, 0, st>>>(a);
-  else if (mode == MODE_TWO) render_fwd_kernel<MODE_TWO, PX, REC><<<grid, 256 / PX, 0, st>>>(a);
-  else render_fwd_kernel<MODE_SPLIT, PX, REC><<<grid, 256 / PX, 0, st>>>(a);
+  if (mode == MODE_PLAIN) render_fwd_kernel<MODE_PLAIN, PX, REC, BATCH><<<grid, 256 / PX, 0, st>>>(a);
+  else if (mode == MODE_TWO) render_fwd_kernel<MODE_TWO, PX, REC, BATCH><<<grid, 256 / PX, 0, st>>>(a);
+  else render_fwd_kernel<MODE_SPLIT, PX, REC, BATCH><<<grid, 256 / PX, 0, st>>>(a);
+}
+
+template <bool REC, int BATCH>
+static void launch_fwd_batch(const RenderArgs& a, int mode, unsigned grid, cudaStream_t st) {
+  switch (a.px_fwd) {
+    case 1: launch_fwd_px<1, REC, BATCH>(a, mode, grid, st); break;
+    case 4: launch_fwd_px<4, REC, BATCH>(a, mode, grid, st); break;
+    default: launch_fwd_px<2, REC, BATCH>(a, mode, grid, st); break;
+  }
 }
 
 template <bool REC>
 static void launch_fwd_rec(const RenderArgs& a, int mode, unsigned grid, cudaStream_t st) {
-  switch (a.px_fwd) {
-    case 1: launch_fwd_px<1, REC>(a, mode, grid, st); break;
-    case 4: launch_fwd_px<4, REC>(a, mode, grid, st); break;
-    default: launch_fwd_px<2, REC>(a, mode, grid, st); break;
+  switch (a.batch_fwd) {
+    case 128: launch_fwd_batch<REC, 128>(a, mode, grid, st); break;
+    case 512: launch_fwd_batch<REC, 512>(a, mode, grid, st); break;
+    default: launch_fwd_batch<REC, 256>(a, mode, grid, st); break;
   }
 }
 
-template <int PX>
+template <int PX, int BATCH>
 static void launch_bwd_px(const RenderArgs& a, int mode, unsigned grid, cudaStream_t st) {
-  if (mode == MODE_PLAIN) render_bwd_kernel<MODE_PLAIN, PX><<<grid, 256 / PX, 0, st>>>(a);
-  else if (mode == MODE_TWO) render_bwd_kernel<MODE_TWO, PX><<<grid, 256 / PX, 0, st>>>(a);
-  else render_bwd_kernel<MODE_SPLIT, PX><<<grid, 256 / PX, 0, st>>>(a);
+  if (mode == MODE_PLAIN) render_bwd_kernel<MODE_PLAIN, PX, BATCH><<<grid, 256 / PX, 0, st>>>(a);
+  else if (mode == MODE_TWO) render_bwd_kernel<MODE_TWO, PX, BATCH><<<grid, 256 / PX, 0, st>>>(a);
+  else render_bwd_kernel<MODE_SPLIT, PX, BATCH><<<grid, 256 / PX, 0, st>>>(a);
+}
+
+template <int BATCH>
+static void launch_bwd_batch(const RenderArgs& a, int mode, unsigned grid, cudaStream_t st) {
+  switch (a.px_bwd) {
+    case 1: launch_bwd_px<1, BATCH>(a, mode, grid, st); break;
+    case 4: launch_bwd_px<4, BATCH>(a, mode, grid, st); break;
+    default: launch_bwd_px<2, BATCH>(a, mode, grid, st); break;
+  }
 }
 
 cudaError_t launch_render_fwd(const RenderArgs& a, int mode, int64_t total_tiles, cudaStream_t st) {
@@ -434,11 +451,8 @@ cudaError_t launch_render_fwd(const RenderArgs& a, int mode, int64_t total_tiles
 cudaError_t launch_render_bwd(const RenderArgs& a, int mode, int64_t total_tiles, cudaStream_t st) {
   if (total_tiles == 0) return cudaSuccess;
   const unsigned grid = (unsigned)total_tiles;
-  switch (a.px_bwd) {
-    case 1: launch_bwd_px<1>(a, mode, grid, st); break;
-    case 4: launch_bwd_px<4>(a, mode, grid, st); break;
-    default: launch_bwd_px<2>(a, mode, grid, st); break;
-  }
+  if (a.batch_bwd == 128) launch_bwd_batch<128>(a, mode, grid, st);
+  else launch_bwd_batch<256>(a, mode, grid, st);
   count_launches(1);
   return cudaGetLastError();
 }

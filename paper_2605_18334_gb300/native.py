@@ -49,9 +49,9 @@ class sr_camera(C.Structure):
 class sr_config(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("alpha_min", C.c_float), ("alpha_max", C.c_float),
                 ("t_stop", C.c_float), ("dilation", C.c_float), ("fov_clamp", C.c_float), ("near_z", C.c_float),
-                ("bg", C.c_float * 3), ("antialias_comp", C.c_int32), ("render_blocks_per_sm", C.c_int32),
+                ("bg", C.c_float * 3), ("antialias_comp", C.c_int32), ("fwd_batch", C.c_int32),
                 ("sort_spin_limit", C.c_int32), ("fwd_pixels_per_thread", C.c_int32),
-                ("bwd_pixels_per_thread", C.c_int32), ("forward_only", C.c_int32), ("reserved_", C.c_int32 * 1)]
+                ("bwd_pixels_per_thread", C.c_int32), ("forward_only", C.c_int32), ("bwd_batch", C.c_int32)]
 
 
 class sr_grads(C.Structure):

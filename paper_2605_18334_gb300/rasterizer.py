@@ -38,6 +38,8 @@ class Config:
     fwd_pixels_per_thread: int = 0   # 0: library default (2)
     bwd_pixels_per_thread: int = 0
     forward_only: bool = False       # plan without backward state (blend masks)
+    fwd_batch: int = 0               # records staged per batch by the composites (0: 256)
+    bwd_batch: int = 0
 
     def to_c(self) -> N.sr_config:
         c = N.sr_config()
@@ -51,6 +53,8 @@ class Config:
         c.fwd_pixels_per_thread = int(self.fwd_pixels_per_thread)
         c.bwd_pixels_per_thread = int(self.bwd_pixels_per_thread)
         c.forward_only = 1 if self.forward_only else 0
+        c.fwd_batch = int(self.fwd_batch)
+        c.bwd_batch = int(self.bwd_batch)
         return c
 
 
@@ -269,11 +273,21 @@ class Rasterizer:
             self.config.bwd_pixels_per_thread = int(bwd)
         self.cfg_c = self.config.to_c()
 
+    def set_batch(self, fwd: int | None = None, bwd: int | None = None):
+        """Records the composites stage in shared memory per batch."""
+        if fwd is not None:
+            self.config.fwd_batch = int(fwd)
+        if bwd is not None:
+            self.config.bwd_batch = int(bwd)
+        self.cfg_c = self.config.to_c()
+
     def autotune(self, g: Gaussians, d_images: torch.Tensor | None = None, candidates=(1, 2, 4), reps: int = 3,
-                 stream=None) -> dict:
-        """Choose how many pixels each thread of the forward and backward
-        composites owns by timing every candidate on this frame (CUDA events
-        on the launching stream, best of ``reps``) and keep the fastest.
+                 stream=None, batches=((128, 256, 512), (128, 256))) -> dict:
+        """Choose the launch shape of the forward and backward composites by
+        timing candidates on this frame (CUDA events on the launching stream,
+        best of ``reps``): first how many pixels each thread owns, then how
+        many Gaussian records a block stages in shared memory per batch
+        (``batches`` = forward and backward candidates); keeps the fastest.
         The results do not depend on the choice."""
         s = stream if stream is not None else torch.cuda.current_stream()
         self.forward(g, stream)
@@ -296,7 +310,14 @@ class Rasterizer:
             fwd[px] = best_of(lambda: self.render_fwd(stream))
         pf = min(fwd, key=fwd.get)
         self.set_pixels_per_thread(fwd=pf)
-        out = {"fwd_ms": fwd, "fwd_pixels_per_thread": pf}
+        fb = {}
+        for bt in batches[0]:
+            self.set_batch(fwd=bt)
+            self.render_fwd(stream)  # warm
+            fb[bt] = best_of(lambda: self.render_fwd(stream))
+        bf = min(fb, key=fb.get)
+        self.set_batch(fwd=bf)
+        out = {"fwd_ms": fwd, "fwd_pixels_per_thread": pf, "fwd_batch_ms": fb, "fwd_batch": bf}
         if d_images is not None:
             self.render_fwd(stream)
             bwd = {}
@@ -306,7 +327,14 @@ class Rasterizer:
                 bwd[px] = best_of(lambda: self.backward(g, d_images, stream))
             pb = min(bwd, key=bwd.get)
             self.set_pixels_per_thread(bwd=pb)
-            out.update(bwd_ms=bwd, bwd_pixels_per_thread=pb)
+            bb = {}
+            for bt in batches[1]:
+                self.set_batch(bwd=bt)
+                self.backward(g, d_images, stream)  # warm
+                bb[bt] = best_of(lambda: self.backward(g, d_images, stream))
+            bbest = min(bb, key=bb.get)
+            self.set_batch(bwd=bbest)
+            out.update(bwd_ms=bwd, bwd_pixels_per_thread=pb, bwd_batch_ms=bb, bwd_batch=bbest)
         return out
 
     # -- read-only views of the workspace (tests and diagnostics) ---------

@@ -110,7 +110,7 @@ def test_plan_layout(lib):
     assert p1.sort_bits == 32 and p1.sort_passes == 0
 
 
-@pytest.mark.parametrize("bad", ["n", "deg", "views", "cap", "tile", "size", "dtype", "alpha"])
+@pytest.mark.parametrize("bad", ["n", "deg", "views", "cap", "tile", "size", "dtype", "alpha", "fbatch", "bbatch"])
 def test_plan_rejects_invalid(lib, bad):
     cfg = Config().to_c()
     cams = [N.sr_camera_from_gl(np.eye(4), 64, 64, 1.0, 1.0)]
@@ -132,6 +132,10 @@ def test_plan_rejects_invalid(lib, bad):
         g.dt_sh = 7
     elif bad == "alpha":
         cfg.alpha_max = 1.5
+    elif bad == "fbatch":
+        cfg.fwd_batch = 64
+    elif bad == "bbatch":
+        cfg.bwd_batch = 512
     arr = (N.sr_camera * 1)(*cams)
     p = N.sr_plan()
     s = lib.sr_plan_init(C.byref(p), C.byref(cfg), C.byref(g), arr, n_views, cap)

@@ -341,13 +341,15 @@ def test_backward_batched_views_sum():
     compare_grads(gr, tot, GRAD_FIELDS)
 
 
-@pytest.mark.parametrize("px", [1, 2, 4])
-def test_pixels_per_thread_launch_shapes(px):
-    """Every launch shape of the composites gives the oracle's image and
-    gradients (the autotuner only changes speed)."""
+@pytest.mark.parametrize("px,fb,bb", [(1, 128, 128), (2, 256, 256), (4, 512, 128), (2, 512, 128), (1, 0, 0)])
+def test_pixels_per_thread_launch_shapes(px, fb, bb):
+    """Every launch shape of the composites (pixels per thread, records per
+    staged batch) gives the oracle's image and gradients (the autotuner only
+    changes speed)."""
     sc = scenes.cluster(seed=31, n=4000, sh_degree=1, two_opacities=True)
     cams = [scenes.identity_camera(100, 70)]
-    cfg = Config(fwd_pixels_per_thread=px, bwd_pixels_per_thread=px, bg=(0.1, 0.0, 0.2))
+    cfg = Config(fwd_pixels_per_thread=px, bwd_pixels_per_thread=px, fwd_batch=fb, bwd_batch=bb,
+                 bg=(0.1, 0.0, 0.2))
     r, g = gpu_forward(sc, cams, cfg)
     check_view(r, sc, cams, 0, cfg)
     up = scenes.upstream_grad(31, 70, 100)
@@ -365,6 +367,7 @@ def test_autotune_picks_a_shape_and_keeps_results():
     ref_g = r.backward(g, up)["means"].clone()
     res = r.autotune(g, up)
     assert res["fwd_pixels_per_thread"] in (1, 2, 4) and res["bwd_pixels_per_thread"] in (1, 2, 4)
+    assert res["fwd_batch"] in (128, 256, 512) and res["bwd_batch"] in (128, 256)
     r.forward(g)
     assert torch.equal(r.images, ref)
     gm = r.backward(g, up)["means"]
