@@ -241,6 +241,182 @@ __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float 
                : "memory");
 }
 
+// Per-thread pixel state of the backward composite and the contribution of
+// one record to the thread's pixels.  Scalar form: any PX.
+template <int MODE, int PX, bool PACKED = (PX % 2 == 0)>
+struct BwdPixels {
+  float T[PX], g0[PX], g1[PX], g2[PX], R0[PX], R1[PX], R2[PX];
+
+  __device__ __forceinline__ void init(int p, const float* bg) {
+    T[p] = 1.0f;
+    g0[p] = g1[p] = g2[p] = 0.0f;
+    R0[p] = bg[0];
+    R1[p] = bg[1];
+    R2[p] = bg[2];
+  }
+  __device__ __forceinline__ void load(int p, float t, float c0, float c1, float c2) {
+    T[p] = t;
+    g0[p] = c0;
+    g1[p] = c1;
+    g2[p] = c2;
+  }
+  // Adds to gr the record's gradient components over the pixels whose mask
+  // word has `bit` set; returns whether there was one.
+  __device__ __forceinline__ bool visit(const uint32_t (&bw)[PX], uint32_t bit, const float4& r0, const float4& r1,
+                                        const float4& r2, const float4& r3, float fx, int py0, float amax,
+                                        float (&gr)[16]) {
+    const float a_ = -2.0f * kLn2 * r0.z, b_ = -kLn2 * r0.w, c_ = -2.0f * kLn2 * r1.x;
+    bool contrib = false;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) gr[k] = 0.0f;
+#pragma unroll
+    for (int p = 0; p < PX; ++p) {
+      if (!((bw[p] >> bit) & 1u)) continue;  // not blended in the forward pass
+      PairEval e;
+      // blended in the forward pass: the same arithmetic passes the alpha gate again
+      eval_pair<MODE, false>(r0, r1, r2, r3.w, fx, (float)(py0 + p) + 0.5f, e);
+      const float alpha = fminf(e.alpha, amax);
+      contrib = true;
+      const float one_m = 1.0f - alpha;
+      T[p] = __fdividef(T[p], one_m);  // T_k (alpha <= alpha_max < 1)
+      const float w = alpha * T[p];
+      gr[G_R] += w * g0[p];
+      gr[G_G] += w * g1[p];
+      gr[G_BL] += w * g2[p];
+      const float dLda = T[p] * (g0[p] * (r3.x - R0[p]) + g1[p] * (r3.y - R1[p]) + g2[p] * (r3.z - R2[p]));
+      R0[p] = alpha * r3.x + one_m * R0[p];
+      R1[p] = alpha * r3.y + one_m * R1[p];
+      R2[p] = alpha * r3.z + one_m * R2[p];
+      if (e.alpha <= amax) {  // the clamp has zero derivative
+        const float S = e.G * e.E;           // skew kernel G' (1 + erf z)
+        const float gS = dLda * e.o * S;
+        const float gz = dLda * e.o * e.G * kTwoOverSqrtPi * e.ez;  // dL/dz
+        float gdx = -gS * (a_ * e.dx + b_ * e.dy) + gz * r1.y;
+        float gdy = -gS * (b_ * e.dx + c_ * e.dy) + gz * r1.z;
+        gr[G_M] += dLda * S;
+        gr[G_A] += -0.5f * gS * e.dx * e.dx;
+        gr[G_B] += -gS * e.dx * e.dy;
+        gr[G_C] += -0.5f * gS * e.dy * e.dy;
+        gr[G_BX] += gz * e.dx * kInvSqrt2;
+        gr[G_BY] += gz * e.dy * kInvSqrt2;
+        if (MODE != MODE_PLAIN) {
+          gr[G_H] += dLda * e.eu * S;
+          const float gzu = dLda * r2.x * S * kTwoOverSqrtPi * e.ezu;
+          gdx += gzu * r2.y;
+          gdy += gzu * r2.z;
+          gr[G_UX] += gzu * e.dx * kInvSqrt2;
+          gr[G_UY] += gzu * e.dy * kInvSqrt2;
+        }
+        gr[G_MX] -= gdx;
+        gr[G_MY] -= gdy;
+      }
+    }
+    return contrib;
+  }
+};
+
+// Packed form (even PX): pixels 2q and 2q + 1 of the thread's column share
+// dx and every operation runs on both at once (FP32x2).  A pixel whose bit is
+// clear takes alpha = 0 (its colour state is unchanged exactly) and a zero
+// dL/dalpha, so it adds nothing.
+template <int MODE, int PX>
+struct BwdPixels<MODE, PX, true> {
+  static constexpr int Q = PX / 2;
+  float2 T[Q], g0[Q], g1[Q], g2[Q], R0[Q], R1[Q], R2[Q];
+
+  __device__ __forceinline__ static void put(float2& v, int p, float x) {
+    if (p & 1) v.y = x;
+    else v.x = x;
+  }
+  __device__ __forceinline__ void init(int p, const float* bg) {
+    put(T[p >> 1], p, 1.0f);
+    put(g0[p >> 1], p, 0.0f);
+    put(g1[p >> 1], p, 0.0f);
+    put(g2[p >> 1], p, 0.0f);
+    put(R0[p >> 1], p, bg[0]);
+    put(R1[p >> 1], p, bg[1]);
+    put(R2[p >> 1], p, bg[2]);
+  }
+  __device__ __forceinline__ void load(int p, float t, float c0, float c1, float c2) {
+    put(T[p >> 1], p, t);
+    put(g0[p >> 1], p, c0);
+    put(g1[p >> 1], p, c1);
+    put(g2[p >> 1], p, c2);
+  }
+  __device__ __forceinline__ bool visit(const uint32_t (&bw)[PX], uint32_t bit, const float4& r0, const float4& r1,
+                                        const float4& r2, const float4& r3, float fx, int py0, float amax,
+                                        float (&gr)[16]) {
+    const float a_ = -2.0f * kLn2 * r0.z, b_ = -kLn2 * r0.w, c_ = -2.0f * kLn2 * r1.x;
+    float2 acc[16];
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const bool m0 = (bw[2 * q] >> bit) & 1u, m1 = (bw[2 * q + 1] >> bit) & 1u;
+      float2 t[16];
+      if (m0 || m1) {
+        any = true;
+        PairEval2 e;
+        eval_pair2<MODE>(r0, r1, r2, fx, (float)(py0 + 2 * q) + 0.5f, e);
+        const float2 alpha = make_float2(m0 ? fminf(e.alpha.x, amax) : 0.0f, m1 ? fminf(e.alpha.y, amax) : 0.0f);
+        const float2 one_m = add2(f2(1.0f), neg2(alpha));
+        // T_k = T_{k+1} / (1 - alpha) as a product with the reciprocal (rcp.approx)
+        const float2 Tn = mul2(T[q], make_float2(rcp_approx(one_m.x), rcp_approx(one_m.y)));
+        T[q] = make_float2(m0 ? Tn.x : T[q].x, m1 ? Tn.y : T[q].y);
+        const float2 w = mul2(alpha, T[q]);
+        t[G_R] = mul2(w, g0[q]);
+        t[G_G] = mul2(w, g1[q]);
+        t[G_BL] = mul2(w, g2[q]);
+        const float2 c0 = f2(r3.x), c1 = f2(r3.y), c2 = f2(r3.z);
+        float2 s = mul2(g0[q], add2(c0, neg2(R0[q])));
+        s = fma2(g1[q], add2(c1, neg2(R1[q])), s);
+        s = fma2(g2[q], add2(c2, neg2(R2[q])), s);
+        const float2 dl = mul2(T[q], s);
+        R0[q] = fma2(alpha, c0, mul2(one_m, R0[q]));
+        R1[q] = fma2(alpha, c1, mul2(one_m, R1[q]));
+        R2[q] = fma2(alpha, c2, mul2(one_m, R2[q]));
+        // dL/dalpha through the unclamped alpha (the clamp has zero derivative)
+        const float2 dLda = make_float2(m0 && e.alpha.x <= amax ? dl.x : 0.0f, m1 && e.alpha.y <= amax ? dl.y : 0.0f);
+        const float2 S = mul2(e.G, e.E);  // skew kernel G' (1 + erf z)
+        const float2 dlo = mul2(dLda, e.o);
+        const float2 gS = mul2(dlo, S);
+        const float2 gz = mul2(mul2(mul2(dlo, e.G), f2(kTwoOverSqrtPi)), e.ez);  // dL/dz
+        float2 gdx = fma2(neg2(gS), fma2(f2(b_), e.dy, f2(a_ * e.dx)), mul2(gz, f2(r1.y)));
+        float2 gdy = fma2(neg2(gS), fma2(f2(c_), e.dy, f2(b_ * e.dx)), mul2(gz, f2(r1.z)));
+        const float2 dx = f2(e.dx);
+        t[G_M] = mul2(dLda, S);
+        t[G_A] = mul2(gS, f2(-0.5f * e.dx * e.dx));
+        t[G_B] = mul2(mul2(neg2(gS), dx), e.dy);
+        t[G_C] = mul2(mul2(gS, f2(-0.5f)), mul2(e.dy, e.dy));
+        t[G_BX] = mul2(gz, f2(e.dx * kInvSqrt2));
+        t[G_BY] = mul2(mul2(gz, e.dy), f2(kInvSqrt2));
+        if (MODE != MODE_PLAIN) {
+          t[G_H] = mul2(mul2(dLda, e.eu), S);
+          const float2 gzu = mul2(mul2(mul2(mul2(dLda, f2(r2.x)), S), f2(kTwoOverSqrtPi)), e.ezu);
+          gdx = fma2(gzu, f2(r2.y), gdx);
+          gdy = fma2(gzu, f2(r2.z), gdy);
+          t[G_UX] = mul2(gzu, f2(e.dx * kInvSqrt2));
+          t[G_UY] = mul2(mul2(gzu, e.dy), f2(kInvSqrt2));
+        } else {
+          t[G_H] = t[G_UX] = t[G_UY] = f2(0.0f);
+        }
+        t[G_MX] = neg2(gdx);
+        t[G_MY] = neg2(gdy);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) t[k] = f2(0.0f);
+      }
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        if (k == G_ABS || k == G_PAD) continue;
+        acc[k] = q == 0 ? t[k] : add2(acc[k], t[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) gr[k] = (k == G_ABS || k == G_PAD) ? 0.0f : acc[k].x + acc[k].y;
+    return any;
+  }
+};
+
 template <int MODE, int PX, int BATCH>
 __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
   constexpr int NT = 256 / PX;
@@ -263,7 +439,7 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
   const int64_t plane = (int64_t)tc.vi.width * tc.vi.height;
   const float* gimg = a.d_images + tc.vi.image_offset;
 
-  float T[PX], g0[PX], g1[PX], g2[PX], R0[PX], R1[PX], R2[PX];
+  BwdPixels<MODE, PX> pix;
   uint32_t my_end[PX], bw[PX];
   const int pi0 = pm.pi0;
   const uint32_t* mbase = mask_tile_base(a.mask, range, tile);
@@ -271,19 +447,12 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
 #pragma unroll
   for (int p = 0; p < PX; ++p) {
     const int py = py0 + p;
-    T[p] = 1.0f;
-    g0[p] = g1[p] = g2[p] = 0.0f;
+    pix.init(p, a.cfg.bg);
     my_end[p] = range.x;
-    R0[p] = a.cfg.bg[0];
-    R1[p] = a.cfg.bg[1];
-    R2[p] = a.cfg.bg[2];
     if (px < tc.vi.width && py < tc.vi.height) {
-      const int64_t pix = (int64_t)py * tc.vi.width + px;
-      g0[p] = gimg[pix];
-      g1[p] = gimg[plane + pix];
-      g2[p] = gimg[2 * plane + pix];
-      T[p] = a.t_final[tc.vi.pixel_offset + pix];
-      const uint32_t nc = a.n_contrib[tc.vi.pixel_offset + pix];
+      const int64_t pix_i = (int64_t)py * tc.vi.width + px;
+      pix.load(p, a.t_final[tc.vi.pixel_offset + pix_i], gimg[pix_i], gimg[plane + pix_i], gimg[2 * plane + pix_i]);
+      const uint32_t nc = a.n_contrib[tc.vi.pixel_offset + pix_i];
       my_end[p] = min(range.y, range.x + nc);
       my_max = max(my_max, nc);
     }
@@ -323,60 +492,14 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
         const uint32_t bit = 31u - __clz(todo);
         todo &= ~(1u << bit);
         const int j = (int)(chunk_first + bit - bstart);
-      float gr[16];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) gr[k] = 0.0f;
-      bool contrib = false;
-      const float4 r0 = s_r0[j], r1 = s_r1[j], r3 = s_r3[j];
-      const float4 r2 = MODE == MODE_PLAIN ? r0 : s_r2[j];
-      // natural-unit conic from the log2-prescaled record
-      const float a_ = -2.0f * kLn2 * r0.z, b_ = -kLn2 * r0.w, c_ = -2.0f * kLn2 * r1.x;
-#pragma unroll
-      for (int p = 0; p < PX; ++p) {
-        if (!((bw[p] >> bit) & 1u)) continue;  // not blended in the forward pass
-        PairEval e;
-        // blended in the forward pass: the same arithmetic passes the alpha gate again
-        eval_pair<MODE, false>(r0, r1, r2, r3.w, fx, (float)(py0 + p) + 0.5f, e);
-        const float alpha = fminf(e.alpha, amax);
-        contrib = true;
-        const float one_m = 1.0f - alpha;
-        T[p] = __fdividef(T[p], one_m);  // T_k (alpha <= alpha_max < 1)
-        const float w = alpha * T[p];
-        gr[G_R] += w * g0[p];
-        gr[G_G] += w * g1[p];
-        gr[G_BL] += w * g2[p];
-        const float dLda = T[p] * (g0[p] * (r3.x - R0[p]) + g1[p] * (r3.y - R1[p]) + g2[p] * (r3.z - R2[p]));
-        R0[p] = alpha * r3.x + one_m * R0[p];
-        R1[p] = alpha * r3.y + one_m * R1[p];
-        R2[p] = alpha * r3.z + one_m * R2[p];
-        if (e.alpha <= amax) {  // the clamp has zero derivative
-          const float S = e.G * e.E;           // skew kernel G' (1 + erf z)
-          const float gS = dLda * e.o * S;
-          const float gz = dLda * e.o * e.G * kTwoOverSqrtPi * e.ez;  // dL/dz
-          float gdx = -gS * (a_ * e.dx + b_ * e.dy) + gz * r1.y;
-          float gdy = -gS * (b_ * e.dx + c_ * e.dy) + gz * r1.z;
-          gr[G_M] += dLda * S;
-          gr[G_A] += -0.5f * gS * e.dx * e.dx;
-          gr[G_B] += -gS * e.dx * e.dy;
-          gr[G_C] += -0.5f * gS * e.dy * e.dy;
-          gr[G_BX] += gz * e.dx * kInvSqrt2;
-          gr[G_BY] += gz * e.dy * kInvSqrt2;
-          if (MODE != MODE_PLAIN) {
-            gr[G_H] += dLda * e.eu * S;
-            const float gzu = dLda * r2.x * S * kTwoOverSqrtPi * e.ezu;
-            gdx += gzu * r2.y;
-            gdy += gzu * r2.z;
-            gr[G_UX] += gzu * e.dx * kInvSqrt2;
-            gr[G_UY] += gzu * e.dy * kInvSqrt2;
-          }
-          gr[G_MX] -= gdx;
-          gr[G_MY] -= gdy;
+        const float4 r0 = s_r0[j], r1 = s_r1[j], r3 = s_r3[j];
+        const float4 r2 = MODE == MODE_PLAIN ? r0 : s_r2[j];
+        float gr[16];
+        const bool contrib = pix.visit(bw, bit, r0, r1, r2, r3, fx, py0, amax, gr);
+        if (__any_sync(0xffffffffu, contrib)) {
+          const float sum = warp_transpose_sum16(gr, lane);
+          if ((lane & 1) == 0 && sum != 0.0f) atomicAdd(&s_acc[lane >> 1][j], sum);
         }
-      }
-      if (__any_sync(0xffffffffu, contrib)) {
-        const float sum = warp_transpose_sum16(gr, lane);
-        if ((lane & 1) == 0 && sum != 0.0f) atomicAdd(&s_acc[lane >> 1][j], sum);
-      }
       }
       jhi = jlo - 1;
     }
