@@ -231,14 +231,20 @@ struct PairEval2 {
   float2 dy, G, E, ez, o, eu, ezu, alpha;
 };
 
-template <int MODE>
-__device__ __forceinline__ void eval_pair2(const float4& r0, const float4& r1, const float4& r2, float px, float py,
-                                           PairEval2& e) {
+// The exponent P2 of both pixels (what the alpha gate tests).
+__device__ __forceinline__ float2 pair2_exponent(const float4& r0, const float4& r1, float px, float py,
+                                                 PairEval2& e) {
   e.dx = __fadd_rn(px, -r0.x);
   e.dy = add2(make_float2(py, py + 1.0f), f2(-r0.y));
   const float2 dx = f2(e.dx);
   const float2 lin = fma2(f2(r0.z), dx, mul2(f2(r0.w), e.dy));
-  const float2 p2 = fma2(lin, dx, mul2(mul2(f2(r1.x), e.dy), e.dy));
+  return fma2(lin, dx, mul2(mul2(f2(r1.x), e.dy), e.dy));
+}
+
+// The rest of the evaluation from the exponent: kernel, erf terms, opacity, alpha.
+template <int MODE>
+__device__ __forceinline__ void pair2_alpha(const float4& r1, const float4& r2, float2 p2, PairEval2& e) {
+  const float2 dx = f2(e.dx);
   e.G = make_float2(ex2_approx(p2.x), ex2_approx(p2.y));
   if (r1.y == 0.0f && r1.z == 0.0f) {
     e.E = f2(1.0f);
@@ -266,6 +272,12 @@ __device__ __forceinline__ void eval_pair2(const float4& r0, const float4& r1, c
     e.o = fma2(f2(r2.x), e.eu, f2(r1.w));
   }
   e.alpha = mul2(mul2(e.o, e.G), e.E);
+}
+
+template <int MODE>
+__device__ __forceinline__ void eval_pair2(const float4& r0, const float4& r1, const float4& r2, float px, float py,
+                                           PairEval2& e) {
+  pair2_alpha<MODE>(r1, r2, pair2_exponent(r0, r1, px, py, e), e);
 }
 
 // Footprint of a record: the region

@@ -2,13 +2,16 @@
 // the reverse replay that differentiates it (Alg. 2).
 //
 // One block per 16x16 tile; each thread owns PX vertically adjacent pixels
-// of one column, so a warp covers a 16 x 2*PX block.  The tile's depth-sorted
-// records are staged into shared memory in batches of 256 (gathered 64-byte
-// records), then every pixel walks the batch:
+// of one column, so a warp covers an 8-wide block of 4*PX rows.  The tile's
+// depth-sorted records are staged into shared memory in batches (128, 256 or
+// 512 gathered 64-byte records), then every pixel walks the batch:
 //   alpha = min(alpha_max, o G' (1 + erf z)),  skip if alpha < alpha_min,
 //   stop before the Gaussian whose T' = T (1 - alpha) would fall below t_stop,
 //   C += c alpha T, T = T'.
 // A block leaves as soon as every pixel has stopped (__syncthreads_count).
+// With an even PX a thread takes its rows two at a time: they share dx, and
+// the packed FP32x2 instructions of sm_100+ evaluate and blend both in one
+// instruction stream, with results equal to the scalar path bit for bit.
 //
 // Backward per pixel from its last blended Gaussian down: T_k = T_{k+1} /
 // (1 - alpha_k), R_{k+1} = colour behind k normalised by T_{k+1} (the
@@ -106,10 +109,19 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
   const float amin = a.cfg.alpha_min, amax = a.cfg.alpha_max, tstop = a.cfg.t_stop;
   uint32_t* mbase = REC ? mask_tile_base(a.mask, range, tile) : nullptr;
 
+  // colour state: scalar, or (even PX) packed per pair of rows for FP32x2 arithmetic
+  constexpr bool PACKED = PX % 2 == 0;
+  constexpr int Q = (PX + 1) / 2;
   float T[PX], C0[PX], C1[PX], C2[PX];
+  float2 T2[Q], D0[Q], D1[Q], D2[Q];
   uint32_t last[PX], stop[PX], mw[PX];
   bool done[PX];
   int active = 0;  // pixels of this thread still compositing
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    T2[q] = f2(1.0f);
+    D0[q] = D1[q] = D2[q] = f2(0.0f);
+  }
 #pragma unroll
   for (int p = 0; p < PX; ++p) {
     T[p] = 1.0f;
@@ -133,29 +145,82 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
         for (int j = jc; j < jend; ++j) {
           const float4 r0 = s_r0[j], r1 = s_r1[j], r3 = s_r3[j];
           const float4 r2 = MODE == MODE_PLAIN ? r0 : s_r2[j];
+          if constexpr (PACKED) {
+            // rows 2q and 2q + 1 together; a row that fails the gate, the
+            // alpha_min test or has stopped takes alpha = 0 in the packed
+            // blend, which leaves its T and colour unchanged exactly
 #pragma unroll
-          for (int p = 0; p < PX; ++p) {
-            if (PX > 1 && done[p]) continue;
-            PairEval e;
-            if (!eval_pair<MODE>(r0, r1, r2, r3.w, fx, (float)(py0 + p) + 0.5f, e)) continue;
-            const float alpha = fminf(e.alpha, amax);
-            if (alpha < amin) continue;
-            const float Tn = __fmaf_rn(-T[p], alpha, T[p]);
-            if (Tn < tstop) {
-              done[p] = true;
-              stop[p] = start + j + 1;
-              if (REC) mbase[chunk * 256 + pi0 + p * kTile] = mw[p];
-              if (--active == 0) goto batch_done;  // the only exit test, off the hot path
-              continue;
+            for (int q = 0; q < Q; ++q) {
+              if (done[2 * q] && done[2 * q + 1]) continue;
+              PairEval2 e;
+              const float2 p2 = pair2_exponent(r0, r1, fx, (float)(py0 + 2 * q) + 0.5f, e);
+              const bool g0 = !done[2 * q] && p2.x >= r3.w, g1 = !done[2 * q + 1] && p2.y >= r3.w;
+              if (!(g0 || g1)) continue;
+              pair2_alpha<MODE>(r1, r2, p2, e);
+              const float al0 = fminf(e.alpha.x, amax), al1 = fminf(e.alpha.y, amax);
+              const bool b0 = g0 && al0 >= amin, b1 = g1 && al1 >= amin;
+              if (!(b0 || b1)) continue;
+              float2 al = make_float2(b0 ? al0 : 0.0f, b1 ? al1 : 0.0f);
+              float2 Tn = fma2(neg2(T2[q]), al, T2[q]);
+              const bool s0 = b0 && Tn.x < tstop, s1 = b1 && Tn.y < tstop;
+              if (s0 || s1) {
+                if (s0) {
+                  done[2 * q] = true;
+                  stop[2 * q] = start + j + 1;
+                  if (REC) mbase[chunk * 256 + pi0 + 2 * q * kTile] = mw[2 * q];
+                  al.x = 0.0f;
+                  Tn.x = T2[q].x;
+                  --active;
+                }
+                if (s1) {
+                  done[2 * q + 1] = true;
+                  stop[2 * q + 1] = start + j + 1;
+                  if (REC) mbase[chunk * 256 + pi0 + (2 * q + 1) * kTile] = mw[2 * q + 1];
+                  al.y = 0.0f;
+                  Tn.y = T2[q].y;
+                  --active;
+                }
+                if (active == 0) goto batch_done;
+              }
+              const bool c0 = b0 && !s0, c1 = b1 && !s1;
+              const float2 w = mul2(al, T2[q]);
+              D0[q] = fma2(f2(r3.x), w, D0[q]);
+              D1[q] = fma2(f2(r3.y), w, D1[q]);
+              D2[q] = fma2(f2(r3.z), w, D2[q]);
+              T2[q] = Tn;
+              blended += (uint32_t)c0 + (uint32_t)c1;
+              if (REC) {
+                mw[2 * q] |= (uint32_t)c0 << (j & 31);
+                mw[2 * q + 1] |= (uint32_t)c1 << (j & 31);
+              }
+              if (c0) last[2 * q] = start + j + 1 - range.x;
+              if (c1) last[2 * q + 1] = start + j + 1 - range.x;
             }
-            ++blended;
-            if (REC) mw[p] |= 1u << (j & 31);
-            const float w = __fmul_rn(alpha, T[p]);
-            C0[p] = __fmaf_rn(r3.x, w, C0[p]);
-            C1[p] = __fmaf_rn(r3.y, w, C1[p]);
-            C2[p] = __fmaf_rn(r3.z, w, C2[p]);
-            T[p] = Tn;
-            last[p] = start + j + 1 - range.x;
+          } else {
+#pragma unroll
+            for (int p = 0; p < PX; ++p) {
+              if (PX > 1 && done[p]) continue;
+              PairEval e;
+              if (!eval_pair<MODE>(r0, r1, r2, r3.w, fx, (float)(py0 + p) + 0.5f, e)) continue;
+              const float alpha = fminf(e.alpha, amax);
+              if (alpha < amin) continue;
+              const float Tn = __fmaf_rn(-T[p], alpha, T[p]);
+              if (Tn < tstop) {
+                done[p] = true;
+                stop[p] = start + j + 1;
+                if (REC) mbase[chunk * 256 + pi0 + p * kTile] = mw[p];
+                if (--active == 0) goto batch_done;  // the only exit test, off the hot path
+                continue;
+              }
+              ++blended;
+              if (REC) mw[p] |= 1u << (j & 31);
+              const float w = __fmul_rn(alpha, T[p]);
+              C0[p] = __fmaf_rn(r3.x, w, C0[p]);
+              C1[p] = __fmaf_rn(r3.y, w, C1[p]);
+              C2[p] = __fmaf_rn(r3.z, w, C2[p]);
+              T[p] = Tn;
+              last[p] = start + j + 1 - range.x;
+            }
           }
         }
         if (REC) {
@@ -187,6 +252,16 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
   }
   const int64_t plane = (int64_t)tc.vi.width * tc.vi.height;
   float* img = a.images + tc.vi.image_offset;
+  if constexpr (PACKED) {
+#pragma unroll
+    for (int p = 0; p < PX; ++p) {
+      const bool hi = p & 1;
+      T[p] = hi ? T2[p >> 1].y : T2[p >> 1].x;
+      C0[p] = hi ? D0[p >> 1].y : D0[p >> 1].x;
+      C1[p] = hi ? D1[p >> 1].y : D1[p >> 1].x;
+      C2[p] = hi ? D2[p >> 1].y : D2[p >> 1].x;
+    }
+  }
 #pragma unroll
   for (int p = 0; p < PX; ++p) {
     const int py = py0 + p;
