@@ -202,12 +202,15 @@ sr_status sr_preprocess(const sr_plan* plan, const sr_gaussians* g, const sr_cam
 /* Tile binning and depth sort: exclusive scan of the tile counts, one
  * (global tile << 32 | FP32 depth bits) key per touched tile in Gaussian
  * index order, a stable LSD radix sort (ties keep index order), and per-tile
- * [start, end) ranges.  If keys_needed is non-NULL the call synchronises the
- * stream once, stores the number of keys the frame needs, returns
- * SR_ERR_CAPACITY (nothing to render) if it exceeds plan->key_capacity and
- * skips radix passes whose digit is the same for every key.  If NULL, the
- * call never blocks (for CUDA-graph capture): every pass runs and an
- * overflow is reported through the status word (sr_read_status). */
+ * [start, end) ranges.  If keys_needed is non-NULL the call blocks until
+ * the key emission is done, stores the number of keys the frame needs and
+ * returns SR_ERR_CAPACITY (nothing to render) if it exceeds
+ * plan->key_capacity; the tile sort is queued behind the count's readback
+ * (through a pinned host buffer) so the device does not idle meanwhile, and
+ * where no pinned memory can be had the sort waits for the count and skips
+ * radix passes whose digit is the same for every key.  If NULL, the call
+ * never blocks (for CUDA-graph capture): every pass runs and an overflow is
+ * reported through the status word (sr_read_status). */
 sr_status sr_bin_sort(const sr_plan* plan, const sr_config* cfg, void* ws, int64_t* keys_needed, void* stream);
 
 /* Forward composite of all views.  images: plan->image_offset[n_views]

@@ -252,6 +252,20 @@ static BinArgs bin_args(const sr_plan* p, const sr_config* cfg, void* ws) {
   return b;
 }
 
+// One pinned status buffer per host thread (portable across devices), for
+// the overlapped key-count readback; nullptr if pinned memory is unavailable.
+static Status* pinned_status() {
+  thread_local Status* buf = nullptr;
+  thread_local bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, sizeof(Status), cudaHostAllocPortable) == cudaSuccess) buf = static_cast<Status*>(p);
+    else cudaGetLastError();
+  }
+  return buf;
+}
+
 sr_status sr_bin_sort(const sr_plan* p, const sr_config* cfg, void* ws, int64_t* keys_needed, void* stream) {
   sr_status s = check_plan(p, ws);
   if (s != SR_OK) return s;
@@ -262,19 +276,34 @@ sr_status sr_bin_sort(const sr_plan* p, const sr_config* cfg, void* ws, int64_t*
   if (e != cudaSuccess) return SR_ERR_CUDA;
   int run[kMaxPasses];
   for (int k = 0; k < kMaxPasses; ++k) run[k] = 1;
-  long long known = -1;
-  if (keys_needed) {
-    Status h;
-    e = cudaMemcpyAsync(&h, b.ws.status, sizeof(Status), cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return SR_ERR_CUDA;
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return SR_ERR_CUDA;
-    *keys_needed = (int64_t)h.keys_needed;
-    if (h.keys_needed > (unsigned long long)p->key_capacity) return SR_ERR_CAPACITY;
-    known = (long long)h.keys_needed;
-    for (int k = 0; k < p->sort_passes; ++k) run[k] = h.pass_trivial[kMaxPasses + k] ? 0 : 1;
+  if (!keys_needed) return from_cuda(launch_bin_phase2(b, run, -1, st));
+  // Synchronous form.  With a pinned status buffer the key count is copied
+  // back while the tile passes (grids sized for the capacity; blocks past the
+  // device-side key count leave at once) are already queued behind it, so the
+  // GPU does not idle during the host round trip; the call still returns only
+  // once the count is known.  Without one, the passes wait for the count and
+  // are sized by it (trivial passes skipped).
+  Status* h = pinned_status();
+  cudaEvent_t ev = nullptr;
+  if (h && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) ev = nullptr;
+  if (h && ev) {
+    const bool ok = cudaMemcpyAsync(h, b.ws.status, sizeof(Status), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                    cudaEventRecord(ev, st) == cudaSuccess && launch_bin_phase2(b, run, -1, st) == cudaSuccess &&
+                    cudaEventSynchronize(ev) == cudaSuccess;
+    cudaEventDestroy(ev);
+    if (!ok) return SR_ERR_CUDA;
+    *keys_needed = (int64_t)h->keys_needed;
+    return h->keys_needed > (unsigned long long)p->key_capacity ? SR_ERR_CAPACITY : SR_OK;
   }
-  return from_cuda(launch_bin_phase2(b, run, known, st));
+  Status hs;
+  e = cudaMemcpyAsync(&hs, b.ws.status, sizeof(Status), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return SR_ERR_CUDA;
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return SR_ERR_CUDA;
+  *keys_needed = (int64_t)hs.keys_needed;
+  if (hs.keys_needed > (unsigned long long)p->key_capacity) return SR_ERR_CAPACITY;
+  for (int k = 0; k < p->sort_passes; ++k) run[k] = hs.pass_trivial[kMaxPasses + k] ? 0 : 1;
+  return from_cuda(launch_bin_phase2(b, run, (long long)hs.keys_needed, st));
 }
 
 static RenderArgs render_args(const sr_plan* p, const sr_config* cfg, void* ws) {

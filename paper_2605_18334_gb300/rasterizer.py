@@ -123,6 +123,15 @@ def _stream_ptr(stream=None) -> int:
     return int(s.cuda_stream)
 
 
+def _prefer_default(times: dict, default, margin: float = 0.02):
+    """The fastest candidate, unless the default is within ``margin`` of it
+    (timing noise should not flip a launch parameter between frames)."""
+    best = min(times, key=times.get)
+    if default in times and times[default] <= times[best] * (1.0 + margin):
+        return default
+    return best
+
+
 class Rasterizer:
     """One plan (Gaussian count, SH degree, cameras) and its device buffers."""
 
@@ -315,7 +324,7 @@ class Rasterizer:
             self.set_batch(fwd=bt)
             self.render_fwd(stream)  # warm
             fb[bt] = best_of(lambda: self.render_fwd(stream))
-        bf = min(fb, key=fb.get)
+        bf = _prefer_default(fb, 256)
         self.set_batch(fwd=bf)
         out = {"fwd_ms": fwd, "fwd_pixels_per_thread": pf, "fwd_batch_ms": fb, "fwd_batch": bf}
         if d_images is not None:
@@ -332,7 +341,7 @@ class Rasterizer:
                 self.set_batch(bwd=bt)
                 self.backward(g, d_images, stream)  # warm
                 bb[bt] = best_of(lambda: self.backward(g, d_images, stream))
-            bbest = min(bb, key=bb.get)
+            bbest = _prefer_default(bb, 256)
             self.set_batch(bwd=bbest)
             out.update(bwd_ms=bwd, bwd_pixels_per_thread=pb, bwd_batch_ms=bb, bwd_batch=bbest)
         return out
