@@ -324,6 +324,7 @@ def run_ours(args):
         out["variants"] = variants(args, sc, cam, up, dev, flush)
         out["variants"]["trajectory_64"] = trajectory(args, sc, dev, flush)
         out["variants"]["train_step"] = train_step(args, sc, cam, dev, flush)
+        out["variants"]["densify"] = densify_step(args, sc, dev, flush)
     out["e2e"] = e2e(args, sc, cam, up, dev, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, cam, up, args.cpu_budget)
@@ -438,6 +439,63 @@ def train_step(args, sc, cam, dev, flush):
                          "adam": round(ms[3], 4)},
            "adam_GBps": round(adam_bytes / (ms[3] / 1e3) / 1e9, 1), "loss": round(float(tr.loss.loss.item()), 6)}
     del tr, g
+    torch.cuda.empty_cache()
+    return out
+
+
+def densify_step(args, sc, dev, flush):
+    """One densification of the 1M scene (remove / keep / clone / split from
+    seeded synthetic statistics, thresholds that densify about a fifth of
+    the Gaussians), device time of sr_densify with the L2 flushed before
+    each call; algorithmic bytes: every input Gaussian and its statistics
+    read once, every output Gaussian and its map entry written once."""
+    import numpy as np
+    import torch
+
+    from paper_2605_18334_gb300 import native as N
+    from paper_2605_18334_gb300.densify import densify
+    from paper_2605_18334_gb300.rasterizer import Gaussians, _stream_ptr
+
+    g = Gaussians.from_scene(sc, device=dev)
+    n = g.n
+    rng = np.random.default_rng(11)
+    uv = torch.as_tensor(rng.exponential(0.1, n).astype(np.float32), device=dev)
+    seen = torch.as_tensor(rng.integers(1, 8, n).astype(np.int32), device=dev)
+    zm = torch.as_tensor(rng.exponential(0.05, n).astype(np.float32), device=dev)
+    cfg = dict(grad_uv=0.04, grad_z=0.2, log_scale_split=-3.5, logit_prune=-2.5)
+    res = densify(g, uv, seen, zm, **cfg)  # sizes, and the output arrays the timed calls rewrite
+    cap = 2 * n
+    outs = [torch.empty(cap, 3, device=dev), torch.empty(cap, 3, device=dev), torch.empty(cap, 4, device=dev),
+            torch.empty(cap, device=dev), torch.empty(cap, 3, device=dev), torch.empty(cap, g.sh[0].numel(), device=dev)]
+    arrays = N.sr_scene_arrays(*[t.data_ptr() for t in outs[:5]], None, outs[5].data_ptr())
+    src_map = torch.empty(cap, dtype=torch.int32, device=dev)
+    counts = torch.zeros(4, dtype=torch.int64, device=dev)
+    scratch = torch.empty(N.sr_densify_scratch_size(n), dtype=torch.uint8, device=dev)
+    c_cfg = N.sr_densify_config(cfg["grad_uv"], cfg["grad_z"], cfg["log_scale_split"], cfg["logit_prune"])
+    gc = g.to_c()
+    stream = torch.cuda.current_stream()
+
+    def call():
+        N.sr_densify(gc, uv.data_ptr(), seen.data_ptr(), zm.data_ptr(), c_cfg, arrays, src_map.data_ptr(),
+                     counts.data_ptr(), scratch.data_ptr(), _stream_ptr(stream))
+
+    for _ in range(3):
+        call()
+    ts = []
+    for _ in range(10):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        call()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = float(np.median(ts))
+    per_g = 4 * (3 + 3 + 4 + 1 + 3 + g.sh[0].numel())
+    nbytes = n * (per_g + 12) + res.counts["total"] * (per_g + 4)
+    out = {"ms": round(ms, 4), "counts": res.counts, "GBps": round(nbytes / (ms / 1e3) / 1e9, 1),
+           "input_gaussians_per_s": round(n / (ms / 1e3), 1)}
+    del g, res, outs
     torch.cuda.empty_cache()
     return out
 

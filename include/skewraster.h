@@ -355,6 +355,67 @@ sr_status sr_adam_step(const sr_adam_group* groups, int32_t n_groups, int64_t st
 sr_status sr_densify_stats(const float* means2d_abs, const float* depth_grad, int64_t n, float* uv_sum,
                            int32_t* seen, float* z_max, void* stream);
 
+/* ---- Densification (Sec. "Depth-Aware Densification Strategy"; Fig. "split") ----
+ * From the statistics sr_densify_stats collects, each of the n Gaussians is
+ * (decisions in FP32):
+ *   removed  if its largest opacity logit < logit_prune;
+ *   else split or cloned if uv_sum / seen >= grad_uv (g^(uv); 0 when seen is
+ *            0) or z_max >= grad_z (g^(z), Eq. depth_grad): split if its
+ *            largest log-scale > log_scale_split, cloned otherwise;
+ *   else kept.
+ * A split cuts the skew Gaussian at its centre across its largest axis k
+ * (first of equal maxima); each child stands for one half and takes that
+ * half's mean and variance along the axis (centre moved by s_k m along the
+ * axis, log-scale log s_k + log(v) / 2 on it), skew component 0 on the axis
+ * and eta_j / sqrt(1 + eta_k^2) on the others (the parent's marginal skew);
+ * rotation, opacities, SH and split direction are copied.
+ * Output order: the kept Gaussians (cloned ones included) in index order,
+ * then the clones' copies in index order, then for each split Gaussian in
+ * index order its child on the + side of the axis and its child on the -
+ * side.  There are at most 2n outputs. */
+typedef struct sr_densify_config {
+  float grad_uv;              /* threshold on uv_sum / seen */
+  float grad_z;               /* threshold on z_max */
+  float log_scale_split;      /* largest log-scale above which a densified Gaussian is split */
+  float logit_prune;          /* Gaussians whose largest opacity logit is below are removed */
+} sr_densify_config;
+
+/* FP32 attribute arrays of a scene (the outputs of sr_densify), caller-owned,
+ * same layouts as sr_gaussians; split_dir NULL iff the input has none. */
+typedef struct sr_scene_arrays {
+  float* means;
+  float* log_scales;
+  float* quats;               /* 16-byte aligned */
+  float* opacity_logits;
+  float* skew;
+  float* split_dir;
+  float* sh;
+} sr_scene_arrays;
+
+/* Bytes of device scratch sr_densify needs for n Gaussians. */
+size_t sr_densify_scratch_size(int64_t n);
+
+/* g: FP32 attributes (dt_sh = dt_scale = dt_skew = SR_F32), 0 <= n < 2^30;
+ * uv_sum, seen, z_max: [n] device statistics; out: device arrays with room
+ * for 2n Gaussians; src_map (optional, [2n] device): per output, its source
+ * index | kind << 30 with kind 0 kept, 1 clone copy, 2 child on the + side,
+ * 3 child on the - side; counts: device int64[4] = kept, cloned, split,
+ * total outputs (read them back to learn the new size); scratch:
+ * sr_densify_scratch_size(n) device bytes.  Asynchronous on stream.
+ * Errors: SR_ERR_INVALID for NULL pointers, other dtypes, n out of range or
+ * misaligned quaternion arrays; SR_ERR_CUDA if a launch fails. */
+sr_status sr_densify(const sr_gaussians* g, const float* uv_sum, const int32_t* seen, const float* z_max,
+                     const sr_densify_config* cfg, const sr_scene_arrays* out, uint32_t* src_map, int64_t* counts,
+                     void* scratch, void* stream);
+
+/* Per-Gaussian state after sr_densify (e.g. Adam moments), width floats per
+ * Gaussian: for each output j < min(counts[3], cap), out[j] = in[source(j)]
+ * if j is a kept Gaussian, zeros for clone copies and children.  in: [n,
+ * width], out: [cap, width], src_map and counts from sr_densify (device).
+ * Errors: SR_ERR_INVALID for NULL pointers or negative sizes. */
+sr_status sr_densify_remap(const float* in, int32_t width, const uint32_t* src_map, const int64_t* counts,
+                           int64_t cap, float* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -480,6 +480,62 @@ sr_status sr_densify_stats(const float* means2d_abs, const float* depth_grad, in
   return e == cudaSuccess ? SR_OK : SR_ERR_CUDA;
 }
 
+size_t sr_densify_scratch_size(int64_t n) { return densify_scratch_bytes(n < 0 ? 0 : n); }
+
+sr_status sr_densify(const sr_gaussians* g, const float* uv_sum, const int32_t* seen, const float* z_max,
+                     const sr_densify_config* cfg, const sr_scene_arrays* out, uint32_t* src_map, int64_t* counts,
+                     void* scratch, void* stream) {
+  if (!g || !cfg || !out || !counts || !scratch) return SR_ERR_INVALID;
+  if (g->n < 0 || g->n >= ((int64_t)1 << 30) || g->sh_degree < 0 || g->sh_degree > 3) return SR_ERR_INVALID;
+  if (g->dt_sh != SR_F32 || g->dt_scale != SR_F32 || g->dt_skew != SR_F32) return SR_ERR_INVALID;
+  if (g->n > 0) {
+    if (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->skew || !g->sh) return SR_ERR_INVALID;
+    if (!uv_sum || !seen || !z_max) return SR_ERR_INVALID;
+    if (!out->means || !out->log_scales || !out->quats || !out->opacity_logits || !out->skew || !out->sh)
+      return SR_ERR_INVALID;
+    if ((g->split_dir != nullptr) != (out->split_dir != nullptr)) return SR_ERR_INVALID;
+    if (!aligned16(g->quats) || !aligned16(out->quats)) return SR_ERR_INVALID;
+  }
+  DensifyArgs a;
+  a.means = static_cast<const float*>(g->means);
+  a.log_scales = static_cast<const float*>(g->log_scales);
+  a.quats = static_cast<const float*>(g->quats);
+  a.opacity = static_cast<const float*>(g->opacity_logits);
+  a.skew = static_cast<const float*>(g->skew);
+  a.split_dir = static_cast<const float*>(g->split_dir);
+  a.sh = static_cast<const float*>(g->sh);
+  a.n = g->n;
+  a.two = g->two_opacities ? 1 : 0;
+  a.k3 = 3 * (g->sh_degree + 1) * (g->sh_degree + 1);
+  a.sh_vec4 = (a.k3 % 4 == 0 && aligned16(g->sh) && aligned16(out->sh)) ? 1 : 0;
+  a.uv_sum = uv_sum;
+  a.seen = seen;
+  a.z_max = z_max;
+  a.grad_uv = cfg->grad_uv;
+  a.grad_z = cfg->grad_z;
+  a.log_scale_split = cfg->log_scale_split;
+  a.logit_prune = cfg->logit_prune;
+  a.o_means = out->means;
+  a.o_log_scales = out->log_scales;
+  a.o_quats = out->quats;
+  a.o_opacity = out->opacity_logits;
+  a.o_skew = out->skew;
+  a.o_split_dir = out->split_dir;
+  a.o_sh = out->sh;
+  a.src_map = src_map;
+  a.counts = counts;
+  a.block_sums = static_cast<uint32_t*>(scratch);
+  return from_cuda(launch_densify(a, static_cast<cudaStream_t>(stream)));
+}
+
+sr_status sr_densify_remap(const float* in, int32_t width, const uint32_t* src_map, const int64_t* counts,
+                           int64_t cap, float* out, void* stream) {
+  if (width < 0 || cap < 0) return SR_ERR_INVALID;
+  if (width > 0 && cap > 0 && (!in || !src_map || !counts || !out)) return SR_ERR_INVALID;
+  return from_cuda(launch_densify_remap(in, width, src_map, counts, cap, out, device_sms(),
+                                        static_cast<cudaStream_t>(stream)));
+}
+
 sr_status sr_read_status(const sr_plan* p, void* ws, int64_t* keys_needed, void* stream) {
   sr_status s = check_plan(p, ws);
   if (s != SR_OK) return s;

@@ -56,6 +56,34 @@ struct RenderArgs {     // forward and backward composite
   int px_bwd;
 };
 
+struct DensifyArgs {     // densification
+  const float* means;
+  const float* log_scales;
+  const float* quats;
+  const float* opacity;
+  const float* skew;
+  const float* split_dir;  // or null
+  const float* sh;
+  int64_t n;
+  int two;                 // two opacity logits per Gaussian
+  int k3;                  // SH floats per Gaussian
+  int sh_vec4;             // SH rows 16-byte aligned: float4 copies
+  const float* uv_sum;
+  const int32_t* seen;
+  const float* z_max;
+  float grad_uv, grad_z, log_scale_split, logit_prune;
+  float* o_means;
+  float* o_log_scales;
+  float* o_quats;
+  float* o_opacity;
+  float* o_skew;
+  float* o_split_dir;
+  float* o_sh;
+  uint32_t* src_map;       // or null
+  int64_t* counts;         // [4] kept, cloned, split, total
+  uint32_t* block_sums;    // scratch [blocks][4]
+};
+
 cudaError_t launch_preprocess_fwd(const PreArgs& a, cudaStream_t st, int sms);
 cudaError_t launch_preprocess_bwd(const BwdArgs& a, cudaStream_t st, int sms);
 cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms);
@@ -69,6 +97,10 @@ cudaError_t launch_loss(const float* images, const float* targets, float lambda,
                         int64_t total_pixels, cudaStream_t st);
 cudaError_t launch_adam(const sr_adam_group* groups, int n_groups, int64_t step, float b1, float b2, float eps,
                         int sms, cudaStream_t st);
+size_t densify_scratch_bytes(int64_t n);
+cudaError_t launch_densify(const DensifyArgs& a, cudaStream_t st);
+cudaError_t launch_densify_remap(const float* in, int width, const uint32_t* src_map, const int64_t* counts,
+                                 int64_t cap, float* out, int sms, cudaStream_t st);
 cudaError_t launch_densify_stats(const float* g_uv, const float* g_z, int64_t n, float* uv_sum, int32_t* seen,
                                  float* z_max, int sms, cudaStream_t st);
 

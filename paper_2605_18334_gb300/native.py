@@ -23,7 +23,7 @@ EXPORTS = ["sr_abi_version", "sr_status_string", "sr_config_default", "sr_camera
            "sr_workspace_size", "sr_preprocess", "sr_bin_sort", "sr_render_fwd", "sr_render_bwd", "sr_read_status",
            "sr_kernel_launches", "sr_frame_counters", "sr_sort_keys_noalloc", "sr_render_bwd_composite",
            "sr_render_bwd_project", "sr_selftest_bounded_wait", "sr_loss_scratch_size", "sr_loss_l1_dssim",
-           "sr_adam_step", "sr_densify_stats"]
+           "sr_adam_step", "sr_densify_stats", "sr_densify_scratch_size", "sr_densify", "sr_densify_remap"]
 
 SR_ADAM_MAX_GROUPS = 16
 
@@ -31,6 +31,16 @@ SR_ADAM_MAX_GROUPS = 16
 class sr_adam_group(C.Structure):
     _fields_ = [("param", C.c_void_p), ("grad", C.c_void_p), ("m", C.c_void_p), ("v", C.c_void_p), ("n", C.c_int64),
                 ("lr", C.c_float), ("lr_rest", C.c_float), ("period", C.c_int32), ("split_at", C.c_int32)]
+
+
+class sr_densify_config(C.Structure):
+    _fields_ = [("grad_uv", C.c_float), ("grad_z", C.c_float), ("log_scale_split", C.c_float),
+                ("logit_prune", C.c_float)]
+
+
+class sr_scene_arrays(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logits", C.c_void_p), ("skew", C.c_void_p), ("split_dir", C.c_void_p), ("sh", C.c_void_p)]
 
 
 class sr_gaussians(C.Structure):
@@ -138,6 +148,14 @@ def load(build_if_missing: bool = True):
         lib.sr_densify_stats.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p]
         lib.sr_densify_stats.restype = C.c_int
+        lib.sr_densify_scratch_size.restype = C.c_size_t
+        lib.sr_densify_scratch_size.argtypes = [C.c_int64]
+        lib.sr_densify.argtypes = [P(sr_gaussians), C.c_void_p, C.c_void_p, C.c_void_p, P(sr_densify_config),
+                                   P(sr_scene_arrays), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.sr_densify.restype = C.c_int
+        lib.sr_densify_remap.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                         C.c_void_p]
+        lib.sr_densify_remap.restype = C.c_int
         for name in ("sr_config_default", "sr_camera_from_gl", "sr_plan_init", "sr_preprocess", "sr_bin_sort",
                      "sr_render_fwd", "sr_render_bwd", "sr_read_status", "sr_render_bwd_composite",
                      "sr_render_bwd_project"):
@@ -274,6 +292,25 @@ def sr_densify_stats(g_uv_ptr: int, g_z_ptr: int, n: int, uv_sum_ptr: int, seen_
     check("sr_densify_stats", load().sr_densify_stats(C.c_void_p(g_uv_ptr), C.c_void_p(g_z_ptr), C.c_int64(n),
                                                       C.c_void_p(uv_sum_ptr), C.c_void_p(seen_ptr),
                                                       C.c_void_p(z_max_ptr), C.c_void_p(stream)))
+
+
+def sr_densify_scratch_size(n: int) -> int:
+    return int(load().sr_densify_scratch_size(C.c_int64(n)))
+
+
+def sr_densify(g, uv_sum_ptr: int, seen_ptr: int, z_max_ptr: int, cfg, out, src_map_ptr: int, counts_ptr: int,
+               scratch_ptr: int, stream: int) -> None:
+    check("sr_densify", load().sr_densify(C.byref(g), C.c_void_p(uv_sum_ptr), C.c_void_p(seen_ptr),
+                                          C.c_void_p(z_max_ptr), C.byref(cfg), C.byref(out),
+                                          C.c_void_p(src_map_ptr), C.c_void_p(counts_ptr), C.c_void_p(scratch_ptr),
+                                          C.c_void_p(stream)))
+
+
+def sr_densify_remap(in_ptr: int, width: int, src_map_ptr: int, counts_ptr: int, cap: int, out_ptr: int,
+                     stream: int) -> None:
+    check("sr_densify_remap", load().sr_densify_remap(C.c_void_p(in_ptr), C.c_int32(width), C.c_void_p(src_map_ptr),
+                                                      C.c_void_p(counts_ptr), C.c_int64(cap), C.c_void_p(out_ptr),
+                                                      C.c_void_p(stream)))
 
 
 def sr_read_status(plan, ws_ptr: int, stream: int):

@@ -195,3 +195,33 @@ def test_training_calls_reject_invalid_arguments_without_device_work(lib):
     g.grad = None
     arr = (N.sr_adam_group * 1)(g)
     assert lib.sr_adam_step(arr, 1, 1, C.c_float(0.9), C.c_float(0.999), C.c_float(1e-15), None) == N.SR_ERR_INVALID
+
+
+def test_densify_calls_reject_invalid_arguments_without_device_work(lib):
+    g = _desc(100, deg=1)
+    for f in ("means", "log_scales", "quats", "opacity_logits", "skew", "sh"):
+        setattr(g, f, 4096)
+    ok = C.c_void_p(4096)
+    cfg = N.sr_densify_config(0.1, 0.1, -3.0, -2.0)
+    out = N.sr_scene_arrays()
+    for f in ("means", "log_scales", "quats", "opacity_logits", "skew", "sh"):
+        setattr(out, f, 8192)
+    assert lib.sr_densify_scratch_size(C.c_int64(100)) >= 16
+    call = lambda gg, oo, cc=cfg: lib.sr_densify(C.byref(gg), ok, ok, ok, C.byref(cc), C.byref(oo), None, ok, ok, None)
+    g.dt_sh = N.SR_BF16  # FP32 attributes only
+    assert call(g, out) == N.SR_ERR_INVALID
+    g.dt_sh = N.SR_F32
+    g.n = 1 << 30  # source indices must fit in 30 bits
+    assert call(g, out) == N.SR_ERR_INVALID
+    g.n = 100
+    out.sh = None
+    assert call(g, out) == N.SR_ERR_INVALID
+    out.sh = 8192
+    out.split_dir = 8192  # an output split direction without an input one
+    assert call(g, out) == N.SR_ERR_INVALID
+    out.split_dir = None
+    out.quats = 8192 + 4  # read and written as float4
+    assert call(g, out) == N.SR_ERR_INVALID
+    assert lib.sr_densify(C.byref(g), ok, ok, ok, None, C.byref(out), None, ok, ok, None) == N.SR_ERR_INVALID
+    assert lib.sr_densify_remap(ok, -1, ok, ok, 10, ok, None) == N.SR_ERR_INVALID
+    assert lib.sr_densify_remap(None, 3, ok, ok, 10, ok, None) == N.SR_ERR_INVALID
