@@ -134,8 +134,8 @@ __device__ __forceinline__ void copy3(const float* s, float* d) {
   d[2] = s[2];
 }
 
-// one output Gaussian: a copy of Gaussian i, or (side = +1 / -1) one of its
-// split children
+// one output Gaussian but its SH row: a copy of Gaussian i, or (side = +1 /
+// -1) one of its split children
 __device__ __forceinline__ void write_gaussian(const DensifyArgs& a, int64_t i, int64_t p, int side) {
   const float* mu = a.means + 3 * i;
   const float* ls = a.log_scales + 3 * i;
@@ -198,17 +198,15 @@ __device__ __forceinline__ void write_gaussian(const DensifyArgs& a, int64_t i, 
       oe[j] = j == k ? 0.0f : eta[j] * rk;
     }
   }
-  const float* s = a.sh + (int64_t)a.k3 * i;
-  float* d = a.o_sh + (int64_t)a.k3 * p;
-  if (a.sh_vec4) {
-    for (int c = 0; c < a.k3 / 4; ++c) reinterpret_cast<float4*>(d)[c] = reinterpret_cast<const float4*>(s)[c];
-  } else {
-    for (int c = 0; c < a.k3; ++c) d[c] = s[c];
-  }
 }
 
+// The SH rows (most of the bytes) are copied by the whole block once every
+// output of its 1024 Gaussians is placed: consecutive threads take
+// consecutive floats (float4s) of consecutive outputs, so reads and writes
+// are coalesced.
 __global__ void __launch_bounds__(kDenThreads) densify_scatter_kernel(DensifyArgs a) {
   __shared__ unsigned long long s_warp[32];
+  __shared__ uint32_t s_src[2 * kDenBlock], s_dst[2 * kDenBlock];
   const int64_t base = (int64_t)blockIdx.x * kDenBlock + (int64_t)threadIdx.x * kDenItems;
   int act[kDenItems];
   unsigned long long w = 0;
@@ -223,17 +221,24 @@ __global__ void __launch_bounds__(kDenThreads) densify_scatter_kernel(DensifyArg
   int64_t keep = bo[0] + (int64_t)(ex & kField);
   int64_t clone = a.counts[0] + bo[1] + (int64_t)((ex >> 21) & kField);
   int64_t split = a.counts[0] + a.counts[1] + 2 * (bo[2] + (int64_t)((ex >> 42) & kField));
+  // this thread's first slot in the block's list of (source, output) rows
+  int slot = (int)((ex & kField) + ((ex >> 21) & kField) + 2 * ((ex >> 42) & kField));
+  const int n_rows = (int)((total & kField) + ((total >> 21) & kField) + 2 * ((total >> 42) & kField));
 #pragma unroll
   for (int j = 0; j < kDenItems; ++j) {
     const int64_t i = base + j;
     if (act[j] == ACT_KEEP || act[j] == ACT_CLONE) {
       write_gaussian(a, i, keep, 0);
       if (a.src_map) a.src_map[keep] = (uint32_t)i;
+      s_src[slot] = (uint32_t)i;
+      s_dst[slot++] = (uint32_t)keep;
       ++keep;
     }
     if (act[j] == ACT_CLONE) {
       write_gaussian(a, i, clone, 0);
       if (a.src_map) a.src_map[clone] = (uint32_t)i | (1u << 30);
+      s_src[slot] = (uint32_t)i;
+      s_dst[slot++] = (uint32_t)clone;
       ++clone;
     }
     if (act[j] == ACT_SPLIT) {
@@ -243,7 +248,27 @@ __global__ void __launch_bounds__(kDenThreads) densify_scatter_kernel(DensifyArg
         a.src_map[split] = (uint32_t)i | (2u << 30);
         a.src_map[split + 1] = (uint32_t)i | (3u << 30);
       }
+      s_src[slot] = (uint32_t)i;
+      s_dst[slot++] = (uint32_t)split;
+      s_src[slot] = (uint32_t)i;
+      s_dst[slot++] = (uint32_t)(split + 1);
       split += 2;
+    }
+  }
+  __syncthreads();
+  if (a.sh_vec4) {
+    const int w = a.k3 / 4;
+    const float4* s = reinterpret_cast<const float4*>(a.sh);
+    float4* d = reinterpret_cast<float4*>(a.o_sh);
+    for (int e = threadIdx.x; e < n_rows * w; e += kDenThreads) {
+      const int r = e / w, c = e - r * w;
+      d[(int64_t)s_dst[r] * w + c] = s[(int64_t)s_src[r] * w + c];
+    }
+  } else {
+    const int w = a.k3;
+    for (int e = threadIdx.x; e < n_rows * w; e += kDenThreads) {
+      const int r = e / w, c = e - r * w;
+      a.o_sh[(int64_t)s_dst[r] * w + c] = a.sh[(int64_t)s_src[r] * w + c];
     }
   }
 }
