@@ -30,8 +30,6 @@ namespace sr {
 constexpr int kWin = 11, kHalf = 5, kHalo = kTile + 2 * kHalf;  // 26
 constexpr float kC1 = 0.0001f, kC2 = 0.0009f;                  // (0.01)^2, (0.03)^2
 
-__constant__ float c_win[kWin];
-
 struct LossArgs {
   const float* images;
   const float* targets;
@@ -45,6 +43,7 @@ struct LossArgs {
   int64_t total_tiles;
   int64_t total_values;  // 3 * total pixels
   float lambda;
+  float win[kWin];       // normalised Gaussian window (kernel parameters: no separate upload)
 };
 
 struct TileRef {
@@ -53,55 +52,54 @@ struct TileRef {
   int64_t plane;    // offset of this channel's [H][W] plane
 };
 
-__device__ __forceinline__ TileRef loss_tile(const LossArgs& a, int64_t b) {
+__device__ __forceinline__ TileRef loss_tile(const LossArgs& a, uint32_t b) {
   TileRef t;
-  const int ch = (int)(b / a.total_tiles);
-  const int64_t tile = b - (int64_t)ch * a.total_tiles;
+  const uint32_t tt = (uint32_t)a.total_tiles;  // < 2^31 tiles per plan
+  const uint32_t ch = b / tt;
+  const uint32_t tile = b - ch * tt;
   const int v = view_of_tile(a.views, a.n_views, tile);
   t.vi = a.views[v];
-  const int lt = (int)(tile - t.vi.tile_base);
+  const int lt = (int)(tile - (uint32_t)t.vi.tile_base);
   t.x0 = (lt % t.vi.tiles_x) * kTile;
   t.y0 = (lt / t.vi.tiles_x) * kTile;
   t.plane = t.vi.image_offset + (int64_t)ch * t.vi.width * t.vi.height;
   return t;
 }
 
-// Separable window sums over a 16 x 16 tile with a 5-pixel halo, in shared
-// memory, with sliding windows in registers: the horizontal pass takes one
-// (halo row, map) per thread (26 loads, 16 outputs of 11 taps), the
-// vertical pass one (tile column, map) per thread; s_v[m][y][x] receives map
-// m filtered at tile pixel (x, y).  MAP(m, r, c) reads map m at halo (r, c).
-template <int NM, class Map>
-__device__ __forceinline__ void window_sums(const Map& MAP, float (*s_h)[kHalo][kTile + 1],
-                                            float (*s_v)[kTile][kTile + 1]) {
-  for (int it = threadIdx.x; it < NM * kHalo; it += blockDim.x) {
-    const int m = it / kHalo, r = it - m * kHalo;
-    float in[kHalo];
+// Separable window sums over a 16 x 16 tile with a 5-pixel halo (26 x 26),
+// in shared memory.  Two values that are filtered alike travel as one float2
+// (x and y; x^2 and y^2; u and v) so each tap is one packed FP32x2 FMA.  The
+// horizontal pass gives each of 208 threads one halo row and two adjacent
+// output columns (12 inputs, 11 taps); its results are stored transposed
+// (column-major), so the vertical pass reads a column's 12 inputs as
+// contiguous 16-byte vectors; a vertical-pass thread owns one tile column and
+// two adjacent rows and finishes its two pixels itself.
+constexpr int kHp = kHalo + 2;  // padded row length (even: 8-byte aligned pairs)
+
+struct WinWeights {
+  float w[kWin];
+  __device__ __forceinline__ explicit WinWeights(const LossArgs& a) {
 #pragma unroll
-    for (int c = 0; c < kHalo; ++c) in[c] = MAP(m, r, c);
-#pragma unroll
-    for (int c = 0; c < kTile; ++c) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int k = 0; k < kWin; ++k) acc = __fmaf_rn(c_win[k], in[c + k], acc);
-      s_h[m][r][c] = acc;
-    }
+    for (int k = 0; k < kWin; ++k) w[k] = a.win[k];
   }
-  __syncthreads();
-  for (int it = threadIdx.x; it < NM * kTile; it += blockDim.x) {
-    const int m = it / kTile, c = it - m * kTile;
-    float in[kHalo];
+};
+
+// sum_k w_k v[k + o] for o = 0, 1 (two adjacent outputs of a 12-input run)
+__device__ __forceinline__ void taps2(const WinWeights& W, const float2 (&v)[kWin + 1], float2& o0, float2& o1) {
+  o0 = o1 = make_float2(0.0f, 0.0f);
 #pragma unroll
-    for (int r = 0; r < kHalo; ++r) in[r] = s_h[m][r][c];
-#pragma unroll
-    for (int r = 0; r < kTile; ++r) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int k = 0; k < kWin; ++k) acc = __fmaf_rn(c_win[k], in[r + k], acc);
-      s_v[m][r][c] = acc;
-    }
+  for (int k = 0; k < kWin; ++k) {
+    o0 = fma2(f2(W.w[k]), v[k], o0);
+    o1 = fma2(f2(W.w[k]), v[k + 1], o1);
   }
-  __syncthreads();
+}
+__device__ __forceinline__ void taps1(const WinWeights& W, const float (&v)[kWin + 1], float& o0, float& o1) {
+  o0 = o1 = 0.0f;
+#pragma unroll
+  for (int k = 0; k < kWin; ++k) {
+    o0 = __fmaf_rn(W.w[k], v[k], o0);
+    o1 = __fmaf_rn(W.w[k], v[k + 1], o1);
+  }
 }
 
 __device__ __forceinline__ void block_sum2(float a, float b, float* s_red, float* out_a, float* out_b) {
@@ -129,87 +127,119 @@ __device__ __forceinline__ void block_sum2(float a, float b, float* s_red, float
 
 // moments, SSIM and the maps u, v, k of one channel of one tile
 __global__ void __launch_bounds__(256) ssim_fwd_kernel(LossArgs a) {
-  __shared__ float s_in[2][kHalo][kHalo + 1];  // x, y of the tile and its halo
-  __shared__ float s_h[5][kHalo][kTile + 1];
-  __shared__ float s_v[5][kTile][kTile + 1];   // windowed x, y, x^2, y^2, xy
+  __shared__ __align__(16) float2 s_xy[kHalo][kHp];    // (x, y) of the tile and its halo
+  __shared__ __align__(16) float2 s_a[kTile][kHp];     // horizontal sums of (x, y), [column][row]
+  __shared__ __align__(16) float2 s_b[kTile][kHp];     // ... of (x^2, y^2)
+  __shared__ __align__(16) float s_c[kTile][kHp];      // ... of x y
   __shared__ float s_red[16];
   const TileRef t = loss_tile(a, blockIdx.x);
   const int W = t.vi.width, H = t.vi.height;
   // the tile and its halo: every load of the thread issued before the stores
   constexpr int kPer = (kHalo * kHalo + 255) / 256;
-  float xs[kPer], ys[kPer];
+  float2 xy[kPer];
 #pragma unroll
   for (int j = 0; j < kPer; ++j) {
     const int i = threadIdx.x + 256 * j, r = i / kHalo, c = i - r * kHalo;
     const int px = t.x0 - kHalf + c, py = t.y0 - kHalf + r;
-    xs[j] = ys[j] = 0.0f;
+    xy[j] = make_float2(0.0f, 0.0f);
     if (i < kHalo * kHalo && px >= 0 && px < W && py >= 0 && py < H) {
       const int64_t o = t.plane + (int64_t)py * W + px;
-      xs[j] = a.images[o];
-      ys[j] = a.targets[o];
+      xy[j] = make_float2(a.images[o], a.targets[o]);
     }
   }
 #pragma unroll
   for (int j = 0; j < kPer; ++j) {
     const int i = threadIdx.x + 256 * j, r = i / kHalo, c = i - r * kHalo;
-    if (i < kHalo * kHalo) {
-      s_in[0][r][c] = xs[j];
-      s_in[1][r][c] = ys[j];
-    }
+    if (i < kHalo * kHalo) s_xy[r][c] = xy[j];
   }
   __syncthreads();
-  const auto moments = [&](int m, int r, int c) {
-    const float x = s_in[0][r][c], y = s_in[1][r][c];
-    return m == 0 ? x : m == 1 ? y : m == 2 ? x * x : m == 3 ? y * y : x * y;
-  };
-  window_sums<5>(moments, s_h, s_v);
-  float mo[5];
-  {
-    const int ty = threadIdx.x / kTile, tx = threadIdx.x - ty * kTile;
+  const WinWeights Wt(a);
+  if (threadIdx.x < kHalo * (kTile / 2)) {  // horizontal: halo row r, output columns c0, c0 + 1
+    const int r = threadIdx.x >> 3, c0 = (threadIdx.x & 7) * 2;
+    float2 p[kWin + 1], q[kWin + 1];
+    float m[kWin + 1];
 #pragma unroll
-    for (int m = 0; m < 5; ++m) mo[m] = s_v[m][ty][tx];
+    for (int j = 0; j <= kWin; ++j) {
+      p[j] = s_xy[r][c0 + j];
+      q[j] = mul2(p[j], p[j]);
+      m[j] = p[j].x * p[j].y;
+    }
+    float2 a0, a1, b0, b1;
+    float e0, e1;
+    taps2(Wt, p, a0, a1);
+    taps2(Wt, q, b0, b1);
+    taps1(Wt, m, e0, e1);
+    s_a[c0][r] = a0;
+    s_a[c0 + 1][r] = a1;
+    s_b[c0][r] = b0;
+    s_b[c0 + 1][r] = b1;
+    s_c[c0][r] = e0;
+    s_c[c0 + 1][r] = e1;
   }
-  const int ty = threadIdx.x / kTile, tx = threadIdx.x - ty * kTile;
-  const int px = t.x0 + tx, py = t.y0 + ty;
+  __syncthreads();
   float s_val = 0.0f, l1 = 0.0f;
-  if (px < W && py < H) {
-    const float mx = mo[0], my = mo[1];
-    const float sx = mo[2] - mx * mx, sy = mo[3] - my * my, sxy = mo[4] - mx * my;
-    const float A1 = 2.0f * mx * my + kC1, A2 = 2.0f * sxy + kC2;
-    const float B1 = mx * mx + my * my + kC1, B2 = sx + sy + kC2;
-    const float inv = 1.0f / (B1 * B2);
-    s_val = A1 * A2 * inv;
-    const float da = 2.0f * A2 * (my * B1 - mx * A1) * inv / B1;
-    const float db = -s_val / B2;
-    const float dc = 2.0f * A1 * inv;
+  if (threadIdx.x < kTile * (kTile / 2)) {  // vertical: column c, rows r0, r0 + 1
+    const int c = threadIdx.x >> 3, r0 = (threadIdx.x & 7) * 2;
+    float2 p[kWin + 1], q[kWin + 1];
+    float m[kWin + 1];
+#pragma unroll
+    for (int j = 0; j <= kWin; ++j) {
+      p[j] = s_a[c][r0 + j];
+      q[j] = s_b[c][r0 + j];
+      m[j] = s_c[c][r0 + j];
+    }
+    float2 mu[2], sq[2];
+    float cr[2];
+    taps2(Wt, p, mu[0], mu[1]);
+    taps2(Wt, q, sq[0], sq[1]);
+    taps1(Wt, m, cr[0], cr[1]);
     const float g = -a.lambda / (float)a.total_values;  // dL/dS
-    const int64_t o = t.plane + (int64_t)py * W + px;
-    a.maps[o] = g * (da - 2.0f * mx * db - my * dc);
-    a.maps[a.total_values + o] = g * db;
-    a.maps[2 * a.total_values + o] = g * dc;
-    l1 = fabsf(s_in[0][ty + kHalf][tx + kHalf] - s_in[1][ty + kHalf][tx + kHalf]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int px = t.x0 + c, py = t.y0 + r0 + h;
+      if (px < W && py < H) {
+        const float mx = mu[h].x, my = mu[h].y;
+        const float sx = sq[h].x - mx * mx, sy = sq[h].y - my * my, sxy = cr[h] - mx * my;
+        const float A1 = 2.0f * mx * my + kC1, A2 = 2.0f * sxy + kC2;
+        const float B1 = mx * mx + my * my + kC1, B2 = sx + sy + kC2;
+        const float inv = 1.0f / (B1 * B2);
+        const float S = A1 * A2 * inv;
+        const float da = 2.0f * A2 * (my * B1 - mx * A1) * inv / B1;
+        const float db = -S / B2;
+        const float dc = 2.0f * A1 * inv;
+        const int64_t o = t.plane + (int64_t)py * W + px;
+        a.maps[o] = g * (da - 2.0f * mx * db - my * dc);
+        a.maps[a.total_values + o] = g * db;
+        a.maps[2 * a.total_values + o] = g * dc;
+        const float2 v = s_xy[r0 + h + kHalf][c + kHalf];
+        s_val += S;
+        l1 += fabsf(v.x - v.y);
+      }
+    }
   }
   block_sum2(s_val, l1, s_red, &a.partial[blockIdx.x], &a.partial[gridDim.x + blockIdx.x]);
 }
 
 // dL/dC = (w * u) + 2 x (w * v) + y (w * k) + (1 - lambda) sign(x - y) / N
 __global__ void __launch_bounds__(256) ssim_bwd_kernel(LossArgs a) {
-  __shared__ float s_in[3][kHalo][kHalo + 1];
-  __shared__ float s_h[3][kHalo][kTile + 1];
-  __shared__ float s_v[3][kTile][kTile + 1];
+  __shared__ __align__(16) float2 s_uv[kHalo][kHp];
+  __shared__ __align__(16) float s_k[kHalo][kHp];
+  __shared__ __align__(16) float2 s_a[kTile][kHp];  // horizontal sums of (u, v), [column][row]
+  __shared__ __align__(16) float s_c[kTile][kHp];   // ... of k
   const TileRef t = loss_tile(a, blockIdx.x);
   const int W = t.vi.width, H = t.vi.height;
   constexpr int kPer = (kHalo * kHalo + 255) / 256;
-  float us[kPer], vs[kPer], ks[kPer];
+  float2 uv[kPer];
+  float ks[kPer];
 #pragma unroll
   for (int j = 0; j < kPer; ++j) {
     const int i = threadIdx.x + 256 * j, r = i / kHalo, c = i - r * kHalo;
     const int px = t.x0 - kHalf + c, py = t.y0 - kHalf + r;
-    us[j] = vs[j] = ks[j] = 0.0f;
+    uv[j] = make_float2(0.0f, 0.0f);
+    ks[j] = 0.0f;
     if (i < kHalo * kHalo && px >= 0 && px < W && py >= 0 && py < H) {
       const int64_t o = t.plane + (int64_t)py * W + px;
-      us[j] = a.maps[o];
-      vs[j] = a.maps[a.total_values + o];
+      uv[j] = make_float2(a.maps[o], a.maps[a.total_values + o]);
       ks[j] = a.maps[2 * a.total_values + o];
     }
   }
@@ -217,38 +247,77 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(LossArgs a) {
   for (int j = 0; j < kPer; ++j) {
     const int i = threadIdx.x + 256 * j, r = i / kHalo, c = i - r * kHalo;
     if (i < kHalo * kHalo) {
-      s_in[0][r][c] = us[j];
-      s_in[1][r][c] = vs[j];
-      s_in[2][r][c] = ks[j];
+      s_uv[r][c] = uv[j];
+      s_k[r][c] = ks[j];
     }
   }
   __syncthreads();
-  const auto maps = [&](int m, int r, int c) { return s_in[m][r][c]; };
-  window_sums<3>(maps, s_h, s_v);
-  float f[3];
-  {
-    const int ty = threadIdx.x / kTile, tx = threadIdx.x - ty * kTile;
+  const WinWeights Wt(a);
+  if (threadIdx.x < kHalo * (kTile / 2)) {
+    const int r = threadIdx.x >> 3, c0 = (threadIdx.x & 7) * 2;
+    float2 p[kWin + 1];
+    float m[kWin + 1];
 #pragma unroll
-    for (int m = 0; m < 3; ++m) f[m] = s_v[m][ty][tx];
+    for (int j = 0; j <= kWin; ++j) {
+      p[j] = s_uv[r][c0 + j];
+      m[j] = s_k[r][c0 + j];
+    }
+    float2 a0, a1;
+    float e0, e1;
+    taps2(Wt, p, a0, a1);
+    taps1(Wt, m, e0, e1);
+    s_a[c0][r] = a0;
+    s_a[c0 + 1][r] = a1;
+    s_c[c0][r] = e0;
+    s_c[c0 + 1][r] = e1;
   }
-  const int ty = threadIdx.x / kTile, tx = threadIdx.x - ty * kTile;
-  const int px = t.x0 + tx, py = t.y0 + ty;
-  if (px < W && py < H) {
-    const int64_t o = t.plane + (int64_t)py * W + px;
-    const float x = a.images[o], y = a.targets[o];
-    const float d = x - y;
-    const float sgn = d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f);
-    a.d_images[o] = f[0] + 2.0f * x * f[1] + y * f[2] + (1.0f - a.lambda) * sgn / (float)a.total_values;
+  __syncthreads();
+  if (threadIdx.x < kTile * (kTile / 2)) {
+    const int c = threadIdx.x >> 3, r0 = (threadIdx.x & 7) * 2;
+    float2 p[kWin + 1];
+    float m[kWin + 1];
+#pragma unroll
+    for (int j = 0; j <= kWin; ++j) {
+      p[j] = s_a[c][r0 + j];
+      m[j] = s_c[c][r0 + j];
+    }
+    float2 f[2];
+    float fk[2];
+    taps2(Wt, p, f[0], f[1]);
+    taps1(Wt, m, fk[0], fk[1]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int px = t.x0 + c, py = t.y0 + r0 + h;
+      if (px < W && py < H) {
+        const int64_t o = t.plane + (int64_t)py * W + px;
+        const float x = a.images[o], y = a.targets[o];
+        const float d = x - y;
+        const float sgn = d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f);
+        a.d_images[o] = f[h].x + 2.0f * x * f[h].y + y * fk[h] + (1.0f - a.lambda) * sgn / (float)a.total_values;
+      }
+    }
   }
 }
 
-// L from the per-block sums (one block, fixed order: deterministic)
-__global__ void __launch_bounds__(256) loss_reduce_kernel(LossArgs a, int blocks) {
-  __shared__ float s_red[16];
+// L from the per-block sums (one block, fixed order: deterministic); eight
+// loads of a thread in flight at a time, not one
+constexpr int kReduceThreads = 1024;
+__global__ void __launch_bounds__(kReduceThreads) loss_reduce_kernel(LossArgs a, int blocks) {
+  __shared__ float s_red[2 * kReduceThreads / 32];
   float s = 0.0f, l = 0.0f;
-  for (int i = threadIdx.x; i < blocks; i += blockDim.x) {
-    s += a.partial[i];
-    l += a.partial[blocks + i];
+  for (int i0 = threadIdx.x; i0 < blocks; i0 += 8 * kReduceThreads) {
+    float vs[8], vl[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + u * kReduceThreads;
+      vs[u] = i < blocks ? a.partial[i] : 0.0f;
+      vl[u] = i < blocks ? a.partial[blocks + i] : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      s += vs[u];
+      l += vl[u];
+    }
   }
   float ts = 0.0f, tl = 0.0f;
   block_sum2(s, l, s_red, &ts, &tl);
@@ -357,8 +426,8 @@ __global__ void __launch_bounds__(256) densify_stats_kernel(const float* __restr
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-static cudaError_t upload_window(cudaStream_t st) {
-  float w[kWin];
+// w_k = exp(-(k - 5)^2 / (2 * 1.5^2)), normalised to sum 1, in FP64, rounded once
+static void window_weights(float* w) {
   double sum = 0.0, e[kWin];
   for (int k = 0; k < kWin; ++k) {
     const double d = k - kHalf;
@@ -366,7 +435,6 @@ static cudaError_t upload_window(cudaStream_t st) {
     sum += e[k];
   }
   for (int k = 0; k < kWin; ++k) w[k] = (float)(e[k] / sum);
-  return cudaMemcpyToSymbolAsync(c_win, w, sizeof(w), 0, cudaMemcpyHostToDevice, st);
 }
 
 size_t loss_scratch_bytes(int64_t total_pixels, int64_t total_tiles) {
@@ -378,9 +446,8 @@ size_t loss_scratch_bytes(int64_t total_pixels, int64_t total_tiles) {
 cudaError_t launch_loss(const float* images, const float* targets, float lambda, float* d_images, float* loss,
                         float* ssim_l1, void* scratch, const ViewInfo* views, int n_views, int64_t total_tiles,
                         int64_t total_pixels, cudaStream_t st) {
-  cudaError_t e = upload_window(st);
-  if (e != cudaSuccess) return e;
   LossArgs a;
+  window_weights(a.win);
   a.images = images;
   a.targets = targets;
   a.d_images = d_images;
@@ -397,7 +464,7 @@ cudaError_t launch_loss(const float* images, const float* targets, float lambda,
   const int64_t blocks = 3 * total_tiles;
   ssim_fwd_kernel<<<(unsigned)blocks, 256, 0, st>>>(a);
   ssim_bwd_kernel<<<(unsigned)blocks, 256, 0, st>>>(a);
-  loss_reduce_kernel<<<1, 256, 0, st>>>(a, (int)blocks);
+  loss_reduce_kernel<<<1, kReduceThreads, 0, st>>>(a, (int)blocks);
   count_launches(3);
   return cudaGetLastError();
 }

@@ -108,6 +108,35 @@ class Trainer:
             self.seen = torch.zeros(g.n, dtype=torch.int32, device=dev)
             self.z_max = torch.zeros(g.n, device=dev)
 
+    def densify(self, grad_uv: float, grad_z: float, log_scale_split: float, logit_prune: float,
+                stream=None) -> dict:
+        """One densification (``sr_densify``) from the statistics collected
+        since the last one: the scene is replaced by the densified one, the
+        Adam moments follow their Gaussians (new ones start at zero), the
+        statistics restart from zero and the rasterizer is re-planned for the
+        new size.  Returns the counts (kept, cloned, split, total)."""
+        if not self.densify_stats:
+            raise RuntimeError("the trainer was made without densify_stats=True")
+        from .densify import densify, remap_state
+        res = densify(self.g, self.uv_sum, self.seen, self.z_max, grad_uv, grad_z, log_scale_split, logit_prune,
+                      stream)
+        ng = res.gaussians
+        for k, (m, v) in list(self.adam.state.items()):
+            self.adam.state[k] = (remap_state(m, res, stream), remap_state(v, res, stream))
+        self.g = ng
+        self.adam.g = ng
+        cams, cfg = self.rast.cams, self.rast.config
+        cap = max(1 << 16, int(self.rast.key_capacity * max(1.0, ng.n / max(1, res.src_map.numel() // 2))))
+        self.rast = Rasterizer(ng, cams, cfg, key_capacity=cap)
+        self.loss = PhotometricLoss(self.rast, self.loss.lam)
+        self.grads = None
+        dev = ng.means.device
+        self.uv_sum = torch.zeros(ng.n, device=dev)
+        self.seen = torch.zeros(ng.n, dtype=torch.int32, device=dev)
+        self.z_max = torch.zeros(ng.n, device=dev)
+        self.last_densify = res  # source and kind of every new Gaussian
+        return res.counts
+
     def step(self, stream=None) -> torch.Tensor:
         """One training step; returns the device loss of the rendered frame."""
         self.rast.forward(self.g, stream)

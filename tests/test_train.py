@@ -233,3 +233,39 @@ def test_densification_statistics_accumulate_over_steps():
     np.testing.assert_array_equal(tr.seen.cpu().numpy(), seen)
     np.testing.assert_array_equal(tr.z_max.cpu().numpy(), zmax.astype(np.float32))
     assert seen.max() == 4 and zmax.max() > 0
+
+
+@pytest.mark.gpu
+def test_training_with_densification_keeps_going():
+    """Steps, one densification from the collected statistics (the trainer
+    re-plans for the new size and carries the Adam moments over), more steps:
+    the scene grows by the clone copies and split children, the moments of
+    kept Gaussians survive and new ones start at zero, and the loss keeps
+    falling."""
+    _gpu()
+    from paper_2605_18334_gb300 import scenes
+    from paper_2605_18334_gb300.rasterizer import Config, Gaussians, Rasterizer
+    from paper_2605_18334_gb300.train import Trainer
+
+    sc = scenes.cluster(seed=19, n=3000, sh_degree=1)
+    cams = [scenes.identity_camera(96, 64)]
+    target_scene = sc.subset(np.arange(sc.n))
+    target_scene.means = (sc.means + np.random.default_rng(2).normal(0, 0.02, sc.means.shape)).astype(np.float32)
+    gt = Gaussians.from_scene(target_scene)
+    targets = Rasterizer(gt, cams, Config()).forward(gt).clone()
+    tr = Trainer(Gaussians.from_scene(sc), cams, targets, lr=dict(means=1e-3), densify_stats=True)
+    losses = [float(tr.step().item()) for _ in range(10)]
+    m_before = tr.adam.state["means"][0].clone()
+    uv = (tr.uv_sum / tr.seen.clamp(min=1)).cpu().numpy()
+    thr = float(np.quantile(uv[uv > 0], 0.8))
+    n0 = tr.g.n
+    counts = tr.densify(grad_uv=thr, grad_z=1e30, log_scale_split=-4.0, logit_prune=-1e30)
+    assert counts["cloned"] > 0 and counts["split"] > 0
+    assert tr.g.n == counts["total"] == counts["kept"] + counts["cloned"] + 2 * counts["split"] > n0
+    m_after = tr.adam.state["means"][0]
+    src = tr.last_densify.src[:counts["kept"]]
+    assert torch.equal(m_after[:counts["kept"]], m_before[src])
+    assert torch.count_nonzero(m_after[counts["kept"]:]) == 0
+    assert tr.seen.numel() == tr.g.n and int(tr.seen.sum()) == 0
+    losses += [float(tr.step().item()) for _ in range(10)]
+    assert np.isfinite(losses).all() and losses[-1] < losses[0], losses
