@@ -102,6 +102,7 @@ __device__ __forceinline__ void scan_load(const uint32_t* __restrict__ cnt, int6
 
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ cnt, int64_t m,
                                                                    unsigned long long* __restrict__ part) {
+  pdl_entry();
   __shared__ unsigned long long s_warp[kScanThreads / 32];
   const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
   uint32_t v[kScanItems];
@@ -116,6 +117,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_
 
 __global__ void __launch_bounds__(1024) scan_parts_kernel(unsigned long long* part, int nb, Status* st,
                                                           unsigned long long cap) {
+  pdl_entry();
   __shared__ unsigned long long s_warp[32];
   unsigned long long carry = 0;
   for (int c0 = 0; c0 < nb; c0 += 1024) {
@@ -136,6 +138,7 @@ __global__ void __launch_bounds__(1024) scan_parts_kernel(unsigned long long* pa
 __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint32_t* __restrict__ cnt, int64_t m,
                                                                  const unsigned long long* __restrict__ part,
                                                                  uint32_t* __restrict__ offsets) {
+  pdl_entry();
   __shared__ unsigned long long s_warp[kScanThreads / 32];
   const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
   uint32_t v[kScanItems];
@@ -273,6 +276,7 @@ __global__ void __launch_bounds__(256, 4) duplicate_kernel(int64_t n, int n_view
                                                         uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                         unsigned long long cap, uint32_t* __restrict__ tile_hist,
                                                         int passes) {
+  pdl_entry();
   __shared__ TileHist th;
   for (int i = threadIdx.x; i < 257; i += blockDim.x) th.diff0[i] = 0;
   for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&th.h[0][0])[i] = 0u;
@@ -435,6 +439,7 @@ __global__ void __launch_bounds__(256) histogram_kernel(const KEY* __restrict__ 
                                                         const unsigned long long* count_dev,
                                                         unsigned long long count, int passes,
                                                         uint32_t* __restrict__ hist) {
+  pdl_entry();
   __shared__ uint32_t s_h[kMaxPasses][256];
   for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&s_h[0][0])[i] = 0u;
   __syncthreads();
@@ -455,6 +460,7 @@ __global__ void __launch_bounds__(256) histogram_kernel(const KEY* __restrict__ 
 __global__ void __launch_bounds__(256) hist_scan_kernel(uint32_t* __restrict__ hist, uint32_t* trivial,
                                                         const unsigned long long* count_dev,
                                                         unsigned long long count) {
+  pdl_entry();
   __shared__ unsigned long long s_warp[8];
   const int p = blockIdx.x;
   const unsigned long long kn = element_count(count_dev, count);
@@ -518,6 +524,7 @@ constexpr int kLookbackWindow = 4;  // look-back words in flight per digit
 
 template <class KEY>
 __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(PassArgs<KEY> a) {
+  pdl_entry();
   constexpr int NW = kSortThreads / 32;
   extern __shared__ __align__(16) unsigned char s_raw[];
   SortSmem<KEY>& sm = *reinterpret_cast<SortSmem<KEY>*>(s_raw);
@@ -680,6 +687,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(PassArgs<KEY>
 __global__ void __launch_bounds__(256) ranges_kernel(const uint32_t* __restrict__ keys, Status* st,
                                                      unsigned long long cap, uint2* __restrict__ ranges,
                                                      int sorted_buf) {
+  pdl_entry();
   const unsigned long long kn = element_count(&st->keys_needed, cap);
   if (blockIdx.x == 0 && threadIdx.x == 0) st->sorted_buf = (uint32_t)sorted_buf;
   for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < kn;
@@ -738,7 +746,7 @@ static int run_passes(const KEY* keys_in, const uint32_t* vals_in, KEY* const* k
     pa.n_tiles = n_tiles;
     pa.sorted_buf = (p == last && buf_ids) ? buf_ids[out] : 0;
     pa.out_gather = p == last ? last_gather : nullptr;
-    onesweep_kernel<KEY><<<(unsigned)parts, kSortThreads, sizeof(SortSmem<KEY>), st>>>(pa);
+    launch_pdl(onesweep_kernel<KEY>, dim3((unsigned)parts), dim3(kSortThreads), sizeof(SortSmem<KEY>), st, pa);
     count_launches(1);
     cur = out;
   }
@@ -750,22 +758,25 @@ static int run_passes(const KEY* keys_in, const uint32_t* vals_in, KEY* const* k
 cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms) {
   const int64_t m = a.n * a.n_views;
   cudaError_t e;
-  // status word, histograms and ranges start at zero every frame
+  // status word, histograms, look-back words of both sorts and ranges start
+  // at zero every frame; the last four are consecutive workspace slots, so
+  // one memset clears them all
   if ((e = cudaMemsetAsync(a.ws.status, 0, sizeof(Status), st)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(a.ws.hist, 0, sizeof(uint32_t) * 2 * kMaxPasses * 256, st)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(a.ws.ranges, 0, sizeof(uint2) * a.total_tiles, st)) != cudaSuccess) return e;
+  {
+    char* lo = reinterpret_cast<char*>(a.ws.hist);
+    char* hi = reinterpret_cast<char*>(a.ws.ranges + a.total_tiles);
+    if ((e = cudaMemsetAsync(lo, 0, (size_t)(hi - lo), st)) != cudaSuccess) return e;
+  }
   const unsigned long long um = (unsigned long long)m;
   const unsigned long long dparts = (um + kSortPart - 1) / kSortPart;
   const uint32_t* perm = a.ws.perm[0];
   const uint32_t* cnt_sorted = a.ws.dkey[0];
   if (m > 0) {
-    if ((e = cudaMemsetAsync(a.ws.lookback_d, 0, sizeof(unsigned long long) * 256 * kDepthPasses * dparts, st)) !=
-        cudaSuccess)
-      return e;
     // depth sort of the records (values: record indices)
-    histogram_kernel<uint32_t><<<clamp_grid((um + 255) / 256, sms, 4), 256, 0, st>>>(a.ws.dkey[0], nullptr, um,
-                                                                                      kDepthPasses, a.ws.hist);
-    hist_scan_kernel<<<kDepthPasses, 256, 0, st>>>(a.ws.hist, a.ws.status->pass_trivial, nullptr, um);
+    launch_pdl(histogram_kernel<uint32_t>, dim3(clamp_grid((um + 255) / 256, sms, 4)), dim3(256), 0, st,
+               (const uint32_t*)a.ws.dkey[0], (const unsigned long long*)nullptr, um, (int)kDepthPasses, a.ws.hist);
+    launch_pdl(hist_scan_kernel, dim3(kDepthPasses), dim3(256), 0, st, a.ws.hist, a.ws.status->pass_trivial,
+               (const unsigned long long*)nullptr, um);
     count_launches(2);
     uint32_t* const kb[2] = {a.ws.dkey[1], a.ws.dkey[0]};
     uint32_t* const vb[2] = {a.ws.perm[1], a.ws.perm[0]};
@@ -779,22 +790,24 @@ cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms) {
   }
   const int nb = (int)((m + kScanBlock - 1) / kScanBlock);
   if (m > 0) {
-    scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(cnt_sorted, m, a.ws.scan_part);
+    launch_pdl(scan_reduce_kernel, dim3(nb), dim3(kScanThreads), 0, st, cnt_sorted, m, a.ws.scan_part);
     count_launches(1);
   }
-  scan_parts_kernel<<<1, 1024, 0, st>>>(a.ws.scan_part, nb, a.ws.status, a.cap);
+  launch_pdl(scan_parts_kernel, dim3(1), dim3(1024), 0, st, a.ws.scan_part, nb, a.ws.status, a.cap);
   count_launches(1);
   if (m > 0) {
-    scan_down_kernel<<<nb, kScanThreads, 0, st>>>(cnt_sorted, m, a.ws.scan_part, a.ws.offsets);
+    launch_pdl(scan_down_kernel, dim3(nb), dim3(kScanThreads), 0, st, cnt_sorted, m,
+               (const unsigned long long*)a.ws.scan_part, a.ws.offsets);
     // keys and the tile sort's digit histograms
-    duplicate_kernel<<<clamp_grid((m + 255) / 256, sms, 4), 256, 0, st>>>(
-        a.n, a.n_views, a.ws.views, perm, cnt_sorted, a.ws.offsets, a.ws.rect, a.ws.rec, a.ws.foot, a.ws.keys[0],
-        a.ws.vals[0], a.cap, a.ws.hist + kMaxPasses * 256, a.passes);
+    launch_pdl(duplicate_kernel, dim3(clamp_grid((m + 255) / 256, sms, 4)), dim3(256), 0, st, a.n, a.n_views,
+               (const ViewInfo*)a.ws.views, perm, cnt_sorted, (const uint32_t*)a.ws.offsets, (const uint2*)a.ws.rect,
+               (const float4*)a.ws.rec, (const float4*)a.ws.foot, a.ws.keys[0], a.ws.vals[0], a.cap,
+               a.ws.hist + kMaxPasses * 256, a.passes);
     count_launches(2);
   }
   if (a.passes > 0) {
-    hist_scan_kernel<<<a.passes, 256, 0, st>>>(a.ws.hist + kMaxPasses * 256, a.ws.status->pass_trivial + kMaxPasses,
-                                               &a.ws.status->keys_needed, a.cap);
+    launch_pdl(hist_scan_kernel, dim3(a.passes), dim3(256), 0, st, a.ws.hist + kMaxPasses * 256,
+               a.ws.status->pass_trivial + kMaxPasses, (const unsigned long long*)&a.ws.status->keys_needed, a.cap);
     count_launches(1);
   }
   return cudaGetLastError();
@@ -817,6 +830,7 @@ __device__ __forceinline__ int tile_bucket(const uint2* ranges, int64_t t) {
 constexpr int64_t kOrderOneBlock = 65536;
 __global__ void __launch_bounds__(1024) tile_order_block_kernel(const uint2* __restrict__ ranges, int64_t tiles,
                                                                 uint32_t* __restrict__ order) {
+  pdl_entry();
   __shared__ uint32_t s_cnt[33], s_cur[33];
   if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0u;
   __syncthreads();
@@ -836,6 +850,7 @@ __global__ void __launch_bounds__(1024) tile_order_block_kernel(const uint2* __r
 
 __global__ void __launch_bounds__(256) tile_order_count_kernel(const uint2* __restrict__ ranges, int64_t tiles,
                                                                uint32_t* __restrict__ cnt) {
+  pdl_entry();
   __shared__ uint32_t s_cnt[33];
   if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0u;
   __syncthreads();
@@ -849,6 +864,7 @@ __global__ void __launch_bounds__(256) tile_order_scatter_kernel(const uint2* __
                                                                  const uint32_t* __restrict__ cnt,
                                                                  uint32_t* __restrict__ cursor,
                                                                  uint32_t* __restrict__ order) {
+  pdl_entry();
   __shared__ uint32_t s_base[33];
   if (threadIdx.x == 0) {
     uint32_t run = 0;
@@ -871,10 +887,7 @@ cudaError_t launch_bin_phase2(const BinArgs& a, const int* run, long long keys_k
   const unsigned long long parts = (kn + kSortPart - 1) / kSortPart;
   cudaError_t e;
   int r = -1;  // buffer of kb/vb holding the sorted result, -1: no pass ran
-  if (parts > 0 && a.passes > 0) {
-    if ((e = cudaMemsetAsync(a.ws.lookback, 0, sizeof(unsigned long long) * 256 * a.passes * parts, st)) !=
-        cudaSuccess)
-      return e;
+  if (parts > 0 && a.passes > 0) {  // look-back words zeroed by phase 1
     uint32_t* const kb[2] = {a.ws.keys[1], a.ws.keys[0]};
     uint32_t* const vb[2] = {a.ws.vals[1], a.ws.vals[0]};
     const int ws_index[2] = {1, 0};  // kb[i] is ws.keys[ws_index[i]]
@@ -892,7 +905,8 @@ cudaError_t launch_bin_phase2(const BinArgs& a, const int* run, long long keys_k
   }
   // composite order of the tiles
   if (a.total_tiles <= kOrderOneBlock) {
-    tile_order_block_kernel<<<1, 1024, 0, st>>>(a.ws.ranges, a.total_tiles, a.ws.tile_order);
+    launch_pdl(tile_order_block_kernel, dim3(1), dim3(1024), 0, st, (const uint2*)a.ws.ranges, a.total_tiles,
+               a.ws.tile_order);
     count_launches(1);
   } else {
     uint32_t* counters = a.ws.tile_order + a.total_tiles;

@@ -29,6 +29,7 @@ enum WsSlot {
   WS_SCAN_PART,    // uint64_t[scan blocks + 1]
   WS_KEYS0, WS_KEYS1,  // uint32_t[cap] global tile ids, ping-pong
   WS_VALS0, WS_VALS1,  // uint32_t[cap] record indices, ping-pong
+  // WS_HIST .. WS_RANGES are cleared together every frame: keep them adjacent
   WS_HIST,         // uint32_t[2 * kMaxPasses][256] digit counts -> exclusive offsets (depth, tile)
   WS_LOOKBACK_D,   // uint64_t[parts(M)][kDepthPasses][256] look-back words of the depth sort
   WS_LOOKBACK,     // uint64_t[parts(cap)][tile passes][256] look-back words of the tile sort
@@ -39,6 +40,8 @@ enum WsSlot {
   WS_TILE_ORDER,   // uint32_t[tiles] composite order (longest key lists first) + uint32_t[2][64] counters
   WS_NUM_SLOTS
 };
+static_assert(WS_LOOKBACK_D == WS_HIST + 1 && WS_LOOKBACK == WS_HIST + 2 && WS_RANGES == WS_HIST + 3,
+              "the per-frame cleared slots must be adjacent");
 
 constexpr int kMaxPasses = 8;          // per sort: 8-bit digits of at most 64-bit keys
 constexpr int kDepthPasses = 4;        // 32-bit depth keys
@@ -109,6 +112,17 @@ constexpr float kAsA2 = -0.284496736f;
 constexpr float kAsA3 = 1.421413741f;
 constexpr float kAsA4 = -1.453152027f;
 constexpr float kAsA5 = 1.061405429f;
+
+// Programmatic dependent launch (sm_90+).  A kernel launched with
+// launch_pdl may be scheduled while its predecessor in the stream drains:
+// it waits here for the predecessor to complete (its memory included)
+// before anything else, so it may read and write what the predecessor did;
+// and it lets its own dependents be scheduled once all its blocks run.
+// Launched without the attribute, both instructions do nothing.
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;

@@ -84,6 +84,24 @@ struct DensifyArgs {     // densification
   uint32_t* block_sums;    // scratch [blocks][4]
 };
 
+// Launch with programmatic stream serialisation: the kernel (which calls
+// pdl_entry first) may be scheduled during its predecessor's last wave.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 cudaError_t launch_preprocess_fwd(const PreArgs& a, cudaStream_t st, int sms);
 cudaError_t launch_preprocess_bwd(const BwdArgs& a, cudaStream_t st, int sms);
 cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms);

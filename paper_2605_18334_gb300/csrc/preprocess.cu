@@ -283,6 +283,7 @@ __device__ __forceinline__ void load_attr(const sr_gaussians& g, int64_t i, bool
 
 // View table from the cameras (one thread); same layout rule as sr_plan_init.
 __global__ void view_table_kernel(const sr_camera* cams, int n_views, ViewInfo* views) {
+  pdl_entry();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   int64_t tb = 0, io = 0, po = 0;
   for (int v = 0; v < n_views; ++v) {
@@ -336,6 +337,7 @@ __device__ __forceinline__ void stage_sh(const void* sh, int64_t base, int cnt, 
 
 template <int DEG, int DT_SH>
 __global__ void __launch_bounds__(kPreThreads, 5) preprocess_fwd_kernel(PreArgs a) {
+  pdl_entry();
   constexpr int K = (DEG + 1) * (DEG + 1);
   constexpr int K3 = 3 * K, ROW = K3 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -513,6 +515,7 @@ __device__ __forceinline__ void skew_project_bwd(const Proj& P, const float* e, 
 
 template <int DEG, int DT_SH>
 __global__ void __launch_bounds__(kPreThreads, 4) preprocess_bwd_kernel(BwdArgs a) {
+  pdl_entry();
   constexpr int K = (DEG + 1) * (DEG + 1);
   constexpr int K3 = 3 * K, ROW = K3 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -731,7 +734,7 @@ static cudaError_t launch_sized(void (*fn)(Args), const Args& a, int grid, size_
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  fn<<<grid, kPreThreads, smem, st>>>(a);
+  launch_pdl(fn, dim3(grid), dim3(kPreThreads), smem, st, a);
   count_launches(1);
   return cudaGetLastError();
 }

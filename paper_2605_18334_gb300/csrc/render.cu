@@ -97,6 +97,7 @@ struct FwdMinBlocks {
 
 template <int MODE, int PX, bool REC, int BATCH>
 __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_kernel(RenderArgs a) {
+  pdl_entry();
   constexpr int NT = 256 / PX;
   __shared__ float4 s_r0[BATCH], s_r1[BATCH], s_r2[MODE == MODE_PLAIN ? 1 : BATCH], s_r3[BATCH];
   const int64_t tile = a.tile_order[blockIdx.x];
@@ -494,6 +495,7 @@ struct BwdPixels<MODE, PX, true> {
 
 template <int MODE, int PX, int BATCH>
 __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
+  pdl_entry();
   constexpr int NT = 256 / PX;
   __shared__ float4 s_r0[BATCH], s_r1[BATCH], s_r2[MODE == MODE_PLAIN ? 1 : BATCH], s_r3[BATCH];
   __shared__ uint32_t s_id[BATCH];
@@ -598,9 +600,9 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
 // ---------------------------------------------------------------------------
 template <int PX, bool REC, int BATCH>
 static void launch_fwd_px(const RenderArgs& a, int mode, unsigned grid, cudaStream_t st) {
-  if (mode == MODE_PLAIN) render_fwd_kernel<MODE_PLAIN, PX, REC, BATCH><<<grid, 256 / PX, 0, st>>>(a);
-  else if (mode == MODE_TWO) render_fwd_kernel<MODE_TWO, PX, REC, BATCH><<<grid, 256 / PX, 0, st>>>(a);
-  else render_fwd_kernel<MODE_SPLIT, PX, REC, BATCH><<<grid, 256 / PX, 0, st>>>(a);
+  if (mode == MODE_PLAIN) launch_pdl(render_fwd_kernel<MODE_PLAIN, PX, REC, BATCH>, dim3(grid), dim3(256 / PX), 0, st, a);
+  else if (mode == MODE_TWO) launch_pdl(render_fwd_kernel<MODE_TWO, PX, REC, BATCH>, dim3(grid), dim3(256 / PX), 0, st, a);
+  else launch_pdl(render_fwd_kernel<MODE_SPLIT, PX, REC, BATCH>, dim3(grid), dim3(256 / PX), 0, st, a);
 }
 
 template <bool REC, int BATCH>
@@ -623,9 +625,9 @@ static void launch_fwd_rec(const RenderArgs& a, int mode, unsigned grid, cudaStr
 
 template <int PX, int BATCH>
 static void launch_bwd_px(const RenderArgs& a, int mode, unsigned grid, cudaStream_t st) {
-  if (mode == MODE_PLAIN) render_bwd_kernel<MODE_PLAIN, PX, BATCH><<<grid, 256 / PX, 0, st>>>(a);
-  else if (mode == MODE_TWO) render_bwd_kernel<MODE_TWO, PX, BATCH><<<grid, 256 / PX, 0, st>>>(a);
-  else render_bwd_kernel<MODE_SPLIT, PX, BATCH><<<grid, 256 / PX, 0, st>>>(a);
+  if (mode == MODE_PLAIN) launch_pdl(render_bwd_kernel<MODE_PLAIN, PX, BATCH>, dim3(grid), dim3(256 / PX), 0, st, a);
+  else if (mode == MODE_TWO) launch_pdl(render_bwd_kernel<MODE_TWO, PX, BATCH>, dim3(grid), dim3(256 / PX), 0, st, a);
+  else launch_pdl(render_bwd_kernel<MODE_SPLIT, PX, BATCH>, dim3(grid), dim3(256 / PX), 0, st, a);
 }
 
 template <int BATCH>
