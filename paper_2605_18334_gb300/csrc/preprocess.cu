@@ -282,9 +282,7 @@ __device__ __forceinline__ void load_attr(const sr_gaussians& g, int64_t i, bool
 
 
 // View table from the cameras (one thread); same layout rule as sr_plan_init.
-__global__ void view_table_kernel(const sr_camera* cams, int n_views, ViewInfo* views) {
-  pdl_entry();
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ void write_view_table(const sr_camera* cams, int n_views, ViewInfo* views) {
   int64_t tb = 0, io = 0, po = 0;
   for (int v = 0; v < n_views; ++v) {
     ViewInfo vi;
@@ -301,6 +299,12 @@ __global__ void view_table_kernel(const sr_camera* cams, int n_views, ViewInfo* 
     io += 3 * (int64_t)vi.width * vi.height;
     po += (int64_t)vi.width * vi.height;
   }
+}
+
+// only for frames without Gaussians (the projection writes the table otherwise)
+__global__ void view_table_kernel(const sr_camera* cams, int n_views, ViewInfo* views) {
+  pdl_entry();
+  if (threadIdx.x == 0 && blockIdx.x == 0) write_view_table(cams, n_views, views);
 }
 
 // Block shape of the per-Gaussian kernels: 4 warps; each warp takes 32
@@ -345,6 +349,7 @@ __global__ void __launch_bounds__(kPreThreads, 5) preprocess_fwd_kernel(PreArgs 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* s_sh = reinterpret_cast<float*>(smem_raw + cams_bytes(a.n_views)) + warp * 32 * ROW;
   for (int v = threadIdx.x; v < a.n_views; v += blockDim.x) s_cams[v] = a.cams[v];
+  if (blockIdx.x == 0 && threadIdx.x == 0) write_view_table(a.cams, a.n_views, a.ws.views);
   __syncthreads();
   const int64_t n = a.g.n;
   const bool has_split = a.g.split_dir != nullptr;
@@ -751,10 +756,11 @@ static size_t sh_stage_bytes(int deg, int tiles_per_warp) {
 }
 
 cudaError_t launch_preprocess_fwd(const PreArgs& a, cudaStream_t st, int sms) {
-  view_table_kernel<<<1, 32, 0, st>>>(a.cams, a.n_views, a.ws.views);
-  count_launches(1);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || a.g.n == 0) return e;
+  if (a.g.n == 0) {
+    launch_pdl(view_table_kernel, dim3(1), dim3(32), 0, st, a.cams, a.n_views, a.ws.views);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   const int grid = grid_for(a.g.n, sms);
   const size_t smem = cams_bytes(a.n_views) + sh_stage_bytes(a.g.sh_degree, 1);
 #define SR_DEG_CASE(D)                                                                              \

@@ -127,6 +127,7 @@ __device__ __forceinline__ void block_sum2(float a, float b, float* s_red, float
 
 // moments, SSIM and the maps u, v, k of one channel of one tile
 __global__ void __launch_bounds__(256) ssim_fwd_kernel(LossArgs a) {
+  pdl_entry();
   __shared__ __align__(16) float2 s_xy[kHalo][kHp];    // (x, y) of the tile and its halo
   __shared__ __align__(16) float2 s_a[kTile][kHp];     // horizontal sums of (x, y), [column][row]
   __shared__ __align__(16) float2 s_b[kTile][kHp];     // ... of (x^2, y^2)
@@ -222,6 +223,7 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(LossArgs a) {
 
 // dL/dC = (w * u) + 2 x (w * v) + y (w * k) + (1 - lambda) sign(x - y) / N
 __global__ void __launch_bounds__(256) ssim_bwd_kernel(LossArgs a) {
+  pdl_entry();
   __shared__ __align__(16) float2 s_uv[kHalo][kHp];
   __shared__ __align__(16) float s_k[kHalo][kHp];
   __shared__ __align__(16) float2 s_a[kTile][kHp];  // horizontal sums of (u, v), [column][row]
@@ -303,6 +305,7 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(LossArgs a) {
 // loads of a thread in flight at a time, not one
 constexpr int kReduceThreads = 1024;
 __global__ void __launch_bounds__(kReduceThreads) loss_reduce_kernel(LossArgs a, int blocks) {
+  pdl_entry();
   __shared__ float s_red[2 * kReduceThreads / 32];
   float s = 0.0f, l = 0.0f;
   for (int i0 = threadIdx.x; i0 < blocks; i0 += 8 * kReduceThreads) {
@@ -363,6 +366,7 @@ __device__ __forceinline__ void adam_one(float& p, float g, float& m, float& v, 
 }
 
 __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
+  pdl_entry();
   const AdamGroupDev& G = a.grp[blockIdx.y];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -413,6 +417,7 @@ __global__ void __launch_bounds__(256) densify_stats_kernel(const float* __restr
                                                             const float* __restrict__ g_z, int64_t n,
                                                             float* __restrict__ uv_sum, int32_t* __restrict__ seen,
                                                             float* __restrict__ z_max) {
+  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float u = g_uv[i];
     if (u > 0.0f) {
@@ -462,9 +467,9 @@ cudaError_t launch_loss(const float* images, const float* targets, float lambda,
   a.total_values = 3 * total_pixels;
   a.lambda = lambda;
   const int64_t blocks = 3 * total_tiles;
-  ssim_fwd_kernel<<<(unsigned)blocks, 256, 0, st>>>(a);
-  ssim_bwd_kernel<<<(unsigned)blocks, 256, 0, st>>>(a);
-  loss_reduce_kernel<<<1, kReduceThreads, 0, st>>>(a, (int)blocks);
+  launch_pdl(ssim_fwd_kernel, dim3((unsigned)blocks), dim3(256), 0, st, a);
+  launch_pdl(ssim_bwd_kernel, dim3((unsigned)blocks), dim3(256), 0, st, a);
+  launch_pdl(loss_reduce_kernel, dim3(1), dim3(kReduceThreads), 0, st, a, (int)blocks);
   count_launches(3);
   return cudaGetLastError();
 }
@@ -495,7 +500,7 @@ cudaError_t launch_adam(const sr_adam_group* groups, int n_groups, int64_t step,
   a.inv_sqrt_bc2 = (float)(1.0 / std::sqrt(bc2));
   const int64_t want = (max_n / 4 + 255) / 256;
   const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
-  adam_kernel<<<dim3(gx, (unsigned)n_groups), 256, 0, st>>>(a);
+  launch_pdl(adam_kernel, dim3(gx, (unsigned)n_groups), dim3(256), 0, st, a);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -504,7 +509,7 @@ cudaError_t launch_densify_stats(const float* g_uv, const float* g_z, int64_t n,
                                  float* z_max, int sms, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8));
-  densify_stats_kernel<<<grid, 256, 0, st>>>(g_uv, g_z, n, uv_sum, seen, z_max);
+  launch_pdl(densify_stats_kernel, dim3(grid), dim3(256), 0, st, g_uv, g_z, n, uv_sum, seen, z_max);
   count_launches(1);
   return cudaGetLastError();
 }
