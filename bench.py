@@ -610,8 +610,7 @@ def e2e(args, sc, cam, up, dev, world):
     def compute(i):
         comp.wait_event(ev_in[i])
         comp.wait_event(ev_out[i])
-        r.forward(gbuf[i])
-        img_d[i].copy_(r.images, non_blocking=True)
+        r.forward(gbuf[i], out=img_d[i])
         gout[i] = r.backward(gbuf[i], dbuf[i], out=gout[i])
         ev_done[i].record(comp)
 

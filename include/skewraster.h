@@ -206,8 +206,9 @@ sr_status sr_preprocess(const sr_plan* plan, const sr_gaussians* g, const sr_cam
  * the key emission is done, stores the number of keys the frame needs and
  * returns SR_ERR_CAPACITY (nothing to render) if it exceeds
  * plan->key_capacity; the tile sort is queued behind the count's readback
- * (through a pinned host buffer) so the device does not idle meanwhile, and
- * where no pinned memory can be had the sort waits for the count and skips
+ * (a kernel writes it into mapped pinned host memory, so it never waits for
+ * the caller's own copies) and the device does not idle meanwhile; where no
+ * mapped pinned memory can be had the sort waits for the count and skips
  * radix passes whose digit is the same for every key.  If NULL, the call
  * never blocks (for CUDA-graph capture): every pass runs and an overflow is
  * reported through the status word (sr_read_status). */

@@ -252,16 +252,20 @@ static BinArgs bin_args(const sr_plan* p, const sr_config* cfg, void* ws) {
   return b;
 }
 
-// One pinned status buffer per host thread (portable across devices), for
-// the overlapped key-count readback; nullptr if pinned memory is unavailable.
+// One mapped pinned status buffer per host thread (portable across devices)
+// for the key-count readback: a kernel writes it (no copy engine, so the
+// readback never queues behind the caller's own large transfers); nullptr
+// if mapped pinned memory is unavailable.
 static Status* pinned_status() {
   thread_local Status* buf = nullptr;
   thread_local bool tried = false;
   if (!tried) {
     tried = true;
     void* p = nullptr;
-    if (cudaHostAlloc(&p, sizeof(Status), cudaHostAllocPortable) == cudaSuccess) buf = static_cast<Status*>(p);
-    else cudaGetLastError();
+    if (cudaHostAlloc(&p, sizeof(Status), cudaHostAllocPortable | cudaHostAllocMapped) == cudaSuccess)
+      buf = static_cast<Status*>(p);
+    else
+      cudaGetLastError();
   }
   return buf;
 }
@@ -277,17 +281,23 @@ sr_status sr_bin_sort(const sr_plan* p, const sr_config* cfg, void* ws, int64_t*
   int run[kMaxPasses];
   for (int k = 0; k < kMaxPasses; ++k) run[k] = 1;
   if (!keys_needed) return from_cuda(launch_bin_phase2(b, run, -1, st));
-  // Synchronous form.  With a pinned status buffer the key count is copied
-  // back while the tile passes (grids sized for the capacity; blocks past the
-  // device-side key count leave at once) are already queued behind it, so the
-  // GPU does not idle during the host round trip; the call still returns only
-  // once the count is known.  Without one, the passes wait for the count and
-  // are sized by it (trivial passes skipped).
+  // Synchronous form.  With a mapped pinned status buffer a one-block kernel
+  // writes the status into host memory while the tile passes (grids sized
+  // for the capacity; blocks past the device-side key count leave at once)
+  // are already queued behind it, so the GPU does not idle during the host
+  // round trip; the call still returns only once the count is known.
+  // Without one, the passes wait for the count and are sized by it (trivial
+  // passes skipped).
   Status* h = pinned_status();
+  Status* h_dev = nullptr;
+  if (h && cudaHostGetDevicePointer(reinterpret_cast<void**>(&h_dev), h, 0) != cudaSuccess) {
+    cudaGetLastError();
+    h_dev = nullptr;
+  }
   cudaEvent_t ev = nullptr;
-  if (h && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) ev = nullptr;
-  if (h && ev) {
-    const bool ok = cudaMemcpyAsync(h, b.ws.status, sizeof(Status), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+  if (h_dev && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) ev = nullptr;
+  if (h_dev && ev) {
+    const bool ok = launch_status_export(b.ws.status, h_dev, st) == cudaSuccess &&
                     cudaEventRecord(ev, st) == cudaSuccess && launch_bin_phase2(b, run, -1, st) == cudaSuccess &&
                     cudaEventSynchronize(ev) == cudaSuccess;
     cudaEventDestroy(ev);

@@ -444,10 +444,16 @@ __global__ void __launch_bounds__(256) histogram_kernel(const KEY* __restrict__ 
   for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&s_h[0][0])[i] = 0u;
   __syncthreads();
   const unsigned long long kn = element_count(count_dev, count);
-  for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < kn;
-       k += (unsigned long long)gridDim.x * blockDim.x) {
-    const unsigned long long key = keys[k];
-    for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p][(key >> (8 * p)) & 0xffu], 1u);
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  // four keys of a thread in flight at a time
+  for (unsigned long long k0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k0 < kn; k0 += 4 * stride) {
+    unsigned long long key[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) key[u] = k0 + u * stride < kn ? (unsigned long long)keys[k0 + u * stride] : 0ull;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (k0 + u * stride < kn)
+        for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p][(key[u] >> (8 * p)) & 0xffu], 1u);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
@@ -773,7 +779,8 @@ cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms) {
   const uint32_t* cnt_sorted = a.ws.dkey[0];
   if (m > 0) {
     // depth sort of the records (values: record indices)
-    launch_pdl(histogram_kernel<uint32_t>, dim3(clamp_grid((um + 255) / 256, sms, 4)), dim3(256), 0, st,
+    // one block per SM: each bin's count goes to global memory from few blocks
+    launch_pdl(histogram_kernel<uint32_t>, dim3(clamp_grid((um + 255) / 256, sms, 1)), dim3(256), 0, st,
                (const uint32_t*)a.ws.dkey[0], (const unsigned long long*)nullptr, um, (int)kDepthPasses, a.ws.hist);
     launch_pdl(hist_scan_kernel, dim3(kDepthPasses), dim3(256), 0, st, a.ws.hist, a.ws.status->pass_trivial,
                (const unsigned long long*)nullptr, um);
@@ -917,6 +924,25 @@ cudaError_t launch_bin_phase2(const BinArgs& a, const int* run, long long keys_k
                                                      a.ws.tile_order);
     count_launches(2);
   }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// The status word into mapped host memory (the synchronous key-count readback)
+// ---------------------------------------------------------------------------
+__global__ void status_export_kernel(const Status* __restrict__ src, Status* dst) {
+  pdl_entry();
+  constexpr int kWords = (int)(sizeof(Status) / sizeof(uint32_t));
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  for (int i = threadIdx.x; i < kWords; i += blockDim.x) d[i] = s[i];
+  __threadfence_system();
+}
+
+cudaError_t launch_status_export(const Status* src, Status* dst_mapped, cudaStream_t st) {
+  static_assert(sizeof(Status) % sizeof(uint32_t) == 0, "status word size");
+  launch_pdl(status_export_kernel, dim3(1), dim3(32), 0, st, src, dst_mapped);
+  count_launches(1);
   return cudaGetLastError();
 }
 

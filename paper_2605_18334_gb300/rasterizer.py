@@ -187,13 +187,19 @@ class Rasterizer:
     def bin_sort(self, stream=None, sync: bool = True):
         return N.sr_bin_sort(self.plan, self.cfg_c, self.ws.data_ptr(), _stream_ptr(stream), sync=sync)
 
-    def render_fwd(self, stream=None):
-        N.sr_render_fwd(self.plan, self.cfg_c, self.ws.data_ptr(), self.images.data_ptr(), self.t_final.data_ptr(),
+    def render_fwd(self, stream=None, out: torch.Tensor | None = None):
+        img = self.images if out is None else out
+        if out is not None and (out.dtype != torch.float32 or not out.is_contiguous() or
+                                out.numel() != self.images.numel() or out.device != self.images.device):
+            raise ValueError("out must be a contiguous float32 tensor shaped like the image buffer")
+        N.sr_render_fwd(self.plan, self.cfg_c, self.ws.data_ptr(), img.data_ptr(), self.t_final.data_ptr(),
                         self.n_contrib.data_ptr(), _stream_ptr(stream))
+        return img
 
-    def forward(self, g: Gaussians, stream=None, grow: bool = True) -> torch.Tensor:
+    def forward(self, g: Gaussians, stream=None, grow: bool = True, out: torch.Tensor | None = None) -> torch.Tensor:
         """Preprocess, bin and sort (growing the key capacity if the frame
-        needs more), composite.  Returns the flat image buffer."""
+        needs more), composite.  Returns the flat image buffer (``out`` if
+        given, else the rasterizer's own)."""
         self.preprocess(g, stream)
         try:
             self.keys = self.bin_sort(stream)
@@ -203,8 +209,7 @@ class Rasterizer:
             self._make_plan(int(e.keys_needed * 1.25) + 1024)
             self.preprocess(g, stream)
             self.keys = self.bin_sort(stream)
-        self.render_fwd(stream)
-        return self.images
+        return self.render_fwd(stream, out)
 
     def backward_composite(self, d_images: torch.Tensor, stream=None):
         """Reverse replay of the last forward (2D gradients stay in the workspace)."""
