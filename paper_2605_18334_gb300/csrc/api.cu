@@ -236,6 +236,7 @@ sr_status sr_preprocess(const sr_plan* p, const sr_gaussians* g, const sr_camera
   a.cfg = to_dev(*cfg);
   a.mode = p->render_mode;
   a.ws = ws_ptrs(*p, ws);
+  a.d2 = p->forward_only ? nullptr : reinterpret_cast<float4*>(a.ws.d2);
   return from_cuda(launch_preprocess_fwd(a, static_cast<cudaStream_t>(stream), device_sms()));
 }
 
@@ -363,7 +364,11 @@ sr_status sr_render_bwd_composite(const sr_plan* p, const sr_config* cfg, void* 
   if (p->forward_only) return SR_ERR_UNSUPPORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const Ws w = ws_ptrs(*p, ws);
-  cudaError_t e = cudaMemsetAsync(w.d2, 0, sizeof(float) * kD2Stride * (size_t)(p->n * p->n_views), st);
+  // the 2D-gradient records start at zero: the projection zeroed this
+  // frame's touched records unless a backward composite has used them since
+  // (a device-side test; the clear kernel then zeroes them all)
+  cudaError_t e = launch_d2_clear(w.status, reinterpret_cast<float4*>(w.d2),
+                                  (int64_t)kD2Stride / 4 * p->n * p->n_views, device_sms(), st);
   if (e != cudaSuccess) return SR_ERR_CUDA;
   RenderArgs r = render_args(p, cfg, ws);
   r.t_final = const_cast<float*>(t_final);

@@ -21,6 +21,7 @@
 // preceding partitions (each wait bounded), and scatters each digit's run
 // contiguously.
 #include <algorithm>
+#include <cstddef>
 #include <mutex>
 
 #include "kernels.cuh"
@@ -767,7 +768,7 @@ cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms) {
   // status word, histograms, look-back words of both sorts and ranges start
   // at zero every frame; the last four are consecutive workspace slots, so
   // one memset clears them all
-  if ((e = cudaMemsetAsync(a.ws.status, 0, sizeof(Status), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.ws.status, 0, offsetof(Status, d2_fresh), st)) != cudaSuccess) return e;
   {
     char* lo = reinterpret_cast<char*>(a.ws.hist);
     char* hi = reinterpret_cast<char*>(a.ws.ranges + a.total_tiles);

@@ -68,6 +68,11 @@ struct Status {
   uint32_t pad1;
   unsigned long long pairs_tested;    // render_fwd: (pixel, Gaussian) pairs evaluated
   unsigned long long pairs_blended;   // render_fwd: pairs composited
+  // last, kept across bin_sort's per-frame clear: 1 once the projection has
+  // zeroed this frame's 2D-gradient records and no backward composite has
+  // added into them since
+  uint32_t d2_fresh;
+  uint32_t pad2;
 };
 
 // host-side launch counter (diagnostics; defined in api.cu)

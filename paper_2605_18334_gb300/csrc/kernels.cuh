@@ -12,6 +12,7 @@ struct PreArgs {        // preprocess forward
   CfgDev cfg;
   int mode;             // RenderMode
   Ws ws;
+  float4* d2;           // 2D-gradient records to zero for touched records (null: forward-only plan)
 };
 
 struct BwdArgs {        // preprocess backward
@@ -110,6 +111,7 @@ cudaError_t launch_bin_phase2(const BinArgs& a, const int* run, long long keys_k
 cudaError_t launch_selftest_bounded_wait(const Ws& ws, unsigned long long cap, int spin_limit, cudaStream_t st);
 cudaError_t launch_render_fwd(const RenderArgs& a, int mode, int64_t total_tiles, cudaStream_t st);
 cudaError_t launch_render_bwd(const RenderArgs& a, int mode, int64_t total_tiles, cudaStream_t st);
+cudaError_t launch_d2_clear(Status* status, float4* d2, int64_t n4, int sms, cudaStream_t st);
 size_t loss_scratch_bytes(int64_t total_pixels, int64_t total_tiles);
 cudaError_t launch_loss(const float* images, const float* targets, float lambda, float* d_images, float* loss,
                         float* ssim_l1, void* scratch, const ViewInfo* views, int n_views, int64_t total_tiles,

@@ -349,7 +349,10 @@ __global__ void __launch_bounds__(kPreThreads, 5) preprocess_fwd_kernel(PreArgs 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* s_sh = reinterpret_cast<float*>(smem_raw + cams_bytes(a.n_views)) + warp * 32 * ROW;
   for (int v = threadIdx.x; v < a.n_views; v += blockDim.x) s_cams[v] = a.cams[v];
-  if (blockIdx.x == 0 && threadIdx.x == 0) write_view_table(a.cams, a.n_views, a.ws.views);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    write_view_table(a.cams, a.n_views, a.ws.views);
+    a.ws.status->d2_fresh = a.d2 ? 1u : 0u;
+  }
   __syncthreads();
   const int64_t n = a.g.n;
   const bool has_split = a.g.split_dir != nullptr;
@@ -475,6 +478,10 @@ __global__ void __launch_bounds__(kPreThreads, 5) preprocess_fwd_kernel(PreArgs 
           r[1] = make_float4(-0.5f * kLog2e * P.c, P.beta[0] * kInvSqrt2, P.beta[1] * kInvSqrt2, m_);
           r[2] = make_float4(h_, (P.beta[0] + P.ud[0]) * kInvSqrt2, (P.beta[1] + P.ud[1]) * kInvSqrt2, 0.0f);
           r[3] = make_float4(rgb[0], rgb[1], rgb[2], thr);
+          if (a.d2) {  // the record's 2D gradients start at zero for the backward
+            float4* z = a.d2 + 4 * m;
+            z[0] = z[1] = z[2] = z[3] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          }
         }
       }
       a.ws.ntouch[m] = ntouch;

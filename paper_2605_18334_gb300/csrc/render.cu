@@ -20,6 +20,8 @@
 // then sums its lanes with a transposing butterfly, warps add into padded
 // shared-memory accumulators, and each block issues one set of vector atomics
 // per Gaussian per batch.
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace sr {
@@ -493,9 +495,28 @@ struct BwdPixels<MODE, PX, true> {
   }
 };
 
+// Zero the 2D-gradient records unless the projection zeroed this frame's
+// touched records and no backward composite has used them since (the
+// backward composite that follows marks them used).
+__global__ void __launch_bounds__(256) d2_clear_kernel(Status* status, float4* d2, int64_t n4) {
+  pdl_entry();
+  if (status->d2_fresh) return;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x)
+    d2[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+cudaError_t launch_d2_clear(Status* status, float4* d2, int64_t n4, int sms, cudaStream_t st) {
+  const int64_t want = (n4 + 255) / 256;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
+  launch_pdl(d2_clear_kernel, dim3(grid), dim3(256), 0, st, status, d2, n4);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 template <int MODE, int PX, int BATCH>
 __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
   pdl_entry();
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.status->d2_fresh = 0u;  // read by the next d2_clear_kernel only
   constexpr int NT = 256 / PX;
   __shared__ float4 s_r0[BATCH], s_r1[BATCH], s_r2[MODE == MODE_PLAIN ? 1 : BATCH], s_r3[BATCH];
   __shared__ uint32_t s_id[BATCH];

@@ -501,3 +501,24 @@ def test_composite_order_over_many_tiles():
     for v in range(len(cams)):
         pix = np.stack([rng.integers(0, 1920, 300), rng.integers(0, 1080, 300)], 1).astype(np.int32)
         check_view(r, sc, cams, v, Config(), pixels=pix)
+
+
+def test_repeated_backward_calls_restart_from_zero():
+    """The 2D-gradient records are zeroed by the projection for its frame and
+    again by the backward itself when a backward composite has used them
+    since: a second backward after one forward, a composite-only call
+    followed by a full backward, and a re-render without a new projection
+    all give the first backward's gradients."""
+    sc = scenes.cluster(seed=35, n=3000, sh_degree=1)
+    cams = [scenes.identity_camera(96, 72)]
+    r, g = gpu_forward(sc, cams)
+    up = torch.as_tensor(scenes.upstream_grad(35, 72, 96)).cuda().reshape(-1).contiguous()
+    ref = {k: v.clone() for k, v in r.backward(g, up).items() if v is not None}
+    again = r.backward(g, up)
+    r.backward_composite(up)
+    after_composite = r.backward(g, up)
+    r.render_fwd()  # same frame rendered again, no new projection
+    rerender = r.backward(g, up)
+    for got in (again, after_composite, rerender):
+        for k in ("means", "skew", "sh", "opacity_logits"):
+            assert rel_err(got[k].cpu().numpy(), ref[k].cpu().numpy()) < 1e-5, k
