@@ -293,7 +293,7 @@ def run_ours(args):
     # DRAM bytes per launch (read + write) of the dominant kernel from the ncu
     # capture summarised in profiles/kernels_full_unbounded_1m_1080p.md, for
     # the launch shape it was taken in (None for any other shape or workload)
-    ncu_traffic = {("render_bwd_composite", 2, 256): 96.47e6}
+    ncu_traffic = {("render_bwd_composite", 2, 128): 96.99e6, ("render_bwd_composite", 2, 256): 96.73e6}
     traffic = None
     if args.n == 1_000_000:
         shape = ((tune["bwd_pixels_per_thread"], r.config.bwd_batch or 256) if dom == 3 else
