@@ -289,6 +289,65 @@ def _comp_indep(z, cam, s_dil, log_s=math.log(0.5)):
     return ind["comp"]
 
 
+# ---------------------------------------------------------------------------
+# Enhanced opacity (the alpha equation with two opacities and a split direction)
+# ---------------------------------------------------------------------------
+
+def test_enhanced_opacity_equal_logits_is_one_opacity():
+    """alpha_1 = alpha_2 makes h = 0: the image equals the one-opacity image,
+    whatever the split direction."""
+    sc = scenes.cluster(seed=71, n=300, sh_degree=1, two_opacities=True, split=True)
+    sc.opacity_logits[:, 1] = sc.opacity_logits[:, 0]
+    one = scenes.Scene(sc.means, sc.log_scales, sc.quats, np.ascontiguousarray(sc.opacity_logits[:, 0]), sc.skew,
+                       sc.sh, sc.sh_degree, None)
+    cam = oracle.camera_from_gl(scenes.identity_camera(48, 40))
+    cfg = oracle.config()
+    a, b = oracle.render(sc, cam, cfg), oracle.render(one, cam, cfg)
+    np.testing.assert_allclose(a["rgb"], b["rgb"], rtol=0, atol=1e-13)
+
+
+def test_enhanced_opacity_split_direction_and_limits():
+    """With zero skew the projected split direction is the skew projection of
+    d itself, u_2 = Sigma_d^-1 delta_2(d) / sqrt(1 - delta_2^T Sigma_d^-1 delta_2)
+    with delta_2(d) = A R S d / sqrt(1 + |d|^2) (computed here independently),
+    and the opacity factor m + h erf(u_2^T delta / sqrt 2) tends to comp
+    sigmoid(l_1) far along +u_2 and comp sigmoid(l_2) far along -u_2: the
+    ratio alpha(delta) / alpha(-delta) (equal kernels, zero skew) approaches
+    sigmoid(l_1) / sigmoid(l_2), and is 1 across u_2."""
+    cam = oracle.camera_from_gl(scenes.identity_camera(257, 257))
+    cfg = oracle.config()
+    mu, log_s, q = [0.0, 0.0, 5.0], np.log([0.4, 0.3, 0.2]), [0.9, 0.2, -0.1, 0.3]
+    d = np.array([1.5, -0.7, 0.4])
+    l1, l2 = 2.0, -1.0
+    sc = one_gaussian_scene(mu, log_s, q, [0.0, 0.0, 0.0], logit=l1, logit2=l2, split=d)
+    rec = oracle.preprocess(sc, cam, cfg)["rec"][0]
+    W2C, f = cam_arrays(cam)
+    ind = independent_projection(np.array(mu), log_s, np.array(q), np.zeros(3), W2C, f)
+    d2 = ind["A"] @ ind["R"] @ ind["S"] @ (d / math.sqrt(1.0 + d @ d))
+    Si = np.linalg.inv(ind["Sd"])
+    u = Si @ d2 / math.sqrt(1.0 - d2 @ Si @ d2)
+    np.testing.assert_allclose(rec[9:11], u, rtol=1e-6)
+    assert rec[5] == 0.0 and rec[6] == 0.0
+    assert np.allclose(rec[0:2], [128.5, 128.5])  # the centre is the centre of pixel (128, 128)
+    pc = np.array([128, 128])
+    s1, s2 = 1 / (1 + math.exp(-l1)), 1 / (1 + math.exp(-l2))
+    # o(e) + o(-e) = 2 m = comp (s1 + s2) for any offset e, with the independent Sigma_d and comp
+    rng = np.random.default_rng(3)
+    offs = rng.integers(-20, 21, size=(64, 2))
+    al_p = oracle.alpha_at(rec, (pc + offs).astype(np.int32))
+    al_n = oracle.alpha_at(rec, (pc - offs).astype(np.int32))
+    G = np.exp(-0.5 * np.einsum("ni,ij,nj->n", offs, Si, offs))
+    np.testing.assert_allclose(al_p + al_n, ind["comp"] * (s1 + s2) * G, rtol=1e-6, atol=1e-300)
+    # far along +u_2 / -u_2 the ratio tends to s1 / s2
+    ud = u / np.linalg.norm(u)
+    errs = []
+    for t in (2.0, 4.0, 6.0):  # u^T e / sqrt 2 = t
+        off = np.round(t * math.sqrt(2.0) / np.linalg.norm(u) * ud)
+        al = oracle.alpha_at(rec, np.array([pc + off, pc - off]).astype(np.int32))
+        errs.append(abs(al[0] / al[1] / (s1 / s2) - 1.0))
+    assert errs[-1] < 1e-3 and errs[0] > errs[-1]
+
+
 def test_compositing_closed_form_at_splat_centres():
     """Splats on the optical axis of a 65x65 view land exactly on the centre of
     pixel (32, 32), where delta = 0: alpha = min(alpha_max, comp sigmoid(l))
