@@ -52,7 +52,7 @@ extern "C" {
 #endif
 
 #define SR_MAX_VIEWS 256
-#define SR_ABI_VERSION 1
+#define SR_ABI_VERSION 2
 
 typedef enum sr_status {
   SR_OK = 0,
@@ -156,7 +156,7 @@ typedef struct sr_plan {
   int64_t pixel_offset[SR_MAX_VIEWS + 1]; /* element offset of view v's [H][W] state */
   int32_t width[SR_MAX_VIEWS], height[SR_MAX_VIEWS];
   size_t ws_bytes;            /* workspace size to allocate (256-byte aligned base) */
-  size_t off[24];             /* internal offsets into the workspace */
+  size_t off[32];             /* internal offsets into the workspace */
 } sr_plan;
 
 /* Version of this ABI (SR_ABI_VERSION). */

@@ -205,6 +205,7 @@ sr_status sr_plan_init(sr_plan* p, const sr_config* cfg, const sr_gaussians* g, 
   sizes[WS_FOOT] = sizeof(float4) * 4 * (size_t)m;
   sizes[WS_MASK] = p->forward_only ? 0 : sizeof(uint32_t) * 256 * (size_t)(key_capacity / 32 + tb + 1);
   sizes[WS_TILE_ORDER] = sizeof(uint32_t) * ((size_t)tb + 128);
+  sizes[WS_SHJAC] = p->forward_only ? 0 : sizeof(float4) * 3 * (size_t)m;
   size_t off = 0;
   for (int k = 0; k < WS_NUM_SLOTS; ++k) {
     p->off[k] = off;

@@ -38,6 +38,7 @@ enum WsSlot {
   WS_FOOT,         // float4[M][4] footprint constants or packed row spans (row_tile_span)
   WS_MASK,         // uint32_t[(cap/32 + tiles + 1) * 256] per-pixel blend masks (see render.cu)
   WS_TILE_ORDER,   // uint32_t[tiles] composite order (longest key lists first) + uint32_t[2][64] counters
+  WS_SHJAC,        // float4[M][3] d colour / d view direction (3x3) and the colour clamp bits (backward only)
   WS_NUM_SLOTS
 };
 static_assert(WS_LOOKBACK_D == WS_HIST + 1 && WS_LOOKBACK == WS_HIST + 2 && WS_RANGES == WS_HIST + 3,
@@ -474,6 +475,7 @@ struct Ws {
   float4* foot;
   uint32_t* mask;   // null when the plan is forward-only
   uint32_t* tile_order;
+  float4* shjac;    // null when the plan is forward-only
 };
 
 inline Ws ws_ptrs(const sr_plan& p, void* base) {
@@ -504,6 +506,7 @@ inline Ws ws_ptrs(const sr_plan& p, void* base) {
   w.foot = reinterpret_cast<float4*>(at(WS_FOOT));
   w.mask = p.forward_only ? nullptr : reinterpret_cast<uint32_t*>(at(WS_MASK));
   w.tile_order = reinterpret_cast<uint32_t*>(at(WS_TILE_ORDER));
+  w.shjac = p.forward_only ? nullptr : reinterpret_cast<float4*>(at(WS_SHJAC));
   return w;
 }
 

@@ -62,46 +62,48 @@ __device__ __forceinline__ void sh_eval(float x, float y, float z, float* Y) {
 }
 
 // d/d(x,y,z) of sum_k gY[k] Y_k, the polynomials above.
-template <int DEG>
-__device__ __forceinline__ void sh_grad(float x, float y, float z, const float* gY, float* gd) {
+// gY[k] at gYs[k * S] (S = 3: one colour channel of an [K][3] SH array)
+template <int DEG, int S = 1>
+__device__ __forceinline__ void sh_grad(float x, float y, float z, const float* gYs, float* gd) {
+  const auto gY = [&](int k) { return gYs[k * S]; };
   gd[0] = gd[1] = gd[2] = 0.0f;
   if (DEG < 1) return;
-  gd[1] += -kSH1 * gY[1];
-  gd[2] += kSH1 * gY[2];
-  gd[0] += -kSH1 * gY[3];
+  gd[1] += -kSH1 * gY(1);
+  gd[2] += kSH1 * gY(2);
+  gd[0] += -kSH1 * gY(3);
   if (DEG < 2) return;
   const float xx = x * x, yy = y * y, zz = z * z;
-  gd[0] += kSH2a * y * gY[4];
-  gd[1] += kSH2a * x * gY[4];
-  gd[1] += -kSH2a * z * gY[5];
-  gd[2] += -kSH2a * y * gY[5];
-  gd[0] += -2.0f * kSH2b * x * gY[6];
-  gd[1] += -2.0f * kSH2b * y * gY[6];
-  gd[2] += 4.0f * kSH2b * z * gY[6];
-  gd[0] += -kSH2a * z * gY[7];
-  gd[2] += -kSH2a * x * gY[7];
-  gd[0] += 2.0f * kSH2c * x * gY[8];
-  gd[1] += -2.0f * kSH2c * y * gY[8];
+  gd[0] += kSH2a * y * gY(4);
+  gd[1] += kSH2a * x * gY(4);
+  gd[1] += -kSH2a * z * gY(5);
+  gd[2] += -kSH2a * y * gY(5);
+  gd[0] += -2.0f * kSH2b * x * gY(6);
+  gd[1] += -2.0f * kSH2b * y * gY(6);
+  gd[2] += 4.0f * kSH2b * z * gY(6);
+  gd[0] += -kSH2a * z * gY(7);
+  gd[2] += -kSH2a * x * gY(7);
+  gd[0] += 2.0f * kSH2c * x * gY(8);
+  gd[1] += -2.0f * kSH2c * y * gY(8);
   if (DEG < 3) return;
-  gd[0] += -6.0f * kSH3a * x * y * gY[9];
-  gd[1] += -kSH3a * (3.0f * xx - 3.0f * yy) * gY[9];
-  gd[0] += kSH3b * y * z * gY[10];
-  gd[1] += kSH3b * x * z * gY[10];
-  gd[2] += kSH3b * x * y * gY[10];
-  gd[0] += 2.0f * kSH3c * x * y * gY[11];
-  gd[1] += -kSH3c * (4.0f * zz - xx - 3.0f * yy) * gY[11];
-  gd[2] += -8.0f * kSH3c * y * z * gY[11];
-  gd[0] += -6.0f * kSH3d * x * z * gY[12];
-  gd[1] += -6.0f * kSH3d * y * z * gY[12];
-  gd[2] += kSH3d * (6.0f * zz - 3.0f * xx - 3.0f * yy) * gY[12];
-  gd[0] += -kSH3c * (4.0f * zz - 3.0f * xx - yy) * gY[13];
-  gd[1] += 2.0f * kSH3c * x * y * gY[13];
-  gd[2] += -8.0f * kSH3c * x * z * gY[13];
-  gd[0] += 2.0f * kSH3e * x * z * gY[14];
-  gd[1] += -2.0f * kSH3e * y * z * gY[14];
-  gd[2] += kSH3e * (xx - yy) * gY[14];
-  gd[0] += -kSH3a * (3.0f * xx - 3.0f * yy) * gY[15];
-  gd[1] += 6.0f * kSH3a * x * y * gY[15];
+  gd[0] += -6.0f * kSH3a * x * y * gY(9);
+  gd[1] += -kSH3a * (3.0f * xx - 3.0f * yy) * gY(9);
+  gd[0] += kSH3b * y * z * gY(10);
+  gd[1] += kSH3b * x * z * gY(10);
+  gd[2] += kSH3b * x * y * gY(10);
+  gd[0] += 2.0f * kSH3c * x * y * gY(11);
+  gd[1] += -kSH3c * (4.0f * zz - xx - 3.0f * yy) * gY(11);
+  gd[2] += -8.0f * kSH3c * y * z * gY(11);
+  gd[0] += -6.0f * kSH3d * x * z * gY(12);
+  gd[1] += -6.0f * kSH3d * y * z * gY(12);
+  gd[2] += kSH3d * (6.0f * zz - 3.0f * xx - 3.0f * yy) * gY(12);
+  gd[0] += -kSH3c * (4.0f * zz - 3.0f * xx - yy) * gY(13);
+  gd[1] += 2.0f * kSH3c * x * y * gY(13);
+  gd[2] += -8.0f * kSH3c * x * z * gY(13);
+  gd[0] += 2.0f * kSH3e * x * z * gY(14);
+  gd[1] += -2.0f * kSH3e * y * z * gY(14);
+  gd[2] += kSH3e * (xx - yy) * gY(14);
+  gd[0] += -kSH3a * (3.0f * xx - 3.0f * yy) * gY(15);
+  gd[1] += 6.0f * kSH3a * x * y * gY(15);
 }
 
 struct Attr {
@@ -461,12 +463,25 @@ __global__ void __launch_bounds__(kPreThreads, 5) preprocess_fwd_kernel(PreArgs 
           float Y[16];
           sh_eval<DEG>(P.dir[0], P.dir[1], P.dir[2], Y);
           float rgb[3];
+          uint32_t clamped = 0u;
 #pragma unroll
           for (int ch = 0; ch < 3; ++ch) {
             float acc = 0.5f;
 #pragma unroll
             for (int k = 0; k < K; ++k) acc += Y[k] * sh[3 * k + ch];
             rgb[ch] = fmaxf(acc, 0.0f);
+            clamped |= (acc < 0.0f ? 1u : 0u) << ch;
+          }
+          if (a.ws.shjac) {
+            // per channel: d colour / d direction (the backward's view-direction
+            // term, so it need not read the SH coefficients) and the clamp flag
+            float4* jp = a.ws.shjac + 3 * m;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+              float J[3];
+              sh_grad<DEG, 3>(P.dir[0], P.dir[1], P.dir[2], sh + ch, J);
+              jp[ch] = make_float4(J[0], J[1], J[2], (clamped >> ch) & 1u ? 1.0f : 0.0f);
+            }
           }
           const float m_ = P.comp * (P.o1 + P.o2) * 0.5f;
           const float h_ = P.comp * (P.o1 - P.o2) * 0.5f;
@@ -533,8 +548,7 @@ __global__ void __launch_bounds__(kPreThreads, 4) preprocess_bwd_kernel(BwdArgs 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   sr_camera* s_cams = reinterpret_cast<sr_camera*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* s_sh = reinterpret_cast<float*>(smem_raw + cams_bytes(a.n_views)) + warp * 64 * ROW;
-  float* s_gsh = s_sh + 32 * ROW;
+  float* s_gsh = reinterpret_cast<float*>(smem_raw + cams_bytes(a.n_views)) + warp * 32 * ROW;
   for (int v = threadIdx.x; v < a.n_views; v += blockDim.x) s_cams[v] = a.cams[v];
   __syncthreads();
   const int64_t n = a.g.n;
@@ -543,9 +557,7 @@ __global__ void __launch_bounds__(kPreThreads, 4) preprocess_bwd_kernel(BwdArgs 
   for (int64_t base = ((int64_t)blockIdx.x * kPreWarps + warp) * 32; base < n;
        base += (int64_t)gridDim.x * kPreWarps * 32) {
     const int cnt = (int)(n - base < 32 ? n - base : 32);
-    stage_sh<K3, DT_SH>(a.g.sh, base, cnt, s_sh, lane);
     float* gsh = s_gsh + lane * ROW;
-    const float* sh = s_sh + lane * ROW;
 #pragma unroll
     for (int k = 0; k < K3; ++k) gsh[k] = 0.0f;
     __syncwarp();
@@ -572,26 +584,23 @@ __global__ void __launch_bounds__(kPreThreads, 4) preprocess_bwd_kernel(BwdArgs 
       g_abs += sqrtf(gd[G_MX] * gd[G_MX] + gd[G_MY] * gd[G_MY]);
       float gmu_v[3];  // this view's dL/dmu
 
-      // colour -> SH coefficients and view direction
+      // colour -> SH coefficients and view direction: with the forward's
+      // d colour / d direction J and clamp bits, the SH coefficients
+      // themselves are not needed (d colour / d coefficient is Y)
       float Y[16];
       sh_eval<DEG>(P.dir[0], P.dir[1], P.dir[2], Y);
-      float gY[16];
-#pragma unroll
-      for (int k = 0; k < K; ++k) gY[k] = 0.0f;
+      const float4* jp = a.ws.shjac + 3 * m;
+      float gdir[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
-        float acc = 0.5f;
+        const float4 J = jp[ch];  // d colour_ch / d direction, clamp flag
+        const float gc_ = J.w != 0.0f ? 0.0f : gd[G_R + ch];
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc += Y[k] * sh[3 * k + ch];
-        const float gc_ = acc < 0.0f ? 0.0f : gd[G_R + ch];
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          gsh[3 * k + ch] += Y[k] * gc_;
-          gY[k] += sh[3 * k + ch] * gc_;
-        }
+        for (int k = 0; k < K; ++k) gsh[3 * k + ch] += Y[k] * gc_;
+        gdir[0] += gc_ * J.x;
+        gdir[1] += gc_ * J.y;
+        gdir[2] += gc_ * J.z;
       }
-      float gdir[3];
-      sh_grad<DEG>(P.dir[0], P.dir[1], P.dir[2], gY, gdir);
       {
         const float dd = P.dir[0] * gdir[0] + P.dir[1] * gdir[1] + P.dir[2] * gdir[2];
         const float il = 1.0f / P.dlen;
@@ -788,7 +797,7 @@ cudaError_t launch_preprocess_fwd(const PreArgs& a, cudaStream_t st, int sms) {
 cudaError_t launch_preprocess_bwd(const BwdArgs& a, cudaStream_t st, int sms) {
   if (a.g.n == 0) return cudaSuccess;
   const int grid = grid_for(a.g.n, sms);
-  const size_t smem = cams_bytes(a.n_views) + sh_stage_bytes(a.g.sh_degree, 2);
+  const size_t smem = cams_bytes(a.n_views) + sh_stage_bytes(a.g.sh_degree, 1);
 #define SR_DEG_CASE(D)                                                                              \
   case D:                                                                                           \
     if (a.g.dt_sh == SR_F32) return launch_sized(preprocess_bwd_kernel<D, SR_F32>, a, grid, smem, st);   \

@@ -14,7 +14,7 @@ import threading
 from . import build as _build
 
 SR_MAX_VIEWS = 256
-SR_ABI_VERSION = 1
+SR_ABI_VERSION = 2
 
 SR_OK, SR_ERR_INVALID, SR_ERR_CAPACITY, SR_ERR_CUDA, SR_ERR_TIMEOUT, SR_ERR_UNSUPPORTED = range(6)
 SR_F32, SR_BF16, SR_F16 = 0, 1, 2
@@ -77,7 +77,7 @@ class sr_plan(C.Structure):
                 ("key_capacity", C.c_int64), ("total_tiles", C.c_int64), ("total_pixels", C.c_int64),
                 ("tile_base", C.c_int64 * (SR_MAX_VIEWS + 1)), ("image_offset", C.c_int64 * (SR_MAX_VIEWS + 1)),
                 ("pixel_offset", C.c_int64 * (SR_MAX_VIEWS + 1)), ("width", C.c_int32 * SR_MAX_VIEWS),
-                ("height", C.c_int32 * SR_MAX_VIEWS), ("ws_bytes", C.c_size_t), ("off", C.c_size_t * 24)]
+                ("height", C.c_int32 * SR_MAX_VIEWS), ("ws_bytes", C.c_size_t), ("off", C.c_size_t * 32)]
 
 
 class SkewRasterError(RuntimeError):
