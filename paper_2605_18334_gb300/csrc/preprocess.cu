@@ -62,49 +62,52 @@ __device__ __forceinline__ void sh_eval(float x, float y, float z, float* Y) {
 }
 
 // d/d(x,y,z) of sum_k gY[k] Y_k, the polynomials above.
-// gY[k] at gYs[k * S] (S = 3: one colour channel of an [K][3] SH array)
-template <int DEG, int S = 1>
-__device__ __forceinline__ void sh_grad(float x, float y, float z, const float* gYs, float* gd) {
-  const auto gY = [&](int k) { return gYs[k * S]; };
-  gd[0] = gd[1] = gd[2] = 0.0f;
+// d colour / d direction of all three channels at once: J[ch][d] = sum_k
+// sh[3 k + ch] dY_k / d dir_d (sh_grad with the three channels sharing the
+// basis derivatives)
+template <int DEG>
+__device__ __forceinline__ void sh_grad3(float x, float y, float z, const float* sh, float (&J)[3][3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) J[c][0] = J[c][1] = J[c][2] = 0.0f;
   if (DEG < 1) return;
-  gd[1] += -kSH1 * gY(1);
-  gd[2] += kSH1 * gY(2);
-  gd[0] += -kSH1 * gY(3);
+  { const float e = -kSH1; J[0][1] += e * sh[3]; J[1][1] += e * sh[4]; J[2][1] += e * sh[5]; }
+  { const float e = kSH1; J[0][2] += e * sh[6]; J[1][2] += e * sh[7]; J[2][2] += e * sh[8]; }
+  { const float e = -kSH1; J[0][0] += e * sh[9]; J[1][0] += e * sh[10]; J[2][0] += e * sh[11]; }
   if (DEG < 2) return;
   const float xx = x * x, yy = y * y, zz = z * z;
-  gd[0] += kSH2a * y * gY(4);
-  gd[1] += kSH2a * x * gY(4);
-  gd[1] += -kSH2a * z * gY(5);
-  gd[2] += -kSH2a * y * gY(5);
-  gd[0] += -2.0f * kSH2b * x * gY(6);
-  gd[1] += -2.0f * kSH2b * y * gY(6);
-  gd[2] += 4.0f * kSH2b * z * gY(6);
-  gd[0] += -kSH2a * z * gY(7);
-  gd[2] += -kSH2a * x * gY(7);
-  gd[0] += 2.0f * kSH2c * x * gY(8);
-  gd[1] += -2.0f * kSH2c * y * gY(8);
+  { const float e = kSH2a * y; J[0][0] += e * sh[12]; J[1][0] += e * sh[13]; J[2][0] += e * sh[14]; }
+  { const float e = kSH2a * x; J[0][1] += e * sh[12]; J[1][1] += e * sh[13]; J[2][1] += e * sh[14]; }
+  { const float e = -kSH2a * z; J[0][1] += e * sh[15]; J[1][1] += e * sh[16]; J[2][1] += e * sh[17]; }
+  { const float e = -kSH2a * y; J[0][2] += e * sh[15]; J[1][2] += e * sh[16]; J[2][2] += e * sh[17]; }
+  { const float e = -2.0f * kSH2b * x; J[0][0] += e * sh[18]; J[1][0] += e * sh[19]; J[2][0] += e * sh[20]; }
+  { const float e = -2.0f * kSH2b * y; J[0][1] += e * sh[18]; J[1][1] += e * sh[19]; J[2][1] += e * sh[20]; }
+  { const float e = 4.0f * kSH2b * z; J[0][2] += e * sh[18]; J[1][2] += e * sh[19]; J[2][2] += e * sh[20]; }
+  { const float e = -kSH2a * z; J[0][0] += e * sh[21]; J[1][0] += e * sh[22]; J[2][0] += e * sh[23]; }
+  { const float e = -kSH2a * x; J[0][2] += e * sh[21]; J[1][2] += e * sh[22]; J[2][2] += e * sh[23]; }
+  { const float e = 2.0f * kSH2c * x; J[0][0] += e * sh[24]; J[1][0] += e * sh[25]; J[2][0] += e * sh[26]; }
+  { const float e = -2.0f * kSH2c * y; J[0][1] += e * sh[24]; J[1][1] += e * sh[25]; J[2][1] += e * sh[26]; }
   if (DEG < 3) return;
-  gd[0] += -6.0f * kSH3a * x * y * gY(9);
-  gd[1] += -kSH3a * (3.0f * xx - 3.0f * yy) * gY(9);
-  gd[0] += kSH3b * y * z * gY(10);
-  gd[1] += kSH3b * x * z * gY(10);
-  gd[2] += kSH3b * x * y * gY(10);
-  gd[0] += 2.0f * kSH3c * x * y * gY(11);
-  gd[1] += -kSH3c * (4.0f * zz - xx - 3.0f * yy) * gY(11);
-  gd[2] += -8.0f * kSH3c * y * z * gY(11);
-  gd[0] += -6.0f * kSH3d * x * z * gY(12);
-  gd[1] += -6.0f * kSH3d * y * z * gY(12);
-  gd[2] += kSH3d * (6.0f * zz - 3.0f * xx - 3.0f * yy) * gY(12);
-  gd[0] += -kSH3c * (4.0f * zz - 3.0f * xx - yy) * gY(13);
-  gd[1] += 2.0f * kSH3c * x * y * gY(13);
-  gd[2] += -8.0f * kSH3c * x * z * gY(13);
-  gd[0] += 2.0f * kSH3e * x * z * gY(14);
-  gd[1] += -2.0f * kSH3e * y * z * gY(14);
-  gd[2] += kSH3e * (xx - yy) * gY(14);
-  gd[0] += -kSH3a * (3.0f * xx - 3.0f * yy) * gY(15);
-  gd[1] += 6.0f * kSH3a * x * y * gY(15);
+  { const float e = -6.0f * kSH3a * x * y; J[0][0] += e * sh[27]; J[1][0] += e * sh[28]; J[2][0] += e * sh[29]; }
+  { const float e = -kSH3a * (3.0f * xx - 3.0f * yy); J[0][1] += e * sh[27]; J[1][1] += e * sh[28]; J[2][1] += e * sh[29]; }
+  { const float e = kSH3b * y * z; J[0][0] += e * sh[30]; J[1][0] += e * sh[31]; J[2][0] += e * sh[32]; }
+  { const float e = kSH3b * x * z; J[0][1] += e * sh[30]; J[1][1] += e * sh[31]; J[2][1] += e * sh[32]; }
+  { const float e = kSH3b * x * y; J[0][2] += e * sh[30]; J[1][2] += e * sh[31]; J[2][2] += e * sh[32]; }
+  { const float e = 2.0f * kSH3c * x * y; J[0][0] += e * sh[33]; J[1][0] += e * sh[34]; J[2][0] += e * sh[35]; }
+  { const float e = -kSH3c * (4.0f * zz - xx - 3.0f * yy); J[0][1] += e * sh[33]; J[1][1] += e * sh[34]; J[2][1] += e * sh[35]; }
+  { const float e = -8.0f * kSH3c * y * z; J[0][2] += e * sh[33]; J[1][2] += e * sh[34]; J[2][2] += e * sh[35]; }
+  { const float e = -6.0f * kSH3d * x * z; J[0][0] += e * sh[36]; J[1][0] += e * sh[37]; J[2][0] += e * sh[38]; }
+  { const float e = -6.0f * kSH3d * y * z; J[0][1] += e * sh[36]; J[1][1] += e * sh[37]; J[2][1] += e * sh[38]; }
+  { const float e = kSH3d * (6.0f * zz - 3.0f * xx - 3.0f * yy); J[0][2] += e * sh[36]; J[1][2] += e * sh[37]; J[2][2] += e * sh[38]; }
+  { const float e = -kSH3c * (4.0f * zz - 3.0f * xx - yy); J[0][0] += e * sh[39]; J[1][0] += e * sh[40]; J[2][0] += e * sh[41]; }
+  { const float e = 2.0f * kSH3c * x * y; J[0][1] += e * sh[39]; J[1][1] += e * sh[40]; J[2][1] += e * sh[41]; }
+  { const float e = -8.0f * kSH3c * x * z; J[0][2] += e * sh[39]; J[1][2] += e * sh[40]; J[2][2] += e * sh[41]; }
+  { const float e = 2.0f * kSH3e * x * z; J[0][0] += e * sh[42]; J[1][0] += e * sh[43]; J[2][0] += e * sh[44]; }
+  { const float e = -2.0f * kSH3e * y * z; J[0][1] += e * sh[42]; J[1][1] += e * sh[43]; J[2][1] += e * sh[44]; }
+  { const float e = kSH3e * (xx - yy); J[0][2] += e * sh[42]; J[1][2] += e * sh[43]; J[2][2] += e * sh[44]; }
+  { const float e = -kSH3a * (3.0f * xx - 3.0f * yy); J[0][0] += e * sh[45]; J[1][0] += e * sh[46]; J[2][0] += e * sh[47]; }
+  { const float e = 6.0f * kSH3a * x * y; J[0][1] += e * sh[45]; J[1][1] += e * sh[46]; J[2][1] += e * sh[47]; }
 }
+
 
 struct Attr {
   float mu[3], ls[3], qr[4], eta[3], dsp[3];
@@ -476,12 +479,11 @@ __global__ void __launch_bounds__(kPreThreads, 5) preprocess_fwd_kernel(PreArgs 
             // per channel: d colour / d direction (the backward's view-direction
             // term, so it need not read the SH coefficients) and the clamp flag
             float4* jp = a.ws.shjac + 3 * m;
+            float J[3][3];
+            sh_grad3<DEG>(P.dir[0], P.dir[1], P.dir[2], sh, J);
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-              float J[3];
-              sh_grad<DEG, 3>(P.dir[0], P.dir[1], P.dir[2], sh + ch, J);
-              jp[ch] = make_float4(J[0], J[1], J[2], (clamped >> ch) & 1u ? 1.0f : 0.0f);
-            }
+            for (int ch = 0; ch < 3; ++ch)
+              jp[ch] = make_float4(J[ch][0], J[ch][1], J[ch][2], (clamped >> ch) & 1u ? 1.0f : 0.0f);
           }
           const float m_ = P.comp * (P.o1 + P.o2) * 0.5f;
           const float h_ = P.comp * (P.o1 - P.o2) * 0.5f;
