@@ -88,7 +88,14 @@ struct ViewInfo {
 };
 
 // 2D-gradient record slots (float[16] per (view, Gaussian))
-enum D2Slot { G_MX, G_MY, G_A, G_B, G_C, G_BX, G_BY, G_M, G_H, G_UX, G_UY, G_R, G_G, G_BL, G_ABS, G_PAD };
+// The order puts the slots that are always zero (G_ABS, G_PAD) at 7 and 15
+// and those zero with one opacity (G_UX, G_UY) at 6 and 14: the backward's
+// transposing warp reduction pairs slot i with i + 8 first and skips pairs
+// that are zero in every lane.  (Mirrored by D2_SLOTS in the Python binding.)
+enum D2Slot {
+  G_MX = 0, G_MY = 1, G_A = 2, G_B = 3, G_C = 4, G_BX = 5, G_UX = 6, G_ABS = 7,
+  G_BY = 8, G_M = 9, G_R = 10, G_G = 11, G_BL = 12, G_H = 13, G_UY = 14, G_PAD = 15
+};
 
 // Render record: four float4 per (view, Gaussian).
 //  r0 = (mx, my, A2, B2)     exponent in log2 units: P2 = A2 dx^2 + B2 dx dy + C2 dy^2

@@ -283,9 +283,14 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
 // step a lane keeps half of its values and sends the other half to its
 // partner, so 8 + 4 + 2 + 1 + 1 shuffles replace 16 x 5.  Returns, in every
 // lane, the warp total of value index (lane >> 1) & 15.
+// ZERO6: slots 6 and 14 are zero in every lane (one opacity); slots 7 and 15
+// always are, so their first-step exchange is skipped.
+static_assert(G_ABS == 7 && G_PAD == 15 && G_UX == 6 && G_UY == 14, "reduction pairs of zero slots");
+template <bool ZERO6>
 __device__ __forceinline__ float warp_transpose_sum16(float (&v)[16], int lane) {
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
+    if (i == G_ABS || (ZERO6 && i == G_UX)) continue;  // v[i] and v[i + 8] are zero: so is the sum
     const bool hi = lane & 16;
     const float send = hi ? v[i] : v[i + 8];
     const float keep = hi ? v[i + 8] : v[i];
@@ -595,7 +600,7 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
         float gr[16];
         const bool contrib = pix.visit(bw, bit, r0, r1, r2, r3, fx, py0, amax, gr);
         if (__any_sync(0xffffffffu, contrib)) {
-          const float sum = warp_transpose_sum16(gr, lane);
+          const float sum = warp_transpose_sum16<MODE == MODE_PLAIN>(gr, lane);
           if ((lane & 1) == 0 && sum != 0.0f) atomicAdd(&s_acc[lane >> 1][j], sum);
         }
       }

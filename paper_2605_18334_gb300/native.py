@@ -27,6 +27,11 @@ EXPORTS = ["sr_abi_version", "sr_status_string", "sr_config_default", "sr_camera
 
 SR_ADAM_MAX_GROUPS = 16
 
+# 2D gradients of a render record (dL/d of mean, conic, skew, opacity terms,
+# colour) and their slots in the library's 16-float workspace records
+D2_NAMES = ["mx", "my", "a", "b", "c", "bx", "by", "m", "h", "ux", "uy", "r", "g", "bl"]
+D2_SLOTS = [0, 1, 2, 3, 4, 5, 8, 9, 13, 6, 14, 10, 11, 12]
+
 
 class sr_adam_group(C.Structure):
     _fields_ = [("param", C.c_void_p), ("grad", C.c_void_p), ("m", C.c_void_p), ("v", C.c_void_p), ("n", C.c_int64),

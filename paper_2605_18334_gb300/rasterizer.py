@@ -389,8 +389,11 @@ class Rasterizer:
         return self._slot(self._S_RECT, 8 * m).view(torch.int32).view(m, 2)
 
     def d2(self) -> torch.Tensor:
+        """The 2D gradients of every (view, Gaussian) record after a backward
+        composite, [M, 14] in the order of ``native.D2_NAMES``."""
         m = self.plan.n * self.n_views
-        return self._slot(self._S_D2, 64 * m).view(torch.float32).view(m, 16)
+        raw = self._slot(self._S_D2, 64 * m).view(torch.float32).view(m, 16)
+        return raw[:, torch.as_tensor(N.D2_SLOTS, device=raw.device)]
 
 
 def shard_views(cameras: list, rank: int, world: int) -> list:
