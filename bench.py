@@ -293,7 +293,7 @@ def run_ours(args):
     # DRAM bytes per launch (read + write) of the dominant kernel from the ncu
     # capture summarised in profiles/kernels_full_unbounded_1m_1080p.md, for
     # the launch shape it was taken in (None for any other shape or workload)
-    ncu_traffic = {("render_bwd_composite", 2, 128): 96.99e6, ("render_bwd_composite", 2, 256): 96.73e6}
+    ncu_traffic = {("render_bwd_composite", 2, 128): 96.91e6, ("render_bwd_composite", 2, 256): 96.49e6}
     traffic = None
     if args.n == 1_000_000:
         shape = ((tune["bwd_pixels_per_thread"], r.config.bwd_batch or 256) if dom == 3 else
@@ -371,6 +371,15 @@ def variants(args, sc, cam, up, dev, flush):
         fwd = timed(lambda: r.forward(g), K, flush, stream)
         fb = timed(lambda: (r.forward(g), r.backward(g, d_img)), K, flush, stream)
         res[name] = {"fwd_frames_per_s": round(1e3 / fwd, 2), "fwdbwd_frames_per_s": round(1e3 / fb, 2)}
+        if name == "fp32":
+            # a render-only plan (no blend masks, no backward state): what a viewer uses
+            rf = Rasterizer(g, [cam], Config(forward_only=True), key_capacity=int(12 * args.n))
+            rf.autotune(g)
+            for _ in range(3):
+                rf.forward(g)
+            res["fp32_forward_only_plan"] = {"fwd_frames_per_s": round(1e3 / timed(lambda: rf.forward(g), K, flush,
+                                                                                     stream), 2)}
+            del rf
         del r, g
         torch.cuda.empty_cache()
     # batched + BF16: 8 views of the orbit at 1080p in one plan, BF16 SH,
