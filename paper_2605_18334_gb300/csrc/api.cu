@@ -5,8 +5,20 @@
 #include <cstring>
 
 #include "kernels.cuh"
+#include "nvtx3/nvToolsExt.h"
 
 using namespace sr;
+
+namespace {
+// A named range around each stage call for profilers (NVTX; a no-op unless a
+// tool is attached).
+struct StageRange {
+  explicit StageRange(const char* name) { nvtxRangePushA(name); }
+  ~StageRange() { nvtxRangePop(); }
+  StageRange(const StageRange&) = delete;
+  StageRange& operator=(const StageRange&) = delete;
+};
+}  // namespace
 
 namespace {
 std::atomic<unsigned long long> g_launches{0};
@@ -225,6 +237,7 @@ static sr_status check_plan(const sr_plan* p, void* ws) {
 
 sr_status sr_preprocess(const sr_plan* p, const sr_gaussians* g, const sr_camera* cams_dev, const sr_config* cfg,
                         void* ws, void* stream) {
+  const StageRange range_("sr_preprocess");
   sr_status s = check_plan(p, ws);
   if (s != SR_OK) return s;
   if ((s = check_config(cfg)) != SR_OK) return s;
@@ -273,6 +286,7 @@ static Status* pinned_status() {
 }
 
 sr_status sr_bin_sort(const sr_plan* p, const sr_config* cfg, void* ws, int64_t* keys_needed, void* stream) {
+  const StageRange range_("sr_bin_sort");
   sr_status s = check_plan(p, ws);
   if (s != SR_OK) return s;
   if ((s = check_config(cfg)) != SR_OK) return s;
@@ -345,6 +359,7 @@ static RenderArgs render_args(const sr_plan* p, const sr_config* cfg, void* ws) 
 
 sr_status sr_render_fwd(const sr_plan* p, const sr_config* cfg, void* ws, float* images, float* t_final,
                         uint32_t* n_contrib, void* stream) {
+  const StageRange range_("sr_render_fwd");
   sr_status s = check_plan(p, ws);
   if (s != SR_OK) return s;
   if ((s = check_config(cfg)) != SR_OK) return s;
@@ -358,6 +373,7 @@ sr_status sr_render_fwd(const sr_plan* p, const sr_config* cfg, void* ws, float*
 
 sr_status sr_render_bwd_composite(const sr_plan* p, const sr_config* cfg, void* ws, const float* d_images,
                                   const float* t_final, const uint32_t* n_contrib, void* stream) {
+  const StageRange range_("sr_render_bwd_composite");
   sr_status s = check_plan(p, ws);
   if (s != SR_OK) return s;
   if ((s = check_config(cfg)) != SR_OK) return s;
@@ -380,6 +396,7 @@ sr_status sr_render_bwd_composite(const sr_plan* p, const sr_config* cfg, void* 
 
 sr_status sr_render_bwd_project(const sr_plan* p, const sr_gaussians* g, const sr_camera* cams_dev,
                                 const sr_config* cfg, void* ws, const sr_grads* out, void* stream) {
+  const StageRange range_("sr_render_bwd_project");
   sr_status s = check_plan(p, ws);
   if (s != SR_OK) return s;
   if ((s = check_config(cfg)) != SR_OK) return s;
@@ -457,6 +474,7 @@ size_t sr_loss_scratch_size(const sr_plan* p) {
 
 sr_status sr_loss_l1_dssim(const sr_plan* p, void* ws, const float* images, const float* targets, float lambda,
                            float* d_images, float* loss, float* ssim_l1, void* scratch, void* stream) {
+  const StageRange range_("sr_loss_l1_dssim");
   sr_status s = check_plan(p, ws);
   if (s != SR_OK) return s;
   if (!images || !targets || !d_images || !loss || !scratch) return SR_ERR_INVALID;
@@ -472,6 +490,7 @@ sr_status sr_loss_l1_dssim(const sr_plan* p, void* ws, const float* images, cons
 
 sr_status sr_adam_step(const sr_adam_group* groups, int32_t n_groups, int64_t step, float beta1, float beta2,
                        float eps, void* stream) {
+  const StageRange range_("sr_adam_step");
   if (!groups || n_groups < 1 || n_groups > SR_ADAM_MAX_GROUPS || step < 1) return SR_ERR_INVALID;
   if (!(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f && eps > 0.0f)) return SR_ERR_INVALID;
   for (int i = 0; i < n_groups; ++i) {
@@ -487,6 +506,7 @@ sr_status sr_adam_step(const sr_adam_group* groups, int32_t n_groups, int64_t st
 
 sr_status sr_densify_stats(const float* means2d_abs, const float* depth_grad, int64_t n, float* uv_sum,
                            int32_t* seen, float* z_max, void* stream) {
+  const StageRange range_("sr_densify_stats");
   if (n < 0) return SR_ERR_INVALID;
   if (n > 0 && (!means2d_abs || !depth_grad || !uv_sum || !seen || !z_max)) return SR_ERR_INVALID;
   int dev = 0, sms = 152;
@@ -501,6 +521,7 @@ size_t sr_densify_scratch_size(int64_t n) { return densify_scratch_bytes(n < 0 ?
 sr_status sr_densify(const sr_gaussians* g, const float* uv_sum, const int32_t* seen, const float* z_max,
                      const sr_densify_config* cfg, const sr_scene_arrays* out, uint32_t* src_map, int64_t* counts,
                      void* scratch, void* stream) {
+  const StageRange range_("sr_densify");
   if (!g || !cfg || !out || !counts || !scratch) return SR_ERR_INVALID;
   if (g->n < 0 || g->n >= ((int64_t)1 << 30) || g->sh_degree < 0 || g->sh_degree > 3) return SR_ERR_INVALID;
   if (g->dt_sh != SR_F32 || g->dt_scale != SR_F32 || g->dt_skew != SR_F32) return SR_ERR_INVALID;
@@ -546,6 +567,7 @@ sr_status sr_densify(const sr_gaussians* g, const float* uv_sum, const int32_t* 
 
 sr_status sr_densify_remap(const float* in, int32_t width, const uint32_t* src_map, const int64_t* counts,
                            int64_t cap, float* out, void* stream) {
+  const StageRange range_("sr_densify_remap");
   if (width < 0 || cap < 0) return SR_ERR_INVALID;
   if (width > 0 && cap > 0 && (!in || !src_map || !counts || !out)) return SR_ERR_INVALID;
   return from_cuda(launch_densify_remap(in, width, src_map, counts, cap, out, device_sms(),
