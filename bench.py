@@ -52,7 +52,7 @@ def parse():
                     help="backward pixels per thread (0: autotune)")
     ap.add_argument("--fwd-batch", type=int, default=256, choices=[128, 256, 512],
                     help="forward records per staged batch when the launch shape is fixed")
-    ap.add_argument("--bwd-batch", type=int, default=256, choices=[128, 256],
+    ap.add_argument("--bwd-batch", type=int, default=128, choices=[128, 256],
                     help="backward records per staged batch when the launch shape is fixed")
     return ap.parse_args()
 
@@ -255,7 +255,7 @@ def run_ours(args):
     cfgd = config_dict(args.n)
     cfgd["launch"] = {"fwd_pixels_per_thread": tune["fwd_pixels_per_thread"],
                       "bwd_pixels_per_thread": tune["bwd_pixels_per_thread"],
-                      "fwd_batch": r.config.fwd_batch or 256, "bwd_batch": r.config.bwd_batch or 256,
+                      "fwd_batch": r.config.fwd_batch or 256, "bwd_batch": r.config.bwd_batch or 128,
                       "autotuned": not tune.get("fixed")}
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K,
            "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,

@@ -112,7 +112,7 @@ typedef struct sr_config {
   int32_t bwd_pixels_per_thread; /* 1, 2 or 4 (0 = 2): pixels each thread of sr_render_bwd owns */
   int32_t forward_only;       /* plans made with 1 record no per-pixel blend masks (less workspace);
                                  sr_render_bwd on them returns SR_ERR_UNSUPPORTED */
-  int32_t bwd_batch;          /* 128 or 256 (0 = 256): records sr_render_bwd stages per batch */
+  int32_t bwd_batch;          /* 128 or 256 (0 = 128): records sr_render_bwd stages per batch */
 } sr_config;
 
 /* Gradients of the loss w.r.t. the attributes, FP32, device, caller-owned,

@@ -351,7 +351,7 @@ static RenderArgs render_args(const sr_plan* p, const sr_config* cfg, void* ws) 
   r.mask = w.mask;
   r.tile_order = w.tile_order;
   r.batch_fwd = cfg->fwd_batch > 0 ? cfg->fwd_batch : 256;
-  r.batch_bwd = cfg->bwd_batch > 0 ? cfg->bwd_batch : 256;
+  r.batch_bwd = cfg->bwd_batch > 0 ? cfg->bwd_batch : 128;
   r.px_fwd = cfg->fwd_pixels_per_thread > 0 ? cfg->fwd_pixels_per_thread : 2;
   r.px_bwd = cfg->bwd_pixels_per_thread > 0 ? cfg->bwd_pixels_per_thread : 2;
   return r;

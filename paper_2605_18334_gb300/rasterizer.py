@@ -38,8 +38,8 @@ class Config:
     fwd_pixels_per_thread: int = 0   # 0: library default (2)
     bwd_pixels_per_thread: int = 0
     forward_only: bool = False       # plan without backward state (blend masks)
-    fwd_batch: int = 0               # records staged per batch by the composites (0: 256)
-    bwd_batch: int = 0
+    fwd_batch: int = 0               # records staged per batch by the forward composite (0: 256)
+    bwd_batch: int = 0               # ... by the backward composite (0: 128)
 
     def to_c(self) -> N.sr_config:
         c = N.sr_config()
@@ -346,7 +346,7 @@ class Rasterizer:
                 self.set_batch(bwd=bt)
                 self.backward(g, d_images, stream)  # warm
                 bb[bt] = best_of(lambda: self.backward(g, d_images, stream))
-            bbest = _prefer_default(bb, 256)
+            bbest = _prefer_default(bb, 128)
             self.set_batch(bwd=bbest)
             out.update(bwd_ms=bwd, bwd_pixels_per_thread=pb, bwd_batch_ms=bb, bwd_batch=bbest)
         return out
