@@ -89,13 +89,15 @@ struct ViewInfo {
 
 // 2D-gradient record slots (float[16] per (view, Gaussian))
 // The order puts the slots that are always zero (G_ABS, G_PAD) at 7 and 15
-// and those zero with one opacity (G_UX, G_UY) at 6 and 14: the backward's
-// transposing warp reduction pairs slot i with i + 8 first and skips pairs
-// that are zero in every lane.  (Mirrored by D2_SLOTS in the Python binding.)
+// and those zero with one opacity (G_UX, G_UY) at 3 and 11: the backward's
+// transposing warp reduction pairs slot i with i + 8, then i with i + 4, and
+// skips pairs that are zero in every lane.  (Mirrored by D2_SLOTS in the
+// Python binding.)
 enum D2Slot {
-  G_MX = 0, G_MY = 1, G_A = 2, G_B = 3, G_C = 4, G_BX = 5, G_UX = 6, G_ABS = 7,
-  G_BY = 8, G_M = 9, G_R = 10, G_G = 11, G_BL = 12, G_H = 13, G_UY = 14, G_PAD = 15
+  G_MX = 0, G_MY = 1, G_A = 2, G_UX = 3, G_B = 4, G_C = 5, G_BX = 6, G_ABS = 7,
+  G_BY = 8, G_M = 9, G_H = 10, G_UY = 11, G_R = 12, G_G = 13, G_BL = 14, G_PAD = 15
 };
+static_assert(G_G == G_R + 1 && G_BL == G_R + 2, "colour slots are read as G_R + channel");
 
 // Render record: four float4 per (view, Gaussian).
 //  r0 = (mx, my, A2, B2)     exponent in log2 units: P2 = A2 dx^2 + B2 dx dy + C2 dy^2

@@ -283,14 +283,14 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
 // step a lane keeps half of its values and sends the other half to its
 // partner, so 8 + 4 + 2 + 1 + 1 shuffles replace 16 x 5.  Returns, in every
 // lane, the warp total of value index (lane >> 1) & 15.
-// ZERO6: slots 6 and 14 are zero in every lane (one opacity); slots 7 and 15
-// always are, so their first-step exchange is skipped.
-static_assert(G_ABS == 7 && G_PAD == 15 && G_UX == 6 && G_UY == 14, "reduction pairs of zero slots");
-template <bool ZERO6>
+// ZERO3: slots 3 and 11 are zero in every lane (one opacity); slots 7 and 15
+// always are, so their exchanges are skipped.
+static_assert(G_ABS == 7 && G_PAD == 15 && G_UX == 3 && G_UY == 11, "reduction pairs of zero slots");
+template <bool ZERO3>
 __device__ __forceinline__ float warp_transpose_sum16(float (&v)[16], int lane) {
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    if (i == G_ABS || (ZERO6 && i == G_UX)) continue;  // v[i] and v[i + 8] are zero: so is the sum
+    if (i == 7 || (ZERO3 && i == 3)) continue;  // v[i] and v[i + 8] are zero: so is the sum
     const bool hi = lane & 16;
     const float send = hi ? v[i] : v[i + 8];
     const float keep = hi ? v[i + 8] : v[i];
@@ -298,6 +298,7 @@ __device__ __forceinline__ float warp_transpose_sum16(float (&v)[16], int lane) 
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
+    if (ZERO3 && i == 3) continue;  // positions 3 and 7 hold slots 3, 11, 7 and 15: zero
     const bool hi = lane & 8;
     const float send = hi ? v[i] : v[i + 4];
     const float keep = hi ? v[i + 4] : v[i];

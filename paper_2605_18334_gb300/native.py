@@ -30,7 +30,7 @@ SR_ADAM_MAX_GROUPS = 16
 # 2D gradients of a render record (dL/d of mean, conic, skew, opacity terms,
 # colour) and their slots in the library's 16-float workspace records
 D2_NAMES = ["mx", "my", "a", "b", "c", "bx", "by", "m", "h", "ux", "uy", "r", "g", "bl"]
-D2_SLOTS = [0, 1, 2, 3, 4, 5, 8, 9, 13, 6, 14, 10, 11, 12]
+D2_SLOTS = [0, 1, 2, 4, 5, 6, 8, 9, 10, 3, 11, 12, 13, 14]
 
 
 class sr_adam_group(C.Structure):
