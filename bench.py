@@ -619,7 +619,7 @@ def e2e(args, sc, cam, up, dev, world):
     def compute(i):
         comp.wait_event(ev_in[i])
         comp.wait_event(ev_out[i])
-        r.forward(gbuf[i], out=img_d[i])
+        r.forward(gbuf[i], out=img_d[i], sync=False)  # no host stall per frame; capacity checked after the run
         gout[i] = r.backward(gbuf[i], dbuf[i], out=gout[i])
         ev_done[i].record(comp)
 
@@ -646,6 +646,7 @@ def e2e(args, sc, cam, up, dev, world):
     t0 = time.perf_counter()
     run(K)
     dt = max_over_ranks(time.perf_counter() - t0, world)
+    r.check()  # the frames (all of the same scene) fitted the key capacity; raises otherwise
     return {"value": round(world * K / dt, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "copies": "double-buffered, overlapped with compute"}
 

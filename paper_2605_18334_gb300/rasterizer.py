@@ -196,11 +196,17 @@ class Rasterizer:
                         self.n_contrib.data_ptr(), _stream_ptr(stream))
         return img
 
-    def forward(self, g: Gaussians, stream=None, grow: bool = True, out: torch.Tensor | None = None) -> torch.Tensor:
+    def forward(self, g: Gaussians, stream=None, grow: bool = True, out: torch.Tensor | None = None,
+                sync: bool = True) -> torch.Tensor:
         """Preprocess, bin and sort (growing the key capacity if the frame
         needs more), composite.  Returns the flat image buffer (``out`` if
-        given, else the rasterizer's own)."""
+        given, else the rasterizer's own).  With ``sync=False`` nothing
+        blocks the host (the key count is not read back): a frame that
+        overflows the key capacity is then reported by ``check()``."""
         self.preprocess(g, stream)
+        if not sync:
+            self.bin_sort(stream, sync=False)
+            return self.render_fwd(stream, out)
         try:
             self.keys = self.bin_sort(stream)
         except N.SkewRasterError as e:
@@ -210,6 +216,17 @@ class Rasterizer:
             self.preprocess(g, stream)
             self.keys = self.bin_sort(stream)
         return self.render_fwd(stream, out)
+
+    def check(self, stream=None) -> int:
+        """Synchronise and read the last frame's status word: raises
+        SkewRasterError on a key-capacity overflow or a bounded wait that gave
+        up; returns the frame's key count."""
+        s, keys = N.sr_read_status(self.plan, self.ws.data_ptr(), _stream_ptr(stream))
+        if s != N.SR_OK:
+            err = N.SkewRasterError("sr_read_status", s)
+            err.keys_needed = keys
+            raise err
+        return keys
 
     def backward_composite(self, d_images: torch.Tensor, stream=None):
         """Reverse replay of the last forward (2D gradients stay in the workspace)."""

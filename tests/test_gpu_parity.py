@@ -13,6 +13,7 @@ import pytest
 import torch
 
 import oracle
+from paper_2605_18334_gb300 import native as N
 from paper_2605_18334_gb300 import scenes
 from paper_2605_18334_gb300.rasterizer import Config, Gaussians, Rasterizer
 from tests.parity_util import (GRAD_RTOL, IMG_ATOL, compare_keys, dequantised, gpu_records_to_oracle_layout,
@@ -522,3 +523,20 @@ def test_repeated_backward_calls_restart_from_zero():
     for got in (again, after_composite, rerender):
         for k in ("means", "skew", "sh", "opacity_logits"):
             assert rel_err(got[k].cpu().numpy(), ref[k].cpu().numpy()) < 1e-5, k
+
+
+def test_non_blocking_forward_matches_and_reports_overflow():
+    """forward(sync=False) renders the same image without a host round trip,
+    and an overflow of the key capacity is reported by check()."""
+    sc = scenes.cluster(seed=37, n=4000, sh_degree=1)
+    cams = [scenes.identity_camera(96, 72)]
+    r, g = gpu_forward(sc, cams)
+    ref = r.images.clone()
+    keys = r.keys
+    r.forward(g, sync=False)
+    assert torch.equal(r.images, ref) and r.check() == keys
+    small = Rasterizer(g, cams, Config(), key_capacity=max(1, keys // 2))
+    small.forward(g, sync=False)
+    with pytest.raises(N.SkewRasterError) as e:
+        small.check()
+    assert e.value.status == N.SR_ERR_CAPACITY and e.value.keys_needed == keys
