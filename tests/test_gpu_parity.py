@@ -540,3 +540,48 @@ def test_non_blocking_forward_matches_and_reports_overflow():
     with pytest.raises(N.SkewRasterError) as e:
         small.check()
     assert e.value.status == N.SR_ERR_CAPACITY and e.value.keys_needed == keys
+
+
+def test_near_degenerate_splats():
+    """Needle- and disc-like Gaussians (one or two axes 10^-4 of the others),
+    extreme skew (|eta| up to 40) and centres just beyond the near plane or
+    far outside the view: FP32 projection, binning and compositing still
+    match the FP64 oracle (binning exactly, images within 1e-4, gradients
+    within 1e-3)."""
+    rng = np.random.default_rng(41)
+    sc = scenes.cluster(seed=41, n=3000, sh_degree=1)
+    n = sc.n
+    thin = rng.random(n) < 0.4
+    axis = rng.integers(0, 3, n)
+    ls = sc.log_scales.astype(np.float64)
+    ls[thin, axis[thin]] = ls[thin, axis[thin]] - 9.0          # needles / discs
+    two = thin & (rng.random(n) < 0.3)
+    ls[two, (axis[two] + 1) % 3] -= 9.0
+    sc.log_scales[:] = ls.astype(np.float32)
+    big = rng.random(n) < 0.05
+    sc.skew[big] = (rng.normal(0, 1, (int(big.sum()), 3)) * 20.0).astype(np.float32)
+    near = rng.random(n) < 0.02
+    sc.means[near, 2] = rng.uniform(0.19, 0.3, int(near.sum())).astype(np.float32)
+    cams = [scenes.identity_camera(96, 80)]
+    r, g = gpu_forward(sc, cams)
+    check_view(r, sc, cams, 0, Config())
+    up = scenes.upstream_grad(41, 80, 96)
+    gr = r.backward(g, torch.as_tensor(up).cuda().reshape(-1).contiguous())
+    og = oracle.render_backward(sc, oracle.camera_from_gl(cams[0]), oracle_config(Config()), up)
+    compare_grads(gr, og, GRAD_FIELDS)
+
+
+def test_maximum_view_count():
+    """A plan with the maximum number of views (SR_MAX_VIEWS) of mixed small
+    sizes renders every view as its own frame would: spot-checked views
+    against the oracle, and all views against single-view plans."""
+    sc = scenes.cluster(seed=43, n=2000, sh_degree=0)
+    sizes = ((16, 16), (24, 8), (17, 31))
+    cams = scenes.trajectory_cameras(N.SR_MAX_VIEWS, radius=4.0, resolutions=sizes)
+    r, g = gpu_forward(sc, cams)
+    assert r.plan.n_views == N.SR_MAX_VIEWS
+    for v in (0, 1, 2, 127, N.SR_MAX_VIEWS - 1):
+        check_view(r, sc, cams, v, Config())
+    for v in range(0, N.SR_MAX_VIEWS, 17):
+        r1, g1 = gpu_forward(sc, [cams[v]])
+        assert torch.equal(r.view_image(r.images, v), r1.view_image(r1.images, 0)), v
