@@ -227,7 +227,10 @@ sr_status sr_render_fwd(const sr_plan* plan, const sr_config* cfg, void* ws, flo
  * giving -sqrt(2/pi) beta e^{-z^2} inside the bracket of dL/dmu), FP32
  * gradients reduced per warp before global atomics, then the chain rule
  * through the projection into *out (overwritten).  Needs the ws, t_final and
- * n_contrib of the matching forward call and the same g and cams_dev. */
+ * n_contrib of the matching forward call and the same g and cams_dev.  May be
+ * called again for the same frame (another d_images): the workspace's 2D
+ * gradients, zeroed by sr_preprocess for its frame, are cleared again on the
+ * device when a backward has used them since. */
 sr_status sr_render_bwd(const sr_plan* plan, const sr_gaussians* g, const sr_camera* cams_dev, const sr_config* cfg,
                         void* ws, const float* d_images, const float* t_final, const uint32_t* n_contrib,
                         const sr_grads* out, void* stream);
