@@ -835,7 +835,7 @@ __device__ __forceinline__ int tile_bucket(const uint2* ranges, int64_t t) {
 
 // one block for up to kOrderOneBlock tiles: count, scan and scatter in
 // shared memory
-constexpr int64_t kOrderOneBlock = 65536;
+constexpr int64_t kOrderOneBlock = 16384;
 __global__ void __launch_bounds__(1024) tile_order_block_kernel(const uint2* __restrict__ ranges, int64_t tiles,
                                                                 uint32_t* __restrict__ order) {
   pdl_entry();
@@ -920,9 +920,10 @@ cudaError_t launch_bin_phase2(const BinArgs& a, const int* run, long long keys_k
     uint32_t* counters = a.ws.tile_order + a.total_tiles;
     if ((e = cudaMemsetAsync(counters, 0, sizeof(uint32_t) * 128, st)) != cudaSuccess) return e;
     const unsigned tgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((a.total_tiles + 255) / 256, 1024));
-    tile_order_count_kernel<<<tgrid, 256, 0, st>>>(a.ws.ranges, a.total_tiles, counters);
-    tile_order_scatter_kernel<<<tgrid, 256, 0, st>>>(a.ws.ranges, a.total_tiles, counters, counters + 64,
-                                                     a.ws.tile_order);
+    launch_pdl(tile_order_count_kernel, dim3(tgrid), dim3(256), 0, st, (const uint2*)a.ws.ranges, a.total_tiles,
+               counters);
+    launch_pdl(tile_order_scatter_kernel, dim3(tgrid), dim3(256), 0, st, (const uint2*)a.ws.ranges, a.total_tiles,
+               (const uint32_t*)counters, counters + 64, a.ws.tile_order);
     count_launches(2);
   }
   return cudaGetLastError();
