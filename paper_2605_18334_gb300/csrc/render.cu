@@ -402,7 +402,10 @@ struct BwdPixels {
 // Packed form (even PX): pixels 2q and 2q + 1 of the thread's column share
 // dx and every operation runs on both at once (FP32x2).  A pixel whose bit is
 // clear takes alpha = 0 (its colour state is unchanged exactly) and a zero
-// dL/dalpha, so it adds nothing.
+// dL/dalpha, so it adds nothing.  Every lane evaluates the pair, bits set or
+// not: the warp issues the same instructions as with the clear lanes idle in
+// a branch, and no zero-fill or reconvergence follows (every factor is
+// finite, so the products with the zero alpha and dL/dalpha are zeros).
 template <int MODE, int PX>
 struct BwdPixels<MODE, PX, true> {
   static constexpr int Q = PX / 2;
@@ -437,58 +440,53 @@ struct BwdPixels<MODE, PX, true> {
     for (int q = 0; q < Q; ++q) {
       const bool m0 = (bw[2 * q] >> bit) & 1u, m1 = (bw[2 * q + 1] >> bit) & 1u;
       float2 t[16];
-      if (m0 || m1) {
-        any = true;
-        PairEval2 e;
-        eval_pair2<MODE>(r0, r1, r2, fx, (float)(py0 + 2 * q) + 0.5f, e);
-        const float2 alpha = make_float2(m0 ? fminf(e.alpha.x, amax) : 0.0f, m1 ? fminf(e.alpha.y, amax) : 0.0f);
-        const float2 one_m = add2(f2(1.0f), neg2(alpha));
-        // T_k = T_{k+1} / (1 - alpha) as a product with the reciprocal (rcp.approx)
-        const float2 Tn = mul2(T[q], make_float2(rcp_approx(one_m.x), rcp_approx(one_m.y)));
-        T[q] = make_float2(m0 ? Tn.x : T[q].x, m1 ? Tn.y : T[q].y);
-        const float2 w = mul2(alpha, T[q]);
-        t[G_R] = mul2(w, g0[q]);
-        t[G_G] = mul2(w, g1[q]);
-        t[G_BL] = mul2(w, g2[q]);
-        const float2 c0 = f2(r3.x), c1 = f2(r3.y), c2 = f2(r3.z);
-        float2 s = mul2(g0[q], add2(c0, neg2(R0[q])));
-        s = fma2(g1[q], add2(c1, neg2(R1[q])), s);
-        s = fma2(g2[q], add2(c2, neg2(R2[q])), s);
-        const float2 dl = mul2(T[q], s);
-        R0[q] = fma2(alpha, c0, mul2(one_m, R0[q]));
-        R1[q] = fma2(alpha, c1, mul2(one_m, R1[q]));
-        R2[q] = fma2(alpha, c2, mul2(one_m, R2[q]));
-        // dL/dalpha through the unclamped alpha (the clamp has zero derivative)
-        const float2 dLda = make_float2(m0 && e.alpha.x <= amax ? dl.x : 0.0f, m1 && e.alpha.y <= amax ? dl.y : 0.0f);
-        const float2 S = mul2(e.G, e.E);  // skew kernel G' (1 + erf z)
-        const float2 dlo = mul2(dLda, e.o);
-        const float2 gS = mul2(dlo, S);
-        const float2 gz = mul2(mul2(mul2(dlo, e.G), f2(kTwoOverSqrtPi)), e.ez);  // dL/dz
-        float2 gdx = fma2(neg2(gS), fma2(f2(b_), e.dy, f2(a_ * e.dx)), mul2(gz, f2(r1.y)));
-        float2 gdy = fma2(neg2(gS), fma2(f2(c_), e.dy, f2(b_ * e.dx)), mul2(gz, f2(r1.z)));
-        const float2 dx = f2(e.dx);
-        t[G_M] = mul2(dLda, S);
-        t[G_A] = mul2(gS, f2(-0.5f * e.dx * e.dx));
-        t[G_B] = mul2(mul2(neg2(gS), dx), e.dy);
-        t[G_C] = mul2(mul2(gS, f2(-0.5f)), mul2(e.dy, e.dy));
-        t[G_BX] = mul2(gz, f2(e.dx * kInvSqrt2));
-        t[G_BY] = mul2(mul2(gz, e.dy), f2(kInvSqrt2));
-        if (MODE != MODE_PLAIN) {
-          t[G_H] = mul2(mul2(dLda, e.eu), S);
-          const float2 gzu = mul2(mul2(mul2(mul2(dLda, f2(r2.x)), S), f2(kTwoOverSqrtPi)), e.ezu);
-          gdx = fma2(gzu, f2(r2.y), gdx);
-          gdy = fma2(gzu, f2(r2.z), gdy);
-          t[G_UX] = mul2(gzu, f2(e.dx * kInvSqrt2));
-          t[G_UY] = mul2(mul2(gzu, e.dy), f2(kInvSqrt2));
-        } else {
-          t[G_H] = t[G_UX] = t[G_UY] = f2(0.0f);
-        }
-        t[G_MX] = neg2(gdx);
-        t[G_MY] = neg2(gdy);
+      any |= m0 || m1;
+      PairEval2 e;
+      eval_pair2<MODE>(r0, r1, r2, fx, (float)(py0 + 2 * q) + 0.5f, e);
+      const float2 alpha = make_float2(m0 ? fminf(e.alpha.x, amax) : 0.0f, m1 ? fminf(e.alpha.y, amax) : 0.0f);
+      const float2 one_m = add2(f2(1.0f), neg2(alpha));
+      // T_k = T_{k+1} / (1 - alpha) as a product with the reciprocal (rcp.approx)
+      const float2 Tn = mul2(T[q], make_float2(rcp_approx(one_m.x), rcp_approx(one_m.y)));
+      T[q] = make_float2(m0 ? Tn.x : T[q].x, m1 ? Tn.y : T[q].y);
+      const float2 w = mul2(alpha, T[q]);
+      t[G_R] = mul2(w, g0[q]);
+      t[G_G] = mul2(w, g1[q]);
+      t[G_BL] = mul2(w, g2[q]);
+      const float2 c0 = f2(r3.x), c1 = f2(r3.y), c2 = f2(r3.z);
+      float2 s = mul2(g0[q], add2(c0, neg2(R0[q])));
+      s = fma2(g1[q], add2(c1, neg2(R1[q])), s);
+      s = fma2(g2[q], add2(c2, neg2(R2[q])), s);
+      const float2 dl = mul2(T[q], s);
+      R0[q] = fma2(alpha, c0, mul2(one_m, R0[q]));
+      R1[q] = fma2(alpha, c1, mul2(one_m, R1[q]));
+      R2[q] = fma2(alpha, c2, mul2(one_m, R2[q]));
+      // dL/dalpha through the unclamped alpha (the clamp has zero derivative)
+      const float2 dLda = make_float2(m0 && e.alpha.x <= amax ? dl.x : 0.0f, m1 && e.alpha.y <= amax ? dl.y : 0.0f);
+      const float2 S = mul2(e.G, e.E);  // skew kernel G' (1 + erf z)
+      const float2 dlo = mul2(dLda, e.o);
+      const float2 gS = mul2(dlo, S);
+      const float2 gz = mul2(mul2(mul2(dlo, e.G), f2(kTwoOverSqrtPi)), e.ez);  // dL/dz
+      float2 gdx = fma2(neg2(gS), fma2(f2(b_), e.dy, f2(a_ * e.dx)), mul2(gz, f2(r1.y)));
+      float2 gdy = fma2(neg2(gS), fma2(f2(c_), e.dy, f2(b_ * e.dx)), mul2(gz, f2(r1.z)));
+      const float2 dx = f2(e.dx);
+      t[G_M] = mul2(dLda, S);
+      t[G_A] = mul2(gS, f2(-0.5f * e.dx * e.dx));
+      t[G_B] = mul2(mul2(neg2(gS), dx), e.dy);
+      t[G_C] = mul2(mul2(gS, f2(-0.5f)), mul2(e.dy, e.dy));
+      t[G_BX] = mul2(gz, f2(e.dx * kInvSqrt2));
+      t[G_BY] = mul2(mul2(gz, e.dy), f2(kInvSqrt2));
+      if (MODE != MODE_PLAIN) {
+        t[G_H] = mul2(mul2(dLda, e.eu), S);
+        const float2 gzu = mul2(mul2(mul2(mul2(dLda, f2(r2.x)), S), f2(kTwoOverSqrtPi)), e.ezu);
+        gdx = fma2(gzu, f2(r2.y), gdx);
+        gdy = fma2(gzu, f2(r2.z), gdy);
+        t[G_UX] = mul2(gzu, f2(e.dx * kInvSqrt2));
+        t[G_UY] = mul2(mul2(gzu, e.dy), f2(kInvSqrt2));
       } else {
-#pragma unroll
-        for (int k = 0; k < 16; ++k) t[k] = f2(0.0f);
+        t[G_H] = t[G_UX] = t[G_UY] = f2(0.0f);
       }
+      t[G_MX] = neg2(gdx);
+      t[G_MY] = neg2(gdy);
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         if (k == G_ABS || k == G_PAD) continue;
