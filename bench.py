@@ -293,10 +293,10 @@ def run_ours(args):
     # DRAM bytes per launch (read + write) of the dominant kernel from the ncu
     # capture summarised in profiles/kernels_full_unbounded_1m_1080p.md, for
     # the launch shape it was taken in (None for any other shape or workload)
-    ncu_traffic = {("render_bwd_composite", 2, 128): 96.91e6, ("render_bwd_composite", 2, 256): 96.49e6}
+    ncu_traffic = {("render_bwd_composite", 2, 128): 96.62e6, ("render_bwd_composite", 2, 256): 96.61e6}
     traffic = None
     if args.n == 1_000_000:
-        shape = ((tune["bwd_pixels_per_thread"], r.config.bwd_batch or 256) if dom == 3 else
+        shape = ((tune["bwd_pixels_per_thread"], r.config.bwd_batch or 128) if dom == 3 else
                  (tune["fwd_pixels_per_thread"], r.config.fwd_batch or 256))
         traffic = ncu_traffic.get((names[dom],) + shape)
     if dom in ops:
