@@ -759,7 +759,8 @@ def run_mixed_5m(args):
     del sc
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-    K = max(2, args.steps // 5)
+    K = max(3, args.steps // 5)
+    W = max(3, args.warmup)  # untimed calls before each timed section
     # A: 32 views at 4K, forward only, 4 groups of 8 views through one plan
     cams4k = scenes.trajectory_cameras(32, resolutions=((3840, 2160),))
     groups = [cams4k[i:i + 8] for i in range(0, 32, 8)]
@@ -776,7 +777,8 @@ def run_mixed_5m(args):
             ra.set_cameras(grp)
             ra.forward(g)
 
-    traj()
+    for _ in range(W):
+        traj()
     ms_a = timed(traj, K, flush, stream)
     cap_a = ra.key_capacity
     del ra
@@ -789,19 +791,21 @@ def run_mixed_5m(args):
     rb.forward(g)
     rb.autotune(g, flat)
     fb = lambda: (rb.forward(g), rb.backward(g, flat))
-    fb()
+    for _ in range(W):
+        fb()
     ms_batched = timed(fb, K, flush, stream)
     ws_batched = int(rb.plan.ws_bytes)
     keys_b = int(rb.keys)
     del rb
     torch.cuda.empty_cache()
     plans = {}
-    render_views_recompute(g, cams, ups, Config(), plans)
+    for _ in range(W):
+        render_views_recompute(g, cams, ups, Config(), plans)
     ms_recompute = timed(lambda: render_views_recompute(g, cams, ups, Config(), plans), K, flush, stream)
     ws_recompute = sum(int(r.plan.ws_bytes) for r in plans.values())
     value = 8 / (ms_batched / 1e3)
     out = {"metric": METRIC, "value": round(value, 3), "unit": "views/s", "n_gpus": world, "steps": K,
-           "warmup": 1, "ms_per_step": round(ms_batched, 3), "higher_is_better": True, "scaling": "weak",
+           "warmup": W, "ms_per_step": round(ms_batched, 3), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32 (SH stored bf16)", "data": "synthetic",
            "config": {"workload": "mixed_5m", "gaussians": 5_000_000, "zero_skew_fraction": 0.5,
                       "l2": "flushed (256 MiB memset) before each step"},
