@@ -393,7 +393,7 @@ def variants(args, sc, cam, up, dev, flush):
     up8 = torch.cat([torch.as_tensor(scenes.upstream_grad(70 + v, 1080, 1920), device=dev).reshape(-1)
                      for v in range(8)]).contiguous()
     r.autotune(g, up8)
-    for _ in range(2):
+    for _ in range(3):
         r.forward(g)
         r.backward(g, up8)
     fwd = timed(lambda: r.forward(g), K, flush, stream)
@@ -541,7 +541,7 @@ def trajectory(args, sc, dev, flush, n_views=64):
         r.preprocess(g, s)
         r.bin_sort(s, sync=False)
         r.render_fwd(s)
-    for _ in range(2):
+    for _ in range(3):
         graph.replay()
     torch.cuda.synchronize()
     K = max(3, args.steps // 4)
