@@ -225,3 +225,17 @@ def test_densify_calls_reject_invalid_arguments_without_device_work(lib):
     assert lib.sr_densify(C.byref(g), ok, ok, ok, None, C.byref(out), None, ok, ok, None) == N.SR_ERR_INVALID
     assert lib.sr_densify_remap(ok, -1, ok, ok, 10, ok, None) == N.SR_ERR_INVALID
     assert lib.sr_densify_remap(None, 3, ok, ok, 10, ok, None) == N.SR_ERR_INVALID
+
+
+def test_autotune_keeps_the_default_within_the_margin():
+    from paper_2605_18334_gb300.rasterizer import _prefer_default
+
+    # the default stays unless another candidate is more than 2% faster
+    assert _prefer_default({128: 0.456, 256: 0.4475}, 128) == 128
+    assert _prefer_default({128: 0.456, 256: 0.440}, 128) == 256
+    # ties and a faster default
+    assert _prefer_default({128: 0.5, 256: 0.5}, 256) == 256
+    assert _prefer_default({1: 0.76, 2: 0.58, 4: 0.64}, 2) == 2
+    # a default that was not timed: the fastest candidate
+    assert _prefer_default({1: 0.76, 4: 0.64}, 2) == 4
+    assert _prefer_default({128: 0.456, 256: 0.4475}, 128, margin=0.0) == 256
