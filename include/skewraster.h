@@ -28,8 +28,9 @@
  *    only.
  *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
  *    default stream).  All device work is enqueued asynchronously on it;
- *    only sr_bin_sort with a non-NULL keys_needed and sr_read_status block
- *    the host (they read a few bytes back from the device).
+ *    only sr_bin_sort with a non-NULL keys_needed, sr_read_status,
+ *    sr_frame_counters, sr_selftest_bounded_wait and sr_sort_keys_noalloc
+ *    block the host (they read a few bytes back from the device).
  *  - Errors: every call returns an sr_status; nothing is thrown across the
  *    ABI.  Host-side argument checks run first and leave the device
  *    untouched on failure.  Device-side failures (key capacity exceeded, a
@@ -199,9 +200,15 @@ size_t sr_workspace_size(const sr_plan* plan);
 sr_status sr_preprocess(const sr_plan* plan, const sr_gaussians* g, const sr_camera* cams_dev, const sr_config* cfg,
                         void* ws, void* stream);
 
-/* Tile binning and depth sort: exclusive scan of the tile counts, one
- * (global tile << 32 | FP32 depth bits) key per touched tile in Gaussian
- * index order, a stable LSD radix sort (ties keep index order), and per-tile
+/* Tile binning and depth sort.  The records are first sorted by their FP32
+ * depth bits (4 stable 8-bit LSD radix passes over the records, ties in
+ * record-index order); an exclusive scan of the tile counts, taken in that
+ * depth order, places each record's keys; one 32-bit global tile id per
+ * touched tile (row-major within the record) is emitted in depth order with
+ * the record index as value; a stable LSD radix sort over the tile-id bits
+ * only then leaves every tile's keys in (depth bits, record index) order.
+ * The result is the list a stable sort of 64-bit (global tile << 32 | depth
+ * bits) keys emitted in record-index order would give, with per-tile
  * [start, end) ranges.  If keys_needed is non-NULL the call blocks until
  * the key emission is done, stores the number of keys the frame needs and
  * returns SR_ERR_CAPACITY (nothing to render) if it exceeds
@@ -249,13 +256,20 @@ sr_status sr_render_bwd(const sr_plan* plan, const sr_gaussians* g, const sr_cam
  * SR_ERR_INVALID.
  *
  * Scratch: one fixed array of about 16 MiB in the library's device memory,
- * present on every GPU that loads the library until the process exits.  The
- * first call on a device looks up that array's device address (with the
- * device current), so make the first call before any CUDA-graph stream
- * capture.  Every call reuses the same array and the work it enqueues
- * clears what must start at zero; calls whose work overlaps on the GPU
- * (different streams, or several host threads) race on it and must be
- * serialised by the caller. */
+ * present on every GPU that loads the library until the process exits.
+ * Each call looks up that array's device address on the current device
+ * (cudaGetSymbolAddress; the address can change after a cudaDeviceReset).
+ * Every call reuses the same array and the work it enqueues clears what
+ * must start at zero; calls whose work overlaps on the GPU (different
+ * streams, or several host threads) race on it and must be serialised by the
+ * caller.
+ *
+ * Completion: the call ends by reading the sort's 4-byte status word back
+ * and synchronising the stream, so the output is ready when it returns.  It
+ * returns SR_ERR_TIMEOUT if one of the sort's bounded look-back waits gave
+ * up (the output is then not sorted), and SR_ERR_CUDA only when one of its
+ * own launches or its readback failed (errors left pending by earlier,
+ * unrelated calls are neither reported nor cleared). */
 #define SR_NOALLOC_MAX_KEYS (1u << 20)
 sr_status sr_sort_keys_noalloc(const uint64_t* keys_in, const uint32_t* vals_in, int64_t n, int32_t sort_bits,
                                uint64_t* keys_out, uint32_t* vals_out, void* stream);

@@ -29,11 +29,12 @@ _lock = threading.Lock()
 _lib = None
 
 # Parity tolerances for decisions taken in floating point (documented in the
-# design notes): a pair whose alpha lies within TOL_ALPHA of alpha_min, or
-# whose T' lies within TOL_T (relative) of T_stop, makes its pixel
-# "decision-ambiguous"; a rectangle edge within TOL_PX of a pixel-centre
-# boundary makes a Gaussian's tile set ambiguous.
-TOL_ALPHA = 2e-6
+# design notes, with the FP32 errors measured against them): a pair whose
+# alpha lies within TOL_ALPHA (relative) of alpha_min or of alpha_max, or
+# whose T' lies within TOL_T (relative) of T_stop, is "decision-ambiguous";
+# a rectangle edge within TOL_PX of a pixel-centre boundary makes a
+# Gaussian's tile set ambiguous.
+TOL_ALPHA = 5e-4
 TOL_T = 1e-3
 TOL_PX = 2e-3
 
@@ -173,9 +174,10 @@ def all_pixels(cam: Camera) -> np.ndarray:
 
 
 def render(scene, cam: Camera, cfg: Config, pixels=None, pre=None, tol_alpha=TOL_ALPHA, tol_t=TOL_T) -> dict:
-    """Brute-force render: every visible Gaussian, in (depth key, index) order,
-    at each listed pixel (default: all pixels, row-major).  With the default
-    pixel list, ``rgb`` is [H,W,3] and the other outputs [H,W]."""
+    """Brute-force render (mode A): every visible Gaussian, in (depth key,
+    index) order, at each listed pixel (default: all pixels, row-major).  With
+    the default pixel list, ``rgb`` is [H,W,3] and the other outputs [H,W].
+    ``tol_alpha`` is relative to alpha_min, ``tol_t`` to t_stop."""
     pre = pre or preprocess(scene, cam, cfg)
     full = pixels is None
     pix = all_pixels(cam) if full else np.ascontiguousarray(np.asarray(pixels, np.int32).reshape(-1, 2))
@@ -197,31 +199,125 @@ def render(scene, cam: Camera, cfg: Config, pixels=None, pre=None, tol_alpha=TOL
     return out
 
 
-def render_backward(scene, cam: Camera, cfg: Config, dL_dC, pixels=None, pre=None) -> dict:
+class _GradsOut(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("means", "log_scales", "quats", "opac", "skew", "split", "sh")]
+
+
+def _grad_arrays(scene, with_split):
+    n = scene.n
+    K = (scene.sh_degree + 1) ** 2
+    nop = 2 if np.asarray(scene.opacity_logits).ndim == 2 else 1
+    d = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
+             opacity_logits=np.zeros((n, nop)), skew=np.zeros((n, 3)),
+             split_dir=np.zeros((n, 3)) if with_split else None, sh=np.zeros((n, K, 3)))
+    s = _GradsOut(*[_p(d[k]).value if d[k] is not None else None
+                    for k in ("means", "log_scales", "quats", "opacity_logits", "skew", "split_dir", "sh")])
+    return d, s
+
+
+def _flat_opac(d, nop):
+    if nop == 1:
+        d["opacity_logits"] = d["opacity_logits"].reshape(-1)
+    return d
+
+
+def render_frame(scene, cam: Camera, cfg: Config, pre=None, gpu_lists=None, tol_alpha=TOL_ALPHA,
+                 tol_t=TOL_T, want_lists: bool = False) -> dict:
+    """Whole frame by mode B (per-pixel lists of the Gaussians whose footprint
+    reaches the pixel, in depth order; equal to mode A bit for bit).  With
+    ``gpu_lists`` = (offsets [H*W+1] int64, ids int32), the gate and stop
+    decisions of another renderer (which blended ids[off[p]:off[p+1]] at pixel
+    p, row-major) are replayed: ``status`` is nonzero at pixels where one of
+    them is not admissible, ``rgb``/``T`` are the FP64 results under them.
+    ``stats``: flipped-decision counts and the largest margins.
+    ``want_lists``: also return ``lists`` = (offsets, ids) of the Gaussians
+    each pixel blended (a second pass)."""
+    assert tol_alpha < 1e-2 or gpu_lists is None, "mode B's lists hold only pairs with alpha >= alpha_min (1 - 1e-2)"
+    pre = pre or preprocess(scene, cam, cfg)
+    H, W = cam.height, cam.width
+    m = H * W
+    rgb = np.zeros((m, 3))
+    T = np.zeros(m)
+    last = np.zeros(m, np.int64)
+    cnt = np.zeros(m, np.int32)
+    amb = np.zeros(m, np.int32)
+    status = np.zeros(m, np.int32)
+    st = np.zeros(8)
+    if gpu_lists is not None:
+        off = np.ascontiguousarray(gpu_lists[0], np.int64)
+        ids = np.ascontiguousarray(gpu_lists[1], np.int32)
+        assert off.shape == (m + 1,)
+    else:
+        off = ids = None
+    lib().or_render_frame(C.byref(cam), C.byref(cfg), C.c_int64(scene.n), _p(pre["rec"]), _p(pre["depth_bits"]),
+                          _p(pre["_vis32"]), C.c_double(tol_alpha), C.c_double(tol_t), _p(off), _p(ids), _p(rgb),
+                          _p(T), _p(last), _p(cnt), _p(amb), _p(status), _p(st), None, None)
+    lists = None
+    if want_lists:
+        loff = np.zeros(m + 1, np.int64)
+        np.cumsum(cnt, out=loff[1:])
+        lids = np.zeros(max(1, int(loff[-1])), np.int32)
+        t2 = [np.zeros_like(a) for a in (rgb, T, last, cnt, amb, status)]
+        lib().or_render_frame(C.byref(cam), C.byref(cfg), C.c_int64(scene.n), _p(pre["rec"]),
+                              _p(pre["depth_bits"]), _p(pre["_vis32"]), C.c_double(tol_alpha), C.c_double(tol_t),
+                              _p(off), _p(ids), *[_p(a) for a in t2], None, _p(loff), _p(lids))
+        lists = (loff, lids[:int(loff[-1])])
+    names = ["flipped_pixels", "flipped_gate", "flipped_stop", "max_gate_margin", "max_stop_margin",
+             "inadmissible_pixels", "candidate_pairs", "ambiguous_pixels"]
+    stats = {k: (float(v) if "margin" in k else int(v)) for k, v in zip(names, st)}
+    return dict(rgb=rgb.reshape(H, W, 3), T=T.reshape(H, W), last=last.reshape(H, W), count=cnt.reshape(H, W),
+                ambiguous=amb.astype(bool).reshape(H, W), status=status.reshape(H, W), stats=stats, lists=lists)
+
+
+def render_backward(scene, cam: Camera, cfg: Config, dL_dC, pixels=None, pre=None, frame: bool = False,
+                    gpu_lists=None, bounds: bool = False, tol_alpha=TOL_ALPHA, tol_t=TOL_T) -> dict:
     """Gradients of L = sum(dL_dC * C).  ``dL_dC`` is planar [3,H,W] when
-    ``pixels`` is None, else [n_pix,3] aligned with ``pixels``."""
+    ``pixels`` is None, else [n_pix,3] aligned with ``pixels``.  ``frame``:
+    every pixel through mode B (else mode A over the pixel list, default all
+    pixels).  ``gpu_lists`` (indexed like the pixels): replay another
+    renderer's gate and stop decisions.  ``bounds``: also return, per
+    element, ``scale`` (the rounding-error scale: sum of the magnitudes of
+    the terms) and ``slack`` (the terms whose alpha_max or colour clamp lies
+    within tolerance), as dicts of the same layouts."""
+    assert tol_alpha < 1e-2 or not frame or gpu_lists is None, "mode B's lists hold only pairs with alpha >= alpha_min (1 - 1e-2)"
     pre = pre or preprocess(scene, cam, cfg)
     n = scene.n
     if pixels is None:
-        pix = all_pixels(cam)
         g = np.ascontiguousarray(np.asarray(dL_dC, np.float64).reshape(3, -1).T)
+        pix = None if frame else all_pixels(cam)
     else:
+        assert not frame
         pix = np.ascontiguousarray(np.asarray(pixels, np.int32).reshape(-1, 2))
         g = np.ascontiguousarray(np.asarray(dL_dC, np.float64).reshape(-1, 3))
     a = _Arrays(scene)
-    K = (scene.sh_degree + 1) ** 2
     nop = 2 if a.opac.ndim == 2 else 1
     d2 = np.zeros((n, NDIFF))
-    gm, gl, gs = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 3))
-    gq = np.zeros((n, 4))
-    go = np.zeros((n, nop))
-    gd = np.zeros((n, 3)) if a.split is not None else None
-    gsh = np.zeros((n, K, 3))
+    d2s = np.zeros((n, NDIFF)) if bounds else None
+    d2l = np.zeros((n, NDIFF)) if bounds else None
+    G, Gs = _grad_arrays(scene, a.split is not None)
+    S, Ss = _grad_arrays(scene, a.split is not None) if bounds else (None, None)
+    L, Ls = _grad_arrays(scene, a.split is not None) if bounds else (None, None)
+    if gpu_lists is not None:
+        off = np.ascontiguousarray(gpu_lists[0], np.int64)
+        ids = np.ascontiguousarray(gpu_lists[1], np.int32)
+        assert off.shape == (g.shape[0] + 1,)
+    else:
+        off = ids = None
+    bad = C.c_int64(0)
     lib().or_render_backward(C.byref(a.s), C.byref(cam), C.byref(cfg), _p(pre["rec"]), _p(pre["depth_bits"]),
-                             _p(pre["_vis32"]), C.c_int64(pix.shape[0]), _p(pix), _p(g), _p(d2), _p(gm), _p(gl),
-                             _p(gq), _p(go), _p(gs), _p(gd), _p(gsh))
-    return dict(d2=d2, means=gm, log_scales=gl, quats=gq, opacity_logits=go.reshape(n) if nop == 1 else go,
-                skew=gs, split_dir=gd, sh=gsh)
+                             _p(pre["_vis32"]), C.c_int64(0 if pix is None else pix.shape[0]), _p(pix), _p(g),
+                             _p(off), _p(ids), C.c_double(tol_alpha), C.c_double(tol_t), _p(d2), _p(d2s), _p(d2l),
+                             C.byref(Gs), C.byref(Ss) if bounds else None, C.byref(Ls) if bounds else None,
+                             C.byref(bad))
+    out = _flat_opac(G, nop)
+    out["d2"] = d2
+    out["inadmissible_pixels"] = int(bad.value)
+    if bounds:
+        out["scale"] = _flat_opac(S, nop)
+        out["scale"]["d2"] = d2s
+        out["slack"] = _flat_opac(L, nop)
+        out["slack"]["d2"] = d2l
+    return out
 
 
 def bin_keys(pre: dict, cam: Camera, cfg: Config, tile_base: int = 0, val_base: int = 0):

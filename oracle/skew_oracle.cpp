@@ -227,7 +227,7 @@ inline float depth_f32(const OrCamera& c, const double* mu) {
 // colour coefficients (colour is linear in them).  Writes NREC entries.
 template <class S>
 void project(const S* theta, bool two_opac, bool has_split, const double* sh, int deg,
-             const OrCamera& c, const OrConfig& cfg, S* rec) {
+             const OrCamera& c, const OrConfig& cfg, S* rec, bool colour_clamp = true) {
   const S* mu = theta + P_MU;
   // world -> camera
   S t[3];
@@ -302,7 +302,7 @@ void project(const S* theta, bool two_opac, bool has_split, const double* sh, in
   for (int ch = 0; ch < 3; ++ch) {
     S acc(0.5);
     for (int k = 0; k < K; ++k) acc = acc + sh[3 * k + ch] * Y[k];
-    rec[R_CR + ch] = relu(acc);
+    rec[R_CR + ch] = colour_clamp ? relu(acc) : acc;
   }
 
   rec[R_MX] = c.fx * t[0] / t[2] + c.cx;
@@ -572,176 +572,610 @@ void or_preprocess(const OrScene* s, const OrCamera* c, const OrConfig* cfg, dou
   }
 }
 
+}  // extern "C"
+
+namespace {
+
+int or_num_threads_impl() {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 // Depth order of the visible Gaussians: by (FP32 depth bits, index).
-static std::vector<int64_t> depth_order(int64_t n, const uint32_t* depth_bits, const int32_t* visible) {
-  std::vector<int64_t> order;
+static std::vector<int32_t> depth_order(int64_t n, const uint32_t* depth_bits, const int32_t* visible) {
+  std::vector<int32_t> order;
   for (int64_t i = 0; i < n; ++i)
-    if (visible[i]) order.push_back(i);
+    if (visible[i]) order.push_back((int32_t)i);
   std::stable_sort(order.begin(), order.end(),
-                   [&](int64_t a, int64_t b) { return depth_bits[a] < depth_bits[b]; });
+                   [&](int32_t a, int32_t b) { return depth_bits[a] < depth_bits[b]; });
   return order;
 }
 
-// One pixel, brute force over every visible Gaussian in depth order (Alg. 1,
-// Eq. color).  Fills the list of blended Gaussians with their alpha, T and
-// whether alpha was clamped, and reports decision-ambiguous pairs.
-struct Blend { int64_t id; double alpha; double T; int clamped; };
+// One blended pair of a pixel: its alpha, the transmittance in front of it,
+// whether alpha_max clamped it and whether that clamp decision lies within
+// the tolerance of alpha_max (its derivative is then ambiguous).
+struct Blend { int32_t id; double alpha; double T; int clamped; int clamp_near; };
 
-static void composite_pixel(const std::vector<int64_t>& order, const double* rec, const OrConfig& cfg,
-                            int px, int py, double tol_alpha, double tol_t, double* C, double* T_out,
-                            int* ambiguous, std::vector<Blend>* blended, uint64_t* signature = nullptr) {
+// What a pixel's decisions looked like.  ambiguous: some pair lies within
+// the tolerance of the gate or of the stop.  For a replay of another
+// renderer's decisions: status 0 if every decision it took is admissible,
+// else the kind of the first inadmissible one (1: blended a pair below the
+// gate, 2: blended a pair past the stop, 3: skipped a pair it should have
+// stopped at, 4: skipped a pair it should have blended, 5: blended a pair
+// this pixel's list does not hold, or out of order); flips counts the
+// decisions that differ from the FP64 ones, margin the largest relative
+// distance of such a decision's alpha (gate) or T' (stop) to its threshold.
+struct PixelDecisions {
+  int ambiguous = 0;
+  int status = 0;
+  int flips_gate = 0, flips_stop = 0;
+  double margin_gate = 0.0, margin_stop = 0.0;
+};
+
+// Front-to-back compositing of one pixel over a depth-ordered candidate list
+// ids[0..m) (Alg. 1, Eq. color): alpha = min(alpha_max, alpha_raw); a pair
+// with alpha < alpha_min is skipped; the stop comes before the Gaussian whose
+// T' = T (1 - alpha) falls below t_stop; C = sum c alpha T + T_final bg.
+// Decisions are FP64's own, or, when gpu is non-null, those of another
+// renderer that blended exactly gpu[0..ng) (in order): each of its decisions
+// must then either agree with FP64 or lie within the tolerance (tol_a
+// relative to alpha_min, tol_t relative to t_stop) of its threshold.
+// Candidates missing from ids must have alpha < alpha_min (1 - tol_a).
+static void composite_list(const int32_t* ids, int64_t m, const int32_t* gpu, int64_t ng, const double* rec,
+                           const OrConfig& cfg, int px, int py, double tol_a, double tol_t, double* C,
+                           double* T_out, std::vector<Blend>* blended, PixelDecisions* dec,
+                           uint64_t* signature = nullptr) {
   double T = 1.0, acc[3] = {0.0, 0.0, 0.0};
-  int amb = 0;
   uint64_t sig = 1469598103934665603ull;  // FNV-1a over the discrete decisions
   const double x = px + 0.5, y = py + 0.5;
-  for (int64_t id : order) {
+  const double amin = cfg.alpha_min, amax = cfg.alpha_max, tstop = cfg.t_stop;
+  int64_t k = 0;  // next pair the other renderer blended
+  for (int64_t j = 0; j < m; ++j) {
+    const int32_t id = ids[j];
     const double* r = rec + (size_t)NREC * id;
-    double a_raw = alpha_raw<double>(r, x, y);
-    double a = std::min(cfg.alpha_max, a_raw);
-    if (std::fabs(a - cfg.alpha_min) < tol_alpha) amb = 1;
-    if (a < cfg.alpha_min) continue;
-    double Tn = T * (1.0 - a);
-    if (std::fabs(Tn - cfg.t_stop) < tol_t * cfg.t_stop) amb = 1;
-    sig = (sig ^ (uint64_t)(2 * id + (a_raw > cfg.alpha_max))) * 1099511628211ull;
-    if (Tn < cfg.t_stop) { sig = (sig ^ 0xffffull) * 1099511628211ull; break; }
+    const double a_raw = alpha_raw<double>(r, x, y);
+    const double a = std::min(amax, a_raw);
+    const bool pass = a >= amin;
+    const bool near_gate = std::fabs(a - amin) < tol_a * amin;
+    if (near_gate) dec->ambiguous = 1;
+    if (!pass && !gpu) continue;
+    const double Tn = T * (1.0 - a);
+    const bool stop = Tn < tstop;
+    const bool near_stop = std::fabs(Tn - tstop) < tol_t * tstop;
+    if (pass && near_stop) dec->ambiguous = 1;
+    bool take;
+    if (!gpu) {
+      sig = (sig ^ (uint64_t)(2 * (int64_t)id + (a_raw > amax))) * 1099511628211ull;
+      if (stop) { sig = (sig ^ 0xffffull) * 1099511628211ull; break; }
+      take = true;
+    } else if (k < ng && gpu[k] == id) {
+      // blended by the other renderer
+      if (!pass) {
+        if (!near_gate) { dec->status = 1; break; }
+        ++dec->flips_gate;
+        dec->margin_gate = std::max(dec->margin_gate, std::fabs(a - amin) / amin);
+      }
+      if (stop) {
+        if (!near_stop) { dec->status = 2; break; }
+        ++dec->flips_stop;
+        dec->margin_stop = std::max(dec->margin_stop, std::fabs(Tn - tstop) / tstop);
+      }
+      take = true;
+      ++k;
+    } else {
+      // not blended by the other renderer
+      if (!pass) continue;
+      if (k == ng && (stop || near_stop)) {  // it stopped here
+        if (!stop) {
+          ++dec->flips_stop;
+          dec->margin_stop = std::max(dec->margin_stop, std::fabs(Tn - tstop) / tstop);
+        }
+        break;
+      }
+      if (near_gate) {  // it saw alpha below the gate
+        ++dec->flips_gate;
+        dec->margin_gate = std::max(dec->margin_gate, std::fabs(a - amin) / amin);
+        continue;
+      }
+      dec->status = stop ? 3 : 4;
+      break;
+    }
+    if (!take) continue;
     for (int ch = 0; ch < 3; ++ch) acc[ch] += r[R_CR + ch] * a * T;
-    if (blended) blended->push_back({id, a, T, a_raw > cfg.alpha_max});
+    if (blended)
+      blended->push_back({id, a, T, a_raw > amax, std::fabs(a_raw - amax) < tol_a * amax ? 1 : 0});
     T = Tn;
   }
+  if (gpu && dec->status == 0 && k < ng) dec->status = 5;
   for (int ch = 0; ch < 3; ++ch) C[ch] = acc[ch] + T * cfg.bg[ch];
   *T_out = T;
-  *ambiguous = amb;
   if (signature) *signature = sig;
 }
 
-// Render a list of pixels (pix[2*j] = px, pix[2*j+1] = py).  out_rgb [n_pix,3],
+// ---------------------------------------------------------------------------
+// Mode B: the same composite, with each pixel's candidate list restricted to
+// the Gaussians whose footprint reaches it.  A Gaussian can have
+// alpha >= tau_s = alpha_min (1 - kScatterSlack) only inside the ellipse
+// d^T A d <= rho_s^2 with rho_s^2 = 2 ln(kappa o_max comp / tau_s) (the
+// conservative footprint, whose bound holds for any threshold), so every
+// pair left out has alpha < tau_s: mode A skips it and flags nothing
+// (tol_a < kScatterSlack), and mode B's result equals mode A's bit for bit.
+// ---------------------------------------------------------------------------
+constexpr double kScatterSlack = 1e-2;
+
+struct Scatter {
+  int width = 0, height = 0;
+  std::vector<int64_t> row_off;  // [height + 1]
+  std::vector<int32_t> id;       // per row, the Gaussians reaching it, in depth order
+  std::vector<int32_t> x0, x1;   // columns of their pixel centres in the row (inclusive)
+};
+
+// Rows and columns of pixel centres inside a Gaussian's scatter ellipse.
+struct Ellipse { double a, b, c, rho2, mx, my; bool on; };
+
+static Ellipse scatter_ellipse(const double* r, const OrConfig& cfg) {
+  Ellipse e{r[R_A], r[R_B], r[R_C], 0.0, r[R_MX], r[R_MY], false};
+  const double tau = cfg.alpha_min * (1.0 - kScatterSlack);
+  const double omax = r[R_COMP] * std::max(r[R_O1], r[R_O2]);
+  if (2.0 * omax < tau) return e;
+  const double rho0sq = 2.0 * std::log(2.0 * omax / tau);
+  const double bx = r[R_BX], by = r[R_BY];
+  const double bsb = bx * bx * r[R_DXX] + 2.0 * bx * by * r[R_DXY] + by * by * r[R_DYY];
+  const double kappa = 1.0 + std::erf(std::sqrt(rho0sq * bsb) / std::sqrt(2.0));
+  if (kappa * omax < tau) return e;
+  e.rho2 = 2.0 * std::log(kappa * omax / tau) * (1.0 + 1e-9);
+  e.on = true;
+  return e;
+}
+
+static void ellipse_rows(const Ellipse& e, int height, int* y0, int* y1) {
+  const double D = e.a * e.c - e.b * e.b;
+  const double h = std::sqrt(e.a * e.rho2 / D) + 1e-7;
+  *y0 = (int)std::max(0.0, std::ceil(e.my - h - 0.5));
+  *y1 = (int)std::min((double)height - 1.0, std::floor(e.my + h - 0.5));
+}
+
+static bool ellipse_cols(const Ellipse& e, int py, int width, int* x0, int* x1) {
+  const double D = e.a * e.c - e.b * e.b;
+  const double dy = py + 0.5 - e.my;
+  const double disc = e.a * e.rho2 - D * dy * dy;
+  if (disc < 0.0) return false;
+  const double s = std::sqrt(disc);
+  const double lo = (-e.b * dy - s) / e.a - 1e-7, hi = (-e.b * dy + s) / e.a + 1e-7;
+  const double c0 = std::max(0.0, std::ceil(e.mx + lo - 0.5));
+  const double c1 = std::min((double)width - 1.0, std::floor(e.mx + hi - 0.5));
+  if (c0 > c1) return false;
+  *x0 = (int)c0;
+  *x1 = (int)c1;
+  return true;
+}
+
+// Row lists in depth order: the Gaussians are split into contiguous chunks of
+// the depth order, each thread counts and then fills its chunk's entries at
+// offsets that keep the chunks in order.
+static void build_scatter(const std::vector<int32_t>& order, const double* rec, const OrConfig& cfg, int width,
+                          int height, Scatter* s) {
+  s->width = width;
+  s->height = height;
+  const int64_t m = (int64_t)order.size();
+  const int nt = std::max(1, or_num_threads_impl());
+  std::vector<int64_t> cnt((size_t)nt * (height + 1), 0);
+#pragma omp parallel num_threads(nt)
+  {
+    int t = 0;
+#ifdef _OPENMP
+    t = omp_get_thread_num();
+#endif
+    const int64_t lo = m * t / nt, hi = m * (t + 1) / nt;
+    int64_t* c = cnt.data() + (size_t)t * (height + 1);
+    for (int64_t j = lo; j < hi; ++j) {
+      const Ellipse e = scatter_ellipse(rec + (size_t)NREC * order[j], cfg);
+      if (!e.on) continue;
+      int y0, y1, a, b;
+      ellipse_rows(e, height, &y0, &y1);
+      for (int y = y0; y <= y1; ++y)
+        if (ellipse_cols(e, y, width, &a, &b)) ++c[y];
+    }
+  }
+  s->row_off.assign(height + 1, 0);
+  std::vector<int64_t> start((size_t)nt * (height + 1), 0);
+  int64_t tot = 0;
+  for (int y = 0; y < height; ++y) {
+    s->row_off[y] = tot;
+    for (int t = 0; t < nt; ++t) {
+      start[(size_t)t * (height + 1) + y] = tot;
+      tot += cnt[(size_t)t * (height + 1) + y];
+    }
+  }
+  s->row_off[height] = tot;
+  s->id.resize(tot);
+  s->x0.resize(tot);
+  s->x1.resize(tot);
+#pragma omp parallel num_threads(nt)
+  {
+    int t = 0;
+#ifdef _OPENMP
+    t = omp_get_thread_num();
+#endif
+    const int64_t lo = m * t / nt, hi = m * (t + 1) / nt;
+    int64_t* w = start.data() + (size_t)t * (height + 1);
+    for (int64_t j = lo; j < hi; ++j) {
+      const Ellipse e = scatter_ellipse(rec + (size_t)NREC * order[j], cfg);
+      if (!e.on) continue;
+      int y0, y1, a, b;
+      ellipse_rows(e, height, &y0, &y1);
+      for (int y = y0; y <= y1; ++y)
+        if (ellipse_cols(e, y, width, &a, &b)) {
+          const int64_t q = w[y]++;
+          s->id[q] = order[j];
+          s->x0[q] = a;
+          s->x1[q] = b;
+        }
+    }
+  }
+}
+
+// Per-pixel candidate lists of one row (a counting sort of the row's entries
+// by column keeps their depth order).
+struct RowLists {
+  std::vector<int64_t> off;  // [width + 1]
+  std::vector<int32_t> id;
+};
+
+static void row_lists(const Scatter& s, int y, RowLists* L) {
+  const int W = s.width;
+  L->off.assign(W + 1, 0);
+  const int64_t b = s.row_off[y], e = s.row_off[y + 1];
+  for (int64_t q = b; q < e; ++q)
+    for (int x = s.x0[q]; x <= s.x1[q]; ++x) ++L->off[x + 1];
+  for (int x = 0; x < W; ++x) L->off[x + 1] += L->off[x];
+  L->id.resize(L->off[W]);
+  std::vector<int64_t> w(L->off.begin(), L->off.end() - 1);
+  for (int64_t q = b; q < e; ++q)
+    for (int x = s.x0[q]; x <= s.x1[q]; ++x) L->id[w[x]++] = s.id[q];
+}
+
+// ---------------------------------------------------------------------------
+// Backward of one pixel (Appendix "Backward Pass"): for the blended list bl,
+// dC/dalpha_k = c_k T_k - (sum_{i>k} c_i alpha_i T_i + T_N bg) / (1 - alpha_k),
+// the plain derivative of C = sum_i c_i alpha_i T_i + T_N bg, zero where
+// alpha_max clamped alpha; dalpha/d(record) by dual numbers.  Adds into
+// grad[n, NDIFF]; scale (optional) receives, per record entry, the sum over
+// pairs of the magnitudes of the terms a rounding error in any factor
+// scales with; slack (optional), per entry, the magnitude of the
+// alpha-path term of every pair whose clamp decision lies within tolerance.
+// ---------------------------------------------------------------------------
+static void backward_pixel(const std::vector<Blend>& bl, double T_final, const double* g, const double* rec,
+                           const OrConfig& cfg, int px, int py, double* grad, double* scale, double* slack) {
+  const int nb = (int)bl.size();
+  std::vector<double> suffix(3 * (nb + 1), 0.0);  // sum_{i>k} c_i alpha_i T_i + T_N bg
+  std::vector<double> sabs(3 * (nb + 1), 0.0);    // the same with magnitudes
+  for (int ch = 0; ch < 3; ++ch) {
+    suffix[3 * nb + ch] = T_final * cfg.bg[ch];
+    sabs[3 * nb + ch] = std::fabs(T_final * cfg.bg[ch]);
+  }
+  for (int k = nb - 1; k >= 0; --k) {
+    const double* r = rec + (size_t)NREC * bl[k].id;
+    for (int ch = 0; ch < 3; ++ch) {
+      const double t = r[R_CR + ch] * bl[k].alpha * bl[k].T;
+      suffix[3 * k + ch] = suffix[3 * (k + 1) + ch] + t;
+      sabs[3 * k + ch] = sabs[3 * (k + 1) + ch] + std::fabs(t);
+    }
+  }
+  const double x = px + 0.5, y = py + 0.5;
+  for (int k = 0; k < nb; ++k) {
+    const int32_t id = bl[k].id;
+    const double* r = rec + (size_t)NREC * id;
+    double* out = grad + (size_t)NDIFF * id;
+    for (int ch = 0; ch < 3; ++ch) {
+      out[R_CR + ch] += g[ch] * bl[k].alpha * bl[k].T;
+      if (scale) scale[(size_t)NDIFF * id + R_CR + ch] += std::fabs(g[ch] * bl[k].alpha * bl[k].T);
+    }
+    if (bl[k].clamped && !(bl[k].clamp_near && slack)) continue;
+    double dLda = 0.0, wabs = 0.0;
+    for (int ch = 0; ch < 3; ++ch) {
+      dLda += g[ch] * (r[R_CR + ch] * bl[k].T - suffix[3 * (k + 1) + ch] / (1.0 - bl[k].alpha));
+      wabs += std::fabs(g[ch]) * (std::fabs(r[R_CR + ch]) * bl[k].T + sabs[3 * (k + 1) + ch] / (1.0 - bl[k].alpha));
+    }
+    Dual<11> rr[NDIFF];
+    for (int q = 0; q < NDIFF; ++q) rr[q] = Dual<11>(r[q]);
+    for (int q = 0; q < 11; ++q) rr[q].d[q] = 1.0;  // R_MX..R_UY are entries 0..10
+    Dual<11> a = alpha_raw<Dual<11>>(rr, x, y);
+    if (bl[k].clamp_near && slack)
+      for (int q = 0; q < 11; ++q) slack[(size_t)NDIFF * id + q] += std::fabs(dLda * a.d[q]);
+    if (bl[k].clamped) continue;
+    for (int q = 0; q < 11; ++q) out[q] += dLda * a.d[q];
+    if (scale)
+      for (int q = 0; q < 11; ++q) scale[(size_t)NDIFF * id + q] += wabs * std::fabs(a.d[q]);
+  }
+}
+
+// Attribute-gradient outputs (same layouts as the scene; split may be null).
+struct OrGradsOut {
+  double* means;
+  double* log_scales;
+  double* quats;
+  double* opac;
+  double* skew;
+  double* split;
+  double* sh;
+};
+
+// Chain rule from the record gradients d2[n, NDIFF] to every attribute, by
+// dual numbers through the projection; colour is linear in the SH
+// coefficients.  With d2_scale / d2_slack, the same map applied to their
+// magnitudes (|Jacobian| times the entry) goes to scale / slack; a colour
+// channel whose pre-activation lies within 1e-5 of the clamp at zero adds
+// its whole term to slack (the other renderer's clamp may differ).
+static void chain_to_attributes(const OrScene& s, const OrCamera& cam, const OrConfig& cfg, const int32_t* visible,
+                                const double* d2, const double* d2_scale, const double* d2_slack,
+                                const OrGradsOut& G, const OrGradsOut* S, const OrGradsOut* L) {
+  const int64_t n = s.n;
+  const int K = sh_count(s.sh_degree);
+  const int nop = s.two_opac ? 2 : 1;
+  auto zero = [&](const OrGradsOut& o, int64_t i) {
+    for (int k = 0; k < 3; ++k) { o.means[3 * i + k] = 0; o.log_scales[3 * i + k] = 0; o.skew[3 * i + k] = 0; }
+    for (int k = 0; k < 4; ++k) o.quats[4 * i + k] = 0;
+    for (int k = 0; k < nop; ++k) o.opac[nop * i + k] = 0;
+    if (o.split) for (int k = 0; k < 3; ++k) o.split[3 * i + k] = 0;
+    for (int k = 0; k < 3 * K; ++k) o.sh[(size_t)3 * K * i + k] = 0;
+  };
+  auto store = [&](const OrGradsOut& o, int64_t i, const double* gth) {
+    for (int k = 0; k < 3; ++k) o.means[3 * i + k] = gth[P_MU + k];
+    for (int k = 0; k < 3; ++k) o.log_scales[3 * i + k] = gth[P_LS + k];
+    for (int k = 0; k < 4; ++k) o.quats[4 * i + k] = gth[P_Q + k];
+    for (int k = 0; k < nop; ++k) o.opac[nop * i + k] = gth[P_L + k];
+    for (int k = 0; k < 3; ++k) o.skew[3 * i + k] = gth[P_ETA + k];
+    if (o.split) for (int k = 0; k < 3; ++k) o.split[3 * i + k] = gth[P_D + k];
+  };
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; ++i) {
+    zero(G, i);
+    if (S) zero(*S, i);
+    if (L) zero(*L, i);
+    const double* gi = d2 + (size_t)NDIFF * i;
+    bool any = false;
+    for (int q = 0; q < NDIFF; ++q) any |= gi[q] != 0.0;
+    if (d2_slack)
+      for (int q = 0; q < NDIFF; ++q) any |= d2_slack[(size_t)NDIFF * i + q] != 0.0;
+    if (!any || !visible[i]) continue;
+    double th[NPARAM];
+    load_theta(s, i, th);
+    Dual<NPARAM> thd[NPARAM];
+    for (int q = 0; q < NPARAM; ++q) { thd[q] = Dual<NPARAM>(th[q]); thd[q].d[q] = 1.0; }
+    Dual<NPARAM> r[NREC];
+    const double* shi = s.sh + (size_t)3 * K * i;
+    project<Dual<NPARAM>>(thd, s.two_opac, s.split != nullptr, shi, s.sh_degree, cam, cfg, r);
+    double gth[NPARAM] = {0}, sth[NPARAM] = {0}, lth[NPARAM] = {0};
+    for (int q = 0; q < NDIFF; ++q)
+      for (int p = 0; p < NPARAM; ++p) {
+        gth[p] += gi[q] * r[q].d[p];
+        if (S) sth[p] += d2_scale[(size_t)NDIFF * i + q] * std::fabs(r[q].d[p]);
+        if (L) lth[p] += d2_slack[(size_t)NDIFF * i + q] * std::fabs(r[q].d[p]);
+      }
+    // colour channels near the clamp at zero: the pre-activation's derivative
+    double dv[3] = {th[0] - cam.campos[0], th[1] - cam.campos[1], th[2] - cam.campos[2]};
+    double dl = std::sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+    double Y[16];
+    sh_basis<double>(s.sh_degree, dv[0] / dl, dv[1] / dl, dv[2] / dl, Y);
+    double pre[3];
+    for (int ch = 0; ch < 3; ++ch) {
+      pre[ch] = 0.5;
+      for (int k = 0; k < K; ++k) pre[ch] += shi[3 * k + ch] * Y[k];
+    }
+    const bool near0 = std::fabs(pre[0]) < 1e-5 || std::fabs(pre[1]) < 1e-5 || std::fabs(pre[2]) < 1e-5;
+    if (L && near0) {
+      Dual<NPARAM> u[NREC];
+      project<Dual<NPARAM>>(thd, s.two_opac, s.split != nullptr, shi, s.sh_degree, cam, cfg, u, false);
+      for (int ch = 0; ch < 3; ++ch)
+        if (std::fabs(pre[ch]) < 1e-5)
+          for (int p = 0; p < NPARAM; ++p) lth[p] += std::fabs(gi[R_CR + ch] * u[R_CR + ch].d[p]);
+    }
+    store(G, i, gth);
+    if (S) store(*S, i, sth);
+    if (L) store(*L, i, lth);
+    for (int ch = 0; ch < 3; ++ch) {
+      const bool amb = std::fabs(pre[ch]) < 1e-5;
+      for (int k = 0; k < K; ++k) {
+        const size_t o = (size_t)3 * K * i + 3 * k + ch;
+        if (pre[ch] >= 0.0) G.sh[o] = Y[k] * gi[R_CR + ch];
+        if (S) S->sh[o] = std::fabs(Y[k]) * d2_scale[(size_t)NDIFF * i + R_CR + ch];
+        if (L && amb) L->sh[o] = std::fabs(Y[k] * gi[R_CR + ch]);
+      }
+    }
+  }
+}
+
+// Pixel-parallel accumulation of record gradients: one [n, NDIFF] array per
+// thread for each requested output, summed at the end.
+struct Accum {
+  int64_t n;
+  bool want_scale, want_slack;
+  std::vector<std::vector<double>> g, s, l;
+  Accum(int64_t n_, int nt, bool ws, bool wl) : n(n_), want_scale(ws), want_slack(wl), g(nt), s(nt), l(nt) {}
+  void init(int t) {
+    g[t].assign((size_t)n * NDIFF, 0.0);
+    if (want_scale) s[t].assign((size_t)n * NDIFF, 0.0);
+    if (want_slack) l[t].assign((size_t)n * NDIFF, 0.0);
+  }
+  void reduce(double* d2, double* d2s, double* d2l) {
+    std::fill(d2, d2 + (size_t)n * NDIFF, 0.0);
+    if (d2s) std::fill(d2s, d2s + (size_t)n * NDIFF, 0.0);
+    if (d2l) std::fill(d2l, d2l + (size_t)n * NDIFF, 0.0);
+    for (size_t t = 0; t < g.size(); ++t) {
+      if (g[t].empty()) continue;
+#pragma omp parallel for schedule(static)
+      for (int64_t q = 0; q < n * NDIFF; ++q) {
+        d2[q] += g[t][q];
+        if (d2s) d2s[q] += s[t][q];
+        if (d2l) d2l[q] += l[t][q];
+      }
+    }
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+// Render a list of pixels (pix[2*j] = px, pix[2*j+1] = py) by brute force
+// over every visible Gaussian in depth order (mode A).  out_rgb [n_pix,3],
 // out_T [n_pix], out_last [n_pix] (id of the last blended Gaussian or -1),
-// out_count [n_pix] (number blended), out_amb [n_pix], out_sig [n_pix] (a
-// hash of which Gaussians were blended, which were clamped and whether the
-// transmittance stop fired; may be null).
+// out_count [n_pix] (number blended), out_amb [n_pix] (a pair within tol_a
+// (relative to alpha_min) of the gate or within tol_t (relative to t_stop)
+// of the stop), out_sig [n_pix] (a hash of which Gaussians were blended,
+// which were clamped and whether the transmittance stop fired; may be null).
 void or_render_pixels(const OrCamera* cam, const OrConfig* cfg, int64_t n, const double* rec,
                       const uint32_t* depth_bits, const int32_t* visible, int64_t n_pix, const int32_t* pix,
-                      double tol_alpha, double tol_t, double* out_rgb, double* out_T, int64_t* out_last,
+                      double tol_a, double tol_t, double* out_rgb, double* out_T, int64_t* out_last,
                       int32_t* out_count, int32_t* out_amb, uint64_t* out_sig) {
   (void)cam;
-  std::vector<int64_t> order = depth_order(n, depth_bits, visible);
+  const std::vector<int32_t> order = depth_order(n, depth_bits, visible);
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t j = 0; j < n_pix; ++j) {
     std::vector<Blend> bl;
-    int amb;
-    composite_pixel(order, rec, *cfg, pix[2 * j], pix[2 * j + 1], tol_alpha, tol_t, out_rgb + 3 * j,
-                    out_T + j, &amb, &bl, out_sig ? out_sig + j : nullptr);
-    out_amb[j] = amb;
+    PixelDecisions dec;
+    composite_list(order.data(), (int64_t)order.size(), nullptr, 0, rec, *cfg, pix[2 * j], pix[2 * j + 1], tol_a,
+                   tol_t, out_rgb + 3 * j, out_T + j, &bl, &dec, out_sig ? out_sig + j : nullptr);
+    out_amb[j] = dec.ambiguous;
     out_count[j] = (int32_t)bl.size();
     out_last[j] = bl.empty() ? -1 : bl.back().id;
   }
 }
 
-// Gradients of L = sum_pixels sum_ch dL_dC[pixel, ch] * C[pixel, ch] over
-// the listed pixels (dL_dC [n_pix,3]).
-//  * d2 [n, NDIFF]: dL/d(record) — the 2D quantities of Alg. 2;
-//  * the attribute gradients (same layouts as the inputs; split may be null).
-// dC/dalpha_k = c_k T_k - (sum_{i>k} c_i alpha_i T_i + T_N bg) / (1 - alpha_k),
-// the plain derivative of C = sum_i c_i alpha_i T_i + T_N bg; zero where the
-// clamp alpha_max was active.  Everything else by dual numbers.
-void or_render_backward(const OrScene* s, const OrCamera* cam, const OrConfig* cfg, const double* rec,
-                        const uint32_t* depth_bits, const int32_t* visible, int64_t n_pix, const int32_t* pix,
-                        const double* dL_dC, double* d2, double* g_means, double* g_log_scales,
-                        double* g_quats, double* g_opac, double* g_skew, double* g_split, double* g_sh) {
-  const int64_t n = s->n;
-  std::vector<int64_t> order = depth_order(n, depth_bits, visible);
-  std::fill(d2, d2 + (size_t)n * NDIFF, 0.0);
-  int nthreads = or_num_threads();
-  std::vector<std::vector<double>> acc(nthreads);
+// Whole frame, row-major pixels (mode B: per-pixel lists of the Gaussians
+// whose footprint reaches the pixel, in depth order).  Outputs as
+// or_render_pixels, [H*W] per pixel.  With gpu_off non-null, the gate and
+// stop decisions are those of another renderer that blended, at pixel p,
+// gpu_ids[gpu_off[p] .. gpu_off[p+1]) in order: out_status [H*W] (null
+// allowed otherwise) receives each pixel's PixelDecisions status, and stats
+// (null allowed) [8] = pixels with a flipped decision, flipped gate
+// decisions, flipped stop decisions, largest gate margin, largest stop
+// margin, inadmissible pixels, candidate pairs, pixels with an ambiguous pair.
+// With list_off non-null (the prefix sums of an earlier call's out_count),
+// the ids of the Gaussians each pixel blended go to list_ids[list_off[p]..).
+void or_render_frame(const OrCamera* cam, const OrConfig* cfg, int64_t n, const double* rec,
+                     const uint32_t* depth_bits, const int32_t* visible, double tol_a, double tol_t,
+                     const int64_t* gpu_off, const int32_t* gpu_ids, double* out_rgb, double* out_T,
+                     int64_t* out_last, int32_t* out_count, int32_t* out_amb, int32_t* out_status,
+                     double* stats, const int64_t* list_off, int32_t* list_ids) {
+  const int W = cam->width, H = cam->height;
+  const std::vector<int32_t> order = depth_order(n, depth_bits, visible);
+  Scatter sc;
+  build_scatter(order, rec, *cfg, W, H, &sc);
+  double st[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma omp parallel
   {
-    int tid = 0;
-#ifdef _OPENMP
-    tid = omp_get_thread_num();
-#endif
-    std::vector<double>& mine = acc[tid];
-    mine.assign((size_t)n * NDIFF, 0.0);
-#pragma omp for schedule(dynamic, 8)
-    for (int64_t j = 0; j < n_pix; ++j) {
-      const double* g = dL_dC + 3 * j;
-      if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0) continue;
-      std::vector<Blend> bl;
-      double C[3], T_final;
-      int amb;
-      composite_pixel(order, rec, *cfg, pix[2 * j], pix[2 * j + 1], 0.0, 0.0, C, &T_final, &amb, &bl);
-      const int nb = (int)bl.size();
-      // suffix[k] = sum_{i>k} c_i alpha_i T_i + T_N bg  (per channel)
-      std::vector<double> suffix(3 * (nb + 1), 0.0);
-      for (int ch = 0; ch < 3; ++ch) suffix[3 * nb + ch] = T_final * cfg->bg[ch];
-      for (int k = nb - 1; k >= 0; --k) {
-        const double* r = rec + (size_t)NREC * bl[k].id;
-        for (int ch = 0; ch < 3; ++ch)
-          suffix[3 * k + ch] = suffix[3 * (k + 1) + ch] + r[R_CR + ch] * bl[k].alpha * bl[k].T;
-      }
-      const double x = pix[2 * j] + 0.5, y = pix[2 * j + 1] + 0.5;
-      for (int k = 0; k < nb; ++k) {
-        const int64_t id = bl[k].id;
-        const double* r = rec + (size_t)NREC * id;
-        double* out = mine.data() + (size_t)NDIFF * id;
-        for (int ch = 0; ch < 3; ++ch) out[R_CR + ch] += g[ch] * bl[k].alpha * bl[k].T;
-        if (bl[k].clamped) continue;
-        double dLda = 0.0;
-        for (int ch = 0; ch < 3; ++ch)
-          dLda += g[ch] * (r[R_CR + ch] * bl[k].T - suffix[3 * (k + 1) + ch] / (1.0 - bl[k].alpha));
-        Dual<11> rr[NDIFF];
-        for (int q = 0; q < NDIFF; ++q) rr[q] = Dual<11>(r[q]);
-        for (int q = 0; q < 11; ++q) rr[q].d[q] = 1.0;  // R_MX..R_UY are entries 0..10
-        Dual<11> a = alpha_raw<Dual<11>>(rr, x, y);
-        for (int q = 0; q < 11; ++q) out[q] += dLda * a.d[q];
+    double mine[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    RowLists L;
+    std::vector<Blend> bl;
+#pragma omp for schedule(dynamic, 1)
+    for (int y = 0; y < H; ++y) {
+      row_lists(sc, y, &L);
+      mine[6] += (double)L.id.size();
+      for (int x = 0; x < W; ++x) {
+        const int64_t p = (int64_t)y * W + x;
+        bl.clear();
+        PixelDecisions dec;
+        const int32_t* gp = gpu_off ? gpu_ids + gpu_off[p] : nullptr;
+        const int64_t ng = gpu_off ? gpu_off[p + 1] - gpu_off[p] : 0;
+        composite_list(L.id.data() + L.off[x], L.off[x + 1] - L.off[x], gp, ng, rec, *cfg, x, y, tol_a, tol_t,
+                       out_rgb + 3 * p, out_T + p, &bl, &dec);
+        out_amb[p] = dec.ambiguous;
+        out_count[p] = (int32_t)bl.size();
+        out_last[p] = bl.empty() ? -1 : bl.back().id;
+        if (list_off)
+          for (size_t k = 0; k < bl.size(); ++k) list_ids[list_off[p] + (int64_t)k] = bl[k].id;
+        if (out_status) out_status[p] = dec.status;
+        mine[0] += (dec.flips_gate + dec.flips_stop) > 0;
+        mine[1] += dec.flips_gate;
+        mine[2] += dec.flips_stop;
+        mine[3] = std::max(mine[3], dec.margin_gate);
+        mine[4] = std::max(mine[4], dec.margin_stop);
+        mine[5] += dec.status != 0;
+        mine[7] += dec.ambiguous;
       }
     }
+#pragma omp critical
+    {
+      for (int k : {0, 1, 2, 5, 6, 7}) st[k] += mine[k];
+      st[3] = std::max(st[3], mine[3]);
+      st[4] = std::max(st[4], mine[4]);
+    }
   }
-  for (int t = 0; t < nthreads; ++t)
-    if (!acc[t].empty())
-      for (size_t q = 0; q < (size_t)n * NDIFF; ++q) d2[q] += acc[t][q];
+  if (stats) std::copy(st, st + 8, stats);
+}
 
-  // chain through the projection
-  const int K = sh_count(s->sh_degree);
-  const int nop = s->two_opac ? 2 : 1;
-#pragma omp parallel for schedule(dynamic, 64)
-  for (int64_t i = 0; i < n; ++i) {
-    for (int k = 0; k < 3; ++k) { g_means[3 * i + k] = 0; g_log_scales[3 * i + k] = 0; g_skew[3 * i + k] = 0; }
-    for (int k = 0; k < 4; ++k) g_quats[4 * i + k] = 0;
-    for (int k = 0; k < nop; ++k) g_opac[nop * i + k] = 0;
-    if (g_split) for (int k = 0; k < 3; ++k) g_split[3 * i + k] = 0;
-    for (int k = 0; k < 3 * K; ++k) g_sh[(size_t)3 * K * i + k] = 0;
-    const double* gi = d2 + (size_t)NDIFF * i;
-    bool any = false;
-    for (int q = 0; q < NDIFF; ++q) any |= gi[q] != 0.0;
-    if (!any || !visible[i]) continue;
-    double th[NPARAM];
-    load_theta(*s, i, th);
-    Dual<NPARAM> thd[NPARAM];
-    for (int q = 0; q < NPARAM; ++q) { thd[q] = Dual<NPARAM>(th[q]); thd[q].d[q] = 1.0; }
-    Dual<NPARAM> r[NREC];
-    const double* shi = s->sh + (size_t)3 * K * i;
-    project<Dual<NPARAM>>(thd, s->two_opac, s->split != nullptr, shi, s->sh_degree, *cam, *cfg, r);
-    double gth[NPARAM] = {0};
-    for (int q = 0; q < NDIFF; ++q)
-      for (int p = 0; p < NPARAM; ++p) gth[p] += gi[q] * r[q].d[p];
-    for (int k = 0; k < 3; ++k) g_means[3 * i + k] = gth[P_MU + k];
-    for (int k = 0; k < 3; ++k) g_log_scales[3 * i + k] = gth[P_LS + k];
-    for (int k = 0; k < 4; ++k) g_quats[4 * i + k] = gth[P_Q + k];
-    for (int k = 0; k < nop; ++k) g_opac[nop * i + k] = gth[P_L + k];
-    for (int k = 0; k < 3; ++k) g_skew[3 * i + k] = gth[P_ETA + k];
-    if (g_split) for (int k = 0; k < 3; ++k) g_split[3 * i + k] = gth[P_D + k];
-    // colour is linear in the coefficients: dL/dsh_k = Y_k dL/drgb where unclamped
-    double dv[3] = {th[0] - cam->campos[0], th[1] - cam->campos[1], th[2] - cam->campos[2]};
-    double dl = std::sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
-    double Y[16];
-    sh_basis<double>(s->sh_degree, dv[0] / dl, dv[1] / dl, dv[2] / dl, Y);
-    for (int ch = 0; ch < 3; ++ch) {
-      double pre = 0.5;
-      for (int k = 0; k < K; ++k) pre += shi[3 * k + ch] * Y[k];
-      if (pre < 0.0) continue;
-      for (int k = 0; k < K; ++k) g_sh[(size_t)3 * K * i + 3 * k + ch] = Y[k] * gi[R_CR + ch];
+// Gradients of L = sum_pixels sum_ch dL_dC[pixel, ch] * C[pixel, ch].
+//  * mode A (pix non-null): over the listed pixels, dL_dC [n_pix, 3], brute
+//    force over every visible Gaussian; mode B (pix null): every pixel of the
+//    frame, row-major, dL_dC [H*W, 3], per-pixel footprint lists;
+//  * gpu_off / gpu_ids (optional, indexed like dL_dC's rows): the gate and
+//    stop decisions of another renderer, replayed as in or_render_frame
+//    (inadmissible pixels are counted in *n_bad and contribute nothing);
+//  * d2 [n, NDIFF]: dL/d(record), the 2D quantities of Alg. 2; d2_scale and
+//    d2_slack (optional): see backward_pixel;
+//  * G: the attribute gradients; S, L (optional): scale and slack mapped
+//    through the projection (see chain_to_attributes).
+// tol_a: the relative tolerance of the alpha_max clamp (slack) and, with a
+// replay, of the gate; tol_t: of the stop (replay only).
+void or_render_backward(const OrScene* s, const OrCamera* cam, const OrConfig* cfg, const double* rec,
+                        const uint32_t* depth_bits, const int32_t* visible, int64_t n_pix, const int32_t* pix,
+                        const double* dL_dC, const int64_t* gpu_off, const int32_t* gpu_ids, double tol_a,
+                        double tol_t, double* d2, double* d2_scale, double* d2_slack, const OrGradsOut* G,
+                        const OrGradsOut* S, const OrGradsOut* L, int64_t* n_bad) {
+  const int64_t n = s->n;
+  const int W = cam->width, H = cam->height;
+  const std::vector<int32_t> order = depth_order(n, depth_bits, visible);
+  const bool frame = pix == nullptr;
+  Scatter sc;
+  if (frame) build_scatter(order, rec, *cfg, W, H, &sc);
+  const int nt = or_num_threads_impl();
+  Accum acc(n, nt, d2_scale != nullptr, d2_slack != nullptr);
+  int64_t bad = 0;
+#pragma omp parallel num_threads(nt) reduction(+ : bad)
+  {
+    int t = 0;
+#ifdef _OPENMP
+    t = omp_get_thread_num();
+#endif
+    acc.init(t);
+    double* ga = acc.g[t].data();
+    double* sa = acc.want_scale ? acc.s[t].data() : nullptr;
+    double* la = acc.want_slack ? acc.l[t].data() : nullptr;
+    std::vector<Blend> bl;
+    RowLists Lr;
+    auto one = [&](int64_t p, int px, int py, const int32_t* ids, int64_t m) {
+      const double* g = dL_dC + 3 * p;
+      if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0) return;
+      bl.clear();
+      PixelDecisions dec;
+      double C[3], T_final;
+      const int32_t* gp = gpu_off ? gpu_ids + gpu_off[p] : nullptr;
+      const int64_t ng = gpu_off ? gpu_off[p + 1] - gpu_off[p] : 0;
+      composite_list(ids, m, gp, ng, rec, *cfg, px, py, tol_a, tol_t, C, &T_final, &bl, &dec);
+      if (dec.status != 0) { ++bad; return; }
+      backward_pixel(bl, T_final, g, rec, *cfg, px, py, ga, sa, la);
+    };
+    if (frame) {
+#pragma omp for schedule(dynamic, 1)
+      for (int y = 0; y < H; ++y) {
+        row_lists(sc, y, &Lr);
+        for (int x = 0; x < W; ++x)
+          one((int64_t)y * W + x, x, y, Lr.id.data() + Lr.off[x], Lr.off[x + 1] - Lr.off[x]);
+      }
+    } else {
+#pragma omp for schedule(dynamic, 8)
+      for (int64_t j = 0; j < n_pix; ++j)
+        one(j, pix[2 * j], pix[2 * j + 1], order.data(), (int64_t)order.size());
     }
   }
+  acc.reduce(d2, d2_scale, d2_slack);
+  if (n_bad) *n_bad = bad;
+  chain_to_attributes(*s, *cam, *cfg, visible, d2, d2_scale, d2_slack, *G, S, L);
 }
 
 // Tile keys of one view: for each visible Gaussian, in index order, one

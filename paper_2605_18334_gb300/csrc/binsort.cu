@@ -723,7 +723,8 @@ static int run_passes(const KEY* keys_in, const uint32_t* vals_in, KEY* const* k
                       const unsigned long long* count_dev, unsigned long long count, unsigned long long parts,
                       int passes, int key_bits, const int* run, Status* status, int spin_limit,
                       cudaStream_t st, uint2* ranges = nullptr, unsigned long long n_tiles = 0,
-                      const int* buf_ids = nullptr, const uint32_t* last_gather = nullptr) {
+                      const int* buf_ids = nullptr, const uint32_t* last_gather = nullptr,
+                      cudaError_t* first_error = nullptr) {
   int cur = -1;  // -1: still the input
   int last = -1;
   for (int p = 0; p < passes; ++p)
@@ -753,7 +754,9 @@ static int run_passes(const KEY* keys_in, const uint32_t* vals_in, KEY* const* k
     pa.n_tiles = n_tiles;
     pa.sorted_buf = (p == last && buf_ids) ? buf_ids[out] : 0;
     pa.out_gather = p == last ? last_gather : nullptr;
-    launch_pdl(onesweep_kernel<KEY>, dim3((unsigned)parts), dim3(kSortThreads), sizeof(SortSmem<KEY>), st, pa);
+    const cudaError_t e =
+        launch_pdl(onesweep_kernel<KEY>, dim3((unsigned)parts), dim3(kSortThreads), sizeof(SortSmem<KEY>), st, pa);
+    if (first_error && *first_error == cudaSuccess) *first_error = e;
     count_launches(1);
     cur = out;
   }
@@ -1034,26 +1037,12 @@ __global__ void noalloc_reset_kernel(unsigned char* scratch, unsigned long long 
   }
 }
 
-// Device address of the scratch array for the current device, looked up once
-// per device (the first call on a device does it).
+// Device address of the scratch array on the current device, looked up on
+// every call (a cudaDeviceReset reloads the module, which can move it).
 static unsigned char* noalloc_scratch_address(cudaError_t* err) {
-  static std::mutex mu;
-  static unsigned char* addr[64] = {nullptr};
-  int dev = 0;
-  *err = cudaGetDevice(&dev);
-  if (*err != cudaSuccess) return nullptr;
-  if (dev < 0 || dev >= 64) {
-    *err = cudaErrorInvalidDevice;
-    return nullptr;
-  }
-  std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
-    void* p = nullptr;
-    *err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (*err != cudaSuccess) return nullptr;
-    addr[dev] = static_cast<unsigned char*>(p);
-  }
-  return addr[dev];
+  void* p = nullptr;
+  *err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  return *err == cudaSuccess ? static_cast<unsigned char*>(p) : nullptr;
 }
 
 }  // namespace sr
@@ -1082,10 +1071,18 @@ extern "C" sr_status sr_sort_keys_noalloc(const uint64_t* keys_in, const uint32_
   u64* tmp_keys = reinterpret_cast<u64*>(base + kNoallocStatusBytes + kNoallocHistBytes + kNoallocLookbackBytes);
   uint32_t* tmp_vals = reinterpret_cast<uint32_t*>(base + kNoallocStatusBytes + kNoallocHistBytes +
                                                    kNoallocLookbackBytes + kNoallocKeyBytes);
-  noalloc_reset_kernel<<<clamp_grid((un * passes + 255) / 256, sms, 4), 256, 0, st>>>(base, un, passes);
-  histogram_kernel<u64><<<clamp_grid((un + 255) / 256, sms, 4), 256, 0, st>>>(
-      reinterpret_cast<const u64*>(keys_in), nullptr, un, passes, hist);
-  hist_scan_kernel<<<passes, 256, 0, st>>>(hist, status->pass_trivial, nullptr, un);
+  // each launch's own result decides SR_ERR_CUDA (no cudaGetLastError, which
+  // would report, and clear, an error some earlier call left behind)
+  e = launch_plain(noalloc_reset_kernel, dim3(clamp_grid((un * passes + 255) / 256, sms, 4)), dim3(256), 0, st, base,
+                   un, passes);
+  if (e == cudaSuccess)
+    e = launch_pdl(histogram_kernel<u64>, dim3(clamp_grid((un + 255) / 256, sms, 4)), dim3(256), 0, st,
+                   reinterpret_cast<const u64*>(keys_in), (const unsigned long long*)nullptr, un, passes, hist);
+  if (e == cudaSuccess)
+    e = launch_pdl(hist_scan_kernel, dim3(passes), dim3(256), 0, st, hist, status->pass_trivial,
+                   (const unsigned long long*)nullptr, un);
+  count_launches(3);
+  if (e != cudaSuccess) return SR_ERR_CUDA;
   // ping-pong between the scratch buffer and the output so that the last pass
   // writes the output: an odd pass count starts into the output
   u64* const kb[2] = {(passes & 1) ? reinterpret_cast<u64*>(keys_out) : tmp_keys,
@@ -1093,7 +1090,14 @@ extern "C" sr_status sr_sort_keys_noalloc(const uint64_t* keys_in, const uint32_
   uint32_t* const vb[2] = {(passes & 1) ? vals_out : tmp_vals, (passes & 1) ? tmp_vals : vals_out};
   const u64 parts = (un + kSortPart - 1) / kSortPart;
   run_passes<u64>(reinterpret_cast<const u64*>(keys_in), vals_in, kb, vb, hist, lookback, status->part_counter,
-                  nullptr, un, parts, passes, 8 * passes, nullptr, status, 1 << 20, st);
-  count_launches(3);
-  return cudaGetLastError() == cudaSuccess ? SR_OK : SR_ERR_CUDA;
+                  nullptr, un, parts, passes, 8 * passes, nullptr, status, 1 << 20, st, nullptr, 0, nullptr, nullptr,
+                  &e);
+  if (e != cudaSuccess) return SR_ERR_CUDA;
+  // the status word: a look-back wait that gave up leaves the output unsorted
+  uint32_t flags = 0u;
+  if (cudaMemcpyAsync(&flags, &status->flags, sizeof(flags), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return SR_ERR_CUDA;
+  if (flags & kStatusTimeout) return SR_ERR_TIMEOUT;
+  return SR_OK;
 }

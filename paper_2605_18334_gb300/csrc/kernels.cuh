@@ -103,6 +103,21 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+// The same launch without the programmatic attribute, for kernels that do
+// not wait on their predecessor with griddepcontrol.wait.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_plain(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = nullptr;
+  cfg.numAttrs = 0;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 cudaError_t launch_preprocess_fwd(const PreArgs& a, cudaStream_t st, int sms);
 cudaError_t launch_preprocess_bwd(const BwdArgs& a, cudaStream_t st, int sms);
 cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms);

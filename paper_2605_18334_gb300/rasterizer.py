@@ -371,7 +371,7 @@ class Rasterizer:
     # -- read-only views of the workspace (tests and diagnostics) ---------
     # slot numbers of the workspace layout (csrc/common.cuh, enum WsSlot)
     _S_STATUS, _S_REC, _S_DEPTH, _S_RECT, _S_NTOUCH = 0, 2, 3, 8, 9
-    _S_KEYS0, _S_VALS0, _S_D2 = 12, 14, 20
+    _S_KEYS0, _S_VALS0, _S_RANGES, _S_D2, _S_MASK = 12, 14, 19, 20, 22
 
     def _slot(self, k: int, nbytes: int) -> torch.Tensor:
         off = int(self.plan.off[k])
@@ -404,6 +404,24 @@ class Rasterizer:
     def rects(self) -> torch.Tensor:
         m = self.plan.n * self.n_views
         return self._slot(self._S_RECT, 8 * m).view(torch.int32).view(m, 2)
+
+    def ranges(self) -> torch.Tensor:
+        """[total_tiles, 2] int64: [start, end) of each tile's run in the
+        sorted key list of the last frame (empty tiles [0, 0))."""
+        t = int(self.plan.total_tiles)
+        raw = self._slot(self._S_RANGES, 8 * t).view(torch.int32).view(t, 2).to(torch.int64) & 0xFFFFFFFF
+        start = torch.where(raw[:, 1] > 0, (~raw[:, 0]) & 0xFFFFFFFF, torch.zeros_like(raw[:, 0]))
+        return torch.stack([start, raw[:, 1]], 1)
+
+    def blend_masks(self) -> torch.Tensor:
+        """The last forward's per-pixel blend masks (int32 words; layout in
+        render.cu: tile t's word for pixel i of the tile and positions
+        start + 32c .. start + 32c + 31 of its range at ((start >> 5) + t + c)
+        * 256 + i, valid up to the word holding the pixel's last blend)."""
+        if self.plan.forward_only:
+            raise ValueError("forward-only plans keep no blend masks")
+        words = (int(self.plan.key_capacity) // 32 + int(self.plan.total_tiles) + 1) * 256
+        return self._slot(self._S_MASK, 4 * words).view(torch.int32)
 
     def d2(self) -> torch.Tensor:
         """The 2D gradients of every (view, Gaussian) record after a backward

@@ -50,13 +50,6 @@ def gpu_records_to_oracle_layout(rec16: np.ndarray) -> dict:
                 ux=r[:, 9] * math.sqrt(2.0), uy=r[:, 10] * math.sqrt(2.0), rgb=r[:, 12:15], thr=r[:, 15])
 
 
-def tile_ranges(keys: np.ndarray, total_tiles: int) -> np.ndarray:
-    tiles = (keys >> np.uint64(32)).astype(np.int64)
-    starts = np.searchsorted(tiles, np.arange(total_tiles), side="left")
-    ends = np.searchsorted(tiles, np.arange(total_tiles), side="right")
-    return np.stack([starts, ends], 1)
-
-
 def compare_keys(gpu_keys, gpu_vals, or_keys, or_vals, ambiguous_vals):
     """Bit-exact comparison of sorted key lists after removing Gaussians whose
     tile set is decision-ambiguous; returns the number removed."""
@@ -69,13 +62,138 @@ def compare_keys(gpu_keys, gpu_vals, or_keys, or_vals, ambiguous_vals):
     return int(amb.size)
 
 
-def image_error(gpu_img_chw: np.ndarray, or_rgb_hwc: np.ndarray, ambiguous_hw: np.ndarray):
-    d = np.abs(np.transpose(gpu_img_chw, (1, 2, 0)).astype(np.float64) - or_rgb_hwc)
-    d[ambiguous_hw] = 0.0
-    return float(d.max()) if d.size else 0.0
-
-
 def rel_err(a, b):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12))
+
+
+def gpu_blend_lists(r, v: int, rows_per_block: int = 64):
+    """The Gaussians (indices within the view) the GPU forward blended at each
+    pixel of view v, in blend order, read from its blend masks, tile ranges,
+    sorted values and n_contrib: (offsets int64 [H*W + 1], ids int32), pixels
+    row-major."""
+    p = r.plan
+    n = int(p.n)
+    H, W = int(p.height[v]), int(p.width[v])
+    tiles_x = -(-W // 16)
+    tb = int(p.tile_base[v])
+    ranges = r.ranges().cpu().numpy()
+    mask = r.blend_masks().cpu().numpy().view(np.uint32)
+    _, vals = r.sorted_keys()
+    vals = vals.cpu().numpy().astype(np.int64) - v * n
+    nc_all = r.view_state(r.n_contrib, v).cpu().numpy().astype(np.int64).reshape(-1)
+    counts = np.zeros(H * W, np.int64)
+    chunks = []
+    for y0 in range(0, H, rows_per_block):
+        y1 = min(H, y0 + rows_per_block)
+        ys, xs = np.meshgrid(np.arange(y0, y1), np.arange(W), indexing="ij")
+        ys, xs = ys.reshape(-1), xs.reshape(-1)
+        pix = ys * W + xs
+        nc = nc_all[pix]
+        tile = tb + (ys // 16) * tiles_x + xs // 16
+        start = ranges[tile, 0]
+        assert np.all(nc <= ranges[tile, 1] - start)
+        pi = (ys % 16) * 16 + xs % 16
+        nch = (nc + 31) // 32
+        tot = int(nch.sum())
+        if tot == 0:
+            continue
+        owner = np.repeat(np.arange(len(pix)), nch)
+        first = np.repeat(np.cumsum(nch) - nch, nch)
+        c = np.arange(tot) - first
+        words = mask[((start[owner] >> 5) + tile[owner] + c) * 256 + pi[owner]]
+        bits = np.unpackbits(words.view(np.uint8).reshape(-1, 4), axis=1, bitorder="little").astype(bool)
+        bits &= (np.arange(32)[None, :] + 32 * c[:, None]) < nc[owner][:, None]
+        wr, b = np.nonzero(bits)                      # row-major: by pixel, then chunk, then bit
+        pos = 32 * c[wr] + b
+        own = owner[wr]
+        ids = vals[start[own] + pos]
+        counts[pix] = np.bincount(own, minlength=len(pix))
+        chunks.append(ids.astype(np.int32))
+    off = np.zeros(H * W + 1, np.int64)
+    np.cumsum(counts, out=off[1:])
+    ids = np.concatenate(chunks) if chunks else np.zeros(0, np.int32)
+    assert ids.size == off[-1]
+    return off, ids
+
+
+def check_key_order(keys: np.ndarray, vals: np.ndarray):
+    """The sorted list is ordered by (tile, depth bits) with ties in index
+    order, and no (tile, Gaussian) pair repeats."""
+    k = np.asarray(keys).view(np.uint64)
+    v = np.asarray(vals).astype(np.int64)
+    if k.size < 2:
+        return
+    ok = (k[1:] > k[:-1]) | ((k[1:] == k[:-1]) & (v[1:] > v[:-1]))
+    assert ok.all(), int(np.nonzero(~ok)[0][0])
+
+
+def check_ambiguous_tile_sets(keys, vals, pre, amb_ids, rec64, cam, ocfg, v_base: int, tile_base: int,
+                              tol_alpha: float, tol_px: float):
+    """For Gaussians whose FP64 tile set is ambiguous (an edge within tol_px
+    of a pixel-centre boundary, or a cull within tolerance): the GPU's tiles
+    hold every tile with a pixel centre where the FP64 alpha is at least
+    alpha_min (1 + tol_alpha), and lie within the FP64 bounding box of the
+    footprint widened by tol_px.  Returns the number of Gaussians checked."""
+    import oracle as O
+
+    k = np.asarray(keys).view(np.uint64)
+    v = np.asarray(vals).astype(np.int64) - v_base
+    tiles = (k >> np.uint64(32)).astype(np.int64) - tile_base
+    sel = np.isin(v, amb_ids)
+    order = np.argsort(v[sel], kind="stable")
+    gv, gt = v[sel][order], tiles[sel][order]
+    W, H = cam.width, cam.height
+    tiles_x = -(-W // 16)
+    tau, amax = float(ocfg.alpha_min), float(ocfg.alpha_max)
+    checked = 0
+    for i in amb_ids:
+        got = set(gt[np.searchsorted(gv, i, "left"):np.searchsorted(gv, i, "right")].tolist())
+        if not pre["visible"][i]:
+            assert not got, i
+            continue
+        ex, ey = pre["ext"][i, 0], pre["ext"][i, 1]
+        mx, my = rec64[i, 0], rec64[i, 1]
+        x0 = max(0, int(np.ceil(mx - ex - tol_px - 0.5)))
+        x1 = min(W - 1, int(np.floor(mx + ex + tol_px - 0.5)))
+        y0 = max(0, int(np.ceil(my - ey - tol_px - 0.5)))
+        y1 = min(H - 1, int(np.floor(my + ey + tol_px - 0.5)))
+        allowed = set()
+        need = set()
+        if x0 <= x1 and y0 <= y1:
+            ys, xs = np.meshgrid(np.arange(y0, y1 + 1), np.arange(x0, x1 + 1), indexing="ij")
+            px = np.stack([xs.reshape(-1), ys.reshape(-1)], 1).astype(np.int32)
+            t = (px[:, 1] // 16) * tiles_x + px[:, 0] // 16
+            allowed = set(np.unique(t).tolist())
+            a = np.minimum(O.alpha_at(pre["rec"][i], px), amax)
+            need = set(np.unique(t[a >= tau * (1 + tol_alpha)]).tolist())
+        assert need <= got, (i, sorted(need - got))
+        assert got <= allowed, (i, sorted(got - allowed))
+        checked += 1
+    return checked
+
+
+def compare_grads_elementwise(got: dict, ref: dict, fields, rtol: float = 1e-3):
+    """Element-by-element gradient bar: |g - g_ref| <= rtol * scale + slack,
+    where scale is the oracle's sum of the magnitudes of the terms summed into
+    the element (the scale a rounding error in any term grows with) and slack
+    the magnitude of the terms whose alpha_max or colour clamp decision lies
+    within tolerance (either decision is admissible).  Returns, per field,
+    (worst ratio |g - g_ref| / (rtol * scale + slack), the share of elements
+    within rtol of |g_ref|, the number of elements)."""
+    out = {}
+    for k in fields:
+        a = got[k].detach().cpu().numpy().astype(np.float64).reshape(-1)
+        b = np.asarray(ref[k], np.float64).reshape(-1)
+        s = np.asarray(ref["scale"][k], np.float64).reshape(-1)
+        sl = np.asarray(ref["slack"][k], np.float64).reshape(-1)
+        bound = rtol * s + sl + 1e-30
+        err = np.abs(a - b)
+        ratio = err / bound
+        worst = int(np.argmax(ratio)) if ratio.size else 0
+        within = float(np.mean(err <= rtol * np.abs(b) + 1e-12 * np.abs(b).max())) if b.size else 1.0
+        out[k] = (float(ratio[worst]) if ratio.size else 0.0, within, int(b.size))
+        assert ratio.size == 0 or ratio[worst] <= 1.0, (
+            k, worst, float(a[worst]), float(b[worst]), float(s[worst]), float(sl[worst]))
+    return out

@@ -1,10 +1,14 @@
 """Parity of the CUDA path (called through the C ABI) with the FP64 oracle.
 
-Bars (design notes): depth keys, tile counts and sorted key lists bit-exact
-(Gaussians whose FP64 tile edge lies within 2e-3 px of a pixel-centre
-boundary are excluded and counted); images within 1e-4 max abs per channel
-on pixels that are not decision-ambiguous (counted); gradients within 1e-3
-relative error per tensor.
+Bars (design notes): depth keys, tile counts and the sorted key list
+bit-exact, except for Gaussians whose FP64 tile edge lies within TOL_PX of a
+pixel-centre boundary, whose tile sets are counted and checked for validity
+instead; every pixel's image within 1e-4 max abs per channel of the oracle
+replaying the GPU's own gate and stop decisions, each of which must agree
+with FP64's or lie within the stated tolerance of its threshold (no pixel is
+excluded); gradients within 1e-3 relative error per tensor and, element by
+element, within 1e-3 of the oracle's rounding-error scale plus the terms
+whose clamp decision is within tolerance.
 """
 import math
 
@@ -16,8 +20,9 @@ import oracle
 from paper_2605_18334_gb300 import native as N
 from paper_2605_18334_gb300 import scenes
 from paper_2605_18334_gb300.rasterizer import Config, Gaussians, Rasterizer
-from tests.parity_util import (GRAD_RTOL, IMG_ATOL, compare_keys, dequantised, gpu_records_to_oracle_layout,
-                               image_error, oracle_config, rel_err, tile_ranges)
+from tests.parity_util import (GRAD_RTOL, IMG_ATOL, check_ambiguous_tile_sets, check_key_order, compare_grads_elementwise,
+                               compare_keys, dequantised, gpu_blend_lists, gpu_records_to_oracle_layout,
+                               oracle_config, rel_err)
 
 pytestmark = pytest.mark.gpu
 
@@ -34,18 +39,23 @@ def gpu_forward(scene, cams, cfg=None, key_capacity=None, **dtypes):
     return r, g
 
 
-def oracle_view(scene, cam, cfg, pixels=None):
+def check_view(r, scene, cams, v, cfg, check_keys=True, label=""):
+    """Compare view v of the GPU frame with the oracle: every Gaussian's depth
+    key, tile count and record, every key of the sorted list, and every pixel.
+
+    Gaussians whose FP64 tile set is ambiguous (an edge within TOL_PX of a
+    pixel-centre boundary, or the cull within tolerance) are counted; their
+    tile counts and keys are checked for validity (every tile where the FP64
+    alpha clears alpha_min (1 + TOL_ALPHA) present, none outside the FP64
+    box widened by TOL_PX) and all others bit for bit.  The image, T and the
+    blend lists are compared at every pixel against the oracle replaying the
+    GPU's own gate and stop decisions (read from its blend masks), each of
+    which must agree with FP64's or lie within tolerance of its threshold.
+    Returns the counters (also printed)."""
+    cam = cams[v]
     oc = oracle.camera_from_gl(cam)
     ocfg = oracle_config(cfg)
     pre = oracle.preprocess(scene, oc, ocfg)
-    out = oracle.render(scene, oc, ocfg, pixels=pixels, pre=pre)
-    return oc, ocfg, pre, out
-
-
-def check_view(r, scene, cams, v, cfg, pixels=None, check_keys=True):
-    """Compare view v of the GPU frame with the oracle; returns stats."""
-    cam = cams[v]
-    oc, ocfg, pre, out = oracle_view(scene, cam, cfg, pixels)
     n = scene.n
     p = r.plan
     stats = {}
@@ -56,11 +66,14 @@ def check_view(r, scene, cams, v, cfg, pixels=None, check_keys=True):
     or_cnt = np.where(pre["visible"], pre["ntouch"], 0)
     amb = pre["rect_ambig"]
     np.testing.assert_array_equal(cnt[~amb], or_cnt[~amb])
+    stats["touching"] = int(((cnt > 0) | (or_cnt > 0)).sum())
     stats["rect_ambiguous"] = int(amb.sum())
     # records of the rendered Gaussians
     sel = np.nonzero((cnt > 0) & ~amb)[0]
     g = gpu_records_to_oracle_layout(r.records().cpu().numpy()[v * n:(v + 1) * n][sel])
     o = pre["rec"][sel]
+    if sel.size:
+        stats["mu2_max_abs_err_px"] = float(max(np.abs(g["mx"] - o[:, 0]).max(), np.abs(g["my"] - o[:, 1]).max()))
     np.testing.assert_allclose(g["mx"], o[:, 0], atol=2e-3, rtol=1e-6)
     np.testing.assert_allclose(g["my"], o[:, 1], atol=2e-3, rtol=1e-6)
     for k, col in (("a", 2), ("b", 3), ("c", 4)):
@@ -72,51 +85,48 @@ def check_view(r, scene, cams, v, cfg, pixels=None, check_keys=True):
     np.testing.assert_allclose(g["m"], o[:, 7], atol=2e-6, rtol=1e-4)
     np.testing.assert_allclose(g["h"], o[:, 8], atol=2e-6, rtol=1e-4)
     np.testing.assert_allclose(g["rgb"], o[:, 11:14], atol=2e-5, rtol=1e-5)
-    # sorted keys
+    # sorted keys: order, bit-exact list of the unambiguous Gaussians, valid
+    # tile sets of the ambiguous ones
     keys, vals = r.sorted_keys()
     keys = keys.cpu().numpy().view(np.uint64)
     vals = vals.cpu().numpy().astype(np.int64)
     tb = int(p.tile_base[v]), int(p.tile_base[v + 1])
     sel_k = ((keys >> np.uint64(32)) >= tb[0]) & ((keys >> np.uint64(32)) < tb[1])
     if check_keys:
+        check_key_order(keys[sel_k], vals[sel_k])
         ok, ov = oracle.bin_keys(pre, oc, ocfg, tile_base=tb[0], val_base=v * n)
-        stats["key_excluded"] = compare_keys(keys[sel_k], vals[sel_k], ok, ov, np.nonzero(amb)[0] + v * n)
+        amb_ids = np.nonzero(amb)[0]
+        compare_keys(keys[sel_k], vals[sel_k], ok, ov, amb_ids + v * n)
         stats["keys"] = int(sel_k.sum())
-    # image, transmittance, last contributor
+        stats["keys_of_ambiguous"] = int(np.isin(vals[sel_k] - v * n, amb_ids).sum())
+        stats["ambiguous_tile_sets_checked"] = check_ambiguous_tile_sets(
+            keys[sel_k], vals[sel_k], pre, amb_ids, pre["rec"], oc, ocfg, v * n, tb[0], oracle.TOL_ALPHA,
+            oracle.TOL_PX)
+        for i in amb_ids:
+            assert cnt[i] == int((vals[sel_k] == i + v * n).sum())
+    # every pixel, under the GPU's own gate and stop decisions
+    lists = gpu_blend_lists(r, v)
+    rep = oracle.render_frame(scene, oc, ocfg, pre=pre, gpu_lists=lists)
+    st = rep["stats"]
+    assert st["inadmissible_pixels"] == 0, (st, np.argwhere(rep["status"] != 0)[:8])
     img = r.view_image(r.images, v).cpu().numpy()
     T = r.view_state(r.t_final, v).cpu().numpy()
-    nc = r.view_state(r.n_contrib, v).cpu().numpy().astype(np.int64)
-    H, W = cam["height"], cam["width"]
-    if pixels is None:
-        pix = oracle.all_pixels(oc)
-        amb_px = out["ambiguous"].reshape(-1)
-        or_rgb = out["rgb"].reshape(-1, 3)
-        or_T = out["T"].reshape(-1)
-        or_last = out["last"].reshape(-1)
-    else:
-        pix = np.asarray(pixels)
-        amb_px, or_rgb, or_T, or_last = out["ambiguous"], out["rgb"], out["T"], out["last"]
-    gi = img[:, pix[:, 1], pix[:, 0]].T
-    d = np.abs(gi.astype(np.float64) - or_rgb)
-    d[amb_px] = 0
+    d = np.abs(np.transpose(img, (1, 2, 0)).astype(np.float64) - rep["rgb"])
     stats["img_max_abs"] = float(d.max()) if d.size else 0.0
-    stats["ambiguous_px"] = int(amb_px.sum())
+    dT = np.abs(T.astype(np.float64) - rep["T"])
+    stats["T_max_abs"] = float(dT.max()) if dT.size else 0.0
+    stats["T_max_rel"] = float((dT / np.maximum(rep["T"], 1e-30)).max()) if dT.size else 0.0
+    stats["pixels"] = int(T.size)
+    stats["pixels_excluded"] = 0
+    for k in ("flipped_pixels", "flipped_gate", "flipped_stop", "max_gate_margin", "max_stop_margin",
+              "ambiguous_pixels"):
+        stats[k] = st[k]
+    stats["blends"] = int(lists[1].size)
+    print(f"parity {label or 'view'} v{v}: " + " ".join(f"{k}={val:.3g}" if isinstance(val, float) else f"{k}={val}"
+                                                   for k, val in stats.items()))
     assert stats["img_max_abs"] <= IMG_ATOL, stats
-    dT = np.abs(T[pix[:, 1], pix[:, 0]] - or_T)
-    dT[amb_px] = 0
-    assert dT.max() <= 1e-4, dT.max()
-    # last blended Gaussian (unique once the gate and stop decisions agree)
-    rng = tile_ranges(keys, int(p.total_tiles))
-    tiles_x = -(-W // 16)
-    tile = tb[0] + (pix[:, 1] // 16) * tiles_x + pix[:, 0] // 16
-    ncp = nc[pix[:, 1], pix[:, 0]]
-    if len(vals) == 0:
-        gl = np.full(len(pix), -1, np.int64)
-    else:
-        gl = np.where(ncp > 0, vals[np.clip(rng[tile, 0] + ncp - 1, 0, len(vals) - 1)] - v * n, -1)
-    ok = ~amb_px
-    np.testing.assert_array_equal(gl[ok], or_last[ok])
-    return stats, pre, out
+    assert stats["T_max_abs"] <= 1e-4, stats
+    return stats, pre, rep
 
 
 # ---------------------------------------------------------------------------
@@ -140,15 +150,12 @@ def test_ragged_image_sizes(W, H):
     check_view(r, sc, cams, 0, Config())
 
 
-def test_cluster_100k_720p_sampled_pixels():
-    """100k Gaussians, SH degree 3, 1280x720: keys bit-exact for the whole
-    frame, image at 4,000 sampled pixels."""
+def test_cluster_100k_720p_full_frame():
+    """100k Gaussians, SH degree 3, 1280x720: every key and every pixel."""
     sc = scenes.cluster()
     cams = [scenes.identity_camera(1280, 720)]
     r, _ = gpu_forward(sc, cams)
-    rng = np.random.default_rng(0)
-    pix = np.stack([rng.integers(0, 1280, 4000), rng.integers(0, 720, 4000)], 1).astype(np.int32)
-    stats, _, _ = check_view(r, sc, cams, 0, Config(), pixels=pix)
+    stats, _, _ = check_view(r, sc, cams, 0, Config(), label="cluster_100k_720p")
     assert stats["keys"] > 100_000
 
 
@@ -273,14 +280,40 @@ def test_graph_captured_frame_matches_eager():
 GRAD_FIELDS = ["means", "log_scales", "quats", "opacity_logits", "skew", "sh"]
 
 
-def compare_grads(gr, og, fields, rtol=GRAD_RTOL):
-    errs = {}
-    for k in fields:
-        a = gr[k].detach().cpu().numpy().astype(np.float64)
-        b = og[k]
-        errs[k] = rel_err(a, b)
+def compare_grads(gr, og, fields, rtol=GRAD_RTOL, label=""):
+    """Per tensor: ||g - g_ref|| / ||g_ref|| <= rtol; with the oracle's
+    bounds (``scale``/``slack``), also element by element (see
+    compare_grads_elementwise).  Prints both."""
+    errs = {k: rel_err(gr[k].detach().cpu().numpy().astype(np.float64), og[k]) for k in fields}
+    msg = " ".join(f"{k}={e:.2e}" for k, e in errs.items())
+    if "scale" in og:
+        el = compare_grads_elementwise(gr, og, fields)
+        msg += " | per element (worst bound ratio, share within 1e-3 rel): " + " ".join(
+            f"{k}=({w:.2f},{s:.4f})" for k, (w, s, _) in el.items())
+    print(f"grads {label}: {msg}")
     assert all(e <= rtol for e in errs.values()), errs
     return errs
+
+
+def oracle_grads(r, sc, cams, cfg, ups):
+    """The oracle's gradients of sum_v <ups[v], image_v>, replaying the GPU's
+    gate and stop decisions in every view, with element-wise bounds."""
+    tot = None
+    for v, c in enumerate(cams):
+        og = oracle.render_backward(sc, oracle.camera_from_gl(c), oracle_config(cfg), ups[v], frame=True,
+                                    gpu_lists=gpu_blend_lists(r, v), bounds=True)
+        assert og["inadmissible_pixels"] == 0
+        if tot is None:
+            tot = og
+            continue
+        for k, val in og.items():
+            if isinstance(val, dict):
+                for kk, vv in val.items():
+                    if vv is not None:
+                        tot[k][kk] = tot[k][kk] + vv
+            elif isinstance(val, np.ndarray):
+                tot[k] = tot[k] + val
+    return tot
 
 
 def test_backward_fd_crop_2k():
@@ -289,42 +322,41 @@ def test_backward_fd_crop_2k():
     sc, cam = scenes.fd_crop_scene()
     cams = [cam]
     r, g = gpu_forward(sc, cams)
-    dimg = torch.as_tensor(scenes.upstream_grad(3, 32, 32)).cuda().reshape(-1).contiguous()
-    gr = r.backward(g, dimg)
-    oc = oracle.camera_from_gl(cam)
-    og = oracle.render_backward(sc, oc, oracle_config(Config()), scenes.upstream_grad(3, 32, 32))
-    compare_grads(gr, og, GRAD_FIELDS)
-    # 2D gradients of the records too
+    up = scenes.upstream_grad(3, 32, 32)
+    gr = r.backward(g, torch.as_tensor(up).cuda().reshape(-1).contiguous())
+    og = oracle_grads(r, sc, cams, Config(), [up])
+    compare_grads(gr, og, GRAD_FIELDS, label="fd_crop_2k")
+    # 2D gradients of the records too, per column and element by element
     d2 = r.d2().cpu().numpy()
     cnt = r.tile_counts().cpu().numpy() > 0
-    o2 = og["d2"]
+    o2, s2, l2 = og["d2"], og["scale"]["d2"], og["slack"]["d2"]
     for col in (0, 1, 2, 3, 4, 5, 6, 7, 11, 12, 13):
         assert rel_err(d2[cnt, col], o2[cnt, col]) <= GRAD_RTOL, col
+        assert np.all(np.abs(d2[cnt, col] - o2[cnt, col]) <= GRAD_RTOL * s2[cnt, col] + l2[cnt, col] + 1e-30), col
 
 
 @pytest.mark.parametrize("two,split,deg", [(True, False, 1), (True, True, 3), (False, False, 0)])
 def test_backward_modes(two, split, deg):
     sc = scenes.cluster(seed=9, n=1500, sh_degree=deg, two_opacities=two, split=split)
     cams = [scenes.identity_camera(96, 72)]
-    r, g = gpu_forward(sc, cams, cfg=Config(bg=(0.3, 0.2, 0.1)))
+    cfg = Config(bg=(0.3, 0.2, 0.1))
+    r, g = gpu_forward(sc, cams, cfg=cfg)
     up = scenes.upstream_grad(9, 72, 96)
     gr = r.backward(g, torch.as_tensor(up).cuda().reshape(-1).contiguous())
-    og = oracle.render_backward(sc, oracle.camera_from_gl(cams[0]), oracle_config(Config(bg=(0.3, 0.2, 0.1))), up)
-    compare_grads(gr, og, GRAD_FIELDS + (["split_dir"] if split else []))
+    og = oracle_grads(r, sc, cams, cfg, [up])
+    compare_grads(gr, og, GRAD_FIELDS + (["split_dir"] if split else []), label=f"modes {two} {split} {deg}")
 
 
-def test_backward_cluster_100k_sparse_upstream():
-    """Full 100k / 720p frame; the upstream gradient is nonzero on 400
-    random pixels, so the oracle can sum the exact per-Gaussian gradients."""
+def test_backward_cluster_100k_dense_upstream():
+    """Full 100k / 720p frame with an upstream gradient N(0,1) at every pixel
+    and channel: every gradient element within its bound."""
     sc = scenes.cluster()
     cams = [scenes.identity_camera(1280, 720)]
     r, g = gpu_forward(sc, cams)
-    up, flat = scenes.sparse_upstream_grad(1, 720, 1280, 400)
+    up = scenes.upstream_grad(1, 720, 1280)
     gr = r.backward(g, torch.as_tensor(up).cuda().reshape(-1).contiguous())
-    pix = np.stack([flat % 1280, flat // 1280], 1).astype(np.int32)
-    og = oracle.render_backward(sc, oracle.camera_from_gl(cams[0]), oracle_config(Config()),
-                                up.reshape(3, -1)[:, flat].T, pixels=pix)
-    compare_grads(gr, og, GRAD_FIELDS)
+    og = oracle_grads(r, sc, cams, Config(), [up])
+    compare_grads(gr, og, GRAD_FIELDS, label="cluster_100k_720p")
 
 
 def test_backward_batched_views_sum():
@@ -335,11 +367,7 @@ def test_backward_batched_views_sum():
     ups = [scenes.upstream_grad(20 + v, c["height"], c["width"]) for v, c in enumerate(cams)]
     flat = torch.as_tensor(np.concatenate([u.reshape(-1) for u in ups])).cuda().contiguous()
     gr = r.backward(g, flat)
-    tot = None
-    for v, c in enumerate(cams):
-        og = oracle.render_backward(sc, oracle.camera_from_gl(c), oracle_config(Config()), ups[v])
-        tot = og if tot is None else {k: (tot[k] + og[k] if og[k] is not None else None) for k in og}
-    compare_grads(gr, tot, GRAD_FIELDS)
+    compare_grads(gr, oracle_grads(r, sc, cams, Config(), ups), GRAD_FIELDS, label="two views")
 
 
 @pytest.mark.parametrize("px,fb,bb", [(1, 128, 128), (2, 256, 256), (4, 512, 128), (2, 512, 128), (1, 0, 0)])
@@ -352,11 +380,10 @@ def test_pixels_per_thread_launch_shapes(px, fb, bb):
     cfg = Config(fwd_pixels_per_thread=px, bwd_pixels_per_thread=px, fwd_batch=fb, bwd_batch=bb,
                  bg=(0.1, 0.0, 0.2))
     r, g = gpu_forward(sc, cams, cfg)
-    check_view(r, sc, cams, 0, cfg)
+    check_view(r, sc, cams, 0, cfg, label=f"shape {px} {fb} {bb}")
     up = scenes.upstream_grad(31, 70, 100)
     gr = r.backward(g, torch.as_tensor(up).cuda().reshape(-1).contiguous())
-    og = oracle.render_backward(sc, oracle.camera_from_gl(cams[0]), oracle_config(cfg), up)
-    compare_grads(gr, og, GRAD_FIELDS)
+    compare_grads(gr, oracle_grads(r, sc, cams, cfg, [up]), GRAD_FIELDS, label=f"shape {px} {fb} {bb}")
 
 
 def test_autotune_picks_a_shape_and_keeps_results():
@@ -385,7 +412,7 @@ def test_densification_statistics_match_oracle():
     up = scenes.upstream_grad(33, 90, 120)
     gr = r.backward(g, torch.as_tensor(up).cuda().reshape(-1).contiguous(), want_stats=True)
     oc = oracle.camera_from_gl(cams[0])
-    og = oracle.render_backward(sc, oc, oracle_config(Config()), up)
+    og = oracle_grads(r, sc, cams, Config(), [up])
     uv = np.hypot(og["d2"][:, 0], og["d2"][:, 1])
     assert rel_err(gr["means2d_abs"].cpu().numpy(), uv) <= GRAD_RTOL
     W = oracle.camera_fields(oc)["w2c"].reshape(3, 4)[:, :3]
@@ -396,15 +423,15 @@ def test_densification_statistics_match_oracle():
 @pytest.mark.parametrize("dt,bound", [(torch.bfloat16, 0.05), (torch.float16, 0.01)])
 def test_reduced_precision_storage_error_against_fp32_originals(dt, bound):
     """Storage error: the GPU renders from BF16/FP16 SH, log-scales and skew,
-    the oracle from the FP32 originals.  The stated bound is a max abs error
-    per channel of 0.05 (BF16) / 0.01 (FP16) on non-ambiguous pixels."""
+    the oracle from the FP32 originals (its own decisions, every pixel).  The
+    stated bound is a max abs error per channel of 0.05 (BF16) / 0.01
+    (FP16)."""
     sc = scenes.cluster(seed=6, n=5000)
     cams = [scenes.identity_camera(200, 150)]
     r, _ = gpu_forward(sc, cams, sh_dtype=dt, scale_dtype=dt, skew_dtype=dt)
-    _, _, _, out = oracle_view(sc, cams[0], Config())
+    out = oracle.render_frame(sc, oracle.camera_from_gl(cams[0]), oracle_config(Config()))
     img = r.view_image(r.images, 0).cpu().numpy()
     d = np.abs(np.transpose(img, (1, 2, 0)) - out["rgb"])
-    d[out["ambiguous"]] = 0
     print(f"storage error {dt}: max {d.max():.3e} mean {d.mean():.3e}")
     assert d.max() <= bound
 
@@ -435,10 +462,8 @@ def test_autograd_function():
     img = render(r, *leaves[:5], leaves[5], sh_degree=0)
     up = torch.as_tensor(scenes.upstream_grad(4, 48, 48)).cuda().reshape(-1)
     (img * up).sum().backward()
-    og = oracle.render_backward(sc, oracle.camera_from_gl(cams[0]), oracle_config(Config()),
-                                scenes.upstream_grad(4, 48, 48))
-    for t, k in zip(leaves, GRAD_FIELDS):
-        assert rel_err(t.grad.cpu().numpy(), og[k]) <= GRAD_RTOL, k
+    og = oracle_grads(r, sc, cams, Config(), [scenes.upstream_grad(4, 48, 48)])
+    compare_grads({k: t.grad for t, k in zip(leaves, GRAD_FIELDS)}, og, GRAD_FIELDS, label="autograd")
 
 
 def test_recompute_keys_matches_batched_plan():
@@ -464,44 +489,36 @@ def test_recompute_keys_matches_batched_plan():
 
 def test_unbounded_1m_1080p_in_the_bench_launch_configuration():
     """The timed workload at full size (1M skew Gaussians, SH 3, 1920x1080,
-    key capacity 12 N, the autotuned launch shapes): depth keys and tile
-    counts of all 1M Gaussians and the whole sorted key list bit-exact, the
-    image at 2,048 sampled pixels (plus the four corners), and the gradients
-    of an upstream gradient that is nonzero on 256 random pixels, all against
-    the oracle."""
+    key capacity 12 N, the autotuned launch shapes): depth keys, tile counts
+    and records of all 1M Gaussians, the whole sorted key list, every pixel
+    of the image and every gradient element of an upstream gradient N(0,1)
+    at every pixel, all against the oracle (mode B)."""
     sc = scenes.unbounded(seed=2, n=1_000_000)
     cam = scenes.orbit_camera(0.0, 1920, 1080)
     g = Gaussians.from_scene(sc)
     r = Rasterizer(g, [cam], Config(), key_capacity=12 * sc.n)
-    up_dense = torch.as_tensor(scenes.upstream_grad(2, 1080, 1920)).cuda().reshape(-1).contiguous()
-    r.autotune(g, up_dense)
+    up = scenes.upstream_grad(2, 1080, 1920)
+    up_dev = torch.as_tensor(up).cuda().reshape(-1).contiguous()
+    r.autotune(g, up_dev)
     r.forward(g)
     torch.cuda.synchronize()
-    rng = np.random.default_rng(11)
-    pix = np.stack([rng.integers(0, 1920, 2048), rng.integers(0, 1080, 2048)], 1)
-    pix = np.concatenate([pix, [[0, 0], [1919, 0], [0, 1079], [1919, 1079]]]).astype(np.int32)
-    stats, _, _ = check_view(r, sc, [cam], 0, Config(), pixels=pix)
+    stats, _, _ = check_view(r, sc, [cam], 0, Config(), label="unbounded_1m_1080p")
     assert stats["keys"] > 5_000_000
-    up, flat = scenes.sparse_upstream_grad(3, 1080, 1920, 256)
-    gr = r.backward(g, torch.as_tensor(up).cuda().reshape(-1).contiguous())
-    pix_b = np.stack([flat % 1920, flat // 1920], 1).astype(np.int32)
-    og = oracle.render_backward(sc, oracle.camera_from_gl(cam), oracle_config(Config()),
-                                up.reshape(3, -1)[:, flat].T, pixels=pix_b)
-    compare_grads(gr, og, GRAD_FIELDS)
+    assert stats["rect_ambiguous"] <= 4e-3 * stats["touching"]
+    gr = r.backward(g, up_dev)
+    compare_grads(gr, oracle_grads(r, sc, [cam], Config(), [up]), GRAD_FIELDS, label="unbounded_1m_1080p")
 
 
 def test_composite_order_over_many_tiles():
     """Nine 1080p views (73,440 tiles, past the one-block ordering of the
-    composites' tile order): every view's keys bit-exact and its image at
-    sampled pixels against the oracle."""
+    composites' tile order): every view's keys and pixels against the
+    oracle."""
     sc = scenes.unbounded(seed=21, n=3000)
     cams = scenes.trajectory_cameras(9, resolutions=((1920, 1080),))
     r, _ = gpu_forward(sc, cams)
     assert int(r.plan.total_tiles) > 65536
-    rng = np.random.default_rng(21)
     for v in range(len(cams)):
-        pix = np.stack([rng.integers(0, 1920, 300), rng.integers(0, 1080, 300)], 1).astype(np.int32)
-        check_view(r, sc, cams, v, Config(), pixels=pix)
+        check_view(r, sc, cams, v, Config(), label="nine_1080p")
 
 
 def test_repeated_backward_calls_restart_from_zero():
@@ -564,11 +581,10 @@ def test_near_degenerate_splats():
     sc.means[near, 2] = rng.uniform(0.19, 0.3, int(near.sum())).astype(np.float32)
     cams = [scenes.identity_camera(96, 80)]
     r, g = gpu_forward(sc, cams)
-    check_view(r, sc, cams, 0, Config())
+    check_view(r, sc, cams, 0, Config(), label="near_degenerate")
     up = scenes.upstream_grad(41, 80, 96)
     gr = r.backward(g, torch.as_tensor(up).cuda().reshape(-1).contiguous())
-    og = oracle.render_backward(sc, oracle.camera_from_gl(cams[0]), oracle_config(Config()), up)
-    compare_grads(gr, og, GRAD_FIELDS)
+    compare_grads(gr, oracle_grads(r, sc, cams, Config(), [up]), GRAD_FIELDS, label="near_degenerate")
 
 
 def test_maximum_view_count():

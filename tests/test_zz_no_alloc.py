@@ -53,9 +53,27 @@ def _emission_order(keys, vals):
             torch.from_numpy(np.ascontiguousarray(v[order])).cuda())
 
 
+def _call(lib, in_k, in_v, n, bits):
+    out_k = torch.full_like(in_k, -1)
+    out_v = torch.full_like(in_v, -1)
+    s = lib.sr_sort_keys_noalloc(in_k.data_ptr(), in_v.data_ptr(), n, bits, out_k.data_ptr(), out_v.data_ptr(),
+                                 torch.cuda.current_stream().cuda_stream)
+    # SR_OK also says that no look-back wait of the sort gave up (the call
+    # reads the sort's status word back before it returns)
+    assert s == N.SR_OK, N.status_string(s)
+    return out_k, out_v
+
+
+def _stable_sort_reference(k, v, bits):
+    """numpy's stable sort by the low ceil(bits / 8) bytes of the keys."""
+    kk = k.cpu().numpy().view(np.uint64)
+    mask = np.uint64((1 << (8 * ((bits + 7) // 8))) - 1) if bits < 64 else np.uint64(0xFFFFFFFFFFFFFFFF)
+    order = np.argsort(kk & mask, kind="stable")
+    return kk[order], v.cpu().numpy()[order]
+
+
 def test_noalloc_sort_matches_bin_sort_on_two_calls_in_a_row():
     lib = _lib()
-    stream = torch.cuda.current_stream().cuda_stream
     cases = [(scenes.cluster(seed=21, n=20_000), scenes.identity_camera(320, 240)),   # 41 sort bits: 6 passes
              (scenes.cube_1k(seed=22, n=3_000), scenes.identity_camera(200, 150))]    # 40 sort bits: 5 passes
     passes = []
@@ -64,16 +82,30 @@ def test_noalloc_sort_matches_bin_sort_on_two_calls_in_a_row():
         n = ref_k.numel()
         assert 0 < n <= MAX_KEYS
         in_k, in_v = _emission_order(ref_k, ref_v)
-        out_k = torch.full_like(in_k, -1)
-        out_v = torch.full_like(in_v, -1)
-        s = lib.sr_sort_keys_noalloc(in_k.data_ptr(), in_v.data_ptr(), n, bits, out_k.data_ptr(), out_v.data_ptr(),
-                                     stream)
-        assert s == N.SR_OK, N.status_string(s)
-        torch.cuda.synchronize()
+        out_k, out_v = _call(lib, in_k, in_v, n, bits)
         assert torch.equal(out_k, ref_k)
         assert torch.equal(out_v, ref_v)
         passes.append((bits + 7) // 8)
     assert passes[0] % 2 != passes[1] % 2
+
+
+def test_noalloc_sort_matches_a_stable_sort_with_a_ragged_last_partition():
+    """Random 64-bit keys whose bits above sort_bits are zero, n not a
+    multiple of the 4096-key partition, against numpy's stable argsort."""
+    lib = _lib()
+    rng = np.random.default_rng(5)
+    for n, bits in ((12_345, 37), (MAX_KEYS - 1, 64), (4095, 9), (1, 8)):
+        assert n % 4096 != 0
+        raw = rng.integers(0, 2 ** 63, n, dtype=np.int64).view(np.uint64)
+        raw[rng.random(n) < 0.3] = raw[0]                     # many equal keys: ties must keep input order
+        if bits < 64:
+            raw &= np.uint64((1 << bits) - 1)
+        k = torch.from_numpy(raw.view(np.int64).copy()).cuda()
+        v = torch.from_numpy(np.arange(n, dtype=np.int32)[::-1].copy()).cuda()
+        out_k, out_v = _call(lib, k, v, n, bits)
+        want_k, want_v = _stable_sort_reference(k, v, bits)
+        np.testing.assert_array_equal(out_k.cpu().numpy().view(np.uint64), want_k)
+        np.testing.assert_array_equal(out_v.cpu().numpy(), want_v)
 
 
 def test_noalloc_sort_rejects_oversize_and_bad_arguments():
