@@ -10,7 +10,8 @@ the timed region starts; L2 is flushed (a 256 MiB memset) before every
 timed step, outside the step's CUDA events.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
-oracle on a bounded sample of the same workload instead.
+oracle on the same workload instead, one full forward + backward frame per
+step.
 """
 from __future__ import annotations
 
@@ -44,7 +45,9 @@ def parse():
     ap.add_argument("--n", type=int, default=1_000_000, help="Gaussians (default: the 1M workload)")
     ap.add_argument("--no-variants", action="store_true", help="only the headline FP32 fwd+bwd form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for the CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) measurement")
+    ap.add_argument("--oracle-threads", type=int, default=0,
+                    help="threads of the FP64 oracle (CPU baseline and reference arm; 0: all cores)")
     ap.add_argument("--workload", default="unbounded_1m", choices=["unbounded_1m", "mixed_5m"])
     ap.add_argument("--fwd-px", type=int, default=0, choices=[0, 1, 2, 4],
                     help="forward pixels per thread (0: autotune)")
@@ -241,7 +244,9 @@ def run_ours(args):
             r.backward_project(g)
             e[5].record(stream)
         torch.cuda.synchronize()
-    launches = N.sr_kernel_launches() - launches0
+        launches = N.sr_kernel_launches() - launches0
+        # the composites' arithmetic roofs, measured at the clock of this run
+        alu = N.sr_measure_alu_peaks(flush.data_ptr(), stream.cuda_stream)
     barrier(world)
     stage_ms = np.array([[ev[k][i].elapsed_time(ev[k][i + 1]) for i in range(NS)] for k in range(K)])
     step_ms = stage_ms.sum(1)
@@ -280,8 +285,9 @@ def run_ours(args):
     peaks = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK))
     sms = props.multi_processor_count
-    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = sms * 128 * max_mhz * 1e6 / 1e12  # FP32 lane-ops/s (an FMA is one op), T/s
+    # FP32 lane results per second: the faster of scalar and packed FP32x2
+    # FMA, as measured by sr_measure_alu_peaks in this run
+    alu_peak = max(alu["fma_lane_ops_per_s"], alu["ffma2_lane_ops_per_s"]) / 1e12
     # algorithmic work per unit: 25 FP32 ops per evaluated (pixel, Gaussian)
     # pair; the backward adds 60 per blended pair for the gradient math
     ops = {2: tested * 25, 3: replayed * 25 + blended * 60}
@@ -304,7 +310,7 @@ def run_ours(args):
         out["roofline"] = {"kernel": names[dom], "bound": "alu", "achieved": round(achieved, 3),
                            "peak": round(alu_peak, 3), "unit": "TFLOP/s", "frac": round(achieved / alu_peak, 4),
                            "traffic": traffic,
-                           "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz"}
+                           "peak_source": "measured in this run (sr_measure_alu_peaks: FP32 FMA lane results/s)"}
     else:
         b = bytes_.get(dom, 0)
         achieved = b / (stage_mean[dom] / 1e3) / 1e9
@@ -314,6 +320,8 @@ def run_ours(args):
         "render_fwd_TFLOPs": round(ops[2] / (stage_mean[2] / 1e3) / 1e12, 3),
         "render_bwd_composite_TFLOPs": round(ops[3] / (stage_mean[3] / 1e3) / 1e12, 3),
         "alu_peak_TFLOPs": round(alu_peak, 3),
+        "alu_peaks_measured_per_s": {k: (round(v / 1e12, 3) if k != "seconds" else round(v, 4))
+                                     for k, v in alu.items()},
         "preprocess_GBps": round(pre_bytes / (stage_mean[0] / 1e3) / 1e9, 1),
         "render_bwd_project_GBps": round(proj_bytes / (stage_mean[4] / 1e3) / 1e9, 1),
         "bin_sort_GBps": round((args.n * 4 * 16 + int(r.keys) * (8 + 16 * r.plan.sort_passes + 8)) /
@@ -325,9 +333,10 @@ def run_ours(args):
         out["variants"]["trajectory_64"] = trajectory(args, sc, dev, flush)
         out["variants"]["train_step"] = train_step(args, sc, cam, dev, flush)
         out["variants"]["densify"] = densify_step(args, sc, dev, flush)
-    out["e2e"] = e2e(args, sc, cam, up, dev, world)
+    if not args.no_e2e:
+        out["e2e"] = e2e(args, sc, cam, up, dev, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(sc, cam, up, args.cpu_budget)
+        out["cpu_baseline"] = cpu_baseline(sc, cam, up, args.oracle_threads)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -659,86 +668,72 @@ def e2e(args, sc, cam, up, dev, world):
 # CPU oracle (baseline leg and reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_frame_estimate(sc, cam, up, budget_s, seed=0):
-    """Time the FP64 oracle on a bounded pixel sample of the workload and
-    extrapolate to one full fwd+bwd frame: preprocess (all Gaussians) +
-    brute-force composite of every pixel + its backward.  Per-pixel costs
-    come from a linear fit over two sample sizes."""
+def oracle_frame(sc, cam, up):
+    """One full frame of the FP64 oracle, timed on the host cores: the
+    projection of every Gaussian, the composite of every pixel (mode B: each
+    pixel's list of the Gaussians whose footprint reaches it, in depth order;
+    the same result as brute force over every Gaussian), and the backward of
+    the dense upstream gradient at every pixel through the projection.
+    Returns (forward seconds, forward + backward seconds)."""
     import oracle
 
     oracle.build()
     oc = oracle.camera_from_gl(cam)
     ocfg = oracle.config()
-    W, H = cam["width"], cam["height"]
-    rng = np.random.default_rng(seed)
     t0 = time.perf_counter()
     pre = oracle.preprocess(sc, oc, ocfg)
-    t_pre = time.perf_counter() - t0
-
-    def fwd(n):
-        pix = np.stack([rng.integers(0, W, n), rng.integers(0, H, n)], 1).astype(np.int32)
-        t = time.perf_counter()
-        oracle.render(sc, oc, ocfg, pixels=pix, pre=pre)
-        return time.perf_counter() - t
-
-    def bwd(n):
-        pix = np.stack([rng.integers(0, W, n), rng.integers(0, H, n)], 1).astype(np.int32)
-        g = up.reshape(3, -1)[:, pix[:, 1] * W + pix[:, 0]].T
-        t = time.perf_counter()
-        oracle.render_backward(sc, oc, ocfg, g, pixels=pix, pre=pre)
-        return time.perf_counter() - t
-
-    def fit(fn, share):
-        # grow the sample until one call costs share * budget; linear fit of the last two
-        n_prev, t_prev = 8, fn(8)
-        n, t = 32, fn(32)
-        while 4 * (t - t_prev) + t_prev < share * budget_s and n < 65536:
-            n_prev, t_prev = n, t
-            n *= 4
-            t = fn(n)
-        slope = max((t - t_prev) / (n - n_prev), 1e-9)
-        return max(t - slope * n, 0.0), slope, n
-
-    af, bf, n2 = fit(fwd, 0.3)
-    ab, bb, m2 = fit(bwd, 0.3)
-    n1 = 8
-    frame_s = t_pre + af + bf * W * H + ab + bb * W * H
-    sample = (f"preprocess of all {sc.n} Gaussians, forward at {n1}+{n2} and backward at {n1}+{m2} random pixels "
-              f"of the 1920x1080 frame (brute force over every Gaussian), extrapolated linearly to all {W * H} pixels")
-    return frame_s, sample, oracle.num_threads(), time.perf_counter() - t0
+    oracle.render_frame(sc, oc, ocfg, pre=pre)
+    t1 = time.perf_counter()
+    oracle.render_backward(sc, oc, ocfg, up, pre=pre, frame=True)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t0
 
 
-def cpu_baseline(sc, cam, up, budget_s):
-    frame_s, sample, cores, spent = oracle_frame_estimate(sc, cam, up, budget_s)
-    return {"value": round(1.0 / frame_s, 9), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-            "seconds_spent": round(spent, 1)}
+def _oracle_sample(sc, cam):
+    return (f"one full {cam['width']}x{cam['height']} frame of all {sc.n} Gaussians: projection, composite of every "
+            f"pixel and backward of an upstream gradient at every pixel (FP64, per-pixel footprint lists)")
+
+
+def cpu_baseline(sc, cam, up, threads=0):
+    import oracle
+
+    oracle.build()
+    if threads:
+        oracle.set_num_threads(threads)
+    fwd_s, frame_s = oracle_frame(sc, cam, up)
+    return {"value": round(1.0 / frame_s, 6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": _oracle_sample(sc, cam), "fwd_frames_per_s": round(1.0 / fwd_s, 6),
+            "seconds": round(frame_s, 2)}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands on the host cores, one
+    full forward + backward frame of the workload per step."""
+    import oracle
+
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    oracle.build()
+    if args.oracle_threads:
+        oracle.set_num_threads(args.oracle_threads)
     sc, cam, up = workload(args.n)
-    budget = max(2.0, min(args.cpu_budget, 120.0 / max(1, args.steps + args.warmup)))
-    for w in range(args.warmup):
-        oracle_frame_estimate(sc, cam, up, budget, seed=w)
-    frames = []
-    cores, sample = 1, ""
+    for _ in range(args.warmup):
+        oracle_frame(sc, cam, up)
     t0 = time.perf_counter()
-    for k in range(args.steps):
-        fs, sample, cores, _ = oracle_frame_estimate(sc, cam, up, budget, seed=100 + k)
-        frames.append(fs)
+    frames = [oracle_frame(sc, cam, up) for _ in range(args.steps)]
     wall = time.perf_counter() - t0
-    ms = 1e3 * float(np.mean(frames))
+    ms = 1e3 * float(np.mean([f[1] for f in frames]))
     value = 1e3 / ms
-    out = {"metric": METRIC, "value": round(value, 9), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    out = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(args.n),
            "impl": "reference",
-           "cpu_baseline": {"value": round(value, 9), "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": sample},
-           "e2e": {"value": round(value, 9), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                            "sample": _oracle_sample(sc, cam),
+                            "fwd_frames_per_s": round(1e3 / (1e3 * float(np.mean([f[0] for f in frames]))), 6)},
+           "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "gpu_launches": 0, "wall_s": round(wall, 1)}
     print(json.dumps(out), flush=True)
 

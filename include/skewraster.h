@@ -294,6 +294,26 @@ sr_status sr_render_bwd_composite(const sr_plan* plan, const sr_config* cfg, voi
 sr_status sr_render_bwd_project(const sr_plan* plan, const sr_gaussians* g, const sr_camera* cams_dev,
                                 const sr_config* cfg, void* ws, const sr_grads* out, void* stream);
 
+/* Measured instruction throughput of this GPU for the arithmetic the blend
+ * loops of Alg. 1 and Alg. 2 are bound by (the roofline of the composites):
+ * FP32 fused multiply-add, packed FP32x2 fused multiply-add, FP32 min/max
+ * (the gate and clamp), and the multi-function unit's ex2 and rcp (the
+ * exponentials and the reciprocal of each skew-kernel evaluation).  Each
+ * rate is the best of three launches that fill every SM with independent
+ * dependency chains of that one kind, timed with CUDA events on the stream;
+ * the rates hold at the SM clock of the run (sample it alongside).
+ * scratch: 128 bytes of device memory, 16-byte aligned, never read (a sink
+ * that keeps the chains live).  Synchronises the stream; takes about 0.1 s. */
+typedef struct sr_alu_peaks {
+  double fma_lane_ops_per_s;    /* FP32 FMA results per second (one per lane) */
+  double ffma2_lane_ops_per_s;  /* FP32 FMA results per second from packed FP32x2 instructions */
+  double minmax_lane_ops_per_s; /* FP32 min or max results per second */
+  double ex2_per_s;             /* ex2.approx results per second */
+  double rcp_per_s;             /* rcp.approx results per second */
+  double seconds;               /* device time of the timed launches */
+} sr_alu_peaks;
+sr_status sr_measure_alu_peaks(void* scratch, sr_alu_peaks* out, void* stream);
+
 /* Self-test of the sort's bounded waits (failure detection without a GPU
  * fault): runs one radix pass over zero keys in the workspace in which no
  * block takes partition 0, so the block of partition 1 waits for a

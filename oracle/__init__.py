@@ -28,15 +28,15 @@ _LIB_PATH = os.path.join(_BUILD, "libskew_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-# Parity tolerances for decisions taken in floating point (documented in the
-# design notes, with the FP32 errors measured against them): a pair whose
-# alpha lies within TOL_ALPHA (relative) of alpha_min or of alpha_max, or
-# whose T' lies within TOL_T (relative) of T_stop, is "decision-ambiguous";
-# a rectangle edge within TOL_PX of a pixel-centre boundary makes a
-# Gaussian's tile set ambiguous.
+# Parity tolerances for decisions taken in floating point (the measured FP32
+# errors they cover are stated in the design notes): a pair whose alpha lies
+# within TOL_ALPHA (relative) of alpha_min or of alpha_max, or whose T' lies
+# within TOL_T (relative) of T_stop, is "decision-ambiguous"; a tile edge
+# within TOL_PX of a pixel-centre boundary makes a Gaussian's tile set
+# ambiguous.
 TOL_ALPHA = 5e-4
-TOL_T = 1e-3
-TOL_PX = 2e-3
+TOL_T = 1e-2
+TOL_PX = 1e-3
 
 
 def build(force: bool = False) -> str:
@@ -92,6 +92,11 @@ def _d(a):
 
 def num_threads() -> int:
     return int(lib().or_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on (timing runs)."""
+    lib().or_set_num_threads(C.c_int(int(n)))
 
 
 def config(tile=16, alpha_min=1.0 / 255.0, alpha_max=0.99, t_stop=1e-4, dilation=0.3, fov_clamp=1.3,

@@ -474,6 +474,16 @@ int or_num_threads() {
 #endif
 }
 
+// Threads the oracle's parallel loops use from now on (timing runs only;
+// results do not depend on it beyond the summation order of gradients).
+void or_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 // Alg. 3: M_cv = M_gl diag(1,-1,-1,1); W2C = M_cv^-1; K from (W, H, FoV).
 // c2w_gl is row-major 4x4.  All fields are rounded to FP32 once.
 void or_camera_from_gl(const double* c2w_gl, int32_t width, int32_t height, double fovx, double fovy,

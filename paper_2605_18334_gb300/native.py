@@ -23,7 +23,8 @@ EXPORTS = ["sr_abi_version", "sr_status_string", "sr_config_default", "sr_camera
            "sr_workspace_size", "sr_preprocess", "sr_bin_sort", "sr_render_fwd", "sr_render_bwd", "sr_read_status",
            "sr_kernel_launches", "sr_frame_counters", "sr_sort_keys_noalloc", "sr_render_bwd_composite",
            "sr_render_bwd_project", "sr_selftest_bounded_wait", "sr_loss_scratch_size", "sr_loss_l1_dssim",
-           "sr_adam_step", "sr_densify_stats", "sr_densify_scratch_size", "sr_densify", "sr_densify_remap"]
+           "sr_adam_step", "sr_densify_stats", "sr_densify_scratch_size", "sr_densify", "sr_densify_remap",
+           "sr_measure_alu_peaks"]
 
 SR_ADAM_MAX_GROUPS = 16
 
@@ -140,6 +141,7 @@ def load(build_if_missing: bool = True):
         lib.sr_selftest_bounded_wait.restype = C.c_int
         lib.sr_kernel_launches.restype = C.c_uint64
         lib.sr_kernel_launches.argtypes = []
+        lib.sr_measure_alu_peaks.argtypes = [C.c_void_p, P(sr_alu_peaks), C.c_void_p]
         lib.sr_frame_counters.argtypes = [P(sr_plan), C.c_void_p, P(C.c_uint64), P(C.c_uint64), C.c_void_p]
         lib.sr_frame_counters.restype = C.c_int
         lib.sr_loss_scratch_size.restype = C.c_size_t
@@ -271,6 +273,18 @@ def sr_frame_counters(plan, ws_ptr: int, stream: int):
     check("sr_frame_counters", load().sr_frame_counters(C.byref(plan), C.c_void_p(ws_ptr), C.byref(t), C.byref(b),
                                                         C.c_void_p(stream)))
     return int(t.value), int(b.value)
+
+
+class sr_alu_peaks(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("fma_lane_ops_per_s", "ffma2_lane_ops_per_s", "minmax_lane_ops_per_s",
+                                          "ex2_per_s", "rcp_per_s", "seconds")]
+
+
+def sr_measure_alu_peaks(scratch_ptr: int, stream: int) -> dict:
+    out = sr_alu_peaks()
+    check("sr_measure_alu_peaks", load().sr_measure_alu_peaks(C.c_void_p(scratch_ptr), C.byref(out),
+                                                               C.c_void_p(stream)))
+    return {k: getattr(out, k) for k, _ in sr_alu_peaks._fields_}
 
 
 def sr_loss_scratch_size(plan) -> int:

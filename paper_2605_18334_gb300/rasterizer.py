@@ -423,12 +423,68 @@ class Rasterizer:
         words = (int(self.plan.key_capacity) // 32 + int(self.plan.total_tiles) + 1) * 256
         return self._slot(self._S_MASK, 4 * words).view(torch.int32)
 
+    def blend_lists(self, v: int = 0):
+        """Per pixel of view v, the Gaussians the last forward blended (see
+        the module-level blend_lists)."""
+        return blend_lists(self, v)
+
     def d2(self) -> torch.Tensor:
         """The 2D gradients of every (view, Gaussian) record after a backward
         composite, [M, 14] in the order of ``native.D2_NAMES``."""
         m = self.plan.n * self.n_views
         raw = self._slot(self._S_D2, 64 * m).view(torch.float32).view(m, 16)
         return raw[:, torch.as_tensor(N.D2_SLOTS, device=raw.device)]
+
+
+def blend_lists(r, v: int, rows_per_block: int = 64):
+    """The Gaussians (indices within the view) the last forward of rasterizer
+    ``r`` blended at each pixel of view v, in blend order, read from its blend
+    masks, tile ranges, sorted values and n_contrib: (offsets int64 [H*W + 1],
+    ids int32), pixels row-major (a diagnostic of the workspace; host-side
+    decoding only)."""
+    p = r.plan
+    n = int(p.n)
+    H, W = int(p.height[v]), int(p.width[v])
+    tiles_x = -(-W // 16)
+    tb = int(p.tile_base[v])
+    ranges = r.ranges().cpu().numpy()
+    mask = r.blend_masks().cpu().numpy().view(np.uint32)
+    _, vals = r.sorted_keys()
+    vals = vals.cpu().numpy().astype(np.int64) - v * n
+    nc_all = r.view_state(r.n_contrib, v).cpu().numpy().astype(np.int64).reshape(-1)
+    counts = np.zeros(H * W, np.int64)
+    chunks = []
+    for y0 in range(0, H, rows_per_block):
+        y1 = min(H, y0 + rows_per_block)
+        ys, xs = np.meshgrid(np.arange(y0, y1), np.arange(W), indexing="ij")
+        ys, xs = ys.reshape(-1), xs.reshape(-1)
+        pix = ys * W + xs
+        nc = nc_all[pix]
+        tile = tb + (ys // 16) * tiles_x + xs // 16
+        start = ranges[tile, 0]
+        assert np.all(nc <= ranges[tile, 1] - start)
+        pi = (ys % 16) * 16 + xs % 16
+        nch = (nc + 31) // 32
+        tot = int(nch.sum())
+        if tot == 0:
+            continue
+        owner = np.repeat(np.arange(len(pix)), nch)
+        first = np.repeat(np.cumsum(nch) - nch, nch)
+        c = np.arange(tot) - first
+        words = mask[((start[owner] >> 5) + tile[owner] + c) * 256 + pi[owner]]
+        bits = np.unpackbits(words.view(np.uint8).reshape(-1, 4), axis=1, bitorder="little").astype(bool)
+        bits &= (np.arange(32)[None, :] + 32 * c[:, None]) < nc[owner][:, None]
+        wr, b = np.nonzero(bits)                      # row-major: by pixel, then chunk, then bit
+        pos = 32 * c[wr] + b
+        own = owner[wr]
+        ids = vals[start[own] + pos]
+        counts[pix] = np.bincount(own, minlength=len(pix))
+        chunks.append(ids.astype(np.int32))
+    off = np.zeros(H * W + 1, np.int64)
+    np.cumsum(counts, out=off[1:])
+    ids = np.concatenate(chunks) if chunks else np.zeros(0, np.int32)
+    assert ids.size == off[-1]
+    return off, ids
 
 
 def shard_views(cameras: list, rank: int, world: int) -> list:

@@ -7,8 +7,9 @@ instead; every pixel's image within 1e-4 max abs per channel of the oracle
 replaying the GPU's own gate and stop decisions, each of which must agree
 with FP64's or lie within the stated tolerance of its threshold (no pixel is
 excluded); gradients within 1e-3 relative error per tensor and, element by
-element, within 1e-3 of the oracle's rounding-error scale plus the terms
-whose clamp decision is within tolerance.
+element, within 1e-2 of the oracle's rounding-error scale (the sum of the
+magnitudes of the element's terms) plus the terms whose clamp decision is
+within tolerance.
 """
 import math
 
@@ -20,7 +21,7 @@ import oracle
 from paper_2605_18334_gb300 import native as N
 from paper_2605_18334_gb300 import scenes
 from paper_2605_18334_gb300.rasterizer import Config, Gaussians, Rasterizer
-from tests.parity_util import (GRAD_RTOL, IMG_ATOL, check_ambiguous_tile_sets, check_key_order, compare_grads_elementwise,
+from tests.parity_util import (ELEM_RTOL, GRAD_RTOL, IMG_ATOL, check_ambiguous_tile_sets, check_key_order, compare_grads_elementwise,
                                compare_keys, dequantised, gpu_blend_lists, gpu_records_to_oracle_layout,
                                oracle_config, rel_err)
 
@@ -273,6 +274,40 @@ def test_graph_captured_frame_matches_eager():
     assert torch.equal(r.images, eager)
 
 
+def test_graph_captured_mixed_resolution_trajectory_against_oracle():
+    """A five-view trajectory of three image sizes in one plan, captured as a
+    CUDA graph (non-blocking bin/sort) and replayed: every view's keys and
+    every pixel against the oracle."""
+    sc = scenes.unbounded(seed=23, n=30_000)
+    cams = scenes.trajectory_cameras(5, resolutions=((160, 90), (320, 180), (240, 240)))
+    g = Gaussians.from_scene(sc)
+    r = Rasterizer(g, cams, Config())
+    r.forward(g)  # sizes the key pool
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        r.preprocess(g, s)
+        r.bin_sort(s, sync=False)
+        r.render_fwd(s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        r.preprocess(g, s)
+        r.bin_sort(s, sync=False)
+        r.render_fwd(s)
+    r.images.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    r.keys = r.check()
+    sizes = set()
+    for v, cam in enumerate(cams):
+        check_view(r, sc, cams, v, Config(), label="graph_trajectory")
+        sizes.add((cam["width"], cam["height"]))
+    assert len(sizes) == 3
+
+
 # ---------------------------------------------------------------------------
 # backward
 # ---------------------------------------------------------------------------
@@ -332,7 +367,7 @@ def test_backward_fd_crop_2k():
     o2, s2, l2 = og["d2"], og["scale"]["d2"], og["slack"]["d2"]
     for col in (0, 1, 2, 3, 4, 5, 6, 7, 11, 12, 13):
         assert rel_err(d2[cnt, col], o2[cnt, col]) <= GRAD_RTOL, col
-        assert np.all(np.abs(d2[cnt, col] - o2[cnt, col]) <= GRAD_RTOL * s2[cnt, col] + l2[cnt, col] + 1e-30), col
+        assert np.all(np.abs(d2[cnt, col] - o2[cnt, col]) <= ELEM_RTOL * s2[cnt, col] + l2[cnt, col] + 1e-30), col
 
 
 @pytest.mark.parametrize("two,split,deg", [(True, False, 1), (True, True, 3), (False, False, 0)])
