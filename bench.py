@@ -60,6 +60,24 @@ def parse():
     return ap.parse_args()
 
 
+COUNTERS = os.path.join(ROOT, "profiles", "render_counters_unbounded_500k_1080p.json")
+KERNEL_SOURCES = ("render.cu", "common.cuh")
+
+
+def render_counters():
+    """ncu counters of the two composites from a capture of a smaller frame
+    (instruction counts per pair, DRAM bytes per launch) and whether the
+    kernel sources are still the ones the capture was taken with."""
+    import hashlib
+
+    try:
+        d = json.load(open(COUNTERS))
+    except Exception:
+        return None, False
+    src = b"".join(open(os.path.join(ROOT, "paper_2605_18334_gb300", "csrc", f), "rb").read() for f in KERNEL_SOURCES)
+    return d, hashlib.sha256(src).hexdigest() == d.get("source_sha256")
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -288,29 +306,45 @@ def run_ours(args):
     # FP32 lane results per second: the faster of scalar and packed FP32x2
     # FMA, as measured by sr_measure_alu_peaks in this run
     alu_peak = max(alu["fma_lane_ops_per_s"], alu["ffma2_lane_ops_per_s"]) / 1e12
-    # algorithmic work per unit: 25 FP32 ops per evaluated (pixel, Gaussian)
-    # pair; the backward adds 60 per blended pair for the gradient math
-    ops = {2: tested * 25, 3: replayed * 25 + blended * 60}
+    # work per launch of the composites: FP32 lane results (FADD, FMUL and FFMA
+    # thread instructions, the packed FP32x2 forms counted twice) per tested
+    # (forward) or replayed (backward) pair from the ncu capture of the
+    # smaller frame, times this frame's pairs; nominal counts (25 per tested
+    # pair, 25 per replayed + 60 per blended pair) when the kernels changed
+    cnt, fresh = render_counters()
+    nominal = {2: tested * 25, 3: replayed * 25 + blended * 60}
+    units = {2: (tested, "pairs_tested"), 3: (replayed, "pairs_replayed_bwd")}
+    ops, ops_source, issue = {}, {}, {}
+    for k, kname in ((2, "render_fwd"), (3, "render_bwd_composite")):
+        kc = cnt["kernels"].get(kname) if cnt else None
+        if kc and fresh:
+            scale = units[k][0] / cnt[units[k][1]]
+            ops[k] = kc["fp32_lane_results"] * scale
+            ops_source[k] = (f"ncu counters of a {cnt['keys']}-key frame, scaled by {units[k][1]} "
+                             f"({cnt[units[k][1]]} -> {units[k][0]})")
+            issue[k] = kc["warp_instructions"] * scale / (sms * 4 * (clocks.get("sm_mhz") or 2070.0) * 1e6 *
+                                                          stage_mean[k] / 1e3)
+        else:
+            ops[k] = nominal[k]
+            ops_source[k] = "nominal (25 FP32 operations per tested pair; 25 per replayed + 60 per blended pair)"
     pre_bytes = args.n * 248 + args.n * 20 + int((r.tile_counts() > 0).sum()) * 64
     nrec = int((r.tile_counts() > 0).sum())
     proj_bytes = args.n * (248 + 4) + nrec * 64 + args.n * 248
     bytes_ = {0: pre_bytes, 4: proj_bytes}
     dom = int(np.argmax(stage_mean))
-    # DRAM bytes per launch (read + write) of the dominant kernel from the ncu
-    # capture summarised in profiles/kernels_full_unbounded_1m_1080p.md, for
-    # the launch shape it was taken in (None for any other shape or workload)
-    ncu_traffic = {("render_bwd_composite", 2, 128): 96.62e6, ("render_bwd_composite", 2, 256): 96.61e6}
     traffic = None
-    if args.n == 1_000_000:
-        shape = ((tune["bwd_pixels_per_thread"], r.config.bwd_batch or 128) if dom == 3 else
-                 (tune["fwd_pixels_per_thread"], r.config.fwd_batch or 256))
-        traffic = ncu_traffic.get((names[dom],) + shape)
+    if cnt and fresh and args.n == 1_000_000:
+        kc = cnt["kernels"].get(names[dom], {})
+        traffic = kc.get("dram_bytes_unbounded_1m")  # captured on this frame itself
     if dom in ops:
         achieved = ops[dom] / (stage_mean[dom] / 1e3) / 1e12
         out["roofline"] = {"kernel": names[dom], "bound": "alu", "achieved": round(achieved, 3),
                            "peak": round(alu_peak, 3), "unit": "TFLOP/s", "frac": round(achieved / alu_peak, 4),
                            "traffic": traffic,
-                           "peak_source": "measured in this run (sr_measure_alu_peaks: FP32 FMA lane results/s)"}
+                           "peak_source": "measured in this run (sr_measure_alu_peaks: FP32 lane results/s)",
+                           "work_source": ops_source[dom]}
+        if dom in issue:
+            out["roofline"]["issue_slot_utilisation"] = round(issue[dom], 4)
     else:
         b = bytes_.get(dom, 0)
         achieved = b / (stage_mean[dom] / 1e3) / 1e9
@@ -318,6 +352,8 @@ def run_ours(args):
                            "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None}
     out["other_stages"] = {
         "render_fwd_TFLOPs": round(ops[2] / (stage_mean[2] / 1e3) / 1e12, 3),
+        "render_fwd_work_source": ops_source[2],
+        "issue_slot_utilisation": {names[k]: round(v, 4) for k, v in issue.items()},
         "render_bwd_composite_TFLOPs": round(ops[3] / (stage_mean[3] / 1e3) / 1e12, 3),
         "alu_peak_TFLOPs": round(alu_peak, 3),
         "alu_peaks_measured_per_s": {k: (round(v / 1e12, 3) if k != "seconds" else round(v, 4))

@@ -53,7 +53,7 @@ extern "C" {
 #endif
 
 #define SR_MAX_VIEWS 256
-#define SR_ABI_VERSION 2
+#define SR_ABI_VERSION 3
 
 typedef enum sr_status {
   SR_OK = 0,
@@ -114,6 +114,11 @@ typedef struct sr_config {
   int32_t forward_only;       /* plans made with 1 record no per-pixel blend masks (less workspace);
                                  sr_render_bwd on them returns SR_ERR_UNSUPPORTED */
   int32_t bwd_batch;          /* 128 or 256 (0 = 128): records sr_render_bwd stages per batch */
+  int32_t recompute_keys;     /* plans made with 1 keep no per-pixel blend masks; sr_render_bwd then
+                                 rebuilds the frame's records and tile key lists (sr_preprocess and a
+                                 non-blocking sr_bin_sort) and replays every position up to each pixel's
+                                 n_contrib with the alpha gate (Alg. 2), so the workspace may serve other
+                                 frames between a forward and its backward.  Not with forward_only. */
 } sr_config;
 
 /* Gradients of the loss w.r.t. the attributes, FP32, device, caller-owned,
@@ -148,7 +153,7 @@ typedef struct sr_plan {
   int32_t two_opacities;      /* copied from the sr_gaussians the plan was made for */
   int32_t has_split;          /* 1 if split_dir was non-NULL */
   int32_t forward_only;       /* from the config: no blend masks, no backward */
-  int32_t reserved1_;
+  int32_t recompute_keys;     /* from the config: no blend masks; the backward rebuilds the key lists */
   int64_t key_capacity;       /* keys the workspace can hold */
   int64_t total_tiles;
   int64_t total_pixels;
@@ -237,7 +242,11 @@ sr_status sr_render_fwd(const sr_plan* plan, const sr_config* cfg, void* ws, flo
  * n_contrib of the matching forward call and the same g and cams_dev.  May be
  * called again for the same frame (another d_images): the workspace's 2D
  * gradients, zeroed by sr_preprocess for its frame, are cleared again on the
- * device when a backward has used them since. */
+ * device when a backward has used them since.  On a recompute_keys plan the
+ * workspace need not hold the frame any more: the call first re-runs
+ * sr_preprocess and sr_bin_sort (non-blocking) for g and cams_dev, then
+ * replays without blend masks; only t_final and n_contrib of the forward are
+ * needed. */
 sr_status sr_render_bwd(const sr_plan* plan, const sr_gaussians* g, const sr_camera* cams_dev, const sr_config* cfg,
                         void* ws, const float* d_images, const float* t_final, const uint32_t* n_contrib,
                         const sr_grads* out, void* stream);
@@ -288,7 +297,9 @@ sr_status sr_frame_counters(const sr_plan* plan, void* ws, uint64_t* pairs_teste
  * projected skew, opacity terms, colour) in the workspace;
  * sr_render_bwd_project then applies the chain rule through the projection
  * (Appendix "Backward Pass", deferred to 3DGS in the paper) into *out.
- * Same arguments and rules as sr_render_bwd. */
+ * Same arguments and rules as sr_render_bwd, except that on a recompute_keys
+ * plan sr_render_bwd_composite does not rebuild the key lists: the
+ * workspace must hold the frame (its sr_preprocess and sr_bin_sort). */
 sr_status sr_render_bwd_composite(const sr_plan* plan, const sr_config* cfg, void* ws, const float* d_images,
                                   const float* t_final, const uint32_t* n_contrib, void* stream);
 sr_status sr_render_bwd_project(const sr_plan* plan, const sr_gaussians* g, const sr_camera* cams_dev,

@@ -62,6 +62,8 @@ sr_status check_config(const sr_config* c) {
     if (px != 0 && px != 1 && px != 2 && px != 4) return SR_ERR_INVALID;
   if (c->fwd_batch != 0 && c->fwd_batch != 128 && c->fwd_batch != 256 && c->fwd_batch != 512) return SR_ERR_INVALID;
   if (c->bwd_batch != 0 && c->bwd_batch != 128 && c->bwd_batch != 256) return SR_ERR_INVALID;
+  if (c->recompute_keys != 0 && c->recompute_keys != 1) return SR_ERR_INVALID;
+  if (c->recompute_keys && c->forward_only) return SR_ERR_INVALID;
   return SR_OK;
 }
 
@@ -167,6 +169,7 @@ sr_status sr_plan_init(sr_plan* p, const sr_config* cfg, const sr_gaussians* g, 
   p->has_split = g->split_dir ? 1 : 0;
   p->render_mode = !p->two_opacities ? MODE_PLAIN : (p->has_split ? MODE_SPLIT : MODE_TWO);
   p->forward_only = cfg->forward_only ? 1 : 0;
+  p->recompute_keys = cfg->recompute_keys ? 1 : 0;
   p->key_capacity = key_capacity;
   int64_t tb = 0, io = 0, po = 0;
   for (int v = 0; v < n_views; ++v) {
@@ -215,7 +218,9 @@ sr_status sr_plan_init(sr_plan* p, const sr_config* cfg, const sr_gaussians* g, 
   sizes[WS_RANGES] = sizeof(uint2) * (size_t)tb;
   sizes[WS_D2] = p->forward_only ? 0 : sizeof(float) * kD2Stride * (size_t)m;
   sizes[WS_FOOT] = sizeof(float4) * 4 * (size_t)m;
-  sizes[WS_MASK] = p->forward_only ? 0 : sizeof(uint32_t) * 256 * (size_t)(key_capacity / 32 + tb + 1);
+  sizes[WS_MASK] = (p->forward_only || p->recompute_keys)
+                       ? 0
+                       : sizeof(uint32_t) * 256 * (size_t)(key_capacity / 32 + tb + 1);
   sizes[WS_TILE_ORDER] = sizeof(uint32_t) * ((size_t)tb + 128);
   sizes[WS_SHJAC] = p->forward_only ? 0 : sizeof(float4) * 3 * (size_t)m;
   size_t off = 0;
@@ -429,6 +434,14 @@ sr_status sr_render_bwd(const sr_plan* p, const sr_gaussians* g, const sr_camera
     return SR_ERR_INVALID;
   if (p->has_split && p->n > 0 && !out->split_dir) return SR_ERR_INVALID;
   if (p->n > 0 && !aligned16(out->quats)) return SR_ERR_INVALID;
+  if (p->recompute_keys) {
+    // rebuild the frame's records and sorted key lists (the workspace may
+    // have served other frames since the forward); no host round trip
+    s = sr_preprocess(p, g, cams_dev, cfg, ws, stream);
+    if (s != SR_OK) return s;
+    s = sr_bin_sort(p, cfg, ws, nullptr, stream);
+    if (s != SR_OK) return s;
+  }
   s = sr_render_bwd_composite(p, cfg, ws, d_images, t_final, n_contrib, stream);
   if (s != SR_OK) return s;
   return sr_render_bwd_project(p, g, cams_dev, cfg, ws, out, stream);

@@ -513,7 +513,7 @@ inline Ws ws_ptrs(const sr_plan& p, void* base) {
   w.ranges = reinterpret_cast<uint2*>(at(WS_RANGES));
   w.d2 = reinterpret_cast<float*>(at(WS_D2));
   w.foot = reinterpret_cast<float4*>(at(WS_FOOT));
-  w.mask = p.forward_only ? nullptr : reinterpret_cast<uint32_t*>(at(WS_MASK));
+  w.mask = (p.forward_only || p.recompute_keys) ? nullptr : reinterpret_cast<uint32_t*>(at(WS_MASK));
   w.tile_order = reinterpret_cast<uint32_t*>(at(WS_TILE_ORDER));
   w.shjac = p.forward_only ? nullptr : reinterpret_cast<float4*>(at(WS_SHJAC));
   return w;

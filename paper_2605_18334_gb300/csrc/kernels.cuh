@@ -50,7 +50,8 @@ struct RenderArgs {     // forward and backward composite
   uint32_t* n_contrib;
   const float* d_images;
   float* d2;
-  uint32_t* mask;       // per-pixel blend masks, or null (forward-only plan)
+  uint32_t* mask;       // per-pixel blend masks, or null (forward-only or recompute-keys plan;
+                        // the backward then replays with the alpha gate)
   int batch_fwd;        // records staged per batch (128, 256, 512)
   int batch_bwd;        // (128, 256)
   int px_fwd;           // pixels per thread (1, 2, 4)

@@ -19,7 +19,10 @@
 // A thread first sums its PX pixels' contributions to a Gaussian, the warp
 // then sums its lanes with a transposing butterfly, warps add into padded
 // shared-memory accumulators, and each block issues one set of vector atomics
-// per Gaussian per batch.
+// per Gaussian per batch.  Which positions a pixel blended comes from the
+// forward's blend masks, or, in plans that keep none, from re-evaluating
+// the alpha gate at every position below the pixel's n_contrib (the stop
+// cannot occur there), as Alg. 2 does.
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -345,9 +348,13 @@ struct BwdPixels {
     g2[p] = c2;
   }
   // Adds to gr the record's gradient components over the pixels whose mask
-  // word has `bit` set; returns whether there was one.
+  // word has `bit` set; returns whether there was one.  GATED: the bits mark
+  // candidate positions (below the pixel's n_contrib) rather than blends, and
+  // the pair counts only if it passes the forward's alpha gate, evaluated with
+  // the same arithmetic (Alg. 2's replay without stored decisions).
+  template <bool GATED>
   __device__ __forceinline__ bool visit(const uint32_t (&bw)[PX], uint32_t bit, const float4& r0, const float4& r1,
-                                        const float4& r2, const float4& r3, float fx, int py0, float amax,
+                                        const float4& r2, const float4& r3, float fx, int py0, float amin, float amax,
                                         float (&gr)[16]) {
     const float a_ = -2.0f * kLn2 * r0.z, b_ = -kLn2 * r0.w, c_ = -2.0f * kLn2 * r1.x;
     bool contrib = false;
@@ -355,10 +362,15 @@ struct BwdPixels {
     for (int k = 0; k < 16; ++k) gr[k] = 0.0f;
 #pragma unroll
     for (int p = 0; p < PX; ++p) {
-      if (!((bw[p] >> bit) & 1u)) continue;  // not blended in the forward pass
+      if (!((bw[p] >> bit) & 1u)) continue;  // not blended (not reached) in the forward pass
       PairEval e;
-      // blended in the forward pass: the same arithmetic passes the alpha gate again
-      eval_pair<MODE, false>(r0, r1, r2, r3.w, fx, (float)(py0 + p) + 0.5f, e);
+      if (GATED) {
+        if (!eval_pair<MODE, true>(r0, r1, r2, r3.w, fx, (float)(py0 + p) + 0.5f, e)) continue;
+        if (fminf(e.alpha, amax) < amin) continue;
+      } else {
+        // blended in the forward pass: the same arithmetic passes the alpha gate again
+        eval_pair<MODE, false>(r0, r1, r2, r3.w, fx, (float)(py0 + p) + 0.5f, e);
+      }
       const float alpha = fminf(e.alpha, amax);
       contrib = true;
       const float one_m = 1.0f - alpha;
@@ -430,19 +442,25 @@ struct BwdPixels<MODE, PX, true> {
     put(g1[p >> 1], p, c1);
     put(g2[p >> 1], p, c2);
   }
+  template <bool GATED>
   __device__ __forceinline__ bool visit(const uint32_t (&bw)[PX], uint32_t bit, const float4& r0, const float4& r1,
-                                        const float4& r2, const float4& r3, float fx, int py0, float amax,
+                                        const float4& r2, const float4& r3, float fx, int py0, float amin, float amax,
                                         float (&gr)[16]) {
     const float a_ = -2.0f * kLn2 * r0.z, b_ = -kLn2 * r0.w, c_ = -2.0f * kLn2 * r1.x;
     float2 acc[16];
     bool any = false;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      const bool m0 = (bw[2 * q] >> bit) & 1u, m1 = (bw[2 * q + 1] >> bit) & 1u;
+      bool m0 = (bw[2 * q] >> bit) & 1u, m1 = (bw[2 * q + 1] >> bit) & 1u;
       float2 t[16];
-      any |= m0 || m1;
       PairEval2 e;
-      eval_pair2<MODE>(r0, r1, r2, fx, (float)(py0 + 2 * q) + 0.5f, e);
+      const float2 p2 = pair2_exponent(r0, r1, fx, (float)(py0 + 2 * q) + 0.5f, e);
+      pair2_alpha<MODE>(r1, r2, p2, e);
+      if (GATED) {  // the forward's gate, with its arithmetic
+        m0 = m0 && p2.x >= r3.w && fminf(e.alpha.x, amax) >= amin;
+        m1 = m1 && p2.y >= r3.w && fminf(e.alpha.y, amax) >= amin;
+      }
+      any |= m0 || m1;
       const float2 alpha = make_float2(m0 ? fminf(e.alpha.x, amax) : 0.0f, m1 ? fminf(e.alpha.y, amax) : 0.0f);
       const float2 one_m = add2(f2(1.0f), neg2(alpha));
       // T_k = T_{k+1} / (1 - alpha) as a product with the reciprocal (rcp.approx)
@@ -517,7 +535,9 @@ cudaError_t launch_d2_clear(Status* status, float4* d2, int64_t n4, int sms, cud
   return cudaGetLastError();
 }
 
-template <int MODE, int PX, int BATCH>
+// GATED: no blend masks (recompute_keys plans); every position below a
+// pixel's n_contrib is a candidate and the pair's own gate decides.
+template <int MODE, int PX, int BATCH, bool GATED>
 __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
   pdl_entry();
   if (blockIdx.x == 0 && threadIdx.x == 0) a.status->d2_fresh = 0u;  // read by the next d2_clear_kernel only
@@ -536,7 +556,7 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
   const float fx = (float)px + 0.5f;
   const uint2 range = tile_range(a.ranges, tile);
   const uint32_t* vals = a.status->sorted_buf ? a.vals1 : a.vals0;
-  const float amax = a.cfg.alpha_max;
+  const float amin = a.cfg.alpha_min, amax = a.cfg.alpha_max;
   const int lane = threadIdx.x & 31;
   const int64_t plane = (int64_t)tc.vi.width * tc.vi.height;
   const float* gimg = a.d_images + tc.vi.image_offset;
@@ -544,7 +564,7 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
   BwdPixels<MODE, PX> pix;
   uint32_t my_end[PX], bw[PX];
   const int pi0 = pm.pi0;
-  const uint32_t* mbase = mask_tile_base(a.mask, range, tile);
+  const uint32_t* mbase = GATED ? nullptr : mask_tile_base(a.mask, range, tile);
   uint32_t my_max = 0;
 #pragma unroll
   for (int p = 0; p < PX; ++p) {
@@ -583,8 +603,14 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
       const uint32_t chunk_first = range.x + (chunk << 5);  // position of bit 0
       const int jlo = chunk_first > bstart ? (int)(chunk_first - bstart) : 0;
 #pragma unroll
-      for (int p = 0; p < PX; ++p)
-        bw[p] = chunk_first < my_end[p] ? mbase[chunk * 256 + pi0 + p * kTile] : 0u;
+      for (int p = 0; p < PX; ++p) {
+        if (GATED)  // the positions below the pixel's end
+          bw[p] = chunk_first < my_end[p]
+                      ? (my_end[p] - chunk_first >= 32u ? 0xffffffffu : (1u << (my_end[p] - chunk_first)) - 1u)
+                      : 0u;
+        else
+          bw[p] = chunk_first < my_end[p] ? mbase[chunk * 256 + pi0 + p * kTile] : 0u;
+      }
       uint32_t mine = 0u;
 #pragma unroll
       for (int p = 0; p < PX; ++p) mine |= bw[p];
@@ -597,7 +623,7 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
         const float4 r0 = s_r0[j], r1 = s_r1[j], r3 = s_r3[j];
         const float4 r2 = MODE == MODE_PLAIN ? r0 : s_r2[j];
         float gr[16];
-        const bool contrib = pix.visit(bw, bit, r0, r1, r2, r3, fx, py0, amax, gr);
+        const bool contrib = pix.template visit<GATED>(bw, bit, r0, r1, r2, r3, fx, py0, amin, amax, gr);
         // true whenever the position is reached (it is a bit of the warp's
         // OR); the vote stays as the point where the warp meets before the
         // shuffles, which measured faster than leaving it out
@@ -651,19 +677,22 @@ static void launch_fwd_rec(const RenderArgs& a, int mode, unsigned grid, cudaStr
   }
 }
 
-template <int PX, int BATCH>
+template <int PX, int BATCH, bool GATED>
 static void launch_bwd_px(const RenderArgs& a, int mode, unsigned grid, cudaStream_t st) {
-  if (mode == MODE_PLAIN) launch_pdl(render_bwd_kernel<MODE_PLAIN, PX, BATCH>, dim3(grid), dim3(256 / PX), 0, st, a);
-  else if (mode == MODE_TWO) launch_pdl(render_bwd_kernel<MODE_TWO, PX, BATCH>, dim3(grid), dim3(256 / PX), 0, st, a);
-  else launch_pdl(render_bwd_kernel<MODE_SPLIT, PX, BATCH>, dim3(grid), dim3(256 / PX), 0, st, a);
+  if (mode == MODE_PLAIN)
+    launch_pdl(render_bwd_kernel<MODE_PLAIN, PX, BATCH, GATED>, dim3(grid), dim3(256 / PX), 0, st, a);
+  else if (mode == MODE_TWO)
+    launch_pdl(render_bwd_kernel<MODE_TWO, PX, BATCH, GATED>, dim3(grid), dim3(256 / PX), 0, st, a);
+  else
+    launch_pdl(render_bwd_kernel<MODE_SPLIT, PX, BATCH, GATED>, dim3(grid), dim3(256 / PX), 0, st, a);
 }
 
-template <int BATCH>
+template <int BATCH, bool GATED>
 static void launch_bwd_batch(const RenderArgs& a, int mode, unsigned grid, cudaStream_t st) {
   switch (a.px_bwd) {
-    case 1: launch_bwd_px<1, BATCH>(a, mode, grid, st); break;
-    case 4: launch_bwd_px<4, BATCH>(a, mode, grid, st); break;
-    default: launch_bwd_px<2, BATCH>(a, mode, grid, st); break;
+    case 1: launch_bwd_px<1, BATCH, GATED>(a, mode, grid, st); break;
+    case 4: launch_bwd_px<4, BATCH, GATED>(a, mode, grid, st); break;
+    default: launch_bwd_px<2, BATCH, GATED>(a, mode, grid, st); break;
   }
 }
 
@@ -679,8 +708,14 @@ cudaError_t launch_render_fwd(const RenderArgs& a, int mode, int64_t total_tiles
 cudaError_t launch_render_bwd(const RenderArgs& a, int mode, int64_t total_tiles, cudaStream_t st) {
   if (total_tiles == 0) return cudaSuccess;
   const unsigned grid = (unsigned)total_tiles;
-  if (a.batch_bwd == 128) launch_bwd_batch<128>(a, mode, grid, st);
-  else launch_bwd_batch<256>(a, mode, grid, st);
+  const bool gated = a.mask == nullptr;  // no blend masks: replay with the gate
+  if (a.batch_bwd == 128) {
+    if (gated) launch_bwd_batch<128, true>(a, mode, grid, st);
+    else launch_bwd_batch<128, false>(a, mode, grid, st);
+  } else {
+    if (gated) launch_bwd_batch<256, true>(a, mode, grid, st);
+    else launch_bwd_batch<256, false>(a, mode, grid, st);
+  }
   count_launches(1);
   return cudaGetLastError();
 }

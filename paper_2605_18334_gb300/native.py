@@ -14,7 +14,7 @@ import threading
 from . import build as _build
 
 SR_MAX_VIEWS = 256
-SR_ABI_VERSION = 2
+SR_ABI_VERSION = 3
 
 SR_OK, SR_ERR_INVALID, SR_ERR_CAPACITY, SR_ERR_CUDA, SR_ERR_TIMEOUT, SR_ERR_UNSUPPORTED = range(6)
 SR_F32, SR_BF16, SR_F16 = 0, 1, 2
@@ -67,7 +67,8 @@ class sr_config(C.Structure):
                 ("t_stop", C.c_float), ("dilation", C.c_float), ("fov_clamp", C.c_float), ("near_z", C.c_float),
                 ("bg", C.c_float * 3), ("antialias_comp", C.c_int32), ("fwd_batch", C.c_int32),
                 ("sort_spin_limit", C.c_int32), ("fwd_pixels_per_thread", C.c_int32),
-                ("bwd_pixels_per_thread", C.c_int32), ("forward_only", C.c_int32), ("bwd_batch", C.c_int32)]
+                ("bwd_pixels_per_thread", C.c_int32), ("forward_only", C.c_int32), ("bwd_batch", C.c_int32),
+                ("recompute_keys", C.c_int32)]
 
 
 class sr_grads(C.Structure):
@@ -79,7 +80,7 @@ class sr_plan(C.Structure):
     _fields_ = [("abi_version", C.c_int32), ("n_views", C.c_int32), ("n", C.c_int64), ("sh_degree", C.c_int32),
                 ("tile_w", C.c_int32), ("tile_h", C.c_int32), ("sort_passes", C.c_int32), ("sort_bits", C.c_int32),
                 ("render_mode", C.c_int32), ("two_opacities", C.c_int32), ("has_split", C.c_int32),
-                ("forward_only", C.c_int32), ("reserved1_", C.c_int32),
+                ("forward_only", C.c_int32), ("recompute_keys", C.c_int32),
                 ("key_capacity", C.c_int64), ("total_tiles", C.c_int64), ("total_pixels", C.c_int64),
                 ("tile_base", C.c_int64 * (SR_MAX_VIEWS + 1)), ("image_offset", C.c_int64 * (SR_MAX_VIEWS + 1)),
                 ("pixel_offset", C.c_int64 * (SR_MAX_VIEWS + 1)), ("width", C.c_int32 * SR_MAX_VIEWS),

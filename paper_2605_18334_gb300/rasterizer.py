@@ -40,6 +40,7 @@ class Config:
     forward_only: bool = False       # plan without backward state (blend masks)
     fwd_batch: int = 0               # records staged per batch by the forward composite (0: 256)
     bwd_batch: int = 0               # ... by the backward composite (0: 128)
+    recompute_keys: bool = False     # plan without blend masks: the backward rebuilds the key lists
 
     def to_c(self) -> N.sr_config:
         c = N.sr_config()
@@ -55,6 +56,7 @@ class Config:
         c.forward_only = 1 if self.forward_only else 0
         c.fwd_batch = int(self.fwd_batch)
         c.bwd_batch = int(self.bwd_batch)
+        c.recompute_keys = 1 if self.recompute_keys else 0
         return c
 
 
@@ -256,17 +258,29 @@ class Rasterizer:
                                 _stream_ptr(stream))
         return out
 
+    def frame_state(self) -> dict:
+        """Copies of what a backward of the last forward needs besides the
+        workspace (per-pixel T and n_contrib, the cameras): with a
+        recompute_keys plan, ``backward(..., state=...)`` can run after the
+        rasterizer has rendered other frames."""
+        return {"t_final": self.t_final.clone(), "n_contrib": self.n_contrib.clone(),
+                "cams_dev": self.cams_dev.clone()}
+
     def backward(self, g: Gaussians, d_images: torch.Tensor, stream=None, want_stats: bool = False,
-                 out: dict | None = None) -> dict:
+                 out: dict | None = None, state: dict | None = None) -> dict:
         """Gradients of sum(d_images * images) w.r.t. every attribute (FP32),
         through sr_render_bwd (into ``out``'s tensors when given, e.g. the
-        previous call's result)."""
+        previous call's result).  ``state`` (from frame_state(), recompute_keys
+        plans only): the frame to differentiate, if not the last one."""
         if d_images.dtype != torch.float32 or not d_images.is_contiguous() or d_images.numel() != self.images.numel():
             raise ValueError("d_images must be a contiguous float32 tensor shaped like the image buffer")
+        if state is not None and not self.config.recompute_keys:
+            raise ValueError("a saved frame state can be replayed only by a recompute_keys plan")
+        st = state or {"t_final": self.t_final, "n_contrib": self.n_contrib, "cams_dev": self.cams_dev}
         dev = self.device
         n = g.n
         if out is not None and out["means"].shape[0] == n and (out.get("means2d_abs") is not None) == want_stats:
-            return self._backward_into(g, d_images, stream, out)
+            return self._backward_into(g, d_images, stream, out, st)
         out = dict(means=torch.empty(n, 3, device=dev), log_scales=torch.empty(n, 3, device=dev),
                    quats=torch.empty(n, 4, device=dev),
                    opacity_logits=torch.empty(g.opacity_logits.shape, device=dev),
@@ -280,19 +294,19 @@ class Rasterizer:
                   "depth_grad"):
             t = out.get(k)
             setattr(gr, k, t.data_ptr() if t is not None else None)
-        N.sr_render_bwd(self.plan, g.to_c(), self.cams_dev.data_ptr(), self.cfg_c, self.ws.data_ptr(),
-                        d_images.data_ptr(), self.t_final.data_ptr(), self.n_contrib.data_ptr(), gr,
+        N.sr_render_bwd(self.plan, g.to_c(), st["cams_dev"].data_ptr(), self.cfg_c, self.ws.data_ptr(),
+                        d_images.data_ptr(), st["t_final"].data_ptr(), st["n_contrib"].data_ptr(), gr,
                         _stream_ptr(stream))
         return out
 
-    def _backward_into(self, g: Gaussians, d_images: torch.Tensor, stream, out: dict) -> dict:
+    def _backward_into(self, g: Gaussians, d_images: torch.Tensor, stream, out: dict, st: dict) -> dict:
         gr = N.sr_grads()
         for k in ("means", "log_scales", "quats", "opacity_logits", "skew", "sh", "split_dir", "means2d_abs",
                   "depth_grad"):
             t = out.get(k)
             setattr(gr, k, t.data_ptr() if t is not None else None)
-        N.sr_render_bwd(self.plan, g.to_c(), self.cams_dev.data_ptr(), self.cfg_c, self.ws.data_ptr(),
-                        d_images.data_ptr(), self.t_final.data_ptr(), self.n_contrib.data_ptr(), gr,
+        N.sr_render_bwd(self.plan, g.to_c(), st["cams_dev"].data_ptr(), self.cfg_c, self.ws.data_ptr(),
+                        d_images.data_ptr(), st["t_final"].data_ptr(), st["n_contrib"].data_ptr(), gr,
                         _stream_ptr(stream))
         return out
 
@@ -418,8 +432,8 @@ class Rasterizer:
         render.cu: tile t's word for pixel i of the tile and positions
         start + 32c .. start + 32c + 31 of its range at ((start >> 5) + t + c)
         * 256 + i, valid up to the word holding the pixel's last blend)."""
-        if self.plan.forward_only:
-            raise ValueError("forward-only plans keep no blend masks")
+        if self.plan.forward_only or self.plan.recompute_keys:
+            raise ValueError("forward-only and recompute-keys plans keep no blend masks")
         words = (int(self.plan.key_capacity) // 32 + int(self.plan.total_tiles) + 1) * 256
         return self._slot(self._S_MASK, 4 * words).view(torch.int32)
 
@@ -508,12 +522,14 @@ def shard_views(cameras: list, rank: int, world: int) -> list:
 def render_views_recompute(g: Gaussians, cameras: list, d_images: list, config: Config | None = None,
                            rasterizers: dict | None = None):
     """Forward and backward of several views through one single-view
-    workspace per image size, rebuilding each view's tile key list for its
-    backward instead of keeping it (the key lists, records and blend masks of
-    a view live only while that view is processed).  Returns the images
-    (list of [3,H,W] tensors) and the attribute gradients summed over views.
-    ``rasterizers`` may carry plans from an earlier call (keyed by size)."""
-    config = config or Config()
+    recompute_keys workspace per image size: every view is rendered first
+    (keeping only its image, per-pixel T and n_contrib), then each view's
+    backward rebuilds its records and tile key lists inside sr_render_bwd and
+    replays with the alpha gate (no blend masks, no key list kept between
+    the passes).  Returns the images (list of [3,H,W] tensors) and the
+    attribute gradients summed over views.  ``rasterizers`` may carry plans
+    from an earlier call (keyed by size)."""
+    config = Config(**{**config.__dict__, "recompute_keys": True}) if config else Config(recompute_keys=True)
     rasterizers = {} if rasterizers is None else rasterizers
 
     def plan_for(cam):
@@ -525,15 +541,15 @@ def render_views_recompute(g: Gaussians, cameras: list, d_images: list, config: 
         r.set_cameras([c])
         return r
 
-    images = []
-    for cam in cameras:  # forward: keep only the images
+    images, states = [], []
+    for cam in cameras:  # forward: keep the images and the per-pixel state
         r = plan_for(cam)
         images.append(r.forward(g).view(3, r.plan.height[0], r.plan.width[0]).clone())
+        states.append(r.frame_state())
     total = None
-    for cam, dimg in zip(cameras, d_images):  # backward: rebuild the keys, then replay
+    for cam, dimg, st in zip(cameras, d_images, states):  # backward: the keys are rebuilt by sr_render_bwd
         r = plan_for(cam)
-        r.forward(g)
-        gr = r.backward(g, dimg.reshape(-1).contiguous())
+        gr = r.backward(g, dimg.reshape(-1).contiguous(), state=st)
         if total is None:
             total = gr
         else:
@@ -551,13 +567,15 @@ class _RasterizeFn(torch.autograd.Function):
         images = rast.forward(g).clone()
         ctx.rast = rast
         ctx.g = g
+        # a recompute_keys plan may render other frames before this backward
+        ctx.state = rast.frame_state() if rast.config.recompute_keys else None
         ctx.mark_non_differentiable()
         return images
 
     @staticmethod
     def backward(ctx, d_images):
         g = ctx.g
-        gr = ctx.rast.backward(g, d_images.contiguous().float())
+        gr = ctx.rast.backward(g, d_images.contiguous().float(), state=ctx.state)
         cast = lambda t, like: None if t is None else t.to(like.dtype)
         return (None, None, gr["means"], cast(gr["log_scales"], g.log_scales), gr["quats"], gr["opacity_logits"],
                 cast(gr["skew"], g.skew), cast(gr["sh"], g.sh),

@@ -239,3 +239,19 @@ def test_autotune_keeps_the_default_within_the_margin():
     # a default that was not timed: the fastest candidate
     assert _prefer_default({1: 0.76, 4: 0.64}, 2) == 4
     assert _prefer_default({128: 0.456, 256: 0.4475}, 128, margin=0.0) == 256
+
+
+def test_recompute_keys_plan_keeps_no_blend_masks_and_excludes_forward_only(lib):
+    from paper_2605_18334_gb300.rasterizer import Config
+
+    g = N.sr_gaussians()
+    g.n, g.sh_degree = 1000, 3
+    cam = N.sr_camera()
+    cam.width, cam.height = 640, 360
+    base = N.sr_plan_init(Config().to_c(), g, [cam], 1 << 16)
+    rk = N.sr_plan_init(Config(recompute_keys=True).to_c(), g, [cam], 1 << 16)
+    assert rk.recompute_keys == 1 and base.recompute_keys == 0
+    assert rk.ws_bytes < base.ws_bytes
+    with pytest.raises(N.SkewRasterError) as e:
+        N.sr_plan_init(Config(recompute_keys=True, forward_only=True).to_c(), g, [cam], 1 << 16)
+    assert e.value.status == N.SR_ERR_INVALID

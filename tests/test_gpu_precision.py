@@ -29,9 +29,10 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():  # pragma: no cover - CPU-only container
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
-# stated storage-error bounds (max abs per channel, every pixel), from the
-# figures these tests print on the workloads above, rounded up
-STORAGE_BOUND = {torch.bfloat16: 0.05, torch.float16: 0.01}
+# stated storage-error bounds (max abs per channel, every pixel): the
+# largest figures these tests measured (BF16 0.020 and FP16 0.0142 on the 1M
+# frame, BF16 SH alone 0.010 on the 5M views) times 1.5, rounded up
+STORAGE_BOUND = {torch.bfloat16: 0.03, torch.float16: 0.02}
 
 
 def _errors(r, v, scene, deq, cam, cfg, ref_fp32=None):
@@ -61,8 +62,8 @@ def test_storage_error_1m_1080p_bf16_and_fp16():
         torch.cuda.synchronize()
         arith, smax, smean, ref = _errors(r, 0, sc, dequantised(sc, dt, dt, dt), cam, cfg, ref)
         print(f"precision unbounded_1m_1080p {str(dt).split('.')[-1]} (SH, log-scales, skew): arithmetic max abs "
-              f"{arith:.3e}; storage max abs per channel {np.array2string(smax, precision=3)} mean "
-              f"{np.array2string(smean, precision=3)}")
+              f"{arith:.3e}; storage max abs per channel {np.array2string(smax, precision=4)} mean "
+              f"{np.array2string(smean, formatter={'float_kind': lambda x: f'{x:.2e}'})}")
         assert arith <= IMG_ATOL
         assert smax.max() <= STORAGE_BOUND[dt]
         del r, g
@@ -85,7 +86,9 @@ def test_storage_error_5m_mixed_bf16_sh_8_views_1080p():
         worst_a = max(worst_a, arith)
         worst_s = np.maximum(worst_s, smax)
         means.append(smean)
+    mean = np.mean(means, 0)
     print(f"precision mixed_5m 8x1080p bf16 (SH): arithmetic max abs {worst_a:.3e}; storage max abs per channel "
-          f"{np.array2string(worst_s, precision=3)} mean {np.array2string(np.mean(means, 0), precision=3)}")
+          f"{np.array2string(worst_s, precision=4)} mean "
+          f"{np.array2string(mean, formatter={'float_kind': lambda x: f'{x:.2e}'})}")
     assert worst_a <= IMG_ATOL
     assert worst_s.max() <= STORAGE_BOUND[dt]
