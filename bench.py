@@ -57,6 +57,10 @@ def parse():
                     help="forward records per staged batch when the launch shape is fixed")
     ap.add_argument("--bwd-batch", type=int, default=128, choices=[128, 256],
                     help="backward records per staged batch when the launch shape is fixed")
+    ap.add_argument("--fwd-blocks", type=int, default=0, help="forward blocks per SM cap when the shape is fixed")
+    ap.add_argument("--bwd-blocks", type=int, default=0, help="backward blocks per SM cap when the shape is fixed")
+    ap.add_argument("--persistent", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="persistent composites (bit 0 forward, bit 1 backward) when the shape is fixed")
     return ap.parse_args()
 
 
@@ -229,6 +233,8 @@ def run_ours(args):
     if args.fwd_px and args.bwd_px:  # fixed launch shapes (e.g. for a profiler run)
         r.set_pixels_per_thread(args.fwd_px, args.bwd_px)
         r.set_batch(args.fwd_batch, args.bwd_batch)
+        r.set_blocks_per_sm(args.fwd_blocks, args.bwd_blocks)
+        r.set_persistent(bool(args.persistent & 1), bool(args.persistent & 2))
         tune = {"fwd_pixels_per_thread": args.fwd_px, "bwd_pixels_per_thread": args.bwd_px, "fwd_ms": {},
                 "bwd_ms": {}, "fixed": True}
     else:
@@ -279,7 +285,8 @@ def run_ours(args):
     cfgd["launch"] = {"fwd_pixels_per_thread": tune["fwd_pixels_per_thread"],
                       "bwd_pixels_per_thread": tune["bwd_pixels_per_thread"],
                       "fwd_batch": r.config.fwd_batch or 256, "bwd_batch": r.config.bwd_batch or 128,
-                      "autotuned": not tune.get("fixed")}
+                      "fwd_blocks_per_sm": r.config.fwd_blocks_per_sm, "bwd_blocks_per_sm": r.config.bwd_blocks_per_sm,
+                      "persistent": r.config.persistent, "autotuned": not tune.get("fixed")}
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K,
            "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfgd,
@@ -297,7 +304,13 @@ def run_ours(args):
     out["autotune_ms"] = {"fwd": {str(k): round(v, 4) for k, v in tune["fwd_ms"].items()},
                           "bwd": {str(k): round(v, 4) for k, v in tune["bwd_ms"].items()},
                           "fwd_batch": {str(k): round(v, 4) for k, v in tune.get("fwd_batch_ms", {}).items()},
-                          "bwd_batch": {str(k): round(v, 4) for k, v in tune.get("bwd_batch_ms", {}).items()}}
+                          "bwd_batch": {str(k): round(v, 4) for k, v in tune.get("bwd_batch_ms", {}).items()},
+                          "fwd_blocks_per_sm": {str(k): round(v, 4) for k, v in
+                                                tune.get("fwd_blocks_per_sm_ms", {}).items()},
+                          "bwd_blocks_per_sm": {str(k): round(v, 4) for k, v in
+                                                tune.get("bwd_blocks_per_sm_ms", {}).items()},
+                          "fwd_persistent": {str(k): round(v, 4) for k, v in tune.get("fwd_persistent_ms", {}).items()},
+                          "bwd_persistent": {str(k): round(v, 4) for k, v in tune.get("bwd_persistent_ms", {}).items()}}
 
     # roofline of the dominant stage (measured live with the events above)
     peaks = measured_peaks()
@@ -591,6 +604,17 @@ def trajectory(args, sc, dev, flush, n_views=64):
     torch.cuda.synchronize()
     K = max(3, args.steps // 4)
     ms_graph = timed(graph.replay, K, flush, stream)
+    # the composite alone, one block per tile against a persistent grid
+    composite = {}
+    chosen = r.config.persistent
+    for pers in (0, 1):
+        r.set_persistent(fwd=bool(pers))
+        for _ in range(3):
+            r.render_fwd()
+        composite["persistent" if pers else "block_per_tile"] = round(timed(lambda: r.render_fwd(), K, flush,
+                                                                            stream), 4)
+    r.config.persistent = chosen
+    r.cfg_c = r.config.to_c()
     # the same views one by one, each with its own plan (sized beforehand)
     singles = []
     for c in cams:
@@ -610,7 +634,9 @@ def trajectory(args, sc, dev, flush, n_views=64):
            "batched_graph_fwd_views_per_s": round(n_views / (ms_graph / 1e3), 2),
            "sequential_fwd_views_per_s": round(n_views / (ms_seq / 1e3), 2),
            "batched_ms": round(ms_graph, 3), "sequential_ms": round(ms_seq, 3),
-           "launch": {"fwd_pixels_per_thread": r.config.fwd_pixels_per_thread}}
+           "composite_ms": composite,
+           "launch": {"fwd_pixels_per_thread": r.config.fwd_pixels_per_thread, "fwd_batch": r.config.fwd_batch,
+                      "fwd_blocks_per_sm": r.config.fwd_blocks_per_sm, "persistent": r.config.persistent}}
     del singles, r, graph
     torch.cuda.empty_cache()
     return res

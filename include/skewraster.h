@@ -119,6 +119,12 @@ typedef struct sr_config {
                                  non-blocking sr_bin_sort) and replays every position up to each pixel's
                                  n_contrib with the alpha gate (Alg. 2), so the workspace may serve other
                                  frames between a forward and its backward.  Not with forward_only. */
+  int32_t persistent;         /* bit 0: sr_render_fwd, bit 1: the backward composite launch as many blocks
+                                 as fit on the GPU, each taking tile after tile (longest key lists first)
+                                 from a counter, instead of one block per tile; results are the same */
+  int32_t fwd_blocks_per_sm;  /* 0..32 (0 = as many as fit): cap on the blocks of sr_render_fwd resident on
+                                 an SM (each block then reserves a matching share of shared memory) */
+  int32_t bwd_blocks_per_sm;  /* the same for the backward composite */
 } sr_config;
 
 /* Gradients of the loss w.r.t. the attributes, FP32, device, caller-owned,

@@ -64,6 +64,9 @@ sr_status check_config(const sr_config* c) {
   if (c->bwd_batch != 0 && c->bwd_batch != 128 && c->bwd_batch != 256) return SR_ERR_INVALID;
   if (c->recompute_keys != 0 && c->recompute_keys != 1) return SR_ERR_INVALID;
   if (c->recompute_keys && c->forward_only) return SR_ERR_INVALID;
+  if (c->persistent < 0 || c->persistent > 3) return SR_ERR_INVALID;
+  if (c->fwd_blocks_per_sm < 0 || c->fwd_blocks_per_sm > 32 || c->bwd_blocks_per_sm < 0 || c->bwd_blocks_per_sm > 32)
+    return SR_ERR_INVALID;
   return SR_OK;
 }
 
@@ -221,7 +224,7 @@ sr_status sr_plan_init(sr_plan* p, const sr_config* cfg, const sr_gaussians* g, 
   sizes[WS_MASK] = (p->forward_only || p->recompute_keys)
                        ? 0
                        : sizeof(uint32_t) * 256 * (size_t)(key_capacity / 32 + tb + 1);
-  sizes[WS_TILE_ORDER] = sizeof(uint32_t) * ((size_t)tb + 128);
+  sizes[WS_TILE_ORDER] = sizeof(uint32_t) * ((size_t)tb + 130);
   sizes[WS_SHJAC] = p->forward_only ? 0 : sizeof(float4) * 3 * (size_t)m;
   size_t off = 0;
   for (int k = 0; k < WS_NUM_SLOTS; ++k) {
@@ -359,6 +362,12 @@ static RenderArgs render_args(const sr_plan* p, const sr_config* cfg, void* ws) 
   r.batch_bwd = cfg->bwd_batch > 0 ? cfg->bwd_batch : 128;
   r.px_fwd = cfg->fwd_pixels_per_thread > 0 ? cfg->fwd_pixels_per_thread : 2;
   r.px_bwd = cfg->bwd_pixels_per_thread > 0 ? cfg->bwd_pixels_per_thread : 2;
+  r.n_order = (uint32_t)p->total_tiles;
+  r.persistent = 0;
+  r.work = w.tile_order + p->total_tiles + 128;  // [0]: forward counter, [1]: backward counter
+  r.sms = device_sms();
+  r.blocks_fwd = cfg->fwd_blocks_per_sm;
+  r.blocks_bwd = cfg->bwd_blocks_per_sm;
   return r;
 }
 
@@ -373,6 +382,7 @@ sr_status sr_render_fwd(const sr_plan* p, const sr_config* cfg, void* ws, float*
   r.images = images;
   r.t_final = t_final;
   r.n_contrib = n_contrib;
+  r.persistent = (cfg->persistent & 1) ? 1 : 0;
   return from_cuda(launch_render_fwd(r, p->render_mode, p->total_tiles, static_cast<cudaStream_t>(stream)));
 }
 
@@ -396,6 +406,8 @@ sr_status sr_render_bwd_composite(const sr_plan* p, const sr_config* cfg, void* 
   r.t_final = const_cast<float*>(t_final);
   r.n_contrib = const_cast<uint32_t*>(n_contrib);
   r.d_images = d_images;
+  r.persistent = (cfg->persistent & 2) ? 1 : 0;
+  r.work += 1;
   return from_cuda(launch_render_bwd(r, p->render_mode, p->total_tiles, st));
 }
 

@@ -38,6 +38,7 @@ enum WsSlot {
   WS_FOOT,         // float4[M][4] footprint constants or packed row spans (row_tile_span)
   WS_MASK,         // uint32_t[(cap/32 + tiles + 1) * 256] per-pixel blend masks (see render.cu)
   WS_TILE_ORDER,   // uint32_t[tiles] composite order (longest key lists first) + uint32_t[2][64] counters
+                   // of the ordering + the tile counters of persistent forward and backward composites
   WS_SHJAC,        // float4[M][3] d colour / d view direction (3x3) and the colour clamp bits (backward only)
   WS_NUM_SLOTS
 };

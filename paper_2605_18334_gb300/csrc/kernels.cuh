@@ -56,6 +56,12 @@ struct RenderArgs {     // forward and backward composite
   int batch_bwd;        // (128, 256)
   int px_fwd;           // pixels per thread (1, 2, 4)
   int px_bwd;
+  uint32_t n_order;     // tiles in tile_order
+  int persistent;       // 1: blocks take tiles from *work until none is left
+  uint32_t* work;       // tile counter of a persistent launch (zeroed before it)
+  int sms;
+  int blocks_fwd;       // cap on resident blocks per SM (0: as many as fit)
+  int blocks_bwd;
 };
 
 struct DensifyArgs {     // densification

@@ -1,7 +1,8 @@
 // Per-tile compositing of skew Gaussians: forward (Alg. 1, Eq. color) and
 // the reverse replay that differentiates it (Alg. 2).
 //
-// One block per 16x16 tile; each thread owns PX vertically adjacent pixels
+// One block per 16x16 tile (or, in persistent launches, blocks that take
+// tile after tile from a counter); each thread owns PX vertically adjacent pixels
 // of one column, so a warp covers an 8-wide block of 4*PX rows.  The tile's
 // depth-sorted records are staged into shared memory in batches (128, 256 or
 // 512 gathered 64-byte records), then every pixel walks the batch:
@@ -93,6 +94,15 @@ __device__ __forceinline__ uint32_t* mask_tile_base(uint32_t* mask, uint2 range,
   return mask + ((int64_t)(range.x >> 5) + tile) * 256;
 }
 
+// Persistent launches: a block takes tile after tile of the composite order
+// from a counter (zeroed before the launch) until none is left.
+__device__ __forceinline__ uint32_t next_work(uint32_t* counter, uint32_t* s_next) {
+  __syncthreads();  // the block is done with the previous tile and with *s_next
+  if (threadIdx.x == 0) *s_next = atomicAdd(counter, 1u);
+  __syncthreads();
+  return *s_next;
+}
+
 // occupancy target of the forward composite: 5 blocks of 256 threads per SM
 // for one pixel per thread (<= 51 registers), the compiler's choice otherwise
 template <int PX>
@@ -100,184 +110,188 @@ struct FwdMinBlocks {
   static constexpr int value = PX == 1 ? 5 : 1;
 };
 
-template <int MODE, int PX, bool REC, int BATCH>
+template <int MODE, int PX, bool REC, int BATCH, bool PERSIST>
 __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_kernel(RenderArgs a) {
   pdl_entry();
   constexpr int NT = 256 / PX;
   __shared__ float4 s_r0[BATCH], s_r1[BATCH], s_r2[MODE == MODE_PLAIN ? 1 : BATCH], s_r3[BATCH];
-  const int64_t tile = a.tile_order[blockIdx.x];
-  const TileCoord tc = tile_coord(a, tile);
-  const PixelMap pm = pixel_map<PX>(tc);
-  const int px = pm.px, py0 = pm.py0, pi0 = pm.pi0;
-  const float fx = (float)px + 0.5f;
-  const uint2 range = tile_range(a.ranges, tile);
-  const uint32_t* vals = a.status->sorted_buf ? a.vals1 : a.vals0;
-  const float amin = a.cfg.alpha_min, amax = a.cfg.alpha_max, tstop = a.cfg.t_stop;
-  uint32_t* mbase = REC ? mask_tile_base(a.mask, range, tile) : nullptr;
+  __shared__ uint32_t s_next;
+  for (uint32_t it = PERSIST ? next_work(a.work, &s_next) : blockIdx.x; it < a.n_order;
+       it = PERSIST ? next_work(a.work, &s_next) : a.n_order) {
+    const int64_t tile = a.tile_order[it];
+    const TileCoord tc = tile_coord(a, tile);
+    const PixelMap pm = pixel_map<PX>(tc);
+    const int px = pm.px, py0 = pm.py0, pi0 = pm.pi0;
+    const float fx = (float)px + 0.5f;
+    const uint2 range = tile_range(a.ranges, tile);
+    const uint32_t* vals = a.status->sorted_buf ? a.vals1 : a.vals0;
+    const float amin = a.cfg.alpha_min, amax = a.cfg.alpha_max, tstop = a.cfg.t_stop;
+    uint32_t* mbase = REC ? mask_tile_base(a.mask, range, tile) : nullptr;
 
-  // colour state: scalar, or (even PX) packed per pair of rows for FP32x2 arithmetic
-  constexpr bool PACKED = PX % 2 == 0;
-  constexpr int Q = (PX + 1) / 2;
-  float T[PX], C0[PX], C1[PX], C2[PX];
-  float2 T2[Q], D0[Q], D1[Q], D2[Q];
-  uint32_t last[PX], stop[PX], mw[PX];
-  bool done[PX];
-  int active = 0;  // pixels of this thread still compositing
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    T2[q] = f2(1.0f);
-    D0[q] = D1[q] = D2[q] = f2(0.0f);
-  }
-#pragma unroll
-  for (int p = 0; p < PX; ++p) {
-    T[p] = 1.0f;
-    C0[p] = C1[p] = C2[p] = 0.0f;
-    last[p] = 0;
-    stop[p] = range.y;
-    mw[p] = 0u;
-    done[p] = !(px < tc.vi.width && py0 + p < tc.vi.height);
-    active += done[p] ? 0 : 1;
-  }
-  uint32_t blended = 0;
-  for (uint32_t start = range.x; start < range.y; start += BATCH) {
-    if (__syncthreads_count(active == 0) == NT) break;
-    stage_batch<MODE, BATCH>(a, vals, start, range.y, NT, s_r0, s_r1, s_r2, s_r3, nullptr);
-    __syncthreads();
-    const int cnt = (int)min((uint32_t)BATCH, range.y - start);
-    if (active) {
-      for (int jc = 0; jc < cnt; jc += 32) {  // chunks of 32 positions (one mask word)
-        const int jend = min(cnt, jc + 32);
-        const uint32_t chunk = (start - range.x + jc) >> 5;
-        for (int j = jc; j < jend; ++j) {
-          const float4 r0 = s_r0[j], r1 = s_r1[j], r3 = s_r3[j];
-          const float4 r2 = MODE == MODE_PLAIN ? r0 : s_r2[j];
-          if constexpr (PACKED) {
-            // rows 2q and 2q + 1 together; a row that fails the gate, the
-            // alpha_min test or has stopped takes alpha = 0 in the packed
-            // blend, which leaves its T and colour unchanged exactly
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-              if (done[2 * q] && done[2 * q + 1]) continue;
-              PairEval2 e;
-              const float2 p2 = pair2_exponent(r0, r1, fx, (float)(py0 + 2 * q) + 0.5f, e);
-              const bool g0 = !done[2 * q] && p2.x >= r3.w, g1 = !done[2 * q + 1] && p2.y >= r3.w;
-              if (!(g0 || g1)) continue;
-              pair2_alpha<MODE>(r1, r2, p2, e);
-              const float al0 = fminf(e.alpha.x, amax), al1 = fminf(e.alpha.y, amax);
-              const bool b0 = g0 && al0 >= amin, b1 = g1 && al1 >= amin;
-              if (!(b0 || b1)) continue;
-              float2 al = make_float2(b0 ? al0 : 0.0f, b1 ? al1 : 0.0f);
-              float2 Tn = fma2(neg2(T2[q]), al, T2[q]);
-              const bool s0 = b0 && Tn.x < tstop, s1 = b1 && Tn.y < tstop;
-              if (s0 || s1) {
-                if (s0) {
-                  done[2 * q] = true;
-                  stop[2 * q] = start + j + 1;
-                  if (REC) mbase[chunk * 256 + pi0 + 2 * q * kTile] = mw[2 * q];
-                  al.x = 0.0f;
-                  Tn.x = T2[q].x;
-                  --active;
+    // colour state: scalar, or (even PX) packed per pair of rows for FP32x2 arithmetic
+    constexpr bool PACKED = PX % 2 == 0;
+    constexpr int Q = (PX + 1) / 2;
+    float T[PX], C0[PX], C1[PX], C2[PX];
+    float2 T2[Q], D0[Q], D1[Q], D2[Q];
+    uint32_t last[PX], stop[PX], mw[PX];
+    bool done[PX];
+    int active = 0;  // pixels of this thread still compositing
+  #pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      T2[q] = f2(1.0f);
+      D0[q] = D1[q] = D2[q] = f2(0.0f);
+    }
+  #pragma unroll
+    for (int p = 0; p < PX; ++p) {
+      T[p] = 1.0f;
+      C0[p] = C1[p] = C2[p] = 0.0f;
+      last[p] = 0;
+      stop[p] = range.y;
+      mw[p] = 0u;
+      done[p] = !(px < tc.vi.width && py0 + p < tc.vi.height);
+      active += done[p] ? 0 : 1;
+    }
+    uint32_t blended = 0;
+    for (uint32_t start = range.x; start < range.y; start += BATCH) {
+      if (__syncthreads_count(active == 0) == NT) break;
+      stage_batch<MODE, BATCH>(a, vals, start, range.y, NT, s_r0, s_r1, s_r2, s_r3, nullptr);
+      __syncthreads();
+      const int cnt = (int)min((uint32_t)BATCH, range.y - start);
+      if (active) {
+        for (int jc = 0; jc < cnt; jc += 32) {  // chunks of 32 positions (one mask word)
+          const int jend = min(cnt, jc + 32);
+          const uint32_t chunk = (start - range.x + jc) >> 5;
+          for (int j = jc; j < jend; ++j) {
+            const float4 r0 = s_r0[j], r1 = s_r1[j], r3 = s_r3[j];
+            const float4 r2 = MODE == MODE_PLAIN ? r0 : s_r2[j];
+            if constexpr (PACKED) {
+              // rows 2q and 2q + 1 together; a row that fails the gate, the
+              // alpha_min test or has stopped takes alpha = 0 in the packed
+              // blend, which leaves its T and colour unchanged exactly
+  #pragma unroll
+              for (int q = 0; q < Q; ++q) {
+                if (done[2 * q] && done[2 * q + 1]) continue;
+                PairEval2 e;
+                const float2 p2 = pair2_exponent(r0, r1, fx, (float)(py0 + 2 * q) + 0.5f, e);
+                const bool g0 = !done[2 * q] && p2.x >= r3.w, g1 = !done[2 * q + 1] && p2.y >= r3.w;
+                if (!(g0 || g1)) continue;
+                pair2_alpha<MODE>(r1, r2, p2, e);
+                const float al0 = fminf(e.alpha.x, amax), al1 = fminf(e.alpha.y, amax);
+                const bool b0 = g0 && al0 >= amin, b1 = g1 && al1 >= amin;
+                if (!(b0 || b1)) continue;
+                float2 al = make_float2(b0 ? al0 : 0.0f, b1 ? al1 : 0.0f);
+                float2 Tn = fma2(neg2(T2[q]), al, T2[q]);
+                const bool s0 = b0 && Tn.x < tstop, s1 = b1 && Tn.y < tstop;
+                if (s0 || s1) {
+                  if (s0) {
+                    done[2 * q] = true;
+                    stop[2 * q] = start + j + 1;
+                    if (REC) mbase[chunk * 256 + pi0 + 2 * q * kTile] = mw[2 * q];
+                    al.x = 0.0f;
+                    Tn.x = T2[q].x;
+                    --active;
+                  }
+                  if (s1) {
+                    done[2 * q + 1] = true;
+                    stop[2 * q + 1] = start + j + 1;
+                    if (REC) mbase[chunk * 256 + pi0 + (2 * q + 1) * kTile] = mw[2 * q + 1];
+                    al.y = 0.0f;
+                    Tn.y = T2[q].y;
+                    --active;
+                  }
+                  if (active == 0) goto batch_done;
                 }
-                if (s1) {
-                  done[2 * q + 1] = true;
-                  stop[2 * q + 1] = start + j + 1;
-                  if (REC) mbase[chunk * 256 + pi0 + (2 * q + 1) * kTile] = mw[2 * q + 1];
-                  al.y = 0.0f;
-                  Tn.y = T2[q].y;
-                  --active;
+                const bool c0 = b0 && !s0, c1 = b1 && !s1;
+                const float2 w = mul2(al, T2[q]);
+                D0[q] = fma2(f2(r3.x), w, D0[q]);
+                D1[q] = fma2(f2(r3.y), w, D1[q]);
+                D2[q] = fma2(f2(r3.z), w, D2[q]);
+                T2[q] = Tn;
+                blended += (uint32_t)c0 + (uint32_t)c1;
+                if (REC) {
+                  mw[2 * q] |= (uint32_t)c0 << (j & 31);
+                  mw[2 * q + 1] |= (uint32_t)c1 << (j & 31);
                 }
-                if (active == 0) goto batch_done;
+                if (c0) last[2 * q] = start + j + 1 - range.x;
+                if (c1) last[2 * q + 1] = start + j + 1 - range.x;
               }
-              const bool c0 = b0 && !s0, c1 = b1 && !s1;
-              const float2 w = mul2(al, T2[q]);
-              D0[q] = fma2(f2(r3.x), w, D0[q]);
-              D1[q] = fma2(f2(r3.y), w, D1[q]);
-              D2[q] = fma2(f2(r3.z), w, D2[q]);
-              T2[q] = Tn;
-              blended += (uint32_t)c0 + (uint32_t)c1;
-              if (REC) {
-                mw[2 * q] |= (uint32_t)c0 << (j & 31);
-                mw[2 * q + 1] |= (uint32_t)c1 << (j & 31);
+            } else {
+  #pragma unroll
+              for (int p = 0; p < PX; ++p) {
+                if (PX > 1 && done[p]) continue;
+                PairEval e;
+                if (!eval_pair<MODE>(r0, r1, r2, r3.w, fx, (float)(py0 + p) + 0.5f, e)) continue;
+                const float alpha = fminf(e.alpha, amax);
+                if (alpha < amin) continue;
+                const float Tn = __fmaf_rn(-T[p], alpha, T[p]);
+                if (Tn < tstop) {
+                  done[p] = true;
+                  stop[p] = start + j + 1;
+                  if (REC) mbase[chunk * 256 + pi0 + p * kTile] = mw[p];
+                  if (--active == 0) goto batch_done;  // the only exit test, off the hot path
+                  continue;
+                }
+                ++blended;
+                if (REC) mw[p] |= 1u << (j & 31);
+                const float w = __fmul_rn(alpha, T[p]);
+                C0[p] = __fmaf_rn(r3.x, w, C0[p]);
+                C1[p] = __fmaf_rn(r3.y, w, C1[p]);
+                C2[p] = __fmaf_rn(r3.z, w, C2[p]);
+                T[p] = Tn;
+                last[p] = start + j + 1 - range.x;
               }
-              if (c0) last[2 * q] = start + j + 1 - range.x;
-              if (c1) last[2 * q + 1] = start + j + 1 - range.x;
-            }
-          } else {
-#pragma unroll
-            for (int p = 0; p < PX; ++p) {
-              if (PX > 1 && done[p]) continue;
-              PairEval e;
-              if (!eval_pair<MODE>(r0, r1, r2, r3.w, fx, (float)(py0 + p) + 0.5f, e)) continue;
-              const float alpha = fminf(e.alpha, amax);
-              if (alpha < amin) continue;
-              const float Tn = __fmaf_rn(-T[p], alpha, T[p]);
-              if (Tn < tstop) {
-                done[p] = true;
-                stop[p] = start + j + 1;
-                if (REC) mbase[chunk * 256 + pi0 + p * kTile] = mw[p];
-                if (--active == 0) goto batch_done;  // the only exit test, off the hot path
-                continue;
-              }
-              ++blended;
-              if (REC) mw[p] |= 1u << (j & 31);
-              const float w = __fmul_rn(alpha, T[p]);
-              C0[p] = __fmaf_rn(r3.x, w, C0[p]);
-              C1[p] = __fmaf_rn(r3.y, w, C1[p]);
-              C2[p] = __fmaf_rn(r3.z, w, C2[p]);
-              T[p] = Tn;
-              last[p] = start + j + 1 - range.x;
             }
           }
-        }
-        if (REC) {
-#pragma unroll
-          for (int p = 0; p < PX; ++p)
-            if (!done[p]) {
-              mbase[chunk * 256 + pi0 + p * kTile] = mw[p];
-              mw[p] = 0u;
-            }
+          if (REC) {
+  #pragma unroll
+            for (int p = 0; p < PX; ++p)
+              if (!done[p]) {
+                mbase[chunk * 256 + pi0 + p * kTile] = mw[p];
+                mw[p] = 0u;
+              }
+          }
         }
       }
+    batch_done:;
     }
-  batch_done:;
-  }
-  // work counters: pairs each pixel evaluated (up to its stop) and blended
-  unsigned long long tested = 0;
-#pragma unroll
-  for (int p = 0; p < PX; ++p)
-    if (px < tc.vi.width && py0 + p < tc.vi.height) tested += stop[p] - range.x;
-  unsigned long long b64 = blended;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    tested += __shfl_xor_sync(0xffffffffu, tested, o);
-    b64 += __shfl_xor_sync(0xffffffffu, b64, o);
-  }
-  if ((threadIdx.x & 31) == 0 && tested) {
-    atomicAdd(&a.status->pairs_tested, tested);
-    atomicAdd(&a.status->pairs_blended, b64);
-  }
-  const int64_t plane = (int64_t)tc.vi.width * tc.vi.height;
-  float* img = a.images + tc.vi.image_offset;
-  if constexpr (PACKED) {
-#pragma unroll
+    // work counters: pairs each pixel evaluated (up to its stop) and blended
+    unsigned long long tested = 0;
+  #pragma unroll
+    for (int p = 0; p < PX; ++p)
+      if (px < tc.vi.width && py0 + p < tc.vi.height) tested += stop[p] - range.x;
+    unsigned long long b64 = blended;
+  #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      tested += __shfl_xor_sync(0xffffffffu, tested, o);
+      b64 += __shfl_xor_sync(0xffffffffu, b64, o);
+    }
+    if ((threadIdx.x & 31) == 0 && tested) {
+      atomicAdd(&a.status->pairs_tested, tested);
+      atomicAdd(&a.status->pairs_blended, b64);
+    }
+    const int64_t plane = (int64_t)tc.vi.width * tc.vi.height;
+    float* img = a.images + tc.vi.image_offset;
+    if constexpr (PACKED) {
+  #pragma unroll
+      for (int p = 0; p < PX; ++p) {
+        const bool hi = p & 1;
+        T[p] = hi ? T2[p >> 1].y : T2[p >> 1].x;
+        C0[p] = hi ? D0[p >> 1].y : D0[p >> 1].x;
+        C1[p] = hi ? D1[p >> 1].y : D1[p >> 1].x;
+        C2[p] = hi ? D2[p >> 1].y : D2[p >> 1].x;
+      }
+    }
+  #pragma unroll
     for (int p = 0; p < PX; ++p) {
-      const bool hi = p & 1;
-      T[p] = hi ? T2[p >> 1].y : T2[p >> 1].x;
-      C0[p] = hi ? D0[p >> 1].y : D0[p >> 1].x;
-      C1[p] = hi ? D1[p >> 1].y : D1[p >> 1].x;
-      C2[p] = hi ? D2[p >> 1].y : D2[p >> 1].x;
-    }
-  }
-#pragma unroll
-  for (int p = 0; p < PX; ++p) {
-    const int py = py0 + p;
-    if (px < tc.vi.width && py < tc.vi.height) {
-      const int64_t pix = (int64_t)py * tc.vi.width + px;
-      img[pix] = __fmaf_rn(T[p], a.cfg.bg[0], C0[p]);
-      img[plane + pix] = __fmaf_rn(T[p], a.cfg.bg[1], C1[p]);
-      img[2 * plane + pix] = __fmaf_rn(T[p], a.cfg.bg[2], C2[p]);
-      a.t_final[tc.vi.pixel_offset + pix] = T[p];
-      a.n_contrib[tc.vi.pixel_offset + pix] = last[p];
+      const int py = py0 + p;
+      if (px < tc.vi.width && py < tc.vi.height) {
+        const int64_t pix = (int64_t)py * tc.vi.width + px;
+        img[pix] = __fmaf_rn(T[p], a.cfg.bg[0], C0[p]);
+        img[plane + pix] = __fmaf_rn(T[p], a.cfg.bg[1], C1[p]);
+        img[2 * plane + pix] = __fmaf_rn(T[p], a.cfg.bg[2], C2[p]);
+        a.t_final[tc.vi.pixel_offset + pix] = T[p];
+        a.n_contrib[tc.vi.pixel_offset + pix] = last[p];
+      }
     }
   }
 }
@@ -537,7 +551,7 @@ cudaError_t launch_d2_clear(Status* status, float4* d2, int64_t n4, int sms, cud
 
 // GATED: no blend masks (recompute_keys plans); every position below a
 // pixel's n_contrib is a candidate and the pair's own gate decides.
-template <int MODE, int PX, int BATCH, bool GATED>
+template <int MODE, int PX, int BATCH, bool GATED, bool PERSIST>
 __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
   pdl_entry();
   if (blockIdx.x == 0 && threadIdx.x == 0) a.status->d2_fresh = 0u;  // read by the next d2_clear_kernel only
@@ -549,114 +563,156 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
   // Gaussian per thread) are free of bank conflicts
   __shared__ float s_acc[16][BATCH + 1];
   __shared__ uint32_t s_max;
-  const int64_t tile = a.tile_order[blockIdx.x];
-  const TileCoord tc = tile_coord(a, tile);
-  const PixelMap pm = pixel_map<PX>(tc);
-  const int px = pm.px, py0 = pm.py0;
-  const float fx = (float)px + 0.5f;
-  const uint2 range = tile_range(a.ranges, tile);
-  const uint32_t* vals = a.status->sorted_buf ? a.vals1 : a.vals0;
-  const float amin = a.cfg.alpha_min, amax = a.cfg.alpha_max;
-  const int lane = threadIdx.x & 31;
-  const int64_t plane = (int64_t)tc.vi.width * tc.vi.height;
-  const float* gimg = a.d_images + tc.vi.image_offset;
+  __shared__ uint32_t s_next;
+  for (uint32_t it = PERSIST ? next_work(a.work, &s_next) : blockIdx.x; it < a.n_order;
+       it = PERSIST ? next_work(a.work, &s_next) : a.n_order) {
+    const int64_t tile = a.tile_order[it];
+    const TileCoord tc = tile_coord(a, tile);
+    const PixelMap pm = pixel_map<PX>(tc);
+    const int px = pm.px, py0 = pm.py0;
+    const float fx = (float)px + 0.5f;
+    const uint2 range = tile_range(a.ranges, tile);
+    const uint32_t* vals = a.status->sorted_buf ? a.vals1 : a.vals0;
+    const float amin = a.cfg.alpha_min, amax = a.cfg.alpha_max;
+    const int lane = threadIdx.x & 31;
+    const int64_t plane = (int64_t)tc.vi.width * tc.vi.height;
+    const float* gimg = a.d_images + tc.vi.image_offset;
 
-  BwdPixels<MODE, PX> pix;
-  uint32_t my_end[PX], bw[PX];
-  const int pi0 = pm.pi0;
-  const uint32_t* mbase = GATED ? nullptr : mask_tile_base(a.mask, range, tile);
-  uint32_t my_max = 0;
-#pragma unroll
-  for (int p = 0; p < PX; ++p) {
-    const int py = py0 + p;
-    pix.init(p, a.cfg.bg);
-    my_end[p] = range.x;
-    if (px < tc.vi.width && py < tc.vi.height) {
-      const int64_t pix_i = (int64_t)py * tc.vi.width + px;
-      pix.load(p, a.t_final[tc.vi.pixel_offset + pix_i], gimg[pix_i], gimg[plane + pix_i], gimg[2 * plane + pix_i]);
-      const uint32_t nc = a.n_contrib[tc.vi.pixel_offset + pix_i];
-      my_end[p] = min(range.y, range.x + nc);
-      my_max = max(my_max, nc);
-    }
-  }
-  if (threadIdx.x == 0) s_max = 0;
-  __syncthreads();
-  if (my_max) atomicMax(&s_max, my_max);
-  __syncthreads();
-  const uint32_t end = min(range.y, range.x + s_max);
-
-  for (uint32_t bend = end; bend > range.x;) {
-    const uint32_t bstart = bend - range.x > (uint32_t)BATCH ? bend - BATCH : range.x;
-    __syncthreads();  // previous batch fully consumed
-    stage_batch<MODE, BATCH>(a, vals, bstart, bend, NT, s_r0, s_r1, s_r2, s_r3, s_id);
-    for (int q = threadIdx.x; q < BATCH; q += NT) {
-#pragma unroll
-      for (int k = 0; k < 16; ++k) s_acc[k][q] = 0.0f;
-    }
-    __syncthreads();
-    // walk the batch from the top, one 32-position mask chunk at a time; the
-    // warp visits only the positions one of its lanes blended, in descending
-    // order (the replay recovers T and the colour behind from the top down)
-    for (int jhi = (int)(bend - bstart) - 1; jhi >= 0;) {
-      const uint32_t lp_hi = bstart + (uint32_t)jhi - range.x;
-      const uint32_t chunk = lp_hi >> 5;
-      const uint32_t chunk_first = range.x + (chunk << 5);  // position of bit 0
-      const int jlo = chunk_first > bstart ? (int)(chunk_first - bstart) : 0;
-#pragma unroll
-      for (int p = 0; p < PX; ++p) {
-        if (GATED)  // the positions below the pixel's end
-          bw[p] = chunk_first < my_end[p]
-                      ? (my_end[p] - chunk_first >= 32u ? 0xffffffffu : (1u << (my_end[p] - chunk_first)) - 1u)
-                      : 0u;
-        else
-          bw[p] = chunk_first < my_end[p] ? mbase[chunk * 256 + pi0 + p * kTile] : 0u;
+    BwdPixels<MODE, PX> pix;
+    uint32_t my_end[PX], bw[PX];
+    const int pi0 = pm.pi0;
+    const uint32_t* mbase = GATED ? nullptr : mask_tile_base(a.mask, range, tile);
+    uint32_t my_max = 0;
+  #pragma unroll
+    for (int p = 0; p < PX; ++p) {
+      const int py = py0 + p;
+      pix.init(p, a.cfg.bg);
+      my_end[p] = range.x;
+      if (px < tc.vi.width && py < tc.vi.height) {
+        const int64_t pix_i = (int64_t)py * tc.vi.width + px;
+        pix.load(p, a.t_final[tc.vi.pixel_offset + pix_i], gimg[pix_i], gimg[plane + pix_i], gimg[2 * plane + pix_i]);
+        const uint32_t nc = a.n_contrib[tc.vi.pixel_offset + pix_i];
+        my_end[p] = min(range.y, range.x + nc);
+        my_max = max(my_max, nc);
       }
-      uint32_t mine = 0u;
-#pragma unroll
-      for (int p = 0; p < PX; ++p) mine |= bw[p];
-      const uint32_t hi_bit = (uint32_t)jhi + bstart - chunk_first, lo_bit = (uint32_t)jlo + bstart - chunk_first;
-      uint32_t todo = __reduce_or_sync(0xffffffffu, mine) & ((2u << hi_bit) - 1u) & ~((1u << lo_bit) - 1u);
-      while (todo) {
-        const uint32_t bit = 31u - __clz(todo);
-        todo &= ~(1u << bit);
-        const int j = (int)(chunk_first + bit - bstart);
-        const float4 r0 = s_r0[j], r1 = s_r1[j], r3 = s_r3[j];
-        const float4 r2 = MODE == MODE_PLAIN ? r0 : s_r2[j];
-        float gr[16];
-        const bool contrib = pix.template visit<GATED>(bw, bit, r0, r1, r2, r3, fx, py0, amin, amax, gr);
-        // true whenever the position is reached (it is a bit of the warp's
-        // OR); the vote stays as the point where the warp meets before the
-        // shuffles, which measured faster than leaving it out
-        if (__any_sync(0xffffffffu, contrib)) {
-          const float sum = warp_transpose_sum16<MODE == MODE_PLAIN>(gr, lane);
-          if ((lane & 1) == 0 && sum != 0.0f) atomicAdd(&s_acc[lane >> 1][j], sum);
+    }
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    if (my_max) atomicMax(&s_max, my_max);
+    __syncthreads();
+    const uint32_t end = min(range.y, range.x + s_max);
+
+    for (uint32_t bend = end; bend > range.x;) {
+      const uint32_t bstart = bend - range.x > (uint32_t)BATCH ? bend - BATCH : range.x;
+      __syncthreads();  // previous batch fully consumed
+      stage_batch<MODE, BATCH>(a, vals, bstart, bend, NT, s_r0, s_r1, s_r2, s_r3, s_id);
+      for (int q = threadIdx.x; q < BATCH; q += NT) {
+  #pragma unroll
+        for (int k = 0; k < 16; ++k) s_acc[k][q] = 0.0f;
+      }
+      __syncthreads();
+      // walk the batch from the top, one 32-position mask chunk at a time; the
+      // warp visits only the positions one of its lanes blended, in descending
+      // order (the replay recovers T and the colour behind from the top down)
+      for (int jhi = (int)(bend - bstart) - 1; jhi >= 0;) {
+        const uint32_t lp_hi = bstart + (uint32_t)jhi - range.x;
+        const uint32_t chunk = lp_hi >> 5;
+        const uint32_t chunk_first = range.x + (chunk << 5);  // position of bit 0
+        const int jlo = chunk_first > bstart ? (int)(chunk_first - bstart) : 0;
+  #pragma unroll
+        for (int p = 0; p < PX; ++p) {
+          if (GATED)  // the positions below the pixel's end
+            bw[p] = chunk_first < my_end[p]
+                        ? (my_end[p] - chunk_first >= 32u ? 0xffffffffu : (1u << (my_end[p] - chunk_first)) - 1u)
+                        : 0u;
+          else
+            bw[p] = chunk_first < my_end[p] ? mbase[chunk * 256 + pi0 + p * kTile] : 0u;
         }
+        uint32_t mine = 0u;
+  #pragma unroll
+        for (int p = 0; p < PX; ++p) mine |= bw[p];
+        const uint32_t hi_bit = (uint32_t)jhi + bstart - chunk_first, lo_bit = (uint32_t)jlo + bstart - chunk_first;
+        uint32_t todo = __reduce_or_sync(0xffffffffu, mine) & ((2u << hi_bit) - 1u) & ~((1u << lo_bit) - 1u);
+        while (todo) {
+          const uint32_t bit = 31u - __clz(todo);
+          todo &= ~(1u << bit);
+          const int j = (int)(chunk_first + bit - bstart);
+          const float4 r0 = s_r0[j], r1 = s_r1[j], r3 = s_r3[j];
+          const float4 r2 = MODE == MODE_PLAIN ? r0 : s_r2[j];
+          float gr[16];
+          const bool contrib = pix.template visit<GATED>(bw, bit, r0, r1, r2, r3, fx, py0, amin, amax, gr);
+          // true whenever the position is reached (it is a bit of the warp's
+          // OR); the vote stays as the point where the warp meets before the
+          // shuffles, which measured faster than leaving it out
+          if (__any_sync(0xffffffffu, contrib)) {
+            const float sum = warp_transpose_sum16<MODE == MODE_PLAIN>(gr, lane);
+            if ((lane & 1) == 0 && sum != 0.0f) atomicAdd(&s_acc[lane >> 1][j], sum);
+          }
+        }
+        jhi = jlo - 1;
       }
-      jhi = jlo - 1;
+      __syncthreads();
+      // one set of vector atomics per Gaussian per batch
+      const int cnt = (int)(bend - bstart);
+      for (int q = threadIdx.x; q < cnt; q += NT) {
+        float c[16];
+  #pragma unroll
+        for (int k = 0; k < 16; ++k) c[k] = s_acc[k][q];
+        float* dst = a.d2 + kD2Stride * (int64_t)s_id[q];
+  #pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (c[4 * k] != 0.0f || c[4 * k + 1] != 0.0f || c[4 * k + 2] != 0.0f || c[4 * k + 3] != 0.0f)
+            red_add_v4(dst + 4 * k, c[4 * k], c[4 * k + 1], c[4 * k + 2], c[4 * k + 3]);
+      }
+      bend = bstart;
     }
-    __syncthreads();
-    // one set of vector atomics per Gaussian per batch
-    const int cnt = (int)(bend - bstart);
-    for (int q = threadIdx.x; q < cnt; q += NT) {
-      float c[16];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) c[k] = s_acc[k][q];
-      float* dst = a.d2 + kD2Stride * (int64_t)s_id[q];
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (c[4 * k] != 0.0f || c[4 * k + 1] != 0.0f || c[4 * k + 2] != 0.0f || c[4 * k + 3] != 0.0f)
-          red_add_v4(dst + 4 * k, c[4 * k], c[4 * k + 1], c[4 * k + 2], c[4 * k + 3]);
-    }
-    bend = bstart;
   }
 }
 
 // ---------------------------------------------------------------------------
+// Dynamic shared memory (unused by the kernel) that caps the blocks resident
+// on an SM at `blocks` (0: no cap): with it, blocks + 1 blocks no longer fit
+// in the SM's shared memory, and `blocks` still do.
+template <typename K>
+static size_t occupancy_pad(K kernel, int blocks) {
+  if (blocks <= 0) return 0;
+  int dev = 0, per_sm = 0, reserved = 0;
+  cudaFuncAttributes fa;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, kernel) != cudaSuccess)
+    return 0;
+  const long dyn = (long)per_sm / (blocks + 1) - reserved - (long)fa.sharedSizeBytes + 1;
+  if (dyn <= 0) return 0;  // shared memory already holds fewer than blocks + 1
+  if (dyn > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  return (size_t)dyn;
+}
+
+// Grid of a composite launch: one block per tile, or for a persistent launch
+// as many blocks as fit on the GPU at once (at most one per tile).
+template <typename K>
+static unsigned composite_grid(K kernel, int threads, size_t dyn_smem, const RenderArgs& a, unsigned tiles) {
+  if (!a.persistent) return tiles;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, dyn_smem) != cudaSuccess || occ < 1)
+    occ = 1;
+  return std::min<unsigned>(tiles, (unsigned)occ * (unsigned)std::max(1, a.sms));
+}
+
+template <int PX, bool REC, int BATCH, bool PERSIST>
+static void launch_fwd_kernel(const RenderArgs& a, int mode, unsigned grid, cudaStream_t st) {
+  auto k = mode == MODE_PLAIN ? render_fwd_kernel<MODE_PLAIN, PX, REC, BATCH, PERSIST>
+           : mode == MODE_TWO ? render_fwd_kernel<MODE_TWO, PX, REC, BATCH, PERSIST>
+                              : render_fwd_kernel<MODE_SPLIT, PX, REC, BATCH, PERSIST>;
+  const size_t dyn = occupancy_pad(k, a.blocks_fwd);
+  launch_pdl(k, dim3(composite_grid(k, 256 / PX, dyn, a, grid)), dim3(256 / PX), dyn, st, a);
+}
+
 template <int PX, bool REC, int BATCH>
 static void launch_fwd_px(const RenderArgs& a, int mode, unsigned grid, cudaStream_t st) {
-  if (mode == MODE_PLAIN) launch_pdl(render_fwd_kernel<MODE_PLAIN, PX, REC, BATCH>, dim3(grid), dim3(256 / PX), 0, st, a);
-  else if (mode == MODE_TWO) launch_pdl(render_fwd_kernel<MODE_TWO, PX, REC, BATCH>, dim3(grid), dim3(256 / PX), 0, st, a);
-  else launch_pdl(render_fwd_kernel<MODE_SPLIT, PX, REC, BATCH>, dim3(grid), dim3(256 / PX), 0, st, a);
+  if (a.persistent) launch_fwd_kernel<PX, REC, BATCH, true>(a, mode, grid, st);
+  else launch_fwd_kernel<PX, REC, BATCH, false>(a, mode, grid, st);
 }
 
 template <bool REC, int BATCH>
@@ -677,14 +733,19 @@ static void launch_fwd_rec(const RenderArgs& a, int mode, unsigned grid, cudaStr
   }
 }
 
+template <int PX, int BATCH, bool GATED, bool PERSIST>
+static void launch_bwd_kernel(const RenderArgs& a, int mode, unsigned grid, cudaStream_t st) {
+  auto k = mode == MODE_PLAIN ? render_bwd_kernel<MODE_PLAIN, PX, BATCH, GATED, PERSIST>
+           : mode == MODE_TWO ? render_bwd_kernel<MODE_TWO, PX, BATCH, GATED, PERSIST>
+                              : render_bwd_kernel<MODE_SPLIT, PX, BATCH, GATED, PERSIST>;
+  const size_t dyn = occupancy_pad(k, a.blocks_bwd);
+  launch_pdl(k, dim3(composite_grid(k, 256 / PX, dyn, a, grid)), dim3(256 / PX), dyn, st, a);
+}
+
 template <int PX, int BATCH, bool GATED>
 static void launch_bwd_px(const RenderArgs& a, int mode, unsigned grid, cudaStream_t st) {
-  if (mode == MODE_PLAIN)
-    launch_pdl(render_bwd_kernel<MODE_PLAIN, PX, BATCH, GATED>, dim3(grid), dim3(256 / PX), 0, st, a);
-  else if (mode == MODE_TWO)
-    launch_pdl(render_bwd_kernel<MODE_TWO, PX, BATCH, GATED>, dim3(grid), dim3(256 / PX), 0, st, a);
-  else
-    launch_pdl(render_bwd_kernel<MODE_SPLIT, PX, BATCH, GATED>, dim3(grid), dim3(256 / PX), 0, st, a);
+  if (a.persistent) launch_bwd_kernel<PX, BATCH, GATED, true>(a, mode, grid, st);
+  else launch_bwd_kernel<PX, BATCH, GATED, false>(a, mode, grid, st);
 }
 
 template <int BATCH, bool GATED>
@@ -699,6 +760,7 @@ static void launch_bwd_batch(const RenderArgs& a, int mode, unsigned grid, cudaS
 cudaError_t launch_render_fwd(const RenderArgs& a, int mode, int64_t total_tiles, cudaStream_t st) {
   if (total_tiles == 0) return cudaSuccess;
   const unsigned grid = (unsigned)total_tiles;
+  if (a.persistent && cudaMemsetAsync(a.work, 0, sizeof(uint32_t), st) != cudaSuccess) return cudaGetLastError();
   if (a.mask) launch_fwd_rec<true>(a, mode, grid, st);
   else launch_fwd_rec<false>(a, mode, grid, st);
   count_launches(1);
@@ -708,6 +770,7 @@ cudaError_t launch_render_fwd(const RenderArgs& a, int mode, int64_t total_tiles
 cudaError_t launch_render_bwd(const RenderArgs& a, int mode, int64_t total_tiles, cudaStream_t st) {
   if (total_tiles == 0) return cudaSuccess;
   const unsigned grid = (unsigned)total_tiles;
+  if (a.persistent && cudaMemsetAsync(a.work, 0, sizeof(uint32_t), st) != cudaSuccess) return cudaGetLastError();
   const bool gated = a.mask == nullptr;  // no blend masks: replay with the gate
   if (a.batch_bwd == 128) {
     if (gated) launch_bwd_batch<128, true>(a, mode, grid, st);

@@ -41,6 +41,9 @@ class Config:
     fwd_batch: int = 0               # records staged per batch by the forward composite (0: 256)
     bwd_batch: int = 0               # ... by the backward composite (0: 128)
     recompute_keys: bool = False     # plan without blend masks: the backward rebuilds the key lists
+    persistent: int = 0              # bit 0 forward, bit 1 backward composite: persistent launches
+    fwd_blocks_per_sm: int = 0       # cap on resident forward-composite blocks per SM (0: as many as fit)
+    bwd_blocks_per_sm: int = 0       # ... backward composite
 
     def to_c(self) -> N.sr_config:
         c = N.sr_config()
@@ -57,6 +60,9 @@ class Config:
         c.fwd_batch = int(self.fwd_batch)
         c.bwd_batch = int(self.bwd_batch)
         c.recompute_keys = 1 if self.recompute_keys else 0
+        c.persistent = int(self.persistent)
+        c.fwd_blocks_per_sm = int(self.fwd_blocks_per_sm)
+        c.bwd_blocks_per_sm = int(self.bwd_blocks_per_sm)
         return c
 
 
@@ -326,14 +332,35 @@ class Rasterizer:
             self.config.bwd_batch = int(bwd)
         self.cfg_c = self.config.to_c()
 
+    def set_persistent(self, fwd: bool | None = None, bwd: bool | None = None):
+        """Persistent composite launches (blocks take tiles from a counter)."""
+        bits = int(self.config.persistent)
+        if fwd is not None:
+            bits = (bits | 1) if fwd else (bits & ~1)
+        if bwd is not None:
+            bits = (bits | 2) if bwd else (bits & ~2)
+        self.config.persistent = bits
+        self.cfg_c = self.config.to_c()
+
+    def set_blocks_per_sm(self, fwd: int | None = None, bwd: int | None = None):
+        """Caps on the composites' resident blocks per SM (0: as many as fit)."""
+        if fwd is not None:
+            self.config.fwd_blocks_per_sm = int(fwd)
+        if bwd is not None:
+            self.config.bwd_blocks_per_sm = int(bwd)
+        self.cfg_c = self.config.to_c()
+
     def autotune(self, g: Gaussians, d_images: torch.Tensor | None = None, candidates=(1, 2, 4), reps: int = 3,
-                 stream=None, batches=((128, 256, 512), (128, 256))) -> dict:
+                 stream=None, batches=((128, 256, 512), (128, 256)), blocks=(0, 8, 6, 4)) -> dict:
         """Choose the launch shape of the forward and backward composites by
         timing candidates on this frame (CUDA events on the launching stream,
         best of ``reps``): first how many pixels each thread owns, then how
         many Gaussian records a block stages in shared memory per batch
-        (``batches`` = forward and backward candidates); keeps the fastest.
-        The results do not depend on the choice."""
+        (``batches`` = forward and backward candidates), then a cap on the
+        resident blocks per SM (``blocks``, 0 = none), then one block per tile
+        or a persistent grid; keeps the fastest (a non-default choice only
+        when it is more than 2% faster).  The results do not depend on the
+        choice."""
         s = stream if stream is not None else torch.cuda.current_stream()
         self.forward(g, stream)
 
@@ -362,7 +389,23 @@ class Rasterizer:
             fb[bt] = best_of(lambda: self.render_fwd(stream))
         bf = _prefer_default(fb, 256)
         self.set_batch(fwd=bf)
-        out = {"fwd_ms": fwd, "fwd_pixels_per_thread": pf, "fwd_batch_ms": fb, "fwd_batch": bf}
+        fo = {}
+        for nb in blocks:
+            self.set_blocks_per_sm(fwd=nb)
+            self.render_fwd(stream)  # warm
+            fo[nb] = best_of(lambda: self.render_fwd(stream))
+        ofwd = _prefer_default(fo, 0)
+        self.set_blocks_per_sm(fwd=ofwd)
+        fp = {}
+        for on in (False, True):
+            self.set_persistent(fwd=on)
+            self.render_fwd(stream)  # warm
+            fp[on] = best_of(lambda: self.render_fwd(stream))
+        pfwd = _prefer_default(fp, False)
+        self.set_persistent(fwd=pfwd)
+        out = {"fwd_ms": fwd, "fwd_pixels_per_thread": pf, "fwd_batch_ms": fb, "fwd_batch": bf,
+               "fwd_blocks_per_sm_ms": fo, "fwd_blocks_per_sm": ofwd, "fwd_persistent_ms": fp,
+               "fwd_persistent": pfwd}
         if d_images is not None:
             self.render_fwd(stream)
             bwd = {}
@@ -379,7 +422,22 @@ class Rasterizer:
                 bb[bt] = best_of(lambda: self.backward(g, d_images, stream))
             bbest = _prefer_default(bb, 128)
             self.set_batch(bwd=bbest)
-            out.update(bwd_ms=bwd, bwd_pixels_per_thread=pb, bwd_batch_ms=bb, bwd_batch=bbest)
+            bo = {}
+            for nb in blocks:
+                self.set_blocks_per_sm(bwd=nb)
+                self.backward(g, d_images, stream)  # warm
+                bo[nb] = best_of(lambda: self.backward(g, d_images, stream))
+            obwd = _prefer_default(bo, 0)
+            self.set_blocks_per_sm(bwd=obwd)
+            bp = {}
+            for on in (False, True):
+                self.set_persistent(bwd=on)
+                self.backward(g, d_images, stream)  # warm
+                bp[on] = best_of(lambda: self.backward(g, d_images, stream))
+            pbwd = _prefer_default(bp, False)
+            self.set_persistent(bwd=pbwd)
+            out.update(bwd_ms=bwd, bwd_pixels_per_thread=pb, bwd_batch_ms=bb, bwd_batch=bbest,
+                       bwd_blocks_per_sm_ms=bo, bwd_blocks_per_sm=obwd, bwd_persistent_ms=bp, bwd_persistent=pbwd)
         return out
 
     # -- read-only views of the workspace (tests and diagnostics) ---------

@@ -405,20 +405,21 @@ def test_backward_batched_views_sum():
     compare_grads(gr, oracle_grads(r, sc, cams, Config(), ups), GRAD_FIELDS, label="two views")
 
 
-@pytest.mark.parametrize("px,fb,bb", [(1, 128, 128), (2, 256, 256), (4, 512, 128), (2, 512, 128), (1, 0, 0)])
-def test_pixels_per_thread_launch_shapes(px, fb, bb):
+@pytest.mark.parametrize("px,fb,bb,pers", [(1, 128, 128, 0), (2, 256, 256, 0), (4, 512, 128, 3), (2, 512, 128, 0),
+                                           (1, 0, 0, 0), (2, 256, 128, 3), (1, 128, 256, 1), (4, 256, 256, 2)])
+def test_pixels_per_thread_launch_shapes(px, fb, bb, pers):
     """Every launch shape of the composites (pixels per thread, records per
-    staged batch) gives the oracle's image and gradients (the autotuner only
-    changes speed)."""
+    staged batch, one block per tile or a persistent grid) gives the oracle's
+    image and gradients (the autotuner only changes speed)."""
     sc = scenes.cluster(seed=31, n=4000, sh_degree=1, two_opacities=True)
     cams = [scenes.identity_camera(100, 70)]
     cfg = Config(fwd_pixels_per_thread=px, bwd_pixels_per_thread=px, fwd_batch=fb, bwd_batch=bb,
-                 bg=(0.1, 0.0, 0.2))
+                 bg=(0.1, 0.0, 0.2), persistent=pers)
     r, g = gpu_forward(sc, cams, cfg)
-    check_view(r, sc, cams, 0, cfg, label=f"shape {px} {fb} {bb}")
+    check_view(r, sc, cams, 0, cfg, label=f"shape {px} {fb} {bb} {pers}")
     up = scenes.upstream_grad(31, 70, 100)
     gr = r.backward(g, torch.as_tensor(up).cuda().reshape(-1).contiguous())
-    compare_grads(gr, oracle_grads(r, sc, cams, cfg, [up]), GRAD_FIELDS, label=f"shape {px} {fb} {bb}")
+    compare_grads(gr, oracle_grads(r, sc, cams, cfg, [up]), GRAD_FIELDS, label=f"shape {px} {fb} {bb} {pers}")
 
 
 def test_autotune_picks_a_shape_and_keeps_results():
@@ -431,6 +432,7 @@ def test_autotune_picks_a_shape_and_keeps_results():
     res = r.autotune(g, up)
     assert res["fwd_pixels_per_thread"] in (1, 2, 4) and res["bwd_pixels_per_thread"] in (1, 2, 4)
     assert res["fwd_batch"] in (128, 256, 512) and res["bwd_batch"] in (128, 256)
+    assert res["fwd_persistent"] in (False, True) and res["bwd_persistent"] in (False, True)
     r.forward(g)
     assert torch.equal(r.images, ref)
     gm = r.backward(g, up)["means"]
@@ -622,6 +624,41 @@ def test_composite_order_over_many_tiles():
     assert int(r.plan.total_tiles) > 65536
     for v in range(len(cams)):
         check_view(r, sc, cams, v, Config(), label="nine_1080p")
+
+
+def test_persistent_composites_over_many_views_equal_the_block_per_tile_grid():
+    """Persistent forward and backward composites over a 12-view plan of
+    mixed sizes (far more tiles than resident blocks) give the block-per-tile
+    grid's images bit for bit and its gradients within FP32 atomics'
+    reordering."""
+    sc = scenes.unbounded(seed=24, n=40_000)
+    cams = scenes.trajectory_cameras(12, resolutions=((320, 180), (640, 360), (200, 200)))
+    r, g = gpu_forward(sc, cams)
+    rp, _ = gpu_forward(sc, cams, Config(persistent=3))
+    assert torch.equal(rp.images, r.images)
+    assert torch.equal(rp.n_contrib, r.n_contrib)
+    up = torch.as_tensor(np.concatenate([scenes.upstream_grad(90 + v, c["height"], c["width"]).reshape(-1)
+                                         for v, c in enumerate(cams)])).cuda().contiguous()
+    ref = r.backward(g, up)
+    got = rp.backward(g, up)
+    for k in GRAD_FIELDS:
+        assert rel_err(got[k].cpu().numpy(), ref[k].cpu().numpy()) < 1e-5, k
+
+
+@pytest.mark.parametrize("fb,bb", [(3, 5), (1, 1), (8, 9)])
+def test_blocks_per_sm_caps_leave_results_unchanged(fb, bb):
+    """Capping the composites' resident blocks per SM (shared-memory
+    reservation) changes speed only: images bit for bit, gradients within
+    FP32 atomics' reordering."""
+    sc = scenes.cluster(seed=44, n=6000, sh_degree=1)
+    cams = [scenes.identity_camera(160, 120)]
+    r, g = gpu_forward(sc, cams)
+    rc, _ = gpu_forward(sc, cams, Config(fwd_blocks_per_sm=fb, bwd_blocks_per_sm=bb, persistent=3 if fb == 3 else 0))
+    assert torch.equal(rc.images, r.images)
+    up = torch.as_tensor(scenes.upstream_grad(44, 120, 160)).cuda().reshape(-1).contiguous()
+    ref, got = r.backward(g, up), rc.backward(g, up)
+    for k in GRAD_FIELDS:
+        assert rel_err(got[k].cpu().numpy(), ref[k].cpu().numpy()) < 1e-5, k
 
 
 def test_repeated_backward_calls_restart_from_zero():
