@@ -116,8 +116,8 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
   constexpr int NT = 256 / PX;
   __shared__ float4 s_r0[BATCH], s_r1[BATCH], s_r2[MODE == MODE_PLAIN ? 1 : BATCH], s_r3[BATCH];
   __shared__ uint32_t s_next;
-  for (uint32_t it = PERSIST ? next_work(a.work, &s_next) : blockIdx.x; it < a.n_order;
-       it = PERSIST ? next_work(a.work, &s_next) : a.n_order) {
+  // one tile of the composite order; a persistent block takes tile after tile
+  auto tile_body = [&](uint32_t it) {
     const int64_t tile = a.tile_order[it];
     const TileCoord tc = tile_coord(a, tile);
     const PixelMap pm = pixel_map<PX>(tc);
@@ -152,6 +152,15 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
       active += done[p] ? 0 : 1;
     }
     uint32_t blended = 0;
+    // a pixel's blends are bits of its chunk words (mw): the blend count and
+    // the last blended position (one past it, relative to the tile's first
+    // key) are taken from each word once, when its chunk ends or the pixel stops
+    auto fold = [&](int p, uint32_t chunk) {
+      if (mw[p]) {
+        blended += __popc(mw[p]);
+        last[p] = (chunk << 5) + 32u - __clz(mw[p]);
+      }
+    };
     for (uint32_t start = range.x; start < range.y; start += BATCH) {
       if (__syncthreads_count(active == 0) == NT) break;
       stage_batch<MODE, BATCH>(a, vals, start, range.y, NT, s_r0, s_r1, s_r2, s_r3, nullptr);
@@ -162,6 +171,7 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
           const int jend = min(cnt, jc + 32);
           const uint32_t chunk = (start - range.x + jc) >> 5;
           for (int j = jc; j < jend; ++j) {
+            const uint32_t bit = 1u << (j & 31);  // the position's bit in the chunk's blend words
             const float4 r0 = s_r0[j], r1 = s_r1[j], r3 = s_r3[j];
             const float4 r2 = MODE == MODE_PLAIN ? r0 : s_r2[j];
             if constexpr (PACKED) {
@@ -186,6 +196,7 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
                   if (s0) {
                     done[2 * q] = true;
                     stop[2 * q] = start + j + 1;
+                    fold(2 * q, chunk);
                     if (REC) mbase[chunk * 256 + pi0 + 2 * q * kTile] = mw[2 * q];
                     al.x = 0.0f;
                     Tn.x = T2[q].x;
@@ -194,6 +205,7 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
                   if (s1) {
                     done[2 * q + 1] = true;
                     stop[2 * q + 1] = start + j + 1;
+                    fold(2 * q + 1, chunk);
                     if (REC) mbase[chunk * 256 + pi0 + (2 * q + 1) * kTile] = mw[2 * q + 1];
                     al.y = 0.0f;
                     Tn.y = T2[q].y;
@@ -207,13 +219,8 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
                 D1[q] = fma2(f2(r3.y), w, D1[q]);
                 D2[q] = fma2(f2(r3.z), w, D2[q]);
                 T2[q] = Tn;
-                blended += (uint32_t)c0 + (uint32_t)c1;
-                if (REC) {
-                  mw[2 * q] |= (uint32_t)c0 << (j & 31);
-                  mw[2 * q + 1] |= (uint32_t)c1 << (j & 31);
-                }
-                if (c0) last[2 * q] = start + j + 1 - range.x;
-                if (c1) last[2 * q + 1] = start + j + 1 - range.x;
+                if (c0) mw[2 * q] |= bit;
+                if (c1) mw[2 * q + 1] |= bit;
               }
             } else {
   #pragma unroll
@@ -227,29 +234,27 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
                 if (Tn < tstop) {
                   done[p] = true;
                   stop[p] = start + j + 1;
+                  fold(p, chunk);
                   if (REC) mbase[chunk * 256 + pi0 + p * kTile] = mw[p];
                   if (--active == 0) goto batch_done;  // the only exit test, off the hot path
                   continue;
                 }
-                ++blended;
-                if (REC) mw[p] |= 1u << (j & 31);
+                mw[p] |= bit;
                 const float w = __fmul_rn(alpha, T[p]);
                 C0[p] = __fmaf_rn(r3.x, w, C0[p]);
                 C1[p] = __fmaf_rn(r3.y, w, C1[p]);
                 C2[p] = __fmaf_rn(r3.z, w, C2[p]);
                 T[p] = Tn;
-                last[p] = start + j + 1 - range.x;
               }
             }
           }
-          if (REC) {
   #pragma unroll
-            for (int p = 0; p < PX; ++p)
-              if (!done[p]) {
-                mbase[chunk * 256 + pi0 + p * kTile] = mw[p];
-                mw[p] = 0u;
-              }
-          }
+          for (int p = 0; p < PX; ++p)
+            if (!done[p]) {
+              fold(p, chunk);
+              if (REC) mbase[chunk * 256 + pi0 + p * kTile] = mw[p];
+              mw[p] = 0u;
+            }
         }
       }
     batch_done:;
@@ -293,6 +298,11 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
         a.n_contrib[tc.vi.pixel_offset + pix] = last[p];
       }
     }
+  };
+  if (PERSIST) {
+    for (uint32_t it = next_work(a.work, &s_next); it < a.n_order; it = next_work(a.work, &s_next)) tile_body(it);
+  } else {
+    tile_body(blockIdx.x);
   }
 }
 
@@ -362,12 +372,63 @@ struct BwdPixels {
     g2[p] = c2;
   }
   // Adds to gr the record's gradient components over the pixels whose mask
-  // word has `bit` set; returns whether there was one.  GATED: the bits mark
-  // candidate positions (below the pixel's n_contrib) rather than blends, and
-  // the pair counts only if it passes the forward's alpha gate, evaluated with
-  // the same arithmetic (Alg. 2's replay without stored decisions).
-  template <bool GATED>
+  // word has `bit` set; returns whether there was one.
   __device__ __forceinline__ bool visit(const uint32_t (&bw)[PX], uint32_t bit, const float4& r0, const float4& r1,
+                                        const float4& r2, const float4& r3, float fx, int py0, float amax,
+                                        float (&gr)[16]) {
+    const float a_ = -2.0f * kLn2 * r0.z, b_ = -kLn2 * r0.w, c_ = -2.0f * kLn2 * r1.x;
+    bool contrib = false;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) gr[k] = 0.0f;
+#pragma unroll
+    for (int p = 0; p < PX; ++p) {
+      if (!((bw[p] >> bit) & 1u)) continue;  // not blended in the forward pass
+      PairEval e;
+      // blended in the forward pass: the same arithmetic passes the alpha gate again
+      eval_pair<MODE, false>(r0, r1, r2, r3.w, fx, (float)(py0 + p) + 0.5f, e);
+      const float alpha = fminf(e.alpha, amax);
+      contrib = true;
+      const float one_m = 1.0f - alpha;
+      T[p] = __fdividef(T[p], one_m);  // T_k (alpha <= alpha_max < 1)
+      const float w = alpha * T[p];
+      gr[G_R] += w * g0[p];
+      gr[G_G] += w * g1[p];
+      gr[G_BL] += w * g2[p];
+      const float dLda = T[p] * (g0[p] * (r3.x - R0[p]) + g1[p] * (r3.y - R1[p]) + g2[p] * (r3.z - R2[p]));
+      R0[p] = alpha * r3.x + one_m * R0[p];
+      R1[p] = alpha * r3.y + one_m * R1[p];
+      R2[p] = alpha * r3.z + one_m * R2[p];
+      if (e.alpha <= amax) {  // the clamp has zero derivative
+        const float S = e.G * e.E;           // skew kernel G' (1 + erf z)
+        const float gS = dLda * e.o * S;
+        const float gz = dLda * e.o * e.G * kTwoOverSqrtPi * e.ez;  // dL/dz
+        float gdx = -gS * (a_ * e.dx + b_ * e.dy) + gz * r1.y;
+        float gdy = -gS * (b_ * e.dx + c_ * e.dy) + gz * r1.z;
+        gr[G_M] += dLda * S;
+        gr[G_A] += -0.5f * gS * e.dx * e.dx;
+        gr[G_B] += -gS * e.dx * e.dy;
+        gr[G_C] += -0.5f * gS * e.dy * e.dy;
+        gr[G_BX] += gz * e.dx * kInvSqrt2;
+        gr[G_BY] += gz * e.dy * kInvSqrt2;
+        if (MODE != MODE_PLAIN) {
+          gr[G_H] += dLda * e.eu * S;
+          const float gzu = dLda * r2.x * S * kTwoOverSqrtPi * e.ezu;
+          gdx += gzu * r2.y;
+          gdy += gzu * r2.z;
+          gr[G_UX] += gzu * e.dx * kInvSqrt2;
+          gr[G_UY] += gzu * e.dy * kInvSqrt2;
+        }
+        gr[G_MX] -= gdx;
+        gr[G_MY] -= gdy;
+      }
+    }
+    return contrib;
+  }
+  // The same for plans without blend masks: the bits mark candidate
+  // positions (below the pixel's n_contrib) rather than blends, and a pair
+  // counts only if it passes the forward's alpha gate, evaluated with the same
+  // arithmetic (Alg. 2's replay without stored decisions).
+  __device__ __forceinline__ bool visit_gated(const uint32_t (&bw)[PX], uint32_t bit, const float4& r0, const float4& r1,
                                         const float4& r2, const float4& r3, float fx, int py0, float amin, float amax,
                                         float (&gr)[16]) {
     const float a_ = -2.0f * kLn2 * r0.z, b_ = -kLn2 * r0.w, c_ = -2.0f * kLn2 * r1.x;
@@ -378,13 +439,8 @@ struct BwdPixels {
     for (int p = 0; p < PX; ++p) {
       if (!((bw[p] >> bit) & 1u)) continue;  // not blended (not reached) in the forward pass
       PairEval e;
-      if (GATED) {
-        if (!eval_pair<MODE, true>(r0, r1, r2, r3.w, fx, (float)(py0 + p) + 0.5f, e)) continue;
-        if (fminf(e.alpha, amax) < amin) continue;
-      } else {
-        // blended in the forward pass: the same arithmetic passes the alpha gate again
-        eval_pair<MODE, false>(r0, r1, r2, r3.w, fx, (float)(py0 + p) + 0.5f, e);
-      }
+      if (!eval_pair<MODE, true>(r0, r1, r2, r3.w, fx, (float)(py0 + p) + 0.5f, e)) continue;
+      if (fminf(e.alpha, amax) < amin) continue;
       const float alpha = fminf(e.alpha, amax);
       contrib = true;
       const float one_m = 1.0f - alpha;
@@ -456,8 +512,75 @@ struct BwdPixels<MODE, PX, true> {
     put(g1[p >> 1], p, c1);
     put(g2[p >> 1], p, c2);
   }
-  template <bool GATED>
   __device__ __forceinline__ bool visit(const uint32_t (&bw)[PX], uint32_t bit, const float4& r0, const float4& r1,
+                                        const float4& r2, const float4& r3, float fx, int py0, float amax,
+                                        float (&gr)[16]) {
+    const float a_ = -2.0f * kLn2 * r0.z, b_ = -kLn2 * r0.w, c_ = -2.0f * kLn2 * r1.x;
+    float2 acc[16];
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const bool m0 = (bw[2 * q] >> bit) & 1u, m1 = (bw[2 * q + 1] >> bit) & 1u;
+      float2 t[16];
+      any |= m0 || m1;
+      PairEval2 e;
+      eval_pair2<MODE>(r0, r1, r2, fx, (float)(py0 + 2 * q) + 0.5f, e);
+      const float2 alpha = make_float2(m0 ? fminf(e.alpha.x, amax) : 0.0f, m1 ? fminf(e.alpha.y, amax) : 0.0f);
+      const float2 one_m = add2(f2(1.0f), neg2(alpha));
+      // T_k = T_{k+1} / (1 - alpha) as a product with the reciprocal (rcp.approx)
+      const float2 Tn = mul2(T[q], make_float2(rcp_approx(one_m.x), rcp_approx(one_m.y)));
+      T[q] = make_float2(m0 ? Tn.x : T[q].x, m1 ? Tn.y : T[q].y);
+      const float2 w = mul2(alpha, T[q]);
+      t[G_R] = mul2(w, g0[q]);
+      t[G_G] = mul2(w, g1[q]);
+      t[G_BL] = mul2(w, g2[q]);
+      const float2 c0 = f2(r3.x), c1 = f2(r3.y), c2 = f2(r3.z);
+      float2 s = mul2(g0[q], add2(c0, neg2(R0[q])));
+      s = fma2(g1[q], add2(c1, neg2(R1[q])), s);
+      s = fma2(g2[q], add2(c2, neg2(R2[q])), s);
+      const float2 dl = mul2(T[q], s);
+      R0[q] = fma2(alpha, c0, mul2(one_m, R0[q]));
+      R1[q] = fma2(alpha, c1, mul2(one_m, R1[q]));
+      R2[q] = fma2(alpha, c2, mul2(one_m, R2[q]));
+      // dL/dalpha through the unclamped alpha (the clamp has zero derivative)
+      const float2 dLda = make_float2(m0 && e.alpha.x <= amax ? dl.x : 0.0f, m1 && e.alpha.y <= amax ? dl.y : 0.0f);
+      const float2 S = mul2(e.G, e.E);  // skew kernel G' (1 + erf z)
+      const float2 dlo = mul2(dLda, e.o);
+      const float2 gS = mul2(dlo, S);
+      const float2 gz = mul2(mul2(mul2(dlo, e.G), f2(kTwoOverSqrtPi)), e.ez);  // dL/dz
+      float2 gdx = fma2(neg2(gS), fma2(f2(b_), e.dy, f2(a_ * e.dx)), mul2(gz, f2(r1.y)));
+      float2 gdy = fma2(neg2(gS), fma2(f2(c_), e.dy, f2(b_ * e.dx)), mul2(gz, f2(r1.z)));
+      const float2 dx = f2(e.dx);
+      t[G_M] = mul2(dLda, S);
+      t[G_A] = mul2(gS, f2(-0.5f * e.dx * e.dx));
+      t[G_B] = mul2(mul2(neg2(gS), dx), e.dy);
+      t[G_C] = mul2(mul2(gS, f2(-0.5f)), mul2(e.dy, e.dy));
+      t[G_BX] = mul2(gz, f2(e.dx * kInvSqrt2));
+      t[G_BY] = mul2(mul2(gz, e.dy), f2(kInvSqrt2));
+      if (MODE != MODE_PLAIN) {
+        t[G_H] = mul2(mul2(dLda, e.eu), S);
+        const float2 gzu = mul2(mul2(mul2(mul2(dLda, f2(r2.x)), S), f2(kTwoOverSqrtPi)), e.ezu);
+        gdx = fma2(gzu, f2(r2.y), gdx);
+        gdy = fma2(gzu, f2(r2.z), gdy);
+        t[G_UX] = mul2(gzu, f2(e.dx * kInvSqrt2));
+        t[G_UY] = mul2(mul2(gzu, e.dy), f2(kInvSqrt2));
+      } else {
+        t[G_H] = t[G_UX] = t[G_UY] = f2(0.0f);
+      }
+      t[G_MX] = neg2(gdx);
+      t[G_MY] = neg2(gdy);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        if (k == G_ABS || k == G_PAD) continue;
+        acc[k] = q == 0 ? t[k] : add2(acc[k], t[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) gr[k] = (k == G_ABS || k == G_PAD) ? 0.0f : acc[k].x + acc[k].y;
+    return any;
+  }
+  // visit for plans without blend masks: the bits mark candidates, the gate decides
+  __device__ __forceinline__ bool visit_gated(const uint32_t (&bw)[PX], uint32_t bit, const float4& r0, const float4& r1,
                                         const float4& r2, const float4& r3, float fx, int py0, float amin, float amax,
                                         float (&gr)[16]) {
     const float a_ = -2.0f * kLn2 * r0.z, b_ = -kLn2 * r0.w, c_ = -2.0f * kLn2 * r1.x;
@@ -470,10 +593,9 @@ struct BwdPixels<MODE, PX, true> {
       PairEval2 e;
       const float2 p2 = pair2_exponent(r0, r1, fx, (float)(py0 + 2 * q) + 0.5f, e);
       pair2_alpha<MODE>(r1, r2, p2, e);
-      if (GATED) {  // the forward's gate, with its arithmetic
-        m0 = m0 && p2.x >= r3.w && fminf(e.alpha.x, amax) >= amin;
-        m1 = m1 && p2.y >= r3.w && fminf(e.alpha.y, amax) >= amin;
-      }
+      // the forward's gate, with its arithmetic
+      m0 = m0 && p2.x >= r3.w && fminf(e.alpha.x, amax) >= amin;
+      m1 = m1 && p2.y >= r3.w && fminf(e.alpha.y, amax) >= amin;
       any |= m0 || m1;
       const float2 alpha = make_float2(m0 ? fminf(e.alpha.x, amax) : 0.0f, m1 ? fminf(e.alpha.y, amax) : 0.0f);
       const float2 one_m = add2(f2(1.0f), neg2(alpha));
@@ -564,8 +686,8 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
   __shared__ float s_acc[16][BATCH + 1];
   __shared__ uint32_t s_max;
   __shared__ uint32_t s_next;
-  for (uint32_t it = PERSIST ? next_work(a.work, &s_next) : blockIdx.x; it < a.n_order;
-       it = PERSIST ? next_work(a.work, &s_next) : a.n_order) {
+  // one tile of the composite order; a persistent block takes tile after tile
+  auto tile_body = [&](uint32_t it) {
     const int64_t tile = a.tile_order[it];
     const TileCoord tc = tile_coord(a, tile);
     const PixelMap pm = pixel_map<PX>(tc);
@@ -640,7 +762,8 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
           const float4 r0 = s_r0[j], r1 = s_r1[j], r3 = s_r3[j];
           const float4 r2 = MODE == MODE_PLAIN ? r0 : s_r2[j];
           float gr[16];
-          const bool contrib = pix.template visit<GATED>(bw, bit, r0, r1, r2, r3, fx, py0, amin, amax, gr);
+          const bool contrib = GATED ? pix.visit_gated(bw, bit, r0, r1, r2, r3, fx, py0, amin, amax, gr)
+                                   : pix.visit(bw, bit, r0, r1, r2, r3, fx, py0, amax, gr);
           // true whenever the position is reached (it is a bit of the warp's
           // OR); the vote stays as the point where the warp meets before the
           // shuffles, which measured faster than leaving it out
@@ -666,6 +789,11 @@ __global__ void __launch_bounds__(256 / PX) render_bwd_kernel(RenderArgs a) {
       }
       bend = bstart;
     }
+  };
+  if (PERSIST) {
+    for (uint32_t it = next_work(a.work, &s_next); it < a.n_order; it = next_work(a.work, &s_next)) tile_body(it);
+  } else {
+    tile_body(blockIdx.x);
   }
 }
 
@@ -685,7 +813,9 @@ static size_t occupancy_pad(K kernel, int blocks) {
     return 0;
   const long dyn = (long)per_sm / (blocks + 1) - reserved - (long)fa.sharedSizeBytes + 1;
   if (dyn <= 0) return 0;  // shared memory already holds fewer than blocks + 1
-  if (dyn > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  // above 48 KB of shared memory per block (static + dynamic) a kernel must opt in
+  if (dyn + (long)fa.sharedSizeBytes > 48 * 1024)
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   return (size_t)dyn;
 }
 
