@@ -152,15 +152,6 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
       active += done[p] ? 0 : 1;
     }
     uint32_t blended = 0;
-    // a pixel's blends are bits of its chunk words (mw): the blend count and
-    // the last blended position (one past it, relative to the tile's first
-    // key) are taken from each word once, when its chunk ends or the pixel stops
-    auto fold = [&](int p, uint32_t chunk) {
-      if (mw[p]) {
-        blended += __popc(mw[p]);
-        last[p] = (chunk << 5) + 32u - __clz(mw[p]);
-      }
-    };
     for (uint32_t start = range.x; start < range.y; start += BATCH) {
       if (__syncthreads_count(active == 0) == NT) break;
       stage_batch<MODE, BATCH>(a, vals, start, range.y, NT, s_r0, s_r1, s_r2, s_r3, nullptr);
@@ -171,7 +162,6 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
           const int jend = min(cnt, jc + 32);
           const uint32_t chunk = (start - range.x + jc) >> 5;
           for (int j = jc; j < jend; ++j) {
-            const uint32_t bit = 1u << (j & 31);  // the position's bit in the chunk's blend words
             const float4 r0 = s_r0[j], r1 = s_r1[j], r3 = s_r3[j];
             const float4 r2 = MODE == MODE_PLAIN ? r0 : s_r2[j];
             if constexpr (PACKED) {
@@ -196,7 +186,6 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
                   if (s0) {
                     done[2 * q] = true;
                     stop[2 * q] = start + j + 1;
-                    fold(2 * q, chunk);
                     if (REC) mbase[chunk * 256 + pi0 + 2 * q * kTile] = mw[2 * q];
                     al.x = 0.0f;
                     Tn.x = T2[q].x;
@@ -205,7 +194,6 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
                   if (s1) {
                     done[2 * q + 1] = true;
                     stop[2 * q + 1] = start + j + 1;
-                    fold(2 * q + 1, chunk);
                     if (REC) mbase[chunk * 256 + pi0 + (2 * q + 1) * kTile] = mw[2 * q + 1];
                     al.y = 0.0f;
                     Tn.y = T2[q].y;
@@ -219,8 +207,13 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
                 D1[q] = fma2(f2(r3.y), w, D1[q]);
                 D2[q] = fma2(f2(r3.z), w, D2[q]);
                 T2[q] = Tn;
-                if (c0) mw[2 * q] |= bit;
-                if (c1) mw[2 * q + 1] |= bit;
+                blended += (uint32_t)c0 + (uint32_t)c1;
+                if (REC) {
+                  mw[2 * q] |= (uint32_t)c0 << (j & 31);
+                  mw[2 * q + 1] |= (uint32_t)c1 << (j & 31);
+                }
+                if (c0) last[2 * q] = start + j + 1 - range.x;
+                if (c1) last[2 * q + 1] = start + j + 1 - range.x;
               }
             } else {
   #pragma unroll
@@ -234,27 +227,29 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
                 if (Tn < tstop) {
                   done[p] = true;
                   stop[p] = start + j + 1;
-                  fold(p, chunk);
                   if (REC) mbase[chunk * 256 + pi0 + p * kTile] = mw[p];
                   if (--active == 0) goto batch_done;  // the only exit test, off the hot path
                   continue;
                 }
-                mw[p] |= bit;
+                ++blended;
+                if (REC) mw[p] |= 1u << (j & 31);
                 const float w = __fmul_rn(alpha, T[p]);
                 C0[p] = __fmaf_rn(r3.x, w, C0[p]);
                 C1[p] = __fmaf_rn(r3.y, w, C1[p]);
                 C2[p] = __fmaf_rn(r3.z, w, C2[p]);
                 T[p] = Tn;
+                last[p] = start + j + 1 - range.x;
               }
             }
           }
+          if (REC) {
   #pragma unroll
-          for (int p = 0; p < PX; ++p)
-            if (!done[p]) {
-              fold(p, chunk);
-              if (REC) mbase[chunk * 256 + pi0 + p * kTile] = mw[p];
-              mw[p] = 0u;
-            }
+            for (int p = 0; p < PX; ++p)
+              if (!done[p]) {
+                mbase[chunk * 256 + pi0 + p * kTile] = mw[p];
+                mw[p] = 0u;
+              }
+          }
         }
       }
     batch_done:;
