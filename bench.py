@@ -61,8 +61,6 @@ def parse():
     ap.add_argument("--bwd-blocks", type=int, default=0, help="backward blocks per SM cap when the shape is fixed")
     ap.add_argument("--persistent", type=int, default=0, choices=[0, 1, 2, 3],
                     help="persistent composites (bit 0 forward, bit 1 backward) when the shape is fixed")
-    ap.add_argument("--bin-mode", type=int, default=0, choices=[0, 1],
-                    help="binning (0: depth sort + tile sort, 1: tile-major) when the shape is fixed")
     return ap.parse_args()
 
 
@@ -237,8 +235,6 @@ def run_ours(args):
         r.set_batch(args.fwd_batch, args.bwd_batch)
         r.set_blocks_per_sm(args.fwd_blocks, args.bwd_blocks)
         r.set_persistent(bool(args.persistent & 1), bool(args.persistent & 2))
-        r.config.bin_mode = args.bin_mode
-        r.cfg_c = r.config.to_c()
         tune = {"fwd_pixels_per_thread": args.fwd_px, "bwd_pixels_per_thread": args.bwd_px, "fwd_ms": {},
                 "bwd_ms": {}, "fixed": True}
     else:
@@ -286,7 +282,7 @@ def run_ours(args):
     clocks = clk.summary()
 
     cfgd = config_dict(args.n)
-    cfgd["launch"] = {"bin_mode": r.config.bin_mode, "fwd_pixels_per_thread": tune["fwd_pixels_per_thread"],
+    cfgd["launch"] = {"fwd_pixels_per_thread": tune["fwd_pixels_per_thread"],
                       "bwd_pixels_per_thread": tune["bwd_pixels_per_thread"],
                       "fwd_batch": r.config.fwd_batch or 256, "bwd_batch": r.config.bwd_batch or 128,
                       "fwd_blocks_per_sm": r.config.fwd_blocks_per_sm, "bwd_blocks_per_sm": r.config.bwd_blocks_per_sm,
@@ -305,8 +301,7 @@ def run_ours(args):
     out["pairs_blended"] = blended
     out["blends_per_s"] = round(blended / (stage_mean[2] / 1e3), 1)
     out["clocks"] = clocks
-    out["autotune_ms"] = {"bin_mode_forward": {str(k): round(v, 4) for k, v in tune.get("bin_mode_ms", {}).items()},
-                          "fwd": {str(k): round(v, 4) for k, v in tune["fwd_ms"].items()},
+    out["autotune_ms"] = {"fwd": {str(k): round(v, 4) for k, v in tune["fwd_ms"].items()},
                           "bwd": {str(k): round(v, 4) for k, v in tune["bwd_ms"].items()},
                           "fwd_batch": {str(k): round(v, 4) for k, v in tune.get("fwd_batch_ms", {}).items()},
                           "bwd_batch": {str(k): round(v, 4) for k, v in tune.get("bwd_batch_ms", {}).items()},

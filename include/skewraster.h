@@ -125,12 +125,6 @@ typedef struct sr_config {
   int32_t fwd_blocks_per_sm;  /* 0..32 (0 = as many as fit): cap on the blocks of sr_render_fwd resident on
                                  an SM (each block then reserves a matching share of shared memory) */
   int32_t bwd_blocks_per_sm;  /* the same for the backward composite */
-  int32_t bin_mode;           /* how sr_bin_sort builds the sorted key list (the same list either way):
-                                 0: a radix sort of the records by depth, keys emitted in depth order,
-                                 a stable radix sort by tile id; 1: keys counted per tile by
-                                 sr_preprocess, placed into each tile's run by atomic cursors, each
-                                 run sorted by (depth bits, record index).  sr_preprocess and
-                                 sr_bin_sort of one frame must get the same bin_mode. */
 } sr_config;
 
 /* Gradients of the loss w.r.t. the attributes, FP32, device, caller-owned,

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libskewraster.so")
-SOURCES = ["api.cu", "preprocess.cu", "binsort.cu", "render.cu", "train.cu", "densify.cu", "peaks.cu", "tilebin.cu"]
+SOURCES = ["api.cu", "preprocess.cu", "binsort.cu", "render.cu", "train.cu", "densify.cu", "peaks.cu"]
 HEADERS = [os.path.join(CSRC, "common.cuh"), os.path.join(CSRC, "kernels.cuh"), os.path.join(INCLUDE, "skewraster.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -65,7 +65,6 @@ sr_status check_config(const sr_config* c) {
   if (c->recompute_keys != 0 && c->recompute_keys != 1) return SR_ERR_INVALID;
   if (c->recompute_keys && c->forward_only) return SR_ERR_INVALID;
   if (c->persistent < 0 || c->persistent > 3) return SR_ERR_INVALID;
-  if (c->bin_mode != 0 && c->bin_mode != 1) return SR_ERR_INVALID;
   if (c->fwd_blocks_per_sm < 0 || c->fwd_blocks_per_sm > 32 || c->bwd_blocks_per_sm < 0 || c->bwd_blocks_per_sm > 32)
     return SR_ERR_INVALID;
   return SR_OK;
@@ -199,7 +198,7 @@ sr_status sr_plan_init(sr_plan* p, const sr_config* cfg, const sr_gaussians* g, 
   p->sort_bits = 32 + tile_bits;
   p->sort_passes = (tile_bits + 7) / 8;  // the depth bits are sorted once per record, not per key
 
-  const int64_t scan_blocks = (std::max<int64_t>(m, tb) + kScanBlock - 1) / kScanBlock;  // records or tiles
+  const int64_t scan_blocks = (m + kScanBlock - 1) / kScanBlock;
   const int64_t parts = (key_capacity + kSortPart - 1) / kSortPart;
   const int64_t dparts = (m + kSortPart - 1) / kSortPart;
   static_assert(WS_NUM_SLOTS <= (int)(sizeof(p->off) / sizeof(p->off[0])), "plan offset table too small");
@@ -227,9 +226,6 @@ sr_status sr_plan_init(sr_plan* p, const sr_config* cfg, const sr_gaussians* g, 
                        : sizeof(uint32_t) * 256 * (size_t)(key_capacity / 32 + tb + 1);
   sizes[WS_TILE_ORDER] = sizeof(uint32_t) * ((size_t)tb + 130);
   sizes[WS_SHJAC] = p->forward_only ? 0 : sizeof(float4) * 3 * (size_t)m;
-  sizes[WS_TILE_CNT] = sizeof(uint32_t) * (size_t)tb;
-  sizes[WS_TILE_CUR] = sizeof(uint32_t) * (size_t)tb;
-  sizes[WS_TILE_BIG] = sizeof(uint32_t) * (size_t)(tb + 1);
   size_t off = 0;
   for (int k = 0; k < WS_NUM_SLOTS; ++k) {
     p->off[k] = off;
@@ -263,14 +259,6 @@ sr_status sr_preprocess(const sr_plan* p, const sr_gaussians* g, const sr_camera
   a.mode = p->render_mode;
   a.ws = ws_ptrs(*p, ws);
   a.d2 = p->forward_only ? nullptr : reinterpret_cast<float4*>(a.ws.d2);
-  a.tile_cnt = nullptr;
-  if (cfg->bin_mode == 1) {  // tile-major binning: the projection counts the keys of each tile
-    a.tile_cnt = a.ws.tile_cnt;
-    if (p->total_tiles > 0 &&
-        cudaMemsetAsync(a.tile_cnt, 0, sizeof(uint32_t) * (size_t)p->total_tiles, static_cast<cudaStream_t>(stream)) !=
-            cudaSuccess)
-      return SR_ERR_CUDA;
-  }
   return from_cuda(launch_preprocess_fwd(a, static_cast<cudaStream_t>(stream), device_sms()));
 }
 
@@ -312,15 +300,11 @@ sr_status sr_bin_sort(const sr_plan* p, const sr_config* cfg, void* ws, int64_t*
   if ((s = check_config(cfg)) != SR_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const BinArgs b = bin_args(p, cfg, ws);
-  const bool tile_major = cfg->bin_mode == 1;
-  cudaError_t e = tile_major ? launch_tilemajor_phase1(b, st, device_sms()) : launch_bin_phase1(b, st, device_sms());
+  cudaError_t e = launch_bin_phase1(b, st, device_sms());
   if (e != cudaSuccess) return SR_ERR_CUDA;
   int run[kMaxPasses];
   for (int k = 0; k < kMaxPasses; ++k) run[k] = 1;
-  auto phase2 = [&]() {
-    return tile_major ? launch_tilemajor_phase2(b, st, device_sms()) : launch_bin_phase2(b, run, -1, st);
-  };
-  if (!keys_needed) return from_cuda(phase2());
+  if (!keys_needed) return from_cuda(launch_bin_phase2(b, run, -1, st));
   // Synchronous form.  With a mapped pinned status buffer a one-block kernel
   // writes the status into host memory while the tile passes (grids sized
   // for the capacity; blocks past the device-side key count leave at once)
@@ -338,7 +322,7 @@ sr_status sr_bin_sort(const sr_plan* p, const sr_config* cfg, void* ws, int64_t*
   if (h_dev && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) ev = nullptr;
   if (h_dev && ev) {
     const bool ok = launch_status_export(b.ws.status, h_dev, st) == cudaSuccess &&
-                    cudaEventRecord(ev, st) == cudaSuccess && phase2() == cudaSuccess &&
+                    cudaEventRecord(ev, st) == cudaSuccess && launch_bin_phase2(b, run, -1, st) == cudaSuccess &&
                     cudaEventSynchronize(ev) == cudaSuccess;
     cudaEventDestroy(ev);
     if (!ok) return SR_ERR_CUDA;
@@ -352,7 +336,6 @@ sr_status sr_bin_sort(const sr_plan* p, const sr_config* cfg, void* ws, int64_t*
   if (e != cudaSuccess) return SR_ERR_CUDA;
   *keys_needed = (int64_t)hs.keys_needed;
   if (hs.keys_needed > (unsigned long long)p->key_capacity) return SR_ERR_CAPACITY;
-  if (tile_major) return from_cuda(phase2());
   for (int k = 0; k < p->sort_passes; ++k) run[k] = hs.pass_trivial[kMaxPasses + k] ? 0 : 1;
   return from_cuda(launch_bin_phase2(b, run, (long long)hs.keys_needed, st));
 }

@@ -891,13 +891,12 @@ __global__ void __launch_bounds__(256) tile_order_scatter_kernel(const uint2* __
   }
 }
 
-cudaError_t launch_tile_order(const BinArgs& a, cudaStream_t st);
-
 // Phase 2: tile passes (run[p] != 0) and ranges.  keys_known: exact key
 // count (sizes the grids), or -1 to size them for the capacity.
 cudaError_t launch_bin_phase2(const BinArgs& a, const int* run, long long keys_known, cudaStream_t st) {
   const unsigned long long kn = keys_known >= 0 ? (unsigned long long)keys_known : a.cap;
   const unsigned long long parts = (kn + kSortPart - 1) / kSortPart;
+  cudaError_t e;
   int r = -1;  // buffer of kb/vb holding the sorted result, -1: no pass ran
   if (parts > 0 && a.passes > 0) {  // look-back words zeroed by phase 1
     uint32_t* const kb[2] = {a.ws.keys[1], a.ws.keys[0]};
@@ -915,12 +914,7 @@ cudaError_t launch_bin_phase2(const BinArgs& a, const int* run, long long keys_k
     ranges_kernel<<<grid, 256, 0, st>>>(a.ws.keys[0], a.ws.status, a.cap, a.ws.ranges, 0);
     count_launches(1);
   }
-  return launch_tile_order(a, st);
-}
-
-// Composite order of the tiles (longest key lists first).
-cudaError_t launch_tile_order(const BinArgs& a, cudaStream_t st) {
-  cudaError_t e;
+  // composite order of the tiles
   if (a.total_tiles <= kOrderOneBlock) {
     launch_pdl(tile_order_block_kernel, dim3(1), dim3(1024), 0, st, (const uint2*)a.ws.ranges, a.total_tiles,
                a.ws.tile_order);
@@ -936,52 +930,6 @@ cudaError_t launch_tile_order(const BinArgs& a, cudaStream_t st) {
     count_launches(2);
   }
   return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Tile-major binning (see tilebin.cu): the scan of the per-tile key counts
-// gives each tile its run ([start, end), stored as (~start, end)) and a
-// placement cursor at the run's start; the key count and a capacity
-// overflow go to the status word as in the other path.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) tile_runs_kernel(const uint32_t* __restrict__ cnt, int64_t tiles,
-                                                        const uint32_t* __restrict__ start,
-                                                        uint2* __restrict__ ranges) {
-  pdl_entry();
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t c = cnt[t], s = start[t];
-    ranges[t] = c ? make_uint2(~s, s + c) : make_uint2(0u, 0u);
-  }
-}
-
-cudaError_t launch_tilemajor_phase1(const BinArgs& a, cudaStream_t st, int sms) {
-  cudaError_t e;
-  if ((e = cudaMemsetAsync(a.ws.status, 0, offsetof(Status, d2_fresh), st)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(a.ws.tile_big, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
-  const int64_t t = a.total_tiles;
-  const int nb = (int)((t + kScanBlock - 1) / kScanBlock);
-  if (t > 0) {
-    launch_pdl(scan_reduce_kernel, dim3(nb), dim3(kScanThreads), 0, st, (const uint32_t*)a.ws.tile_cnt, t,
-               a.ws.scan_part);
-    count_launches(1);
-  }
-  launch_pdl(scan_parts_kernel, dim3(1), dim3(1024), 0, st, a.ws.scan_part, nb, a.ws.status, a.cap);
-  count_launches(1);
-  if (t > 0) {
-    launch_pdl(scan_down_kernel, dim3(nb), dim3(kScanThreads), 0, st, (const uint32_t*)a.ws.tile_cnt, t,
-               (const unsigned long long*)a.ws.scan_part, a.ws.tile_cur);
-    launch_pdl(tile_runs_kernel, dim3(clamp_grid((t + 255) / 256, sms, 4)), dim3(256), 0, st,
-               (const uint32_t*)a.ws.tile_cnt, t, (const uint32_t*)a.ws.tile_cur, a.ws.ranges);
-    count_launches(2);
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_tilemajor_phase2(const BinArgs& a, cudaStream_t st, int sms) {
-  cudaError_t e;
-  if ((e = launch_tile_scatter(a, st, sms)) != cudaSuccess) return e;
-  if ((e = launch_tile_segsort(a, st, sms)) != cudaSuccess) return e;
-  return launch_tile_order(a, st);
 }
 
 // ---------------------------------------------------------------------------

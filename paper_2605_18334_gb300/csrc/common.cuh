@@ -40,9 +40,6 @@ enum WsSlot {
   WS_TILE_ORDER,   // uint32_t[tiles] composite order (longest key lists first) + uint32_t[2][64] counters
                    // of the ordering + the tile counters of persistent forward and backward composites
   WS_SHJAC,        // float4[M][3] d colour / d view direction (3x3) and the colour clamp bits (backward only)
-  WS_TILE_CNT,     // uint32_t[tiles] keys per tile, counted by the projection (tile-major binning)
-  WS_TILE_CUR,     // uint32_t[tiles] per-tile placement cursor (tile-major binning)
-  WS_TILE_BIG,     // uint32_t[1 + tiles] count and ids of the runs too long for one block's sort
   WS_NUM_SLOTS
 };
 static_assert(WS_LOOKBACK_D == WS_HIST + 1 && WS_LOOKBACK == WS_HIST + 2 && WS_RANGES == WS_HIST + 3,
@@ -489,9 +486,6 @@ struct Ws {
   uint32_t* mask;   // null when the plan is forward-only
   uint32_t* tile_order;
   float4* shjac;    // null when the plan is forward-only
-  uint32_t* tile_cnt;
-  uint32_t* tile_cur;
-  uint32_t* tile_big;
 };
 
 inline Ws ws_ptrs(const sr_plan& p, void* base) {
@@ -523,9 +517,6 @@ inline Ws ws_ptrs(const sr_plan& p, void* base) {
   w.mask = (p.forward_only || p.recompute_keys) ? nullptr : reinterpret_cast<uint32_t*>(at(WS_MASK));
   w.tile_order = reinterpret_cast<uint32_t*>(at(WS_TILE_ORDER));
   w.shjac = p.forward_only ? nullptr : reinterpret_cast<float4*>(at(WS_SHJAC));
-  w.tile_cnt = reinterpret_cast<uint32_t*>(at(WS_TILE_CNT));
-  w.tile_cur = reinterpret_cast<uint32_t*>(at(WS_TILE_CUR));
-  w.tile_big = reinterpret_cast<uint32_t*>(at(WS_TILE_BIG));
   return w;
 }
 

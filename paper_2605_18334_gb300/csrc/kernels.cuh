@@ -13,7 +13,6 @@ struct PreArgs {        // preprocess forward
   int mode;             // RenderMode
   Ws ws;
   float4* d2;           // 2D-gradient records to zero for touched records (null: forward-only plan)
-  uint32_t* tile_cnt;   // per-tile key counts to add into (tile-major binning), or null
 };
 
 struct BwdArgs {        // preprocess backward
@@ -131,12 +130,6 @@ cudaError_t launch_preprocess_bwd(const BwdArgs& a, cudaStream_t st, int sms);
 cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms);
 cudaError_t launch_status_export(const Status* src, Status* dst_mapped, cudaStream_t st);
 cudaError_t launch_bin_phase2(const BinArgs& a, const int* run, long long keys_known, cudaStream_t st);
-// tile-major binning: phase 1 = per-frame state, scan of the tile counts
-// (ranges, cursors, key count); phase 2 = placement, per-tile sorts, order
-cudaError_t launch_tilemajor_phase1(const BinArgs& a, cudaStream_t st, int sms);
-cudaError_t launch_tilemajor_phase2(const BinArgs& a, cudaStream_t st, int sms);
-cudaError_t launch_tile_scatter(const BinArgs& a, cudaStream_t st, int sms);
-cudaError_t launch_tile_segsort(const BinArgs& a, cudaStream_t st, int sms);
 cudaError_t launch_selftest_bounded_wait(const Ws& ws, unsigned long long cap, int spin_limit, cudaStream_t st);
 cudaError_t launch_render_fwd(const RenderArgs& a, int mode, int64_t total_tiles, cudaStream_t st);
 cudaError_t launch_render_bwd(const RenderArgs& a, int mode, int64_t total_tiles, cudaStream_t st);

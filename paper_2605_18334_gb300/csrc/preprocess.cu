@@ -358,15 +358,6 @@ __global__ void __launch_bounds__(kPreThreads, 5) preprocess_fwd_kernel(PreArgs 
     write_view_table(a.cams, a.n_views, a.ws.views);
     a.ws.status->d2_fresh = a.d2 ? 1u : 0u;
   }
-  // first global tile id of each view (tile-major binning counts keys per tile)
-  __shared__ uint32_t s_tbase[SR_MAX_VIEWS];
-  if (a.tile_cnt && threadIdx.x == 0) {
-    uint32_t tb = 0;
-    for (int v = 0; v < a.n_views; ++v) {
-      s_tbase[v] = tb;
-      tb += (uint32_t)(((a.cams[v].width + kTile - 1) / kTile) * ((a.cams[v].height + kTile - 1) / kTile));
-    }
-  }
   __syncthreads();
   const int64_t n = a.g.n;
   const bool has_split = a.g.split_dir != nullptr;
@@ -445,10 +436,6 @@ __global__ void __launch_bounds__(kPreThreads, 5) preprocess_fwd_kernel(PreArgs 
                 int lo, hi;
                 if (row_tile_span(f0, f1, f2, f3, P.mx, P.my, (int)ty, c.width, c.height, lo, hi)) {
                   ntouch += (uint32_t)(hi - lo + 1);
-                  if (a.tile_cnt) {
-                    uint32_t* row = a.tile_cnt + s_tbase[v] + ty * (uint32_t)((c.width + kTile - 1) / kTile);
-                    for (int tx = lo; tx <= hi; ++tx) atomicAdd(row + tx, 1u);
-                  }
                   const uint32_t first = (uint32_t)(lo - (int)tx0);
                   packed = packed && first <= 15u;
                   if (packed) firsts |= first << (4 * rr);

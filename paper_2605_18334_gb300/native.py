@@ -69,7 +69,7 @@ class sr_config(C.Structure):
                 ("sort_spin_limit", C.c_int32), ("fwd_pixels_per_thread", C.c_int32),
                 ("bwd_pixels_per_thread", C.c_int32), ("forward_only", C.c_int32), ("bwd_batch", C.c_int32),
                 ("recompute_keys", C.c_int32), ("persistent", C.c_int32), ("fwd_blocks_per_sm", C.c_int32),
-                ("bwd_blocks_per_sm", C.c_int32), ("bin_mode", C.c_int32)]
+                ("bwd_blocks_per_sm", C.c_int32)]
 
 
 class sr_grads(C.Structure):

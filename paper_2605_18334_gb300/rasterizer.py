@@ -44,7 +44,6 @@ class Config:
     persistent: int = 0              # bit 0 forward, bit 1 backward composite: persistent launches
     fwd_blocks_per_sm: int = 0       # cap on resident forward-composite blocks per SM (0: as many as fit)
     bwd_blocks_per_sm: int = 0       # ... backward composite
-    bin_mode: int = 0                # 0: depth sort + tile sort; 1: per-tile counting, placement and sort
 
     def to_c(self) -> N.sr_config:
         c = N.sr_config()
@@ -64,7 +63,6 @@ class Config:
         c.persistent = int(self.persistent)
         c.fwd_blocks_per_sm = int(self.fwd_blocks_per_sm)
         c.bwd_blocks_per_sm = int(self.bwd_blocks_per_sm)
-        c.bin_mode = int(self.bin_mode)
         return c
 
 
@@ -354,10 +352,9 @@ class Rasterizer:
 
     def autotune(self, g: Gaussians, d_images: torch.Tensor | None = None, candidates=(1, 2, 4), reps: int = 3,
                  stream=None, batches=((128, 256, 512), (128, 256)), blocks=(0, 8, 6, 4)) -> dict:
-        """Choose the binning method and the launch shape of the forward and
-        backward composites by timing candidates on this frame (CUDA events on
-        the launching stream, best of ``reps``): first the binning (over a
-        whole forward), then how many pixels each thread owns, then how
+        """Choose the launch shape of the forward and backward composites by
+        timing candidates on this frame (CUDA events on the launching stream,
+        best of ``reps``): first how many pixels each thread owns, then how
         many Gaussian records a block stages in shared memory per batch
         (``batches`` = forward and backward candidates), then a cap on the
         resident blocks per SM (``blocks``, 0 = none), then one block per tile
@@ -378,17 +375,6 @@ class Rasterizer:
                 ts.append(a.elapsed_time(b))
             return min(ts)
 
-        # binning: depth sort + tile sort, or per-tile counting and sorting
-        # (the same key list); timed over the projection, binning and composite
-        bm = {}
-        for mode in (0, 1):
-            self.config.bin_mode = mode
-            self.cfg_c = self.config.to_c()
-            self.forward(g, stream)  # warm (and grows the plan if needed)
-            bm[mode] = best_of(lambda: self.forward(g, stream))
-        self.config.bin_mode = _prefer_default(bm, 0)
-        self.cfg_c = self.config.to_c()
-        self.forward(g, stream)
         fwd = {}
         for px in candidates:
             self.set_pixels_per_thread(fwd=px)
@@ -417,8 +403,7 @@ class Rasterizer:
             fp[on] = best_of(lambda: self.render_fwd(stream))
         pfwd = _prefer_default(fp, False)
         self.set_persistent(fwd=pfwd)
-        out = {"bin_mode_ms": bm, "bin_mode": self.config.bin_mode,
-               "fwd_ms": fwd, "fwd_pixels_per_thread": pf, "fwd_batch_ms": fb, "fwd_batch": bf,
+        out = {"fwd_ms": fwd, "fwd_pixels_per_thread": pf, "fwd_batch_ms": fb, "fwd_batch": bf,
                "fwd_blocks_per_sm_ms": fo, "fwd_blocks_per_sm": ofwd, "fwd_persistent_ms": fp,
                "fwd_persistent": pfwd}
         if d_images is not None:
@@ -466,16 +451,11 @@ class Rasterizer:
 
     def sorted_keys(self):
         """The last frame's sorted list as (tile << 32 | FP32 depth bits) keys
-        (int64 tensor holding the uint64 bits) and record indices (int32); the
-        tile of each position is read off the tile ranges."""
+        (int64 tensor holding the uint64 bits) and record indices (int32)."""
         kn = int(self.keys)
         st = self._slot(self._S_STATUS, 16).clone().cpu().numpy()
         buf = int(st[4:8].view(np.uint32)[0])
-        rg = self.ranges()
-        lens = (rg[:, 1] - rg[:, 0]).clamp(min=0)
-        tiles = torch.repeat_interleave(torch.arange(rg.shape[0], device=rg.device), lens)
-        if tiles.numel() != kn:
-            raise RuntimeError("tile ranges do not cover the key list")
+        tiles = self._slot(self._S_KEYS0 + buf, 4 * kn).view(torch.int32).to(torch.int64) & 0xFFFFFFFF
         vals = self._slot(self._S_VALS0 + buf, 4 * kn).view(torch.int32)
         depth = self.depth_bits().to(torch.int64) & 0xFFFFFFFF
         keys = (tiles << 32) | depth[vals.to(torch.int64)] if kn else tiles

@@ -661,70 +661,6 @@ def test_blocks_per_sm_caps_leave_results_unchanged(fb, bb):
         assert rel_err(got[k].cpu().numpy(), ref[k].cpu().numpy()) < 1e-5, k
 
 
-def _bin_mode_pair(sc, cams, key_capacity=None):
-    r0, g = gpu_forward(sc, cams, Config(bin_mode=0), key_capacity=key_capacity)
-    r1, _ = gpu_forward(sc, cams, Config(bin_mode=1), key_capacity=key_capacity)
-    k0, v0 = r0.sorted_keys()
-    k1, v1 = r1.sorted_keys()
-    assert r0.keys == r1.keys
-    assert torch.equal(k0, k1) and torch.equal(v0, v1)
-    assert torch.equal(r0.ranges(), r1.ranges())
-    assert torch.equal(r0.images, r1.images) and torch.equal(r0.n_contrib, r1.n_contrib)
-    return r0, r1, g
-
-
-@pytest.mark.parametrize("case", ["cube", "cluster_720p", "trajectory", "nine_1080p", "near_degenerate"])
-def test_tile_major_binning_gives_the_same_key_list(case):
-    """Tile-major binning (per-tile counting, atomic placement, per-tile sort)
-    against the depth-sort-then-tile-sort path: the same key list bit for bit,
-    hence the same images."""
-    if case == "cube":
-        sc, cams = scenes.cube_1k(), [scenes.identity_camera(64, 64)]
-    elif case == "cluster_720p":
-        sc, cams = scenes.cluster(), [scenes.identity_camera(1280, 720)]
-    elif case == "trajectory":
-        sc = scenes.unbounded(seed=7, n=20_000)
-        cams = scenes.trajectory_cameras(5, resolutions=((64, 36), (128, 72), (96, 96)))
-    elif case == "nine_1080p":
-        sc = scenes.unbounded(seed=21, n=3000)
-        cams = scenes.trajectory_cameras(9, resolutions=((1920, 1080),))
-    else:
-        rng = np.random.default_rng(41)
-        sc = scenes.cluster(seed=41, n=3000, sh_degree=1)
-        thin = rng.random(sc.n) < 0.4
-        sc.log_scales[thin, 0] -= 9.0
-        sc.skew[rng.random(sc.n) < 0.05] *= 20.0
-        cams = [scenes.identity_camera(96, 80)]
-    r0, r1, g = _bin_mode_pair(sc, cams)
-    check_view(r1, sc, cams, 0, Config(bin_mode=1), label=f"tile_major {case}")
-
-
-def test_tile_major_binning_with_runs_longer_than_one_block_sorts():
-    """Tiles whose key runs exceed one block's shared-memory sort (4096 keys)
-    are sorted in chunks and merged: 30,000 splats over a 48x48 view give
-    runs of up to ~30,000 keys."""
-    sc = scenes.cube_1k(seed=5, n=30_000)
-    sc.log_scales[:] = np.float32(-1.6)  # large splats: most touch all nine tiles
-    cams = [scenes.identity_camera(48, 48)]
-    r0, r1, g = _bin_mode_pair(sc, cams, key_capacity=400_000)
-    rg = r1.ranges().cpu().numpy()
-    assert (rg[:, 1] - rg[:, 0]).max() > 3 * 4096
-    check_view(r1, sc, cams, 0, Config(bin_mode=1), label="tile_major big runs")
-
-
-def test_tile_major_binning_reports_capacity_overflow():
-    sc = scenes.cube_1k()
-    cams = [scenes.identity_camera(64, 64)]
-    g = Gaussians.from_scene(sc)
-    r = Rasterizer(g, cams, Config(bin_mode=1), key_capacity=100)
-    r.preprocess(g)
-    with pytest.raises(N.SkewRasterError) as e:
-        r.bin_sort()
-    assert e.value.status == N.SR_ERR_CAPACITY and e.value.keys_needed > 100
-    r.forward(g)
-    check_view(r, sc, cams, 0, Config(bin_mode=1), label="tile_major after regrow")
-
-
 def test_repeated_backward_calls_restart_from_zero():
     """The 2D-gradient records are zeroed by the projection for its frame and
     again by the backward itself when a backward composite has used them
