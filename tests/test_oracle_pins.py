@@ -457,6 +457,44 @@ def test_sh_basis_matches_scipy_real_harmonics():
             k += 1
 
 
+def test_sh_colour_uses_the_direction_from_the_camera_to_the_centre():
+    """The view direction of the SH colour points from the camera centre to
+    the Gaussian (the convention the library states).  Cameras on the +x,
+    -x, +z and -z sides of a Gaussian carrying only degree-1 coefficients see
+    the colours that scipy's harmonics give for that direction, and the
+    opposite colours for the reversed one (odd degree: a flipped direction
+    flips the sign of the degree-1 term, which these expected values fail)."""
+    mu = np.array([0.3, -0.2, 4.0])
+    sh = np.zeros((1, 4, 3))
+    sh[0, 1:, 0] = [0.11, -0.07, 0.05]   # red: all three degree-1 coefficients
+    sh[0, 3, 1] = 0.2                    # green: the x-aligned one only
+    sc = scenes.Scene(means=mu[None], log_scales=np.full((1, 3), -3.0), quats=np.array([[1.0, 0, 0, 0]]),
+                      opacity_logits=np.array([2.0]), skew=np.zeros((1, 3)), sh=sh, sh_degree=1)
+    cfg = oracle.config()
+
+    def basis_deg1(d):
+        # real SH of degree 1 from scipy (Condon-Shortley phase included), order m = -1, 0, 1
+        theta, phi = math.acos(d[2]), math.atan2(d[1], d[0])
+        c = special.sph_harm_y(1, 1, theta, phi)
+        return np.array([math.sqrt(2) * c.imag, special.sph_harm_y(1, 0, theta, phi).real, math.sqrt(2) * c.real])
+
+    seen = 0
+    for eye in ([3.0, -0.2, 4.0], [-2.4, -0.2, 4.0], [0.3, -0.2, 1.0], [0.3, -0.2, 7.5]):
+        cam = oracle.camera_from_gl(scenes.camera(scenes.look_at_c2w_cv(eye, mu), 32, 32))
+        pre = oracle.preprocess(sc, cam, cfg)
+        assert pre["visible"][0]
+        campos = np.array(oracle.camera_fields(cam)["campos"])
+        d = (mu - campos) / np.linalg.norm(mu - campos)
+        Y = basis_deg1(d)
+        want = 0.5 + np.array([Y @ sh[0, 1:, 0], Y @ sh[0, 1:, 1], 0.0]) + sh[0, 0] * 0.28209479177387814
+        flipped = 0.5 + np.array([-(Y @ sh[0, 1:, 0]), -(Y @ sh[0, 1:, 1]), 0.0])
+        got = pre["rec"][0, 11:14]
+        np.testing.assert_allclose(got, np.maximum(want, 0.0), atol=1e-6)
+        assert np.abs(got - np.maximum(flipped, 0.0)).max() > 1e-3
+        seen += 1
+    assert seen == 4
+
+
 # ---------------------------------------------------------------------------
 # depth key and binning (tile-based, depth sorted: Preliminaries)
 # ---------------------------------------------------------------------------
