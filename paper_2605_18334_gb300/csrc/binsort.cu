@@ -527,13 +527,9 @@ struct SortSmem {
   uint32_t part;
 };
 
-// Look-back words in flight per digit: WIN.  With many partitions over
-// several waves (the tile passes) the early ones publish their prefixes long
-// before the late ones look back, and 4 words suffice; when every partition
-// of a pass is resident at once (the depth passes over the records), each
-// inclusive prefix travels WIN partitions per round trip, so a wider window
-// shortens the chain.
-template <class KEY, int WIN>
+constexpr int kLookbackWindow = 4;  // look-back words in flight per digit
+
+template <class KEY>
 __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(PassArgs<KEY> a) {
   pdl_entry();
   constexpr int NW = kSortThreads / 32;
@@ -622,7 +618,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(PassArgs<KEY>
   }
 
   // decoupled look-back over the predecessors' words of digit d, a window of
-  // WIN loads in flight: aggregates are summed, an inclusive
+  // kLookbackWindow loads in flight: aggregates are summed, an inclusive
   // prefix ends the walk, a word not yet published is polled again (at most
   // spin_limit times)
   unsigned long long excl = 0;
@@ -633,13 +629,13 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(PassArgs<KEY>
     int spins = 0;
     bool walking = true;
     while (walking) {
-      unsigned long long w[WIN];
+      unsigned long long w[kLookbackWindow];
 #pragma unroll
-      for (int k = 0; k < WIN; ++k)
+      for (int k = 0; k < kLookbackWindow; ++k)
         w[k] = q - k >= 0 ? ld_relaxed_u64(col + (unsigned long long)(q - k) * stride) : 0ull;
       bool stalled = false;
 #pragma unroll
-      for (int k = 0; k < WIN; ++k) {
+      for (int k = 0; k < kLookbackWindow; ++k) {
         if (!walking || stalled || q < 0) continue;
         const unsigned long long v = w[k];
         if (v & kFlagInc) {
@@ -728,16 +724,13 @@ static int run_passes(const KEY* keys_in, const uint32_t* vals_in, KEY* const* k
                       int passes, int key_bits, const int* run, Status* status, int spin_limit,
                       cudaStream_t st, uint2* ranges = nullptr, unsigned long long n_tiles = 0,
                       const int* buf_ids = nullptr, const uint32_t* last_gather = nullptr,
-                      cudaError_t* first_error = nullptr, bool wide_lookback = false) {
+                      cudaError_t* first_error = nullptr) {
   int cur = -1;  // -1: still the input
   int last = -1;
   for (int p = 0; p < passes; ++p)
     if (!run || run[p]) last = p;
   // above the 48 KB default; a host-side attribute, no stream work
-  cudaFuncSetAttribute(onesweep_kernel<KEY, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sizeof(SortSmem<KEY>));
-  cudaFuncSetAttribute(onesweep_kernel<KEY, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sizeof(SortSmem<KEY>));
+  cudaFuncSetAttribute(onesweep_kernel<KEY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SortSmem<KEY>));
   for (int p = 0; p < passes; ++p) {
     if (run && !run[p]) continue;
     const int out = cur == 0 ? 1 : 0;
@@ -762,11 +755,7 @@ static int run_passes(const KEY* keys_in, const uint32_t* vals_in, KEY* const* k
     pa.sorted_buf = (p == last && buf_ids) ? buf_ids[out] : 0;
     pa.out_gather = p == last ? last_gather : nullptr;
     const cudaError_t e =
-        wide_lookback
-            ? launch_pdl(onesweep_kernel<KEY, 16>, dim3((unsigned)parts), dim3(kSortThreads), sizeof(SortSmem<KEY>), st,
-                         pa)
-            : launch_pdl(onesweep_kernel<KEY, 4>, dim3((unsigned)parts), dim3(kSortThreads), sizeof(SortSmem<KEY>), st,
-                         pa);
+        launch_pdl(onesweep_kernel<KEY>, dim3((unsigned)parts), dim3(kSortThreads), sizeof(SortSmem<KEY>), st, pa);
     if (first_error && *first_error == cudaSuccess) *first_error = e;
     count_launches(1);
     cur = out;
@@ -806,8 +795,7 @@ cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms) {
     // tile counts in depth order (what the scan and the key emission read)
     const int r = run_passes<uint32_t>(a.ws.dkey[0], nullptr, kb, vb, a.ws.hist, a.ws.lookback_d,
                                        a.ws.status->part_counter, nullptr, um, dparts, kDepthPasses, 32, nullptr,
-                                       a.ws.status, a.spin_limit, st, nullptr, 0, nullptr, a.ws.ntouch, nullptr,
-                                       dparts <= 4ull * (unsigned long long)sms);
+                                       a.ws.status, a.spin_limit, st, nullptr, 0, nullptr, a.ws.ntouch);
     perm = vb[r];
     cnt_sorted = kb[r];
   }

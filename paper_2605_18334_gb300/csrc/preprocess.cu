@@ -344,14 +344,15 @@ __device__ __forceinline__ void stage_sh(const void* sh, int64_t base, int cnt, 
   }
 }
 
-// Geometry pass: everything but the colour (which needs the SH coefficients
-// and is taken by preprocess_colour_kernel for the records that touch a tile);
-// the record's colour slots are left to that pass.
-__global__ void __launch_bounds__(kPreThreads) preprocess_geom_kernel(PreArgs a) {
+template <int DEG, int DT_SH>
+__global__ void __launch_bounds__(kPreThreads, 5) preprocess_fwd_kernel(PreArgs a) {
   pdl_entry();
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  constexpr int K3 = 3 * K, ROW = K3 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   sr_camera* s_cams = reinterpret_cast<sr_camera*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* s_sh = reinterpret_cast<float*>(smem_raw + cams_bytes(a.n_views)) + warp * 32 * ROW;
   for (int v = threadIdx.x; v < a.n_views; v += blockDim.x) s_cams[v] = a.cams[v];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     write_view_table(a.cams, a.n_views, a.ws.views);
@@ -365,7 +366,10 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_geom_kernel(PreArgs a)
   for (int64_t base = ((int64_t)blockIdx.x * kPreWarps + warp) * 32; base < n;
        base += (int64_t)gridDim.x * kPreWarps * 32) {
     const int cnt = (int)(n - base < 32 ? n - base : 32);
+    stage_sh<K3, DT_SH>(a.g.sh, base, cnt, s_sh, lane);
+    __syncwarp();
     const int64_t i = base + lane;
+    const float* sh = s_sh + lane * ROW;
     if (lane < cnt) {
     Attr A;
     load_attr(a.g, i, has_split, A);
@@ -459,6 +463,28 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_geom_kernel(PreArgs a)
           }
         }
         if (ntouch) {
+          float Y[16];
+          sh_eval<DEG>(P.dir[0], P.dir[1], P.dir[2], Y);
+          float rgb[3];
+          uint32_t clamped = 0u;
+#pragma unroll
+          for (int ch = 0; ch < 3; ++ch) {
+            float acc = 0.5f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc += Y[k] * sh[3 * k + ch];
+            rgb[ch] = fmaxf(acc, 0.0f);
+            clamped |= (acc < 0.0f ? 1u : 0u) << ch;
+          }
+          if (a.ws.shjac) {
+            // per channel: d colour / d direction (the backward's view-direction
+            // term, so it need not read the SH coefficients) and the clamp flag
+            float4* jp = a.ws.shjac + 3 * m;
+            float J[3][3];
+            sh_grad3<DEG>(P.dir[0], P.dir[1], P.dir[2], sh, J);
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch)
+              jp[ch] = make_float4(J[ch][0], J[ch][1], J[ch][2], (clamped >> ch) & 1u ? 1.0f : 0.0f);
+          }
           const float m_ = P.comp * (P.o1 + P.o2) * 0.5f;
           const float h_ = P.comp * (P.o1 - P.o2) * 0.5f;
           // alpha >= tau implies P2 >= log2(tau / (kappa o_max)); a small margin
@@ -468,7 +494,7 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_geom_kernel(PreArgs a)
           r[0] = make_float4(P.mx, P.my, -0.5f * kLog2e * P.a, -kLog2e * P.b);
           r[1] = make_float4(-0.5f * kLog2e * P.c, P.beta[0] * kInvSqrt2, P.beta[1] * kInvSqrt2, m_);
           r[2] = make_float4(h_, (P.beta[0] + P.ud[0]) * kInvSqrt2, (P.beta[1] + P.ud[1]) * kInvSqrt2, 0.0f);
-          r[3] = make_float4(0.0f, 0.0f, 0.0f, thr);  // colour: preprocess_colour_kernel
+          r[3] = make_float4(rgb[0], rgb[1], rgb[2], thr);
           if (a.d2) {  // the record's 2D gradients start at zero for the backward
             float4* z = a.d2 + 4 * m;
             z[0] = z[1] = z[2] = z[3] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -479,79 +505,6 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_geom_kernel(PreArgs a)
       a.ws.rect[m] = rect;
       a.ws.dkey[0][m] = ntouch ? __float_as_uint(tz) : 0xffffffffu;
     }
-    }
-  }
-}
-
-// Colour pass (Preliminaries: SH colour at the view direction from the camera
-// to the centre): for every (view, Gaussian) record that touches a tile, the
-// colour max(0, SH(dir) + 0.5) into the record, and for the backward the
-// colour's Jacobian with respect to the direction and the clamp flags.  A
-// warp takes 32 consecutive Gaussians of one view; only the SH rows of those
-// touching a tile are read, staged through shared memory with coalesced loads.
-template <int DEG, int DT_SH>
-__global__ void __launch_bounds__(kPreThreads) preprocess_colour_kernel(PreArgs a) {
-  pdl_entry();
-  constexpr int K = (DEG + 1) * (DEG + 1);
-  constexpr int K3 = 3 * K, ROW = K3 + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* s_sh = reinterpret_cast<float*>(smem_raw) + warp * 32 * ROW;
-  const int64_t n = a.g.n;
-  const int64_t groups = (n + 31) / 32;
-  const float* means = static_cast<const float*>(a.g.means);
-  for (int64_t gidx = (int64_t)blockIdx.x * kPreWarps + warp; gidx < groups * a.n_views;
-       gidx += (int64_t)gridDim.x * kPreWarps) {
-    const int v = (int)(gidx / groups);
-    const int64_t base = (gidx - (int64_t)v * groups) * 32;
-    const int cnt = (int)(n - base < 32 ? n - base : 32);
-    const int64_t i = base + lane;
-    const int64_t m = (int64_t)v * n + i;
-    const bool need = lane < cnt && a.ws.ntouch[m] != 0u;
-    const uint32_t needs = __ballot_sync(0xffffffffu, need);
-    if (!needs) continue;
-    // the SH rows of the lanes that need them: row r of the group is read
-    // only if lane r needs it (coalesced over the rows that are read)
-    const int64_t off = base * K3;
-#pragma unroll
-    for (int k = 0; k < K3; ++k) {
-      const int w = lane + 32 * k, row = w / K3, col = w - row * K3;
-      if ((needs >> row) & 1u) s_sh[row * ROW + col] = ld<DT_SH>(a.g.sh, off + w);
-    }
-    __syncwarp();
-    if (need) {
-      const sr_camera& c = a.cams[v];
-      const float d0 = __ldg(means + 3 * i) - c.campos[0], d1 = __ldg(means + 3 * i + 1) - c.campos[1],
-                  d2 = __ldg(means + 3 * i + 2) - c.campos[2];
-      const float il = 1.0f / sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-      const float dir[3] = {d0 * il, d1 * il, d2 * il};
-      const float* sh = s_sh + lane * ROW;
-      float Y[16];
-      sh_eval<DEG>(dir[0], dir[1], dir[2], Y);
-      float rgb[3];
-      uint32_t clamped = 0u;
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch) {
-        float acc = 0.5f;
-#pragma unroll
-        for (int k = 0; k < K; ++k) acc += Y[k] * sh[3 * k + ch];
-        rgb[ch] = fmaxf(acc, 0.0f);
-        clamped |= (acc < 0.0f ? 1u : 0u) << ch;
-      }
-      if (a.ws.shjac) {
-        // per channel: d colour / d direction (the backward's view-direction
-        // term, so it need not read the SH coefficients) and the clamp flag
-        float4* jp = a.ws.shjac + 3 * m;
-        float J[3][3];
-        sh_grad3<DEG>(dir[0], dir[1], dir[2], sh, J);
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch)
-          jp[ch] = make_float4(J[ch][0], J[ch][1], J[ch][2], (clamped >> ch) & 1u ? 1.0f : 0.0f);
-      }
-      float* r3 = reinterpret_cast<float*>(a.ws.rec + 4 * m + 3);
-      r3[0] = rgb[0];
-      r3[1] = rgb[1];
-      r3[2] = rgb[2];
     }
     __syncwarp();
   }
@@ -827,15 +780,12 @@ cudaError_t launch_preprocess_fwd(const PreArgs& a, cudaStream_t st, int sms) {
     return cudaGetLastError();
   }
   const int grid = grid_for(a.g.n, sms);
-  cudaError_t e = launch_sized(preprocess_geom_kernel, a, grid, cams_bytes(a.n_views), st);
-  if (e != cudaSuccess) return e;
-  const int cgrid = grid_for(a.g.n * a.n_views, sms);
-  const size_t smem = sh_stage_bytes(a.g.sh_degree, 1);
-#define SR_DEG_CASE(D)                                                                                   \
-  case D:                                                                                                \
-    if (a.g.dt_sh == SR_F32) return launch_sized(preprocess_colour_kernel<D, SR_F32>, a, cgrid, smem, st);   \
-    if (a.g.dt_sh == SR_BF16) return launch_sized(preprocess_colour_kernel<D, SR_BF16>, a, cgrid, smem, st); \
-    return launch_sized(preprocess_colour_kernel<D, SR_F16>, a, cgrid, smem, st);
+  const size_t smem = cams_bytes(a.n_views) + sh_stage_bytes(a.g.sh_degree, 1);
+#define SR_DEG_CASE(D)                                                                              \
+  case D:                                                                                           \
+    if (a.g.dt_sh == SR_F32) return launch_sized(preprocess_fwd_kernel<D, SR_F32>, a, grid, smem, st);   \
+    if (a.g.dt_sh == SR_BF16) return launch_sized(preprocess_fwd_kernel<D, SR_BF16>, a, grid, smem, st); \
+    return launch_sized(preprocess_fwd_kernel<D, SR_F16>, a, grid, smem, st);
   switch (a.g.sh_degree) {
     SR_DEG_CASE(0)
     SR_DEG_CASE(1)
