@@ -103,6 +103,15 @@ __device__ __forceinline__ uint32_t next_work(uint32_t* counter, uint32_t* s_nex
   return *s_next;
 }
 
+// a finished 32-position blend word: its blends are counted and its highest
+// bit is the pixel's last contributor so far (list position + 1)
+__device__ __forceinline__ void credit(uint32_t w, uint32_t cbase, uint32_t& blended, uint32_t& last) {
+  if (w) {
+    blended += __popc(w);
+    last = cbase + 32u - __clz(w);
+  }
+}
+
 // occupancy target of the forward composite: 5 blocks of 256 threads per SM
 // for one pixel per thread (<= 51 registers), the compiler's choice otherwise
 template <int PX>
@@ -133,6 +142,9 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
     constexpr int Q = (PX + 1) / 2;
     float T[PX], C0[PX], C1[PX], C2[PX];
     float2 T2[Q], D0[Q], D1[Q], D2[Q];
+    // mw: the pixel's blend bits in the current chunk of 32 list positions (the
+    // blend mask word when recorded); the blend count and the last contributor
+    // are taken from each finished word, not per blend
     uint32_t last[PX], stop[PX], mw[PX];
     bool done[PX];
     int active = 0;  // pixels of this thread still compositing
@@ -160,7 +172,8 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
       if (active) {
         for (int jc = 0; jc < cnt; jc += 32) {  // chunks of 32 positions (one mask word)
           const int jend = min(cnt, jc + 32);
-          const uint32_t chunk = (start - range.x + jc) >> 5;
+          const uint32_t cbase = start - range.x + jc;  // list position of the chunk's bit 0
+          const uint32_t chunk = cbase >> 5;
           for (int j = jc; j < jend; ++j) {
             const float4 r0 = s_r0[j], r1 = s_r1[j], r3 = s_r3[j];
             const float4 r2 = MODE == MODE_PLAIN ? r0 : s_r2[j];
@@ -186,6 +199,7 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
                   if (s0) {
                     done[2 * q] = true;
                     stop[2 * q] = start + j + 1;
+                    credit(mw[2 * q], cbase, blended, last[2 * q]);
                     if (REC) mbase[chunk * 256 + pi0 + 2 * q * kTile] = mw[2 * q];
                     al.x = 0.0f;
                     Tn.x = T2[q].x;
@@ -194,6 +208,7 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
                   if (s1) {
                     done[2 * q + 1] = true;
                     stop[2 * q + 1] = start + j + 1;
+                    credit(mw[2 * q + 1], cbase, blended, last[2 * q + 1]);
                     if (REC) mbase[chunk * 256 + pi0 + (2 * q + 1) * kTile] = mw[2 * q + 1];
                     al.y = 0.0f;
                     Tn.y = T2[q].y;
@@ -207,13 +222,8 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
                 D1[q] = fma2(f2(r3.y), w, D1[q]);
                 D2[q] = fma2(f2(r3.z), w, D2[q]);
                 T2[q] = Tn;
-                blended += (uint32_t)c0 + (uint32_t)c1;
-                if (REC) {
-                  mw[2 * q] |= (uint32_t)c0 << (j & 31);
-                  mw[2 * q + 1] |= (uint32_t)c1 << (j & 31);
-                }
-                if (c0) last[2 * q] = start + j + 1 - range.x;
-                if (c1) last[2 * q + 1] = start + j + 1 - range.x;
+                mw[2 * q] |= (uint32_t)c0 << (j & 31);
+                mw[2 * q + 1] |= (uint32_t)c1 << (j & 31);
               }
             } else {
   #pragma unroll
@@ -227,29 +237,27 @@ __global__ void __launch_bounds__(256 / PX, FwdMinBlocks<PX>::value) render_fwd_
                 if (Tn < tstop) {
                   done[p] = true;
                   stop[p] = start + j + 1;
+                  credit(mw[p], cbase, blended, last[p]);
                   if (REC) mbase[chunk * 256 + pi0 + p * kTile] = mw[p];
                   if (--active == 0) goto batch_done;  // the only exit test, off the hot path
                   continue;
                 }
-                ++blended;
-                if (REC) mw[p] |= 1u << (j & 31);
+                mw[p] |= 1u << (j & 31);
                 const float w = __fmul_rn(alpha, T[p]);
                 C0[p] = __fmaf_rn(r3.x, w, C0[p]);
                 C1[p] = __fmaf_rn(r3.y, w, C1[p]);
                 C2[p] = __fmaf_rn(r3.z, w, C2[p]);
                 T[p] = Tn;
-                last[p] = start + j + 1 - range.x;
               }
             }
           }
-          if (REC) {
   #pragma unroll
-            for (int p = 0; p < PX; ++p)
-              if (!done[p]) {
-                mbase[chunk * 256 + pi0 + p * kTile] = mw[p];
-                mw[p] = 0u;
-              }
-          }
+          for (int p = 0; p < PX; ++p)
+            if (!done[p]) {
+              credit(mw[p], cbase, blended, last[p]);
+              if (REC) mbase[chunk * 256 + pi0 + p * kTile] = mw[p];
+              mw[p] = 0u;
+            }
         }
       }
     batch_done:;
