@@ -300,6 +300,7 @@ def run_ours(args):
     out["pairs_replayed_bwd"] = replayed
     out["pairs_blended"] = blended
     out["blends_per_s"] = round(blended / (stage_mean[2] / 1e3), 1)
+    out["pairs_tested_per_s"] = round(tested / (stage_mean[2] / 1e3), 1)
     out["clocks"] = clocks
     out["autotune_ms"] = {"fwd": {str(k): round(v, 4) for k, v in tune["fwd_ms"].items()},
                           "bwd": {str(k): round(v, 4) for k, v in tune["bwd_ms"].items()},
@@ -876,8 +877,40 @@ def run_mixed_5m(args):
                               "batched_ms": round(ms_batched, 2), "recompute_ms": round(ms_recompute, 2),
                               "workspace_bytes_batched": ws_batched, "workspace_bytes_recompute": ws_recompute,
                               "keys": keys_b}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_mixed_5m(cams4k[0], cams[0], ups[0].cpu().numpy(), args.oracle_threads)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def cpu_baseline_mixed_5m(cam4k, cam1080, up, threads=0):
+    """The FP64 oracle on the 5M scene, one view of each part: the first 4K
+    view of the trajectory, forward only (its rate stands for the 32-view
+    trajectory's views/s), and the first 1080p view forward + backward (its
+    rate stands for the 8-view step's views/s).  The oracle reads the FP32
+    SH coefficients the BF16 copies were rounded from: the same arithmetic."""
+    import oracle
+
+    from paper_2605_18334_gb300 import scenes
+
+    oracle.build()
+    if threads:
+        oracle.set_num_threads(threads)
+    sc = scenes.mixed_5m()
+    oc = oracle.camera_from_gl(cam4k)
+    ocfg = oracle.config()
+    t0 = time.perf_counter()
+    pre = oracle.preprocess(sc, oc, ocfg)
+    oracle.render_frame(sc, oc, ocfg, pre=pre)
+    fwd4k = time.perf_counter() - t0
+    del pre
+    _, fb = oracle_frame(sc, cam1080, up)
+    return {"value": round(1.0 / fb, 6), "unit": "views/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"one 1920x1080 view of the 8-view step, forward + backward, and one 3840x2160 view of the "
+                       f"32-view trajectory, forward only, of all {sc.n} Gaussians (FP64, per-pixel footprint lists); "
+                       f"each view's rate stands for its part's views/s"),
+            "fwdbwd_1080p_seconds": round(fb, 2), "fwd_4k_views_per_s": round(1.0 / fwd4k, 6),
+            "fwd_4k_seconds": round(fwd4k, 2)}
 
 
 def main():
