@@ -385,6 +385,10 @@ def run_ours(args):
         out["variants"]["densify"] = densify_step(args, sc, dev, flush)
     if not args.no_e2e:
         out["e2e"] = e2e(args, sc, cam, up, dev, world)
+        if not args.no_variants:
+            # the same end-to-end step with BF16 storage of SH, log-scales and
+            # skew: the host-to-device bytes shrink, the gradients stay FP32
+            out["variants"]["bf16_storage_e2e"] = e2e(args, sc, cam, up, dev, world, storage=torch.bfloat16)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, cam, up, args.oracle_threads)
     if rank == 0:
@@ -643,19 +647,22 @@ def trajectory(args, sc, dev, flush, n_views=64):
     return res
 
 
-def e2e(args, sc, cam, up, dev, world):
+def e2e(args, sc, cam, up, dev, world, storage=None):
     """Same metric through the C ABI with host buffers: every step copies the
     scene and the upstream gradient from pinned host memory, renders forward
     and backward, and reads the image and all gradients back into pinned host
     memory.  The copies run on their own streams (one per direction) into and
     out of double buffers, so step k's transfers overlap the compute of its
-    neighbours; the timed region covers all K steps' copies and compute."""
+    neighbours; the timed region covers all K steps' copies and compute.
+    ``storage``: dtype of the SH, log-scale and skew arrays on the host and
+    the device (their gradients stay FP32)."""
     import torch
 
     from paper_2605_18334_gb300.rasterizer import Config, Gaussians, Rasterizer
 
     fields = ("means", "log_scales", "quats", "opacity_logits", "skew", "sh")
-    host = Gaussians.from_scene(sc, device="cpu")
+    st = storage or torch.float32
+    host = Gaussians.from_scene(sc, device="cpu", sh_dtype=st, scale_dtype=st, skew_dtype=st)
     for k in fields:
         setattr(host, k, getattr(host, k).pin_memory())
     up_h = torch.as_tensor(up).reshape(-1).contiguous().pin_memory()
