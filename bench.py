@@ -647,41 +647,71 @@ def trajectory(args, sc, dev, flush, n_views=64):
     return res
 
 
+def _layout(specs):
+    """Byte offsets of (name, shape, dtype) fields packed into one flat buffer,
+    each on a 256-byte boundary, and the buffer's size."""
+    import torch
+
+    offs, off = [], 0
+    for _, shape, dt in specs:
+        off = (off + 255) & ~255
+        n = math.prod(shape) * torch.empty((), dtype=dt).element_size()
+        offs.append((off, n))
+        off += n
+    return offs, off
+
+
+def _carve(buf, specs):
+    """Views of the flat uint8 buffer ``buf`` laid out by ``_layout``."""
+    offs, _ = _layout(specs)
+    return {name: buf[o:o + n].view(dt).view(shape) for (name, shape, dt), (o, n) in zip(specs, offs)}
+
+
 def e2e(args, sc, cam, up, dev, world, storage=None):
     """Same metric through the C ABI with host buffers: every step copies the
     scene and the upstream gradient from pinned host memory, renders forward
     and backward, and reads the image and all gradients back into pinned host
-    memory.  The copies run on their own streams (one per direction) into and
-    out of double buffers, so step k's transfers overlap the compute of its
-    neighbours; the timed region covers all K steps' copies and compute.
-    ``storage``: dtype of the SH, log-scale and skew arrays on the host and
-    the device (their gradients stay FP32)."""
+    memory.  Inputs and results each live in one flat buffer per side (the
+    attribute, image and gradient tensors are views of it), so a step is one
+    host-to-device and one device-to-host copy.  The copies run on their own
+    streams (one per direction) into and out of double buffers, so step k's
+    transfers overlap the compute of its neighbours; the timed region covers
+    all K steps' copies and compute.  ``storage``: dtype of the SH, log-scale
+    and skew arrays on the host and the device (their gradients stay FP32)."""
     import torch
 
     from paper_2605_18334_gb300.rasterizer import Config, Gaussians, Rasterizer
 
     fields = ("means", "log_scales", "quats", "opacity_logits", "skew", "sh")
     st = storage or torch.float32
-    host = Gaussians.from_scene(sc, device="cpu", sh_dtype=st, scale_dtype=st, skew_dtype=st)
+    src = Gaussians.from_scene(sc, device="cpu", sh_dtype=st, scale_dtype=st, skew_dtype=st)
+    up_t = torch.as_tensor(up).reshape(-1).contiguous()
+    in_specs = [(k, tuple(getattr(src, k).shape), getattr(src, k).dtype) for k in fields]
+    in_specs.append(("upstream", tuple(up_t.shape), torch.float32))
+    _, in_bytes = _layout(in_specs)
+
+    def gaussians(v):
+        return Gaussians(*(v[k] for k in fields), src.sh_degree)
+
+    host_in = torch.empty(in_bytes, dtype=torch.uint8).pin_memory()
+    hv = _carve(host_in, in_specs)
     for k in fields:
-        setattr(host, k, getattr(host, k).pin_memory())
-    up_h = torch.as_tensor(up).reshape(-1).contiguous().pin_memory()
-    gbuf = [Gaussians(*(torch.empty_like(getattr(host, k), device=dev) for k in fields), host.sh_degree)
-            for _ in range(2)]
-    dbuf = [torch.empty_like(up_h, device=dev) for _ in range(2)]
+        hv[k].copy_(getattr(src, k))
+    hv["upstream"].copy_(up_t)
+    dev_in = [torch.empty(in_bytes, dtype=torch.uint8, device=dev) for _ in range(2)]
+    dv = [_carve(b, in_specs) for b in dev_in]
     for b in range(2):  # both buffers hold a real frame before anything runs on them
-        for k in fields:
-            getattr(gbuf[b], k).copy_(getattr(host, k))
-        dbuf[b].copy_(up_h)
-    r = Rasterizer(gbuf[0], [cam], Config(), key_capacity=int(12 * args.n))
-    r.autotune(gbuf[0], dbuf[0])
-    img_d = [torch.empty_like(r.images) for _ in range(2)]
-    img_h = [torch.empty(r.images.numel(), dtype=torch.float32).pin_memory() for _ in range(2)]
-    grad_h = [{k: torch.empty(getattr(host, k).shape, dtype=torch.float32).pin_memory() for k in fields}
-              for _ in range(2)]
-    gout = [None, None]
-    h2d = sum(getattr(host, k).numel() * getattr(host, k).element_size() for k in fields) + up_h.numel() * 4
-    d2h = img_h[0].numel() * 4 + sum(t.numel() * 4 for t in grad_h[0].values())
+        dev_in[b].copy_(host_in)
+    r = Rasterizer(gaussians(dv[0]), [cam], Config(), key_capacity=int(12 * args.n))
+    r.autotune(gaussians(dv[0]), dv[0]["upstream"])
+    out_specs = [("image", tuple(r.images.shape), torch.float32)]
+    out_specs += [(k, tuple(getattr(src, k).shape), torch.float32) for k in fields]
+    _, out_bytes = _layout(out_specs)
+    dev_out = [torch.empty(out_bytes, dtype=torch.uint8, device=dev) for _ in range(2)]
+    ov = [_carve(b, out_specs) for b in dev_out]
+    gout = [{k: ov[i][k] for k in fields} | {"split_dir": None} for i in range(2)]
+    host_out = [torch.empty(out_bytes, dtype=torch.uint8).pin_memory() for _ in range(2)]
+    h2d, d2h = in_bytes, out_bytes
     comp = torch.cuda.current_stream()
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
     ev_in = [torch.cuda.Event() for _ in range(2)]    # inputs of buffer i landed
@@ -693,24 +723,21 @@ def e2e(args, sc, cam, up, dev, world, storage=None):
     def copy_in(i):
         with torch.cuda.stream(s_in):
             s_in.wait_event(ev_done[i])
-            for k in fields:
-                getattr(gbuf[i], k).copy_(getattr(host, k), non_blocking=True)
-            dbuf[i].copy_(up_h, non_blocking=True)
+            dev_in[i].copy_(host_in, non_blocking=True)
             ev_in[i].record(s_in)
 
     def compute(i):
         comp.wait_event(ev_in[i])
         comp.wait_event(ev_out[i])
-        r.forward(gbuf[i], out=img_d[i], sync=False)  # no host stall per frame; capacity checked after the run
-        gout[i] = r.backward(gbuf[i], dbuf[i], out=gout[i])
+        g = gaussians(dv[i])
+        r.forward(g, out=ov[i]["image"], sync=False)  # no host stall per frame; capacity checked after the run
+        r.backward(g, dv[i]["upstream"], out=gout[i])
         ev_done[i].record(comp)
 
     def copy_out(i):
         with torch.cuda.stream(s_out):
             s_out.wait_event(ev_done[i])
-            img_h[i].copy_(img_d[i], non_blocking=True)
-            for k in fields:
-                grad_h[i][k].copy_(gout[i][k], non_blocking=True)
+            host_out[i].copy_(dev_out[i], non_blocking=True)
             ev_out[i].record(s_out)
 
     def run(steps):
@@ -731,7 +758,7 @@ def e2e(args, sc, cam, up, dev, world, storage=None):
     r.check()  # the frames (all of the same scene) fitted the key capacity; raises otherwise
     return {"value": round(world * K / dt, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h),
-            "copies": "double-buffered, overlapped with compute"}
+            "copies": "one flat buffer per direction and step, double-buffered, overlapped with compute"}
 
 
 # ---------------------------------------------------------------------------
