@@ -224,7 +224,7 @@ sr_status sr_plan_init(sr_plan* p, const sr_config* cfg, const sr_gaussians* g, 
   sizes[WS_MASK] = (p->forward_only || p->recompute_keys)
                        ? 0
                        : sizeof(uint32_t) * 256 * (size_t)(key_capacity / 32 + tb + 1);
-  sizes[WS_TILE_ORDER] = sizeof(uint32_t) * ((size_t)tb + 130);
+  sizes[WS_TILE_ORDER] = sizeof(uint32_t) * ((size_t)tb + kOrderWords);
   sizes[WS_SHJAC] = p->forward_only ? 0 : sizeof(float4) * 3 * (size_t)m;
   size_t off = 0;
   for (int k = 0; k < WS_NUM_SLOTS; ++k) {
@@ -364,7 +364,7 @@ static RenderArgs render_args(const sr_plan* p, const sr_config* cfg, void* ws) 
   r.px_bwd = cfg->bwd_pixels_per_thread > 0 ? cfg->bwd_pixels_per_thread : 2;
   r.n_order = (uint32_t)p->total_tiles;
   r.persistent = 0;
-  r.work = w.tile_order + p->total_tiles + 128;  // [0]: forward counter, [1]: backward counter
+  r.work = w.tile_order + p->total_tiles + 2 * kOrderBuckets;  // [0]: forward counter, [1]: backward counter
   r.sms = device_sms();
   r.blocks_fwd = cfg->fwd_blocks_per_sm;
   r.blocks_bwd = cfg->bwd_blocks_per_sm;

@@ -825,15 +825,20 @@ cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms) {
 }
 
 // ---------------------------------------------------------------------------
-// Composite order: tiles by descending length of their key lists (log2
-// buckets; empty tiles last), so the heaviest tiles start first and the last
-// wave of the composites holds light ones.  Counters (cnt[64], cursor[64])
-// follow the order array and start at zero.
+// Composite order: tiles by descending length of their key lists, in
+// quarter-octave buckets (four per power of two; empty tiles last), so the
+// heaviest tiles start first and the last wave of the composites holds light
+// ones.  Counters (cnt[kOrderBuckets], cursor[kOrderBuckets]) follow the
+// order array and start at zero.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int tile_bucket(const uint2* ranges, int64_t t) {
   const uint2 r = tile_range(ranges, t);
   const uint32_t len = r.y - r.x;
-  return len ? __clz(len) : 32;  // 0 for the longest lists
+  if (!len) return kOrderBuckets - 1;
+  const int e = 31 - __clz(len);  // floor(log2(len))
+  // the two bits below the leading one (zero-filled below 4)
+  const uint32_t frac = e >= 2 ? (len >> (e - 2)) & 3u : (len << (2 - e)) & 3u;
+  return 4 * (31 - e) + 3 - (int)frac;  // 0 for the longest lists
 }
 
 // one block for up to kOrderOneBlock tiles: count, scan and scatter in
@@ -842,14 +847,14 @@ constexpr int64_t kOrderOneBlock = 16384;
 __global__ void __launch_bounds__(1024) tile_order_block_kernel(const uint2* __restrict__ ranges, int64_t tiles,
                                                                 uint32_t* __restrict__ order) {
   pdl_entry();
-  __shared__ uint32_t s_cnt[33], s_cur[33];
-  if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0u;
+  __shared__ uint32_t s_cnt[kOrderBuckets], s_cur[kOrderBuckets];
+  for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) s_cnt[b] = 0u;
   __syncthreads();
   for (int64_t t = threadIdx.x; t < tiles; t += blockDim.x) atomicAdd(&s_cnt[tile_bucket(ranges, t)], 1u);
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t run = 0;
-    for (int b = 0; b < 33; ++b) {
+    for (int b = 0; b < kOrderBuckets; ++b) {
       s_cur[b] = run;
       run += s_cnt[b];
     }
@@ -862,13 +867,14 @@ __global__ void __launch_bounds__(1024) tile_order_block_kernel(const uint2* __r
 __global__ void __launch_bounds__(256) tile_order_count_kernel(const uint2* __restrict__ ranges, int64_t tiles,
                                                                uint32_t* __restrict__ cnt) {
   pdl_entry();
-  __shared__ uint32_t s_cnt[33];
-  if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0u;
+  __shared__ uint32_t s_cnt[kOrderBuckets];
+  for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) s_cnt[b] = 0u;
   __syncthreads();
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += (int64_t)gridDim.x * blockDim.x)
     atomicAdd(&s_cnt[tile_bucket(ranges, t)], 1u);
   __syncthreads();
-  if (threadIdx.x < 33 && s_cnt[threadIdx.x]) atomicAdd(&cnt[threadIdx.x], s_cnt[threadIdx.x]);
+  for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x)
+    if (s_cnt[b]) atomicAdd(&cnt[b], s_cnt[b]);
 }
 
 __global__ void __launch_bounds__(256) tile_order_scatter_kernel(const uint2* __restrict__ ranges, int64_t tiles,
@@ -876,10 +882,10 @@ __global__ void __launch_bounds__(256) tile_order_scatter_kernel(const uint2* __
                                                                  uint32_t* __restrict__ cursor,
                                                                  uint32_t* __restrict__ order) {
   pdl_entry();
-  __shared__ uint32_t s_base[33];
+  __shared__ uint32_t s_base[kOrderBuckets];
   if (threadIdx.x == 0) {
     uint32_t run = 0;
-    for (int b = 0; b < 33; ++b) {
+    for (int b = 0; b < kOrderBuckets; ++b) {
       s_base[b] = run;
       run += cnt[b];
     }
@@ -921,12 +927,12 @@ cudaError_t launch_bin_phase2(const BinArgs& a, const int* run, long long keys_k
     count_launches(1);
   } else {
     uint32_t* counters = a.ws.tile_order + a.total_tiles;
-    if ((e = cudaMemsetAsync(counters, 0, sizeof(uint32_t) * 128, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(counters, 0, sizeof(uint32_t) * 2 * kOrderBuckets, st)) != cudaSuccess) return e;
     const unsigned tgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((a.total_tiles + 255) / 256, 1024));
     launch_pdl(tile_order_count_kernel, dim3(tgrid), dim3(256), 0, st, (const uint2*)a.ws.ranges, a.total_tiles,
                counters);
     launch_pdl(tile_order_scatter_kernel, dim3(tgrid), dim3(256), 0, st, (const uint2*)a.ws.ranges, a.total_tiles,
-               (const uint32_t*)counters, counters + 64, a.ws.tile_order);
+               (const uint32_t*)counters, counters + kOrderBuckets, a.ws.tile_order);
     count_launches(2);
   }
   return cudaGetLastError();

@@ -37,7 +37,7 @@ enum WsSlot {
   WS_D2,           // float[M][16] per-(view, Gaussian) 2D gradients
   WS_FOOT,         // float4[M][4] footprint constants or packed row spans (row_tile_span)
   WS_MASK,         // uint32_t[(cap/32 + tiles + 1) * 256] per-pixel blend masks (see render.cu)
-  WS_TILE_ORDER,   // uint32_t[tiles] composite order (longest key lists first) + uint32_t[2][64] counters
+  WS_TILE_ORDER,   // uint32_t[tiles] composite order (longest key lists first) + uint32_t[kOrderWords] counters
                    // of the ordering + the tile counters of persistent forward and backward composites
   WS_SHJAC,        // float4[M][3] d colour / d view direction (3x3) and the colour clamp bits (backward only)
   WS_NUM_SLOTS
@@ -55,6 +55,8 @@ constexpr int kScanItems = 16;
 constexpr int kScanBlock = kScanThreads * kScanItems;
 constexpr int kTile = 16;              // tile edge in pixels
 constexpr int kD2Stride = 16;          // floats per 2D-gradient record
+constexpr int kOrderBuckets = 129;     // composite-order buckets: 4 per power of two of 32 bits, + empty
+constexpr int kOrderWords = 2 * kOrderBuckets + 2;  // order counters, then the composites' work counters
 
 // status word flags
 constexpr uint32_t kStatusCapacity = 1u;
