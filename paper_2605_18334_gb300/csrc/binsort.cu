@@ -826,7 +826,7 @@ cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms) {
 
 // ---------------------------------------------------------------------------
 // Composite order: tiles by descending length of their key lists, in
-// quarter-octave buckets (four per power of two; empty tiles last), so the
+// buckets of 1/2^kOrderSubBits of a power of two (empty tiles last), so the
 // heaviest tiles start first and the last wave of the composites holds light
 // ones.  Counters (cnt[kOrderBuckets], cursor[kOrderBuckets]) follow the
 // order array and start at zero.
@@ -835,10 +835,34 @@ __device__ __forceinline__ int tile_bucket(const uint2* ranges, int64_t t) {
   const uint2 r = tile_range(ranges, t);
   const uint32_t len = r.y - r.x;
   if (!len) return kOrderBuckets - 1;
+  constexpr int S = 1 << kOrderSubBits;
   const int e = 31 - __clz(len);  // floor(log2(len))
-  // the two bits below the leading one (zero-filled below 4)
-  const uint32_t frac = e >= 2 ? (len >> (e - 2)) & 3u : (len << (2 - e)) & 3u;
-  return 4 * (31 - e) + 3 - (int)frac;  // 0 for the longest lists
+  // the kOrderSubBits bits below the leading one (zero-filled below 2^kOrderSubBits)
+  const uint32_t frac = e >= kOrderSubBits ? (len >> (e - kOrderSubBits)) & (S - 1u)
+                                           : (len << (kOrderSubBits - e)) & (S - 1u);
+  return S * (31 - e) + S - 1 - (int)frac;  // 0 for the longest lists
+}
+
+// exclusive offsets base[b] of the bucket counts cnt[b], by a block of NT threads
+template <int NT>
+__device__ __forceinline__ void bucket_offsets(const uint32_t* cnt, uint32_t* base, unsigned long long* s_warp) {
+  constexpr int K = (kOrderBuckets + NT - 1) / NT;
+  uint32_t c[K];
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int b = (int)threadIdx.x * K + k;
+    c[k] = b < kOrderBuckets ? cnt[b] : 0u;
+    sum += c[k];
+  }
+  unsigned long long total;
+  unsigned long long run = block_exclusive_u64<NT>(sum, s_warp, total);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int b = (int)threadIdx.x * K + k;
+    if (b < kOrderBuckets) base[b] = (uint32_t)run;
+    run += c[k];
+  }
 }
 
 // one block for up to kOrderOneBlock tiles: count, scan and scatter in
@@ -850,15 +874,10 @@ __global__ void __launch_bounds__(1024) tile_order_block_kernel(const uint2* __r
   __shared__ uint32_t s_cnt[kOrderBuckets], s_cur[kOrderBuckets];
   for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) s_cnt[b] = 0u;
   __syncthreads();
+  __shared__ unsigned long long s_warp[32];
   for (int64_t t = threadIdx.x; t < tiles; t += blockDim.x) atomicAdd(&s_cnt[tile_bucket(ranges, t)], 1u);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t run = 0;
-    for (int b = 0; b < kOrderBuckets; ++b) {
-      s_cur[b] = run;
-      run += s_cnt[b];
-    }
-  }
+  bucket_offsets<1024>(s_cnt, s_cur, s_warp);
   __syncthreads();
   for (int64_t t = threadIdx.x; t < tiles; t += blockDim.x)
     order[atomicAdd(&s_cur[tile_bucket(ranges, t)], 1u)] = (uint32_t)t;
@@ -883,13 +902,8 @@ __global__ void __launch_bounds__(256) tile_order_scatter_kernel(const uint2* __
                                                                  uint32_t* __restrict__ order) {
   pdl_entry();
   __shared__ uint32_t s_base[kOrderBuckets];
-  if (threadIdx.x == 0) {
-    uint32_t run = 0;
-    for (int b = 0; b < kOrderBuckets; ++b) {
-      s_base[b] = run;
-      run += cnt[b];
-    }
-  }
+  __shared__ unsigned long long s_warp[8];
+  bucket_offsets<256>(cnt, s_base, s_warp);
   __syncthreads();
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += (int64_t)gridDim.x * blockDim.x) {
     const int b = tile_bucket(ranges, t);

@@ -55,7 +55,8 @@ constexpr int kScanItems = 16;
 constexpr int kScanBlock = kScanThreads * kScanItems;
 constexpr int kTile = 16;              // tile edge in pixels
 constexpr int kD2Stride = 16;          // floats per 2D-gradient record
-constexpr int kOrderBuckets = 129;     // composite-order buckets: 4 per power of two of 32 bits, + empty
+constexpr int kOrderSubBits = 4;       // composite-order buckets per power of two: 2^kOrderSubBits
+constexpr int kOrderBuckets = 32 * (1 << kOrderSubBits) + 1;  // over 32 bits, + empty
 constexpr int kOrderWords = 2 * kOrderBuckets + 2;  // order counters, then the composites' work counters
 
 // status word flags
