@@ -522,7 +522,7 @@ struct SortSmem {
   uint32_t val[kSortPart];
   uint32_t whist[kSortThreads / 32][256];
   uint32_t lstart[256];
-  unsigned long long gofs[256];
+  uint32_t gofs[256];  // modulo 2^32: positions stay below 2^32
   unsigned long long warp_tot[kSortThreads / 32];
   uint32_t part;
 };
@@ -662,7 +662,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(PassArgs<KEY>
     st_relaxed_u64(lb + d, kFlagInc | (excl + tot));
   }
   // global position of local element i of digit dg: gofs[dg] + i
-  sm.gofs[d] = (unsigned long long)a.digit_base[d] + excl - sm.lstart[d];
+  sm.gofs[d] = (uint32_t)((unsigned long long)a.digit_base[d] + excl - sm.lstart[d]);
   __syncthreads();
 
   // scatter in block-local order, so each digit's run goes out contiguously
@@ -671,7 +671,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(PassArgs<KEY>
   for (uint32_t i = tid; i < count; i += kSortThreads) {
     const KEY k = sm.key[i];
     const uint32_t dg = (uint32_t)(k >> a.shift) & dmask;
-    const unsigned long long g = sm.gofs[dg] + i;
+    const uint32_t g = sm.gofs[dg] + i;
     if (g < kn) {  // always true unless a look-back gave up
       const uint32_t v = sm.val[i];
       a.keys_out[g] = a.out_gather ? (KEY)a.out_gather[v] : k;
