@@ -784,7 +784,7 @@ cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms) {
   if (m > 0) {
     // depth sort of the records (values: record indices)
     // one block per SM: each bin's count goes to global memory from few blocks
-    launch_pdl(histogram_kernel<uint32_t>, dim3(clamp_grid((um + 255) / 256, sms, 1)), dim3(256), 0, st,
+    launch_pdl(histogram_kernel<uint32_t>, dim3(clamp_grid((um + 255) / 256, sms, 2)), dim3(256), 0, st,
                (const uint32_t*)a.ws.dkey[0], (const unsigned long long*)nullptr, um, (int)kDepthPasses, a.ws.hist);
     launch_pdl(hist_scan_kernel, dim3(kDepthPasses), dim3(256), 0, st, a.ws.hist, a.ws.status->pass_trivial,
                (const unsigned long long*)nullptr, um);
