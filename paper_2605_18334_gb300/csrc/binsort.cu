@@ -783,8 +783,8 @@ cudaError_t launch_bin_phase1(const BinArgs& a, cudaStream_t st, int sms) {
   const uint32_t* cnt_sorted = a.ws.dkey[0];
   if (m > 0) {
     // depth sort of the records (values: record indices)
-    // two blocks per SM: each bin's count goes to global memory from few blocks
-    // (one per SM measured slower, and so did the onesweep passes at 5 blocks per SM)
+    // two blocks per SM (one measured slower): each bin's count goes to global
+    // memory from few blocks
     launch_pdl(histogram_kernel<uint32_t>, dim3(clamp_grid((um + 255) / 256, sms, 2)), dim3(256), 0, st,
                (const uint32_t*)a.ws.dkey[0], (const unsigned long long*)nullptr, um, (int)kDepthPasses, a.ws.hist);
     launch_pdl(hist_scan_kernel, dim3(kDepthPasses), dim3(256), 0, st, a.ws.hist, a.ws.status->pass_trivial,
