@@ -443,7 +443,7 @@ class Rasterizer:
     # -- read-only views of the workspace (tests and diagnostics) ---------
     # slot numbers of the workspace layout (csrc/common.cuh, enum WsSlot)
     _S_STATUS, _S_REC, _S_DEPTH, _S_RECT, _S_NTOUCH = 0, 2, 3, 8, 9
-    _S_KEYS0, _S_VALS0, _S_RANGES, _S_D2, _S_MASK = 12, 14, 19, 20, 22
+    _S_KEYS0, _S_VALS0, _S_RANGES, _S_D2, _S_MASK, _S_TILE_ORDER = 12, 14, 19, 20, 22, 23
 
     def _slot(self, k: int, nbytes: int) -> torch.Tensor:
         off = int(self.plan.off[k])
@@ -484,6 +484,12 @@ class Rasterizer:
         raw = self._slot(self._S_RANGES, 8 * t).view(torch.int32).view(t, 2).to(torch.int64) & 0xFFFFFFFF
         start = torch.where(raw[:, 1] > 0, (~raw[:, 0]) & 0xFFFFFFFF, torch.zeros_like(raw[:, 0]))
         return torch.stack([start, raw[:, 1]], 1)
+
+    def tile_order(self) -> torch.Tensor:
+        """[total_tiles] int64: the order in which the last frame's composites
+        take the tiles (heaviest key lists first)."""
+        t = int(self.plan.total_tiles)
+        return self._slot(self._S_TILE_ORDER, 4 * t).view(torch.int32).to(torch.int64) & 0xFFFFFFFF
 
     def blend_masks(self) -> torch.Tensor:
         """The last forward's per-pixel blend masks (int32 words; layout in

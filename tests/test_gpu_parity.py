@@ -614,14 +614,50 @@ def test_unbounded_1m_1080p_in_the_bench_launch_configuration():
     compare_grads(gr, oracle_grads(r, sc, [cam], Config(), [up]), GRAD_FIELDS, label="unbounded_1m_1080p")
 
 
+def order_bucket(length: np.ndarray) -> np.ndarray:
+    """Bucket of a key-list length in the composites' tile order: 16 buckets
+    per power of two, heaviest first, empty lists last (the rule the order
+    kernels implement)."""
+    length = np.asarray(length, np.int64)
+    e = np.floor(np.log2(np.maximum(length, 1))).astype(np.int64)
+    frac = np.where(e >= 4, (length >> np.maximum(e - 4, 0)) & 15, (length << np.maximum(4 - e, 0)) & 15)
+    return np.where(length > 0, 16 * (31 - e) + 15 - frac, 16 * 32)
+
+
+def check_tile_order(r):
+    """The composites' tile order is a permutation of every tile, with bucket
+    numbers that never decrease along it (heaviest key lists first)."""
+    order = r.tile_order().cpu().numpy()
+    t = int(r.plan.total_tiles)
+    assert np.array_equal(np.sort(order), np.arange(t))
+    rng = r.ranges().cpu().numpy()
+    b = order_bucket(rng[:, 1] - rng[:, 0])[order]
+    assert np.all(np.diff(b) >= 0)
+    return b
+
+
+def test_composite_order_is_a_bucketed_permutation_of_the_tiles():
+    """One 1280x720 view (3,600 tiles, the one-block ordering): the order
+    holds every tile once, heaviest key lists first; the bucket rule itself
+    is checked at the edges of its ranges."""
+    assert list(order_bucket([0, 1, 2, 3, 15, 16, 17, 31, 32, 1 << 20])) == [
+        512, 16 * 31 + 15, 16 * 30 + 15, 16 * 30 + 7, 16 * 28 + 1, 16 * 27 + 15, 16 * 27 + 14, 16 * 27, 16 * 26 + 15,
+        16 * 11 + 15]
+    sc = scenes.cluster()
+    r, _ = gpu_forward(sc, [scenes.identity_camera(1280, 720)])
+    b = check_tile_order(r)
+    assert len(np.unique(b)) > 16  # the frame spreads over many buckets
+
+
 def test_composite_order_over_many_tiles():
     """Nine 1080p views (73,440 tiles, past the one-block ordering of the
     composites' tile order): every view's keys and pixels against the
-    oracle."""
+    oracle, and the order a bucketed permutation of every tile."""
     sc = scenes.unbounded(seed=21, n=3000)
     cams = scenes.trajectory_cameras(9, resolutions=((1920, 1080),))
     r, _ = gpu_forward(sc, cams)
     assert int(r.plan.total_tiles) > 65536
+    check_tile_order(r)
     for v in range(len(cams)):
         check_view(r, sc, cams, v, Config(), label="nine_1080p")
 
