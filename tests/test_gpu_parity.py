@@ -394,6 +394,24 @@ def test_backward_cluster_100k_dense_upstream():
     compare_grads(gr, og, GRAD_FIELDS, label="cluster_100k_720p")
 
 
+def test_4k_view_of_the_mixed_scene_law_full_frame_and_backward():
+    """One 3840x2160 view (32,400 tiles: two tile-id passes and the
+    many-tile composite order) of 200k Gaussians of the 5M scene's law (half
+    the skew vectors exactly zero): every key and every pixel against the
+    oracle, then an upstream gradient at every pixel and channel with every
+    gradient element within its bound."""
+    sc = scenes.unbounded(seed=5, n=200_000, skew_sigma=2.0, zero_skew_fraction=0.5)
+    cams = scenes.trajectory_cameras(32, resolutions=((3840, 2160),))[:1]
+    r, g = gpu_forward(sc, cams)
+    assert int(r.plan.total_tiles) == 240 * 135
+    check_tile_order(r)
+    check_view(r, sc, cams, 0, Config(), label="mixed_law_200k_4k")
+    up = scenes.upstream_grad(9, 2160, 3840)
+    gr = r.backward(g, torch.as_tensor(up).cuda().reshape(-1).contiguous())
+    og = oracle_grads(r, sc, cams, Config(), [up])
+    compare_grads(gr, og, GRAD_FIELDS, label="mixed_law_200k_4k")
+
+
 def test_backward_batched_views_sum():
     """Gradients of a multi-view plan are the sum over views."""
     sc = scenes.cluster(seed=12, n=3000, sh_degree=1)
