@@ -567,19 +567,19 @@ __global__ void __launch_bounds__(kPreThreads, 4) preprocess_bwd_kernel(BwdArgs 
     if (lane < cnt) {
     float g_mu[3] = {0, 0, 0}, g_ls[3] = {0, 0, 0}, g_q[4] = {0, 0, 0, 0}, g_eta[3] = {0, 0, 0},
           g_dsp[3] = {0, 0, 0}, g_l1 = 0.0f, g_l2 = 0.0f, g_abs = 0.0f, g_depth = 0.0f;
-    bool loaded = false;
+    // the attributes and the first view's tile count and 2D gradients are
+    // loaded together (one memory latency; the gradients of a record that
+    // touches no tile are read and dropped)
     Attr A;
+    load_attr(a.g, i, has_split, A);
     for (int v = 0; v < a.n_views; ++v) {
       const int64_t m = (int64_t)v * n + i;
-      if (a.ws.ntouch[m] == 0) continue;
       const float4* d2p = reinterpret_cast<const float4*>(a.ws.d2 + kD2Stride * m);
+      const uint32_t nt = a.ws.ntouch[m];
       const float4 q0 = d2p[0], q1 = d2p[1], q2 = d2p[2], q3 = d2p[3];
+      if (nt == 0) continue;
       const float gd[16] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w,
                             q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, q3.z, q3.w};
-      if (!loaded) {
-        load_attr(a.g, i, has_split, A);
-        loaded = true;
-      }
       const sr_camera& c = s_cams[v];
       Proj P;
       project(A, c, a.cfg, two, has_split, P);
