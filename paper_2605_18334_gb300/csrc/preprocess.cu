@@ -567,9 +567,9 @@ __global__ void __launch_bounds__(kPreThreads, 4) preprocess_bwd_kernel(BwdArgs 
     if (lane < cnt) {
     float g_mu[3] = {0, 0, 0}, g_ls[3] = {0, 0, 0}, g_q[4] = {0, 0, 0, 0}, g_eta[3] = {0, 0, 0},
           g_dsp[3] = {0, 0, 0}, g_l1 = 0.0f, g_l2 = 0.0f, g_abs = 0.0f, g_depth = 0.0f;
-    // the attributes and the first view's tile count and 2D gradients are
-    // loaded together (one memory latency; the gradients of a record that
-    // touches no tile are read and dropped)
+    // the attributes, and each view's tile count, 2D gradients and colour
+    // Jacobian, are loaded together (one memory latency; what a record that
+    // touches no tile loads is dropped)
     Attr A;
     load_attr(a.g, i, has_split, A);
     for (int v = 0; v < a.n_views; ++v) {
@@ -577,6 +577,8 @@ __global__ void __launch_bounds__(kPreThreads, 4) preprocess_bwd_kernel(BwdArgs 
       const float4* d2p = reinterpret_cast<const float4*>(a.ws.d2 + kD2Stride * m);
       const uint32_t nt = a.ws.ntouch[m];
       const float4 q0 = d2p[0], q1 = d2p[1], q2 = d2p[2], q3 = d2p[3];
+      const float4* jp = a.ws.shjac + 3 * m;
+      const float4 J3[3] = {jp[0], jp[1], jp[2]};  // d colour_ch / d direction, clamp flag
       if (nt == 0) continue;
       const float gd[16] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w,
                             q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, q3.z, q3.w};
@@ -591,11 +593,10 @@ __global__ void __launch_bounds__(kPreThreads, 4) preprocess_bwd_kernel(BwdArgs 
       // themselves are not needed (d colour / d coefficient is Y)
       float Y[16];
       sh_eval<DEG>(P.dir[0], P.dir[1], P.dir[2], Y);
-      const float4* jp = a.ws.shjac + 3 * m;
       float gdir[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
-        const float4 J = jp[ch];  // d colour_ch / d direction, clamp flag
+        const float4 J = J3[ch];
         const float gc_ = J.w != 0.0f ? 0.0f : gd[G_R + ch];
 #pragma unroll
         for (int k = 0; k < K; ++k) gsh[3 * k + ch] += Y[k] * gc_;
