@@ -344,8 +344,11 @@ __device__ __forceinline__ void stage_sh(const void* sh, int64_t base, int cnt, 
   }
 }
 
+// 4 blocks per SM (up to 128 registers): room to hold the attributes while the
+// SH tile's loads are in flight, without spills (5 blocks at 96 registers spill
+// and wait on the two loads one after the other)
 template <int DEG, int DT_SH>
-__global__ void __launch_bounds__(kPreThreads, 5) preprocess_fwd_kernel(PreArgs a) {
+__global__ void __launch_bounds__(kPreThreads, 4) preprocess_fwd_kernel(PreArgs a) {
   pdl_entry();
   constexpr int K = (DEG + 1) * (DEG + 1);
   constexpr int K3 = 3 * K, ROW = K3 + 1;
@@ -366,13 +369,15 @@ __global__ void __launch_bounds__(kPreThreads, 5) preprocess_fwd_kernel(PreArgs 
   for (int64_t base = ((int64_t)blockIdx.x * kPreWarps + warp) * 32; base < n;
        base += (int64_t)gridDim.x * kPreWarps * 32) {
     const int cnt = (int)(n - base < 32 ? n - base : 32);
+    const int64_t i = base + lane;
+    // the attribute loads go out before the SH loads, so both wait on one
+    // memory latency (the SH tile's stores and the warp barrier come after)
+    Attr A;
+    if (lane < cnt) load_attr(a.g, i, has_split, A);
     stage_sh<K3, DT_SH>(a.g.sh, base, cnt, s_sh, lane);
     __syncwarp();
-    const int64_t i = base + lane;
     const float* sh = s_sh + lane * ROW;
     if (lane < cnt) {
-    Attr A;
-    load_attr(a.g, i, has_split, A);
 
     for (int v = 0; v < a.n_views; ++v) {
       const sr_camera& c = s_cams[v];
